@@ -49,7 +49,7 @@ class Params(C.Structure):
         (n, C.c_double) for n in (
             "hard_x", "hard_y", "hard_z", "wheel_r", "k_susp", "c_susp", "rest_len", "wheel_inertia",
             "steer_inertia", "theta_max", "kp", "kd", "tau_steer_max", "tau_drive", "tau_brk_f",
-            "tau_brk_r", "lambda_yaw", "lambda_lat", "u_z_min", "k_contact", "c_contact", "wheelbase",
+            "tau_brk_r", "lambda_yaw", "lambda_lat", "u_z_min", "k_contact", "c_contact", "damp_ramp", "wheelbase",
             "goal_radius", "w_goal", "w_collision", "w_crash", "w_lane_forb", "w_progress",
             "progress_clip", "w_lane", "lane_sigma", "lane_wh", "w_offroad", "offroad_lat",
             "offroad_dist", "w_idle", "idle_speed", "ttc_alpha_v", "ttc_pmax_v", "ttc_floor",

@@ -67,6 +67,7 @@ void or_default_params(or_params* P) {
     P->u_z_min = 0.05;                 /* R12                                                   */
     P->k_contact = 1.0e6;              /* R20 */
     P->c_contact = 1.6e4;
+    P->damp_ramp = 0.01;               /* R13b, R20: dampers ramp in over 1 cm          */
     P->wheelbase = 2.6;
     /* App. G Tab. app_reward_terms */
     P->goal_radius = 3.0;   P->w_goal = 45.0;  P->w_collision = 6.0;  P->w_crash = 10.0;
@@ -346,7 +347,9 @@ static void body_substep(const or_params* P, double* f, const double* act, const
         double wr[3];
         cross3(w, rb, wr);
         double xdot = -(v[2] + wr[2]) / u[2];                  /* R14 */
-        N[i] = fmax(0.0, P->k_susp * x + P->c_susp * xdot);
+        /* R13b: the damper engages over the first damp_ramp of compression, so
+         * the normal force is continuous at touchdown */
+        N[i] = fmax(0.0, P->k_susp * x + P->c_susp * xdot * fmin(1.0, x / P->damp_ramp));
         for (int k = 0; k < 3; ++k) rc[i][k] = rb[k] - t * u[k];   /* contact point - CoM */
         hit[i] = 1;
     }
@@ -377,9 +380,11 @@ static void body_substep(const or_params* P, double* f, const double* act, const
     for (int i = 0; i < 4; ++i)
         spin[i] = f[OR_F_S0 + i] + (i < 2 ? h * thr * P->tau_drive / P->wheel_inertia : 0.0);
 
-    /* 5. friction impulses per wheel in contact, capped by the friction circle */
-    int nc = 0;
-    for (int i = 0; i < 4; ++i) nc += (N[i] > 0);
+    /* 5. friction impulses per wheel in contact, capped by the friction circle;
+     * R16: the chassis share of every wheel's effective mass is that of one of
+     * the four wheels, whichever are loaded (a Jacobi step relaxed by 1/4 never
+     * overshoots and stays continuous when a wheel unloads) */
+    const double nc = 4.0;
     double Pimp[3] = {0, 0, 0}, Limp[3] = {0, 0, 0};
     double spin2[4];
     for (int i = 0; i < 4; ++i) {
@@ -458,7 +463,7 @@ static void pair_contact(const or_params* P, const double* fi, const double* fj,
     double depth = or_sat(P, ci, hi, cj, hj, n);
     if (!(depth > 0)) return;
     double vn = (fi[OR_F_VX] - fj[OR_F_VX]) * n[0] + (fi[OR_F_VY] - fj[OR_F_VY]) * n[1];
-    double Fm = fmax(0.0, P->k_contact * depth + P->c_contact * vn);
+    double Fm = fmax(0.0, P->k_contact * depth + P->c_contact * vn * fmin(1.0, depth / P->damp_ramp));
     Fj[0] = Fm * n[0]; Fj[1] = Fm * n[1];
     Fi[0] = -Fj[0]; Fi[1] = -Fj[1];
     double mx = 0.5 * dx, my = 0.5 * dy;                      /* midpoint - ci ; midpoint - cj = -(m) */
@@ -833,7 +838,9 @@ static void respawn_world(const or_params* P, const or_scene* S, int w, double* 
         int ep = I[a * OR_NI + OR_I_EPISODE] + 1;
         double bx = 0, by = 0, bpsi = 0, bv = P->spawn_v_min, bgx = P->spawn_goal_min, bgy = 0, bscore = -1;
         for (int r = 0; r < P->spawn_tries; ++r) {
-            double x = 0, y = 0, psi = 0, gx = P->spawn_goal_min, gy = 0;
+            /* R28b: a world without lane points spawns slot k at (0, k * spacing),
+             * heading +x, goal spawn_goal_min ahead */
+            double x = 0, y = (a - a0) * P->spawn_spacing, psi = 0, gx = P->spawn_goal_min, gy = y;
             if (nc > 0) {
                 int k = cand[(uint32_t)(draw(seed, a, ep, r, 0) >> 32) % (uint32_t)nc];
                 int p = poly_of_point(S, w, k);

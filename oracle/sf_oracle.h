@@ -88,6 +88,7 @@ typedef struct {
     double lambda_yaw, lambda_lat;
     double u_z_min;               /* ray/plane grazing cut-off                 */
     double k_contact, c_contact;  /* footprint penalty contact                 */
+    double damp_ramp;             /* compression over which dampers engage      */
     double wheelbase;
     /* reward / event constants (App. G) */
     double goal_radius, w_goal, w_collision, w_crash, w_lane_forb;
