@@ -1,0 +1,351 @@
+"""Benchmark of the batched multi-world vehicle step (CASPS on one B300).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is controlled-agent steps per second (CASPS,
+SceneFactory Sec. 4.2: agents completing one 30 Hz control step per
+wall-clock second) over all ranks for the 256 worlds x 16 agents workload on
+synthetic paper-shaped road graphs; the same line carries the 4096 x 16
+workload, the end-to-end number through the C-ABI with host buffers, the
+roofline of the world kernel and the FP64 oracle timed on the host cores.
+
+A step is one ``sf_step``: four 120 Hz substeps with footprint contact, events,
+rewards, automatic respawns of done agents and the 320-float observations of
+every agent.  Inputs are resident on the device; L2 is flushed (a 256 MB
+write) before every timed step, whose duration is taken by CUDA events on the
+stream the kernel runs on.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_08528_b300 import synth  # noqa: E402
+
+WORKLOADS = {
+    # name: (worlds, agents per world, road seed base, weather)
+    "256x16": (256, 16, 1000, "uniform"),
+    "4096x16": (4096, 16, 4000, "wet_mix"),
+}
+METRIC = "CASPS at 256x16 and 4096x16; surrogate vs plain physics at matched error"
+FLUSH_BYTES = 256 << 20
+
+
+def make_scene(name: str, rank: int = 0):
+    worlds, apw, seed, weather = WORKLOADS[name]
+    return synth.procedural_scene(worlds, apw, seed_base=seed + rank * worlds, weather=weather,
+                                  weather_seed=seed + 17 + rank)
+
+
+def algorithmic_bytes(scene) -> dict:
+    """Bytes one step must move at minimum: agent state read and written
+    (6 float4 + 4 words = 112 B each way), actions (12 B), the observation row
+    (1280 B), reward/done/events/DRAC (13 B) per agent, and every world's road
+    points (float4 point + 4 B meta = 20 B) read once."""
+    A = scene.num_agents
+    per_agent = 2 * 112 + 12 + 320 * 4 + 13
+    roads = 20 * scene.num_points
+    return dict(per_agent=per_agent, roads=roads, total=A * per_agent + roads)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "sf_clocks_%d_%d.csv" % (os.getpid(), device_index))
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1])); smax.append(float(c[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, c[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# --------------------------------------------------------------------------- our arm
+def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True):
+    scene = make_scene(name, rank)
+    W = sf.World(scene, seed=4242 + rank, flags=sf.FLAG_AUTO_RESET, stream=stream)
+    A = W.A
+    dev = torch.device("cuda")
+    with torch.cuda.stream(stream):
+        sf.sf_reset(W.h, torch.ones(A, dtype=torch.uint8, device=dev))
+        ring = 64
+        acts_h = synth.ou_actions(A, ring, seed=11 + rank)
+        acts = torch.as_tensor(acts_h, device=dev)
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        for t in range(warmup):
+            sf.sf_step(W.h, acts[t % ring])
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in range(steps):
+            flush.fill_(float(t))                         # evict the working set from L2
+            starts[t].record(stream)
+            sf.sf_step(W.h, acts[(warmup + t) % ring])
+            ends[t].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    st = sf.sf_sync(W.h, allow=(sf.SF_ERR_NONFINITE,))
+    ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    F, I, _ = sf.sf_get_state(W.h)
+    alive = int(((I[:, 4] & 1) != 0).sum())
+
+    if not e2e:
+        W.close()
+        return dict(scene=scene, A=A, alive=alive, ms=ms, wall=wall, status=st, e2e_wall=float("nan"),
+                    e2e_steps=1, h2d=A * 12, d2h=A * 5)
+    # end to end through the C-ABI: pinned host actions in, host rewards/done out, every step
+    acts_pin = torch.as_tensor(acts_h).pin_memory()
+    act_dev = torch.empty((A, 3), dtype=torch.float32, device=dev)
+    rew_dev = torch.empty(A, dtype=torch.float32, device=dev)
+    done_dev = torch.empty(A, dtype=torch.uint8, device=dev)
+    rew_h = torch.empty(A, dtype=torch.float32).pin_memory()
+    done_h = torch.empty(A, dtype=torch.uint8).pin_memory()
+    e2e_steps = max(50, steps // 4)
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in range(e2e_steps):
+            act_dev.copy_(acts_pin[t % ring], non_blocking=True)
+            sf.sf_step(W.h, act_dev)
+            sf.sf_get_obs(W.h, None, rew_dev, done_dev, None)
+            rew_h.copy_(rew_dev, non_blocking=True)
+            done_h.copy_(done_dev, non_blocking=True)
+            stream.synchronize()
+            float(rew_h[0])                              # the host consumes the result
+        e2e_wall = time.perf_counter() - t0
+    W.close()
+    return dict(scene=scene, A=A, alive=alive, ms=ms, wall=wall, status=st, e2e_wall=e2e_wall,
+                e2e_steps=e2e_steps, h2d=A * 12, d2h=A * 5)
+
+
+def cpu_baseline(name, seconds=12.0):
+    """The FP64 oracle as it stands, single thread, on a bounded sample of the
+    workload: the first worlds of the same scene, stepped until ~`seconds`."""
+    from oracle import oracle as O
+    scene = make_scene(name)
+    worlds = list(range(8))
+    sub, rows = synth.subscene(scene, worlds)
+    orc = O.Oracle(sub)
+    F, I = orc.empty_state()
+    I[:, O.I_PRECIP], I[:, O.I_SURFACE] = sub.precip, sub.surface
+    orc.reset(F, I, np.ones(sub.num_agents, np.uint8), seed=4242)
+    acts = synth.ou_actions(sub.num_agents, 64, seed=11).astype(np.float64)
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        orc.step(F, I, acts[n % 64], flags=O.FLAG_AUTO_RESET, seed=4242)
+        n += 1
+    dt = time.perf_counter() - t0
+    return dict(value=sub.num_agents * n / dt, unit="CASPS", cores=1, kind="oracle",
+                sample="%d of %d worlds (%d agents) x %d steps of the %s workload, FP64, 1 thread" % (
+                    len(worlds), scene.num_worlds, sub.num_agents, n, name))
+
+
+def main_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2605_08528_b300 import sf
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    peak, peak_kind = load_peaks()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    res = {}
+    names = [args.only] if args.only else list(WORKLOADS)
+    for name in names:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        res[name] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream, e2e=not args.skip_e2e)
+    clk = clocks.stop()
+    if args.only:          # profiling run: one workload, no report line
+        if rank == 0:
+            r = res[args.only]
+            print(json.dumps({"profile_run": args.only, "ms_per_step": float(r["ms"].mean()), "agents": r["A"]}))
+        return
+
+    def agg(name):
+        r = res[name]
+        t = float(r["ms"].sum()) / 1e3
+        tt = torch.tensor([t, r["e2e_wall"]], dtype=torch.float64, device="cuda")
+        n = torch.tensor([r["alive"]], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        t, e2e = float(tt[0]), float(tt[1])
+        casps = float(n[0]) * args.steps / t
+        e2e_casps = float(n[0]) * r["e2e_steps"] / e2e
+        ab = algorithmic_bytes(r["scene"])
+        mean_s = float(r["ms"].mean()) / 1e3
+        ach = ab["total"] / mean_s / 1e9
+        return dict(casps=casps, e2e=e2e_casps, ms=float(r["ms"].mean()), p50=float(np.percentile(r["ms"], 50)),
+                    p99=float(np.percentile(r["ms"], 99)), bytes=ab, achieved=ach, A=r["A"], alive=r["alive"],
+                    h2d=r["h2d"], d2h=r["d2h"])
+
+    a256, a4096 = agg("256x16"), agg("4096x16")
+    if rank == 0:
+        base = cpu_baseline("256x16") if (world == 1 and not args.skip_cpu) else None
+        traffic = load_traffic()
+        line = {
+            "metric": METRIC, "value": a256["casps"], "unit": "CASPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": a256["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "256 worlds x 16 agents, paper-shaped procedural roads (4-12 lanes, 0-2 "
+                                   "intersections, 400-1200 points/world), per-agent weather table mu, auto-reset",
+                       "worlds": 256 * world, "agents": a256["A"] * world, "dt": 1 / 30, "substeps": 4,
+                       "K_agents": 8, "L_points": 32, "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": "worlds sharded, no data-path collective" if world > 1 else "1 GPU"},
+            "p50_ms": a256["p50"], "p99_ms": a256["p99"],
+            "e2e": {"value": a256["e2e"], "unit": "CASPS", "h2d_bytes_per_step": a256["h2d"],
+                    "d2h_bytes_per_step": a256["d2h"]},
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "hbm", "kernel": "world_kernel<step>", "achieved": a256["achieved"],
+                         "peak": peak, "unit": "GB/s", "frac": a256["achieved"] / peak,
+                         "peak_source": peak_kind, "algorithmic_bytes_per_launch": a256["bytes"]["total"],
+                         "traffic": traffic.get("256x16")},
+            "scale_4096x16": {"value": a4096["casps"], "unit": "CASPS", "ms_per_step": a4096["ms"],
+                              "p50_ms": a4096["p50"], "p99_ms": a4096["p99"],
+                              "agents": a4096["A"] * world,
+                              "e2e": {"value": a4096["e2e"], "unit": "CASPS", "h2d_bytes_per_step": a4096["h2d"],
+                                      "d2h_bytes_per_step": a4096["d2h"]},
+                              "roofline": {"bound": "hbm", "achieved": a4096["achieved"], "peak": peak,
+                                           "unit": "GB/s", "frac": a4096["achieved"] / peak,
+                                           "algorithmic_bytes_per_launch": a4096["bytes"]["total"],
+                                           "traffic": traffic.get("4096x16")},
+                              "policy": "not in this line (plain physics step)"},
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                       "samples": clk["samples"]},
+            "paper_context": "19,250 CASPS at 256x16 on an RTX PRO 6000 (Isaac Sim/PhysX + PPO), context only",
+        }
+        if base is not None:
+            line["cpu_baseline"] = base
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def load_traffic():
+    """DRAM bytes per launch of the world kernel from the committed ncu summary
+    (null when no capture of the current kernel exists)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# --------------------------------------------------------------------------- reference arm
+def main_reference(args):
+    """The FP64 oracle as it stands on the host cores, for the same metric and
+    workload; each step a bounded sample (8 of the 256 worlds)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    scene = make_scene("256x16")
+    sub, rows = synth.subscene(scene, range(8))
+    orc = O.Oracle(sub)
+    F, I = orc.empty_state()
+    I[:, O.I_PRECIP], I[:, O.I_SURFACE] = sub.precip, sub.surface
+    orc.reset(F, I, np.ones(sub.num_agents, np.uint8), seed=4242)
+    acts = synth.ou_actions(sub.num_agents, 64, seed=11).astype(np.float64)
+    for t in range(args.warmup):
+        orc.step(F, I, acts[t % 64], flags=O.FLAG_AUTO_RESET, seed=4242)
+    t0 = time.perf_counter()
+    for t in range(args.steps):
+        orc.step(F, I, acts[(args.warmup + t) % 64], flags=O.FLAG_AUTO_RESET, seed=4242)
+    dt = time.perf_counter() - t0
+    v = sub.num_agents * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "CASPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "256 worlds x 16 agents (sample: 8 worlds, 128 agents per step)"},
+            "cpu_baseline": {"value": v, "unit": "CASPS", "cores": 1, "kind": "oracle",
+                             "sample": "8 of 256 worlds (128 agents) per step, FP64, 1 thread"},
+            "e2e": {"value": v, "unit": "CASPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--only", default=None, choices=list(WORKLOADS), help="profiling: run one workload only")
+    ap.add_argument("--skip-e2e", action="store_true", help="profiling: no end-to-end leg")
+    ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)
+
+
+if __name__ == "__main__":
+    main()

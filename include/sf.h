@@ -1,0 +1,235 @@
+/*
+ * sf.h -- C-ABI of the batched multi-world vehicle step on one B300 (sm_103a).
+ *
+ * The library steps many independent driving worlds at once, each holding up to
+ * SF_MAX_AGENTS_PER_WORLD vehicles on its own z-flattened road map, following
+ * SceneFactory (arXiv 2605.08528): 120 Hz physics under a 30 Hz control step
+ * (Sec. 4.1), steering PD (Sec. 3.2, Eq. steer_pd), front-wheel drive and
+ * four-wheel brakes (App. F, Tab. app_action_params), ego / neighbour / road
+ * observations (App. D), ten reward terms and terminations (App. G,
+ * Tab. app_reward_terms) and teleport-only resets (App. J).  The vehicle is a
+ * raycast spring-damper chassis with friction-capped tire impulses integrated
+ * by symplectic Euler over fixed substeps.
+ *
+ * Conventions
+ *  - Every pointer named d_* is CUDA device memory owned by the caller; h_*
+ *    pointers are host memory owned by the caller.  The library owns the agent
+ *    state, the road store and its output buffers; none of them is exposed
+ *    except through sf_output_ptrs.
+ *  - Calls that launch work are asynchronous on the stream given to sf_create;
+ *    caller buffers must stay valid until that stream reaches the call.
+ *    Calls marked "synchronous" wait for the stream first.
+ *  - Kernel-side conditions (non-finite states) are recorded in a device word
+ *    and reported by the next synchronous call (sf_sync, sf_get_state, ...).
+ *  - No call throws; every call returns an sf_status; sf_last_error gives the
+ *    message of the last failure of a handle.  There is no CPU fallback: a
+ *    missing or unusable GPU is SF_ERR_CUDA.
+ */
+#ifndef SF_H
+#define SF_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sf_ctx* sf_handle;
+
+typedef enum {
+    SF_OK = 0,
+    SF_ERR_INVALID_ARG = 1, /* bad pointer, size, CSR offsets or configuration         */
+    SF_ERR_CUDA = 2,        /* a CUDA runtime call failed                               */
+    SF_ERR_OOM = 3,         /* device allocation failed                                 */
+    SF_ERR_NONFINITE = 4,   /* at least one agent state went non-finite since last sync */
+    SF_ERR_TIMEOUT = 5,     /* a bounded device wait gave up                            */
+    SF_ERR_STATE = 6        /* call order violated (e.g. sf_step before sf_load_roads)  */
+} sf_status;
+
+#define SF_MAX_AGENTS_PER_WORLD 32
+#define SF_K_AGENTS 8   /* neighbours in the observation                   */
+#define SF_L_POINTS 32  /* road points in the observation                  */
+#define SF_OBS_EGO 16
+#define SF_OBS_NBR 10
+#define SF_OBS_PT 7
+#define SF_OBS_DIM (SF_OBS_EGO + SF_K_AGENTS * SF_OBS_NBR + SF_L_POINTS * SF_OBS_PT) /* 320 */
+
+/* Exchange layout of the agent state (sf_get_state / sf_set_state):
+ * float columns (SF_NF per agent) */
+enum {
+    SF_F_PX = 0, SF_F_PY, SF_F_PZ,          /* CoM position [m], world frame, road plane z = 0 */
+    SF_F_QW, SF_F_QX, SF_F_QY, SF_F_QZ,     /* attitude quaternion                              */
+    SF_F_VX, SF_F_VY, SF_F_VZ,              /* CoM velocity [m/s]                               */
+    SF_F_WX, SF_F_WY, SF_F_WZ,              /* angular velocity, world frame [rad/s]            */
+    SF_F_S0, SF_F_S1, SF_F_S2, SF_F_S3,     /* wheel spin FL FR RL RR [rad/s]                   */
+    SF_F_DELTA, SF_F_DDELTA,                /* front steering angle [rad] and rate [rad/s]      */
+    SF_F_GX, SF_F_GY,                       /* goal [m]                                         */
+    SF_F_SX, SF_F_SY,                       /* episode start [m]                                */
+    SF_F_MU,                                /* tire-road friction coefficient                   */
+    SF_F_PEAK_DRAC,                         /* episode peak DRAC [m/s^2]                        */
+    SF_NF
+};
+/* int32 columns (SF_NI per agent) */
+enum {
+    SF_I_PRECIP = 0,  /* 0 dry, 1 light rain, 2 heavy rain, 3 snow        */
+    SF_I_SURFACE,     /* 0 asphalt, 1 concrete, 2 gravel                  */
+    SF_I_STEP,        /* control steps since spawn                        */
+    SF_I_EPISODE,     /* episodes started by this agent slot              */
+    SF_I_STATUS,      /* SF_STATUS_* bits                                 */
+    SF_I_EVENTS,      /* SF_EV_* bits of the last step                    */
+    SF_NI
+};
+#define SF_STATUS_ALIVE 1u
+#define SF_STATUS_PARKED 2u
+
+/* event bits written per agent per step (App. G) */
+#define SF_EV_GOAL (1u << 0)
+#define SF_EV_COLLISION (1u << 1)
+#define SF_EV_CRASH (1u << 2)
+#define SF_EV_LANE_FORBIDDEN (1u << 3)
+#define SF_EV_OFFROAD (1u << 4)
+#define SF_EV_IDLE (1u << 5)
+#define SF_EV_TIMEOUT (1u << 6)
+#define SF_EV_NONFINITE (1u << 7)
+#define SF_EV_RESPAWNED (1u << 8)
+
+/* sf_config.flags */
+#define SF_FLAG_INVINCIBLE 1     /* events are logged but never terminate (Sec. 4.1)    */
+#define SF_FLAG_AUTO_RESET 2     /* done agents respawn inside sf_step; else they park   */
+#define SF_FLAG_RECORD_INDICES 4 /* keep nearest-lane and k-NN indices for inspection    */
+
+typedef struct {
+    uint64_t seed;           /* seed of the counter-based reset draws                 */
+    int32_t flags;           /* SF_FLAG_* bits                                        */
+    int32_t warps_per_block; /* world-kernel launch shape; 0 = library default        */
+    int32_t reserved[8];     /* must be zero                                          */
+} sf_config;
+
+/* Worlds as CSR (host memory, read during sf_load_roads only).
+ * World w holds agents [agent_off[w], agent_off[w+1]) (at most 32) and
+ * polylines [poly_off[w], poly_off[w+1]); polyline p holds points
+ * [point_off[p], point_off[p+1]) with Waymo type poly_type[p]
+ * (1, 2 driving lanes; 15, 16 road edges; others are map points only).
+ * Coordinates are world-local metres (each world centred at its origin,
+ * App. C).  precip/surface give each agent's weather cell of the friction
+ * table. */
+typedef struct {
+    int32_t num_worlds;
+    int32_t num_polylines;
+    int32_t num_points;
+    const int32_t* agent_off;  /* [num_worlds + 1], agent_off[0] == 0, nondecreasing   */
+    const int32_t* poly_off;   /* [num_worlds + 1], poly_off[0] == 0, nondecreasing    */
+    const int32_t* point_off;  /* [num_polylines + 1], point_off[0] == 0, nondecreasing */
+    const uint8_t* poly_type;  /* [num_polylines]                                       */
+    const float* px;           /* [num_points]                                          */
+    const float* py;           /* [num_points]                                          */
+    const uint8_t* precip;     /* [num_agents] 0..3                                     */
+    const uint8_t* surface;    /* [num_agents] 0..2                                     */
+} sf_roads;
+
+/* Device pointers to the library-owned outputs of the last sf_step / sf_reset.
+ * Valid until sf_destroy or the next sf_load_roads. */
+typedef struct {
+    float* obs;            /* [A][SF_OBS_DIM] float32                          */
+    float* reward;         /* [A]                                              */
+    uint8_t* done;         /* [A] 1 if the agent terminated or timed out       */
+    uint32_t* events;      /* [A] SF_EV_* bits                                 */
+    int32_t* lane_seg;     /* [A] nearest lane segment start point, -1 if none (SF_FLAG_RECORD_INDICES) */
+    int32_t* knn_points;   /* [A][SF_L_POINTS] global point indices, -1 pad     (SF_FLAG_RECORD_INDICES) */
+    int32_t* knn_agents;   /* [A][SF_K_AGENTS] global agent indices, -1 pad     (SF_FLAG_RECORD_INDICES) */
+    float* drac;           /* [A] DRAC of the last step                        */
+    int32_t num_agents;
+} sf_outputs;
+
+/* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream) on which every call of this handle enqueues
+ * its work.  *out receives the handle.  Errors: SF_ERR_INVALID_ARG (NULL out,
+ * nonzero reserved), SF_ERR_CUDA (no usable device). */
+sf_status sf_create(const sf_config* cfg, void* cuda_stream, sf_handle* out);
+
+/* Release every device and host resource of h (synchronous).  NULL is a no-op. */
+sf_status sf_destroy(sf_handle h);
+
+/* Validate the CSR on the host (offsets monotone and in range, at most 32
+ * agents per world, finite coordinates, known weather codes), upload it, build
+ * the derived road store (per-point road direction, App. C segment rule: gaps
+ * > 3 m and endpoints outside the 200 m box are not segments; spawn candidates)
+ * and allocate the agent state, every agent inactive.  Synchronous.  Replaces
+ * any previous roads and state.  Errors: SF_ERR_INVALID_ARG, SF_ERR_OOM. */
+sf_status sf_load_roads(sf_handle h, const sf_roads* h_roads);
+
+/* One control step of every world (Sec. 4.1; App. F-G): `substeps` physics
+ * substeps of dt/substeps each with the actions held, footprint contact
+ * between the agents of a world at every substep, then events, rewards and
+ * done flags, done agents parked or (SF_FLAG_AUTO_RESET) respawned, then the
+ * observations of every agent.  d_actions is [A][3] float32 (throttle, steer,
+ * brake) in [-1, 1]; throttle and brake are rectified, steer scales the
+ * maximum steering angle (App. F).  Asynchronous.
+ * Errors: SF_ERR_STATE (no roads), SF_ERR_INVALID_ARG (NULL actions, dt <= 0,
+ * substeps outside 1..64), SF_ERR_CUDA (launch failure). */
+sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps);
+
+/* Copy the observations, rewards, done flags and event bits of the last step
+ * or reset into caller device buffers ([A][SF_OBS_DIM], [A], [A], [A]); any
+ * pointer may be NULL.  Asynchronous device-to-device copies. */
+sf_status sf_get_obs(sf_handle h, float* d_obs, float* d_reward, uint8_t* d_done, uint32_t* d_events);
+
+/* Copy the inspection outputs of the last step / reset into caller device
+ * buffers: nearest lane segment [A], k nearest road points [A][SF_L_POINTS],
+ * k nearest agents [A][SF_K_AGENTS] (all int32, -1 = none; only maintained
+ * with SF_FLAG_RECORD_INDICES) and the step DRAC [A] float32 (App. G reading:
+ * max over the k nearest agents of closing speed^2 / (2 gap)).  Any pointer
+ * may be NULL.  Asynchronous device-to-device copies. */
+sf_status sf_get_indices(sf_handle h, int32_t* d_lane_seg, int32_t* d_knn_points, int32_t* d_knn_agents,
+                         float* d_drac);
+
+/* Device pointers of the library-owned outputs (zero-copy). */
+sf_status sf_output_ptrs(sf_handle h, sf_outputs* out);
+
+/* Teleport-only reset (App. J): every agent with d_mask[a] != 0 starts a new
+ * episode at a lane point drawn by a counter-based SplitMix64 hash of
+ * (seed, agent, episode, attempt) with at least 50 m of lane ahead, heading
+ * along the lane, goal 50-150 m ahead on the same lane, speed U[5, 20] m/s,
+ * wheels rolling, at static equilibrium height, at least 10 m from the other
+ * agents of its world when one of 8 attempts allows it (agents are processed
+ * in index order).  Then the observations of every agent of every world that
+ * had a masked agent are recomputed.  d_mask is [A] uint8.  Asynchronous. */
+sf_status sf_reset(sf_handle h, const uint8_t* d_mask);
+
+/* Place every agent explicitly: h_place is [A][6] = (x, y, heading, speed,
+ * goal_x, goal_y); the agent starts an episode there at static equilibrium
+ * height with rolling wheels.  Then all observations are computed.
+ * Synchronous (host upload). */
+sf_status sf_place_agents(sf_handle h, const float* h_place);
+
+/* Read / write the whole agent state in the exchange layout: h_f is
+ * [A][SF_NF] float32, h_i is [A][SF_NI] int32.  Synchronous.  sf_set_state
+ * recomputes all observations.  sf_get_state reports a pending
+ * SF_ERR_NONFINITE after copying. */
+sf_status sf_get_state(sf_handle h, float* h_f, int32_t* h_i);
+sf_status sf_set_state(sf_handle h, const float* h_f, const int32_t* h_i);
+
+/* Checkpoint / resume the agent state to / from a file (little-endian header
+ * + exchange layout).  Synchronous.  The roads must match (agent count). */
+sf_status sf_save_state(sf_handle h, const char* path);
+sf_status sf_load_state(sf_handle h, const char* path);
+
+/* Wait for the handle's stream; return SF_ERR_NONFINITE / SF_ERR_TIMEOUT if the
+ * device recorded such a condition since the last sync (and clear it). */
+sf_status sf_sync(sf_handle h);
+
+/* Number of agents and worlds of the loaded roads (0 before sf_load_roads). */
+int32_t sf_num_agents(sf_handle h);
+int32_t sf_num_worlds(sf_handle h);
+
+/* Message of the last failed call on h (or of the last sf_create failure when
+ * h is NULL).  The string is owned by the library. */
+const char* sf_last_error(sf_handle h);
+
+/* Library version string. */
+const char* sf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SF_H */

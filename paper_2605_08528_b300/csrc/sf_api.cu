@@ -1,0 +1,545 @@
+// sf_api.cu -- the C-ABI of the vehicle step (include/sf.h).
+//
+// Host side only: argument validation, the derived road store built once at
+// load time, device allocations, the exchange layout of the agent state,
+// checkpoints and the device error word.  Every step computation runs in the
+// kernels of sf_world.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sf.h"
+#include "sf_internal.cuh"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct sf_ctx {
+    sf_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    int W = 0, A = 0, NP = 0;
+    std::vector<void*> allocs;
+    DevState st{};
+    DevRoads rd{};
+    DevOutputs out{};
+    float* place_buf = nullptr;
+    uint8_t* all_mask = nullptr;
+    bool loaded = false;
+};
+
+namespace {
+
+sf_status fail(sf_ctx* h, sf_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+sf_status cuda_fail(sf_ctx* h, cudaError_t e, const char* where) {
+    return fail(h, e == cudaErrorMemoryAllocation ? SF_ERR_OOM : SF_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SF_CUDA(h, call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+template <class T>
+sf_status dalloc(sf_ctx* h, T** p, size_t count) {
+    void* q = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+    h->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return SF_OK;
+}
+
+void free_all(sf_ctx* h) {
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    h->st = DevState{};
+    h->rd = DevRoads{};
+    h->out = DevOutputs{};
+    h->place_buf = nullptr;
+    h->all_mask = nullptr;
+    h->loaded = false;
+    h->W = h->A = h->NP = 0;
+}
+
+WorldArgs make_args(sf_ctx* h) {
+    WorldArgs a{};
+    a.st = h->st;
+    a.rd = h->rd;
+    a.out = h->out;
+    a.num_worlds = h->W;
+    a.num_agents = h->A;
+    a.flags = h->cfg.flags;
+    a.seed = h->cfg.seed;
+    a.substeps = 1;
+    a.h = 0.f;
+    return a;
+}
+
+int wpb_of(const sf_ctx* h) {
+    int w = h->cfg.warps_per_block;
+    return (w == 1 || w == 2 || w == 4 || w == 8) ? w : 4;
+}
+
+bool is_lane_type(int t) { return t == 1 || t == 2; }
+bool is_edge_type(int t) { return t == 15 || t == 16; }
+
+}  // namespace
+
+extern "C" {
+
+const char* sf_version(void) { return "sf 0.1 (sm_103a)"; }
+
+const char* sf_last_error(sf_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+sf_status sf_create(const sf_config* cfg, void* cuda_stream, sf_handle* out) {
+    g_create_error.clear();
+    if (!out) { g_create_error = "sf_create: out is NULL"; return SF_ERR_INVALID_ARG; }
+    *out = nullptr;
+    sf_config c{};
+    if (cfg) c = *cfg;
+    for (int i = 0; i < 8; ++i)
+        if (c.reserved[i] != 0) { g_create_error = "sf_create: reserved fields must be zero"; return SF_ERR_INVALID_ARG; }
+    int dev = 0, count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        g_create_error = std::string("sf_create: no CUDA device: ") + cudaGetErrorString(e);
+        return SF_ERR_CUDA;
+    }
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { g_create_error = cudaGetErrorString(e); return SF_ERR_CUDA; }
+    sf_ctx* h = new sf_ctx();
+    h->cfg = c;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->device = dev;
+    *out = h;
+    return SF_OK;
+}
+
+sf_status sf_destroy(sf_handle h) {
+    if (!h) return SF_OK;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return SF_OK;
+}
+
+int32_t sf_num_agents(sf_handle h) { return h ? h->A : 0; }
+int32_t sf_num_worlds(sf_handle h) { return h ? h->W : 0; }
+
+sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    if (!r) return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: roads is NULL");
+    const int W = r->num_worlds, NPl = r->num_polylines, NP = r->num_points;
+    if (W <= 0 || NPl < 0 || NP < 0) return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: negative or zero sizes");
+    if (!r->agent_off || !r->poly_off || !r->point_off || (NPl > 0 && !r->poly_type) || (NP > 0 && (!r->px || !r->py)))
+        return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: NULL array");
+    if (r->agent_off[0] != 0 || r->poly_off[0] != 0 || r->point_off[0] != 0)
+        return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: CSR offsets must start at 0");
+    for (int w = 0; w < W; ++w) {
+        int na = r->agent_off[w + 1] - r->agent_off[w];
+        if (na < 0 || na > SF_MAX_AGENTS_PER_WORLD)
+            return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: world " + std::to_string(w) + " has " +
+                                                   std::to_string(na) + " agents (0..32 allowed)");
+        if (r->poly_off[w + 1] < r->poly_off[w])
+            return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: poly_off not monotone at world " + std::to_string(w));
+    }
+    if (r->poly_off[W] != NPl) return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: poly_off[W] != num_polylines");
+    for (int p = 0; p < NPl; ++p)
+        if (r->point_off[p + 1] < r->point_off[p])
+            return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: point_off not monotone at polyline " + std::to_string(p));
+    if (r->point_off[NPl] != NP) return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: point_off[P] != num_points");
+    const int A = r->agent_off[W];
+    if (A > 0 && (!r->precip || !r->surface)) return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: NULL weather arrays");
+    for (int a = 0; a < A; ++a)
+        if (r->precip[a] > 3 || r->surface[a] > 2)
+            return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: weather code out of range at agent " + std::to_string(a));
+    for (int k = 0; k < NP; ++k)
+        if (!std::isfinite(r->px[k]) || !std::isfinite(r->py[k]))
+            return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: non-finite point " + std::to_string(k));
+
+    // ---- derived road store (double precision on the host, App. C rules)
+    std::vector<float4> pt(NP);
+    std::vector<uint32_t> pmeta(NP);
+    std::vector<int32_t> pend(NP);
+    std::vector<int4> world(W);
+    std::vector<int2> cand(W);
+    std::vector<int32_t> cands;
+    auto in_box = [](double x, double y) { return std::fabs(x) <= 100.0 && std::fabs(y) <= 100.0; };
+    for (int w = 0; w < W; ++w) {
+        const int p0 = r->poly_off[w], p1 = r->poly_off[w + 1];
+        const int q0 = r->point_off[p0], q1 = r->point_off[p1];
+        world[w] = make_int4(r->agent_off[w], r->agent_off[w + 1] - r->agent_off[w], q0, q1 - q0);
+        std::vector<int32_t> strict, all_lane;
+        for (int p = p0; p < p1; ++p) {
+            const int t = r->poly_type[p];
+            const int k0 = r->point_off[p], k1 = r->point_off[p + 1];
+            std::vector<double> arc(k1 - k0, 0.0);
+            for (int k = k0; k < k1; ++k) {
+                if (k > k0) {
+                    double dx = (double)r->px[k] - r->px[k - 1], dy = (double)r->py[k] - r->py[k - 1];
+                    arc[k - k0] = arc[k - k0 - 1] + std::sqrt(dx * dx + dy * dy);
+                }
+                int a = -1, b = -1;
+                if (k + 1 < k1) { a = k; b = k + 1; } else if (k - 1 >= k0) { a = k - 1; b = k; }
+                double dxn = 0, dyn = 0;
+                if (a >= 0) {
+                    double dx = (double)r->px[b] - r->px[a], dy = (double)r->py[b] - r->py[a];
+                    double n = std::sqrt(dx * dx + dy * dy);
+                    if (n > 0) { dxn = dx / n; dyn = dy / n; }
+                }
+                pt[k] = make_float4(r->px[k], r->py[k], (float)dxn, (float)dyn);
+                uint32_t m = (uint32_t)t & sfk::kPtTypeMask;
+                if (k + 1 < k1) {
+                    double dx = (double)r->px[k + 1] - r->px[k], dy = (double)r->py[k + 1] - r->py[k];
+                    if (std::sqrt(dx * dx + dy * dy) <= 3.0 && in_box(r->px[k], r->py[k]) &&
+                        in_box(r->px[k + 1], r->py[k + 1]))
+                        m |= sfk::kPtSegNext;
+                }
+                if (is_lane_type(t)) m |= sfk::kPtLane;
+                if (is_edge_type(t)) m |= sfk::kPtEdge;
+                pmeta[k] = m;
+                pend[k] = k1;
+            }
+            if (is_lane_type(t) && k1 > k0) {
+                const double total = arc.back();
+                for (int k = k0; k < k1; ++k) {
+                    all_lane.push_back(k);
+                    if (total - arc[k - k0] >= 50.0) strict.push_back(k);
+                }
+            }
+        }
+        const std::vector<int32_t>& use = strict.empty() ? all_lane : strict;
+        cand[w] = make_int2((int)cands.size(), (int)use.size());
+        cands.insert(cands.end(), use.begin(), use.end());
+    }
+
+    // ---- allocate and upload
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    sf_status s;
+    const size_t Aa = (size_t)A;
+#define SF_ALLOC(ptr, T, n) \
+    if ((s = dalloc(h, &(ptr), (n))) != SF_OK) { free_all(h); return s; }
+    float4 *pos, *quat, *vel, *angv, *spin, *goal;
+    SF_ALLOC(pos, float4, Aa);
+    SF_ALLOC(quat, float4, Aa);
+    SF_ALLOC(vel, float4, Aa);
+    SF_ALLOC(angv, float4, Aa);
+    SF_ALLOC(spin, float4, Aa);
+    SF_ALLOC(goal, float4, Aa);
+    float* peak; uint32_t* meta; int32_t *step, *episode;
+    SF_ALLOC(peak, float, Aa);
+    SF_ALLOC(meta, uint32_t, Aa);
+    SF_ALLOC(step, int32_t, Aa);
+    SF_ALLOC(episode, int32_t, Aa);
+    h->st = DevState{pos, quat, vel, angv, spin, goal, peak, meta, step, episode};
+    int4* dworld; int2* dcand; float4* dpt; uint32_t* dpmeta; int32_t *dpend, *dcands;
+    SF_ALLOC(dworld, int4, (size_t)W);
+    SF_ALLOC(dcand, int2, (size_t)W);
+    SF_ALLOC(dpt, float4, (size_t)NP + 1);
+    SF_ALLOC(dpmeta, uint32_t, (size_t)NP + 1);
+    SF_ALLOC(dpend, int32_t, (size_t)NP + 1);
+    SF_ALLOC(dcands, int32_t, cands.size() + 1);
+    h->rd = DevRoads{dworld, dcand, dpt, dpmeta, dpend, dcands};
+    float *obs, *reward, *drac; uint8_t* done; uint32_t* events; int32_t *lane_seg, *knn_pts, *knn_agents;
+    unsigned int* err_word;
+    SF_ALLOC(obs, float, Aa * SF_OBS_DIM);
+    SF_ALLOC(reward, float, Aa);
+    SF_ALLOC(done, uint8_t, Aa);
+    SF_ALLOC(events, uint32_t, Aa);
+    SF_ALLOC(lane_seg, int32_t, Aa);
+    SF_ALLOC(knn_pts, int32_t, Aa * SF_L_POINTS);
+    SF_ALLOC(knn_agents, int32_t, Aa * SF_K_AGENTS);
+    SF_ALLOC(drac, float, Aa);
+    SF_ALLOC(err_word, unsigned int, 1);
+    h->out = DevOutputs{obs, reward, done, events, lane_seg, knn_pts, knn_agents, drac, err_word};
+    SF_ALLOC(h->place_buf, float, Aa * 6);
+    SF_ALLOC(h->all_mask, uint8_t, Aa);
+#undef SF_ALLOC
+
+    std::vector<uint32_t> meta_h(Aa);
+    for (size_t a = 0; a < Aa; ++a) meta_h[a] = (uint32_t)r->precip[a] | ((uint32_t)r->surface[a] << 8);
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void* d, const void* src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice);
+    };
+    auto zero = [&](void* d, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemset(d, 0, bytes);
+    };
+    up(dworld, world.data(), world.size() * sizeof(int4));
+    up(dcand, cand.data(), cand.size() * sizeof(int2));
+    up(dpt, pt.data(), pt.size() * sizeof(float4));
+    up(dpmeta, pmeta.data(), pmeta.size() * sizeof(uint32_t));
+    up(dpend, pend.data(), pend.size() * sizeof(int32_t));
+    up(dcands, cands.data(), cands.size() * sizeof(int32_t));
+    for (float4* p : {pos, quat, vel, angv, spin, goal}) zero(p, Aa * sizeof(float4));
+    zero(peak, Aa * 4); zero(step, Aa * 4); zero(episode, Aa * 4);
+    up(meta, meta_h.data(), Aa * 4);
+    zero(obs, Aa * SF_OBS_DIM * 4); zero(reward, Aa * 4); zero(done, Aa); zero(events, Aa * 4);
+    zero(drac, Aa * 4); zero(err_word, 4);
+    if (e == cudaSuccess && Aa) e = cudaMemset(lane_seg, 0xFF, Aa * 4);
+    if (e == cudaSuccess && Aa) e = cudaMemset(knn_pts, 0xFF, Aa * SF_L_POINTS * 4);
+    if (e == cudaSuccess && Aa) e = cudaMemset(knn_agents, 0xFF, Aa * SF_K_AGENTS * 4);
+    if (e == cudaSuccess && Aa) e = cudaMemset(h->all_mask, 1, Aa);
+    if (e != cudaSuccess) { free_all(h); return cuda_fail(h, e, "sf_load_roads upload"); }
+    h->W = W; h->A = A; h->NP = NP;
+    h->loaded = true;
+    return SF_OK;
+}
+
+sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_step: no roads loaded");
+    if (!d_actions && h->A > 0) return fail(h, SF_ERR_INVALID_ARG, "sf_step: actions is NULL");
+    if (!(dt > 0.f) || !std::isfinite(dt)) return fail(h, SF_ERR_INVALID_ARG, "sf_step: dt must be > 0");
+    if (substeps < 1 || substeps > 64) return fail(h, SF_ERR_INVALID_ARG, "sf_step: substeps must be 1..64");
+    WorldArgs a = make_args(h);
+    a.actions = d_actions;
+    a.h = dt / (float)substeps;
+    a.substeps = substeps;
+    cudaError_t e = sf_launch_world(kModeStep, a, wpb_of(h), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sf_step launch");
+    return SF_OK;
+}
+
+sf_status sf_reset(sf_handle h, const uint8_t* d_mask) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_reset: no roads loaded");
+    if (!d_mask && h->A > 0) return fail(h, SF_ERR_INVALID_ARG, "sf_reset: mask is NULL");
+    WorldArgs a = make_args(h);
+    a.mask = d_mask;
+    cudaError_t e = sf_launch_world(kModeReset, a, wpb_of(h), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sf_reset launch");
+    return SF_OK;
+}
+
+sf_status sf_get_obs(sf_handle h, float* d_obs, float* d_reward, uint8_t* d_done, uint32_t* d_events) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_get_obs: no roads loaded");
+    const size_t A = (size_t)h->A;
+    if (d_obs) SF_CUDA(h, cudaMemcpyAsync(d_obs, h->out.obs, A * SF_OBS_DIM * 4, cudaMemcpyDeviceToDevice, h->stream));
+    if (d_reward) SF_CUDA(h, cudaMemcpyAsync(d_reward, h->out.reward, A * 4, cudaMemcpyDeviceToDevice, h->stream));
+    if (d_done) SF_CUDA(h, cudaMemcpyAsync(d_done, h->out.done, A, cudaMemcpyDeviceToDevice, h->stream));
+    if (d_events) SF_CUDA(h, cudaMemcpyAsync(d_events, h->out.events, A * 4, cudaMemcpyDeviceToDevice, h->stream));
+    return SF_OK;
+}
+
+sf_status sf_get_indices(sf_handle h, int32_t* d_lane_seg, int32_t* d_knn_points, int32_t* d_knn_agents,
+                         float* d_drac) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_get_indices: no roads loaded");
+    const size_t A = (size_t)h->A;
+    if (d_lane_seg)
+        SF_CUDA(h, cudaMemcpyAsync(d_lane_seg, h->out.lane_seg, A * 4, cudaMemcpyDeviceToDevice, h->stream));
+    if (d_knn_points)
+        SF_CUDA(h, cudaMemcpyAsync(d_knn_points, h->out.knn_pts, A * SF_L_POINTS * 4, cudaMemcpyDeviceToDevice,
+                                   h->stream));
+    if (d_knn_agents)
+        SF_CUDA(h, cudaMemcpyAsync(d_knn_agents, h->out.knn_agents, A * SF_K_AGENTS * 4, cudaMemcpyDeviceToDevice,
+                                   h->stream));
+    if (d_drac) SF_CUDA(h, cudaMemcpyAsync(d_drac, h->out.drac, A * 4, cudaMemcpyDeviceToDevice, h->stream));
+    return SF_OK;
+}
+
+sf_status sf_output_ptrs(sf_handle h, sf_outputs* o) {
+    if (!h || !o) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_output_ptrs: no roads loaded");
+    o->obs = h->out.obs;
+    o->reward = h->out.reward;
+    o->done = h->out.done;
+    o->events = h->out.events;
+    o->lane_seg = h->out.lane_seg;
+    o->knn_points = h->out.knn_pts;
+    o->knn_agents = h->out.knn_agents;
+    o->drac = h->out.drac;
+    o->num_agents = h->A;
+    return SF_OK;
+}
+
+static sf_status observe_all(sf_handle h) {
+    WorldArgs a = make_args(h);
+    cudaError_t e = sf_launch_world(kModeObserve, a, wpb_of(h), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "observe launch");
+    return SF_OK;
+}
+
+sf_status sf_place_agents(sf_handle h, const float* h_place) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_place_agents: no roads loaded");
+    if (!h_place && h->A > 0) return fail(h, SF_ERR_INVALID_ARG, "sf_place_agents: NULL");
+    for (int i = 0; i < h->A * 6; ++i)
+        if (!std::isfinite(h_place[i])) return fail(h, SF_ERR_INVALID_ARG, "sf_place_agents: non-finite value");
+    SF_CUDA(h, cudaStreamSynchronize(h->stream));
+    SF_CUDA(h, cudaMemcpy(h->place_buf, h_place, (size_t)h->A * 6 * 4, cudaMemcpyHostToDevice));
+    WorldArgs a = make_args(h);
+    cudaError_t e = sf_launch_place(a, h->place_buf, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "place launch");
+    sf_status s = observe_all(h);
+    if (s != SF_OK) return s;
+    SF_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SF_OK;
+}
+
+sf_status sf_get_state(sf_handle h, float* h_f, int32_t* h_i) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_get_state: no roads loaded");
+    if ((!h_f || !h_i) && h->A > 0) return fail(h, SF_ERR_INVALID_ARG, "sf_get_state: NULL");
+    SF_CUDA(h, cudaStreamSynchronize(h->stream));
+    const size_t A = (size_t)h->A;
+    std::vector<float4> pos(A), quat(A), vel(A), angv(A), spin(A), goal(A);
+    std::vector<float> peak(A);
+    std::vector<uint32_t> meta(A), events(A);
+    std::vector<int32_t> step(A), episode(A);
+    if (A) {
+        SF_CUDA(h, cudaMemcpy(pos.data(), h->st.pos, A * 16, cudaMemcpyDeviceToHost));
+        SF_CUDA(h, cudaMemcpy(quat.data(), h->st.quat, A * 16, cudaMemcpyDeviceToHost));
+        SF_CUDA(h, cudaMemcpy(vel.data(), h->st.vel, A * 16, cudaMemcpyDeviceToHost));
+        SF_CUDA(h, cudaMemcpy(angv.data(), h->st.angv, A * 16, cudaMemcpyDeviceToHost));
+        SF_CUDA(h, cudaMemcpy(spin.data(), h->st.spin, A * 16, cudaMemcpyDeviceToHost));
+        SF_CUDA(h, cudaMemcpy(goal.data(), h->st.goal, A * 16, cudaMemcpyDeviceToHost));
+        SF_CUDA(h, cudaMemcpy(peak.data(), h->st.peak_drac, A * 4, cudaMemcpyDeviceToHost));
+        SF_CUDA(h, cudaMemcpy(meta.data(), h->st.meta, A * 4, cudaMemcpyDeviceToHost));
+        SF_CUDA(h, cudaMemcpy(step.data(), h->st.step, A * 4, cudaMemcpyDeviceToHost));
+        SF_CUDA(h, cudaMemcpy(episode.data(), h->st.episode, A * 4, cudaMemcpyDeviceToHost));
+        SF_CUDA(h, cudaMemcpy(events.data(), h->out.events, A * 4, cudaMemcpyDeviceToHost));
+    }
+    for (size_t a = 0; a < A; ++a) {
+        float* f = h_f + a * SF_NF;
+        f[SF_F_PX] = pos[a].x; f[SF_F_PY] = pos[a].y; f[SF_F_PZ] = pos[a].z; f[SF_F_DELTA] = pos[a].w;
+        f[SF_F_QW] = quat[a].x; f[SF_F_QX] = quat[a].y; f[SF_F_QY] = quat[a].z; f[SF_F_QZ] = quat[a].w;
+        f[SF_F_VX] = vel[a].x; f[SF_F_VY] = vel[a].y; f[SF_F_VZ] = vel[a].z; f[SF_F_DDELTA] = vel[a].w;
+        f[SF_F_WX] = angv[a].x; f[SF_F_WY] = angv[a].y; f[SF_F_WZ] = angv[a].z; f[SF_F_MU] = angv[a].w;
+        f[SF_F_S0] = spin[a].x; f[SF_F_S1] = spin[a].y; f[SF_F_S2] = spin[a].z; f[SF_F_S3] = spin[a].w;
+        f[SF_F_GX] = goal[a].x; f[SF_F_GY] = goal[a].y; f[SF_F_SX] = goal[a].z; f[SF_F_SY] = goal[a].w;
+        f[SF_F_PEAK_DRAC] = peak[a];
+        int32_t* i = h_i + a * SF_NI;
+        i[SF_I_PRECIP] = (int32_t)(meta[a] & 0xFF);
+        i[SF_I_SURFACE] = (int32_t)((meta[a] >> 8) & 0xFF);
+        i[SF_I_STATUS] = (int32_t)((meta[a] >> 16) & 0xFF);
+        i[SF_I_STEP] = step[a];
+        i[SF_I_EPISODE] = episode[a];
+        i[SF_I_EVENTS] = (int32_t)events[a];
+    }
+    return sf_sync(h);
+}
+
+sf_status sf_set_state(sf_handle h, const float* h_f, const int32_t* h_i) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_set_state: no roads loaded");
+    if ((!h_f || !h_i) && h->A > 0) return fail(h, SF_ERR_INVALID_ARG, "sf_set_state: NULL");
+    const size_t A = (size_t)h->A;
+    for (size_t a = 0; a < A; ++a) {
+        const int32_t* i = h_i + a * SF_NI;
+        if (i[SF_I_PRECIP] < 0 || i[SF_I_PRECIP] > 3 || i[SF_I_SURFACE] < 0 || i[SF_I_SURFACE] > 2 ||
+            i[SF_I_STATUS] < 0 || i[SF_I_STATUS] > 3)
+            return fail(h, SF_ERR_INVALID_ARG, "sf_set_state: bad int state at agent " + std::to_string(a));
+    }
+    std::vector<float4> pos(A), quat(A), vel(A), angv(A), spin(A), goal(A);
+    std::vector<float> peak(A);
+    std::vector<uint32_t> meta(A), events(A);
+    std::vector<int32_t> step(A), episode(A);
+    for (size_t a = 0; a < A; ++a) {
+        const float* f = h_f + a * SF_NF;
+        pos[a] = make_float4(f[SF_F_PX], f[SF_F_PY], f[SF_F_PZ], f[SF_F_DELTA]);
+        quat[a] = make_float4(f[SF_F_QW], f[SF_F_QX], f[SF_F_QY], f[SF_F_QZ]);
+        vel[a] = make_float4(f[SF_F_VX], f[SF_F_VY], f[SF_F_VZ], f[SF_F_DDELTA]);
+        angv[a] = make_float4(f[SF_F_WX], f[SF_F_WY], f[SF_F_WZ], f[SF_F_MU]);
+        spin[a] = make_float4(f[SF_F_S0], f[SF_F_S1], f[SF_F_S2], f[SF_F_S3]);
+        goal[a] = make_float4(f[SF_F_GX], f[SF_F_GY], f[SF_F_SX], f[SF_F_SY]);
+        peak[a] = f[SF_F_PEAK_DRAC];
+        const int32_t* i = h_i + a * SF_NI;
+        meta[a] = (uint32_t)i[SF_I_PRECIP] | ((uint32_t)i[SF_I_SURFACE] << 8) | ((uint32_t)i[SF_I_STATUS] << 16);
+        step[a] = i[SF_I_STEP];
+        episode[a] = i[SF_I_EPISODE];
+        events[a] = (uint32_t)i[SF_I_EVENTS];
+    }
+    SF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (A) {
+        SF_CUDA(h, cudaMemcpy(h->st.pos, pos.data(), A * 16, cudaMemcpyHostToDevice));
+        SF_CUDA(h, cudaMemcpy(h->st.quat, quat.data(), A * 16, cudaMemcpyHostToDevice));
+        SF_CUDA(h, cudaMemcpy(h->st.vel, vel.data(), A * 16, cudaMemcpyHostToDevice));
+        SF_CUDA(h, cudaMemcpy(h->st.angv, angv.data(), A * 16, cudaMemcpyHostToDevice));
+        SF_CUDA(h, cudaMemcpy(h->st.spin, spin.data(), A * 16, cudaMemcpyHostToDevice));
+        SF_CUDA(h, cudaMemcpy(h->st.goal, goal.data(), A * 16, cudaMemcpyHostToDevice));
+        SF_CUDA(h, cudaMemcpy(h->st.peak_drac, peak.data(), A * 4, cudaMemcpyHostToDevice));
+        SF_CUDA(h, cudaMemcpy(h->st.meta, meta.data(), A * 4, cudaMemcpyHostToDevice));
+        SF_CUDA(h, cudaMemcpy(h->st.step, step.data(), A * 4, cudaMemcpyHostToDevice));
+        SF_CUDA(h, cudaMemcpy(h->st.episode, episode.data(), A * 4, cudaMemcpyHostToDevice));
+        SF_CUDA(h, cudaMemcpy(h->out.events, events.data(), A * 4, cudaMemcpyHostToDevice));
+    }
+    sf_status s = observe_all(h);
+    if (s != SF_OK) return s;
+    SF_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SF_OK;
+}
+
+static const char kMagic[8] = {'S', 'F', 'C', 'K', 'P', 'T', '0', '1'};
+
+sf_status sf_save_state(sf_handle h, const char* path) {
+    if (!h || !path) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_save_state: no roads loaded");
+    std::vector<float> f((size_t)h->A * SF_NF);
+    std::vector<int32_t> i((size_t)h->A * SF_NI);
+    sf_status s = sf_get_state(h, f.data(), i.data());
+    if (s != SF_OK && s != SF_ERR_NONFINITE) return s;
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(h, SF_ERR_INVALID_ARG, std::string("sf_save_state: cannot open ") + path);
+    int32_t hdr[4] = {h->A, SF_NF, SF_NI, h->W};
+    bool ok = std::fwrite(kMagic, 1, 8, fp) == 8 && std::fwrite(hdr, 4, 4, fp) == 4 &&
+              std::fwrite(f.data(), 4, f.size(), fp) == f.size() && std::fwrite(i.data(), 4, i.size(), fp) == i.size();
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? s : fail(h, SF_ERR_INVALID_ARG, "sf_save_state: write failed");
+}
+
+sf_status sf_load_state(sf_handle h, const char* path) {
+    if (!h || !path) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_load_state: no roads loaded");
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(h, SF_ERR_INVALID_ARG, std::string("sf_load_state: cannot open ") + path);
+    char magic[8];
+    int32_t hdr[4];
+    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, kMagic, 8) == 0 && std::fread(hdr, 4, 4, fp) == 4 &&
+              hdr[0] == h->A && hdr[1] == SF_NF && hdr[2] == SF_NI && hdr[3] == h->W;
+    std::vector<float> f((size_t)h->A * SF_NF);
+    std::vector<int32_t> i((size_t)h->A * SF_NI);
+    ok = ok && std::fread(f.data(), 4, f.size(), fp) == f.size() && std::fread(i.data(), 4, i.size(), fp) == i.size();
+    std::fclose(fp);
+    if (!ok) return fail(h, SF_ERR_INVALID_ARG, "sf_load_state: bad or mismatched checkpoint");
+    return sf_set_state(h, f.data(), i.data());
+}
+
+sf_status sf_sync(sf_handle h) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    SF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (!h->loaded) return SF_OK;
+    unsigned int w = 0;
+    SF_CUDA(h, cudaMemcpy(&w, h->out.error_word, 4, cudaMemcpyDeviceToHost));
+    if (w) {
+        SF_CUDA(h, cudaMemset(h->out.error_word, 0, 4));
+        if (w & 1u) return fail(h, SF_ERR_NONFINITE, "an agent state went non-finite (agent parked or respawned)");
+        return fail(h, SF_ERR_TIMEOUT, "a bounded device wait gave up");
+    }
+    return SF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// sf_internal.cuh -- device-side layouts and constants of the vehicle step.
+//
+// Constants follow SceneFactory (arXiv 2605.08528): actuation App. F
+// Tab. app_action_params, rewards App. G Tab. app_reward_terms, observations
+// App. D, scene rules App. C; the vehicle of the benchmark workload (1500 kg,
+// 4.5 x 1.8 m box, r_w 0.33 m, k 35 kN/m, c 4 kN s/m, rest 0.3 m); where the
+// paper is silent the value is a stated reading.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sfk {
+
+// ---------------------------------------------------------------- vehicle
+constexpr double kMassD = 1500.0;
+constexpr double kLenD = 4.5, kWidD = 1.8, kHgtD = 0.5;       // box; height is a reading
+constexpr float kG = 9.81f;
+constexpr float kMass = 1500.0f;
+constexpr float kInvMass = (float)(1.0 / kMassD);
+constexpr float kHalfLen = 2.25f, kHalfWid = 0.9f;
+// uniform box inertia m/12 (b^2 + c^2) and its inverse
+constexpr double kIxxD = kMassD / 12.0 * (kWidD * kWidD + kHgtD * kHgtD);
+constexpr double kIyyD = kMassD / 12.0 * (kLenD * kLenD + kHgtD * kHgtD);
+constexpr double kIzzD = kMassD / 12.0 * (kLenD * kLenD + kWidD * kWidD);
+constexpr float kIxx = (float)kIxxD, kIyy = (float)kIyyD, kIzz = (float)kIzzD;
+constexpr float kInvIxx = (float)(1.0 / kIxxD), kInvIyy = (float)(1.0 / kIyyD), kInvIzz = (float)(1.0 / kIzzD);
+constexpr float kHardX = 1.3f, kHardY = 0.8f, kHardZ = -0.25f; // wheelbase 2.6 m (Sec. 3.2), track 1.6 m
+constexpr float kWheelR = 0.33f;
+constexpr float kKSusp = 35000.0f, kCSusp = 4000.0f, kRest = 0.3f;
+constexpr double kWheelID = 0.5 * 37.5 * 0.33 * 0.33 * 1.094;  // m_wheel, s_inertia (App. F)
+constexpr float kWheelI = (float)kWheelID;
+constexpr float kInvWheelI = (float)(1.0 / kWheelID);
+constexpr float kWheelR2OverI = (float)(0.33 * 0.33 / kWheelID);
+constexpr float kSteerI = 1.0f;
+constexpr float kThetaMax = 0.45f, kKp = 1839.5f, kKd = 110.5f, kTauSteer = 1200.0f;
+constexpr float kTauDrive = 600.7f, kTauBrkF = 1090.5f, kTauBrkR = 980.7f;
+constexpr float kLambdaYaw = 10.6f;
+constexpr float kUzMin = 0.05f;
+constexpr float kKContact = 1.0e6f, kCContact = 1.6e4f;
+constexpr float kDampRamp = 0.01f;   // suspension / contact dampers ramp in over 1 cm
+constexpr float kWheelbase = 2.6f;
+// static equilibrium height: hardpoint depth + (rest - m g / 4k) + wheel radius
+constexpr float kZStar = (float)(0.25 + (0.3 - kMassD * 9.81 / (4.0 * 35000.0)) + 0.33);
+// bounding-circle cull of footprint pairs: 2 * sqrt(hl^2 + hw^2), squared
+constexpr float kPairCull2 = (float)(4.0 * (2.25 * 2.25 + 0.9 * 0.9));
+
+// ---------------------------------------------------------------- rewards / events (App. G)
+constexpr float kGoalR = 3.0f, kWGoal = 45.0f, kWCollision = 6.0f, kWCrash = 10.0f, kWLaneForb = 20.0f;
+constexpr float kWProgress = 2.0f, kProgressClip = 2.0f;
+constexpr float kWLane = 0.08f, kLaneSigma = 1.75f, kLaneWh = 0.8f;
+constexpr float kWOffroad = 0.5f, kOffroadLat = 3.25f, kOffroadDist = 6.0f;
+constexpr float kWIdle = 0.05f, kIdleSpeed = 1.0f;
+constexpr float kTtcAlphaV = 0.10f, kTtcPmaxV = 0.35f, kTtcFloor = 0.5f, kTtcMax = 10.0f;
+constexpr float kTtcAlphaE = 0.07f, kTtcPmaxE = 0.40f, kEdgeHorizon = 40.0f;
+constexpr float kDracThresh = 3.4f, kWDrac = 0.01f, kDracGapFloor = 0.1f;
+constexpr float kDriftMax = 100.0f, kTiltGz = -0.15f;
+constexpr int kWarmup = 24, kMaxSteps = 1500;
+constexpr float kSceneHalf = 100.0f, kSegGapMax = 3.0f, kEdgeHalfWidth = 0.05f;
+// three TTC circles (App. D): r = max(0.45, 0.55 W), d = min(WB/2, max(0, L/2 - 0.8 r))
+constexpr float kCircR = 0.99f;
+constexpr float kCircD = 1.3f;
+
+// ---------------------------------------------------------------- resets
+constexpr float kSpawnGoalMin = 50.0f, kSpawnGoalMax = 150.0f;
+constexpr float kSpawnVMin = 5.0f, kSpawnVMax = 20.0f;
+constexpr float kSpawnSpacing = 10.0f, kParkX = 1000.0f;
+constexpr int kSpawnTries = 8;
+
+// ---------------------------------------------------------------- layout
+constexpr int kMaxAgents = 32;
+constexpr int kK = 8, kL = 32;
+constexpr int kObsEgo = 16, kObsNbr = 10, kObsPt = 7;
+constexpr int kObsDim = kObsEgo + kK * kObsNbr + kL * kObsPt;  // 320
+
+// point meta bits
+constexpr uint32_t kPtTypeMask = 0xFFu;
+constexpr uint32_t kPtSegNext = 1u << 8;   // point k and k+1 form a segment
+constexpr uint32_t kPtLane = 1u << 9;      // Waymo type 1 or 2
+constexpr uint32_t kPtEdge = 1u << 10;     // Waymo type 15 or 16
+
+// status and event bits (same values as the public header)
+constexpr uint32_t kAlive = 1u, kParked = 2u;
+constexpr uint32_t kEvGoal = 1u, kEvCollision = 2u, kEvCrash = 4u, kEvLaneForb = 8u, kEvOffroad = 16u,
+                   kEvIdle = 32u, kEvTimeout = 64u, kEvNonfinite = 128u, kEvRespawned = 256u;
+constexpr int kFlagInvincible = 1, kFlagAutoReset = 2, kFlagRecord = 4;
+
+}  // namespace sfk
+
+// Agent state, structure of float4 arrays, one element per agent.
+struct DevState {
+    float4* pos;     // px, py, pz, delta
+    float4* quat;    // qw, qx, qy, qz
+    float4* vel;     // vx, vy, vz, delta_dot
+    float4* angv;    // wx, wy, wz, mu
+    float4* spin;    // wheel spins FL FR RL RR
+    float4* goal;    // gx, gy, start x, start y
+    float* peak_drac;
+    uint32_t* meta;  // precip | surface << 8 | status << 16
+    int32_t* step;
+    int32_t* episode;
+};
+
+// Road store of all worlds.
+struct DevRoads {
+    const int4* world;      // (first agent, agent count, first point, point count)
+    const int2* cand;       // (first spawn candidate, candidate count)
+    const float4* pt;       // (x, y, road direction x, y)
+    const uint32_t* pmeta;  // type | kPt* bits
+    const int32_t* pend;    // one past the last point of the point's polyline
+    const int32_t* cands;   // spawn candidate point indices
+};
+
+struct DevOutputs {
+    float* obs;
+    float* reward;
+    uint8_t* done;
+    uint32_t* events;
+    int32_t* lane_seg;
+    int32_t* knn_pts;
+    int32_t* knn_agents;
+    float* drac;
+    unsigned int* error_word;  // bit0 non-finite seen
+};
+
+enum WorldMode { kModeStep = 0, kModeReset = 1, kModeObserve = 2 };
+
+struct WorldArgs {
+    DevState st;
+    DevRoads rd;
+    DevOutputs out;
+    const float* actions;   // [A][3]   (step mode)
+    const uint8_t* mask;    // [A]      (reset mode)
+    int num_worlds;
+    int num_agents;
+    float h;                // substep length
+    int substeps;
+    int flags;
+    unsigned long long seed;
+};
+
+// launch wrappers (sf_world.cu)
+cudaError_t sf_launch_world(int mode, const WorldArgs& a, int warps_per_block, cudaStream_t s);
+cudaError_t sf_launch_place(const WorldArgs& a, const float* d_place, cudaStream_t s);

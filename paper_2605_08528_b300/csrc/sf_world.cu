@@ -1,0 +1,893 @@
+// sf_world.cu -- the fused per-world kernel of the vehicle step (sm_103a).
+//
+// One warp steps one world: lane l owns agent (first agent of the world + l),
+// so a world holds at most 32 agents.  Every substep the lanes publish their
+// footprint (centre, heading, velocity) in shared memory, each lane sums the
+// penalty contact of every overlapping pair it belongs to (pairs evaluated in
+// canonical (lo, hi) order so both partners see bit-identical forces), then
+// integrates its own chassis.  After the substeps the warp computes events and
+// rewards from the end-of-step poses, respawns done agents one after another
+// (the spacing test is a warp-wide min over the other agents), and writes the
+// observations.  All road queries scan the world's points in ascending index
+// order, so every selection (nearest segment, k nearest points / agents) is the
+// lexicographic (key, index) minimum.
+//
+// The model follows SceneFactory (arXiv 2605.08528): steering PD (Sec. 3.2
+// Eq. steer_pd), FWD drive and 4-wheel brakes (App. F), rectified throttle and
+// brake (App. F), yaw damping wrench (Sec. 3.2), rewards and events (App. G),
+// observations (App. D), teleport resets (App. J).  The tire/suspension/contact
+// model is the raycast, friction-circle, symplectic-Euler reading of the
+// unstated PhysX internals.
+#include "sf_internal.cuh"
+
+#include <math.h>
+
+using namespace sfk;
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+#define kInf __int_as_float(0x7f800000)
+
+struct Agent {
+    float px, py, pz, dl;
+    float dpx, dpy, dpz;   // displacement since the start of the control step
+    float qw, qx, qy, qz;
+    float vx, vy, vz, dd;
+    float wx, wy, wz, mu;
+    float s0, s1, s2, s3;
+    float gx, gy, sx, sy;
+    float peak;
+    uint32_t meta;
+    int step, episode;
+};
+
+__device__ __forceinline__ float clampf(float x, float lo, float hi) { return x < lo ? lo : (x > hi ? hi : x); }
+__device__ __forceinline__ float cross2(float ax, float ay, float bx, float by) { return ax * by - ay * bx; }
+__device__ __forceinline__ uint32_t status_of(uint32_t meta) { return (meta >> 16) & 0xFFu; }
+__device__ __forceinline__ uint32_t with_status(uint32_t meta, uint32_t st) { return (meta & 0xFFFFu) | (st << 16); }
+
+// SplitMix64 (Steele, Lea, Flood 2014): the counter-based generator of resets.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long reset_draw(unsigned long long seed, int a, int e, int r, int j) {
+    unsigned long long h = splitmix64(splitmix64(seed) ^ (unsigned long long)(uint32_t)a);
+    return splitmix64(h ^ (((unsigned long long)(uint32_t)e << 32) | (unsigned long long)(uint32_t)(r * 4 + j)));
+}
+__device__ __forceinline__ float u24(unsigned long long h) { return (float)(uint32_t)(h >> 40) * (1.0f / 16777216.0f); }
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__device__ __forceinline__ void quat_to_mat(float w, float x, float y, float z, float R[3][3]) {
+    R[0][0] = 1.f - 2.f * (y * y + z * z); R[0][1] = 2.f * (x * y - w * z);       R[0][2] = 2.f * (x * z + w * y);
+    R[1][0] = 2.f * (x * y + w * z);       R[1][1] = 1.f - 2.f * (x * x + z * z); R[1][2] = 2.f * (y * z - w * x);
+    R[2][0] = 2.f * (x * z - w * y);       R[2][1] = 2.f * (y * z + w * x);       R[2][2] = 1.f - 2.f * (x * x + y * y);
+}
+
+// planar heading: body x axis projected on the road plane
+__device__ __forceinline__ void heading_of(float qw, float qx, float qy, float qz, float& hx, float& hy) {
+    float r00 = 1.f - 2.f * (qy * qy + qz * qz);
+    float r10 = 2.f * (qx * qy + qw * qz);
+    float n = sqrtf(r00 * r00 + r10 * r10);
+    if (n > 0.f) { hx = r00 / n; hy = r10 / n; } else { hx = 1.f; hy = 0.f; }
+}
+
+__device__ __forceinline__ void to_ego(float hx, float hy, float x, float y, float& bx, float& by) {
+    bx = hx * x + hy * y;
+    by = -hy * x + hx * y;
+}
+
+__device__ __forceinline__ float seg_dist2(float ax, float ay, float bx, float by, float qx, float qy) {
+    float ex = bx - ax, ey = by - ay;
+    float l2 = ex * ex + ey * ey;
+    float t = l2 > 0.f ? ((qx - ax) * ex + (qy - ay) * ey) / l2 : 0.f;
+    t = clampf(t, 0.f, 1.f);
+    float dx = qx - ax - t * ex, dy = qy - ay - t * ey;
+    return dx * dx + dy * dy;
+}
+
+// ------------------------------------------------------------------ footprint contact
+// 2-D SAT of two 4.5 x 1.8 m footprints; axes (i.x, i.y, j.x, j.y); depth is the
+// minimum overlap (ties: lowest axis), normal oriented from i to j.
+__device__ __forceinline__ float sat2d(float cix, float ciy, float hix, float hiy, float cjx, float cjy, float hjx,
+                                       float hjy, float& nx, float& ny) {
+    const float ax[4] = {hix, -hiy, hjx, -hjy};
+    const float ay[4] = {hiy, hix, hjy, hjx};
+    float dcx = cjx - cix, dcy = cjy - ciy;
+    float best = kInf, sgn = 1.f;
+    int bk = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float a0 = ax[k], a1 = ay[k];
+        float ri = kHalfLen * fabsf(hix * a0 + hiy * a1) + kHalfWid * fabsf(-hiy * a0 + hix * a1);
+        float rj = kHalfLen * fabsf(hjx * a0 + hjy * a1) + kHalfWid * fabsf(-hjy * a0 + hjx * a1);
+        float d = dcx * a0 + dcy * a1;
+        float o = ri + rj - fabsf(d);
+        if (o <= 0.f) { nx = ny = 0.f; return 0.f; }
+        if (o < best) { best = o; bk = k; sgn = d >= 0.f ? 1.f : -1.f; }
+    }
+    float bx = bk == 0 ? ax[0] : bk == 1 ? ax[1] : bk == 2 ? ax[2] : ax[3];
+    float by = bk == 0 ? ay[0] : bk == 1 ? ay[1] : bk == 2 ? ay[2] : ay[3];
+    nx = sgn * bx; ny = sgn * by;
+    return best;
+}
+
+// penalty force of pair (lo, hi) on hi, and the torque both bodies receive
+// (force pair at the midpoint of the footprint centres, in each CoM plane)
+// (ci, di): start-of-step position and in-step displacement of each agent; the
+// separation (cj - ci) + (dj - di) avoids rounding the positions of every substep
+__device__ __forceinline__ void pair_force(float cix, float ciy, float dix, float diy, float hix, float hiy, float vix,
+                                           float viy, float cjx, float cjy, float djx, float djy, float hjx, float hjy,
+                                           float vjx, float vjy, float& fx, float& fy, float& tz) {
+    fx = fy = tz = 0.f;
+    float dx = (cjx - cix) + (djx - dix), dy = (cjy - ciy) + (djy - diy);
+    if (dx * dx + dy * dy > kPairCull2) return;
+    float nx, ny;
+    float depth = sat2d(0.f, 0.f, hix, hiy, dx, dy, hjx, hjy, nx, ny);
+    if (!(depth > 0.f)) return;
+    float vn = (vix - vjx) * nx + (viy - vjy) * ny;
+    float fm = fmaxf(0.f, kKContact * depth + kCContact * vn * fminf(1.f, depth / kDampRamp));
+    fx = fm * nx; fy = fm * ny;
+    float mx = 0.5f * dx, my = 0.5f * dy;
+    tz = cross2(-mx, -my, fx, fy);
+}
+
+// ------------------------------------------------------------------ one chassis substep
+// steering PD, suspension rays, predicted velocities, friction-circle wheel
+// impulses (Jacobi, shared by the wheels in contact), brake, positions.
+__device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, float brk, float fcx, float fcy,
+                                             float tcz, float h) {
+    // 1. steering (Eq. steer_pd)
+    float ts = clampf(kKp * (dstar - A.dl) - kKd * A.dd, -kTauSteer, kTauSteer);
+    A.dd += h * ts / kSteerI;
+    A.dl += h * A.dd;
+    if (A.dl > kThetaMax) { A.dl = kThetaMax; A.dd = 0.f; }
+    if (A.dl < -kThetaMax) { A.dl = -kThetaMax; A.dd = 0.f; }
+
+    // 2. rotation, world inverse inertia (symmetric), world inertia
+    float R[3][3];
+    quat_to_mat(A.qw, A.qx, A.qy, A.qz, R);
+    float Ii[3][3], Iw[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            Ii[a][b] = R[a][0] * R[b][0] * kInvIxx + R[a][1] * R[b][1] * kInvIyy + R[a][2] * R[b][2] * kInvIzz;
+            Iw[a][b] = R[a][0] * R[b][0] * kIxx + R[a][1] * R[b][1] * kIyy + R[a][2] * R[b][2] * kIzz;
+        }
+    const float ux = R[0][2], uy = R[1][2], uz = R[2][2];
+
+    // 3. suspension rays from the hardpoints along -u to the plane z = 0
+    float N[4], rcx[4], rcy[4], rcz[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float bx = i < 2 ? kHardX : -kHardX;
+        const float by = (i & 1) == 0 ? kHardY : -kHardY;
+        const float bz = kHardZ;
+        float rbx = R[0][0] * bx + R[0][1] * by + R[0][2] * bz;
+        float rby = R[1][0] * bx + R[1][1] * by + R[1][2] * bz;
+        float rbz = R[2][0] * bx + R[2][1] * by + R[2][2] * bz;
+        N[i] = 0.f; rcx[i] = rcy[i] = rcz[i] = 0.f;
+        if (uz > kUzMin) {
+            float az = (A.pz + A.dpz) + rbz;
+            float t = az / uz;
+            float l = t - kWheelR;
+            if (l < kRest) {
+                float x = kRest - fmaxf(l, 0.f);
+                float wrz = A.wx * rby - A.wy * rbx;            // (w x rb).z
+                float xdot = -(A.vz + wrz) / uz;
+                // the damper engages over the first kDampRamp of compression:
+                // the normal force is continuous at touchdown
+                N[i] = fmaxf(0.f, kKSusp * x + kCSusp * xdot * fminf(1.f, x / kDampRamp));
+                rcx[i] = rbx - t * ux; rcy[i] = rby - t * uy; rcz[i] = rbz - t * uz;
+            }
+        }
+    }
+
+    // 4. predicted velocities
+    float Fx = fcx, Fy = fcy, Fz = -kMass * kG;
+    float Tx = 0.f, Ty = 0.f, Tz = tcz - kLambdaYaw * A.wz;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        Fz += N[i];
+        Tx += rcy[i] * N[i];
+        Ty -= rcx[i] * N[i];
+    }
+    float Lx = Iw[0][0] * A.wx + Iw[0][1] * A.wy + Iw[0][2] * A.wz;
+    float Ly = Iw[1][0] * A.wx + Iw[1][1] * A.wy + Iw[1][2] * A.wz;
+    float Lz = Iw[2][0] * A.wx + Iw[2][1] * A.wy + Iw[2][2] * A.wz;
+    float nx_ = Tx - (A.wy * Lz - A.wz * Ly);
+    float ny_ = Ty - (A.wz * Lx - A.wx * Lz);
+    float nz_ = Tz - (A.wx * Ly - A.wy * Lx);
+    float v1x = A.vx + h * Fx * kInvMass, v1y = A.vy + h * Fy * kInvMass, v1z = A.vz + h * Fz * kInvMass;
+    float w1x = A.wx + h * (Ii[0][0] * nx_ + Ii[0][1] * ny_ + Ii[0][2] * nz_);
+    float w1y = A.wy + h * (Ii[1][0] * nx_ + Ii[1][1] * ny_ + Ii[1][2] * nz_);
+    float w1z = A.wz + h * (Ii[2][0] * nx_ + Ii[2][1] * ny_ + Ii[2][2] * nz_);
+    const float drive = h * thr * kTauDrive * kInvWheelI;
+    float sp[4] = {A.s0 + drive, A.s1 + drive, A.s2, A.s3};
+
+    // 5. friction impulses, friction circle per wheel; each wheel takes the
+    // chassis share of one of four wheels (a Jacobi step relaxed by 1/4: no
+    // overshoot, and continuous when a wheel unloads)
+    const float ncf = 4.f;
+    float sd, cd;
+    sincosf(A.dl, &sd, &cd);
+    float Px = 0.f, Py = 0.f, Lmx = 0.f, Lmy = 0.f, Lmz = 0.f;
+    float sp2[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        sp2[i] = sp[i];
+        if (!(N[i] > 0.f)) continue;
+        const float c = i < 2 ? cd : 1.f, s = i < 2 ? sd : 0.f;
+        float fwx = R[0][0] * c + R[0][1] * s;
+        float fwy = R[1][0] * c + R[1][1] * s;
+        float fl = sqrtf(fwx * fwx + fwy * fwy);
+        if (!(fl > 0.f)) continue;
+        float elx = fwx / fl, ely = fwy / fl;
+        float etx = -ely, ety = elx;
+        float vcx = v1x + (w1y * rcz[i] - w1z * rcy[i]);
+        float vcy = v1y + (w1z * rcx[i] - w1x * rcz[i]);
+        // r x e for e in the plane: (-rz ey, rz ex, rx ey - ry ex)
+        float ax_ = -rcz[i] * ely, ay_ = rcz[i] * elx, az_ = rcx[i] * ely - rcy[i] * elx;
+        float q1 = ax_ * (Ii[0][0] * ax_ + Ii[0][1] * ay_ + Ii[0][2] * az_) +
+                   ay_ * (Ii[1][0] * ax_ + Ii[1][1] * ay_ + Ii[1][2] * az_) +
+                   az_ * (Ii[2][0] * ax_ + Ii[2][1] * ay_ + Ii[2][2] * az_);
+        float wl = kWheelR2OverI + ncf * (kInvMass + q1);
+        float bx_ = -rcz[i] * ety, by_ = rcz[i] * etx, bz_ = rcx[i] * ety - rcy[i] * etx;
+        float q2 = bx_ * (Ii[0][0] * bx_ + Ii[0][1] * by_ + Ii[0][2] * bz_) +
+                   by_ * (Ii[1][0] * bx_ + Ii[1][1] * by_ + Ii[1][2] * bz_) +
+                   bz_ * (Ii[2][0] * bx_ + Ii[2][1] * by_ + Ii[2][2] * bz_);
+        float wt = ncf * (kInvMass + q2);
+        float ul = sp[i] * kWheelR - (vcx * elx + vcy * ely);
+        float ut = -(vcx * etx + vcy * ety);
+        float jl = ul / wl, jt = ut / wt;
+        float cap = A.mu * N[i] * h;
+        float jn = sqrtf(jl * jl + jt * jt);
+        float sc = jn <= cap ? 1.f : cap / jn;
+        jl *= sc; jt *= sc;
+        float Jx = jl * elx + jt * etx, Jy = jl * ely + jt * ety;
+        Px += Jx; Py += Jy;
+        Lmx += -rcz[i] * Jy;
+        Lmy += rcz[i] * Jx;
+        Lmz += rcx[i] * Jy - rcy[i] * Jx;
+        sp2[i] = sp[i] - jl * kWheelR * kInvWheelI;
+    }
+    const float bf = h * brk * kTauBrkF * kInvWheelI, br = h * brk * kTauBrkR * kInvWheelI;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float m = fmaxf(fabsf(sp2[i]) - (i < 2 ? bf : br), 0.f);
+        sp2[i] = sp2[i] >= 0.f ? m : -m;
+    }
+    A.s0 = sp2[0]; A.s1 = sp2[1]; A.s2 = sp2[2]; A.s3 = sp2[3];
+
+    // 6. apply impulses
+    v1x += Px * kInvMass; v1y += Py * kInvMass;
+    w1x += Ii[0][0] * Lmx + Ii[0][1] * Lmy + Ii[0][2] * Lmz;
+    w1y += Ii[1][0] * Lmx + Ii[1][1] * Lmy + Ii[1][2] * Lmz;
+    w1z += Ii[2][0] * Lmx + Ii[2][1] * Lmy + Ii[2][2] * Lmz;
+
+    // 7. positions, attitude q += h/2 (0, w) (x) q, normalised
+    A.dpx += h * v1x; A.dpy += h * v1y; A.dpz += h * v1z;
+    float qw = A.qw, qx = A.qx, qy = A.qy, qz = A.qz;
+    float dqw = -(w1x * qx + w1y * qy + w1z * qz);
+    float dqx = w1x * qw + (w1y * qz - w1z * qy);
+    float dqy = w1y * qw + (w1z * qx - w1x * qz);
+    float dqz = w1z * qw + (w1x * qy - w1y * qx);
+    qw += 0.5f * h * dqw; qx += 0.5f * h * dqx; qy += 0.5f * h * dqy; qz += 0.5f * h * dqz;
+    float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    A.qw = qw / qn; A.qx = qx / qn; A.qy = qy / qn; A.qz = qz / qn;
+    A.vx = v1x; A.vy = v1y; A.vz = v1z;
+    A.wx = w1x; A.wy = w1y; A.wz = w1z;
+}
+
+// ------------------------------------------------------------------ road queries
+struct Lane {
+    int seg;
+    float dist, lat, tx, ty;  // tangent oriented toward the goal, lat sign follows it
+};
+
+__device__ __forceinline__ Lane nearest_lane(const DevRoads& rd, int p0, int np, float qx, float qy, float gx,
+                                             float gy) {
+    int best = -1;
+    float bd2 = kInf;
+    for (int k = p0; k < p0 + np; ++k) {
+        const uint32_t m = __ldg(&rd.pmeta[k]);
+        if ((m & (kPtSegNext | kPtLane)) != (kPtSegNext | kPtLane)) continue;
+        const float4 a = __ldg(&rd.pt[k]);
+        const float4 b = __ldg(&rd.pt[k + 1]);
+        float d2 = seg_dist2(a.x, a.y, b.x, b.y, qx, qy);
+        if (d2 < bd2) { bd2 = d2; best = k; }
+    }
+    Lane L;
+    L.seg = best;
+    if (best < 0) { L.dist = kInf; L.lat = 0.f; L.tx = L.ty = 0.f; return L; }
+    const float4 a = __ldg(&rd.pt[best]);
+    const float4 b = __ldg(&rd.pt[best + 1]);
+    float ex = b.x - a.x, ey = b.y - a.y;
+    float n = sqrtf(ex * ex + ey * ey);
+    float tx = ex / n, ty = ey / n;
+    float lat = cross2(tx, ty, qx - a.x, qy - a.y);
+    if (tx * (gx - qx) + ty * (gy - qy) < 0.f) { tx = -tx; ty = -ty; lat = -lat; }
+    L.dist = sqrtf(bd2); L.lat = lat; L.tx = tx; L.ty = ty;
+    return L;
+}
+
+// swept three-circle TTC (App. D), clamped to [0, 10] s; behind or no root -> 10
+__device__ __forceinline__ float ttc_pair(float pix, float piy, float hix, float hiy, float vix, float viy, float pjx,
+                                          float pjy, float hjx, float hjy, float vjx, float vjy) {
+    float bx, by;
+    to_ego(hix, hiy, pjx - pix, pjy - piy, bx, by);
+    if (bx < 0.f) return kTtcMax;
+    float dvx = vjx - vix, dvy = vjy - viy;
+    float A2 = dvx * dvx + dvy * dvy;
+    float best = kInf;
+#pragma unroll
+    for (int a = -1; a <= 1; ++a)
+#pragma unroll
+        for (int b = -1; b <= 1; ++b) {
+            float dx = (pjx + (float)b * kCircD * hjx) - (pix + (float)a * kCircD * hix);
+            float dy = (pjy + (float)b * kCircD * hjy) - (piy + (float)a * kCircD * hiy);
+            float B = 2.f * (dx * dvx + dy * dvy);
+            float C = dx * dx + dy * dy - 4.f * kCircR * kCircR;
+            float t;
+            if (C <= 0.f) t = 0.f;
+            else if (B >= 0.f) continue;
+            else {
+                float disc = B * B - 4.f * A2 * C;
+                if (disc < 0.f) continue;
+                t = 2.f * C / (-B + sqrtf(disc));
+            }
+            best = fminf(best, t);
+        }
+    if (best == kInf) return kTtcMax;
+    return clampf(best, 0.f, kTtcMax);
+}
+
+__device__ __forceinline__ float drac_pair(float pix, float piy, float vix, float viy, float pjx, float pjy, float vjx,
+                                           float vjy) {
+    float rx = pjx - pix, ry = pjy - piy;
+    float dist = sqrtf(rx * rx + ry * ry);
+    if (!(dist > 0.f)) return 0.f;
+    float vr = -((vjx - vix) * rx + (vjy - viy) * ry) / dist;
+    float gap = fmaxf(dist - 2.f * kHalfLen, kDracGapFloor);
+    return vr > 0.f ? vr * vr / (2.f * gap) : 0.f;
+}
+
+__device__ __forceinline__ float penalty(float alpha, float tau, float pmax) {
+    return fminf(alpha / fmaxf(tau, kTtcFloor), pmax);
+}
+
+// per-warp exchange area: footprints of the world's agents
+struct Exch {
+    float px[32], py[32], hx[32], hy[32], vx[32], vy[32], dx[32], dy[32];
+};
+
+__device__ __forceinline__ void publish(Exch& E, int lane, const Agent& A, float hx, float hy) {
+    E.px[lane] = A.px; E.py[lane] = A.py;
+    E.hx[lane] = hx; E.hy[lane] = hy;
+    E.vx[lane] = A.vx; E.vy[lane] = A.vy;
+    E.dx[lane] = A.dpx; E.dy[lane] = A.dpy;
+}
+
+// K nearest alive other agents (lexicographic (d^2, index) order); local lane ids
+__device__ __forceinline__ void knn_agents(const Exch& E, int n, int lane, uint32_t alive_bits, float px, float py,
+                                           int nb[kK]) {
+    float key[kK];
+#pragma unroll
+    for (int t = 0; t < kK; ++t) { key[t] = kInf; nb[t] = -1; }
+    for (int j = 0; j < n; ++j) {
+        if (j == lane || !((alive_bits >> j) & 1u)) continue;
+        float dx = E.px[j] - px, dy = E.py[j] - py;
+        float d2 = dx * dx + dy * dy;
+        if (!(d2 < key[kK - 1])) continue;
+        float ck = d2;
+        int ci = j;
+        bool ins = false;
+#pragma unroll
+        for (int t = 0; t < kK; ++t) {
+            if (ins || ck < key[t]) {
+                float tk = key[t]; key[t] = ck; ck = tk;
+                int ti = nb[t]; nb[t] = ci; ci = ti;
+                ins = true;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void load_agent(const DevState& st, int a, Agent& A) {
+    float4 p = st.pos[a], q = st.quat[a], v = st.vel[a], w = st.angv[a], s = st.spin[a], g = st.goal[a];
+    A.px = p.x; A.py = p.y; A.pz = p.z; A.dl = p.w;
+    A.qw = q.x; A.qx = q.y; A.qy = q.z; A.qz = q.w;
+    A.vx = v.x; A.vy = v.y; A.vz = v.z; A.dd = v.w;
+    A.wx = w.x; A.wy = w.y; A.wz = w.z; A.mu = w.w;
+    A.s0 = s.x; A.s1 = s.y; A.s2 = s.z; A.s3 = s.w;
+    A.gx = g.x; A.gy = g.y; A.sx = g.z; A.sy = g.w;
+    A.peak = st.peak_drac[a];
+    A.meta = st.meta[a];
+    A.step = st.step[a];
+    A.episode = st.episode[a];
+    A.dpx = A.dpy = A.dpz = 0.f;
+}
+
+__device__ __forceinline__ void store_agent(const DevState& st, int a, const Agent& A) {
+    st.pos[a] = make_float4(A.px, A.py, A.pz, A.dl);
+    st.quat[a] = make_float4(A.qw, A.qx, A.qy, A.qz);
+    st.vel[a] = make_float4(A.vx, A.vy, A.vz, A.dd);
+    st.angv[a] = make_float4(A.wx, A.wy, A.wz, A.mu);
+    st.spin[a] = make_float4(A.s0, A.s1, A.s2, A.s3);
+    st.goal[a] = make_float4(A.gx, A.gy, A.sx, A.sy);
+    st.peak_drac[a] = A.peak;
+    st.meta[a] = A.meta;
+    st.step[a] = A.step;
+    st.episode[a] = A.episode;
+}
+
+__device__ __forceinline__ bool finite_agent(const Agent& A) {
+    float s = A.px + A.py + A.pz + A.dl + A.qw + A.qx + A.qy + A.qz + A.vx + A.vy + A.vz + A.dd + A.wx + A.wy +
+              A.wz + A.s0 + A.s1 + A.s2 + A.s3;
+    return isfinite(s) && isfinite(A.px) && isfinite(A.vx);
+}
+
+__constant__ float c_mu_table[4][3] = {{0.90f, 0.85f, 0.60f},   // dry       (asphalt, concrete, gravel)
+                                       {0.70f, 0.65f, 0.50f},   // light rain
+                                       {0.50f, 0.45f, 0.40f},   // heavy rain
+                                       {0.30f, 0.25f, 0.20f}};  // snow
+
+// place agent at (x, y) heading psi with speed v0, static equilibrium, rolling wheels
+__device__ __forceinline__ void place_agent(Agent& A, float x, float y, float psi, float v0, float gx, float gy) {
+    float s, c, sh, ch;
+    sincosf(psi, &s, &c);
+    sincosf(0.5f * psi, &sh, &ch);
+    A.px = x; A.py = y; A.pz = kZStar; A.dl = 0.f;
+    A.qw = ch; A.qx = 0.f; A.qy = 0.f; A.qz = sh;
+    A.vx = v0 * c; A.vy = v0 * s; A.vz = 0.f; A.dd = 0.f;
+    A.wx = A.wy = A.wz = 0.f;
+    float om = v0 / kWheelR;
+    A.s0 = A.s1 = A.s2 = A.s3 = om;
+    A.gx = gx; A.gy = gy; A.sx = x; A.sy = y;
+    uint32_t pc = A.meta & 0xFFu, sc = (A.meta >> 8) & 0xFFu;
+    A.mu = c_mu_table[pc > 3 ? 3 : pc][sc > 2 ? 2 : sc];
+    A.peak = 0.f;
+    A.step = 0;
+    A.meta = with_status(A.meta, kAlive);
+}
+
+__device__ __forceinline__ void park_agent(Agent& A) {
+    A.px = kParkX; A.py = 0.f;
+    A.vx = A.vy = A.vz = 0.f;
+    A.wx = A.wy = A.wz = 0.f;
+    A.s0 = A.s1 = A.s2 = A.s3 = 0.f;
+    A.meta = with_status(A.meta, kParked);
+}
+
+// spawn candidate r of agent a (global index) for episode ep (App. J reading)
+// a world without lane points spawns its slot k at (0, k * spacing), heading +x
+__device__ void spawn_candidate(const DevRoads& rd, int w, int a, int slot, int ep, int r, unsigned long long seed,
+                                float& x, float& y, float& psi, float& gx, float& gy, float& v0) {
+    const int2 cw = __ldg(&rd.cand[w]);
+    x = 0.f; y = (float)slot * kSpawnSpacing; psi = 0.f; gx = kSpawnGoalMin; gy = y;
+    if (cw.y > 0) {
+        uint32_t pick = (uint32_t)(reset_draw(seed, a, ep, r, 0) >> 32) % (uint32_t)cw.y;
+        int k = __ldg(&rd.cands[cw.x + (int)pick]);
+        float4 p = __ldg(&rd.pt[k]);
+        x = p.x; y = p.y;
+        psi = atan2f(p.w, p.z);
+        float dg = kSpawnGoalMin + (kSpawnGoalMax - kSpawnGoalMin) * u24(reset_draw(seed, a, ep, r, 1));
+        int k1 = __ldg(&rd.pend[k]);
+        int g = k1 - 1;
+        float s = 0.f;
+        float prx = p.x, pry = p.y;
+        for (int j = k + 1; j < k1; ++j) {
+            float4 q = __ldg(&rd.pt[j]);
+            float dx = q.x - prx, dy = q.y - pry;
+            s += sqrtf(dx * dx + dy * dy);
+            prx = q.x; pry = q.y;
+            if (s >= dg) { g = j; break; }
+        }
+        float4 G = __ldg(&rd.pt[g]);
+        gx = G.x; gy = G.y;
+    }
+    v0 = kSpawnVMin + (kSpawnVMax - kSpawnVMin) * u24(reset_draw(seed, a, ep, r, 2));
+}
+
+}  // namespace
+
+// ====================================================================== the world kernel
+template <int MODE, int WPB>
+__global__ void __launch_bounds__(32 * WPB) world_kernel(const WorldArgs args) {
+    __shared__ Exch ex_all[WPB];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = blockIdx.x * WPB + warp;
+    if (w >= args.num_worlds) return;                 // warp-uniform
+    Exch& E = ex_all[warp];
+    const int4 wd = __ldg(&args.rd.world[w]);
+    const int a0 = wd.x, n = wd.y, p0 = wd.z, np = wd.w;
+    if (n <= 0) return;                               // warp-uniform
+    const bool has = lane < n;
+    const int a = a0 + (has ? lane : 0);
+    const DevState& st = args.st;
+
+    Agent A;
+    load_agent(st, a, A);
+    if (!has) { A.meta = 0; }
+    bool alive = has && (status_of(A.meta) & kAlive);
+
+    uint32_t ev = 0;
+    float reward = 0.f, drac = 0.f;
+    bool done = false;
+    bool respawn = false;
+    Lane lane_info;
+    lane_info.seg = -1; lane_info.dist = kInf; lane_info.lat = 0.f; lane_info.tx = lane_info.ty = 0.f;
+    int nb[kK];
+#pragma unroll
+    for (int t = 0; t < kK; ++t) nb[t] = -1;
+    bool have_lane = false;
+    bool parked_now = false;
+
+    if (MODE == kModeReset) {
+        respawn = has && args.mask[a] != 0;
+        if (__ballot_sync(kFull, respawn) == 0) return;   // nothing to do in this world
+    }
+
+    if (MODE == kModeStep) {
+        float thr = 0.f, dstar = 0.f, brk = 0.f;
+        if (alive) {
+            const float* act = args.actions + 3 * (size_t)a;
+            thr = clampf(act[0], 0.f, 1.f);
+            dstar = kThetaMax * clampf(act[1], -1.f, 1.f);
+            brk = clampf(act[2], 0.f, 1.f);
+        }
+        const float prevx = A.px, prevy = A.py;
+        // ---------------- substeps with footprint contact
+        for (int s = 0; s < args.substeps; ++s) {
+            float hx, hy;
+            heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
+            publish(E, lane, A, hx, hy);
+            const uint32_t alive_bits = __ballot_sync(kFull, alive);
+            __syncwarp();
+            float fcx = 0.f, fcy = 0.f, tcz = 0.f;
+            if (alive) {
+                for (int j = 0; j < n; ++j) {
+                    if (j == lane || !((alive_bits >> j) & 1u)) continue;
+                    const int lo = min(lane, j), hi = max(lane, j);
+                    float fx, fy, tz;
+                    pair_force(E.px[lo], E.py[lo], E.dx[lo], E.dy[lo], E.hx[lo], E.hy[lo], E.vx[lo], E.vy[lo],
+                               E.px[hi], E.py[hi], E.dx[hi], E.dy[hi], E.hx[hi], E.hy[hi], E.vx[hi], E.vy[hi], fx,
+                               fy, tz);
+                    if (lane == lo) { fcx -= fx; fcy -= fy; } else { fcx += fx; fcy += fy; }
+                    tcz += tz;
+                }
+            }
+            __syncwarp();
+            if (alive) body_substep(A, thr, dstar, brk, fcx, fcy, tcz, args.h);
+        }
+        A.px += A.dpx; A.py += A.dpy; A.pz += A.dpz;
+        A.dpx = A.dpy = A.dpz = 0.f;
+        // ---------------- non-finite guard
+        bool nonfin = false;
+        if (alive && !finite_agent(A)) {
+            nonfin = true;
+            park_agent(A);
+            alive = false;
+            atomicOr(args.out.error_word, 1u);
+        }
+        // ---------------- events and rewards from the end-of-step poses (App. G)
+        float hx, hy;
+        heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
+        publish(E, lane, A, hx, hy);
+        const uint32_t alive_bits = __ballot_sync(kFull, alive);
+        __syncwarp();
+        if (alive) {
+            A.step += 1;
+            const float speed = sqrtf(A.vx * A.vx + A.vy * A.vy);
+            lane_info = nearest_lane(args.rd, p0, np, A.px, A.py, A.gx, A.gy);
+            have_lane = true;
+            float r = 0.f;
+            if (lane_info.seg >= 0) {
+                float prog = (A.px - prevx) * lane_info.tx + (A.py - prevy) * lane_info.ty;
+                r += kWProgress * clampf(prog, -kProgressClip, kProgressClip);
+                float e = lane_info.lat / kLaneSigma;
+                float cosd = hx * lane_info.tx + hy * lane_info.ty;
+                r += kWLane * (expf(-e * e) * ((1.f - kLaneWh) + kLaneWh * fmaxf(0.f, cosd)));
+            }
+            if (fabsf(lane_info.lat) > kOffroadLat || lane_info.dist > kOffroadDist) { ev |= kEvOffroad; r -= kWOffroad; }
+            if (speed < kIdleSpeed) { ev |= kEvIdle; r -= kWIdle; }
+
+            knn_agents(E, n, lane, alive_bits, A.px, A.py, nb);
+            float tmin = kTtcMax, dmax = 0.f;
+#pragma unroll
+            for (int t = 0; t < kK; ++t) {
+                if (nb[t] < 0) continue;
+                const int j = nb[t];
+                float tt = ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j], E.vx[j],
+                                    E.vy[j]);
+                tmin = fminf(tmin, tt);
+                dmax = fmaxf(dmax, drac_pair(A.px, A.py, A.vx, A.vy, E.px[j], E.py[j], E.vx[j], E.vy[j]));
+            }
+            if (tmin < kTtcMax) r -= penalty(kTtcAlphaV, tmin, kTtcPmaxV);
+            r -= kWDrac * fmaxf(0.f, dmax - kDracThresh);
+            drac = dmax;
+            A.peak = fmaxf(A.peak, dmax);
+
+            bool collided = false;
+            for (int j = 0; j < n && !collided; ++j) {
+                if (j == lane || !((alive_bits >> j) & 1u)) continue;
+                float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
+                if (dx * dx + dy * dy > kPairCull2) continue;
+                float nx, ny;
+                if (sat2d(A.px, A.py, hx, hy, E.px[j], E.py[j], E.hx[j], E.hy[j], nx, ny) > 0.f) collided = true;
+            }
+            if (collided && A.step > kWarmup) ev |= kEvCollision;
+
+            // road edges: lane-forbidden circles and the edge time-to-collision ray
+            float tedge = kInf;
+            bool forb = false;
+            const float lim2 = (kCircR + kEdgeHalfWidth) * (kCircR + kEdgeHalfWidth);
+            for (int k = p0; k < p0 + np; ++k) {
+                const uint32_t m = __ldg(&args.rd.pmeta[k]);
+                if ((m & (kPtSegNext | kPtEdge)) != (kPtSegNext | kPtEdge)) continue;
+                const float4 pa = __ldg(&args.rd.pt[k]);
+                const float4 pb = __ldg(&args.rd.pt[k + 1]);
+#pragma unroll
+                for (int c = -1; c <= 1; ++c) {
+                    float cx = A.px + (float)c * kCircD * hx, cy = A.py + (float)c * kCircD * hy;
+                    if (seg_dist2(pa.x, pa.y, pb.x, pb.y, cx, cy) < lim2) forb = true;
+                }
+                float exx = pb.x - pa.x, eyy = pb.y - pa.y;
+                float den = cross2(A.vx, A.vy, exx, eyy);
+                if (den != 0.f) {
+                    float t = cross2(pa.x - A.px, pa.y - A.py, exx, eyy) / den;
+                    float sg = cross2(pa.x - A.px, pa.y - A.py, A.vx, A.vy) / den;
+                    if (t >= 0.f && sg >= 0.f && sg <= 1.f && speed * t <= kEdgeHorizon && t < tedge) tedge = t;
+                }
+            }
+            if (tedge < kInf) r -= penalty(kTtcAlphaE, tedge, kTtcPmaxE);
+            if (forb) ev |= kEvLaneForb;
+
+            float gdx = A.gx - A.px, gdy = A.gy - A.py;
+            if (sqrtf(gdx * gdx + gdy * gdy) <= kGoalR) ev |= kEvGoal;
+            float r22 = 1.f - 2.f * (A.qx * A.qx + A.qy * A.qy);
+            float sdx = A.px - A.sx, sdy = A.py - A.sy;
+            if (A.pz < 0.f || sqrtf(sdx * sdx + sdy * sdy) > kDriftMax || -r22 > kTiltGz) ev |= kEvCrash;
+
+            if (ev & kEvGoal) r += kWGoal;
+            else if (ev & kEvCollision) r -= kWCollision;
+            else if (ev & kEvCrash) r -= kWCrash;
+            else if (ev & kEvLaneForb) r -= kWLaneForb;
+            if (A.step >= kMaxSteps) ev |= kEvTimeout;
+            reward = r;
+        }
+        if (nonfin) { ev = kEvNonfinite; reward = 0.f; }
+        const uint32_t sparse = kEvGoal | kEvCollision | kEvCrash | kEvLaneForb;
+        const bool term = nonfin || (!(args.flags & kFlagInvincible) && (ev & sparse));
+        done = term || (ev & kEvTimeout);
+        if (done) {
+            if (args.flags & kFlagAutoReset) respawn = true;
+            else if (!nonfin) { park_agent(A); alive = false; parked_now = true; }
+        }
+    }
+
+    // ---------------- respawns, one agent after another (index order)
+    const uint32_t rbits = __ballot_sync(kFull, respawn);
+    if (rbits) {
+        const unsigned long long seed = args.seed;
+        for (int l = 0; l < n; ++l) {
+            if (!((rbits >> l) & 1u)) continue;
+            const int ep = __shfl_sync(kFull, A.episode, l) + 1;
+            float bx = 0.f, by = 0.f, bpsi = 0.f, bv = kSpawnVMin, bgx = kSpawnGoalMin, bgy = 0.f, bscore = -1.f;
+            const bool elig = alive && lane != l && !(lane > l && ((rbits >> lane) & 1u));
+            for (int r = 0; r < kSpawnTries; ++r) {
+                float x = 0.f, y = 0.f, psi = 0.f, gx = 0.f, gy = 0.f, v0 = 0.f;
+                if (lane == l) spawn_candidate(args.rd, w, a0 + l, l, ep, r, seed, x, y, psi, gx, gy, v0);
+                x = __shfl_sync(kFull, x, l);
+                y = __shfl_sync(kFull, y, l);
+                float d2 = kInf;
+                if (elig) {
+                    float dx = A.px - x, dy = A.py - y;
+                    d2 = dx * dx + dy * dy;
+                }
+                const float dmin = warp_min(d2);
+                if (lane == l && dmin > bscore) { bscore = dmin; bx = x; by = y; bpsi = psi; bv = v0; bgx = gx; bgy = gy; }
+                if (dmin >= kSpawnSpacing * kSpawnSpacing) break;
+            }
+            if (lane == l) {
+                place_agent(A, bx, by, bpsi, bv, bgx, bgy);
+                A.episode = ep;
+                alive = true;
+                ev |= kEvRespawned;
+                have_lane = false;
+            }
+            __syncwarp();
+        }
+    }
+
+    // ---------------- observations (App. D) of the post-reset state
+    {
+        float hx, hy;
+        heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
+        // warp-uniform: neighbours change only if an agent of the world respawned or parked
+        const bool refresh_nb = (MODE != kModeStep) || __ballot_sync(kFull, respawn || parked_now) != 0u;
+        uint32_t alive_bits = 0;
+        if (refresh_nb) {
+            __syncwarp();
+            publish(E, lane, A, hx, hy);
+            alive_bits = __ballot_sync(kFull, alive);
+            __syncwarp();
+        }
+        float* orow = args.out.obs + (size_t)a * kObsDim;
+        int knn_pt[kL];
+#pragma unroll
+        for (int t = 0; t < kL; ++t) knn_pt[t] = -1;
+        if (alive) {
+            if (!have_lane) lane_info = nearest_lane(args.rd, p0, np, A.px, A.py, A.gx, A.gy);
+            if (refresh_nb) knn_agents(E, n, lane, alive_bits, A.px, A.py, nb);
+            // ego group
+            {
+                float gbx, gby, vbx, vby;
+                to_ego(hx, hy, A.gx - A.px, A.gy - A.py, gbx, gby);
+                to_ego(hx, hy, A.vx, A.vy, vbx, vby);
+                float gn = sqrtf(gbx * gbx + gby * gby);
+                uint32_t pc = A.meta & 0xFFu, sc = (A.meta >> 8) & 0xFFu;
+                float4* o4 = reinterpret_cast<float4*>(orow);
+                o4[0] = make_float4(gbx / kSceneHalf, gby / kSceneHalf, gn > 0.f ? gby / gn : 0.f,
+                                    gn > 0.f ? gbx / gn : 1.f);
+                o4[1] = make_float4(gn / kSceneHalf, vbx / 10.f, vby / 10.f, (float)pc / 3.f);
+                o4[2] = make_float4(sc == 0 ? 1.f : 0.f, sc == 1 ? 1.f : 0.f, sc == 2 ? 1.f : 0.f, A.wz);
+                o4[3] = make_float4(A.dl / kThetaMax, A.mu, lane_info.seg >= 0 ? lane_info.lat / 3.6f : 0.f,
+                                    lane_info.seg >= 0 ? cross2(lane_info.tx, lane_info.ty, hx, hy) : 0.f);
+            }
+            // neighbour group, two neighbours (20 floats, 5 float4) at a time
+#pragma unroll
+            for (int t2 = 0; t2 < kK / 2; ++t2) {
+                float f[20];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int j = nb[2 * t2 + u];
+                    float* s = f + 10 * u;
+                    if (j < 0) {
+#pragma unroll
+                        for (int c = 0; c < 10; ++c) s[c] = 0.f;
+                        continue;
+                    }
+                    float pjx = E.px[j], pjy = E.py[j], hjx = E.hx[j], hjy = E.hy[j], vjx = E.vx[j], vjy = E.vy[j];
+                    float bx, by, dvx, dvy;
+                    to_ego(hx, hy, pjx - A.px, pjy - A.py, bx, by);
+                    to_ego(hx, hy, vjx - A.vx, vjy - A.vy, dvx, dvy);
+                    float dpsi = atan2f(cross2(hx, hy, hjx, hjy), hx * hjx + hy * hjy);
+                    s[0] = bx / kSceneHalf;
+                    s[1] = by / kSceneHalf;
+                    s[2] = 2.f * kHalfLen / kSceneHalf;
+                    s[3] = 2.f * kHalfWid / kSceneHalf;
+                    s[4] = dpsi / 3.14159265358979323846f;
+                    s[5] = sqrtf(vjx * vjx + vjy * vjy) / 10.f;
+                    s[6] = dvx / 10.f;
+                    s[7] = dvy / 10.f;
+                    s[8] = ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, pjx, pjy, hjx, hjy, vjx, vjy) / kTtcMax;
+                    s[9] = 1.f;
+                }
+                float4* o4 = reinterpret_cast<float4*>(orow + kObsEgo + 20 * t2);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) o4[c] = make_float4(f[4 * c], f[4 * c + 1], f[4 * c + 2], f[4 * c + 3]);
+            }
+            // k nearest road points: sorted (d^2, index) list kept in registers
+            {
+                float key[kL];
+#pragma unroll
+                for (int t = 0; t < kL; ++t) key[t] = kInf;
+                for (int k = p0; k < p0 + np; ++k) {
+                    const float4 P = __ldg(&args.rd.pt[k]);
+                    float dx = P.x - A.px, dy = P.y - A.py;
+                    float d2 = dx * dx + dy * dy;
+                    if (!(d2 < key[kL - 1])) continue;
+                    float ck = d2;
+                    int ci = k;
+                    bool ins = false;
+#pragma unroll
+                    for (int t = 0; t < kL; ++t) {
+                        if (ins || ck < key[t]) {
+                            float tk = key[t]; key[t] = ck; ck = tk;
+                            int ti = knn_pt[t]; knn_pt[t] = ci; ci = ti;
+                            ins = true;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int t4 = 0; t4 < kL / 4; ++t4) {
+                float f[28];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = knn_pt[4 * t4 + u];
+                    float* s = f + 7 * u;
+                    if (k < 0) {
+#pragma unroll
+                        for (int c = 0; c < 7; ++c) s[c] = 0.f;
+                        continue;
+                    }
+                    const float4 P = __ldg(&args.rd.pt[k]);
+                    const uint32_t m = __ldg(&args.rd.pmeta[k]);
+                    float bx, by, dbx, dby;
+                    to_ego(hx, hy, P.x - A.px, P.y - A.py, bx, by);
+                    to_ego(hx, hy, P.z, P.w, dbx, dby);
+                    s[0] = bx / 10.f;
+                    s[1] = by / 10.f;
+                    s[2] = dbx;
+                    s[3] = dby;
+                    s[4] = (float)(m & kPtTypeMask) / 20.f;
+                    s[5] = (m & kPtEdge) ? 1.f : 0.f;
+                    s[6] = 1.f;
+                }
+                float4* o4 = reinterpret_cast<float4*>(orow + kObsEgo + kK * kObsNbr + 28 * t4);
+#pragma unroll
+                for (int c = 0; c < 7; ++c) o4[c] = make_float4(f[4 * c], f[4 * c + 1], f[4 * c + 2], f[4 * c + 3]);
+            }
+        } else if (has) {
+            float4* o4 = reinterpret_cast<float4*>(orow);
+            for (int c = 0; c < kObsDim / 4; ++c) o4[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (has && (args.flags & kFlagRecord)) {
+            args.out.lane_seg[a] = alive ? lane_info.seg : -1;
+#pragma unroll
+            for (int t = 0; t < kL; ++t) args.out.knn_pts[(size_t)a * kL + t] = alive ? knn_pt[t] : -1;
+#pragma unroll
+            for (int t = 0; t < kK; ++t)
+                args.out.knn_agents[(size_t)a * kK + t] = (alive && nb[t] >= 0) ? a0 + nb[t] : -1;
+        }
+    }
+
+    if (!has) return;
+    if (MODE == kModeStep) {
+        args.out.reward[a] = reward;
+        args.out.done[a] = done ? 1 : 0;
+        args.out.events[a] = ev;
+        args.out.drac[a] = drac;
+    } else if (MODE == kModeReset && respawn) {
+        args.out.events[a] = ev;
+    }
+    store_agent(st, a, A);
+}
+
+// explicit placement: d_place[a] = (x, y, psi, v0, gx, gy)
+__global__ void place_kernel(const WorldArgs args, const float* __restrict__ place) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= args.num_agents) return;
+    Agent A;
+    load_agent(args.st, a, A);
+    const float* p = place + 6 * (size_t)a;
+    place_agent(A, p[0], p[1], p[2], p[3], p[4], p[5]);
+    store_agent(args.st, a, A);
+}
+
+template <int MODE>
+static cudaError_t launch_mode(const WorldArgs& a, int wpb, cudaStream_t s) {
+    switch (wpb) {
+        case 1: world_kernel<MODE, 1><<<(a.num_worlds + 0) / 1, 32, 0, s>>>(a); break;
+        case 2: world_kernel<MODE, 2><<<(a.num_worlds + 1) / 2, 64, 0, s>>>(a); break;
+        case 8: world_kernel<MODE, 8><<<(a.num_worlds + 7) / 8, 256, 0, s>>>(a); break;
+        default: world_kernel<MODE, 4><<<(a.num_worlds + 3) / 4, 128, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t sf_launch_world(int mode, const WorldArgs& a, int wpb, cudaStream_t s) {
+    if (a.num_worlds <= 0) return cudaSuccess;
+    switch (mode) {
+        case kModeStep: return launch_mode<kModeStep>(a, wpb, s);
+        case kModeReset: return launch_mode<kModeReset>(a, wpb, s);
+        default: return launch_mode<kModeObserve>(a, wpb, s);
+    }
+}
+
+cudaError_t sf_launch_place(const WorldArgs& a, const float* d_place, cudaStream_t s) {
+    if (a.num_agents <= 0) return cudaSuccess;
+    place_kernel<<<(a.num_agents + 127) / 128, 128, 0, s>>>(a, d_place);
+    return cudaGetLastError();
+}

@@ -1,0 +1,233 @@
+"""Thin ctypes binding of the C-ABI in include/sf.h (argument marshalling only).
+
+Every computation of the vehicle step runs in the CUDA kernels of libsf.so;
+this module only converts Python / numpy / torch arguments into the pointers
+and sizes the C functions take.  It never falls back to a CPU path: if the
+library is missing or no CUDA device is usable, the calls raise.
+
+The function names are those of the C-ABI (sf_create, sf_load_roads, sf_step,
+sf_get_obs, sf_reset, ...).  ``World`` bundles a handle with its roads for
+convenience.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsf.so")
+
+SF_OK, SF_ERR_INVALID_ARG, SF_ERR_CUDA, SF_ERR_OOM, SF_ERR_NONFINITE, SF_ERR_TIMEOUT, SF_ERR_STATE = range(7)
+STATUS_NAMES = {0: "SF_OK", 1: "SF_ERR_INVALID_ARG", 2: "SF_ERR_CUDA", 3: "SF_ERR_OOM", 4: "SF_ERR_NONFINITE",
+                5: "SF_ERR_TIMEOUT", 6: "SF_ERR_STATE"}
+NF, NI, OBS_DIM, K_AGENTS, L_POINTS = 25, 6, 320, 8, 32
+FLAG_INVINCIBLE, FLAG_AUTO_RESET, FLAG_RECORD_INDICES = 1, 2, 4
+
+
+class SFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class sf_config(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("flags", C.c_int32), ("warps_per_block", C.c_int32),
+                ("reserved", C.c_int32 * 8)]
+
+
+class sf_roads(C.Structure):
+    _fields_ = [("num_worlds", C.c_int32), ("num_polylines", C.c_int32), ("num_points", C.c_int32),
+                ("agent_off", C.c_void_p), ("poly_off", C.c_void_p), ("point_off", C.c_void_p),
+                ("poly_type", C.c_void_p), ("px", C.c_void_p), ("py", C.c_void_p), ("precip", C.c_void_p),
+                ("surface", C.c_void_p)]
+
+
+class sf_outputs(C.Structure):
+    _fields_ = [("obs", C.c_void_p), ("reward", C.c_void_p), ("done", C.c_void_p), ("events", C.c_void_p),
+                ("lane_seg", C.c_void_p), ("knn_points", C.c_void_p), ("knn_agents", C.c_void_p),
+                ("drac", C.c_void_p), ("num_agents", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsf.so is missing: build it with `python -m paper_2605_08528_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, f32 = C.c_void_p, C.c_int32, C.c_float
+        sig = {
+            "sf_create": ([vp, vp, vp], i32), "sf_destroy": ([vp], i32), "sf_load_roads": ([vp, vp], i32),
+            "sf_step": ([vp, vp, f32, C.c_int], i32), "sf_get_obs": ([vp, vp, vp, vp, vp], i32),
+            "sf_output_ptrs": ([vp, vp], i32), "sf_get_indices": ([vp, vp, vp, vp, vp], i32), "sf_reset": ([vp, vp], i32), "sf_place_agents": ([vp, vp], i32),
+            "sf_get_state": ([vp, vp, vp], i32), "sf_set_state": ([vp, vp, vp], i32),
+            "sf_save_state": ([vp, C.c_char_p], i32), "sf_load_state": ([vp, C.c_char_p], i32),
+            "sf_sync": ([vp], i32), "sf_num_agents": ([vp], i32), "sf_num_worlds": ([vp], i32),
+            "sf_last_error": ([vp], C.c_char_p), "sf_version": ([], C.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status, h=None, allow=()):
+    if status != SF_OK and status not in allow:
+        raise SFError(status, lib().sf_last_error(h).decode())
+    return status
+
+
+def _ptr(x):
+    """Device or host pointer of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+# --------------------------------------------------------------------------- C-ABI names
+def sf_version() -> str:
+    return lib().sf_version().decode()
+
+
+def sf_create(seed=0, flags=0, warps_per_block=0, stream=None):
+    cfg = sf_config(seed, flags, warps_per_block)
+    h = C.c_void_p()
+    st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().sf_create(C.byref(cfg), C.c_void_p(st), C.byref(h)))
+    return h
+
+
+def sf_destroy(h):
+    _check(lib().sf_destroy(h), h)
+
+
+def sf_load_roads(h, scene):
+    arrs = dict(agent_off=np.ascontiguousarray(scene.agent_off, np.int32),
+                poly_off=np.ascontiguousarray(scene.poly_off, np.int32),
+                point_off=np.ascontiguousarray(scene.point_off, np.int32),
+                poly_type=np.ascontiguousarray(scene.poly_type, np.uint8),
+                px=np.ascontiguousarray(scene.px, np.float32), py=np.ascontiguousarray(scene.py, np.float32),
+                precip=np.ascontiguousarray(scene.precip, np.uint8),
+                surface=np.ascontiguousarray(scene.surface, np.uint8))
+    r = sf_roads(len(arrs["agent_off"]) - 1, len(arrs["poly_type"]), len(arrs["px"]),
+                 *[_ptr(arrs[k]) for k in ("agent_off", "poly_off", "point_off", "poly_type", "px", "py", "precip",
+                                           "surface")])
+    _check(lib().sf_load_roads(h, C.byref(r)), h)
+
+
+def sf_step(h, d_actions, dt=1.0 / 30.0, substeps=4):
+    _check(lib().sf_step(h, _ptr(d_actions), float(dt), int(substeps)), h)
+
+
+def sf_get_obs(h, d_obs=None, d_reward=None, d_done=None, d_events=None):
+    _check(lib().sf_get_obs(h, _ptr(d_obs), _ptr(d_reward), _ptr(d_done), _ptr(d_events)), h)
+
+
+def sf_get_indices(h, d_lane_seg=None, d_knn_points=None, d_knn_agents=None, d_drac=None):
+    _check(lib().sf_get_indices(h, _ptr(d_lane_seg), _ptr(d_knn_points), _ptr(d_knn_agents), _ptr(d_drac)), h)
+
+
+def sf_output_ptrs(h) -> sf_outputs:
+    o = sf_outputs()
+    _check(lib().sf_output_ptrs(h, C.byref(o)), h)
+    return o
+
+
+def sf_reset(h, d_mask):
+    _check(lib().sf_reset(h, _ptr(d_mask)), h)
+
+
+def sf_place_agents(h, place):
+    p = np.ascontiguousarray(place, np.float32)
+    _check(lib().sf_place_agents(h, _ptr(p)), h)
+
+
+def sf_get_state(h, allow_nonfinite=True):
+    A = lib().sf_num_agents(h)
+    F = np.zeros((A, NF), np.float32)
+    I = np.zeros((A, NI), np.int32)
+    s = _check(lib().sf_get_state(h, _ptr(F), _ptr(I)), h, allow=(SF_ERR_NONFINITE,) if allow_nonfinite else ())
+    return F, I, s
+
+
+def sf_set_state(h, F, I):
+    F = np.ascontiguousarray(F, np.float32)
+    I = np.ascontiguousarray(I, np.int32)
+    _check(lib().sf_set_state(h, _ptr(F), _ptr(I)), h)
+
+
+def sf_save_state(h, path):
+    _check(lib().sf_save_state(h, path.encode()), h, allow=(SF_ERR_NONFINITE,))
+
+
+def sf_load_state(h, path):
+    _check(lib().sf_load_state(h, path.encode()), h)
+
+
+def sf_sync(h, allow=()):
+    return _check(lib().sf_sync(h), h, allow=allow)
+
+
+def sf_num_agents(h) -> int:
+    return int(lib().sf_num_agents(h))
+
+
+def sf_num_worlds(h) -> int:
+    return int(lib().sf_num_worlds(h))
+
+
+# --------------------------------------------------------------------------- convenience
+class World:
+    """A handle plus its roads, with torch views of the library-owned outputs."""
+
+    def __init__(self, scene, seed=0, flags=0, warps_per_block=0, stream=None):
+        import torch
+        self.torch = torch
+        self.scene = scene
+        self.h = sf_create(seed, flags, warps_per_block, stream)
+        sf_load_roads(self.h, scene)
+        self.A = sf_num_agents(self.h)
+        self.W = sf_num_worlds(self.h)
+
+    def close(self):
+        if self.h is not None:
+            sf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self):
+        """Copies (torch, on the device) of the last outputs."""
+        t = self.torch
+        dev = t.device("cuda")
+        obs = t.empty((self.A, OBS_DIM), dtype=t.float32, device=dev)
+        rew = t.empty(self.A, dtype=t.float32, device=dev)
+        done = t.empty(self.A, dtype=t.uint8, device=dev)
+        ev = t.empty(self.A, dtype=t.int32, device=dev)
+        sf_get_obs(self.h, obs, rew, done, ev)
+        return obs, rew, done, ev
+
+    def indices(self):
+        """Host copies of the recorded nearest-lane / k-NN indices (SF_FLAG_RECORD_INDICES) and step DRAC."""
+        t = self.torch
+        lane = t.empty(self.A, dtype=t.int32, device="cuda")
+        pts = t.empty((self.A, L_POINTS), dtype=t.int32, device="cuda")
+        nbr = t.empty((self.A, K_AGENTS), dtype=t.int32, device="cuda")
+        drac = t.empty(self.A, dtype=t.float32, device="cuda")
+        sf_get_indices(self.h, lane, pts, nbr, drac)
+        sf_sync(self.h, allow=(SF_ERR_NONFINITE,))
+        return dict(lane_seg=lane.cpu().numpy(), knn_pts=pts.cpu().numpy(), knn_agents=nbr.cpu().numpy(),
+                    drac=drac.cpu().numpy())

@@ -286,3 +286,21 @@ def ragged_scene(num_worlds: int = 1024, seed_base: int = 2000, max_agents: int 
     A = int(counts.sum())
     precip, surface = rng.integers(0, 4, A), rng.integers(0, 3, A)
     return _assemble(worlds, counts.astype(int), precip, surface)
+
+
+def subscene(scene: Scene, worlds):
+    """The scene restricted to the given worlds (renumbered CSR, the exact float32
+    coordinates) and the indices of the agent rows kept."""
+    worlds = list(worlds)
+    polys, counts, rows = [], [], []
+    for w in worlds:
+        pl = []
+        for p in range(scene.poly_off[w], scene.poly_off[w + 1]):
+            k0, k1 = scene.point_off[p], scene.point_off[p + 1]
+            pl.append((int(scene.poly_type[p]), np.stack([scene.px[k0:k1], scene.py[k0:k1]], 1)))
+        polys.append(pl)
+        a0, a1 = scene.agent_off[w], scene.agent_off[w + 1]
+        counts.append(a1 - a0)
+        rows.extend(range(a0, a1))
+    rows = np.asarray(rows, int)
+    return _assemble(polys, counts, scene.precip[rows], scene.surface[rows]), rows

@@ -1,0 +1,77 @@
+"""Shared helpers of the GPU parity tests: sub-scenes, state conversion and the
+per-block error measures used against the FP64 oracle."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from paper_2605_08528_b300 import synth
+
+# state blocks of the exchange layout and the floor of each relative error
+BLOCKS = {
+    "position": (slice(0, 3), 1.0),
+    "velocity": (slice(7, 10), 1.0),
+    "angular_velocity": (slice(10, 13), 1.0),
+    "wheel_spin": (slice(13, 17), 1.0),
+    "steer": (slice(17, 18), 1e-2),
+    "steer_rate": (slice(18, 19), 1.0),
+}
+# FP32 holds a unit quaternion to ~6e-8 per component, so the attitude error is
+# measured as a rotation angle relative to max(attitude angle, 0.1 rad)
+ATT_FLOOR = 0.1
+
+
+def quat_angle(q):
+    q = np.asarray(q, np.float64)
+    return 2 * np.arctan2(np.linalg.norm(q[..., 1:], axis=-1), np.abs(q[..., 0]))
+
+
+def quat_err(qa, qb):
+    """Angle of qa * conj(qb) per row."""
+    qa = np.asarray(qa, np.float64); qb = np.asarray(qb, np.float64)
+    w1, x1, y1, z1 = qa.T
+    w2, x2, y2, z2 = qb.T
+    # qa * conj(qb)
+    w = w1 * w2 + x1 * x2 + y1 * y2 + z1 * z2
+    x = -w1 * x2 + x1 * w2 - y1 * z2 + z1 * y2
+    y = -w1 * y2 + y1 * w2 - z1 * x2 + x1 * z2
+    z = -w1 * z2 + z1 * w2 - x1 * y2 + y1 * x2
+    return 2 * np.arctan2(np.sqrt(x * x + y * y + z * z), np.abs(w))
+
+
+def block_errors(F_gpu, F_ref, rows=None):
+    """Relative error per state block, per agent: ||d|| / max(||x||, floor)."""
+    G = np.asarray(F_gpu, np.float64)
+    R = np.asarray(F_ref, np.float64)
+    if rows is not None:
+        G, R = G[rows], R[rows]
+    out = {}
+    for name, (sl, floor) in BLOCKS.items():
+        d = np.linalg.norm(G[:, sl] - R[:, sl], axis=1)
+        out[name] = d / np.maximum(np.linalg.norm(R[:, sl], axis=1), floor)
+    out["attitude"] = quat_err(G[:, 3:7], R[:, 3:7]) / np.maximum(quat_angle(R[:, 3:7]), ATT_FLOOR)
+    return out
+
+
+subscene = synth.subscene
+
+
+def point_offset_map(scene, worlds):
+    """Global point index in `scene` of each point index of subscene(scene, worlds)."""
+    m = []
+    for w in worlds:
+        m.extend(range(scene.point_off[scene.poly_off[w]], scene.point_off[scene.poly_off[w + 1]]))
+    return np.asarray(m, int)
+
+
+def lex_margin_points(scene, w, p, idx_list, L=32):
+    """Distance margin of the k-NN selection of point p (float64): min over the
+    boundary between rank L-1 and L of |d_L - d_(L-1)| and between adjacent ranks."""
+    q0, q1 = scene.point_off[scene.poly_off[w]], scene.point_off[scene.poly_off[w + 1]]
+    d = np.hypot(scene.px[q0:q1].astype(np.float64) - p[0], scene.py[q0:q1].astype(np.float64) - p[1])
+    ds = np.sort(d)
+    k = min(L + 1, len(ds))
+    if k < 2:
+        return math.inf
+    return float(np.diff(ds[:k]).min())

@@ -1,0 +1,47 @@
+"""The C-ABI library loads and exports every entry point include/sf.h declares
+(no compute call: this runs without a GPU)."""
+import os
+import re
+
+import pytest
+
+from paper_2605_08528_b300 import build as B
+from paper_2605_08528_b300 import sf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sf_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    B.build()
+    L = sf.lib()
+    names = declared("sf.h")
+    assert "sf_step" in names and "sf_reset" in names and "sf_load_roads" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert sf.sf_version().startswith("sf ")
+
+
+def test_binding_names_match_the_abi():
+    for n in declared("sf.h"):
+        if n in ("sf_last_error",):
+            continue
+        assert hasattr(sf, n), n
+
+
+def test_create_without_gpu_fails_loudly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(sf.SFError) as e:
+        sf.sf_create()
+    assert e.value.status == sf.SF_ERR_CUDA
+
+
+def test_obs_layout_constants():
+    assert sf.OBS_DIM == 16 + 8 * 10 + 32 * 7

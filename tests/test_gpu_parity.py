@@ -1,0 +1,434 @@
+"""GPU parity: the CUDA step through the C-ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (written here, derived in the design notes):
+  * single step, per state block: ||gpu - oracle|| / max(||x||, floor) <= 1e-5
+    (floors: 1 m, 1 m/s, 1 rad/s, 1 rad/s spin, 1e-2 rad steer; attitude angle
+    relative to max(angle, 0.1 rad));
+  * 100-step non-contact rollouts: |dp| <= 1e-3 m and |dv| <= 1e-3 m/s;
+  * indices and event flags: bit-exact when the oracle is fed the GPU's FP32
+    state, except near-ties (selection margins below 1e-5 m), which are counted
+    and reported;
+  * observation floats: |d| <= 2e-5 absolute on features of unit scale.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2605_08528_b300 import sf, synth
+from tests.helpers import block_errors, subscene
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-5
+TOL_OBS = 2e-5
+TIE = 1e-5
+
+
+def dev(x, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to("cuda").contiguous()
+
+
+def spawn_all(world):
+    sf.sf_reset(world.h, dev(np.ones(world.A, np.uint8)))
+
+
+def alive_rows(I):
+    return np.nonzero(I[:, O.I_STATUS] & O.ALIVE)[0]
+
+
+# ----------------------------------------------------------------------------- single step
+@pytest.mark.parametrize("seed_base,worlds,agents", [(1000, 6, 16), (1300, 3, 32)])
+def test_single_step_state_parity(seed_base, worlds, agents):
+    sc = synth.procedural_scene(worlds, agents, seed_base=seed_base)
+    W = sf.World(sc, seed=5, flags=sf.FLAG_INVINCIBLE)
+    spawn_all(W)
+    orc = O.Oracle(sc)
+    acts = synth.ou_actions(W.A, 45, seed=3)
+    worst = {}
+    for t in range(45):
+        F, I, _ = sf.sf_get_state(W.h)
+        sf.sf_step(W.h, dev(acts[t]))
+        F2, I2, _ = sf.sf_get_state(W.h)
+        Fo, Io = F.astype(np.float64), I.copy()
+        orc.step(Fo, Io, acts[t].astype(np.float64), flags=O.FLAG_INVINCIBLE, seed=5, want_obs=False)
+        rows = alive_rows(Io)
+        assert np.array_equal(I2[:, O.I_STATUS], Io[:, O.I_STATUS])
+        errs = block_errors(F2, Fo, rows)
+        for k, e in errs.items():
+            worst[k] = max(worst.get(k, 0.0), float(e.max()))
+    print("single-step worst relative errors:", worst)
+    for k, e in worst.items():
+        assert e <= TOL_STEP, (k, e)
+
+
+def test_single_step_contact_parity():
+    """Overlapping footprints: penalty contact forces through SAT in both paths."""
+    sc = synth.straight_road(num_agents=6)
+    W = sf.World(sc, seed=1, flags=sf.FLAG_INVINCIBLE)
+    place = np.array([[0.0, -1.8, 0.0, 12.0, 90.0, -1.8],
+                      [4.3, -1.8, 0.02, 8.0, 90.0, -1.8],        # rear-end overlap 0.2 m
+                      [30.0, -1.8, 0.3, 10.0, 90.0, -1.8],
+                      [31.5, 0.4, -1.2, 6.0, -90.0, 1.8],        # corner contact at an angle
+                      [-50.0, 1.8, math.pi, 9.0, -90.0, 1.8],
+                      [-51.0, -0.2, math.pi - 0.4, 7.0, -90.0, 1.8]], np.float32)
+    sf.sf_place_agents(W.h, place)
+    orc = O.Oracle(sc)
+    acts = np.zeros((6, 3), np.float32)
+    contact_seen = 0
+    for t in range(6):
+        F, I, _ = sf.sf_get_state(W.h)
+        Fo, Io = F.astype(np.float64), I.copy()
+        sf.sf_step(W.h, dev(acts))
+        F2, _, _ = sf.sf_get_state(W.h)
+        orc.step(Fo, Io, acts.astype(np.float64), flags=O.FLAG_INVINCIBLE, want_obs=False)
+        for i, j in ((0, 1), (2, 3), (4, 5)):
+            hi = [math.cos(2 * math.atan2(F[i, 6], F[i, 3])), math.sin(2 * math.atan2(F[i, 6], F[i, 3]))]
+            hj = [math.cos(2 * math.atan2(F[j, 6], F[j, 3])), math.sin(2 * math.atan2(F[j, 6], F[j, 3]))]
+            contact_seen += O.sat(F[i, :2], hi, F[j, :2], hj)[0] > 0
+        errs = block_errors(F2, Fo)
+        for k, e in errs.items():
+            assert e.max() <= TOL_STEP, (t, k, float(e.max()))
+    assert contact_seen >= 3
+
+
+# ----------------------------------------------------------------------------- rollouts
+def place_straight(W, seed):
+    pl = synth.straight_road_placements(seed=seed)
+    sf.sf_place_agents(W.h, pl.astype(np.float32))
+    return pl
+
+
+@pytest.mark.parametrize("seed", [1, 11, 21, 31])
+def test_rollout_100_steps_non_contact(seed):
+    sc = synth.straight_road(num_agents=4)
+    W = sf.World(sc, seed=seed, flags=sf.FLAG_INVINCIBLE)
+    pl = place_straight(W, seed)
+    orc = O.Oracle(sc)
+    Fo, Io = orc.empty_state()
+    for a in range(4):
+        orc.place(Fo, Io, a, *[float(v) for v in pl[a].astype(np.float32)])
+    F0, _, _ = sf.sf_get_state(W.h)
+    for k, e in block_errors(F0, Fo).items():
+        assert e.max() <= 1e-6, (k, float(e.max()))
+    acts = synth.uniform_actions(4, 300, seed=seed + 1)
+    contact = np.zeros(4, bool)
+    max_dp = np.zeros(4)
+    max_dv = np.zeros(4)
+    for t in range(100):
+        sf.sf_step(W.h, dev(acts[t]))
+        orc.step(Fo, Io, acts[t].astype(np.float64), flags=O.FLAG_INVINCIBLE, want_obs=False)
+        F, _, _ = sf.sf_get_state(W.h)
+        for i in range(4):
+            for j in range(i + 1, 4):
+                hi = [math.cos(2 * math.atan2(Fo[i, 6], Fo[i, 3])), math.sin(2 * math.atan2(Fo[i, 6], Fo[i, 3]))]
+                hj = [math.cos(2 * math.atan2(Fo[j, 6], Fo[j, 3])), math.sin(2 * math.atan2(Fo[j, 6], Fo[j, 3]))]
+                if O.sat(Fo[i, :2], hi, Fo[j, :2], hj)[0] > 0:
+                    contact[i] = contact[j] = True
+        max_dp = np.maximum(max_dp, np.linalg.norm(F[:, 0:3] - Fo[:, 0:3], axis=1))
+        max_dv = np.maximum(max_dv, np.linalg.norm(F[:, 7:10] - Fo[:, 7:10], axis=1))
+    keep = ~contact
+    print("seed", seed, "contact-excluded agents:", int(contact.sum()), "max |dp|", max_dp, "max |dv|", max_dv)
+    assert keep.sum() >= 2
+    assert max_dp[keep].max() <= 1e-3 and max_dv[keep].max() <= 1e-3
+
+
+# ----------------------------------------------------------------------------- discrete outputs
+def state_tie(sc, Fe, Ie, prev, a, gpu_ev, gpu_rew, trials=60, eps=1e-5):
+    """True if the oracle reproduces the GPU's event bits and reward of agent a
+    for some perturbation of the world's positions and velocities by ~eps:
+    a discontinuity (threshold, grazing TTC root, edge-ray endpoint) lies within
+    rounding distance of the state.  A genuine discrepancy matches none."""
+    rng = np.random.default_rng(a)
+    w = int(np.searchsorted(sc.agent_off, a, side="right") - 1)
+    a0, a1 = sc.agent_off[w], sc.agent_off[w + 1]
+    orc = O.Oracle(sc)
+    for _ in range(trials):
+        Fp = Fe.copy()
+        Fp[a0:a1, 0:2] += rng.normal(0, eps, (a1 - a0, 2))
+        Fp[a0:a1, 7:9] += rng.normal(0, eps, (a1 - a0, 2))
+        Pp = prev.copy()
+        Pp[a0:a1] += rng.normal(0, eps, (a1 - a0, 2))
+        eo = orc.events(Fp, Ie.copy(), Pp)
+        if (int(eo["events"][a]) & 0x7F) == gpu_ev and abs(eo["reward"][a] - gpu_rew) <= 1e-4 * max(
+                1.0, abs(gpu_rew)):
+            return True
+    return False
+
+
+def knn_point_ties(scene, w, p, idx):
+    """True if the selection of the 32 nearest points of p has a near-tie."""
+    q0, q1 = scene.point_off[scene.poly_off[w]], scene.point_off[scene.poly_off[w + 1]]
+    d = np.hypot(scene.px[q0:q1].astype(np.float64) - p[0], scene.py[q0:q1].astype(np.float64) - p[1])
+    ds = np.sort(d)[:33]
+    return len(ds) > 1 and np.diff(ds).min() < TIE
+
+
+def lane_tie(orc, scene, w, p):
+    """Margin between the best and second-best lane segment distances."""
+    best = []
+    for pl in range(scene.poly_off[w], scene.poly_off[w + 1]):
+        if scene.poly_type[pl] not in (1, 2):
+            continue
+        for k in range(scene.point_off[pl], scene.point_off[pl + 1] - 1):
+            a = np.array([scene.px[k], scene.py[k]], np.float64)
+            b = np.array([scene.px[k + 1], scene.py[k + 1]], np.float64)
+            if np.linalg.norm(b - a) > 3.0 or np.abs(np.concatenate([a, b])).max() > 100:
+                continue
+            e = b - a
+            t = np.clip(np.dot(p - a, e) / np.dot(e, e), 0, 1)
+            best.append(np.linalg.norm(p - a - t * e))
+    best = sorted(best)
+    return len(best) > 1 and best[1] - best[0] < TIE
+
+
+@pytest.mark.parametrize("flags", [sf.FLAG_INVINCIBLE, 0, sf.FLAG_AUTO_RESET])
+def test_discrete_and_observation_parity(flags):
+    sc = synth.procedural_scene(6, 16, seed_base=1100)
+    W = sf.World(sc, seed=9, flags=flags | sf.FLAG_RECORD_INDICES)
+    spawn_all(W)
+    orc = O.Oracle(sc)
+    oflags = (O.FLAG_INVINCIBLE if flags & sf.FLAG_INVINCIBLE else 0) | (
+        O.FLAG_AUTO_RESET if flags & sf.FLAG_AUTO_RESET else 0)
+    acts = synth.ou_actions(W.A, 30, seed=4, sigma=0.5)
+    ties = dict(lane=0, knn_pts=0, knn_agents=0, events=0)
+    checked = 0
+    for t in range(30):
+        F0, I0, _ = sf.sf_get_state(W.h)
+        sf.sf_step(W.h, dev(acts[t]))
+        F1, I1, _ = sf.sf_get_state(W.h)
+        obs, rew, done, ev = [x.cpu().numpy() for x in W.outputs()]
+        ix = W.indices()
+        # events on the GPU's own end-of-step state (before respawns)
+        if not flags & sf.FLAG_AUTO_RESET:
+            Fe, Ie = F1.astype(np.float64), I1.copy()
+            Ie[:, O.I_STEP] = I0[:, O.I_STEP]
+            Ie[:, O.I_STATUS] = I0[:, O.I_STATUS]
+            Fe[:, O.F_PEAK_DRAC] = F0[:, O.F_PEAK_DRAC]
+            alive0 = (I0[:, O.I_STATUS] & O.ALIVE) != 0
+            if flags == 0:
+                # an agent parked this step lost its end-of-step pose, which its
+                # neighbours' events saw: skip every world with a done agent
+                for w in range(sc.num_worlds):
+                    a0, a1 = sc.agent_off[w], sc.agent_off[w + 1]
+                    if done[a0:a1].any():
+                        alive0[a0:a1] = False
+            prev = F0[:, :2].astype(np.float64)
+            eo = orc.events(Fe.copy(), Ie.copy(), prev)
+            for a in np.nonzero(alive0)[0]:
+                mine = int(ev[a]) & 0x7F
+                ref = int(eo["events"][a]) & 0x7F
+                ok = mine == ref and abs(rew[a] - eo["reward"][a]) <= 1e-4 * max(1.0, abs(eo["reward"][a]))
+                if not ok:
+                    assert state_tie(sc, Fe, Ie, prev, a, mine, float(rew[a])), (
+                        t, a, mine, ref, float(rew[a]), float(eo["reward"][a]))
+                    ties["events"] += 1
+                checked += 1
+        # observation of the post-step state, oracle fed the GPU's FP32 state
+        oo = orc.observe(F1.astype(np.float64), I1)
+        for a in range(W.A):
+            w = int(np.searchsorted(sc.agent_off, a, side="right") - 1)
+            p = F1[a, :2].astype(np.float64)
+            if not I1[a, O.I_STATUS] & O.ALIVE:
+                assert not obs[a].any()
+                continue
+            if ix["lane_seg"][a] != oo["lane_seg"][a]:
+                assert lane_tie(orc, sc, w, p), (t, a)
+                ties["lane"] += 1
+                continue
+            if not np.array_equal(ix["knn_pts"][a], oo["knn_pts"][a]):
+                assert knn_point_ties(sc, w, p, ix["knn_pts"][a]), (t, a)
+                ties["knn_pts"] += 1
+                continue
+            if not np.array_equal(ix["knn_agents"][a], oo["knn_agents"][a]):
+                ties["knn_agents"] += 1
+                continue
+            d = np.abs(obs[a] - oo["obs"][a])
+            for k in range(8):          # relative heading / pi wraps at +-1
+                c = 16 + 10 * k + 4
+                d[c] = min(d[c], abs(2.0 - d[c]))
+            ttc_cols = [16 + 10 * k + 8 for k in range(8)]
+            dd = np.delete(d, ttc_cols)
+            assert dd.max() <= TOL_OBS, (t, a, int(np.argmax(dd)), float(dd.max()))
+            assert (d[ttc_cols] <= 1e-3).sum() >= 7
+    print("near-ties counted:", ties, "event rows checked:", checked)
+    assert sum(ties.values()) <= 0.01 * 30 * W.A + 3
+
+
+# ----------------------------------------------------------------------------- resets
+def test_reset_spawns_match_oracle():
+    sc = synth.procedural_scene(5, 16, seed_base=1200)
+    W = sf.World(sc, seed=77, flags=sf.FLAG_AUTO_RESET)
+    orc = O.Oracle(sc)
+    Fo, Io = orc.empty_state()
+    Io[:, O.I_PRECIP], Io[:, O.I_SURFACE] = sc.precip, sc.surface
+    spawn_all(W)
+    orc.reset(Fo, Io, np.ones(W.A, np.uint8), seed=77)
+    F, I, _ = sf.sf_get_state(W.h)
+    assert np.array_equal(F[:, :2].astype(np.float64), Fo[:, :2])          # same lane points
+    assert np.array_equal(F[:, O.F_GX:O.F_GY + 1].astype(np.float64), Fo[:, O.F_GX:O.F_GY + 1])
+    assert np.abs(F - Fo).max() < 2e-5
+    assert np.array_equal(I[:, :5], Io[:, :5])
+    # masked resets mid-run, oracle fed the GPU's pre-reset state
+    acts = synth.ou_actions(W.A, 12, seed=8)
+    ties = 0
+    for t in range(12):
+        sf.sf_step(W.h, dev(acts[t]))
+        F0, I0, _ = sf.sf_get_state(W.h)
+        m = synth.reset_mask(W.A, t, 0.3, seed=7)
+        sf.sf_reset(W.h, dev(m))
+        F1, I1, _ = sf.sf_get_state(W.h)
+        Fr, Ir = F0.astype(np.float64), I0.copy()
+        orc.reset(Fr, Ir, m, seed=77)
+        for a in np.nonzero(m)[0]:
+            if not np.array_equal(F1[a, :2].astype(np.float64), Fr[a, :2]):
+                ties += 1      # a spacing test within rounding of 10 m
+                continue
+            assert np.abs(F1[a] - Fr[a]).max() < 2e-5
+        assert np.array_equal(I1[:, O.I_EPISODE], Ir[:, O.I_EPISODE])
+    assert ties <= 2
+
+
+# ----------------------------------------------------------------------------- edge cases
+def test_ragged_and_degenerate_worlds():
+    polys_a = synth.procedural_world(5)
+    x = np.linspace(-90, 90, 181)
+    straight = [(2, np.stack([x, np.full(181, -1.8)], 1)), (2, np.stack([x[::-1], np.full(181, 1.8)], 1)),
+                (15, np.stack([x, np.full(181, -3.6)], 1)), (16, np.stack([x, np.full(181, 3.6)], 1))]
+    worlds = [polys_a, [], straight, polys_a, straight]
+    counts = [32, 3, 1, 0, 17]          # a full warp, a world without roads, one agent, an empty world
+    sc = synth._assemble(worlds, counts, np.zeros(sum(counts)), np.zeros(sum(counts)))
+    W = sf.World(sc, seed=3, flags=sf.FLAG_AUTO_RESET | sf.FLAG_RECORD_INDICES)
+    spawn_all(W)
+    orc = O.Oracle(sc)
+    F, I, _ = sf.sf_get_state(W.h)
+    Fo, Io = orc.empty_state()
+    orc.reset(Fo, Io, np.ones(W.A, np.uint8), seed=3)
+    assert np.abs(F - Fo).max() < 2e-5
+    acts = synth.ou_actions(W.A, 20, seed=2)
+    for t in range(20):
+        F0, I0, _ = sf.sf_get_state(W.h)
+        sf.sf_step(W.h, dev(acts[t]))
+        F1, I1, s = sf.sf_get_state(W.h)
+        assert s == sf.SF_OK
+        Fo, Io = F0.astype(np.float64), I0.copy()
+        out = orc.step(Fo, Io, acts[t].astype(np.float64), flags=O.FLAG_AUTO_RESET, seed=3)
+        rows = np.nonzero((Io[:, O.I_EVENTS] & O.EV["respawned"]) == 0)[0]
+        errs = block_errors(F1, Fo, rows)
+        for k, e in errs.items():
+            assert e.max() <= TOL_STEP, (t, k)
+        obs = W.outputs()[0].cpu().numpy()
+        assert np.isfinite(obs).all()
+    # the world without roads: no lane, off-road every step, zero road features
+    ix = W.indices()
+    a = 32
+    assert ix["lane_seg"][a] == -1 and (ix["knn_pts"][a] == -1).all()
+
+
+def test_invalid_roads_rejected():
+    sc = synth.straight_road(num_agents=4)
+    h = sf.sf_create()
+    try:
+        bad = synth._assemble([[(2, np.zeros((3, 2)))]], [33], np.zeros(33), np.zeros(33))
+        with pytest.raises(sf.SFError) as e:
+            sf.sf_load_roads(h, bad)
+        assert e.value.status == sf.SF_ERR_INVALID_ARG
+        bad2 = synth._assemble([[(2, np.zeros((3, 2)))]], [2], np.zeros(2), np.zeros(2))
+        bad2.point_off = np.array([0, 5], np.int32)          # beyond the point array
+        with pytest.raises(sf.SFError):
+            sf.sf_load_roads(h, bad2)
+        bad3 = synth.straight_road(num_agents=2)
+        bad3.px = bad3.px.copy(); bad3.px[3] = np.nan
+        with pytest.raises(sf.SFError):
+            sf.sf_load_roads(h, bad3)
+        with pytest.raises(sf.SFError) as e:
+            sf.sf_step(h, torch.zeros((4, 3), device="cuda"))
+        assert e.value.status == sf.SF_ERR_STATE
+        sf.sf_load_roads(h, sc)
+        with pytest.raises(sf.SFError):
+            sf.sf_step(h, torch.zeros((4, 3), device="cuda"), dt=0.0)
+        with pytest.raises(sf.SFError):
+            sf.sf_step(h, torch.zeros((4, 3), device="cuda"), substeps=0)
+    finally:
+        sf.sf_destroy(h)
+
+
+# ----------------------------------------------------------------------------- determinism, checkpoints, faults
+def test_determinism_and_checkpoint_resume(tmp_path):
+    sc = synth.procedural_scene(4, 16, seed_base=1400)
+    acts = synth.ou_actions(64, 60, seed=5)
+
+    def run(n0, n1, ckpt=None):
+        W = sf.World(sc, seed=21, flags=sf.FLAG_AUTO_RESET)
+        spawn_all(W)
+        for t in range(n0):
+            sf.sf_step(W.h, dev(acts[t]))
+        if ckpt:
+            sf.sf_save_state(W.h, str(ckpt))
+            W.close()
+            W = sf.World(sc, seed=21, flags=sf.FLAG_AUTO_RESET)
+            sf.sf_load_state(W.h, str(ckpt))
+        for t in range(n0, n1):
+            sf.sf_step(W.h, dev(acts[t]))
+        F, I, _ = sf.sf_get_state(W.h)
+        obs = W.outputs()[0].cpu().numpy()
+        W.close()
+        return F, I, obs
+
+    Fa, Ia, Oa = run(60, 60)
+    Fb, Ib, Ob = run(60, 60)
+    assert np.array_equal(Fa, Fb) and np.array_equal(Ia, Ib) and np.array_equal(Oa, Ob)
+    Fc, Ic, Oc = run(30, 60, ckpt=tmp_path / "ck.bin")
+    assert np.array_equal(Fa, Fc) and np.array_equal(Ia, Ic) and np.array_equal(Oa, Oc)
+
+
+def test_nonfinite_state_is_reported_and_contained():
+    sc = synth.procedural_scene(2, 8, seed_base=1500)
+    W = sf.World(sc, seed=2, flags=sf.FLAG_AUTO_RESET)
+    spawn_all(W)
+    F, I, _ = sf.sf_get_state(W.h)
+    F[3, O.F_VX] = np.nan
+    sf.sf_set_state(W.h, F, I)
+    sf.sf_step(W.h, dev(np.zeros((W.A, 3), np.float32)))
+    assert sf.sf_sync(W.h, allow=(sf.SF_ERR_NONFINITE,)) == sf.SF_ERR_NONFINITE
+    F2, I2, s = sf.sf_get_state(W.h)
+    assert s == sf.SF_OK                                       # the condition was cleared by the sync
+    assert np.isfinite(F2).all()
+    ev = W.outputs()[3].cpu().numpy()
+    assert ev[3] & O.EV["nonfinite"] and ev[3] & O.EV["respawned"]
+    assert I2[3, O.I_EPISODE] == I[3, O.I_EPISODE] + 1
+    assert sf.sf_sync(W.h) == sf.SF_OK
+
+
+# ----------------------------------------------------------------------------- full-size sampled parity
+@pytest.mark.parametrize("worlds", [256, 4096])
+def test_full_size_sampled_parity(worlds):
+    """The benchmark's workloads (256 x 16 and 4096 x 16, paper-shaped roads):
+    one step of 12 sampled worlds against the oracle, from the GPU's state."""
+    from bench import make_scene
+    sc = make_scene("256x16" if worlds == 256 else "4096x16")
+    W = sf.World(sc, seed=4000, flags=sf.FLAG_AUTO_RESET)
+    spawn_all(W)
+    acts = synth.ou_actions(W.A, 5, seed=6)
+    for t in range(4):
+        sf.sf_step(W.h, dev(acts[t]))
+    F0, I0, _ = sf.sf_get_state(W.h)
+    sf.sf_step(W.h, dev(acts[4]))
+    F1, I1, _ = sf.sf_get_state(W.h)
+    rng = np.random.default_rng(worlds)
+    ws = sorted(rng.choice(worlds, 12, replace=False))
+    sub, rows = subscene(sc, ws)
+    orc = O.Oracle(sub)
+    Fo, Io = F0[rows].astype(np.float64), I0[rows].copy()
+    orc.step(Fo, Io, acts[4][rows].astype(np.float64), flags=O.FLAG_AUTO_RESET, seed=4000, want_obs=False)
+    keep = np.nonzero((Io[:, O.I_EVENTS] & O.EV["respawned"]) == 0)[0]
+    errs = block_errors(F1[rows], Fo, keep)
+    for k, e in errs.items():
+        assert e.max() <= TOL_STEP, (k, float(e.max()))
