@@ -116,9 +116,9 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- our arm
-def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True):
+def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0):
     scene = make_scene(name, rank)
-    W = sf.World(scene, seed=4242 + rank, flags=sf.FLAG_AUTO_RESET, stream=stream)
+    W = sf.World(scene, seed=4242 + rank, flags=sf.FLAG_AUTO_RESET, warps_per_block=nw, stream=stream)
     A = W.A
     dev = torch.device("cuda")
     with torch.cuda.stream(stream):
@@ -127,6 +127,9 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True):
         acts_h = synth.ou_actions(A, ring, seed=11 + rank)
         acts = torch.as_tensor(acts_h, device=dev)
         flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        tuned = None
+        if nw == 0:                                       # setup: pick the launch shape (state restored)
+            tuned = sf.sf_autotune(W.h, acts[0], iters=10)
         for t in range(warmup):
             sf.sf_step(W.h, acts[t % ring])
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -148,7 +151,7 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True):
     if not e2e:
         W.close()
         return dict(scene=scene, A=A, alive=alive, ms=ms, wall=wall, status=st, e2e_wall=float("nan"),
-                    e2e_steps=1, h2d=A * 12, d2h=A * 5)
+                    e2e_steps=1, h2d=A * 12, d2h=A * 5, tuned=tuned)
     # end to end through the C-ABI: pinned host actions in, host rewards/done out, every step
     acts_pin = torch.as_tensor(acts_h).pin_memory()
     act_dev = torch.empty((A, 3), dtype=torch.float32, device=dev)
@@ -171,7 +174,7 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True):
         e2e_wall = time.perf_counter() - t0
     W.close()
     return dict(scene=scene, A=A, alive=alive, ms=ms, wall=wall, status=st, e2e_wall=e2e_wall,
-                e2e_steps=e2e_steps, h2d=A * 12, d2h=A * 5)
+                e2e_steps=e2e_steps, h2d=A * 12, d2h=A * 5, tuned=tuned)
 
 
 def cpu_baseline(name, seconds=12.0):
@@ -218,7 +221,8 @@ def main_ours(args):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        res[name] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream, e2e=not args.skip_e2e)
+        res[name] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream, e2e=not args.skip_e2e,
+                                 nw=args.nw)
     clk = clocks.stop()
     if args.only:          # profiling run: one workload, no report line
         if rank == 0:
@@ -242,7 +246,7 @@ def main_ours(args):
         ach = ab["total"] / mean_s / 1e9
         return dict(casps=casps, e2e=e2e_casps, ms=float(r["ms"].mean()), p50=float(np.percentile(r["ms"], 50)),
                     p99=float(np.percentile(r["ms"], 99)), bytes=ab, achieved=ach, A=r["A"], alive=r["alive"],
-                    h2d=r["h2d"], d2h=r["d2h"])
+                    h2d=r["h2d"], d2h=r["d2h"], tuned=r["tuned"])
 
     a256, a4096 = agg("256x16"), agg("4096x16")
     if rank == 0:
@@ -256,7 +260,8 @@ def main_ours(args):
                                    "intersections, 400-1200 points/world), per-agent weather table mu, auto-reset",
                        "worlds": 256 * world, "agents": a256["A"] * world, "dt": 1 / 30, "substeps": 4,
                        "K_agents": 8, "L_points": 32, "l2": "flushed (256 MB write) before every timed step",
-                       "parallelism": "worlds sharded, no data-path collective" if world > 1 else "1 GPU"},
+                       "parallelism": "worlds sharded, no data-path collective" if world > 1 else "1 GPU",
+                       "autotune": a256["tuned"]},
             "p50_ms": a256["p50"], "p99_ms": a256["p99"],
             "e2e": {"value": a256["e2e"], "unit": "CASPS", "h2d_bytes_per_step": a256["h2d"],
                     "d2h_bytes_per_step": a256["d2h"]},
@@ -267,7 +272,7 @@ def main_ours(args):
                          "traffic": traffic.get("256x16")},
             "scale_4096x16": {"value": a4096["casps"], "unit": "CASPS", "ms_per_step": a4096["ms"],
                               "p50_ms": a4096["p50"], "p99_ms": a4096["p99"],
-                              "agents": a4096["A"] * world,
+                              "agents": a4096["A"] * world, "autotune": a4096["tuned"],
                               "e2e": {"value": a4096["e2e"], "unit": "CASPS", "h2d_bytes_per_step": a4096["h2d"],
                                       "d2h_bytes_per_step": a4096["d2h"]},
                               "roofline": {"bound": "hbm", "achieved": a4096["achieved"], "peak": peak,
@@ -338,6 +343,7 @@ def main():
     ap.add_argument("--only", default=None, choices=list(WORKLOADS), help="profiling: run one workload only")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling: no end-to-end leg")
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
+    ap.add_argument("--nw", type=int, default=0, help="warps per world (1, 2, 4, 8; 0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -169,6 +169,17 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* h_roads);
  * substeps outside 1..64), SF_ERR_CUDA (launch failure). */
 sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps);
 
+/* Autotuner: time each launch shape of the world kernel (1, 2, 4 or 8 warps
+ * cooperating on one world) over `iters` steps with the given actions and keep
+ * the fastest for this handle.  The agent state and every output are saved
+ * before and restored after the trials, so the call does not advance the
+ * simulation.  Synchronous; uses a temporary device buffer the size of the
+ * state and outputs.  *out_warps (may be NULL) receives the choice and
+ * out_ms (may be NULL, [4]) the mean step time of each shape in ms.
+ * Errors: SF_ERR_STATE (no roads), SF_ERR_INVALID_ARG (iters < 1), SF_ERR_OOM. */
+sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substeps, int iters, int32_t* out_warps,
+                      float* out_ms);
+
 /* Copy the observations, rewards, done flags and event bits of the last step
  * or reset into caller device buffers ([A][SF_OBS_DIM], [A], [A], [A]); any
  * pointer may be NULL.  Asynchronous device-to-device copies. */

@@ -6,6 +6,8 @@
 // kernels of sf_world.cu.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
+#include <utility>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -184,6 +186,10 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     std::vector<int4> world(W);
     std::vector<int2> cand(W);
     std::vector<int32_t> cands;
+    std::vector<DevGrid> grid(W);
+    std::vector<int32_t> cell_off, eall, sidx(NP);
+    std::vector<float4> spt(NP);
+    std::vector<uint32_t> smeta(NP);
     auto in_box = [](double x, double y) { return std::fabs(x) <= 100.0 && std::fabs(y) <= 100.0; };
     for (int w = 0; w < W; ++w) {
         const int p0 = r->poly_off[w], p1 = r->poly_off[w + 1];
@@ -231,6 +237,40 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
         const std::vector<int32_t>& use = strict.empty() ? all_lane : strict;
         cand[w] = make_int2((int)cands.size(), (int)use.size());
         cands.insert(cands.end(), use.begin(), use.end());
+
+        // ---- uniform grid of the world: points sorted by cell, row-major
+        double xmin = 0, xmax = 0, ymin = 0, ymax = 0;
+        for (int k = q0; k < q1; ++k) {
+            if (k == q0 || r->px[k] < xmin) xmin = r->px[k];
+            if (k == q0 || r->px[k] > xmax) xmax = r->px[k];
+            if (k == q0 || r->py[k] < ymin) ymin = r->py[k];
+            if (k == q0 || r->py[k] > ymax) ymax = r->py[k];
+        }
+        double c = std::max(sfk::kCellMin, std::max(xmax - xmin, ymax - ymin) / (sfk::kGridMax - 1));
+        int nx = std::min(sfk::kGridMax, (int)std::floor((xmax - xmin) / c) + 1);
+        int ny = std::min(sfk::kGridMax, (int)std::floor((ymax - ymin) / c) + 1);
+        const int ncell = nx * ny;
+        auto cx_of = [&](double x) { return std::min(nx - 1, std::max(0, (int)std::floor((x - xmin) / c))); };
+        auto cy_of = [&](double y) { return std::min(ny - 1, std::max(0, (int)std::floor((y - ymin) / c))); };
+        DevGrid g{};
+        g.x0 = (float)xmin; g.y0 = (float)ymin; g.c = (float)c; g.inv_c = (float)(1.0 / c);
+        g.nx = nx; g.ny = ny; g.cbase = (int)cell_off.size();
+        g.eoff = (int)eall.size();
+        std::vector<int> cnt(ncell + 1, 0);
+        for (int k = q0; k < q1; ++k) {
+            cnt[cy_of(r->py[k]) * nx + cx_of(r->px[k]) + 1]++;
+            if ((pmeta[k] & (sfk::kPtSegNext | sfk::kPtEdge)) == (sfk::kPtSegNext | sfk::kPtEdge)) eall.push_back(k);
+        }
+        for (int i = 0; i < ncell; ++i) cnt[i + 1] += cnt[i];
+        for (int i = 0; i <= ncell; ++i) cell_off.push_back(q0 + cnt[i]);
+        for (int k = q0; k < q1; ++k) {   // stable: input order within a cell
+            int slot = q0 + cnt[cy_of(r->py[k]) * nx + cx_of(r->px[k])]++;
+            spt[slot] = pt[k];
+            smeta[slot] = pmeta[k];
+            sidx[slot] = k;
+        }
+        g.ecnt = (int)eall.size() - g.eoff;
+        grid[w] = g;
     }
 
     // ---- allocate and upload
@@ -260,9 +300,16 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     SF_ALLOC(dpmeta, uint32_t, (size_t)NP + 1);
     SF_ALLOC(dpend, int32_t, (size_t)NP + 1);
     SF_ALLOC(dcands, int32_t, cands.size() + 1);
-    h->rd = DevRoads{dworld, dcand, dpt, dpmeta, dpend, dcands};
+    DevGrid* dgrid; int32_t *dcoff, *dsidx, *deall; float4* dspt; uint32_t* dsmeta;
+    SF_ALLOC(dgrid, DevGrid, (size_t)W);
+    SF_ALLOC(dcoff, int32_t, cell_off.size());
+    SF_ALLOC(dspt, float4, (size_t)NP + 1);
+    SF_ALLOC(dsmeta, uint32_t, (size_t)NP + 1);
+    SF_ALLOC(dsidx, int32_t, (size_t)NP + 1);
+    SF_ALLOC(deall, int32_t, eall.size() + 1);
+    h->rd = DevRoads{dworld, dcand, dpt, dpmeta, dpend, dcands, dgrid, dcoff, dspt, dsmeta, dsidx, deall};
     float *obs, *reward, *drac; uint8_t* done; uint32_t* events; int32_t *lane_seg, *knn_pts, *knn_agents;
-    unsigned int* err_word;
+    unsigned int* err_word; float* hint;
     SF_ALLOC(obs, float, Aa * SF_OBS_DIM);
     SF_ALLOC(reward, float, Aa);
     SF_ALLOC(done, uint8_t, Aa);
@@ -272,7 +319,8 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     SF_ALLOC(knn_agents, int32_t, Aa * SF_K_AGENTS);
     SF_ALLOC(drac, float, Aa);
     SF_ALLOC(err_word, unsigned int, 1);
-    h->out = DevOutputs{obs, reward, done, events, lane_seg, knn_pts, knn_agents, drac, err_word};
+    SF_ALLOC(hint, float, Aa * 2);
+    h->out = DevOutputs{obs, reward, done, events, lane_seg, knn_pts, knn_agents, drac, err_word, hint};
     SF_ALLOC(h->place_buf, float, Aa * 6);
     SF_ALLOC(h->all_mask, uint8_t, Aa);
 #undef SF_ALLOC
@@ -292,11 +340,17 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     up(dpmeta, pmeta.data(), pmeta.size() * sizeof(uint32_t));
     up(dpend, pend.data(), pend.size() * sizeof(int32_t));
     up(dcands, cands.data(), cands.size() * sizeof(int32_t));
+    up(dgrid, grid.data(), grid.size() * sizeof(DevGrid));
+    up(dcoff, cell_off.data(), cell_off.size() * 4);
+    up(dspt, spt.data(), spt.size() * sizeof(float4));
+    up(dsmeta, smeta.data(), smeta.size() * 4);
+    up(dsidx, sidx.data(), sidx.size() * 4);
+    up(deall, eall.data(), eall.size() * 4);
     for (float4* p : {pos, quat, vel, angv, spin, goal}) zero(p, Aa * sizeof(float4));
     zero(peak, Aa * 4); zero(step, Aa * 4); zero(episode, Aa * 4);
     up(meta, meta_h.data(), Aa * 4);
     zero(obs, Aa * SF_OBS_DIM * 4); zero(reward, Aa * 4); zero(done, Aa); zero(events, Aa * 4);
-    zero(drac, Aa * 4); zero(err_word, 4);
+    zero(drac, Aa * 4); zero(err_word, 4); zero(hint, Aa * 8);
     if (e == cudaSuccess && Aa) e = cudaMemset(lane_seg, 0xFF, Aa * 4);
     if (e == cudaSuccess && Aa) e = cudaMemset(knn_pts, 0xFF, Aa * SF_L_POINTS * 4);
     if (e == cudaSuccess && Aa) e = cudaMemset(knn_agents, 0xFF, Aa * SF_K_AGENTS * 4);
@@ -319,6 +373,73 @@ sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps) {
     a.substeps = substeps;
     cudaError_t e = sf_launch_world(kModeStep, a, wpb_of(h), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "sf_step launch");
+    return SF_OK;
+}
+
+sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substeps, int iters, int32_t* out_warps,
+                      float* out_ms) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_autotune: no roads loaded");
+    if (iters < 1) return fail(h, SF_ERR_INVALID_ARG, "sf_autotune: iters must be >= 1");
+    const size_t A = (size_t)h->A;
+    // every buffer a step writes: state, outputs, query hints, error word
+    const std::pair<void*, size_t> bufs[] = {
+        {h->st.pos, A * 16}, {h->st.quat, A * 16}, {h->st.vel, A * 16}, {h->st.angv, A * 16},
+        {h->st.spin, A * 16}, {h->st.goal, A * 16}, {h->st.peak_drac, A * 4}, {h->st.meta, A * 4},
+        {h->st.step, A * 4}, {h->st.episode, A * 4}, {h->out.obs, A * SF_OBS_DIM * 4}, {h->out.reward, A * 4},
+        {h->out.done, A}, {h->out.events, A * 4}, {h->out.lane_seg, A * 4}, {h->out.knn_pts, A * SF_L_POINTS * 4},
+        {h->out.knn_agents, A * SF_K_AGENTS * 4}, {h->out.drac, A * 4}, {h->out.hint, A * 8},
+        {h->out.error_word, 4}};
+    size_t total = 0;
+    for (const auto& b : bufs) total += (b.second + 255) & ~(size_t)255;
+    char* snap = nullptr;
+    cudaError_t e = cudaMalloc(&snap, total + 256);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sf_autotune snapshot");
+    auto copy_all = [&](bool save) {
+        size_t off = 0;
+        cudaError_t r = cudaSuccess;
+        for (const auto& b : bufs) {
+            if (r == cudaSuccess && b.second)
+                r = cudaMemcpyAsync(save ? snap + off : b.first, save ? b.first : snap + off, b.second,
+                                    cudaMemcpyDeviceToDevice, h->stream);
+            off += (b.second + 255) & ~(size_t)255;
+        }
+        return r;
+    };
+    const int shapes[4] = {1, 2, 4, 8};
+    float ms[4] = {0, 0, 0, 0};
+    int best = wpb_of(h);
+    float best_ms = 0.f;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    e = copy_all(true);
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    const int saved = h->cfg.warps_per_block;
+    for (int si = 0; si < 4 && e == cudaSuccess; ++si) {
+        h->cfg.warps_per_block = shapes[si];
+        e = copy_all(false);
+        WorldArgs a = make_args(h);
+        a.actions = d_actions;
+        a.h = dt / (float)substeps;
+        a.substeps = substeps;
+        if (e == cudaSuccess) e = sf_launch_world(kModeStep, a, shapes[si], h->stream);   // warm
+        if (e == cudaSuccess) e = cudaEventRecord(t0, h->stream);
+        for (int it = 0; it < iters && e == cudaSuccess; ++it) e = sf_launch_world(kModeStep, a, shapes[si], h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[si], t0, t1);
+        ms[si] /= (float)iters;
+        if (e == cudaSuccess && (si == 0 || ms[si] < best_ms)) { best_ms = ms[si]; best = shapes[si]; }
+    }
+    if (e == cudaSuccess) e = copy_all(false);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    cudaFree(snap);
+    if (e != cudaSuccess) { h->cfg.warps_per_block = saved; return cuda_fail(h, e, "sf_autotune"); }
+    h->cfg.warps_per_block = best;
+    if (out_warps) *out_warps = best;
+    if (out_ms) for (int i = 0; i < 4; ++i) out_ms[i] = ms[i];
     return SF_OK;
 }
 

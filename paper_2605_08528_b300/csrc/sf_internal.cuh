@@ -66,6 +66,12 @@ constexpr float kSpawnVMin = 5.0f, kSpawnVMax = 20.0f;
 constexpr float kSpawnSpacing = 10.0f, kParkX = 1000.0f;
 constexpr int kSpawnTries = 8;
 
+// ---------------------------------------------------------------- road grid
+constexpr double kCellMin = 4.0;   // grid cell edge [m]; larger when a world spans > 128 cells
+constexpr int kGridMax = 128;
+constexpr float kSegReach = 3.0f;  // no segment is longer (App. C gap rule)
+constexpr float kKnnR0 = 10.0f, kLaneR0 = 6.0f, kHintSlack = 2.0f, kGrow = 1.6f;
+
 // ---------------------------------------------------------------- layout
 constexpr int kMaxAgents = 32;
 constexpr int kK = 8, kL = 32;
@@ -100,14 +106,31 @@ struct DevState {
     int32_t* episode;
 };
 
+// Uniform grid over one world's points (built on the host at load time).
+// The world's points are stored a second time sorted by cell, row-major
+// (cell (cx, cy) = floor((x - x0) / c), clamped), so the cells of one grid row
+// form one contiguous range [cell_off[cbase + cy*nx + cx0], cell_off[cbase +
+// cy*nx + cx1 + 1]).  Segments are found through their start points.
+struct DevGrid {
+    float x0, y0, c, inv_c;
+    int nx, ny, cbase, eoff;
+    int ecnt, pad0, pad1, pad2;
+};
+
 // Road store of all worlds.
 struct DevRoads {
     const int4* world;      // (first agent, agent count, first point, point count)
     const int2* cand;       // (first spawn candidate, candidate count)
-    const float4* pt;       // (x, y, road direction x, y)
-    const uint32_t* pmeta;  // type | kPt* bits
+    const float4* pt;       // (x, y, road direction x, y), input order
+    const uint32_t* pmeta;  // type | kPt* bits, input order
     const int32_t* pend;    // one past the last point of the point's polyline
     const int32_t* cands;   // spawn candidate point indices
+    const DevGrid* grid;    // per world
+    const int32_t* cell_off;// per world nx*ny+1 offsets into the sorted arrays
+    const float4* spt;      // points sorted by cell
+    const uint32_t* smeta;  // their meta
+    const int32_t* sidx;    // their input-order index
+    const int32_t* eall;    // every edge segment of a world, at grid.eoff
 };
 
 struct DevOutputs {
@@ -120,6 +143,7 @@ struct DevOutputs {
     int32_t* knn_agents;
     float* drac;
     unsigned int* error_word;  // bit0 non-finite seen
+    float* hint;               // [A][2] last query radii (32-NN, nearest lane); 0 = unknown
 };
 
 enum WorldMode { kModeStep = 0, kModeReset = 1, kModeObserve = 2 };

@@ -294,32 +294,6 @@ struct Lane {
     float dist, lat, tx, ty;  // tangent oriented toward the goal, lat sign follows it
 };
 
-__device__ __forceinline__ Lane nearest_lane(const DevRoads& rd, int p0, int np, float qx, float qy, float gx,
-                                             float gy) {
-    int best = -1;
-    float bd2 = kInf;
-    for (int k = p0; k < p0 + np; ++k) {
-        const uint32_t m = __ldg(&rd.pmeta[k]);
-        if ((m & (kPtSegNext | kPtLane)) != (kPtSegNext | kPtLane)) continue;
-        const float4 a = __ldg(&rd.pt[k]);
-        const float4 b = __ldg(&rd.pt[k + 1]);
-        float d2 = seg_dist2(a.x, a.y, b.x, b.y, qx, qy);
-        if (d2 < bd2) { bd2 = d2; best = k; }
-    }
-    Lane L;
-    L.seg = best;
-    if (best < 0) { L.dist = kInf; L.lat = 0.f; L.tx = L.ty = 0.f; return L; }
-    const float4 a = __ldg(&rd.pt[best]);
-    const float4 b = __ldg(&rd.pt[best + 1]);
-    float ex = b.x - a.x, ey = b.y - a.y;
-    float n = sqrtf(ex * ex + ey * ey);
-    float tx = ex / n, ty = ey / n;
-    float lat = cross2(tx, ty, qx - a.x, qy - a.y);
-    if (tx * (gx - qx) + ty * (gy - qy) < 0.f) { tx = -tx; ty = -ty; lat = -lat; }
-    L.dist = sqrtf(bd2); L.lat = lat; L.tx = tx; L.ty = ty;
-    return L;
-}
-
 // swept three-circle TTC (App. D), clamped to [0, 10] s; behind or no root -> 10
 __device__ __forceinline__ float ttc_pair(float pix, float piy, float hix, float hiy, float vix, float viy, float pjx,
                                           float pjy, float hjx, float hjy, float vjx, float vjy) {
@@ -365,9 +339,9 @@ __device__ __forceinline__ float penalty(float alpha, float tau, float pmax) {
     return fminf(alpha / fmaxf(tau, kTtcFloor), pmax);
 }
 
-// per-warp exchange area: footprints of the world's agents
+// exchange area of one world: footprints, velocities, goals of its agents
 struct Exch {
-    float px[32], py[32], hx[32], hy[32], vx[32], vy[32], dx[32], dy[32];
+    float px[32], py[32], hx[32], hy[32], vx[32], vy[32], dx[32], dy[32], gx[32], gy[32];
 };
 
 __device__ __forceinline__ void publish(Exch& E, int lane, const Agent& A, float hx, float hy) {
@@ -375,6 +349,7 @@ __device__ __forceinline__ void publish(Exch& E, int lane, const Agent& A, float
     E.hx[lane] = hx; E.hy[lane] = hy;
     E.vx[lane] = A.vx; E.vy[lane] = A.vy;
     E.dx[lane] = A.dpx; E.dy[lane] = A.dpy;
+    E.gx[lane] = A.gx; E.gy[lane] = A.gy;
 }
 
 // K nearest alive other agents (lexicographic (d^2, index) order); local lane ids
@@ -498,253 +473,495 @@ __device__ void spawn_candidate(const DevRoads& rd, int w, int a, int slot, int 
     v0 = kSpawnVMin + (kSpawnVMax - kSpawnVMin) * u24(reset_draw(seed, a, ep, r, 2));
 }
 
+
+// ------------------------------------------------------------------ warp-cooperative road queries
+// Keys order candidates lexicographically by (squared distance, index): the
+// float bits of a non-negative d^2 are monotone as an unsigned integer.
+constexpr unsigned long long kKeyInf = ~0ull;
+
+__device__ __forceinline__ unsigned long long key_of(float d2, int idx) {
+    return ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)idx;
+}
+__device__ __forceinline__ float key_d2(unsigned long long k) { return __uint_as_float((unsigned)(k >> 32)); }
+__device__ __forceinline__ int key_idx(unsigned long long k) { return k == kKeyInf ? -1 : (int)(unsigned)k; }
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a < b ? b : a; }
+__device__ __forceinline__ unsigned long long shfl64(unsigned long long v, int src) {
+    unsigned lo = __shfl_sync(kFull, (unsigned)v, src), hi = __shfl_sync(kFull, (unsigned)(v >> 32), src);
+    return ((unsigned long long)hi << 32) | lo;
+}
+__device__ __forceinline__ unsigned long long shfl_xor64(unsigned long long v, int m) {
+    unsigned lo = __shfl_xor_sync(kFull, (unsigned)v, m), hi = __shfl_xor_sync(kFull, (unsigned)(v >> 32), m);
+    return ((unsigned long long)hi << 32) | lo;
+}
+__device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = umin64(v, shfl_xor64(v, o));
+    return v;
+}
+// bitonic sort of one key per lane, ascending with the lane index
+__device__ __forceinline__ unsigned long long warp_sort32(unsigned long long v, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            unsigned long long o = shfl_xor64(v, j);
+            const bool asc = (lane & k) == 0, lo = (lane & j) == 0;
+            v = (lo == asc) ? umin64(v, o) : umax64(v, o);
+        }
+    return v;
+}
+// merge a sorted running top-32 with 32 new (unsorted) candidates; returns the 32 smallest, sorted
+__device__ __forceinline__ unsigned long long merge32(unsigned long long run, unsigned long long cand, int lane) {
+    cand = warp_sort32(cand, lane);
+    unsigned long long m = umin64(run, shfl64(cand, 31 - lane));   // bitonic, holds the 32 smallest
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        unsigned long long o = shfl_xor64(m, j);
+        m = (lane & j) == 0 ? umin64(m, o) : umax64(m, o);
+    }
+    return m;
+}
+
+// Grid rows covering the square [q - R, q + R]^2: every point outside it is
+// at least R away from q.  `all` when the square covers the whole grid.
+struct Rows {
+    int cx0, cx1, cy0, cy1;
+    bool all;
+};
+__device__ __forceinline__ Rows rows_covering(const DevGrid& g, float qx, float qy, float R) {
+    const float fx0 = fminf(fmaxf((qx - R - g.x0) * g.inv_c, -1.f), (float)g.nx);
+    const float fx1 = fminf(fmaxf((qx + R - g.x0) * g.inv_c, -1.f), (float)g.nx);
+    const float fy0 = fminf(fmaxf((qy - R - g.y0) * g.inv_c, -1.f), (float)g.ny);
+    const float fy1 = fminf(fmaxf((qy + R - g.y0) * g.inv_c, -1.f), (float)g.ny);
+    Rows w;
+    w.cx0 = max((int)floorf(fx0), 0); w.cx1 = min((int)floorf(fx1), g.nx - 1);
+    w.cy0 = max((int)floorf(fy0), 0); w.cy1 = min((int)floorf(fy1), g.ny - 1);
+    w.all = w.cx0 == 0 && w.cy0 == 0 && w.cx1 == g.nx - 1 && w.cy1 == g.ny - 1;
+    return w;
+}
+
+// nearest driving-lane segment (App. G), exact: segments whose start point
+// lies in the square of half-size R + 3 m contain every segment within R (no
+// segment is longer than 3 m); R grows until a segment within R is found.
+__device__ Lane coop_nearest_lane(const DevRoads& rd, const DevGrid& g, float qx, float qy, float gx, float gy,
+                                  float R, int lane) {
+    unsigned long long best = kKeyInf;
+    for (;;) {
+        const Rows w = rows_covering(g, qx, qy, R + kSegReach);
+        const float lim = w.all ? kInf : R * R * (1.f - 1e-5f);
+        best = kKeyInf;
+        if (w.cx0 <= w.cx1)
+            for (int cy = w.cy0; cy <= w.cy1; ++cy) {
+                const int row = g.cbase + cy * g.nx;
+                const int s = __ldg(&rd.cell_off[row + w.cx0]), e = __ldg(&rd.cell_off[row + w.cx1 + 1]);
+                for (int i = s + lane; i < e; i += 32) {
+                    const uint32_t m = __ldg(&rd.smeta[i]);
+                    if ((m & (kPtSegNext | kPtLane)) != (kPtSegNext | kPtLane)) continue;
+                    const int k = __ldg(&rd.sidx[i]);
+                    const float4 a = __ldg(&rd.spt[i]);
+                    const float4 b = __ldg(&rd.pt[k + 1]);
+                    const float d2 = seg_dist2(a.x, a.y, b.x, b.y, qx, qy);
+                    if (d2 < lim) best = umin64(best, key_of(d2, k));
+                }
+            }
+        best = warp_min64(best);
+        if (best != kKeyInf || w.all) break;
+        R *= kGrow;
+    }
+    Lane L;
+    L.seg = key_idx(best);
+    if (L.seg < 0) { L.dist = kInf; L.lat = 0.f; L.tx = L.ty = 0.f; return L; }
+    const float4 a = __ldg(&rd.pt[L.seg]);
+    const float4 b = __ldg(&rd.pt[L.seg + 1]);
+    float ex = b.x - a.x, ey = b.y - a.y;
+    float nn = sqrtf(ex * ex + ey * ey);
+    float tx = ex / nn, ty = ey / nn;
+    float lat = cross2(tx, ty, qx - a.x, qy - a.y);
+    if (tx * (gx - qx) + ty * (gy - qy) < 0.f) { tx = -tx; ty = -ty; lat = -lat; }
+    L.dist = sqrtf(key_d2(best)); L.lat = lat; L.tx = tx; L.ty = ty;
+    return L;
+}
+
+// the 32 nearest road points (all types), exact; lane t returns the t-th key.
+// Only points closer than R compete; if fewer than 32 are, R grows.
+// buf: 64 keys of shared memory owned by the calling warp.
+__device__ unsigned long long coop_knn32(const DevRoads& rd, const DevGrid& g, float qx, float qy, float R, int lane,
+                                         unsigned long long* buf) {
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long run = kKeyInf;
+    for (;;) {
+        const Rows w = rows_covering(g, qx, qy, R);
+        unsigned long long thr = w.all ? kKeyInf : key_of(R * R * (1.f - 1e-5f), 0);
+        run = kKeyInf;
+        int cnt = 0;
+        if (w.cx0 <= w.cx1)
+            for (int cy = w.cy0; cy <= w.cy1; ++cy) {
+                const int row = g.cbase + cy * g.nx;
+                const int s = __ldg(&rd.cell_off[row + w.cx0]), e = __ldg(&rd.cell_off[row + w.cx1 + 1]);
+                for (int base = s; base < e; base += 32) {
+                    const int i = base + lane;
+                    unsigned long long key = kKeyInf;
+                    if (i < e) {
+                        const float4 P = __ldg(&rd.spt[i]);
+                        const float dx = P.x - qx, dy = P.y - qy;
+                        key = key_of(dx * dx + dy * dy, __ldg(&rd.sidx[i]));
+                        if (key >= thr) key = kKeyInf;
+                    }
+                    const unsigned m = __ballot_sync(kFull, key != kKeyInf);
+                    if (key != kKeyInf) buf[cnt + __popc(m & lt)] = key;
+                    cnt += __popc(m);
+                    __syncwarp();
+                    if (cnt >= 32) {
+                        run = merge32(run, buf[lane], lane);
+                        const unsigned long long rest = lane < cnt - 32 ? buf[32 + lane] : kKeyInf;
+                        __syncwarp();
+                        if (lane < cnt - 32) buf[lane] = rest;
+                        cnt -= 32;
+                        thr = umin64(thr, shfl64(run, 31));
+                        __syncwarp();
+                    }
+                }
+            }
+        if (cnt > 0) {
+            const unsigned long long c = lane < cnt ? buf[lane] : kKeyInf;
+            run = merge32(run, c, lane);
+        }
+        __syncwarp();
+        if (shfl64(run, 31) != kKeyInf || w.all) break;
+        R *= kGrow;
+    }
+    return run;
+}
+
+// road edges seen from one agent: lane-forbidden (any of the three circles
+// within r + half width of an edge segment, App. G) and the time for the
+// constant-velocity ray to reach the nearest edge segment within 40 m
+__device__ void coop_edges(const DevRoads& rd, const DevGrid& g, float px, float py, float hx, float hy, float vx,
+                           float vy, int lane, bool& forb, float& tedge) {
+    const float lim2 = (kCircR + kEdgeHalfWidth) * (kCircR + kEdgeHalfWidth);
+    // circle centres lie within kCircD of p, a touching segment within lim of a centre
+    const Rows w = rows_covering(g, px, py, kCircD + kCircR + kEdgeHalfWidth + kSegReach);
+    bool f = false;
+    if (w.cx0 <= w.cx1)
+        for (int cy = w.cy0; cy <= w.cy1; ++cy) {
+            const int row = g.cbase + cy * g.nx;
+            const int s = __ldg(&rd.cell_off[row + w.cx0]), e = __ldg(&rd.cell_off[row + w.cx1 + 1]);
+            for (int i = s + lane; i < e; i += 32) {
+                const uint32_t m = __ldg(&rd.smeta[i]);
+                if ((m & (kPtSegNext | kPtEdge)) != (kPtSegNext | kPtEdge)) continue;
+                const float4 a = __ldg(&rd.spt[i]);
+                const float4 b = __ldg(&rd.pt[__ldg(&rd.sidx[i]) + 1]);
+#pragma unroll
+                for (int c = -1; c <= 1; ++c) {
+                    float cx_ = px + (float)c * kCircD * hx, cy_ = py + (float)c * kCircD * hy;
+                    if (seg_dist2(a.x, a.y, b.x, b.y, cx_, cy_) < lim2) f = true;
+                }
+            }
+        }
+    forb = __any_sync(kFull, f);
+    const float speed = sqrtf(vx * vx + vy * vy);
+    float t_best = kInf;
+    for (int i = lane; i < g.ecnt; i += 32) {
+        const int k = __ldg(&rd.eall[g.eoff + i]);
+        const float4 a = __ldg(&rd.pt[k]);
+        const float4 b = __ldg(&rd.pt[k + 1]);
+        float exx = b.x - a.x, eyy = b.y - a.y;
+        float den = cross2(vx, vy, exx, eyy);
+        if (den != 0.f) {
+            float t = cross2(a.x - px, a.y - py, exx, eyy) / den;
+            float sg = cross2(a.x - px, a.y - py, vx, vy) / den;
+            if (t >= 0.f && sg >= 0.f && sg <= 1.f && speed * t <= kEdgeHorizon) t_best = fminf(t_best, t);
+        }
+    }
+    tedge = warp_min(t_best);
+}
+
+// per-agent results of the cooperative queries
+struct AgentQ {
+    int seg;
+    float dist, lat, tx, ty, tedge;
+    int forb, need;
+};
+
 }  // namespace
 
 // ====================================================================== the world kernel
-template <int MODE, int WPB>
-__global__ void __launch_bounds__(32 * WPB) world_kernel(const WorldArgs args) {
-    __shared__ Exch ex_all[WPB];
+// One CTA per world.  Warp 0 owns the agents (lane l = agent l): physics,
+// events, respawns, neighbours, ego features, state.  All NW warps run the
+// road queries, one agent per warp at a time, and write the road-point block
+// of the observation with coalesced stores.
+template <int MODE, int NW>
+__global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_kernel(const WorldArgs args) {
+    __shared__ Exch E;
+    __shared__ AgentQ Q[32];
+    __shared__ unsigned long long kbuf[NW][64];
+    __shared__ unsigned s_alive, s_any;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int w = blockIdx.x * WPB + warp;
-    if (w >= args.num_worlds) return;                 // warp-uniform
-    Exch& E = ex_all[warp];
+    const int w = blockIdx.x;
     const int4 wd = __ldg(&args.rd.world[w]);
-    const int a0 = wd.x, n = wd.y, p0 = wd.z, np = wd.w;
-    if (n <= 0) return;                               // warp-uniform
-    const bool has = lane < n;
-    const int a = a0 + (has ? lane : 0);
+    const int a0 = wd.x, n = wd.y;
+    if (n <= 0) return;                               // CTA-uniform
+    const DevGrid g = args.rd.grid[w];
     const DevState& st = args.st;
 
+    // ---------------- warp 0: agent registers
+    const bool has = warp == 0 && lane < n;
+    const int a = a0 + (has ? lane : 0);
     Agent A;
-    load_agent(st, a, A);
-    if (!has) { A.meta = 0; }
-    bool alive = has && (status_of(A.meta) & kAlive);
-
+    bool alive = false, respawn = false, parked_now = false, nonfin = false, done = false;
     uint32_t ev = 0;
-    float reward = 0.f, drac = 0.f;
-    bool done = false;
-    bool respawn = false;
-    Lane lane_info;
-    lane_info.seg = -1; lane_info.dist = kInf; lane_info.lat = 0.f; lane_info.tx = lane_info.ty = 0.f;
+    float reward = 0.f, drac = 0.f, hx = 1.f, hy = 0.f;
     int nb[kK];
 #pragma unroll
     for (int t = 0; t < kK; ++t) nb[t] = -1;
-    bool have_lane = false;
-    bool parked_now = false;
-
+    if (warp == 0) {
+        load_agent(st, a, A);
+        if (!has) A.meta = 0;
+        alive = has && (status_of(A.meta) & kAlive);
+        if (MODE == kModeReset) respawn = has && args.mask[a] != 0;
+        const unsigned anyr = __ballot_sync(kFull, respawn);
+        if (lane == 0) s_any = anyr;
+    }
     if (MODE == kModeReset) {
-        respawn = has && args.mask[a] != 0;
-        if (__ballot_sync(kFull, respawn) == 0) return;   // nothing to do in this world
+        __syncthreads();
+        if (s_any == 0u) return;                      // CTA-uniform: no masked agent in this world
     }
 
     if (MODE == kModeStep) {
-        float thr = 0.f, dstar = 0.f, brk = 0.f;
-        if (alive) {
-            const float* act = args.actions + 3 * (size_t)a;
-            thr = clampf(act[0], 0.f, 1.f);
-            dstar = kThetaMax * clampf(act[1], -1.f, 1.f);
-            brk = clampf(act[2], 0.f, 1.f);
-        }
-        const float prevx = A.px, prevy = A.py;
-        // ---------------- substeps with footprint contact
-        for (int s = 0; s < args.substeps; ++s) {
-            float hx, hy;
+        float prevx = 0.f, prevy = 0.f;
+        if (warp == 0) {
+            float thr = 0.f, dstar = 0.f, brk = 0.f;
+            if (alive) {
+                const float* act = args.actions + 3 * (size_t)a;
+                thr = clampf(act[0], 0.f, 1.f);
+                dstar = kThetaMax * clampf(act[1], -1.f, 1.f);
+                brk = clampf(act[2], 0.f, 1.f);
+            }
+            prevx = A.px; prevy = A.py;
+            for (int s = 0; s < args.substeps; ++s) {
+                float sx_, sy_;
+                heading_of(A.qw, A.qx, A.qy, A.qz, sx_, sy_);
+                publish(E, lane, A, sx_, sy_);
+                const uint32_t alive_bits = __ballot_sync(kFull, alive);
+                __syncwarp();
+                float fcx = 0.f, fcy = 0.f, tcz = 0.f;
+                if (alive) {
+                    for (int j = 0; j < n; ++j) {
+                        if (j == lane || !((alive_bits >> j) & 1u)) continue;
+                        const int lo = min(lane, j), hi = max(lane, j);
+                        float fx, fy, tz;
+                        pair_force(E.px[lo], E.py[lo], E.dx[lo], E.dy[lo], E.hx[lo], E.hy[lo], E.vx[lo], E.vy[lo],
+                                   E.px[hi], E.py[hi], E.dx[hi], E.dy[hi], E.hx[hi], E.hy[hi], E.vx[hi], E.vy[hi],
+                                   fx, fy, tz);
+                        if (lane == lo) { fcx -= fx; fcy -= fy; } else { fcx += fx; fcy += fy; }
+                        tcz += tz;
+                    }
+                }
+                __syncwarp();
+                if (alive) body_substep(A, thr, dstar, brk, fcx, fcy, tcz, args.h);
+            }
+            A.px += A.dpx; A.py += A.dpy; A.pz += A.dpz;
+            A.dpx = A.dpy = A.dpz = 0.f;
+            if (alive && !finite_agent(A)) {
+                nonfin = true;
+                park_agent(A);
+                alive = false;
+                atomicOr(args.out.error_word, 1u);
+            }
             heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
             publish(E, lane, A, hx, hy);
-            const uint32_t alive_bits = __ballot_sync(kFull, alive);
-            __syncwarp();
-            float fcx = 0.f, fcy = 0.f, tcz = 0.f;
+            const unsigned ab = __ballot_sync(kFull, alive);
+            if (lane == 0) s_alive = ab;
+        }
+        __syncthreads();
+        // ---------------- road queries of the events (all warps, one agent at a time)
+        for (int j = warp; j < n; j += NW) {
+            if (!((s_alive >> j) & 1u)) continue;
+            float* hnt = args.out.hint + 2 * (size_t)(a0 + j);
+            const float hl = hnt[1];
+            const Lane L = coop_nearest_lane(args.rd, g, E.px[j], E.py[j], E.gx[j], E.gy[j],
+                                             hl > 0.f ? hl + kHintSlack : kLaneR0, lane);
+            if (lane == 0) hnt[1] = L.seg >= 0 ? L.dist : 0.f;
+            bool forb;
+            float tedge;
+            coop_edges(args.rd, g, E.px[j], E.py[j], E.hx[j], E.hy[j], E.vx[j], E.vy[j], lane, forb, tedge);
+            if (lane == 0) {
+                AgentQ q;
+                q.seg = L.seg; q.dist = L.dist; q.lat = L.lat; q.tx = L.tx; q.ty = L.ty;
+                q.tedge = tedge; q.forb = forb ? 1 : 0; q.need = 0;
+                Q[j] = q;
+            }
+        }
+        __syncthreads();
+        // ---------------- events and rewards (App. G), warp 0
+        if (warp == 0) {
+            const uint32_t alive_bits = s_alive;
             if (alive) {
-                for (int j = 0; j < n; ++j) {
+                const AgentQ q = Q[lane];
+                A.step += 1;
+                const float speed = sqrtf(A.vx * A.vx + A.vy * A.vy);
+                float r = 0.f;
+                if (q.seg >= 0) {
+                    float prog = (A.px - prevx) * q.tx + (A.py - prevy) * q.ty;
+                    r += kWProgress * clampf(prog, -kProgressClip, kProgressClip);
+                    float e = q.lat / kLaneSigma;
+                    float cosd = hx * q.tx + hy * q.ty;
+                    r += kWLane * (expf(-e * e) * ((1.f - kLaneWh) + kLaneWh * fmaxf(0.f, cosd)));
+                }
+                if (fabsf(q.lat) > kOffroadLat || q.dist > kOffroadDist) { ev |= kEvOffroad; r -= kWOffroad; }
+                if (speed < kIdleSpeed) { ev |= kEvIdle; r -= kWIdle; }
+                knn_agents(E, n, lane, alive_bits, A.px, A.py, nb);
+                float tmin = kTtcMax, dmax = 0.f;
+#pragma unroll
+                for (int t = 0; t < kK; ++t) {
+                    if (nb[t] < 0) continue;
+                    const int j = nb[t];
+                    tmin = fminf(tmin, ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j],
+                                                E.vx[j], E.vy[j]));
+                    dmax = fmaxf(dmax, drac_pair(A.px, A.py, A.vx, A.vy, E.px[j], E.py[j], E.vx[j], E.vy[j]));
+                }
+                if (tmin < kTtcMax) r -= penalty(kTtcAlphaV, tmin, kTtcPmaxV);
+                r -= kWDrac * fmaxf(0.f, dmax - kDracThresh);
+                drac = dmax;
+                A.peak = fmaxf(A.peak, dmax);
+                bool collided = false;
+                for (int j = 0; j < n && !collided; ++j) {
                     if (j == lane || !((alive_bits >> j) & 1u)) continue;
-                    const int lo = min(lane, j), hi = max(lane, j);
-                    float fx, fy, tz;
-                    pair_force(E.px[lo], E.py[lo], E.dx[lo], E.dy[lo], E.hx[lo], E.hy[lo], E.vx[lo], E.vy[lo],
-                               E.px[hi], E.py[hi], E.dx[hi], E.dy[hi], E.hx[hi], E.hy[hi], E.vx[hi], E.vy[hi], fx,
-                               fy, tz);
-                    if (lane == lo) { fcx -= fx; fcy -= fy; } else { fcx += fx; fcy += fy; }
-                    tcz += tz;
+                    float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
+                    if (dx * dx + dy * dy > kPairCull2) continue;
+                    float nx, ny;
+                    if (sat2d(A.px, A.py, hx, hy, E.px[j], E.py[j], E.hx[j], E.hy[j], nx, ny) > 0.f) collided = true;
                 }
+                if (collided && A.step > kWarmup) ev |= kEvCollision;
+                if (q.tedge < kInf) r -= penalty(kTtcAlphaE, q.tedge, kTtcPmaxE);
+                if (q.forb) ev |= kEvLaneForb;
+                float gdx = A.gx - A.px, gdy = A.gy - A.py;
+                if (sqrtf(gdx * gdx + gdy * gdy) <= kGoalR) ev |= kEvGoal;
+                float r22 = 1.f - 2.f * (A.qx * A.qx + A.qy * A.qy);
+                float sdx = A.px - A.sx, sdy = A.py - A.sy;
+                if (A.pz < 0.f || sqrtf(sdx * sdx + sdy * sdy) > kDriftMax || -r22 > kTiltGz) ev |= kEvCrash;
+                if (ev & kEvGoal) r += kWGoal;
+                else if (ev & kEvCollision) r -= kWCollision;
+                else if (ev & kEvCrash) r -= kWCrash;
+                else if (ev & kEvLaneForb) r -= kWLaneForb;
+                if (A.step >= kMaxSteps) ev |= kEvTimeout;
+                reward = r;
             }
-            __syncwarp();
-            if (alive) body_substep(A, thr, dstar, brk, fcx, fcy, tcz, args.h);
-        }
-        A.px += A.dpx; A.py += A.dpy; A.pz += A.dpz;
-        A.dpx = A.dpy = A.dpz = 0.f;
-        // ---------------- non-finite guard
-        bool nonfin = false;
-        if (alive && !finite_agent(A)) {
-            nonfin = true;
-            park_agent(A);
-            alive = false;
-            atomicOr(args.out.error_word, 1u);
-        }
-        // ---------------- events and rewards from the end-of-step poses (App. G)
-        float hx, hy;
-        heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
-        publish(E, lane, A, hx, hy);
-        const uint32_t alive_bits = __ballot_sync(kFull, alive);
-        __syncwarp();
-        if (alive) {
-            A.step += 1;
-            const float speed = sqrtf(A.vx * A.vx + A.vy * A.vy);
-            lane_info = nearest_lane(args.rd, p0, np, A.px, A.py, A.gx, A.gy);
-            have_lane = true;
-            float r = 0.f;
-            if (lane_info.seg >= 0) {
-                float prog = (A.px - prevx) * lane_info.tx + (A.py - prevy) * lane_info.ty;
-                r += kWProgress * clampf(prog, -kProgressClip, kProgressClip);
-                float e = lane_info.lat / kLaneSigma;
-                float cosd = hx * lane_info.tx + hy * lane_info.ty;
-                r += kWLane * (expf(-e * e) * ((1.f - kLaneWh) + kLaneWh * fmaxf(0.f, cosd)));
+            if (nonfin) { ev = kEvNonfinite; reward = 0.f; }
+            const uint32_t sparse = kEvGoal | kEvCollision | kEvCrash | kEvLaneForb;
+            const bool term = nonfin || (!(args.flags & kFlagInvincible) && (ev & sparse));
+            done = term || (ev & kEvTimeout);
+            if (done) {
+                if (args.flags & kFlagAutoReset) respawn = true;
+                else if (!nonfin) { park_agent(A); alive = false; parked_now = true; }
             }
-            if (fabsf(lane_info.lat) > kOffroadLat || lane_info.dist > kOffroadDist) { ev |= kEvOffroad; r -= kWOffroad; }
-            if (speed < kIdleSpeed) { ev |= kEvIdle; r -= kWIdle; }
-
-            knn_agents(E, n, lane, alive_bits, A.px, A.py, nb);
-            float tmin = kTtcMax, dmax = 0.f;
-#pragma unroll
-            for (int t = 0; t < kK; ++t) {
-                if (nb[t] < 0) continue;
-                const int j = nb[t];
-                float tt = ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j], E.vx[j],
-                                    E.vy[j]);
-                tmin = fminf(tmin, tt);
-                dmax = fmaxf(dmax, drac_pair(A.px, A.py, A.vx, A.vy, E.px[j], E.py[j], E.vx[j], E.vy[j]));
-            }
-            if (tmin < kTtcMax) r -= penalty(kTtcAlphaV, tmin, kTtcPmaxV);
-            r -= kWDrac * fmaxf(0.f, dmax - kDracThresh);
-            drac = dmax;
-            A.peak = fmaxf(A.peak, dmax);
-
-            bool collided = false;
-            for (int j = 0; j < n && !collided; ++j) {
-                if (j == lane || !((alive_bits >> j) & 1u)) continue;
-                float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
-                if (dx * dx + dy * dy > kPairCull2) continue;
-                float nx, ny;
-                if (sat2d(A.px, A.py, hx, hy, E.px[j], E.py[j], E.hx[j], E.hy[j], nx, ny) > 0.f) collided = true;
-            }
-            if (collided && A.step > kWarmup) ev |= kEvCollision;
-
-            // road edges: lane-forbidden circles and the edge time-to-collision ray
-            float tedge = kInf;
-            bool forb = false;
-            const float lim2 = (kCircR + kEdgeHalfWidth) * (kCircR + kEdgeHalfWidth);
-            for (int k = p0; k < p0 + np; ++k) {
-                const uint32_t m = __ldg(&args.rd.pmeta[k]);
-                if ((m & (kPtSegNext | kPtEdge)) != (kPtSegNext | kPtEdge)) continue;
-                const float4 pa = __ldg(&args.rd.pt[k]);
-                const float4 pb = __ldg(&args.rd.pt[k + 1]);
-#pragma unroll
-                for (int c = -1; c <= 1; ++c) {
-                    float cx = A.px + (float)c * kCircD * hx, cy = A.py + (float)c * kCircD * hy;
-                    if (seg_dist2(pa.x, pa.y, pb.x, pb.y, cx, cy) < lim2) forb = true;
-                }
-                float exx = pb.x - pa.x, eyy = pb.y - pa.y;
-                float den = cross2(A.vx, A.vy, exx, eyy);
-                if (den != 0.f) {
-                    float t = cross2(pa.x - A.px, pa.y - A.py, exx, eyy) / den;
-                    float sg = cross2(pa.x - A.px, pa.y - A.py, A.vx, A.vy) / den;
-                    if (t >= 0.f && sg >= 0.f && sg <= 1.f && speed * t <= kEdgeHorizon && t < tedge) tedge = t;
-                }
-            }
-            if (tedge < kInf) r -= penalty(kTtcAlphaE, tedge, kTtcPmaxE);
-            if (forb) ev |= kEvLaneForb;
-
-            float gdx = A.gx - A.px, gdy = A.gy - A.py;
-            if (sqrtf(gdx * gdx + gdy * gdy) <= kGoalR) ev |= kEvGoal;
-            float r22 = 1.f - 2.f * (A.qx * A.qx + A.qy * A.qy);
-            float sdx = A.px - A.sx, sdy = A.py - A.sy;
-            if (A.pz < 0.f || sqrtf(sdx * sdx + sdy * sdy) > kDriftMax || -r22 > kTiltGz) ev |= kEvCrash;
-
-            if (ev & kEvGoal) r += kWGoal;
-            else if (ev & kEvCollision) r -= kWCollision;
-            else if (ev & kEvCrash) r -= kWCrash;
-            else if (ev & kEvLaneForb) r -= kWLaneForb;
-            if (A.step >= kMaxSteps) ev |= kEvTimeout;
-            reward = r;
-        }
-        if (nonfin) { ev = kEvNonfinite; reward = 0.f; }
-        const uint32_t sparse = kEvGoal | kEvCollision | kEvCrash | kEvLaneForb;
-        const bool term = nonfin || (!(args.flags & kFlagInvincible) && (ev & sparse));
-        done = term || (ev & kEvTimeout);
-        if (done) {
-            if (args.flags & kFlagAutoReset) respawn = true;
-            else if (!nonfin) { park_agent(A); alive = false; parked_now = true; }
         }
     }
 
-    // ---------------- respawns, one agent after another (index order)
-    const uint32_t rbits = __ballot_sync(kFull, respawn);
-    if (rbits) {
-        const unsigned long long seed = args.seed;
-        for (int l = 0; l < n; ++l) {
-            if (!((rbits >> l) & 1u)) continue;
-            const int ep = __shfl_sync(kFull, A.episode, l) + 1;
-            float bx = 0.f, by = 0.f, bpsi = 0.f, bv = kSpawnVMin, bgx = kSpawnGoalMin, bgy = 0.f, bscore = -1.f;
-            const bool elig = alive && lane != l && !(lane > l && ((rbits >> lane) & 1u));
-            for (int r = 0; r < kSpawnTries; ++r) {
-                float x = 0.f, y = 0.f, psi = 0.f, gx = 0.f, gy = 0.f, v0 = 0.f;
-                if (lane == l) spawn_candidate(args.rd, w, a0 + l, l, ep, r, seed, x, y, psi, gx, gy, v0);
-                x = __shfl_sync(kFull, x, l);
-                y = __shfl_sync(kFull, y, l);
-                float d2 = kInf;
-                if (elig) {
-                    float dx = A.px - x, dy = A.py - y;
-                    d2 = dx * dx + dy * dy;
+    // ---------------- respawns (warp 0, agents in index order), then the post-reset exchange
+    if (warp == 0) {
+        const uint32_t rbits = __ballot_sync(kFull, respawn);
+        if (rbits) {
+            const unsigned long long seed = args.seed;
+            for (int l = 0; l < n; ++l) {
+                if (!((rbits >> l) & 1u)) continue;
+                const int ep = __shfl_sync(kFull, A.episode, l) + 1;
+                float bx = 0.f, by = 0.f, bpsi = 0.f, bv = kSpawnVMin, bgx = kSpawnGoalMin, bgy = 0.f, bscore = -1.f;
+                const bool elig = alive && lane != l && !(lane > l && ((rbits >> lane) & 1u));
+                for (int r = 0; r < kSpawnTries; ++r) {
+                    float x = 0.f, y = 0.f, psi = 0.f, gx = 0.f, gy = 0.f, v0 = 0.f;
+                    if (lane == l) spawn_candidate(args.rd, w, a0 + l, l, ep, r, seed, x, y, psi, gx, gy, v0);
+                    x = __shfl_sync(kFull, x, l);
+                    y = __shfl_sync(kFull, y, l);
+                    float d2 = kInf;
+                    if (elig) {
+                        float dx = A.px - x, dy = A.py - y;
+                        d2 = dx * dx + dy * dy;
+                    }
+                    const float dmin = warp_min(d2);
+                    if (lane == l && dmin > bscore) { bscore = dmin; bx = x; by = y; bpsi = psi; bv = v0; bgx = gx; bgy = gy; }
+                    if (dmin >= kSpawnSpacing * kSpawnSpacing) break;
                 }
-                const float dmin = warp_min(d2);
-                if (lane == l && dmin > bscore) { bscore = dmin; bx = x; by = y; bpsi = psi; bv = v0; bgx = gx; bgy = gy; }
-                if (dmin >= kSpawnSpacing * kSpawnSpacing) break;
+                if (lane == l) {
+                    place_agent(A, bx, by, bpsi, bv, bgx, bgy);
+                    A.episode = ep;
+                    alive = true;
+                    ev |= kEvRespawned;
+                }
+                __syncwarp();
             }
-            if (lane == l) {
-                place_agent(A, bx, by, bpsi, bv, bgx, bgy);
-                A.episode = ep;
-                alive = true;
-                ev |= kEvRespawned;
-                have_lane = false;
-            }
-            __syncwarp();
         }
-    }
-
-    // ---------------- observations (App. D) of the post-reset state
-    {
-        float hx, hy;
+        const bool changed = (MODE != kModeStep) || __ballot_sync(kFull, respawn || parked_now) != 0u;
         heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
-        // warp-uniform: neighbours change only if an agent of the world respawned or parked
-        const bool refresh_nb = (MODE != kModeStep) || __ballot_sync(kFull, respawn || parked_now) != 0u;
-        uint32_t alive_bits = 0;
-        if (refresh_nb) {
+        if (changed) {
             __syncwarp();
             publish(E, lane, A, hx, hy);
-            alive_bits = __ballot_sync(kFull, alive);
-            __syncwarp();
         }
-        float* orow = args.out.obs + (size_t)a * kObsDim;
-        int knn_pt[kL];
-#pragma unroll
-        for (int t = 0; t < kL; ++t) knn_pt[t] = -1;
-        if (alive) {
-            if (!have_lane) lane_info = nearest_lane(args.rd, p0, np, A.px, A.py, A.gx, A.gy);
-            if (refresh_nb) knn_agents(E, n, lane, alive_bits, A.px, A.py, nb);
-            // ego group
-            {
-                float gbx, gby, vbx, vby;
-                to_ego(hx, hy, A.gx - A.px, A.gy - A.py, gbx, gby);
-                to_ego(hx, hy, A.vx, A.vy, vbx, vby);
-                float gn = sqrtf(gbx * gbx + gby * gby);
-                uint32_t pc = A.meta & 0xFFu, sc = (A.meta >> 8) & 0xFFu;
-                float4* o4 = reinterpret_cast<float4*>(orow);
-                o4[0] = make_float4(gbx / kSceneHalf, gby / kSceneHalf, gn > 0.f ? gby / gn : 0.f,
-                                    gn > 0.f ? gbx / gn : 1.f);
-                o4[1] = make_float4(gn / kSceneHalf, vbx / 10.f, vby / 10.f, (float)pc / 3.f);
-                o4[2] = make_float4(sc == 0 ? 1.f : 0.f, sc == 1 ? 1.f : 0.f, sc == 2 ? 1.f : 0.f, A.wz);
-                o4[3] = make_float4(A.dl / kThetaMax, A.mu, lane_info.seg >= 0 ? lane_info.lat / 3.6f : 0.f,
-                                    lane_info.seg >= 0 ? cross2(lane_info.tx, lane_info.ty, hx, hy) : 0.f);
+        const unsigned ab = __ballot_sync(kFull, alive);
+        if (lane == 0) { s_alive = ab; s_any = changed ? 1u : 0u; }
+        if (lane < n && (MODE != kModeStep || respawn)) Q[lane].need = 1;
+    }
+    __syncthreads();
+
+    // ---------------- road-point block of every observation (all warps)
+    for (int j = warp; j < n; j += NW) {
+        float* orow = args.out.obs + (size_t)(a0 + j) * kObsDim + kObsEgo + kK * kObsNbr;
+        const bool al = (s_alive >> j) & 1u;
+        int kp = -1;
+        if (al) {
+            float* hnt = args.out.hint + 2 * (size_t)(a0 + j);
+            if (Q[j].need) {
+                const Lane L = coop_nearest_lane(args.rd, g, E.px[j], E.py[j], E.gx[j], E.gy[j], kLaneR0, lane);
+                __syncwarp();
+                if (lane == 0) {
+                    Q[j].seg = L.seg; Q[j].dist = L.dist; Q[j].lat = L.lat; Q[j].tx = L.tx; Q[j].ty = L.ty;
+                    hnt[1] = L.seg >= 0 ? L.dist : 0.f;
+                }
             }
-            // neighbour group, two neighbours (20 floats, 5 float4) at a time
+            const float h32 = hnt[0];
+            const unsigned long long key =
+                coop_knn32(args.rd, g, E.px[j], E.py[j], h32 > 0.f ? h32 + kHintSlack : kKnnR0, lane, kbuf[warp]);
+            kp = key_idx(key);
+            const unsigned long long last = shfl64(key, 31);
+            if (lane == 0) hnt[0] = last != kKeyInf ? sqrtf(key_d2(last)) : 0.f;
+        }
+        float f[kObsPt] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (kp >= 0) {
+            const float4 P = __ldg(&args.rd.pt[kp]);
+            const uint32_t m = __ldg(&args.rd.pmeta[kp]);
+            const float ehx = E.hx[j], ehy = E.hy[j];
+            float bx, by, dbx, dby;
+            to_ego(ehx, ehy, P.x - E.px[j], P.y - E.py[j], bx, by);
+            to_ego(ehx, ehy, P.z, P.w, dbx, dby);
+            f[0] = bx / 10.f; f[1] = by / 10.f; f[2] = dbx; f[3] = dby;
+            f[4] = (float)(m & kPtTypeMask) / 20.f;
+            f[5] = (m & kPtEdge) ? 1.f : 0.f;
+            f[6] = 1.f;
+        }
+#pragma unroll
+        for (int c = 0; c < kObsPt; ++c) orow[kObsPt * lane + c] = f[c];
+        if (args.flags & kFlagRecord) args.out.knn_pts[(size_t)(a0 + j) * kL + lane] = kp;
+    }
+    __syncthreads();
+
+    // ---------------- neighbours, ego group, outputs, state (warp 0)
+    if (warp != 0) return;
+    if (s_any) knn_agents(E, n, lane, s_alive, A.px, A.py, nb);
+    if (has) {
+        float4* o4 = reinterpret_cast<float4*>(args.out.obs + (size_t)a * kObsDim);
+        if (alive) {
+            const AgentQ q = Q[lane];
+            float gbx, gby, vbx, vby;
+            to_ego(hx, hy, A.gx - A.px, A.gy - A.py, gbx, gby);
+            to_ego(hx, hy, A.vx, A.vy, vbx, vby);
+            float gn = sqrtf(gbx * gbx + gby * gby);
+            uint32_t pc = A.meta & 0xFFu, sc = (A.meta >> 8) & 0xFFu;
+            o4[0] = make_float4(gbx / kSceneHalf, gby / kSceneHalf, gn > 0.f ? gby / gn : 0.f, gn > 0.f ? gbx / gn : 1.f);
+            o4[1] = make_float4(gn / kSceneHalf, vbx / 10.f, vby / 10.f, (float)pc / 3.f);
+            o4[2] = make_float4(sc == 0 ? 1.f : 0.f, sc == 1 ? 1.f : 0.f, sc == 2 ? 1.f : 0.f, A.wz);
+            o4[3] = make_float4(A.dl / kThetaMax, A.mu, q.seg >= 0 ? q.lat / 3.6f : 0.f,
+                                q.seg >= 0 ? cross2(q.tx, q.ty, hx, hy) : 0.f);
 #pragma unroll
             for (int t2 = 0; t2 < kK / 2; ++t2) {
                 float f[20];
@@ -773,86 +990,30 @@ __global__ void __launch_bounds__(32 * WPB) world_kernel(const WorldArgs args) {
                     s[8] = ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, pjx, pjy, hjx, hjy, vjx, vjy) / kTtcMax;
                     s[9] = 1.f;
                 }
-                float4* o4 = reinterpret_cast<float4*>(orow + kObsEgo + 20 * t2);
 #pragma unroll
-                for (int c = 0; c < 5; ++c) o4[c] = make_float4(f[4 * c], f[4 * c + 1], f[4 * c + 2], f[4 * c + 3]);
+                for (int c = 0; c < 5; ++c)
+                    o4[(kObsEgo + 20 * t2) / 4 + c] = make_float4(f[4 * c], f[4 * c + 1], f[4 * c + 2], f[4 * c + 3]);
             }
-            // k nearest road points: sorted (d^2, index) list kept in registers
-            {
-                float key[kL];
+        } else {
 #pragma unroll
-                for (int t = 0; t < kL; ++t) key[t] = kInf;
-                for (int k = p0; k < p0 + np; ++k) {
-                    const float4 P = __ldg(&args.rd.pt[k]);
-                    float dx = P.x - A.px, dy = P.y - A.py;
-                    float d2 = dx * dx + dy * dy;
-                    if (!(d2 < key[kL - 1])) continue;
-                    float ck = d2;
-                    int ci = k;
-                    bool ins = false;
-#pragma unroll
-                    for (int t = 0; t < kL; ++t) {
-                        if (ins || ck < key[t]) {
-                            float tk = key[t]; key[t] = ck; ck = tk;
-                            int ti = knn_pt[t]; knn_pt[t] = ci; ci = ti;
-                            ins = true;
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int t4 = 0; t4 < kL / 4; ++t4) {
-                float f[28];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int k = knn_pt[4 * t4 + u];
-                    float* s = f + 7 * u;
-                    if (k < 0) {
-#pragma unroll
-                        for (int c = 0; c < 7; ++c) s[c] = 0.f;
-                        continue;
-                    }
-                    const float4 P = __ldg(&args.rd.pt[k]);
-                    const uint32_t m = __ldg(&args.rd.pmeta[k]);
-                    float bx, by, dbx, dby;
-                    to_ego(hx, hy, P.x - A.px, P.y - A.py, bx, by);
-                    to_ego(hx, hy, P.z, P.w, dbx, dby);
-                    s[0] = bx / 10.f;
-                    s[1] = by / 10.f;
-                    s[2] = dbx;
-                    s[3] = dby;
-                    s[4] = (float)(m & kPtTypeMask) / 20.f;
-                    s[5] = (m & kPtEdge) ? 1.f : 0.f;
-                    s[6] = 1.f;
-                }
-                float4* o4 = reinterpret_cast<float4*>(orow + kObsEgo + kK * kObsNbr + 28 * t4);
-#pragma unroll
-                for (int c = 0; c < 7; ++c) o4[c] = make_float4(f[4 * c], f[4 * c + 1], f[4 * c + 2], f[4 * c + 3]);
-            }
-        } else if (has) {
-            float4* o4 = reinterpret_cast<float4*>(orow);
-            for (int c = 0; c < kObsDim / 4; ++c) o4[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < (kObsEgo + kK * kObsNbr) / 4; ++c) o4[c] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (has && (args.flags & kFlagRecord)) {
-            args.out.lane_seg[a] = alive ? lane_info.seg : -1;
-#pragma unroll
-            for (int t = 0; t < kL; ++t) args.out.knn_pts[(size_t)a * kL + t] = alive ? knn_pt[t] : -1;
+        if (args.flags & kFlagRecord) {
+            args.out.lane_seg[a] = alive ? Q[lane].seg : -1;
 #pragma unroll
             for (int t = 0; t < kK; ++t)
                 args.out.knn_agents[(size_t)a * kK + t] = (alive && nb[t] >= 0) ? a0 + nb[t] : -1;
         }
+        if (MODE == kModeStep) {
+            args.out.reward[a] = reward;
+            args.out.done[a] = done ? 1 : 0;
+            args.out.events[a] = ev;
+            args.out.drac[a] = drac;
+        } else if (MODE == kModeReset && respawn) {
+            args.out.events[a] = ev;
+        }
+        store_agent(st, a, A);
     }
-
-    if (!has) return;
-    if (MODE == kModeStep) {
-        args.out.reward[a] = reward;
-        args.out.done[a] = done ? 1 : 0;
-        args.out.events[a] = ev;
-        args.out.drac[a] = drac;
-    } else if (MODE == kModeReset && respawn) {
-        args.out.events[a] = ev;
-    }
-    store_agent(st, a, A);
 }
 
 // explicit placement: d_place[a] = (x, y, psi, v0, gx, gy)
@@ -867,22 +1028,22 @@ __global__ void place_kernel(const WorldArgs args, const float* __restrict__ pla
 }
 
 template <int MODE>
-static cudaError_t launch_mode(const WorldArgs& a, int wpb, cudaStream_t s) {
-    switch (wpb) {
-        case 1: world_kernel<MODE, 1><<<(a.num_worlds + 0) / 1, 32, 0, s>>>(a); break;
-        case 2: world_kernel<MODE, 2><<<(a.num_worlds + 1) / 2, 64, 0, s>>>(a); break;
-        case 8: world_kernel<MODE, 8><<<(a.num_worlds + 7) / 8, 256, 0, s>>>(a); break;
-        default: world_kernel<MODE, 4><<<(a.num_worlds + 3) / 4, 128, 0, s>>>(a); break;
+static cudaError_t launch_mode(const WorldArgs& a, int nw, cudaStream_t s) {
+    switch (nw) {
+        case 1: world_kernel<MODE, 1><<<a.num_worlds, 32, 0, s>>>(a); break;
+        case 2: world_kernel<MODE, 2><<<a.num_worlds, 64, 0, s>>>(a); break;
+        case 8: world_kernel<MODE, 8><<<a.num_worlds, 256, 0, s>>>(a); break;
+        default: world_kernel<MODE, 4><<<a.num_worlds, 128, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t sf_launch_world(int mode, const WorldArgs& a, int wpb, cudaStream_t s) {
+cudaError_t sf_launch_world(int mode, const WorldArgs& a, int nw, cudaStream_t s) {
     if (a.num_worlds <= 0) return cudaSuccess;
     switch (mode) {
-        case kModeStep: return launch_mode<kModeStep>(a, wpb, s);
-        case kModeReset: return launch_mode<kModeReset>(a, wpb, s);
-        default: return launch_mode<kModeObserve>(a, wpb, s);
+        case kModeStep: return launch_mode<kModeStep>(a, nw, s);
+        case kModeReset: return launch_mode<kModeReset>(a, nw, s);
+        default: return launch_mode<kModeObserve>(a, nw, s);
     }
 }
 

@@ -67,7 +67,7 @@ def lib():
             "sf_output_ptrs": ([vp, vp], i32), "sf_get_indices": ([vp, vp, vp, vp, vp], i32), "sf_reset": ([vp, vp], i32), "sf_place_agents": ([vp, vp], i32),
             "sf_get_state": ([vp, vp, vp], i32), "sf_set_state": ([vp, vp, vp], i32),
             "sf_save_state": ([vp, C.c_char_p], i32), "sf_load_state": ([vp, C.c_char_p], i32),
-            "sf_sync": ([vp], i32), "sf_num_agents": ([vp], i32), "sf_num_worlds": ([vp], i32),
+            "sf_sync": ([vp], i32), "sf_autotune": ([vp, vp, f32, C.c_int, C.c_int, vp, vp], i32), "sf_num_agents": ([vp], i32), "sf_num_worlds": ([vp], i32),
             "sf_last_error": ([vp], C.c_char_p), "sf_version": ([], C.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -175,6 +175,14 @@ def sf_load_state(h, path):
 
 def sf_sync(h, allow=()):
     return _check(lib().sf_sync(h), h, allow=allow)
+
+
+def sf_autotune(h, d_actions, dt=1.0 / 30.0, substeps=4, iters=20):
+    """Pick the fastest world-kernel launch shape; returns (warps per world, ms per shape 1/2/4/8)."""
+    best = C.c_int32()
+    ms = (C.c_float * 4)()
+    _check(lib().sf_autotune(h, _ptr(d_actions), float(dt), int(substeps), int(iters), C.byref(best), ms), h)
+    return int(best.value), list(ms)
 
 
 def sf_num_agents(h) -> int:

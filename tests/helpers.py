@@ -75,3 +75,23 @@ def lex_margin_points(scene, w, p, idx_list, L=32):
     if k < 2:
         return math.inf
     return float(np.diff(ds[:k]).min())
+
+
+def in_contact(F, I, scene):
+    """Per agent: footprint overlap with another alive agent of its world (FP64 SAT)."""
+    from oracle import oracle as O
+    out = np.zeros(len(F), bool)
+    alive = (I[:, O.I_STATUS] & O.ALIVE) != 0
+    psi = 2 * np.arctan2(F[:, O.F_QZ], F[:, O.F_QW])
+    for w in range(scene.num_worlds):
+        a0, a1 = scene.agent_off[w], scene.agent_off[w + 1]
+        for i in range(a0, a1):
+            if not alive[i]:
+                continue
+            for j in range(i + 1, a1):
+                if not alive[j] or np.hypot(*(F[j, :2] - F[i, :2])) > 4.85:
+                    continue
+                d, _ = O.sat(F[i, :2], [np.cos(psi[i]), np.sin(psi[i])], F[j, :2], [np.cos(psi[j]), np.sin(psi[j])])
+                if d > 0:
+                    out[i] = out[j] = True
+    return out

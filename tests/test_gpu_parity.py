@@ -4,7 +4,10 @@ same seeded inputs.
 Tolerances (written here, derived in the design notes):
   * single step, per state block: ||gpu - oracle|| / max(||x||, floor) <= 1e-5
     (floors: 1 m, 1 m/s, 1 rad/s, 1 rad/s spin, 1e-2 rad steer; attitude angle
-    relative to max(angle, 0.1 rad));
+    relative to max(angle, 0.1 rad)) for agents not in footprint contact; an
+    agent in contact gets 5e-5: the SAT overlap is a sum of ~2-4 m terms whose
+    FP32 rounding (~1e-6 m) the 1e6 N/m penalty turns into ~1 N, i.e. ~1e-5 m/s
+    and ~1.3e-5 rad/s per step;
   * 100-step non-contact rollouts: |dp| <= 1e-3 m and |dv| <= 1e-3 m/s;
   * indices and event flags: bit-exact when the oracle is fed the GPU's FP32
     state, except near-ties (selection margins below 1e-5 m), which are counted
@@ -20,11 +23,12 @@ torch = pytest.importorskip("torch")
 
 from oracle import oracle as O
 from paper_2605_08528_b300 import sf, synth
-from tests.helpers import block_errors, subscene
+from tests.helpers import block_errors, in_contact, subscene
 
 pytestmark = pytest.mark.gpu
 
 TOL_STEP = 1e-5
+TOL_CONTACT = 5e-5
 TOL_OBS = 2e-5
 TIE = 1e-5
 
@@ -313,6 +317,7 @@ def test_ragged_and_degenerate_worlds():
     orc.reset(Fo, Io, np.ones(W.A, np.uint8), seed=3)
     assert np.abs(F - Fo).max() < 2e-5
     acts = synth.ou_actions(W.A, 20, seed=2)
+    n_contact = 0
     for t in range(20):
         F0, I0, _ = sf.sf_get_state(W.h)
         sf.sf_step(W.h, dev(acts[t]))
@@ -321,11 +326,16 @@ def test_ragged_and_degenerate_worlds():
         Fo, Io = F0.astype(np.float64), I0.copy()
         out = orc.step(Fo, Io, acts[t].astype(np.float64), flags=O.FLAG_AUTO_RESET, seed=3)
         rows = np.nonzero((Io[:, O.I_EVENTS] & O.EV["respawned"]) == 0)[0]
+        cont = (in_contact(F0.astype(np.float64), I0, sc) | in_contact(Fo, Io, sc))[rows]
+        n_contact += int(cont.sum())
         errs = block_errors(F1, Fo, rows)
         for k, e in errs.items():
-            assert e.max() <= TOL_STEP, (t, k)
+            i = int(np.argmax(np.where(cont, 0.0, e)))
+            assert np.where(cont, 0.0, e).max() <= TOL_STEP, (t, k, float(e[i]), int(rows[i]))
+            assert e.max() <= TOL_CONTACT, (t, k, float(e.max()))
         obs = W.outputs()[0].cpu().numpy()
         assert np.isfinite(obs).all()
+    print("agent-steps in footprint contact (5e-5 bound):", n_contact)
     # the world without roads: no lane, off-road every step, zero road features
     ix = W.indices()
     a = 32
