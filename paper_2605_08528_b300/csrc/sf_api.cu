@@ -187,7 +187,8 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     std::vector<int2> cand(W);
     std::vector<int32_t> cands;
     std::vector<DevGrid> grid(W);
-    std::vector<int32_t> cell_off, eall, sidx(NP);
+    std::vector<int32_t> cell_off, sidx(NP);
+    std::vector<float4> eall;
     std::vector<float4> spt(NP);
     std::vector<uint32_t> smeta(NP);
     auto in_box = [](double x, double y) { return std::fabs(x) <= 100.0 && std::fabs(y) <= 100.0; };
@@ -259,7 +260,8 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
         std::vector<int> cnt(ncell + 1, 0);
         for (int k = q0; k < q1; ++k) {
             cnt[cy_of(r->py[k]) * nx + cx_of(r->px[k]) + 1]++;
-            if ((pmeta[k] & (sfk::kPtSegNext | sfk::kPtEdge)) == (sfk::kPtSegNext | sfk::kPtEdge)) eall.push_back(k);
+            if ((pmeta[k] & (sfk::kPtSegNext | sfk::kPtEdge)) == (sfk::kPtSegNext | sfk::kPtEdge))
+                eall.push_back(make_float4(r->px[k], r->py[k], r->px[k + 1], r->py[k + 1]));
         }
         for (int i = 0; i < ncell; ++i) cnt[i + 1] += cnt[i];
         for (int i = 0; i <= ncell; ++i) cell_off.push_back(q0 + cnt[i]);
@@ -300,13 +302,13 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     SF_ALLOC(dpmeta, uint32_t, (size_t)NP + 1);
     SF_ALLOC(dpend, int32_t, (size_t)NP + 1);
     SF_ALLOC(dcands, int32_t, cands.size() + 1);
-    DevGrid* dgrid; int32_t *dcoff, *dsidx, *deall; float4* dspt; uint32_t* dsmeta;
+    DevGrid* dgrid; int32_t *dcoff, *dsidx; float4 *dspt, *deall; uint32_t* dsmeta;
     SF_ALLOC(dgrid, DevGrid, (size_t)W);
     SF_ALLOC(dcoff, int32_t, cell_off.size());
     SF_ALLOC(dspt, float4, (size_t)NP + 1);
     SF_ALLOC(dsmeta, uint32_t, (size_t)NP + 1);
     SF_ALLOC(dsidx, int32_t, (size_t)NP + 1);
-    SF_ALLOC(deall, int32_t, eall.size() + 1);
+    SF_ALLOC(deall, float4, eall.size() + 1);
     h->rd = DevRoads{dworld, dcand, dpt, dpmeta, dpend, dcands, dgrid, dcoff, dspt, dsmeta, dsidx, deall};
     float *obs, *reward, *drac; uint8_t* done; uint32_t* events; int32_t *lane_seg, *knn_pts, *knn_agents;
     unsigned int* err_word; float* hint;
@@ -345,7 +347,7 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     up(dspt, spt.data(), spt.size() * sizeof(float4));
     up(dsmeta, smeta.data(), smeta.size() * 4);
     up(dsidx, sidx.data(), sidx.size() * 4);
-    up(deall, eall.data(), eall.size() * 4);
+    up(deall, eall.data(), eall.size() * sizeof(float4));
     for (float4* p : {pos, quat, vel, angv, spin, goal}) zero(p, Aa * sizeof(float4));
     zero(peak, Aa * 4); zero(step, Aa * 4); zero(episode, Aa * 4);
     up(meta, meta_h.data(), Aa * 4);

@@ -130,7 +130,7 @@ struct DevRoads {
     const float4* spt;      // points sorted by cell
     const uint32_t* smeta;  // their meta
     const int32_t* sidx;    // their input-order index
-    const int32_t* eall;    // every edge segment of a world, at grid.eoff
+    const float4* eseg;     // every edge segment of a world (ax, ay, bx, by), at grid.eoff
 };
 
 struct DevOutputs {

@@ -302,6 +302,15 @@ __device__ __forceinline__ float ttc_pair(float pix, float piy, float hix, float
     if (bx < 0.f) return kTtcMax;
     float dvx = vjx - vix, dvy = vjy - viy;
     float A2 = dvx * dvx + dvy * dvy;
+    {   // every circle centre is within kCircD of its car centre: if the centres never come
+        // within 2 (r + d) of each other for t >= 0, no circle pair can touch
+        const float px_ = pjx - pix, py_ = pjy - piy;
+        const float pv = px_ * dvx + py_ * dvy;
+        const float c2 = px_ * px_ + py_ * py_;
+        const float dmin2 = (pv < 0.f && A2 > 0.f) ? c2 - pv * pv / A2 : c2;
+        const float lim = 2.f * (kCircR + kCircD);
+        if (dmin2 > lim * lim * (1.f + 1e-4f) + 1e-3f) return kTtcMax;
+    }
     float best = kInf;
 #pragma unroll
     for (int a = -1; a <= 1; ++a)
@@ -660,19 +669,24 @@ __device__ void coop_edges(const DevRoads& rd, const DevGrid& g, float px, float
             }
         }
     forb = __any_sync(kFull, f);
+    // ray p + v t against every edge segment; the acceptance tests t >= 0,
+    // 0 <= s <= 1 and |v| t <= 40 m are evaluated multiplied through by the
+    // denominator (sign-aware), and only accepted hits divide.  A segment whose
+    // start is farther than 40 m + 3 m cannot be hit within the horizon.
     const float speed = sqrtf(vx * vx + vy * vy);
+    const float reach2 = (kEdgeHorizon + kSegReach) * (kEdgeHorizon + kSegReach);
     float t_best = kInf;
     for (int i = lane; i < g.ecnt; i += 32) {
-        const int k = __ldg(&rd.eall[g.eoff + i]);
-        const float4 a = __ldg(&rd.pt[k]);
-        const float4 b = __ldg(&rd.pt[k + 1]);
-        float exx = b.x - a.x, eyy = b.y - a.y;
-        float den = cross2(vx, vy, exx, eyy);
-        if (den != 0.f) {
-            float t = cross2(a.x - px, a.y - py, exx, eyy) / den;
-            float sg = cross2(a.x - px, a.y - py, vx, vy) / den;
-            if (t >= 0.f && sg >= 0.f && sg <= 1.f && speed * t <= kEdgeHorizon) t_best = fminf(t_best, t);
-        }
+        const float4 sg4 = __ldg(&rd.eseg[g.eoff + i]);
+        const float apx = sg4.x - px, apy = sg4.y - py;
+        if (apx * apx + apy * apy > reach2) continue;
+        const float exx = sg4.z - sg4.x, eyy = sg4.w - sg4.y;
+        const float den = cross2(vx, vy, exx, eyy);
+        if (den == 0.f) continue;
+        const float nt = cross2(apx, apy, exx, eyy), ns = cross2(apx, apy, vx, vy);
+        const bool ok = den > 0.f ? (nt >= 0.f && ns >= 0.f && ns <= den && speed * nt <= kEdgeHorizon * den)
+                                  : (nt <= 0.f && ns <= 0.f && ns >= den && speed * nt >= kEdgeHorizon * den);
+        if (ok) t_best = fminf(t_best, nt / den);
     }
     tedge = warp_min(t_best);
 }
@@ -713,8 +727,9 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     uint32_t ev = 0;
     float reward = 0.f, drac = 0.f, hx = 1.f, hy = 0.f;
     int nb[kK];
+    float tt[kK];
 #pragma unroll
-    for (int t = 0; t < kK; ++t) nb[t] = -1;
+    for (int t = 0; t < kK; ++t) { nb[t] = -1; tt[t] = kTtcMax; }
     if (warp == 0) {
         load_agent(st, a, A);
         if (!has) A.meta = 0;
@@ -817,8 +832,9 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
                 for (int t = 0; t < kK; ++t) {
                     if (nb[t] < 0) continue;
                     const int j = nb[t];
-                    tmin = fminf(tmin, ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j],
-                                                E.vx[j], E.vy[j]));
+                    tt[t] = ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j], E.vx[j],
+                                     E.vy[j]);
+                    tmin = fminf(tmin, tt[t]);
                     dmax = fmaxf(dmax, drac_pair(A.px, A.py, A.vx, A.vy, E.px[j], E.py[j], E.vx[j], E.vy[j]));
                 }
                 if (tmin < kTtcMax) r -= penalty(kTtcAlphaV, tmin, kTtcPmaxV);
@@ -987,7 +1003,8 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
                     s[5] = sqrtf(vjx * vjx + vjy * vjy) / 10.f;
                     s[6] = dvx / 10.f;
                     s[7] = dvy / 10.f;
-                    s[8] = ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, pjx, pjy, hjx, hjy, vjx, vjy) / kTtcMax;
+                    s[8] = (s_any ? ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, pjx, pjy, hjx, hjy, vjx, vjy)
+                                  : tt[2 * t2 + u]) / kTtcMax;
                     s[9] = 1.f;
                 }
 #pragma unroll
