@@ -229,6 +229,57 @@ sf_status sf_load_state(sf_handle h, const char* path);
  * device recorded such a condition since the last sync (and clear it). */
 sf_status sf_sync(sf_handle h);
 
+/* ------------------------------------------------------------------------
+ * BF16 tensor-core MLPs (dynamics surrogate and policy of the step).
+ * An MLP of L dense layers y = act(W x + b), W [out, in] fp32 masters with
+ * bf16 copies for the tcgen05 GEMMs, fp32 accumulation.  Hidden layers use
+ * hidden_act, the last layer out_act (SF_ACT_*).  All device work runs on
+ * the stream given to sf_mlp_create.
+ * ---------------------------------------------------------------------- */
+typedef struct sf_mlp* sf_mlp_handle;
+#define SF_ACT_NONE 0
+#define SF_ACT_ELU 1   /* the paper's network activation (App. E) */
+#define SF_ACT_SILU 2
+#define SF_ACT_TANH 3
+
+/* dims[0..num_layers] are the layer widths (1..4096); 1 <= num_layers <= 8.
+ * Weights start at zero.  Errors: SF_ERR_INVALID_ARG, SF_ERR_OOM, SF_ERR_CUDA. */
+sf_status sf_mlp_create(int num_layers, const int32_t* dims, int hidden_act, int out_act, void* cuda_stream,
+                        sf_mlp_handle* out);
+sf_status sf_mlp_destroy(sf_mlp_handle m);
+const char* sf_mlp_last_error(sf_mlp_handle m);
+
+/* Set / read layer `layer`: h_w [out][in] and h_b [out] fp32 host arrays
+ * (synchronous); sf_mlp_get_layer also returns the last gradients h_gw, h_gb
+ * (any pointer may be NULL). */
+sf_status sf_mlp_set_layer(sf_mlp_handle m, int layer, const float* h_w, const float* h_b);
+sf_status sf_mlp_get_layer(sf_mlp_handle m, int layer, float* h_w, float* h_b, float* h_gw, float* h_gb);
+
+/* Inference: d_y[b][0..out) = MLP(d_x[b][0..in)) for b < batch; d_x has row
+ * stride ldx >= in floats, d_y row stride ldy >= out.  Asynchronous. */
+sf_status sf_mlp_forward(sf_mlp_handle m, const float* d_x, int ldx, int batch, float* d_y, int ldy);
+
+/* One training step on a batch (batch % 8 == 0): forward, mean-squared-error
+ * loss against d_t [batch][out], backward through every layer (gradients kept
+ * for sf_mlp_get_layer) and, if update != 0, an Adam step (beta 0.9, 0.999,
+ * eps 1e-8) with learning rate lr.  h_loss (may be NULL) receives the loss
+ * (synchronous when given). */
+sf_status sf_mlp_train_step(sf_mlp_handle m, const float* d_x, const float* d_t, int batch, float lr, int update,
+                            float* h_loss);
+
+/* Wait for the MLP's stream; SF_ERR_TIMEOUT if a GEMM's bounded wait gave up. */
+sf_status sf_mlp_sync(sf_mlp_handle m);
+
+/* The GEMM itself: C = act(A . B^T + bias) with A [M][K], B [N][K] bf16
+ * row-major device arrays (K % 8 == 0, 16-byte aligned), bias [N] or NULL,
+ * outputs (any may be NULL): f32 [M][ldc], bf16 [M][ldc], transposed bf16
+ * [N][ldt].  tile_n: 64, 128 or 256 output columns per CTA.  d_err (may be
+ * NULL) is a device word that receives bit 2 if a bounded wait expired.
+ * Asynchronous on cuda_stream. */
+sf_status sf_gemm_bf16(const void* d_a, const void* d_b, const float* d_bias, int M, int N, int K, int act,
+                       float* d_out_f32, void* d_out_bf16, void* d_out_bf16_t, int ldc, int ldt, int tile_n,
+                       unsigned* d_err, void* cuda_stream);
+
 /* Number of agents and worlds of the loaded roads (0 before sf_load_roads). */
 int32_t sf_num_agents(sf_handle h);
 int32_t sf_num_worlds(sf_handle h);

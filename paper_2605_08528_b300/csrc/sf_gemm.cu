@@ -1,0 +1,299 @@
+// sf_gemm.cu -- BF16 tensor-core GEMM with a fused epilogue for the MLPs (sm_103a).
+//
+//   C[M, N] = act(A[M, K] . B[N, K]^T + bias[N])
+//
+// A and B are bf16, row-major with K contiguous (B is a weight matrix stored
+// [out, in]); accumulation is fp32.  One CTA computes a 128 x BN tile:
+//   warp 0 lane 0  issues TMA loads of 128 x 64 (A) and BN x 64 (B) K-tiles
+//                  into a STAGES-deep ring (128-byte swizzle);
+//   warp 1 lane 0  issues tcgen05.mma (M 128, N BN, K 16) into a TMEM
+//                  accumulator of BN fp32 columns and commits each stage back;
+//   warps 0-3      read the accumulator with tcgen05.ld (warp w owns rows
+//                  32w..32w+31), add the bias, apply the activation and store.
+// Every mbarrier wait is bounded: on expiry the kernel records SF_GEMM_TIMEOUT
+// in the error word, stops issuing work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sf_gemm.cuh"
+
+namespace {
+
+constexpr int kBM = 128, kBK = 64, kStages = 4, kThreads = 128;
+constexpr uint32_t kWaitLimit = 1u << 30;
+constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait: false (and the error flag) when the barrier has not completed
+// within kWaitNs of wall time
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 63 && global_ns() - t0 > kWaitNs) break;
+    }
+    if (err) atomicOr(err, SF_GEMM_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major operand, rows of 128 B (64 bf16),
+// 128-byte swizzle, 8-row atoms 1024 B apart (stride byte offset).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;      // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024u >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 46;               // descriptor version
+    d |= (uint64_t)2 << 61;               // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both K-major
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float activate(float x, int act) {
+    switch (act) {
+        case SF_ACT_ELU: return x > 0.f ? x : expm1f(x);
+        case SF_ACT_SILU: return x / (1.f + expf(-x));
+        case SF_ACT_TANH: return tanhf(x);
+        default: return x;
+    }
+}
+
+template <int BN>
+struct alignas(1024) GemmSmem {
+    __nv_bfloat16 a[kStages][kBM * kBK];
+    __nv_bfloat16 b[kStages][BN * kBK];
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t done;
+    uint32_t tmem_base;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                   const GemmArgs args) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    GemmSmem<BN>& S = *reinterpret_cast<GemmSmem<BN>*>(
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+    const int nk = (args.K + kBK - 1) / kBK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) { mbar_init(&S.full[s], 1); mbar_init(&S.empty[s], 1); }
+        mbar_init(&S.done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {   // TMEM accumulator: BN fp32 columns x 128 lanes
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                     "r"((uint32_t)BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = S.tmem_base;
+    constexpr uint32_t kTxBytes = (kBM + BN) * kBK * 2;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % kStages;
+            if (kt >= kStages && !mbar_wait(&S.empty[s], ((kt / kStages) & 1) ^ 1, args.err)) break;
+            mbar_expect_tx(&S.full[s], kTxBytes);
+            tma_load_2d(S.a[s], &map_a, kt * kBK, m0, &S.full[s]);
+            tma_load_2d(S.b[s], &map_b, kt * kBK, n0, &S.full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        constexpr uint32_t idesc = instr_desc(kBM, BN);
+        bool ok = true;
+        for (int kt = 0; kt < nk && ok; ++kt) {
+            const int s = kt % kStages;
+            ok = mbar_wait(&S.full[s], (kt / kStages) & 1, args.err);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t ad = smem_desc(smem_u32(S.a[s])), bd = smem_desc(smem_u32(S.b[s]));
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)    // advance 16 bf16 (32 B) along K inside the swizzle atom
+                umma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kt > 0 || k > 0) ? 1u : 0u);
+            umma_commit(&S.empty[s]);
+        }
+        umma_commit(&S.done);                  // arrives when every issued MMA has completed
+    }
+    __syncwarp();
+
+    // ---------------- epilogue: TMEM -> bias + activation -> global
+    const bool have = __all_sync(0xFFFFFFFFu, mbar_wait(&S.done, 0, args.err));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int r = m0 + warp * 32 + lane;
+    if (have) {
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+            const int nb = n0 + c * 32;
+            if (r >= args.M || nb >= args.N) continue;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int n = nb + i;
+                float x = v[i] + ((args.bias && n < args.N) ? args.bias[n] : 0.f);
+                if (args.pre && n < args.N) args.pre[(size_t)r * args.ldc + n] = x;
+                x = activate(x, args.act);
+                if (n < args.N) {
+                    if (args.out_f32) args.out_f32[(size_t)r * args.ldc + n] = x;
+                    if (args.out_bf16) args.out_bf16[(size_t)r * args.ldc + n] = __float2bfloat16_rn(x);
+                    if (args.out_bf16_t) args.out_bf16_t[(size_t)n * args.ldt + r] = __float2bfloat16_rn(x);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+    }
+    // a stage still holding TMA bytes after a timeout must land before exit
+    if (threadIdx.x == 0 && !have) {
+        for (int s = 0; s < kStages && s < nk; ++s) {
+            const int last = ((nk - 1 - s) / kStages) * kStages + s;   // last K tile loaded into stage s
+            mbar_wait(&S.full[s], (last / kStages) & 1, nullptr);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host: tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// bf16 matrix [rows, cols] row-major (cols contiguous), box 64 x box_rows, 128-byte swizzle
+bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_bn(const GemmArgs& g, cudaStream_t s) {
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, g.A, g.M, g.K, kBM) || !make_map(&mb, g.B, g.Nb, g.K, BN)) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(GemmSmem<BN>) + 1024;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((g.N + BN - 1) / BN, (g.M + kBM - 1) / kBM);
+    tc_gemm_kernel<BN><<<grid, kThreads, smem, s>>>(ma, mb, g);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t sf_gemm_launch(const GemmArgs& g, cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    if (g.K <= 0 || g.K % 8 != 0 || g.Nb < 1) return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(g.A) | reinterpret_cast<uintptr_t>(g.B)) & 15) return cudaErrorInvalidValue;
+    switch (g.bn) {
+        case 64: return launch_bn<64>(g, s);
+        case 128: return launch_bn<128>(g, s);
+        case 256: return launch_bn<256>(g, s);
+        default: return cudaErrorInvalidValue;
+    }
+}

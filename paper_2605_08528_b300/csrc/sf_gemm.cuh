@@ -1,0 +1,28 @@
+// sf_gemm.cuh -- arguments of the BF16 tensor-core GEMM (sf_gemm.cu).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/sf.h"   // SF_ACT_* activation codes
+#define SF_GEMM_TIMEOUT 2u   // error-word bit: a bounded mbarrier wait gave up
+
+// C[M, N] = act(A[M, K] . B[N, K]^T + bias[N]); A, B bf16 row-major, K % 8 == 0,
+// 16-byte aligned bases.  Rows of A beyond M and of B beyond Nb read as zero.
+struct GemmArgs {
+    const __nv_bfloat16* A;   // [M, K]
+    const __nv_bfloat16* B;   // [Nb, K]
+    const float* bias;        // [N] or null
+    float* pre;               // [M, ldc] pre-activation (f32) or null
+    float* out_f32;           // [M, ldc] or null
+    __nv_bfloat16* out_bf16;  // [M, ldc] or null
+    __nv_bfloat16* out_bf16_t;// [N, ldt] transposed or null
+    int M, N, Nb, K;
+    int ldc, ldt;
+    int act;
+    int bn;                   // tile width 64, 128 or 256
+    unsigned* err;            // device error word (SF_GEMM_TIMEOUT)
+};
+
+cudaError_t sf_gemm_launch(const GemmArgs& g, cudaStream_t s);

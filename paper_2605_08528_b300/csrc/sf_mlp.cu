@@ -1,0 +1,421 @@
+// sf_mlp.cu -- BF16 MLPs on the tensor cores: inference and training (Adam).
+//
+// An MLP of L dense layers y = act_l(W_l x + b_l) keeps fp32 master weights,
+// bf16 copies W_l [out, in] (forward) and W_l^T [in, out] (backward), and for
+// a training batch the bf16 layer inputs X_l [B, in], their transposes X_l^T
+// and the fp32 pre-activations Z_l [B, out].  Every product runs in the
+// tcgen05 GEMM of sf_gemm.cu (C = act(A B^T + bias)):
+//   forward   X_{l+1} = act(X_l W_l^T + b_l)          A = X_l,      B = W_l
+//   weights   dW_l    = dZ_l^T X_l                     A = dZ_l^T,   B = X_l^T
+//   inputs    dX_l    = dZ_l W_l                       A = dZ_l,     B = W_l^T
+// with dZ_l = dX_{l+1} * act'(Z_l) computed elementwise, bias gradients by a
+// column reduction, and an Adam step that refreshes both bf16 copies.  Widths
+// are padded to multiples of 8 (the GEMM's 16-byte row rule) with zeros.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sf.h"
+#include "sf_gemm.cuh"
+
+namespace {
+
+constexpr int kMaxLayers = 8;
+
+int pad8(int x) { return (x + 7) & ~7; }
+
+__device__ __forceinline__ float act_grad(float z, int act) {
+    switch (act) {
+        case SF_ACT_ELU: return z > 0.f ? 1.f : expf(z);
+        case SF_ACT_SILU: {
+            const float s = 1.f / (1.f + expf(-z));
+            return s * (1.f + z * (1.f - s));
+        }
+        case SF_ACT_TANH: {
+            const float t = tanhf(z);
+            return 1.f - t * t;
+        }
+        default: return 1.f;
+    }
+}
+
+// x [B, n] f32 -> bf16 [B, ld] (zero padded) and optionally bf16^T [ld, B]
+__global__ void to_bf16_kernel(const float* __restrict__ x, int B, int n, int ldx, __nv_bfloat16* __restrict__ y,
+                               int ld, __nv_bfloat16* __restrict__ yt) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)B * ld) return;
+    const int b = (int)(i / ld), c = (int)(i % ld);
+    const __nv_bfloat16 v = __float2bfloat16_rn(c < n ? x[(size_t)b * ldx + c] : 0.f);
+    y[i] = v;
+    if (yt) yt[(size_t)c * B + b] = v;
+}
+
+// dZ = dA * act'(Z), written as bf16 [B, ld] and bf16^T [ld, B]
+__global__ void act_back_kernel(const float* __restrict__ dA, const float* __restrict__ Z, int B, int n, int ld,
+                                int act, __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)B * ld) return;
+    const int b = (int)(i / ld), c = (int)(i % ld);
+    float g = 0.f;
+    if (c < n) g = dA[(size_t)b * ld + c] * act_grad(Z[(size_t)b * ld + c], act);
+    const __nv_bfloat16 v = __float2bfloat16_rn(g);
+    dz[i] = v;
+    dzt[(size_t)c * B + b] = v;
+}
+
+// mean-squared-error gradient of the output: dY = 2 (y - t) / (B n), loss partial sums
+__global__ void mse_grad_kernel(const float* __restrict__ y, const float* __restrict__ t, int B, int n, int ld,
+                                int ldt, float* __restrict__ dy, float* __restrict__ loss) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.f;
+    if (i < (size_t)B * ld) {
+        const int b = (int)(i / ld), c = (int)(i % ld);
+        float d = 0.f;
+        if (c < n) {
+            d = y[i] - t[(size_t)b * ldt + c];
+            l = d * d;
+        }
+        dy[i] = 2.f * d / ((float)B * (float)n);
+    }
+    if (loss) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o);
+        if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss, l / ((float)B * (float)n));
+    }
+}
+
+// column sums of the bf16 dZ^T rows: db[c] = sum_b dZ[b, c] (one warp per column)
+__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ dzt, int B, int n, float* __restrict__ db) {
+    const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (c >= n) return;
+    float s = 0.f;
+    for (int b = lane; b < B; b += 32) s += __bfloat162float(dzt[(size_t)c * B + b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) db[c] = s;
+}
+
+// Adam (Kingma & Ba) on fp32 masters; refresh bf16 W [out, ldi] and W^T [ldi, ldo]
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2,
+                            int out, int in, int ldi, int ldo, __nv_bfloat16* __restrict__ wb,
+                            __nv_bfloat16* __restrict__ wbt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (wb) {   // weight matrix element (o, k) of [out, in]
+        const int o = i / in, k = i % in;
+        const __nv_bfloat16 hb = __float2bfloat16_rn(wi);
+        wb[(size_t)o * ldi + k] = hb;
+        wbt[(size_t)k * ldo + o] = hb;
+    }
+}
+
+// gather the fp32 weight gradient [out, ldi] into the dense [out, in] layout
+__global__ void compact_kernel(const float* __restrict__ src, int out, int in, int ldi, float* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= out * in) return;
+    dst[i] = src[(size_t)(i / in) * ldi + (i % in)];
+}
+
+__global__ void weights_to_bf16_kernel(const float* __restrict__ w, int out, int in, int ldi, int ldo,
+                                       __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ wbt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= out * in) return;
+    const int o = i / in, k = i % in;
+    const __nv_bfloat16 hb = __float2bfloat16_rn(w[i]);
+    wb[(size_t)o * ldi + k] = hb;
+    wbt[(size_t)k * ldo + o] = hb;
+}
+
+unsigned grid1(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+struct sf_mlp {
+    int L = 0;
+    int dim[kMaxLayers + 1] = {};   // true widths
+    int ld[kMaxLayers + 1] = {};    // padded widths
+    int hidden_act = 0, out_act = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::vector<void*> allocs;
+    // parameters
+    float* w[kMaxLayers] = {};      // fp32 [out, in]
+    float* b[kMaxLayers] = {};      // fp32 [out]
+    __nv_bfloat16* wb[kMaxLayers] = {};    // [out, ld_in], zero padded
+    __nv_bfloat16* wbt[kMaxLayers] = {};   // [ld_in, ld_out]
+    float *gw[kMaxLayers] = {}, *gb[kMaxLayers] = {};
+    float *mw[kMaxLayers] = {}, *vw[kMaxLayers] = {}, *mb[kMaxLayers] = {}, *vb[kMaxLayers] = {};
+    int adam_t = 0;
+    // batch buffers
+    int cap = 0;
+    __nv_bfloat16* x[kMaxLayers + 1] = {};   // [cap, ld_l]
+    __nv_bfloat16* xt[kMaxLayers + 1] = {};  // [ld_l, cap]
+    float* z[kMaxLayers] = {};               // [cap, ld_{l+1}]
+    float* y = nullptr;                      // [cap, ld_L] output f32
+    float* dA = nullptr;                     // [cap, max ld] f32
+    __nv_bfloat16 *dz = nullptr, *dzt = nullptr;
+    float* gwfull = nullptr;                 // [max out, max ld] f32 (padded gradient)
+    float* loss = nullptr;
+    unsigned* errw = nullptr;
+};
+
+namespace {
+
+sf_status mfail(sf_mlp* m, sf_status s, const std::string& e) {
+    if (m) m->err = e;
+    return s;
+}
+
+template <class T>
+cudaError_t malloc_zero(sf_mlp* m, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+    if (e != cudaSuccess) return e;
+    m->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaMemset(q, 0, count * sizeof(T) + 16);
+}
+
+int act_of(const sf_mlp* m, int l) { return l == m->L - 1 ? m->out_act : m->hidden_act; }
+
+int tile_for(int n) { return n >= 256 ? 256 : (n > 64 ? 128 : 64); }
+
+cudaError_t gemm(sf_mlp* m, const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, int M, int N, int Nb,
+                 int K, int act, float* pre, float* out_f32, __nv_bfloat16* out_bf16, __nv_bfloat16* out_t, int ldc,
+                 int ldt) {
+    GemmArgs g{};
+    g.A = A; g.B = B; g.bias = bias; g.pre = pre; g.out_f32 = out_f32; g.out_bf16 = out_bf16; g.out_bf16_t = out_t;
+    g.M = M; g.N = N; g.Nb = Nb; g.K = K; g.ldc = ldc; g.ldt = ldt; g.act = act; g.bn = tile_for(N); g.err = m->errw;
+    return sf_gemm_launch(g, m->stream);
+}
+
+cudaError_t ensure_batch(sf_mlp* m, int B) {
+    if (B <= m->cap) return cudaSuccess;
+    // buffers of a smaller batch stay allocated until destroy; the new set replaces them
+    int maxld = 0;
+    for (int l = 0; l <= m->L; ++l) maxld = maxld > m->ld[l] ? maxld : m->ld[l];
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l <= m->L && e == cudaSuccess; ++l) {
+        e = malloc_zero(m, &m->x[l], (size_t)B * m->ld[l]);
+        if (e == cudaSuccess) e = malloc_zero(m, &m->xt[l], (size_t)B * m->ld[l]);
+    }
+    for (int l = 0; l < m->L && e == cudaSuccess; ++l) e = malloc_zero(m, &m->z[l], (size_t)B * m->ld[l + 1]);
+    if (e == cudaSuccess) e = malloc_zero(m, &m->y, (size_t)B * m->ld[m->L]);
+    if (e == cudaSuccess) e = malloc_zero(m, &m->dA, (size_t)B * maxld);
+    if (e == cudaSuccess) e = malloc_zero(m, &m->dz, (size_t)B * maxld);
+    if (e == cudaSuccess) e = malloc_zero(m, &m->dzt, (size_t)B * maxld);
+    if (e == cudaSuccess) m->cap = B;
+    return e;
+}
+
+// forward of a batch already converted into x[0] (and xt[0] when training)
+cudaError_t forward_core(sf_mlp* m, int B, bool train) {
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < m->L && e == cudaSuccess; ++l) {
+        const bool last = l == m->L - 1;
+        e = gemm(m, m->x[l], m->wb[l], m->b[l], B, m->dim[l + 1], m->dim[l + 1], m->ld[l], act_of(m, l),
+                 train ? m->z[l] : nullptr, last ? m->y : nullptr, last ? nullptr : m->x[l + 1],
+                 (train && !last) ? m->xt[l + 1] : nullptr, m->ld[l + 1], B);
+    }
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+sf_status sf_mlp_create(int num_layers, const int32_t* dims, int hidden_act, int out_act, void* cuda_stream,
+                        sf_mlp_handle* out) {
+    if (!out || !dims || num_layers < 1 || num_layers > kMaxLayers) return SF_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int l = 0; l <= num_layers; ++l)
+        if (dims[l] < 1 || dims[l] > 4096) return SF_ERR_INVALID_ARG;
+    if (hidden_act < 0 || hidden_act > 3 || out_act < 0 || out_act > 3) return SF_ERR_INVALID_ARG;
+    sf_mlp* m = new sf_mlp();
+    m->L = num_layers;
+    for (int l = 0; l <= num_layers; ++l) { m->dim[l] = dims[l]; m->ld[l] = pad8(dims[l]); }
+    m->hidden_act = hidden_act;
+    m->out_act = out_act;
+    m->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = malloc_zero(m, &m->errw, 1);
+    if (e == cudaSuccess) e = malloc_zero(m, &m->loss, 1);
+    int maxo = 0, maxi = 0;
+    for (int l = 0; l < num_layers && e == cudaSuccess; ++l) {
+        const int o = dims[l + 1], i = dims[l];
+        maxo = maxo > m->ld[l + 1] ? maxo : m->ld[l + 1];
+        maxi = maxi > m->ld[l] ? maxi : m->ld[l];
+        e = malloc_zero(m, &m->w[l], (size_t)o * i);
+        if (e == cudaSuccess) e = malloc_zero(m, &m->b[l], (size_t)o);
+        if (e == cudaSuccess) e = malloc_zero(m, &m->wb[l], (size_t)o * m->ld[l]);
+        if (e == cudaSuccess) e = malloc_zero(m, &m->wbt[l], (size_t)m->ld[l] * m->ld[l + 1]);
+        if (e == cudaSuccess) e = malloc_zero(m, &m->gw[l], (size_t)o * i);
+        if (e == cudaSuccess) e = malloc_zero(m, &m->gb[l], (size_t)o);
+        if (e == cudaSuccess) e = malloc_zero(m, &m->mw[l], (size_t)o * i);
+        if (e == cudaSuccess) e = malloc_zero(m, &m->vw[l], (size_t)o * i);
+        if (e == cudaSuccess) e = malloc_zero(m, &m->mb[l], (size_t)o);
+        if (e == cudaSuccess) e = malloc_zero(m, &m->vb[l], (size_t)o);
+    }
+    if (e == cudaSuccess) e = malloc_zero(m, &m->gwfull, (size_t)maxo * maxi);
+    if (e != cudaSuccess) {
+        for (void* p : m->allocs) cudaFree(p);
+        delete m;
+        return e == cudaErrorMemoryAllocation ? SF_ERR_OOM : SF_ERR_CUDA;
+    }
+    *out = m;
+    return SF_OK;
+}
+
+sf_status sf_mlp_destroy(sf_mlp_handle m) {
+    if (!m) return SF_OK;
+    cudaStreamSynchronize(m->stream);
+    for (void* p : m->allocs) cudaFree(p);
+    delete m;
+    return SF_OK;
+}
+
+const char* sf_mlp_last_error(sf_mlp_handle m) { return m ? m->err.c_str() : ""; }
+
+sf_status sf_mlp_set_layer(sf_mlp_handle m, int layer, const float* h_w, const float* h_b) {
+    if (!m || layer < 0 || layer >= m->L || !h_w || !h_b) return SF_ERR_INVALID_ARG;
+    const int o = m->dim[layer + 1], i = m->dim[layer];
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(m->w[layer], h_w, (size_t)o * i * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->b[layer], h_b, (size_t)o * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        weights_to_bf16_kernel<<<grid1((size_t)o * i), 256, 0, m->stream>>>(m->w[layer], o, i, m->ld[layer],
+                                                                            m->ld[layer + 1], m->wb[layer],
+                                                                            m->wbt[layer]);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, cudaGetErrorString(e));
+}
+
+sf_status sf_mlp_get_layer(sf_mlp_handle m, int layer, float* h_w, float* h_b, float* h_gw, float* h_gb) {
+    if (!m || layer < 0 || layer >= m->L) return SF_ERR_INVALID_ARG;
+    const int o = m->dim[layer + 1], i = m->dim[layer];
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e == cudaSuccess && h_w) e = cudaMemcpy(h_w, m->w[layer], (size_t)o * i * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h_b) e = cudaMemcpy(h_b, m->b[layer], (size_t)o * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h_gw) e = cudaMemcpy(h_gw, m->gw[layer], (size_t)o * i * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h_gb) e = cudaMemcpy(h_gb, m->gb[layer], (size_t)o * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, cudaGetErrorString(e));
+}
+
+sf_status sf_mlp_forward(sf_mlp_handle m, const float* d_x, int ldx, int batch, float* d_y, int ldy) {
+    if (!m || !d_x || !d_y || batch < 0 || ldx < m->dim[0] || ldy < m->dim[m->L]) return SF_ERR_INVALID_ARG;
+    if (batch == 0) return SF_OK;
+    cudaError_t e = ensure_batch(m, batch);
+    if (e != cudaSuccess) return mfail(m, e == cudaErrorMemoryAllocation ? SF_ERR_OOM : SF_ERR_CUDA, "batch buffers");
+    to_bf16_kernel<<<grid1((size_t)batch * m->ld[0]), 256, 0, m->stream>>>(d_x, batch, m->dim[0], ldx, m->x[0],
+                                                                           m->ld[0], nullptr);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = forward_core(m, batch, false);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(d_y, (size_t)ldy * 4, m->y, (size_t)m->ld[m->L] * 4, (size_t)m->dim[m->L] * 4, batch,
+                              cudaMemcpyDeviceToDevice, m->stream);
+    return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("sf_mlp_forward: ") + cudaGetErrorString(e));
+}
+
+sf_status sf_mlp_train_step(sf_mlp_handle m, const float* d_x, const float* d_t, int batch, float lr, int update,
+                            float* h_loss) {
+    if (!m || !d_x || !d_t || batch < 8 || batch % 8 != 0) return SF_ERR_INVALID_ARG;
+    cudaError_t e = ensure_batch(m, batch);
+    if (e != cudaSuccess) return mfail(m, SF_ERR_OOM, "batch buffers");
+    const int L = m->L, B = batch;
+    to_bf16_kernel<<<grid1((size_t)B * m->ld[0]), 256, 0, m->stream>>>(d_x, B, m->dim[0], m->dim[0], m->x[0], m->ld[0],
+                                                                       m->xt[0]);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = forward_core(m, B, true);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->loss, 0, 4, m->stream);
+    if (e == cudaSuccess) {
+        mse_grad_kernel<<<grid1((size_t)B * m->ld[L]), 256, 0, m->stream>>>(m->y, d_t, B, m->dim[L], m->ld[L],
+                                                                            m->dim[L], m->dA, m->loss);
+        e = cudaGetLastError();
+    }
+    for (int l = L - 1; l >= 0 && e == cudaSuccess; --l) {
+        const int o = m->dim[l + 1], lo = m->ld[l + 1], li = m->ld[l], i = m->dim[l];
+        act_back_kernel<<<grid1((size_t)B * lo), 256, 0, m->stream>>>(m->dA, m->z[l], B, o, lo, act_of(m, l), m->dz,
+                                                                      m->dzt);
+        e = cudaGetLastError();
+        // dW = dZ^T X  ([o, B] x [li, B]^T), padded gradient then compacted
+        if (e == cudaSuccess)
+            e = gemm(m, m->dzt, m->xt[l], nullptr, o, li, li, B, SF_ACT_NONE, nullptr, m->gwfull, nullptr, nullptr,
+                     li, 0);
+        if (e == cudaSuccess) {
+            compact_kernel<<<grid1((size_t)o * i), 256, 0, m->stream>>>(m->gwfull, o, i, li, m->gw[l]);
+            bias_grad_kernel<<<(o + 7) / 8, 256, 0, m->stream>>>(m->dzt, B, o, m->gb[l]);
+            e = cudaGetLastError();
+        }
+        // dX = dZ W ([B, lo] x [li, lo]^T) -> the next (lower) layer's dA
+        if (e == cudaSuccess && l > 0)
+            e = gemm(m, m->dz, m->wbt[l], nullptr, B, li, li, lo, SF_ACT_NONE, nullptr, m->dA, nullptr, nullptr, li,
+                     0);
+    }
+    if (e == cudaSuccess && update) {
+        ++m->adam_t;
+        const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+        const float c1 = 1.f - std::pow(b1, (float)m->adam_t), c2 = 1.f - std::pow(b2, (float)m->adam_t);
+        for (int l = 0; l < L && e == cudaSuccess; ++l) {
+            const int o = m->dim[l + 1], i = m->dim[l];
+            adam_kernel<<<grid1((size_t)o * i), 256, 0, m->stream>>>(m->w[l], m->gw[l], m->mw[l], m->vw[l], o * i, lr,
+                                                                     b1, b2, eps, c1, c2, o, i, m->ld[l],
+                                                                     m->ld[l + 1], m->wb[l], m->wbt[l]);
+            adam_kernel<<<grid1(o), 256, 0, m->stream>>>(m->b[l], m->gb[l], m->mb[l], m->vb[l], o, lr, b1, b2, eps, c1,
+                                                         c2, 0, 1, 0, 0, nullptr, nullptr);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess && h_loss) {
+        e = cudaMemcpyAsync(h_loss, m->loss, 4, cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    }
+    return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("sf_mlp_train_step: ") + cudaGetErrorString(e));
+}
+
+sf_status sf_mlp_sync(sf_mlp_handle m) {
+    if (!m) return SF_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return mfail(m, SF_ERR_CUDA, cudaGetErrorString(e));
+    unsigned w = 0;
+    e = cudaMemcpy(&w, m->errw, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return mfail(m, SF_ERR_CUDA, cudaGetErrorString(e));
+    if (w & SF_GEMM_TIMEOUT) {
+        cudaMemset(m->errw, 0, 4);
+        return mfail(m, SF_ERR_TIMEOUT, "a tensor-core GEMM gave up waiting for its operands");
+    }
+    return SF_OK;
+}
+
+sf_status sf_gemm_bf16(const void* d_a, const void* d_b, const float* d_bias, int M, int N, int K, int act,
+                       float* d_out_f32, void* d_out_bf16, void* d_out_bf16_t, int ldc, int ldt, int tile_n,
+                       unsigned* d_err, void* cuda_stream) {
+    if (!d_a || !d_b || M < 0 || N < 0 || K <= 0 || K % 8 != 0 || act < 0 || act > 3) return SF_ERR_INVALID_ARG;
+    if (tile_n != 64 && tile_n != 128 && tile_n != 256) return SF_ERR_INVALID_ARG;
+    if (ldc < N && (d_out_f32 || d_out_bf16)) return SF_ERR_INVALID_ARG;
+    if (ldt < M && d_out_bf16_t) return SF_ERR_INVALID_ARG;
+    GemmArgs g{};
+    g.A = static_cast<const __nv_bfloat16*>(d_a);
+    g.B = static_cast<const __nv_bfloat16*>(d_b);
+    g.bias = d_bias;
+    g.out_f32 = d_out_f32;
+    g.out_bf16 = static_cast<__nv_bfloat16*>(d_out_bf16);
+    g.out_bf16_t = static_cast<__nv_bfloat16*>(d_out_bf16_t);
+    g.M = M; g.N = N; g.Nb = N; g.K = K; g.ldc = ldc; g.ldt = ldt; g.act = act; g.bn = tile_n; g.err = d_err;
+    cudaError_t e = sf_gemm_launch(g, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? SF_OK : (e == cudaErrorInvalidValue ? SF_ERR_INVALID_ARG : SF_ERR_CUDA);
+}
+
+}  // extern "C"

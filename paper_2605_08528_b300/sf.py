@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "SF_OK", 1: "SF_ERR_INVALID_ARG", 2: "SF_ERR_CUDA", 3: "SF_ER
                 5: "SF_ERR_TIMEOUT", 6: "SF_ERR_STATE"}
 NF, NI, OBS_DIM, K_AGENTS, L_POINTS = 25, 6, 320, 8, 32
 FLAG_INVINCIBLE, FLAG_AUTO_RESET, FLAG_RECORD_INDICES = 1, 2, 4
+ACT_NONE, ACT_ELU, ACT_SILU, ACT_TANH = 0, 1, 2, 3
 
 
 class SFError(RuntimeError):
@@ -69,6 +70,13 @@ def lib():
             "sf_save_state": ([vp, C.c_char_p], i32), "sf_load_state": ([vp, C.c_char_p], i32),
             "sf_sync": ([vp], i32), "sf_autotune": ([vp, vp, f32, C.c_int, C.c_int, vp, vp], i32), "sf_num_agents": ([vp], i32), "sf_num_worlds": ([vp], i32),
             "sf_last_error": ([vp], C.c_char_p), "sf_version": ([], C.c_char_p),
+            "sf_mlp_create": ([C.c_int, vp, C.c_int, C.c_int, vp, vp], i32), "sf_mlp_destroy": ([vp], i32),
+            "sf_mlp_last_error": ([vp], C.c_char_p), "sf_mlp_set_layer": ([vp, C.c_int, vp, vp], i32),
+            "sf_mlp_get_layer": ([vp, C.c_int, vp, vp, vp, vp], i32),
+            "sf_mlp_forward": ([vp, vp, C.c_int, C.c_int, vp, C.c_int], i32),
+            "sf_mlp_train_step": ([vp, vp, vp, C.c_int, f32, C.c_int, vp], i32), "sf_mlp_sync": ([vp], i32),
+            "sf_gemm_bf16": ([vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int, C.c_int,
+                              C.c_int, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -239,3 +247,66 @@ class World:
         sf_sync(self.h, allow=(SF_ERR_NONFINITE,))
         return dict(lane_seg=lane.cpu().numpy(), knn_pts=pts.cpu().numpy(), knn_agents=nbr.cpu().numpy(),
                     drac=drac.cpu().numpy())
+
+
+# --------------------------------------------------------------------------- MLPs
+def _mcheck(status, m):
+    if status != SF_OK:
+        raise SFError(status, lib().sf_mlp_last_error(m).decode() if m else "")
+    return status
+
+
+def sf_mlp_create(dims, hidden_act, out_act, stream=None):
+    d = (C.c_int32 * len(dims))(*dims)
+    h = C.c_void_p()
+    st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _mcheck(lib().sf_mlp_create(len(dims) - 1, d, int(hidden_act), int(out_act), C.c_void_p(st), C.byref(h)), None)
+    return h
+
+
+def sf_mlp_destroy(m):
+    _mcheck(lib().sf_mlp_destroy(m), None)
+
+
+def sf_mlp_set_layer(m, layer, w, b):
+    w = np.ascontiguousarray(w, np.float32)
+    b = np.ascontiguousarray(b, np.float32)
+    _mcheck(lib().sf_mlp_set_layer(m, int(layer), _ptr(w), _ptr(b)), m)
+
+
+def sf_mlp_get_layer(m, layer, out_dim, in_dim):
+    w = np.zeros((out_dim, in_dim), np.float32)
+    b = np.zeros(out_dim, np.float32)
+    gw = np.zeros((out_dim, in_dim), np.float32)
+    gb = np.zeros(out_dim, np.float32)
+    _mcheck(lib().sf_mlp_get_layer(m, int(layer), _ptr(w), _ptr(b), _ptr(gw), _ptr(gb)), m)
+    return w, b, gw, gb
+
+
+def sf_mlp_forward(m, d_x, batch, d_y, ldx=None, ldy=None):
+    ldx = d_x.shape[-1] if ldx is None else ldx
+    ldy = d_y.shape[-1] if ldy is None else ldy
+    _mcheck(lib().sf_mlp_forward(m, _ptr(d_x), int(ldx), int(batch), _ptr(d_y), int(ldy)), m)
+
+
+def sf_mlp_train_step(m, d_x, d_t, batch, lr, update=True, want_loss=True):
+    loss = np.zeros(1, np.float32)
+    _mcheck(lib().sf_mlp_train_step(m, _ptr(d_x), _ptr(d_t), int(batch), float(lr), int(bool(update)),
+                                    _ptr(loss) if want_loss else None), m)
+    return float(loss[0])
+
+
+def sf_mlp_sync(m):
+    return _mcheck(lib().sf_mlp_sync(m), m)
+
+
+def sf_gemm_bf16(d_a, d_b, d_bias, M, N, K, act=ACT_NONE, d_out_f32=None, d_out_bf16=None, d_out_bf16_t=None,
+                 ldc=None, ldt=None, tile_n=128, d_err=None, stream=None):
+    ldc = N if ldc is None else ldc
+    ldt = M if ldt is None else ldt
+    st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    s = lib().sf_gemm_bf16(_ptr(d_a), _ptr(d_b), _ptr(d_bias), int(M), int(N), int(K), int(act), _ptr(d_out_f32),
+                           _ptr(d_out_bf16), _ptr(d_out_bf16_t), int(ldc), int(ldt), int(tile_n), _ptr(d_err),
+                           C.c_void_p(st))
+    if s != SF_OK:
+        raise SFError(s, "sf_gemm_bf16")
