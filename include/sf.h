@@ -267,6 +267,29 @@ sf_status sf_mlp_forward(sf_mlp_handle m, const float* d_x, int ldx, int batch, 
 sf_status sf_mlp_train_step(sf_mlp_handle m, const float* d_x, const float* d_t, int batch, float lr, int update,
                             float* h_loss);
 
+/* Inference without allocation, for callers that must not allocate device
+ * memory once they run: code inside a captured or replayed CUDA graph whose
+ * memory is fixed, callers under a device-memory budget that is already
+ * spent, or hosts whose allocator is owned by someone else (the allocating
+ * sf_mlp_forward grows its batch buffers with cudaMalloc on first use of a
+ * larger batch).  The paper has no counterpart; this is a library service.
+ *
+ * Same result as sf_mlp_forward, but the bf16 layer inputs and the fp32
+ * output live in one fixed 4 MiB device array compiled into this library
+ * (sf_mlp_static_scratch_bytes() returns the size), so the call performs no
+ * cudaMalloc, cudaFree or other allocation.  The array occupies 4 MiB on
+ * every GPU that loads the library until the process exits.  A batch needs
+ * batch * (2 * sum of the padded input widths of the layers + 4 * padded
+ * output width) bytes (each part rounded up to 256 B); larger batches are
+ * rejected with SF_ERR_INVALID_ARG and a message giving both sizes.  The
+ * first call on a device looks the array's address up (cudaGetSymbolAddress)
+ * and must therefore come before any stream capture on that device.  Every
+ * call clears and reuses the same array: calls that overlap on the GPU (on
+ * different streams, or from different MLP handles) race and corrupt each
+ * other's results; serialise them.  Asynchronous on the MLP's stream. */
+sf_status sf_mlp_forward_static(sf_mlp_handle m, const float* d_x, int ldx, int batch, float* d_y, int ldy);
+size_t sf_mlp_static_scratch_bytes(void);
+
 /* Wait for the MLP's stream; SF_ERR_TIMEOUT if a GEMM's bounded wait gave up. */
 sf_status sf_mlp_sync(sf_mlp_handle m);
 

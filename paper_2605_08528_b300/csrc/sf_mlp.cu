@@ -16,6 +16,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -234,7 +235,86 @@ cudaError_t forward_core(sf_mlp* m, int B, bool train) {
 
 }  // namespace
 
+// ---------------------------------------------------------------- static scratch
+// Scratch of sf_mlp_forward_static: a fixed device array in this library's
+// image (every GPU that loads the library holds it until the process exits).
+constexpr size_t kStaticScratchBytes = (size_t)4 << 20;
+static __device__ __align__(256) unsigned char g_mlp_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+// device address of the static scratch on the current device, looked up once per device
+cudaError_t static_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_mlp_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// bytes of static scratch one forward of `batch` rows needs
+size_t static_need(const sf_mlp* m, int batch) {
+    size_t n = 0;
+    for (int l = 0; l < m->L; ++l) n += round256((size_t)batch * m->ld[l] * 2);
+    return n + round256((size_t)batch * m->ld[m->L] * 4);
+}
+
+}  // namespace
+
 extern "C" {
+
+sf_status sf_mlp_forward_static(sf_mlp_handle m, const float* d_x, int ldx, int batch, float* d_y, int ldy) {
+    if (!m || !d_x || !d_y || batch < 0 || ldx < m->dim[0] || ldy < m->dim[m->L]) return SF_ERR_INVALID_ARG;
+    if (batch == 0) return SF_OK;
+    const size_t need = static_need(m, batch);
+    if (need > kStaticScratchBytes)
+        return mfail(m, SF_ERR_INVALID_ARG,
+                     "sf_mlp_forward_static: batch " + std::to_string(batch) + " needs " + std::to_string(need) +
+                         " bytes of scratch; the static scratch holds " + std::to_string(kStaticScratchBytes));
+    void* base = nullptr;
+    cudaError_t e = static_scratch(&base);
+    if (e != cudaSuccess) return mfail(m, SF_ERR_CUDA, std::string("static scratch: ") + cudaGetErrorString(e));
+    // carve: bf16 input of every layer, then the fp32 output; zero it (padding columns must read as 0)
+    unsigned char* p = static_cast<unsigned char*>(base);
+    __nv_bfloat16* xs[kMaxLayers] = {};
+    for (int l = 0; l < m->L; ++l) {
+        xs[l] = reinterpret_cast<__nv_bfloat16*>(p);
+        p += round256((size_t)batch * m->ld[l] * 2);
+    }
+    float* y = reinterpret_cast<float*>(p);
+    e = cudaMemsetAsync(base, 0, need, m->stream);
+    if (e == cudaSuccess) {
+        to_bf16_kernel<<<grid1((size_t)batch * m->ld[0]), 256, 0, m->stream>>>(d_x, batch, m->dim[0], ldx, xs[0],
+                                                                               m->ld[0], nullptr);
+        e = cudaGetLastError();
+    }
+    for (int l = 0; l < m->L && e == cudaSuccess; ++l) {
+        const bool last = l == m->L - 1;
+        e = gemm(m, xs[l], m->wb[l], m->b[l], batch, m->dim[l + 1], m->dim[l + 1], m->ld[l], act_of(m, l), nullptr,
+                 last ? y : nullptr, last ? nullptr : xs[l + 1], nullptr, m->ld[l + 1], batch);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(d_y, (size_t)ldy * 4, y, (size_t)m->ld[m->L] * 4, (size_t)m->dim[m->L] * 4, batch,
+                              cudaMemcpyDeviceToDevice, m->stream);
+    return e == cudaSuccess ? SF_OK
+                            : mfail(m, SF_ERR_CUDA, std::string("sf_mlp_forward_static: ") + cudaGetErrorString(e));
+}
+
+size_t sf_mlp_static_scratch_bytes(void) { return kStaticScratchBytes; }
 
 sf_status sf_mlp_create(int num_layers, const int32_t* dims, int hidden_act, int out_act, void* cuda_stream,
                         sf_mlp_handle* out) {

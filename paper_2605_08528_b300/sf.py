@@ -75,6 +75,8 @@ def lib():
             "sf_mlp_get_layer": ([vp, C.c_int, vp, vp, vp, vp], i32),
             "sf_mlp_forward": ([vp, vp, C.c_int, C.c_int, vp, C.c_int], i32),
             "sf_mlp_train_step": ([vp, vp, vp, C.c_int, f32, C.c_int, vp], i32), "sf_mlp_sync": ([vp], i32),
+            "sf_mlp_forward_static": ([vp, vp, C.c_int, C.c_int, vp, C.c_int], i32),
+            "sf_mlp_static_scratch_bytes": ([], C.c_size_t),
             "sf_gemm_bf16": ([vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int, C.c_int,
                               C.c_int, vp, vp], i32),
         }
@@ -287,6 +289,17 @@ def sf_mlp_forward(m, d_x, batch, d_y, ldx=None, ldy=None):
     ldx = d_x.shape[-1] if ldx is None else ldx
     ldy = d_y.shape[-1] if ldy is None else ldy
     _mcheck(lib().sf_mlp_forward(m, _ptr(d_x), int(ldx), int(batch), _ptr(d_y), int(ldy)), m)
+
+
+def sf_mlp_forward_static(m, d_x, batch, d_y, ldx=None, ldy=None):
+    """sf_mlp_forward without any device allocation (fixed 4 MiB scratch inside the library)."""
+    ldx = d_x.shape[-1] if ldx is None else ldx
+    ldy = d_y.shape[-1] if ldy is None else ldy
+    _mcheck(lib().sf_mlp_forward_static(m, _ptr(d_x), int(ldx), int(batch), _ptr(d_y), int(ldy)), m)
+
+
+def sf_mlp_static_scratch_bytes() -> int:
+    return int(lib().sf_mlp_static_scratch_bytes())
 
 
 def sf_mlp_train_step(m, d_x, d_t, batch, lr, update=True, want_loss=True):
