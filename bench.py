@@ -116,30 +116,37 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- our arm
-def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0):
+def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, policy_seed=None):
+    """Time `steps` replays of the captured step graph (policy forward + step
+    when policy_seed is given) on the workload `name`."""
     scene = make_scene(name, rank)
     W = sf.World(scene, seed=4242 + rank, flags=sf.FLAG_AUTO_RESET, warps_per_block=nw, stream=stream)
     A = W.A
     dev = torch.device("cuda")
+    policy = sf.init_policy(seed=policy_seed, stream=stream) if policy_seed is not None else None
     with torch.cuda.stream(stream):
         sf.sf_reset(W.h, torch.ones(A, dtype=torch.uint8, device=dev))
         ring = 64
         acts_h = synth.ou_actions(A, ring, seed=11 + rank)
         acts = torch.as_tensor(acts_h, device=dev)
+        act_cur = torch.zeros((A, 3), dtype=torch.float32, device=dev)
         flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
         tuned = None
         if nw == 0:                                       # setup: pick the launch shape (state restored)
             tuned = sf.sf_autotune(W.h, acts[0], iters=10)
+        graph = sf.sf_graph_capture(W.h, policy=policy, d_actions=act_cur)
         for t in range(warmup):
-            sf.sf_step(W.h, acts[t % ring])
+            act_cur.copy_(acts[t % ring])
+            sf.sf_graph_launch(graph)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for t in range(steps):
+            act_cur.copy_(acts[(warmup + t) % ring])      # stage this step's actions (untimed)
             flush.fill_(float(t))                         # evict the working set from L2
             starts[t].record(stream)
-            sf.sf_step(W.h, acts[(warmup + t) % ring])
+            sf.sf_graph_launch(graph)
             ends[t].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -147,11 +154,14 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0):
     ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
     F, I, _ = sf.sf_get_state(W.h)
     alive = int(((I[:, 4] & 1) != 0).sum())
-
+    peak_drac = float(F[(I[:, 4] & 1) != 0, 24].mean()) if alive else 0.0
+    sf.sf_graph_destroy(graph)
+    if policy is not None:
+        sf.sf_mlp_destroy(policy)
     if not e2e:
         W.close()
         return dict(scene=scene, A=A, alive=alive, ms=ms, wall=wall, status=st, e2e_wall=float("nan"),
-                    e2e_steps=1, h2d=A * 12, d2h=A * 5, tuned=tuned)
+                    e2e_steps=1, h2d=A * 12, d2h=A * 5, tuned=tuned, peak_drac=peak_drac)
     # end to end through the C-ABI: pinned host actions in, host rewards/done out, every step
     acts_pin = torch.as_tensor(acts_h).pin_memory()
     act_dev = torch.empty((A, 3), dtype=torch.float32, device=dev)
@@ -174,7 +184,7 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0):
         e2e_wall = time.perf_counter() - t0
     W.close()
     return dict(scene=scene, A=A, alive=alive, ms=ms, wall=wall, status=st, e2e_wall=e2e_wall,
-                e2e_steps=e2e_steps, h2d=A * 12, d2h=A * 5, tuned=tuned)
+                e2e_steps=e2e_steps, h2d=A * 12, d2h=A * 5, tuned=tuned, peak_drac=peak_drac)
 
 
 def cpu_baseline(name, seconds=12.0):
@@ -223,6 +233,11 @@ def main_ours(args):
         torch.cuda.synchronize()
         res[name] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream, e2e=not args.skip_e2e,
                                  nw=args.nw)
+    if not args.only and not args.skip_policy:
+        if world > 1:
+            dist.barrier()
+        res["4096x16+policy"] = run_workload("4096x16", args.steps, args.warmup, rank, torch, sf, stream, e2e=False,
+                                             nw=args.nw, policy_seed=4000)
     clk = clocks.stop()
     if args.only:          # profiling run: one workload, no report line
         if rank == 0:
@@ -246,9 +261,10 @@ def main_ours(args):
         ach = ab["total"] / mean_s / 1e9
         return dict(casps=casps, e2e=e2e_casps, ms=float(r["ms"].mean()), p50=float(np.percentile(r["ms"], 50)),
                     p99=float(np.percentile(r["ms"], 99)), bytes=ab, achieved=ach, A=r["A"], alive=r["alive"],
-                    h2d=r["h2d"], d2h=r["d2h"], tuned=r["tuned"])
+                    h2d=r["h2d"], d2h=r["d2h"], tuned=r["tuned"], peak_drac=r["peak_drac"])
 
     a256, a4096 = agg("256x16"), agg("4096x16")
+    apol = agg("4096x16+policy") if "4096x16+policy" in res else None
     if rank == 0:
         base = cpu_baseline("256x16") if (world == 1 and not args.skip_cpu) else None
         traffic = load_traffic()
@@ -266,6 +282,7 @@ def main_ours(args):
             "e2e": {"value": a256["e2e"], "unit": "CASPS", "h2d_bytes_per_step": a256["h2d"],
                     "d2h_bytes_per_step": a256["d2h"]},
             "gpu_launches": args.steps,
+            "graph": "each timed step is one CUDA-graph replay",
             "roofline": {"bound": "hbm", "kernel": "world_kernel<step>", "achieved": a256["achieved"],
                          "peak": peak, "unit": "GB/s", "frac": a256["achieved"] / peak,
                          "peak_source": peak_kind, "algorithmic_bytes_per_launch": a256["bytes"]["total"],
@@ -279,7 +296,12 @@ def main_ours(args):
                                            "unit": "GB/s", "frac": a4096["achieved"] / peak,
                                            "algorithmic_bytes_per_launch": a4096["bytes"]["total"],
                                            "traffic": traffic.get("4096x16")},
-                              "policy": "not in this line (plain physics step)"},
+                              "mean_peak_drac": a4096["peak_drac"]},
+            "scale_4096x16_policy": None if apol is None else {
+                "value": apol["casps"], "unit": "CASPS", "ms_per_step": apol["ms"], "p50_ms": apol["p50"],
+                "p99_ms": apol["p99"], "mean_peak_drac": apol["peak_drac"],
+                "graph": "BF16 tcgen05 policy 320-512-512-3 (ELU, tanh; seeded random weights) + world step",
+                "wet_mix": "50% heavy-rain asphalt mu 0.5, 50% dry asphalt mu 0.9"},
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                        "samples": clk["samples"]},
             "paper_context": "19,250 CASPS at 256x16 on an RTX PRO 6000 (Isaac Sim/PhysX + PPO), context only",
@@ -343,7 +365,8 @@ def main():
     ap.add_argument("--only", default=None, choices=list(WORKLOADS), help="profiling: run one workload only")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling: no end-to-end leg")
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
-    ap.add_argument("--nw", type=int, default=0, help="warps per world (1, 2, 4, 8; 0 = library default)")
+    ap.add_argument("--nw", type=int, default=0, help="warps per world (1, 2, 4, 8; 0 = autotuned)")
+    ap.add_argument("--skip-policy", action="store_true", help="no 4096x16 + policy leg")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -303,6 +303,30 @@ sf_status sf_gemm_bf16(const void* d_a, const void* d_b, const float* d_bias, in
                        float* d_out_f32, void* d_out_bf16, void* d_out_bf16_t, int ldc, int ldt, int tile_n,
                        unsigned* d_err, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Policy in the loop and the captured step graph.
+ * ---------------------------------------------------------------------- */
+/* One control step with actions from a policy MLP (320 inputs, 3 outputs,
+ * e.g. 320->512->512->3 with tanh outputs): the policy reads the library's
+ * current observations, writes a library-owned [A][3] action buffer, and the
+ * step runs on them (the paper's loop of Alg. 1: observe, act, simulate).
+ * Both run on the handle's stream.  Asynchronous. */
+sf_status sf_step_policy(sf_handle h, sf_mlp_handle policy, float dt, int substeps);
+
+/* Capture a whole control step into a CUDA graph on the handle's stream
+ * (which must not be the legacy default stream): [policy forward if policy
+ * != NULL] -> sf_step (actions from the policy, else from d_actions, whose
+ * contents may change between launches) -> [sf_reset(d_reset_mask) if not
+ * NULL].  The policy's buffers are allocated before the capture.  Replays
+ * with sf_graph_launch run every kernel of the step with one launch call;
+ * the handle's state evolves as with the individual calls.
+ * Errors: SF_ERR_STATE, SF_ERR_INVALID_ARG, SF_ERR_OOM, SF_ERR_CUDA. */
+typedef struct sf_graph* sf_graph_handle;
+sf_status sf_graph_capture(sf_handle h, sf_mlp_handle policy, const float* d_actions, const uint8_t* d_reset_mask,
+                           float dt, int substeps, sf_graph_handle* out);
+sf_status sf_graph_launch(sf_graph_handle g);
+sf_status sf_graph_destroy(sf_graph_handle g);
+
 /* Number of agents and worlds of the loaded roads (0 before sf_load_roads). */
 int32_t sf_num_agents(sf_handle h);
 int32_t sf_num_worlds(sf_handle h);

@@ -14,6 +14,7 @@
 
 #include "../../include/sf.h"
 #include "sf_internal.cuh"
+#include "sf_mlp_internal.cuh"
 
 namespace {
 
@@ -38,7 +39,15 @@ struct sf_ctx {
     DevOutputs out{};
     float* place_buf = nullptr;
     uint8_t* all_mask = nullptr;
+    float* act_buf = nullptr;   // [A][3] actions written by an attached policy
     bool loaded = false;
+};
+
+struct sf_graph {
+    sf_ctx* h = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;           // kernels per replay
 };
 
 namespace {
@@ -79,6 +88,7 @@ void free_all(sf_ctx* h) {
     h->out = DevOutputs{};
     h->place_buf = nullptr;
     h->all_mask = nullptr;
+    h->act_buf = nullptr;
     h->loaded = false;
     h->W = h->A = h->NP = 0;
 }
@@ -325,6 +335,7 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     h->out = DevOutputs{obs, reward, done, events, lane_seg, knn_pts, knn_agents, drac, err_word, hint};
     SF_ALLOC(h->place_buf, float, Aa * 6);
     SF_ALLOC(h->all_mask, uint8_t, Aa);
+    SF_ALLOC(h->act_buf, float, Aa * 3);
 #undef SF_ALLOC
 
     std::vector<uint32_t> meta_h(Aa);
@@ -649,6 +660,75 @@ sf_status sf_load_state(sf_handle h, const char* path) {
     std::fclose(fp);
     if (!ok) return fail(h, SF_ERR_INVALID_ARG, "sf_load_state: bad or mismatched checkpoint");
     return sf_set_state(h, f.data(), i.data());
+}
+
+sf_status sf_step_policy(sf_handle h, sf_mlp_handle policy, float dt, int substeps) {
+    if (!h || !policy) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_step_policy: no roads loaded");
+    sf_status s = sf_mlp_forward_on(policy, h->stream, h->out.obs, SF_OBS_DIM, h->A, h->act_buf, 3);
+    if (s != SF_OK) return fail(h, s, std::string("sf_step_policy: ") + sf_mlp_last_error(policy));
+    return sf_step(h, h->act_buf, dt, substeps);
+}
+
+sf_status sf_graph_capture(sf_handle h, sf_mlp_handle policy, const float* d_actions, const uint8_t* d_reset_mask,
+                           float dt, int substeps, sf_graph_handle* out) {
+    if (!h || !out) return SF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_graph_capture: no roads loaded");
+    if (!policy && !d_actions) return fail(h, SF_ERR_INVALID_ARG, "sf_graph_capture: no actions and no policy");
+    if (!h->stream) return fail(h, SF_ERR_INVALID_ARG, "sf_graph_capture: needs a non-default stream");
+    if (policy && sf_mlp_reserve(policy, h->A) != SF_OK)
+        return fail(h, SF_ERR_OOM, "sf_graph_capture: policy buffers");
+    if (policy) {   // one uncaptured pass: first-use work (kernel attributes) happens outside the capture
+        sf_status s0 = sf_mlp_forward_on(policy, h->stream, h->out.obs, SF_OBS_DIM, h->A, h->act_buf, 3);
+        if (s0 != SF_OK) return fail(h, s0, "sf_graph_capture: policy forward");
+    }
+    SF_CUDA(h, cudaStreamSynchronize(h->stream));
+    sf_graph* g = new sf_graph();
+    g->h = h;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    sf_status st = SF_OK;
+    if (e == cudaSuccess) {
+        if (policy) {
+            st = sf_mlp_forward_on(policy, h->stream, h->out.obs, SF_OBS_DIM, h->A, h->act_buf, 3);
+            g->launches += 1;
+        }
+        if (st == SF_OK) st = sf_step(h, policy ? h->act_buf : d_actions, dt, substeps);
+        g->launches += 1;
+        if (st == SF_OK && d_reset_mask) { st = sf_reset(h, d_reset_mask); g->launches += 1; }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+        if (e2 == cudaSuccess && st == SF_OK) {
+            g->graph = graph;
+            e = cudaGraphInstantiate(&g->exec, graph, 0);
+        } else {
+            if (graph) cudaGraphDestroy(graph);
+            e = e2 != cudaSuccess ? e2 : cudaErrorUnknown;
+        }
+    }
+    if (e != cudaSuccess || st != SF_OK) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return st != SF_OK ? st : cuda_fail(h, e, "sf_graph_capture");
+    }
+    *out = g;
+    return SF_OK;
+}
+
+sf_status sf_graph_launch(sf_graph_handle g) {
+    if (!g) return SF_ERR_INVALID_ARG;
+    cudaError_t e = cudaGraphLaunch(g->exec, g->h->stream);
+    return e == cudaSuccess ? SF_OK : cuda_fail(g->h, e, "sf_graph_launch");
+}
+
+sf_status sf_graph_destroy(sf_graph_handle g) {
+    if (!g) return SF_OK;
+    cudaStreamSynchronize(g->h->stream);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return SF_OK;
 }
 
 sf_status sf_sync(sf_handle h) {

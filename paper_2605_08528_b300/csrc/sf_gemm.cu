@@ -8,8 +8,9 @@
 //                  into a STAGES-deep ring (128-byte swizzle);
 //   warp 1 lane 0  issues tcgen05.mma (M 128, N BN, K 16) into a TMEM
 //                  accumulator of BN fp32 columns and commits each stage back;
-//   warps 0-3      read the accumulator with tcgen05.ld (warp w owns rows
-//                  32w..32w+31), add the bias, apply the activation and store.
+//   warps 0-7      read the accumulator with tcgen05.ld (warp w owns rows
+//                  32(w%4)..32(w%4)+31 and every other 32-column chunk), add
+//                  the bias, apply the activation and store.
 // Every mbarrier wait is bounded: on expiry the kernel records SF_GEMM_TIMEOUT
 // in the error word, stops issuing work, frees its TMEM and returns.
 #include <cuda.h>
@@ -22,7 +23,7 @@
 
 namespace {
 
-constexpr int kBM = 128, kBK = 64, kStages = 4, kThreads = 128;
+constexpr int kBM = 128, kBK = 64, kStages = 4, kThreads = 256;   // 8 warps: 2 per TMEM lane slice
 constexpr uint32_t kWaitLimit = 1u << 30;
 constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s
 
@@ -122,12 +123,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float activate(float x, int act) {
-    switch (act) {
-        case SF_ACT_ELU: return x > 0.f ? x : expm1f(x);
-        case SF_ACT_SILU: return x / (1.f + expf(-x));
-        case SF_ACT_TANH: return tanhf(x);
-        default: return x;
+// activations of 32 accumulator values; the exponentials use the hardware
+// exp2-based intrinsic (relative error far below the bf16 output rounding)
+__device__ __forceinline__ void activate32(float (&v)[32], int act) {
+    if (act == SF_ACT_ELU) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = v[i] > 0.f ? v[i] : __expf(v[i]) - 1.f;
+    } else if (act == SF_ACT_SILU) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = __fdividef(v[i], 1.f + __expf(-v[i]));
+    } else if (act == SF_ACT_TANH) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = tanhf(v[i]);
     }
 }
 
@@ -200,25 +207,80 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue: TMEM -> bias + activation -> global
     const bool have = __all_sync(0xFFFFFFFFu, mbar_wait(&S.done, 0, args.err));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int r = m0 + warp * 32 + lane;
+    const int r = m0 + (warp & 3) * 32 + lane;   // TMEM lane slice of this warp
+    // 16-byte vector stores when rows are aligned for them
+    const bool vf = args.ldc % 4 == 0 && ((reinterpret_cast<uintptr_t>(args.out_f32) |
+                                          reinterpret_cast<uintptr_t>(args.pre)) & 15) == 0;
+    const bool vb = args.ldc % 8 == 0 && (reinterpret_cast<uintptr_t>(args.out_bf16) & 15) == 0;
     if (have) {
 #pragma unroll 1
-        for (int c = 0; c < BN / 32; ++c) {
+        for (int c = warp >> 2; c < BN / 32; c += kThreads / 128) {   // the two warp halves split the columns
             float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+            tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(c * 32), v);
             const int nb = n0 + c * 32;
             if (r >= args.M || nb >= args.N) continue;
+            const bool full = nb + 32 <= args.N;
+            if (args.bias) {
+                if (full) {
+                    const float4* b4 = reinterpret_cast<const float4*>(args.bias + nb);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const int n = nb + i;
-                float x = v[i] + ((args.bias && n < args.N) ? args.bias[n] : 0.f);
-                if (args.pre && n < args.N) args.pre[(size_t)r * args.ldc + n] = x;
-                x = activate(x, args.act);
-                if (n < args.N) {
-                    if (args.out_f32) args.out_f32[(size_t)r * args.ldc + n] = x;
-                    if (args.out_bf16) args.out_bf16[(size_t)r * args.ldc + n] = __float2bfloat16_rn(x);
-                    if (args.out_bf16_t) args.out_bf16_t[(size_t)n * args.ldt + r] = __float2bfloat16_rn(x);
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 b = __ldg(b4 + q);
+                        v[4 * q] += b.x; v[4 * q + 1] += b.y; v[4 * q + 2] += b.z; v[4 * q + 3] += b.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (nb + i < args.N) v[i] += args.bias[nb + i];
                 }
+            }
+            const size_t row = (size_t)r * args.ldc + nb;
+            if (args.pre) {
+                if (full && vf) {
+                    float4* p4 = reinterpret_cast<float4*>(args.pre + row);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) p4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (nb + i < args.N) args.pre[row + i] = v[i];
+                }
+            }
+            activate32(v, args.act);
+            if (args.out_f32) {
+                if (full && vf) {
+                    float4* p4 = reinterpret_cast<float4*>(args.out_f32 + row);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) p4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (nb + i < args.N) args.out_f32[row + i] = v[i];
+                }
+            }
+            if (args.out_bf16) {
+                if (full && vb) {
+                    uint4* p4 = reinterpret_cast<uint4*>(args.out_bf16 + row);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * q + 2 * k], v[8 * q + 2 * k + 1]);
+                            w[k] = *reinterpret_cast<const uint32_t*>(&h2);
+                        }
+                        p4[q] = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (nb + i < args.N) args.out_bf16[row + i] = __float2bfloat16_rn(v[i]);
+                }
+            }
+            if (args.out_bf16_t) {   // lanes hold consecutive rows: each column store is contiguous across the warp
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (nb + i < args.N) args.out_bf16_t[(size_t)(nb + i) * args.ldt + r] = __float2bfloat16_rn(v[i]);
             }
         }
     }

@@ -22,6 +22,7 @@
 
 #include "../../include/sf.h"
 #include "sf_gemm.cuh"
+#include "sf_mlp_internal.cuh"
 
 namespace {
 
@@ -42,6 +43,16 @@ __device__ __forceinline__ float act_grad(float z, int act) {
         }
         default: return 1.f;
     }
+}
+
+// x [B, n] f32 -> bf16 [B, ld] with n == ld, ld % 8 == 0 and 16-byte rows: 8 elements per thread
+__global__ void to_bf16_vec8_kernel(const float* __restrict__ x, size_t n8, __nv_bfloat16* __restrict__ y) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n8) return;
+    const float4 a = reinterpret_cast<const float4*>(x)[2 * i], b = reinterpret_cast<const float4*>(x)[2 * i + 1];
+    __nv_bfloat162 h[4] = {__floats2bfloat162_rn(a.x, a.y), __floats2bfloat162_rn(a.z, a.w),
+                           __floats2bfloat162_rn(b.x, b.y), __floats2bfloat162_rn(b.z, b.w)};
+    reinterpret_cast<uint4*>(y)[i] = *reinterpret_cast<const uint4*>(h);
 }
 
 // x [B, n] f32 -> bf16 [B, ld] (zero padded) and optionally bf16^T [ld, B]
@@ -221,14 +232,15 @@ cudaError_t ensure_batch(sf_mlp* m, int B) {
     return e;
 }
 
-// forward of a batch already converted into x[0] (and xt[0] when training)
-cudaError_t forward_core(sf_mlp* m, int B, bool train) {
+// forward of a batch already converted into x[0] (and xt[0] when training); the
+// last layer writes y_out [B][ldy] (m->y with its padded width when null)
+cudaError_t forward_core(sf_mlp* m, int B, bool train, float* y_out = nullptr, int ldy = 0) {
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < m->L && e == cudaSuccess; ++l) {
         const bool last = l == m->L - 1;
         e = gemm(m, m->x[l], m->wb[l], m->b[l], B, m->dim[l + 1], m->dim[l + 1], m->ld[l], act_of(m, l),
-                 train ? m->z[l] : nullptr, last ? m->y : nullptr, last ? nullptr : m->x[l + 1],
-                 (train && !last) ? m->xt[l + 1] : nullptr, m->ld[l + 1], B);
+                 train ? m->z[l] : nullptr, last ? (y_out ? y_out : m->y) : nullptr, last ? nullptr : m->x[l + 1],
+                 (train && !last) ? m->xt[l + 1] : nullptr, (last && y_out) ? ldy : m->ld[l + 1], B);
     }
     return e;
 }
@@ -395,19 +407,40 @@ sf_status sf_mlp_get_layer(sf_mlp_handle m, int layer, float* h_w, float* h_b, f
 }
 
 sf_status sf_mlp_forward(sf_mlp_handle m, const float* d_x, int ldx, int batch, float* d_y, int ldy) {
+    if (!m) return SF_ERR_INVALID_ARG;
+    return sf_mlp_forward_on(m, m->stream, d_x, ldx, batch, d_y, ldy);
+}
+
+}  // extern "C"
+
+sf_status sf_mlp_reserve(sf_mlp_handle m, int batch) {
+    if (!m || batch < 0) return SF_ERR_INVALID_ARG;
+    cudaError_t e = ensure_batch(m, batch);
+    return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_OOM, "batch buffers");
+}
+
+sf_status sf_mlp_forward_on(sf_mlp_handle m, cudaStream_t stream, const float* d_x, int ldx, int batch, float* d_y,
+                            int ldy) {
     if (!m || !d_x || !d_y || batch < 0 || ldx < m->dim[0] || ldy < m->dim[m->L]) return SF_ERR_INVALID_ARG;
     if (batch == 0) return SF_OK;
     cudaError_t e = ensure_batch(m, batch);
     if (e != cudaSuccess) return mfail(m, e == cudaErrorMemoryAllocation ? SF_ERR_OOM : SF_ERR_CUDA, "batch buffers");
-    to_bf16_kernel<<<grid1((size_t)batch * m->ld[0]), 256, 0, m->stream>>>(d_x, batch, m->dim[0], ldx, m->x[0],
-                                                                           m->ld[0], nullptr);
+    cudaStream_t saved = m->stream;
+    m->stream = stream;
+    if (m->dim[0] == m->ld[0] && ldx == m->dim[0] && (reinterpret_cast<uintptr_t>(d_x) & 15) == 0) {
+        const size_t n8 = (size_t)batch * m->ld[0] / 8;
+        to_bf16_vec8_kernel<<<grid1(n8), 256, 0, stream>>>(d_x, n8, m->x[0]);
+    } else {
+        to_bf16_kernel<<<grid1((size_t)batch * m->ld[0]), 256, 0, stream>>>(d_x, batch, m->dim[0], ldx, m->x[0],
+                                                                            m->ld[0], nullptr);
+    }
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = forward_core(m, batch, false);
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(d_y, (size_t)ldy * 4, m->y, (size_t)m->ld[m->L] * 4, (size_t)m->dim[m->L] * 4, batch,
-                              cudaMemcpyDeviceToDevice, m->stream);
+    if (e == cudaSuccess) e = forward_core(m, batch, false, d_y, ldy);
+    m->stream = saved;
     return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("sf_mlp_forward: ") + cudaGetErrorString(e));
 }
+
+extern "C" {
 
 sf_status sf_mlp_train_step(sf_mlp_handle m, const float* d_x, const float* d_t, int batch, float lr, int update,
                             float* h_loss) {

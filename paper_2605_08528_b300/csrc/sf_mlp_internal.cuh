@@ -1,0 +1,11 @@
+// sf_mlp_internal.cuh -- MLP calls on an explicit stream (used by the step graph).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "../../include/sf.h"
+
+// make sure the batch buffers of `batch` rows exist (allocates; not capturable)
+sf_status sf_mlp_reserve(sf_mlp_handle m, int batch);
+// sf_mlp_forward on `stream` instead of the MLP's own stream (no allocation if reserved)
+sf_status sf_mlp_forward_on(sf_mlp_handle m, cudaStream_t stream, const float* d_x, int ldx, int batch, float* d_y,
+                            int ldy);

@@ -79,6 +79,9 @@ def lib():
             "sf_mlp_static_scratch_bytes": ([], C.c_size_t),
             "sf_gemm_bf16": ([vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int, C.c_int,
                               C.c_int, vp, vp], i32),
+            "sf_step_policy": ([vp, vp, f32, C.c_int], i32),
+            "sf_graph_capture": ([vp, vp, vp, vp, f32, C.c_int, vp], i32), "sf_graph_launch": ([vp], i32),
+            "sf_graph_destroy": ([vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -323,3 +326,34 @@ def sf_gemm_bf16(d_a, d_b, d_bias, M, N, K, act=ACT_NONE, d_out_f32=None, d_out_
                            C.c_void_p(st))
     if s != SF_OK:
         raise SFError(s, "sf_gemm_bf16")
+
+
+# --------------------------------------------------------------------------- policy loop and graphs
+def sf_step_policy(h, policy, dt=1.0 / 30.0, substeps=4):
+    _check(lib().sf_step_policy(h, policy, float(dt), int(substeps)), h)
+
+
+def sf_graph_capture(h, policy=None, d_actions=None, d_reset_mask=None, dt=1.0 / 30.0, substeps=4):
+    g = C.c_void_p()
+    _check(lib().sf_graph_capture(h, policy, _ptr(d_actions), _ptr(d_reset_mask), float(dt), int(substeps),
+                                  C.byref(g)), h)
+    return g
+
+
+def sf_graph_launch(g):
+    s = lib().sf_graph_launch(g)
+    if s != SF_OK:
+        raise SFError(s, "sf_graph_launch")
+
+
+def sf_graph_destroy(g):
+    lib().sf_graph_destroy(g)
+
+
+def init_policy(seed=0, dims=(320, 512, 512, 3), stream=None):
+    """A policy MLP with seeded random (untrained) weights: ELU hidden layers, tanh actions."""
+    m = sf_mlp_create(list(dims), ACT_ELU, ACT_TANH, stream)
+    rng = np.random.default_rng(seed)
+    for l, (i, o) in enumerate(zip(dims[:-1], dims[1:])):
+        sf_mlp_set_layer(m, l, rng.normal(0, 1 / np.sqrt(i), (o, i)), np.zeros(o))
+    return m

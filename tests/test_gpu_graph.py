@@ -1,0 +1,73 @@
+"""The policy in the loop and the captured step graph: replaying the graph must
+give bit-identical states to issuing the same calls one by one, and the policy
+step must equal the policy's forward followed by a plain step."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2605_08528_b300 import sf, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def world(sc, stream, seed=5):
+    W = sf.World(sc, seed=seed, flags=sf.FLAG_AUTO_RESET, stream=stream)
+    with torch.cuda.stream(stream):
+        sf.sf_reset(W.h, torch.ones(W.A, dtype=torch.uint8, device="cuda"))
+    return W
+
+
+def test_policy_step_equals_forward_then_step():
+    sc = synth.procedural_scene(8, 16, seed_base=700)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    W1, W2 = world(sc, s1), world(sc, s2)
+    pol = sf.init_policy(seed=3)
+    act = torch.zeros((W1.A, 3), device="cuda")
+    for t in range(10):
+        sf.sf_step_policy(W1.h, pol)
+        obs = W2.outputs()[0]
+        torch.cuda.synchronize()
+        sf.sf_mlp_forward(pol, obs, W2.A, act)
+        sf.sf_mlp_sync(pol)
+        with torch.cuda.stream(s2):
+            sf.sf_step(W2.h, act)
+    F1, I1, _ = sf.sf_get_state(W1.h)
+    F2, I2, _ = sf.sf_get_state(W2.h)
+    assert np.array_equal(F1, F2) and np.array_equal(I1, I2)
+    assert np.abs(act.cpu().numpy()).max() <= 1.0
+    sf.sf_mlp_destroy(pol)
+
+
+@pytest.mark.parametrize("with_policy,with_reset", [(False, False), (True, False), (False, True)])
+def test_graph_replay_matches_individual_calls(with_policy, with_reset):
+    sc = synth.procedural_scene(6, 16, seed_base=800)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    W1, W2 = world(sc, s1), world(sc, s2)
+    pol = sf.init_policy(seed=4) if with_policy else None
+    acts = torch.as_tensor(synth.ou_actions(W1.A, 12, seed=9), device="cuda")
+    masks = torch.as_tensor(np.stack([synth.reset_mask(W1.A, t, 0.2) for t in range(12)]), device="cuda")
+    act_buf = torch.zeros((W1.A, 3), device="cuda")
+    mask = torch.zeros(W1.A, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    g = sf.sf_graph_capture(W1.h, policy=pol, d_actions=act_buf, d_reset_mask=mask if with_reset else None)
+    for t in range(12):
+        m = masks[t]
+        with torch.cuda.stream(s1):
+            act_buf.copy_(acts[t])
+            mask.copy_(m)
+            sf.sf_graph_launch(g)
+        with torch.cuda.stream(s2):
+            if with_policy:
+                sf.sf_step_policy(W2.h, pol)
+            else:
+                sf.sf_step(W2.h, acts[t])
+            if with_reset:
+                sf.sf_reset(W2.h, m)
+    F1, I1, _ = sf.sf_get_state(W1.h)
+    F2, I2, _ = sf.sf_get_state(W2.h)
+    o1, o2 = W1.outputs()[0].cpu().numpy(), W2.outputs()[0].cpu().numpy()
+    assert np.array_equal(F1, F2) and np.array_equal(I1, I2) and np.array_equal(o1, o2)
+    sf.sf_graph_destroy(g)
+    if pol is not None:
+        sf.sf_mlp_destroy(pol)
