@@ -96,7 +96,7 @@ def lib():
         L.or_nearest_lane.restype = i
         L.or_ttc.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.or_ttc.restype = d
-        L.or_drac.argtypes = [vp, vp, vp, vp, vp]
+        L.or_drac.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.or_drac.restype = d
         L.or_lane_keep_q.argtypes = [vp, d, d]
         L.or_lane_keep_q.restype = d
@@ -219,9 +219,9 @@ def ttc(pi, hi, vi, pj, hj, vj, params=None):
     return lib().or_ttc(C.byref(P), *[_p(x) for x in a])
 
 
-def drac(pi, vi, pj, vj, params=None):
+def drac(pi, vi, pj, vj, hi=(1.0, 0.0), hj=(1.0, 0.0), params=None):
     P = params or default_params()
-    a = [np.asarray(x, np.float64) for x in (pi, vi, pj, vj)]
+    a = [np.asarray(x, np.float64) for x in (pi, hi, vi, pj, hj, vj)]
     return lib().or_drac(C.byref(P), *[_p(x) for x in a])
 
 

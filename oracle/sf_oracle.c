@@ -271,13 +271,18 @@ double or_ttc(const or_params* P, const double pi[2], const double hi[2], const 
     return clampd(best, 0.0, P->ttc_max);
 }
 
-double or_drac(const or_params* P, const double pi[2], const double vi[2], const double pj[2],
-               const double vj[2]) {
+double or_drac(const or_params* P, const double pi[2], const double hi[2], const double vi[2], const double pj[2],
+               const double hj[2], const double vj[2]) {
     double rx = pj[0] - pi[0], ry = pj[1] - pi[1];
     double dist = sqrt(rx * rx + ry * ry);
     if (!(dist > 0)) return 0.0;
-    double vr = -((vj[0] - vi[0]) * rx + (vj[1] - vi[1]) * ry) / dist;   /* closing speed */
-    double gap = fmax(dist - 2 * P->half_len, P->drac_gap_floor);       /* (L_i + L_j)/2 */
+    double ux = rx / dist, uy = ry / dist;
+    double vr = -((vj[0] - vi[0]) * ux + (vj[1] - vi[1]) * uy);          /* closing speed */
+    /* R26: the gap is the free distance along the line of centres: each
+     * footprint reaches hl |h.u| + hw |h_perp.u| toward the other */
+    double ei = P->half_len * fabs(hi[0] * ux + hi[1] * uy) + P->half_wid * fabs(-hi[1] * ux + hi[0] * uy);
+    double ej = P->half_len * fabs(hj[0] * ux + hj[1] * uy) + P->half_wid * fabs(-hj[1] * ux + hj[0] * uy);
+    double gap = fmax(dist - ei - ej, P->drac_gap_floor);
     return vr > 0 ? vr * vr / (2 * gap) : 0.0;
 }
 
@@ -675,7 +680,7 @@ static void events_agent(const or_params* P, const or_scene* S, int w, double* F
         double pj[2] = {g[OR_F_PX], g[OR_F_PY]}, vj[2] = {g[OR_F_VX], g[OR_F_VY]};
         double tt = or_ttc(P, p, hd, v, pj, hj, vj);
         if (tt < tmin) tmin = tt;
-        double dr = or_drac(P, p, v, pj, vj);
+        double dr = or_drac(P, p, hd, v, pj, hj, vj);
         if (dr > dmax) dmax = dr;
     }
     if (tmin < P->ttc_max) r -= or_penalty(P->ttc_alpha_v, tmin, P->ttc_floor, P->ttc_pmax_v);

@@ -174,9 +174,9 @@ int or_nearest_lane(const or_params* P, const or_scene* S, int w, const double q
 /* swept three-circle time to collision between two agents (XY), clamped to [0, ttc_max]. */
 double or_ttc(const or_params* P, const double pi[2], const double hi[2], const double vi[2],
               const double pj[2], const double hj[2], const double vj[2]);
-/* DRAC of j relative to i. */
-double or_drac(const or_params* P, const double pi[2], const double vi[2], const double pj[2],
-               const double vj[2]);
+/* DRAC of j relative to i (headings hi, hj set each footprint's reach along the line of centres). */
+double or_drac(const or_params* P, const double pi[2], const double hi[2], const double vi[2], const double pj[2],
+               const double hj[2], const double vj[2]);
 double or_lane_keep_q(const or_params* P, double lateral, double cos_dpsi);
 /* circle geometry of the TTC test for a box of length L, width W, wheelbase WB. */
 void or_ttc_circles(double L, double W, double WB, double* r, double* d);

@@ -334,13 +334,18 @@ __device__ __forceinline__ float ttc_pair(float pix, float piy, float hix, float
     return clampf(best, 0.f, kTtcMax);
 }
 
-__device__ __forceinline__ float drac_pair(float pix, float piy, float vix, float viy, float pjx, float pjy, float vjx,
-                                           float vjy) {
+// DRAC (App. G reading): closing speed^2 / (2 gap), the gap measured along the
+// line of centres between the two footprints' reaches
+__device__ __forceinline__ float drac_pair(float pix, float piy, float hix, float hiy, float vix, float viy, float pjx,
+                                           float pjy, float hjx, float hjy, float vjx, float vjy) {
     float rx = pjx - pix, ry = pjy - piy;
     float dist = sqrtf(rx * rx + ry * ry);
     if (!(dist > 0.f)) return 0.f;
-    float vr = -((vjx - vix) * rx + (vjy - viy) * ry) / dist;
-    float gap = fmaxf(dist - 2.f * kHalfLen, kDracGapFloor);
+    float ux = rx / dist, uy = ry / dist;
+    float vr = -((vjx - vix) * ux + (vjy - viy) * uy);
+    float ei = kHalfLen * fabsf(hix * ux + hiy * uy) + kHalfWid * fabsf(-hiy * ux + hix * uy);
+    float ej = kHalfLen * fabsf(hjx * ux + hjy * uy) + kHalfWid * fabsf(-hjy * ux + hjx * uy);
+    float gap = fmaxf(dist - ei - ej, kDracGapFloor);
     return vr > 0.f ? vr * vr / (2.f * gap) : 0.f;
 }
 
@@ -835,7 +840,8 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
                     tt[t] = ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j], E.vx[j],
                                      E.vy[j]);
                     tmin = fminf(tmin, tt[t]);
-                    dmax = fmaxf(dmax, drac_pair(A.px, A.py, A.vx, A.vy, E.px[j], E.py[j], E.vx[j], E.vy[j]));
+                    dmax = fmaxf(dmax, drac_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j],
+                                                 E.vx[j], E.vy[j]));
                 }
                 if (tmin < kTtcMax) r -= penalty(kTtcAlphaV, tmin, kTtcPmaxV);
                 r -= kWDrac * fmaxf(0.f, dmax - kDracThresh);

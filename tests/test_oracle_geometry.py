@@ -229,12 +229,16 @@ def test_ttc_lateral_offset_closed_form():
 
 
 def test_drac_hand_cases():
-    # closing 10 m/s, gap 10 m (centres 14.5 m apart, two 4.5 m cars) -> 5.0 m/s^2
+    # closing 10 m/s, gap 10 m (centres 14.5 m apart, two 4.5 m cars in line) -> 5.0 m/s^2
     assert abs(O.drac([0, 0], [10, 0], [14.5, 0], [0, 0]) - 5.0) < 1e-12
     assert O.drac([0, 0], [0, 0], [14.5, 0], [10, 0]) == 0.0             # opening
     assert abs(O.drac([0, 0], [2, 0], [4.0, 0], [0, 0]) - 4.0 / 0.2) < 1e-12   # gap floored at 0.1 m
     # only the radial component closes
     assert abs(O.drac([0, 0], [0, 10], [14.5, 0], [0, 0])) < 1e-12
+    # side by side on adjacent lanes (3.6 m apart): the gap is 3.6 - 2 * 0.9 = 1.8 m
+    assert abs(O.drac([0, 0], [0, 1.0], [0, 3.6], [0, 0]) - 1.0 / (2 * 1.8)) < 1e-12
+    # crossing at right angles: 2.25 + 0.9 of reach along the line of centres
+    assert abs(O.drac([0, 0], [5.0, 0], [10.0, 0], [0, 0], hj=(0.0, 1.0)) - 25.0 / (2 * (10 - 3.15))) < 1e-12
 
 
 def test_lane_keep_score_and_penalty():
