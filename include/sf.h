@@ -327,6 +327,58 @@ sf_status sf_graph_capture(sf_handle h, sf_mlp_handle policy, const float* d_act
 sf_status sf_graph_launch(sf_graph_handle g);
 sf_status sf_graph_destroy(sf_graph_handle g);
 
+/* ------------------------------------------------------------------------
+ * Learned dynamics surrogate: a BF16 MLP 30 -> 256 -> 256 -> 256 -> 16
+ * (SiLU) that predicts one control step of the chassis of an agent that is
+ * alone (no other footprint within 4.85 m + 2 m + |dv| dt), on mu >= 0.3, at
+ * most 35 m/s and tilted less than 10 degrees; the physics substeps remain the
+ * fallback for every other agent, and steering keeps its exact PD recurrence.
+ * Inputs (30, heading frame at t): z, tilt quaternion (4), v (3), omega (3),
+ * wheel spins (4), suspension compressions (4) and rates (4), steer angle and
+ * rate, decoded action (3), mu, 0.  Outputs (16): the step's change of
+ * heading-frame position, body rotation vector, heading-frame velocity and
+ * angular velocity (each minus the constant-velocity prediction) and of the
+ * wheel spins, normalised by the training set's mean and deviation.
+ * ---------------------------------------------------------------------- */
+typedef struct sf_surrogate* sf_surrogate_handle;
+
+/* An untrained surrogate (seeded initial weights) on cuda_stream. */
+sf_status sf_surrogate_create(void* cuda_stream, sf_surrogate_handle* out);
+sf_status sf_surrogate_destroy(sf_surrogate_handle s);
+
+/* One plain physics step of h with d_actions, recording a training
+ * transition for every gated agent that stayed alive and neither respawned,
+ * collided nor crashed: raw inputs appended to d_x [cap][30], raw outputs to
+ * d_y [cap][16] at the device counter *d_count (incremented; rows beyond cap
+ * are dropped).  Asynchronous on h's stream. */
+sf_status sf_surrogate_collect(sf_handle h, sf_surrogate_handle s, const float* d_actions, float dt, int substeps,
+                               float* d_x, float* d_y, unsigned long long cap, unsigned long long* d_count);
+
+/* Fit the normalisation to the n collected rows and run `steps` Adam steps
+ * (mean-squared error of the normalised outputs, batch rows drawn by a
+ * counter hash of (seed, step, row), cosine-decayed learning rate from lr).
+ * Synchronous; *h_loss (may be NULL) receives the last step's loss. */
+sf_status sf_surrogate_train(sf_surrogate_handle s, const float* d_x, const float* d_y, unsigned long long n,
+                             int batch, int steps, float lr, unsigned long long seed, float* h_loss);
+
+/* The surrogate's MLP (for its weights) and its normalisation statistics
+ * (host [92] = input mean[30], input std[30], output mean[16], output std[16]). */
+sf_mlp_handle sf_surrogate_mlp(sf_surrogate_handle s);
+sf_status sf_surrogate_stats(sf_surrogate_handle s, float* h_stats);
+sf_status sf_surrogate_set_stats(sf_surrogate_handle s, const float* h_stats);
+
+/* One control step with the surrogate: every gated agent's chassis follows the
+ * MLP's prediction instead of the substep loop.  With audit != 0 every agent
+ * runs the physics instead and the largest distance between the surrogate's
+ * and the physics' end position over gated agents is recorded (the periodic
+ * audit).  Asynchronous. */
+sf_status sf_step_surrogate(sf_handle h, sf_surrogate_handle s, const float* d_actions, float dt, int substeps,
+                            int audit);
+
+/* Synchronous: the largest audit error since the last call [m] and the number
+ * of agent-steps that used the surrogate; both counters are reset. */
+sf_status sf_surrogate_audit(sf_handle h, float* h_max_err, unsigned long long* h_used);
+
 /* Number of agents and worlds of the loaded roads (0 before sf_load_roads). */
 int32_t sf_num_agents(sf_handle h);
 int32_t sf_num_worlds(sf_handle h);

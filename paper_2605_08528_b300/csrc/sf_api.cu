@@ -40,6 +40,7 @@ struct sf_ctx {
     float* place_buf = nullptr;
     uint8_t* all_mask = nullptr;
     float* act_buf = nullptr;   // [A][3] actions written by an attached policy
+    void* surr = nullptr;       // surrogate step buffers (allocated on first use)
     bool loaded = false;
 };
 
@@ -81,6 +82,7 @@ sf_status dalloc(sf_ctx* h, T** p, size_t count) {
 }
 
 void free_all(sf_ctx* h) {
+    if (h->surr) { ::operator delete(h->surr); h->surr = nullptr; }
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     h->st = DevState{};
@@ -89,6 +91,7 @@ void free_all(sf_ctx* h) {
     h->place_buf = nullptr;
     h->all_mask = nullptr;
     h->act_buf = nullptr;
+    h->surr = nullptr;
     h->loaded = false;
     h->W = h->A = h->NP = 0;
 }
@@ -731,6 +734,184 @@ sf_status sf_graph_destroy(sf_graph_handle g) {
     return SF_OK;
 }
 
+// ====================================================================== dynamics surrogate
+struct sf_surrogate {
+    sf_mlp_handle mlp = nullptr;
+    cudaStream_t stream = nullptr;
+    float* stats = nullptr;       // [30 mean, 30 std, 16 mean, 16 std]
+    float* bx = nullptr;          // training minibatch [batch][30]
+    float* by = nullptr;          // [batch][16]
+    int bcap = 0;
+    bool trained = false;
+    std::string err;
+};
+
+namespace {
+
+struct SurrBufs {                 // per-world-handle buffers of the surrogate step
+    float* x = nullptr;           // [A][32] normalised features
+    float* y = nullptr;           // [A][16] normalised outputs
+    float4* snap = nullptr;       // [5][A]
+    uint8_t* elig = nullptr;      // [A]
+    unsigned* words = nullptr;    // [0] audit error bits, [1] surrogate uses
+};
+
+}  // namespace
+
+static SurrBufs* surr_bufs(sf_ctx* h);
+
+sf_status sf_surrogate_create(void* cuda_stream, sf_surrogate_handle* out) {
+    if (!out) return SF_ERR_INVALID_ARG;
+    *out = nullptr;
+    sf_surrogate* s = new sf_surrogate();
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    const int32_t dims[5] = {kSurrIn, 256, 256, 256, kSurrOut};
+    sf_status st = sf_mlp_create(4, dims, SF_ACT_SILU, SF_ACT_NONE, cuda_stream, &s->mlp);
+    if (st != SF_OK) { delete s; return st; }
+    cudaError_t e = cudaMalloc(&s->stats, 2 * (kSurrIn + kSurrOut) * sizeof(float));
+    if (e != cudaSuccess) { sf_mlp_destroy(s->mlp); delete s; return SF_ERR_OOM; }
+    // identity statistics until trained
+    std::vector<float> st0(2 * (kSurrIn + kSurrOut), 0.f);
+    for (int i = 0; i < kSurrIn; ++i) st0[kSurrIn + i] = 1.f;
+    for (int i = 0; i < kSurrOut; ++i) st0[2 * kSurrIn + kSurrOut + i] = 1.f;
+    cudaMemcpy(s->stats, st0.data(), st0.size() * 4, cudaMemcpyHostToDevice);
+    // He-style initialisation with a fixed seed (weights are trained afterwards)
+    uint64_t z = 0x5EEDull;
+    auto rnd = [&]() {
+        z += 0x9E3779B97F4A7C15ull;
+        uint64_t q = z;
+        q = (q ^ (q >> 30)) * 0xBF58476D1CE4E5B9ull;
+        q = (q ^ (q >> 27)) * 0x94D049BB133111EBull;
+        q ^= q >> 31;
+        return ((double)(q >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+    };
+    for (int l = 0; l < 4; ++l) {
+        const int i = dims[l], o = dims[l + 1];
+        std::vector<float> w((size_t)o * i), b((size_t)o, 0.f);
+        const double a = std::sqrt(6.0 / i) * (l == 3 ? 0.1 : 1.0);
+        for (auto& v : w) v = (float)(a * rnd());
+        st = sf_mlp_set_layer(s->mlp, l, w.data(), b.data());
+        if (st != SF_OK) break;
+    }
+    if (st != SF_OK) { sf_surrogate_destroy(s); return st; }
+    *out = s;
+    return SF_OK;
+}
+
+sf_status sf_surrogate_destroy(sf_surrogate_handle s) {
+    if (!s) return SF_OK;
+    if (s->mlp) sf_mlp_destroy(s->mlp);
+    cudaFree(s->stats);
+    cudaFree(s->bx);
+    cudaFree(s->by);
+    delete s;
+    return SF_OK;
+}
+
+sf_status sf_surrogate_collect(sf_handle h, sf_surrogate_handle s, const float* d_actions, float dt, int substeps,
+                               float* d_x, float* d_y, unsigned long long cap, unsigned long long* d_count) {
+    if (!h || !s || !d_actions || !d_x || !d_y || !d_count) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_surrogate_collect: no roads loaded");
+    SurrBufs* b = surr_bufs(h);
+    if (!b) return fail(h, SF_ERR_OOM, "sf_surrogate_collect: buffers");
+    WorldArgs a = make_args(h);
+    cudaError_t e = sf_launch_surr_gate(a, dt, b->elig, h->stream);
+    if (e == cudaSuccess) e = sf_launch_surr_features(a, d_actions, nullptr, b->x, h->stream);
+    if (e == cudaSuccess) e = sf_launch_surr_snapshot(a, b->snap, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sf_surrogate_collect");
+    sf_status st = sf_step(h, d_actions, dt, substeps);
+    if (st != SF_OK) return st;
+    e = sf_launch_surr_collect(a, b->snap, b->elig, b->x, dt, d_x, d_y, cap, d_count, h->stream);
+    return e == cudaSuccess ? SF_OK : cuda_fail(h, e, "sf_surrogate_collect");
+}
+
+sf_status sf_surrogate_train(sf_surrogate_handle s, const float* d_x, const float* d_y, unsigned long long n,
+                             int batch, int steps, float lr, unsigned long long seed, float* h_loss) {
+    if (!s || !d_x || !d_y || n == 0 || batch < 8 || batch % 8 || steps < 0) return SF_ERR_INVALID_ARG;
+    cudaError_t e = cudaSuccess;
+    if (batch > s->bcap) {
+        cudaFree(s->bx);
+        cudaFree(s->by);
+        s->bx = s->by = nullptr;
+        e = cudaMalloc(&s->bx, (size_t)batch * kSurrIn * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&s->by, (size_t)batch * kSurrOut * 4);
+        if (e != cudaSuccess) { s->err = "sf_surrogate_train: buffers"; return SF_ERR_OOM; }
+        s->bcap = batch;
+    }
+    e = sf_launch_col_stats(d_x, n, kSurrIn, s->stats, s->stream);
+    if (e == cudaSuccess) e = sf_launch_col_stats(d_y, n, kSurrOut, s->stats + 2 * kSurrIn, s->stream);
+    if (e != cudaSuccess) { s->err = cudaGetErrorString(e); return SF_ERR_CUDA; }
+    float loss = 0.f;
+    for (int t = 0; t < steps; ++t) {
+        // cosine decay to 5% of the initial rate
+        const float lr_t = lr * (0.05f + 0.95f * 0.5f * (1.f + std::cos(3.14159265f * (float)t / (float)steps)));
+        e = sf_launch_gather(d_x, d_y, n, s->stats, s->stats + 2 * kSurrIn, batch, seed, (unsigned long long)t, s->bx,
+                             s->by, s->stream);
+        if (e != cudaSuccess) { s->err = cudaGetErrorString(e); return SF_ERR_CUDA; }
+        const bool last = t == steps - 1;
+        sf_status st = sf_mlp_train_step(s->mlp, s->bx, s->by, batch, lr_t, 1, (last && h_loss) ? &loss : nullptr);
+        if (st != SF_OK) { s->err = sf_mlp_last_error(s->mlp); return st; }
+    }
+    if (h_loss) *h_loss = loss;
+    s->trained = true;
+    return sf_mlp_sync(s->mlp);
+}
+
+sf_mlp_handle sf_surrogate_mlp(sf_surrogate_handle s) { return s ? s->mlp : nullptr; }
+
+sf_status sf_surrogate_stats(sf_surrogate_handle s, float* h_stats) {
+    if (!s || !h_stats) return SF_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(h_stats, s->stats, 2 * (kSurrIn + kSurrOut) * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? SF_OK : SF_ERR_CUDA;
+}
+
+sf_status sf_surrogate_set_stats(sf_surrogate_handle s, const float* h_stats) {
+    if (!s || !h_stats) return SF_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(s->stats, h_stats, 2 * (kSurrIn + kSurrOut) * 4, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? SF_OK : SF_ERR_CUDA;
+}
+
+sf_status sf_step_surrogate(sf_handle h, sf_surrogate_handle s, const float* d_actions, float dt, int substeps,
+                            int audit) {
+    if (!h || !s || !d_actions) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_step_surrogate: no roads loaded");
+    if (!(dt > 0.f) || substeps < 1 || substeps > 64) return fail(h, SF_ERR_INVALID_ARG, "sf_step_surrogate: dt");
+    SurrBufs* b = surr_bufs(h);
+    if (!b) return fail(h, SF_ERR_OOM, "sf_step_surrogate: buffers");
+    WorldArgs a = make_args(h);
+    cudaError_t e = sf_launch_surr_features(a, d_actions, s->stats, b->x, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sf_step_surrogate features");
+    sf_status st = sf_mlp_forward_on(s->mlp, h->stream, b->x, kSurrInLd, h->A, b->y, kSurrOut);
+    if (st != SF_OK) return fail(h, st, std::string("sf_step_surrogate: ") + sf_mlp_last_error(s->mlp));
+    a.actions = d_actions;
+    a.h = dt / (float)substeps;
+    a.substeps = substeps;
+    a.surr_y = b->y;
+    a.surr_stats = s->stats + 2 * kSurrIn;
+    a.surr_mode = audit ? 2 : 1;
+    a.audit_err = b->words;
+    a.surr_count = b->words + 1;
+    e = sf_launch_world(kModeStep, a, wpb_of(h), h->stream);
+    return e == cudaSuccess ? SF_OK : cuda_fail(h, e, "sf_step_surrogate");
+}
+
+sf_status sf_surrogate_audit(sf_handle h, float* h_max_err, unsigned long long* h_used) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    SurrBufs* b = surr_bufs(h);
+    if (!b) return fail(h, SF_ERR_OOM, "sf_surrogate_audit: buffers");
+    unsigned w[2] = {0, 0};
+    SF_CUDA(h, cudaStreamSynchronize(h->stream));
+    SF_CUDA(h, cudaMemcpy(w, b->words, 8, cudaMemcpyDeviceToHost));
+    SF_CUDA(h, cudaMemset(b->words, 0, 8));
+    float f;
+    std::memcpy(&f, &w[0], 4);
+    if (h_max_err) *h_max_err = f;
+    if (h_used) *h_used = w[1];
+    return SF_OK;
+}
+
 sf_status sf_sync(sf_handle h) {
     if (!h) return SF_ERR_INVALID_ARG;
     SF_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -746,3 +927,15 @@ sf_status sf_sync(sf_handle h) {
 }
 
 }  // extern "C"
+
+static SurrBufs* surr_bufs(sf_ctx* h) {
+    if (h->surr) return static_cast<SurrBufs*>(h->surr);
+    const size_t A = (size_t)h->A;
+    SurrBufs* b = new SurrBufs();
+    bool ok = dalloc(h, &b->x, A * kSurrInLd) == SF_OK && dalloc(h, &b->y, A * kSurrOut) == SF_OK &&
+              dalloc(h, &b->snap, A * 5) == SF_OK && dalloc(h, &b->elig, A) == SF_OK &&
+              dalloc(h, &b->words, 2) == SF_OK;
+    if (!ok || cudaMemset(b->words, 0, 8) != cudaSuccess) { delete b; return nullptr; }
+    h->surr = b;
+    return b;
+}

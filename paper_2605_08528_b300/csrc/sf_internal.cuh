@@ -160,8 +160,38 @@ struct WorldArgs {
     int substeps;
     int flags;
     unsigned long long seed;
+    // dynamics surrogate (optional): normalised MLP outputs [A][16] and the
+    // output statistics (mean[16], std[16]); mode 0 off, 1 replace the substeps
+    // of gated agents, 2 audit (physics runs, the surrogate's position error is
+    // recorded as the max into *audit_err)
+    const float* surr_y;
+    const float* surr_stats;
+    int surr_mode;
+    unsigned int* audit_err;   // float bits, max-reduced
+    unsigned int* surr_count;  // number of agents that used the surrogate (accumulated)
 };
+
+// surrogate feature / target layout (dynamics surrogate of the step)
+constexpr int kSurrIn = 30, kSurrInLd = 32, kSurrOut = 16;
 
 // launch wrappers (sf_world.cu)
 cudaError_t sf_launch_world(int mode, const WorldArgs& a, int warps_per_block, cudaStream_t s);
 cudaError_t sf_launch_place(const WorldArgs& a, const float* d_place, cudaStream_t s);
+// gate of the surrogate per agent (1 = eligible), from the current state
+cudaError_t sf_launch_surr_gate(const WorldArgs& a, float dt, uint8_t* d_elig, cudaStream_t s);
+// features [A][kSurrInLd] of the current state and actions; normalised when stats ([30] mean, [30] std) given
+cudaError_t sf_launch_surr_features(const WorldArgs& a, const float* d_actions, const float* x_stats, float* d_x,
+                                    cudaStream_t s);
+// snapshot of the dynamic state (pos, quat, vel, angv, spin) into snap[5][A]
+cudaError_t sf_launch_surr_snapshot(const WorldArgs& a, float4* snap, cudaStream_t s);
+// targets of the step just taken from the snapshot; rows of gated, non-respawned agents are appended
+// (features from d_x, targets) to out_x [cap][kSurrIn], out_y [cap][kSurrOut] at *count
+cudaError_t sf_launch_surr_collect(const WorldArgs& a, const float4* snap, const uint8_t* d_elig, const float* d_x,
+                                   float dt, float* out_x, float* out_y, unsigned long long cap,
+                                   unsigned long long* count, cudaStream_t s);
+
+// training kernels of the surrogate (sf_surrogate.cu)
+cudaError_t sf_launch_col_stats(const float* x, unsigned long long n, int k, float* stats, cudaStream_t s);
+cudaError_t sf_launch_gather(const float* x, const float* y, unsigned long long n, const float* xs, const float* ys,
+                             int batch, unsigned long long seed, unsigned long long t, float* bx, float* by,
+                             cudaStream_t s);

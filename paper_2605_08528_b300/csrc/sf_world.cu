@@ -143,14 +143,19 @@ __device__ __forceinline__ void pair_force(float cix, float ciy, float dix, floa
 // ------------------------------------------------------------------ one chassis substep
 // steering PD, suspension rays, predicted velocities, friction-circle wheel
 // impulses (Jacobi, shared by the wheels in contact), brake, positions.
-__device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, float brk, float fcx, float fcy,
-                                             float tcz, float h) {
-    // 1. steering (Eq. steer_pd)
+// steering PD (Eq. steer_pd), semi-implicit, angle clamped: decoupled from the chassis
+__device__ __forceinline__ void steer_substep(Agent& A, float dstar, float h) {
     float ts = clampf(kKp * (dstar - A.dl) - kKd * A.dd, -kTauSteer, kTauSteer);
     A.dd += h * ts / kSteerI;
     A.dl += h * A.dd;
     if (A.dl > kThetaMax) { A.dl = kThetaMax; A.dd = 0.f; }
     if (A.dl < -kThetaMax) { A.dl = -kThetaMax; A.dd = 0.f; }
+}
+
+__device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, float brk, float fcx, float fcy,
+                                             float tcz, float h) {
+    // 1. steering
+    steer_substep(A, dstar, h);
 
     // 2. rotation, world inverse inertia (symmetric), world inertia
     float R[3][3];
@@ -696,6 +701,165 @@ __device__ void coop_edges(const DevRoads& rd, const DevGrid& g, float px, float
     tedge = warp_min(t_best);
 }
 
+// ------------------------------------------------------------------ dynamics surrogate
+// Heading frame at t: rotation by psi about z (psi of the body x axis).
+// Features (30): z, tilt quaternion q_psi^-1 q (4), v and w in the heading
+// frame (3 + 3), wheel spins (4), suspension compressions and rates (4 + 4),
+// steer angle and rate, decoded action (3), mu, 0.
+// Targets (16): R_psi^T dp - v_h dt (3), body rotation vector of q_t^-1 q_t+1
+// - w_body dt (3), R_psi^T v_t+1 - v_h (3), R_psi^T w_t+1 - w_h (3), dOmega (4).
+constexpr float kSurrMuMin = 0.3f, kSurrVMax = 35.0f, kSurrCosTilt = 0.98480775f;   // cos 10 deg
+constexpr float kSurrReach = 4.8466483f + 2.0f;   // two circumradii of the footprint + 2 m
+
+struct Frame {
+    float c, s;      // cos, sin of psi
+};
+__device__ __forceinline__ Frame frame_of(float qw, float qx, float qy, float qz) {
+    float hx, hy;
+    heading_of(qw, qx, qy, qz, hx, hy);
+    Frame f;
+    f.c = hx; f.s = hy;
+    return f;
+}
+__device__ __forceinline__ void to_h(const Frame& f, float x, float y, float& hx_, float& hy_) {
+    hx_ = f.c * x + f.s * y;
+    hy_ = -f.s * x + f.c * y;
+}
+__device__ __forceinline__ void from_h(const Frame& f, float x, float y, float& wx, float& wy) {
+    wx = f.c * x - f.s * y;
+    wy = f.s * x + f.c * y;
+}
+
+__device__ void surr_features(const Agent& A, float thr, float dstar, float brk, float* x) {
+    const Frame f = frame_of(A.qw, A.qx, A.qy, A.qz);
+    const float psi = atan2f(f.s, f.c);
+    float sh, ch;
+    sincosf(0.5f * psi, &sh, &ch);
+    x[0] = A.pz;
+    x[1] = ch * A.qw + sh * A.qz;
+    x[2] = ch * A.qx + sh * A.qy;
+    x[3] = ch * A.qy - sh * A.qx;
+    x[4] = ch * A.qz - sh * A.qw;
+    to_h(f, A.vx, A.vy, x[5], x[6]);
+    x[7] = A.vz;
+    to_h(f, A.wx, A.wy, x[8], x[9]);
+    x[10] = A.wz;
+    x[11] = A.s0; x[12] = A.s1; x[13] = A.s2; x[14] = A.s3;
+    float R[3][3];
+    quat_to_mat(A.qw, A.qx, A.qy, A.qz, R);
+    const float uz = R[2][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float bx = i < 2 ? kHardX : -kHardX, by = (i & 1) == 0 ? kHardY : -kHardY, bz = kHardZ;
+        const float rbx = R[0][0] * bx + R[0][1] * by + R[0][2] * bz;
+        const float rby = R[1][0] * bx + R[1][1] * by + R[1][2] * bz;
+        const float rbz = R[2][0] * bx + R[2][1] * by + R[2][2] * bz;
+        float xc = 0.f, xd = 0.f;
+        if (uz > kUzMin) {
+            const float t = (A.pz + rbz) / uz, l = t - kWheelR;
+            if (l < kRest) {
+                xc = kRest - fmaxf(l, 0.f);
+                xd = -(A.vz + (A.wx * rby - A.wy * rbx)) / uz;
+            }
+        }
+        x[15 + i] = xc;
+        x[19 + i] = xd;
+    }
+    x[23] = A.dl; x[24] = A.dd;
+    x[25] = thr; x[26] = dstar; x[27] = brk;
+    x[28] = A.mu;
+    x[29] = 0.f;
+}
+
+// rotation vector of a unit quaternion (shortest rotation)
+__device__ __forceinline__ void quat_log(float w, float x, float y, float z, float& rx, float& ry, float& rz) {
+    if (w < 0.f) { w = -w; x = -x; y = -y; z = -z; }
+    const float n = sqrtf(x * x + y * y + z * z);
+    const float ang = 2.f * atan2f(n, w);
+    const float k = n > 1e-12f ? ang / n : 2.f;
+    rx = k * x; ry = k * y; rz = k * z;
+}
+
+// targets of one step from the start state (p0, q0, v0, w0, s0) and the end state A
+__device__ void surr_targets(float4 p0, float4 q0, float4 v0, float4 w0, float4 s0, const Agent& A, float dt,
+                             float* y) {
+    const Frame f = frame_of(q0.x, q0.y, q0.z, q0.w);
+    float dph_x, dph_y, vh0x, vh0y, vh1x, vh1y, wh0x, wh0y, wh1x, wh1y;
+    to_h(f, A.px - p0.x, A.py - p0.y, dph_x, dph_y);
+    to_h(f, v0.x, v0.y, vh0x, vh0y);
+    to_h(f, A.vx, A.vy, vh1x, vh1y);
+    to_h(f, w0.x, w0.y, wh0x, wh0y);
+    to_h(f, A.wx, A.wy, wh1x, wh1y);
+    y[0] = dph_x - vh0x * dt;
+    y[1] = dph_y - vh0y * dt;
+    y[2] = (A.pz - p0.z) - v0.z * dt;
+    // q_rel = q0^-1 q1 (body frame at t)
+    const float aw = q0.x, ax = -q0.y, ay = -q0.z, az = -q0.w;
+    const float rw = aw * A.qw - ax * A.qx - ay * A.qy - az * A.qz;
+    const float rx = aw * A.qx + ax * A.qw + (ay * A.qz - az * A.qy);
+    const float ry = aw * A.qy + ay * A.qw + (az * A.qx - ax * A.qz);
+    const float rz = aw * A.qz + az * A.qw + (ax * A.qy - ay * A.qx);
+    float tx, ty, tz;
+    quat_log(rw, rx, ry, rz, tx, ty, tz);
+    float R[3][3];
+    quat_to_mat(q0.x, q0.y, q0.z, q0.w, R);
+    const float wbx = R[0][0] * w0.x + R[1][0] * w0.y + R[2][0] * w0.z;   // R^T w
+    const float wby = R[0][1] * w0.x + R[1][1] * w0.y + R[2][1] * w0.z;
+    const float wbz = R[0][2] * w0.x + R[1][2] * w0.y + R[2][2] * w0.z;
+    y[3] = tx - wbx * dt; y[4] = ty - wby * dt; y[5] = tz - wbz * dt;
+    y[6] = vh1x - vh0x; y[7] = vh1y - vh0y; y[8] = A.vz - v0.z;
+    y[9] = wh1x - wh0x; y[10] = wh1y - wh0y; y[11] = A.wz - w0.z;
+    y[12] = A.s0 - s0.x; y[13] = A.s1 - s0.y; y[14] = A.s2 - s0.z; y[15] = A.s3 - s0.w;
+}
+
+// apply denormalised targets d[16] to the start state (p0 ... s0): the chassis part of A
+__device__ void surr_apply(float4 p0, float4 q0, float4 v0, float4 w0, float4 s0, const float* d, float dt, Agent& A) {
+    const Frame f = frame_of(q0.x, q0.y, q0.z, q0.w);
+    float vh0x, vh0y, wh0x, wh0y, ox, oy;
+    to_h(f, v0.x, v0.y, vh0x, vh0y);
+    to_h(f, w0.x, w0.y, wh0x, wh0y);
+    from_h(f, d[0] + vh0x * dt, d[1] + vh0y * dt, ox, oy);
+    A.px = p0.x + ox; A.py = p0.y + oy; A.pz = p0.z + (d[2] + v0.z * dt);
+    float R[3][3];
+    quat_to_mat(q0.x, q0.y, q0.z, q0.w, R);
+    const float tx = d[3] + (R[0][0] * w0.x + R[1][0] * w0.y + R[2][0] * w0.z) * dt;
+    const float ty = d[4] + (R[0][1] * w0.x + R[1][1] * w0.y + R[2][1] * w0.z) * dt;
+    const float tz = d[5] + (R[0][2] * w0.x + R[1][2] * w0.y + R[2][2] * w0.z) * dt;
+    const float ang = sqrtf(tx * tx + ty * ty + tz * tz);
+    float sa, ca;
+    sincosf(0.5f * ang, &sa, &ca);
+    const float k = ang > 1e-12f ? sa / ang : 0.5f;
+    const float ew = ca, ex = k * tx, ey = k * ty, ez = k * tz;   // exp of the rotation vector
+    float qw = q0.x * ew - q0.y * ex - q0.z * ey - q0.w * ez;       // q0 (x) e
+    float qx = q0.x * ex + q0.y * ew + (q0.z * ez - q0.w * ey);
+    float qy = q0.x * ey + q0.z * ew + (q0.w * ex - q0.y * ez);
+    float qz = q0.x * ez + q0.w * ew + (q0.y * ey - q0.z * ex);
+    const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    A.qw = qw / qn; A.qx = qx / qn; A.qy = qy / qn; A.qz = qz / qn;
+    from_h(f, vh0x + d[6], vh0y + d[7], A.vx, A.vy);
+    A.vz = v0.z + d[8];
+    from_h(f, wh0x + d[9], wh0y + d[10], A.wx, A.wy);
+    A.wz = w0.z + d[11];
+    A.s0 = s0.x + d[12]; A.s1 = s0.y + d[13]; A.s2 = s0.z + d[14]; A.s3 = s0.w + d[15];
+}
+
+// gate of lane `lane` given the exchange area at the start of the step
+__device__ __forceinline__ bool surr_gate(const Exch& E, int n, int lane, uint32_t alive_bits, const Agent& A,
+                                          float dt) {
+    if (!((alive_bits >> lane) & 1u)) return false;
+    if (A.mu < kSurrMuMin) return false;
+    if (A.vx * A.vx + A.vy * A.vy + A.vz * A.vz > kSurrVMax * kSurrVMax) return false;
+    if (1.f - 2.f * (A.qx * A.qx + A.qy * A.qy) < kSurrCosTilt) return false;
+    for (int j = 0; j < n; ++j) {
+        if (j == lane || !((alive_bits >> j) & 1u)) continue;
+        const float dvx = E.vx[j] - A.vx, dvy = E.vy[j] - A.vy;
+        const float reach = kSurrReach + sqrtf(dvx * dvx + dvy * dvy) * dt;
+        const float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
+        if (dx * dx + dy * dy <= reach * reach) return false;
+    }
+    return true;
+}
+
 // per-agent results of the cooperative queries
 struct AgentQ {
     int seg;
@@ -759,12 +923,14 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
                 brk = clampf(act[2], 0.f, 1.f);
             }
             prevx = A.px; prevy = A.py;
+            bool gated = false;
             for (int s = 0; s < args.substeps; ++s) {
                 float sx_, sy_;
                 heading_of(A.qw, A.qx, A.qy, A.qz, sx_, sy_);
                 publish(E, lane, A, sx_, sy_);
                 const uint32_t alive_bits = __ballot_sync(kFull, alive);
                 __syncwarp();
+                if (s == 0 && args.surr_mode != 0) gated = surr_gate(E, n, lane, alive_bits, A, args.h * args.substeps);
                 float fcx = 0.f, fcy = 0.f, tcz = 0.f;
                 if (alive) {
                     for (int j = 0; j < n; ++j) {
@@ -779,10 +945,31 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
                     }
                 }
                 __syncwarp();
-                if (alive) body_substep(A, thr, dstar, brk, fcx, fcy, tcz, args.h);
+                if (alive) {
+                    if (gated && args.surr_mode == 1) steer_substep(A, dstar, args.h);   // chassis from the surrogate
+                    else body_substep(A, thr, dstar, brk, fcx, fcy, tcz, args.h);
+                }
             }
             A.px += A.dpx; A.py += A.dpy; A.pz += A.dpz;
             A.dpx = A.dpy = A.dpz = 0.f;
+            if (gated) {
+                // the start-of-step state is still in global memory (stored at the end of the kernel)
+                const float4 p0 = st.pos[a], q0 = st.quat[a], v0 = st.vel[a], w0 = st.angv[a], s0 = st.spin[a];
+                float d[kSurrOut];
+                const float* yn = args.surr_y + (size_t)a * kSurrOut;
+#pragma unroll
+                for (int k = 0; k < kSurrOut; ++k) d[k] = args.surr_stats[k] + args.surr_stats[kSurrOut + k] * yn[k];
+                const float dt = args.h * args.substeps;
+                if (args.surr_mode == 1) {
+                    surr_apply(p0, q0, v0, w0, s0, d, dt, A);
+                    atomicAdd(args.surr_count, 1u);
+                } else {
+                    Agent P = A;
+                    surr_apply(p0, q0, v0, w0, s0, d, dt, P);
+                    const float ex = P.px - A.px, ey = P.py - A.py, ez = P.pz - A.pz;
+                    atomicMax(args.audit_err, __float_as_uint(sqrtf(ex * ex + ey * ey + ez * ez)));
+                }
+            }
             if (alive && !finite_agent(A)) {
                 nonfin = true;
                 park_agent(A);
@@ -1048,6 +1235,100 @@ __global__ void place_kernel(const WorldArgs args, const float* __restrict__ pla
     const float* p = place + 6 * (size_t)a;
     place_agent(A, p[0], p[1], p[2], p[3], p[4], p[5]);
     store_agent(args.st, a, A);
+}
+
+// gate per agent, one warp per world
+__global__ void surr_gate_kernel(const WorldArgs args, float dt, uint8_t* __restrict__ elig) {
+    __shared__ Exch E;
+    const int w = blockIdx.x, lane = threadIdx.x;
+    const int4 wd = __ldg(&args.rd.world[w]);
+    const int a0 = wd.x, n = wd.y;
+    if (n <= 0) return;
+    const bool has = lane < n;
+    const int a = a0 + (has ? lane : 0);
+    Agent A;
+    load_agent(args.st, a, A);
+    const bool alive = has && (status_of(A.meta) & kAlive);
+    float hx, hy;
+    heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
+    publish(E, lane, A, hx, hy);
+    const uint32_t ab = __ballot_sync(kFull, alive);
+    __syncwarp();
+    const bool g = surr_gate(E, n, lane, ab, A, dt);
+    if (has) elig[a] = g ? 1 : 0;
+}
+
+__global__ void surr_features_kernel(const WorldArgs args, const float* __restrict__ actions,
+                                     const float* __restrict__ stats, float* __restrict__ x) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= args.num_agents) return;
+    Agent A;
+    load_agent(args.st, a, A);
+    const float* act = actions + 3 * (size_t)a;
+    float f[kSurrIn];
+    surr_features(A, clampf(act[0], 0.f, 1.f), kThetaMax * clampf(act[1], -1.f, 1.f), clampf(act[2], 0.f, 1.f), f);
+    float* row = x + (size_t)a * kSurrInLd;
+#pragma unroll
+    for (int k = 0; k < kSurrIn; ++k) row[k] = stats ? (f[k] - stats[k]) / stats[kSurrIn + k] : f[k];
+    row[30] = 0.f;
+    row[31] = 0.f;
+}
+
+__global__ void surr_snapshot_kernel(const WorldArgs args, float4* __restrict__ snap) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int A = args.num_agents;
+    if (a >= A) return;
+    snap[a] = args.st.pos[a];
+    snap[A + a] = args.st.quat[a];
+    snap[2 * A + a] = args.st.vel[a];
+    snap[3 * A + a] = args.st.angv[a];
+    snap[4 * A + a] = args.st.spin[a];
+}
+
+__global__ void surr_collect_kernel(const WorldArgs args, const float4* __restrict__ snap,
+                                    const uint8_t* __restrict__ elig, const float* __restrict__ x, float dt,
+                                    float* __restrict__ out_x, float* __restrict__ out_y, unsigned long long cap,
+                                    unsigned long long* __restrict__ count) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int A = args.num_agents;
+    if (a >= A || !elig[a]) return;
+    const uint32_t ev = args.out.events[a];
+    if (ev & (kEvRespawned | kEvNonfinite | kEvCollision | kEvCrash)) return;
+    Agent S;
+    load_agent(args.st, a, S);
+    if (!(status_of(S.meta) & kAlive)) return;
+    float y[kSurrOut];
+    surr_targets(snap[a], snap[A + a], snap[2 * A + a], snap[3 * A + a], snap[4 * A + a], S, dt, y);
+    const unsigned long long i = atomicAdd(count, 1ull);
+    if (i >= cap) return;
+#pragma unroll
+    for (int k = 0; k < kSurrIn; ++k) out_x[i * kSurrIn + k] = x[(size_t)a * kSurrInLd + k];
+#pragma unroll
+    for (int k = 0; k < kSurrOut; ++k) out_y[i * kSurrOut + k] = y[k];
+}
+
+cudaError_t sf_launch_surr_gate(const WorldArgs& a, float dt, uint8_t* d_elig, cudaStream_t s) {
+    if (a.num_worlds <= 0) return cudaSuccess;
+    surr_gate_kernel<<<a.num_worlds, 32, 0, s>>>(a, dt, d_elig);
+    return cudaGetLastError();
+}
+cudaError_t sf_launch_surr_features(const WorldArgs& a, const float* d_actions, const float* x_stats, float* d_x,
+                                    cudaStream_t s) {
+    if (a.num_agents <= 0) return cudaSuccess;
+    surr_features_kernel<<<(a.num_agents + 127) / 128, 128, 0, s>>>(a, d_actions, x_stats, d_x);
+    return cudaGetLastError();
+}
+cudaError_t sf_launch_surr_snapshot(const WorldArgs& a, float4* snap, cudaStream_t s) {
+    if (a.num_agents <= 0) return cudaSuccess;
+    surr_snapshot_kernel<<<(a.num_agents + 127) / 128, 128, 0, s>>>(a, snap);
+    return cudaGetLastError();
+}
+cudaError_t sf_launch_surr_collect(const WorldArgs& a, const float4* snap, const uint8_t* d_elig, const float* d_x,
+                                   float dt, float* out_x, float* out_y, unsigned long long cap,
+                                   unsigned long long* count, cudaStream_t s) {
+    if (a.num_agents <= 0) return cudaSuccess;
+    surr_collect_kernel<<<(a.num_agents + 127) / 128, 128, 0, s>>>(a, snap, d_elig, d_x, dt, out_x, out_y, cap, count);
+    return cudaGetLastError();
 }
 
 template <int MODE>

@@ -82,6 +82,13 @@ def lib():
             "sf_step_policy": ([vp, vp, f32, C.c_int], i32),
             "sf_graph_capture": ([vp, vp, vp, vp, f32, C.c_int, vp], i32), "sf_graph_launch": ([vp], i32),
             "sf_graph_destroy": ([vp], i32),
+            "sf_surrogate_create": ([vp, vp], i32), "sf_surrogate_destroy": ([vp], i32),
+            "sf_surrogate_collect": ([vp, vp, vp, f32, C.c_int, vp, vp, C.c_uint64, vp], i32),
+            "sf_surrogate_train": ([vp, vp, vp, C.c_uint64, C.c_int, C.c_int, f32, C.c_uint64, vp], i32),
+            "sf_surrogate_mlp": ([vp], vp), "sf_surrogate_stats": ([vp, vp], i32),
+            "sf_surrogate_set_stats": ([vp, vp], i32),
+            "sf_step_surrogate": ([vp, vp, vp, f32, C.c_int, C.c_int], i32),
+            "sf_surrogate_audit": ([vp, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -357,3 +364,62 @@ def init_policy(seed=0, dims=(320, 512, 512, 3), stream=None):
     for l, (i, o) in enumerate(zip(dims[:-1], dims[1:])):
         sf_mlp_set_layer(m, l, rng.normal(0, 1 / np.sqrt(i), (o, i)), np.zeros(o))
     return m
+
+
+# --------------------------------------------------------------------------- dynamics surrogate
+SURR_IN, SURR_OUT = 30, 16
+
+
+def sf_surrogate_create(stream=None):
+    h = C.c_void_p()
+    st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    s = lib().sf_surrogate_create(C.c_void_p(st), C.byref(h))
+    if s != SF_OK:
+        raise SFError(s, "sf_surrogate_create")
+    return h
+
+
+def sf_surrogate_destroy(s):
+    lib().sf_surrogate_destroy(s)
+
+
+def sf_surrogate_collect(h, s, d_actions, d_x, d_y, cap, d_count, dt=1.0 / 30.0, substeps=4):
+    _check(lib().sf_surrogate_collect(h, s, _ptr(d_actions), float(dt), int(substeps), _ptr(d_x), _ptr(d_y),
+                                      int(cap), _ptr(d_count)), h)
+
+
+def sf_surrogate_train(s, d_x, d_y, n, batch=4096, steps=2000, lr=1e-3, seed=1):
+    loss = C.c_float()
+    st = lib().sf_surrogate_train(s, _ptr(d_x), _ptr(d_y), int(n), int(batch), int(steps), float(lr), int(seed),
+                                  C.byref(loss))
+    if st != SF_OK:
+        raise SFError(st, "sf_surrogate_train")
+    return float(loss.value)
+
+
+def sf_surrogate_mlp(s):
+    return C.c_void_p(lib().sf_surrogate_mlp(s))
+
+
+def sf_surrogate_stats(s):
+    out = np.zeros(2 * (SURR_IN + SURR_OUT), np.float32)
+    if lib().sf_surrogate_stats(s, _ptr(out)) != SF_OK:
+        raise SFError(SF_ERR_CUDA, "sf_surrogate_stats")
+    return out
+
+
+def sf_surrogate_set_stats(s, stats):
+    a = np.ascontiguousarray(stats, np.float32)
+    if lib().sf_surrogate_set_stats(s, _ptr(a)) != SF_OK:
+        raise SFError(SF_ERR_CUDA, "sf_surrogate_set_stats")
+
+
+def sf_step_surrogate(h, s, d_actions, dt=1.0 / 30.0, substeps=4, audit=False):
+    _check(lib().sf_step_surrogate(h, s, _ptr(d_actions), float(dt), int(substeps), int(bool(audit))), h)
+
+
+def sf_surrogate_audit(h):
+    e = C.c_float()
+    n = C.c_uint64()
+    _check(lib().sf_surrogate_audit(h, C.byref(e), C.byref(n)), h)
+    return float(e.value), int(n.value)
