@@ -116,7 +116,7 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- our arm
-def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, policy_seed=None):
+def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, policy_seed=None, surrogate=None):
     """Time `steps` replays of the captured step graph (policy forward + step
     when policy_seed is given) on the workload `name`."""
     scene = make_scene(name, rank)
@@ -134,7 +134,9 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, p
         tuned = None
         if nw == 0:                                       # setup: pick the launch shape (state restored)
             tuned = sf.sf_autotune(W.h, acts[0], iters=10)
-        graph = sf.sf_graph_capture(W.h, policy=policy, d_actions=act_cur)
+        graph = sf.sf_graph_capture(W.h, policy=policy, d_actions=act_cur, surrogate=surrogate)
+        if surrogate is not None:
+            sf.sf_surrogate_audit(W.h)                    # reset the usage counter
         for t in range(warmup):
             act_cur.copy_(acts[t % ring])
             sf.sf_graph_launch(graph)
@@ -152,6 +154,7 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, p
         wall = time.perf_counter() - t0
     st = sf.sf_sync(W.h, allow=(sf.SF_ERR_NONFINITE,))
     ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    surr_used = sf.sf_surrogate_audit(W.h)[1] if surrogate is not None else 0
     F, I, _ = sf.sf_get_state(W.h)
     alive = int(((I[:, 4] & 1) != 0).sum())
     peak_drac = float(F[(I[:, 4] & 1) != 0, 24].mean()) if alive else 0.0
@@ -161,7 +164,8 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, p
     if not e2e:
         W.close()
         return dict(scene=scene, A=A, alive=alive, ms=ms, wall=wall, status=st, e2e_wall=float("nan"),
-                    e2e_steps=1, h2d=A * 12, d2h=A * 5, tuned=tuned, peak_drac=peak_drac)
+                    e2e_steps=1, h2d=A * 12, d2h=A * 5, tuned=tuned, peak_drac=peak_drac,
+                    surr_frac=surr_used / float((warmup + steps) * A))
     # end to end through the C-ABI: pinned host actions in, host rewards/done out, every step
     acts_pin = torch.as_tensor(acts_h).pin_memory()
     act_dev = torch.empty((A, 3), dtype=torch.float32, device=dev)
@@ -184,7 +188,7 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, p
         e2e_wall = time.perf_counter() - t0
     W.close()
     return dict(scene=scene, A=A, alive=alive, ms=ms, wall=wall, status=st, e2e_wall=e2e_wall,
-                e2e_steps=e2e_steps, h2d=A * 12, d2h=A * 5, tuned=tuned, peak_drac=peak_drac)
+                e2e_steps=e2e_steps, h2d=A * 12, d2h=A * 5, tuned=tuned, peak_drac=peak_drac, surr_frac=0.0)
 
 
 def cpu_baseline(name, seconds=12.0):
@@ -233,11 +237,32 @@ def main_ours(args):
         torch.cuda.synchronize()
         res[name] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream, e2e=not args.skip_e2e,
                                  nw=args.nw)
+    surr = None
+    surr_info = None
+    if not args.only and not args.skip_surrogate:
+        from paper_2605_08528_b300 import surrogate as SU
+        t0 = time.perf_counter()
+        surr, rows, loss = SU.collect_and_train(make_scene("256x16", rank), transitions=args.surr_rows,
+                                                train_steps=args.surr_steps, seed=31 + rank, stream=stream)
+        t_train = time.perf_counter() - t0
+        lone = synth.procedural_scene(512, 1, seed_base=9000 + 512 * rank)
+        lone.precip[:] = np.minimum(lone.precip, 2)       # mu >= 0.3 cells (the gate's range)
+        err, frac = SU.rollout_error(surr, lone, stream=stream)
+        surr_info = dict(rows=rows, train_steps=args.surr_steps, final_loss=loss, train_s=t_train,
+                         err_mean_m=float(err.mean()), err_p90_m=float(np.percentile(err, 90)),
+                         err_max_m=float(err.max()), gated_fraction_lone=frac)
+        for name in ("256x16", "4096x16"):
+            if world > 1:
+                dist.barrier()
+            res[name + "+surrogate"] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream,
+                                                    e2e=False, nw=args.nw, surrogate=surr)
     if not args.only and not args.skip_policy:
         if world > 1:
             dist.barrier()
         res["4096x16+policy"] = run_workload("4096x16", args.steps, args.warmup, rank, torch, sf, stream, e2e=False,
-                                             nw=args.nw, policy_seed=4000)
+                                             nw=args.nw, policy_seed=4000, surrogate=surr)
+    if surr is not None:
+        sf.sf_surrogate_destroy(surr)
     clk = clocks.stop()
     if args.only:          # profiling run: one workload, no report line
         if rank == 0:
@@ -261,10 +286,11 @@ def main_ours(args):
         ach = ab["total"] / mean_s / 1e9
         return dict(casps=casps, e2e=e2e_casps, ms=float(r["ms"].mean()), p50=float(np.percentile(r["ms"], 50)),
                     p99=float(np.percentile(r["ms"], 99)), bytes=ab, achieved=ach, A=r["A"], alive=r["alive"],
-                    h2d=r["h2d"], d2h=r["d2h"], tuned=r["tuned"], peak_drac=r["peak_drac"])
+                    h2d=r["h2d"], d2h=r["d2h"], tuned=r["tuned"], peak_drac=r["peak_drac"], surr_frac=r["surr_frac"])
 
     a256, a4096 = agg("256x16"), agg("4096x16")
     apol = agg("4096x16+policy") if "4096x16+policy" in res else None
+    asur = {k: agg(k + "+surrogate") for k in ("256x16", "4096x16") if k + "+surrogate" in res}
     if rank == 0:
         base = cpu_baseline("256x16") if (world == 1 and not args.skip_cpu) else None
         traffic = load_traffic()
@@ -300,8 +326,17 @@ def main_ours(args):
             "scale_4096x16_policy": None if apol is None else {
                 "value": apol["casps"], "unit": "CASPS", "ms_per_step": apol["ms"], "p50_ms": apol["p50"],
                 "p99_ms": apol["p99"], "mean_peak_drac": apol["peak_drac"],
-                "graph": "BF16 tcgen05 policy 320-512-512-3 (ELU, tanh; seeded random weights) + world step",
+                "surrogate_fraction": apol["surr_frac"],
+                "graph": "BF16 tcgen05 policy 320-512-512-3 (ELU, tanh; seeded random weights) + surrogate "
+                         "features + BF16 surrogate MLP + world step (surrogate for gated agents, physics fallback)",
                 "wet_mix": "50% heavy-rain asphalt mu 0.5, 50% dry asphalt mu 0.9"},
+            "surrogate": None if surr_info is None else dict(
+                surr_info,
+                error_reference="FP32 physics path (parity with the FP64 oracle <= 4.3e-5 m over 100 steps)",
+                **{"casps_" + k: v["casps"] for k, v in asur.items()},
+                **{"speedup_vs_physics_" + k: v["casps"] / (a256 if k == "256x16" else a4096)["casps"]
+                   for k, v in asur.items()},
+                **{"gated_fraction_" + k: v["surr_frac"] for k, v in asur.items()}),
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                        "samples": clk["samples"]},
             "paper_context": "19,250 CASPS at 256x16 on an RTX PRO 6000 (Isaac Sim/PhysX + PPO), context only",
@@ -367,6 +402,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
     ap.add_argument("--nw", type=int, default=0, help="warps per world (1, 2, 4, 8; 0 = autotuned)")
     ap.add_argument("--skip-policy", action="store_true", help="no 4096x16 + policy leg")
+    ap.add_argument("--skip-surrogate", action="store_true", help="no surrogate training / legs")
+    ap.add_argument("--surr-rows", type=int, default=10_000_000, help="surrogate training transitions")
+    ap.add_argument("--surr-steps", type=int, default=8000, help="surrogate Adam steps")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

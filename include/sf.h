@@ -315,15 +315,17 @@ sf_status sf_step_policy(sf_handle h, sf_mlp_handle policy, float dt, int subste
 
 /* Capture a whole control step into a CUDA graph on the handle's stream
  * (which must not be the legacy default stream): [policy forward if policy
- * != NULL] -> sf_step (actions from the policy, else from d_actions, whose
- * contents may change between launches) -> [sf_reset(d_reset_mask) if not
- * NULL].  The policy's buffers are allocated before the capture.  Replays
- * with sf_graph_launch run every kernel of the step with one launch call;
- * the handle's state evolves as with the individual calls.
+ * != NULL] -> [surrogate features and MLP if surrogate != NULL] -> the step
+ * (sf_step_surrogate with a surrogate, else sf_step; actions from the policy,
+ * else from d_actions, whose contents may change between launches) ->
+ * [sf_reset(d_reset_mask) if not NULL].  Buffers are allocated before the
+ * capture.  Replays with sf_graph_launch run every kernel of the step with
+ * one launch call; the handle's state evolves as with the individual calls.
  * Errors: SF_ERR_STATE, SF_ERR_INVALID_ARG, SF_ERR_OOM, SF_ERR_CUDA. */
 typedef struct sf_graph* sf_graph_handle;
-sf_status sf_graph_capture(sf_handle h, sf_mlp_handle policy, const float* d_actions, const uint8_t* d_reset_mask,
-                           float dt, int substeps, sf_graph_handle* out);
+typedef struct sf_surrogate* sf_surrogate_handle;
+sf_status sf_graph_capture(sf_handle h, sf_mlp_handle policy, sf_surrogate_handle surrogate, const float* d_actions,
+                           const uint8_t* d_reset_mask, float dt, int substeps, sf_graph_handle* out);
 sf_status sf_graph_launch(sf_graph_handle g);
 sf_status sf_graph_destroy(sf_graph_handle g);
 
@@ -340,7 +342,6 @@ sf_status sf_graph_destroy(sf_graph_handle g);
  * angular velocity (each minus the constant-velocity prediction) and of the
  * wheel spins, normalised by the training set's mean and deviation.
  * ---------------------------------------------------------------------- */
-typedef struct sf_surrogate* sf_surrogate_handle;
 
 /* An untrained surrogate (seeded initial weights) on cuda_stream. */
 sf_status sf_surrogate_create(void* cuda_stream, sf_surrogate_handle* out);

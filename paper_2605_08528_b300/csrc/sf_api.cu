@@ -120,6 +120,39 @@ bool is_edge_type(int t) { return t == 15 || t == 16; }
 
 }  // namespace
 
+// ---------------------------------------------------------------- dynamics surrogate objects
+struct sf_surrogate {
+    sf_mlp_handle mlp = nullptr;
+    cudaStream_t stream = nullptr;
+    float* stats = nullptr;       // [30 mean, 30 std, 16 mean, 16 std]
+    float* bx = nullptr;          // training minibatch [batch][30]
+    float* by = nullptr;          // [batch][16]
+    int bcap = 0;
+    bool trained = false;
+    std::string err;
+};
+
+struct SurrBufs {                 // per-world-handle buffers of the surrogate step
+    float* x = nullptr;           // [A][32] normalised features
+    float* y = nullptr;           // [A][16] normalised outputs
+    float4* snap = nullptr;       // [5][A]
+    uint8_t* elig = nullptr;      // [A]
+    unsigned* words = nullptr;    // [0] audit error bits, [1] surrogate uses
+};
+
+
+static SurrBufs* surr_bufs(sf_ctx* h) {
+    if (h->surr) return static_cast<SurrBufs*>(h->surr);
+    const size_t A = (size_t)h->A;
+    SurrBufs* b = new SurrBufs();
+    bool ok = dalloc(h, &b->x, A * kSurrInLd) == SF_OK && dalloc(h, &b->y, A * kSurrOut) == SF_OK &&
+              dalloc(h, &b->snap, A * 5) == SF_OK && dalloc(h, &b->elig, A) == SF_OK &&
+              dalloc(h, &b->words, 2) == SF_OK;
+    if (!ok || cudaMemset(b->words, 0, 8) != cudaSuccess) { delete b; return nullptr; }
+    h->surr = b;
+    return b;
+}
+
 extern "C" {
 
 const char* sf_version(void) { return "sf 0.1 (sm_103a)"; }
@@ -673,8 +706,8 @@ sf_status sf_step_policy(sf_handle h, sf_mlp_handle policy, float dt, int subste
     return sf_step(h, h->act_buf, dt, substeps);
 }
 
-sf_status sf_graph_capture(sf_handle h, sf_mlp_handle policy, const float* d_actions, const uint8_t* d_reset_mask,
-                           float dt, int substeps, sf_graph_handle* out) {
+sf_status sf_graph_capture(sf_handle h, sf_mlp_handle policy, sf_surrogate_handle surrogate, const float* d_actions,
+                           const uint8_t* d_reset_mask, float dt, int substeps, sf_graph_handle* out) {
     if (!h || !out) return SF_ERR_INVALID_ARG;
     *out = nullptr;
     if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_graph_capture: no roads loaded");
@@ -686,6 +719,13 @@ sf_status sf_graph_capture(sf_handle h, sf_mlp_handle policy, const float* d_act
         sf_status s0 = sf_mlp_forward_on(policy, h->stream, h->out.obs, SF_OBS_DIM, h->A, h->act_buf, 3);
         if (s0 != SF_OK) return fail(h, s0, "sf_graph_capture: policy forward");
     }
+    if (surrogate) {
+        SurrBufs* b = surr_bufs(h);
+        if (!b || sf_mlp_reserve(surrogate->mlp, h->A) != SF_OK)
+            return fail(h, SF_ERR_OOM, "sf_graph_capture: surrogate buffers");
+        sf_status s0 = sf_mlp_forward_on(surrogate->mlp, h->stream, b->x, kSurrInLd, h->A, b->y, kSurrOut);
+        if (s0 != SF_OK) return fail(h, s0, "sf_graph_capture: surrogate forward");
+    }
     SF_CUDA(h, cudaStreamSynchronize(h->stream));
     sf_graph* g = new sf_graph();
     g->h = h;
@@ -696,8 +736,11 @@ sf_status sf_graph_capture(sf_handle h, sf_mlp_handle policy, const float* d_act
             st = sf_mlp_forward_on(policy, h->stream, h->out.obs, SF_OBS_DIM, h->A, h->act_buf, 3);
             g->launches += 1;
         }
-        if (st == SF_OK) st = sf_step(h, policy ? h->act_buf : d_actions, dt, substeps);
-        g->launches += 1;
+        const float* acts = policy ? h->act_buf : d_actions;
+        if (st == SF_OK) {
+            if (surrogate) { st = sf_step_surrogate(h, surrogate, acts, dt, substeps, 0); g->launches += 5; }
+            else { st = sf_step(h, acts, dt, substeps); g->launches += 1; }
+        }
         if (st == SF_OK && d_reset_mask) { st = sf_reset(h, d_reset_mask); g->launches += 1; }
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
@@ -735,30 +778,6 @@ sf_status sf_graph_destroy(sf_graph_handle g) {
 }
 
 // ====================================================================== dynamics surrogate
-struct sf_surrogate {
-    sf_mlp_handle mlp = nullptr;
-    cudaStream_t stream = nullptr;
-    float* stats = nullptr;       // [30 mean, 30 std, 16 mean, 16 std]
-    float* bx = nullptr;          // training minibatch [batch][30]
-    float* by = nullptr;          // [batch][16]
-    int bcap = 0;
-    bool trained = false;
-    std::string err;
-};
-
-namespace {
-
-struct SurrBufs {                 // per-world-handle buffers of the surrogate step
-    float* x = nullptr;           // [A][32] normalised features
-    float* y = nullptr;           // [A][16] normalised outputs
-    float4* snap = nullptr;       // [5][A]
-    uint8_t* elig = nullptr;      // [A]
-    unsigned* words = nullptr;    // [0] audit error bits, [1] surrogate uses
-};
-
-}  // namespace
-
-static SurrBufs* surr_bufs(sf_ctx* h);
 
 sf_status sf_surrogate_create(void* cuda_stream, sf_surrogate_handle* out) {
     if (!out) return SF_ERR_INVALID_ARG;
@@ -928,14 +947,3 @@ sf_status sf_sync(sf_handle h) {
 
 }  // extern "C"
 
-static SurrBufs* surr_bufs(sf_ctx* h) {
-    if (h->surr) return static_cast<SurrBufs*>(h->surr);
-    const size_t A = (size_t)h->A;
-    SurrBufs* b = new SurrBufs();
-    bool ok = dalloc(h, &b->x, A * kSurrInLd) == SF_OK && dalloc(h, &b->y, A * kSurrOut) == SF_OK &&
-              dalloc(h, &b->snap, A * 5) == SF_OK && dalloc(h, &b->elig, A) == SF_OK &&
-              dalloc(h, &b->words, 2) == SF_OK;
-    if (!ok || cudaMemset(b->words, 0, 8) != cudaSuccess) { delete b; return nullptr; }
-    h->surr = b;
-    return b;
-}

@@ -80,7 +80,7 @@ def lib():
             "sf_gemm_bf16": ([vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int, C.c_int,
                               C.c_int, vp, vp], i32),
             "sf_step_policy": ([vp, vp, f32, C.c_int], i32),
-            "sf_graph_capture": ([vp, vp, vp, vp, f32, C.c_int, vp], i32), "sf_graph_launch": ([vp], i32),
+            "sf_graph_capture": ([vp, vp, vp, vp, vp, f32, C.c_int, vp], i32), "sf_graph_launch": ([vp], i32),
             "sf_graph_destroy": ([vp], i32),
             "sf_surrogate_create": ([vp, vp], i32), "sf_surrogate_destroy": ([vp], i32),
             "sf_surrogate_collect": ([vp, vp, vp, f32, C.c_int, vp, vp, C.c_uint64, vp], i32),
@@ -340,10 +340,10 @@ def sf_step_policy(h, policy, dt=1.0 / 30.0, substeps=4):
     _check(lib().sf_step_policy(h, policy, float(dt), int(substeps)), h)
 
 
-def sf_graph_capture(h, policy=None, d_actions=None, d_reset_mask=None, dt=1.0 / 30.0, substeps=4):
+def sf_graph_capture(h, policy=None, d_actions=None, d_reset_mask=None, dt=1.0 / 30.0, substeps=4, surrogate=None):
     g = C.c_void_p()
-    _check(lib().sf_graph_capture(h, policy, _ptr(d_actions), _ptr(d_reset_mask), float(dt), int(substeps),
-                                  C.byref(g)), h)
+    _check(lib().sf_graph_capture(h, policy, surrogate, _ptr(d_actions), _ptr(d_reset_mask), float(dt),
+                                  int(substeps), C.byref(g)), h)
     return g
 
 

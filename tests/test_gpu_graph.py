@@ -71,3 +71,26 @@ def test_graph_replay_matches_individual_calls(with_policy, with_reset):
     sf.sf_graph_destroy(g)
     if pol is not None:
         sf.sf_mlp_destroy(pol)
+
+
+def test_graph_with_surrogate_matches_individual_calls():
+    sc = synth.procedural_scene(6, 8, seed_base=820)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    W1, W2 = world(sc, s1), world(sc, s2)
+    sur = sf.sf_surrogate_create(s1)
+    acts = torch.as_tensor(synth.ou_actions(W1.A, 8, seed=2), device="cuda")
+    act_buf = torch.zeros((W1.A, 3), device="cuda")
+    torch.cuda.synchronize()
+    g = sf.sf_graph_capture(W1.h, d_actions=act_buf, surrogate=sur)
+    for t in range(8):
+        with torch.cuda.stream(s1):
+            act_buf.copy_(acts[t])
+            sf.sf_graph_launch(g)
+        with torch.cuda.stream(s2):
+            sf.sf_step_surrogate(W2.h, sur, acts[t])
+    F1, I1, _ = sf.sf_get_state(W1.h)
+    F2, I2, _ = sf.sf_get_state(W2.h)
+    assert np.array_equal(F1, F2) and np.array_equal(I1, I2)
+    assert sf.sf_surrogate_audit(W1.h)[1] == sf.sf_surrogate_audit(W2.h)[1] > 0
+    sf.sf_graph_destroy(g)
+    sf.sf_surrogate_destroy(sur)
