@@ -116,11 +116,13 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- our arm
-def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, policy_seed=None, surrogate=None):
+def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, policy_seed=None, surrogate=None,
+                 pack=0):
     """Time `steps` replays of the captured step graph (policy forward + step
     when policy_seed is given) on the workload `name`."""
     scene = make_scene(name, rank)
-    W = sf.World(scene, seed=4242 + rank, flags=sf.FLAG_AUTO_RESET, warps_per_block=nw, stream=stream)
+    W = sf.World(scene, seed=4242 + rank, flags=sf.FLAG_AUTO_RESET, warps_per_block=nw, stream=stream,
+                 pack_agents=pack)
     A = W.A
     dev = torch.device("cuda")
     policy = sf.init_policy(seed=policy_seed, stream=stream) if policy_seed is not None else None
@@ -236,7 +238,7 @@ def main_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
         res[name] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream, e2e=not args.skip_e2e,
-                                 nw=args.nw)
+                                 nw=args.nw, pack=args.pack)
     surr = None
     surr_info = None
     if not args.only and not args.skip_surrogate:
@@ -255,12 +257,12 @@ def main_ours(args):
             if world > 1:
                 dist.barrier()
             res[name + "+surrogate"] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream,
-                                                    e2e=False, nw=args.nw, surrogate=surr)
+                                                    e2e=False, nw=args.nw, surrogate=surr, pack=args.pack)
     if not args.only and not args.skip_policy:
         if world > 1:
             dist.barrier()
         res["4096x16+policy"] = run_workload("4096x16", args.steps, args.warmup, rank, torch, sf, stream, e2e=False,
-                                             nw=args.nw, policy_seed=4000, surrogate=surr)
+                                             nw=args.nw, policy_seed=4000, surrogate=surr, pack=args.pack)
     if surr is not None:
         sf.sf_surrogate_destroy(surr)
     clk = clocks.stop()
@@ -400,11 +402,12 @@ def main():
     ap.add_argument("--only", default=None, choices=list(WORKLOADS), help="profiling: run one workload only")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling: no end-to-end leg")
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
-    ap.add_argument("--nw", type=int, default=0, help="warps per world (1, 2, 4, 8; 0 = autotuned)")
+    ap.add_argument("--nw", type=int, default=0, help="warps per block (1, 2, 4, 8; 0 = autotuned)")
+    ap.add_argument("--pack", type=int, default=0, help="with --nw: agents per packed block (0 = one world)")
     ap.add_argument("--skip-policy", action="store_true", help="no 4096x16 + policy leg")
     ap.add_argument("--skip-surrogate", action="store_true", help="no surrogate training / legs")
     ap.add_argument("--surr-rows", type=int, default=10_000_000, help="surrogate training transitions")
-    ap.add_argument("--surr-steps", type=int, default=8000, help="surrogate Adam steps")
+    ap.add_argument("--surr-steps", type=int, default=60000, help="surrogate Adam steps")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -102,7 +102,10 @@ typedef struct {
     uint64_t seed;           /* seed of the counter-based reset draws                 */
     int32_t flags;           /* SF_FLAG_* bits                                        */
     int32_t warps_per_block; /* world-kernel launch shape; 0 = library default        */
-    int32_t reserved[8];     /* must be zero                                          */
+    int32_t pack_agents;     /* 0: one world per thread block; 1..32: consecutive     *
+                              * worlds share a block while their agents total at most *
+                              * this many (worlds with more agents get a block alone) */
+    int32_t reserved[7];     /* must be zero                                          */
 } sf_config;
 
 /* Worlds as CSR (host memory, read during sf_load_roads only).
@@ -144,7 +147,7 @@ typedef struct {
 /* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
  * (NULL = legacy default stream) on which every call of this handle enqueues
  * its work.  *out receives the handle.  Errors: SF_ERR_INVALID_ARG (NULL out,
- * nonzero reserved), SF_ERR_CUDA (no usable device). */
+ * nonzero reserved, pack_agents outside 0..32), SF_ERR_CUDA (no usable device). */
 sf_status sf_create(const sf_config* cfg, void* cuda_stream, sf_handle* out);
 
 /* Release every device and host resource of h (synchronous).  NULL is a no-op. */
@@ -169,15 +172,19 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* h_roads);
  * substeps outside 1..64), SF_ERR_CUDA (launch failure). */
 sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps);
 
-/* Autotuner: time each launch shape of the world kernel (1, 2, 4 or 8 warps
- * cooperating on one world) over `iters` steps with the given actions and keep
- * the fastest for this handle.  The agent state and every output are saved
- * before and restored after the trials, so the call does not advance the
- * simulation.  Synchronous; uses a temporary device buffer the size of the
- * state and outputs.  *out_warps (may be NULL) receives the choice and
- * out_ms (may be NULL, [4]) the mean step time of each shape in ms.
+/* Autotuner: time each launch shape of the world kernel over `iters` steps
+ * with the given actions and keep the fastest for this handle.  Shapes are
+ * (warps per block in 1, 2, 4, 8) x (world packing off, on): shape s has
+ * 1 << (s & 3) warps and packing (s >= 4) groups consecutive worlds into
+ * blocks of at most pack_agents agents (32 when the handle was created with
+ * 0).  The agent state and every output are saved before and restored after
+ * the trials, so the call does not advance the simulation.  Synchronous; uses
+ * a temporary device buffer the size of the state and outputs.
+ * out_shape (may be NULL, [2]) receives the chosen warps per block and
+ * pack_agents (0 = no packing); out_ms (may be NULL, [8]) the mean step time
+ * of each shape in ms.
  * Errors: SF_ERR_STATE (no roads), SF_ERR_INVALID_ARG (iters < 1), SF_ERR_OOM. */
-sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substeps, int iters, int32_t* out_warps,
+sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substeps, int iters, int32_t* out_shape,
                       float* out_ms);
 
 /* Copy the observations, rewards, done flags and event bits of the last step

@@ -41,6 +41,9 @@ struct sf_ctx {
     uint8_t* all_mask = nullptr;
     float* act_buf = nullptr;   // [A][3] actions written by an attached policy
     void* surr = nullptr;       // surrogate step buffers (allocated on first use)
+    int4* packs_single = nullptr;   // one world per block
+    int4* packs_packed = nullptr;   // consecutive worlds up to pack_cap agents per block
+    int n_single = 0, n_packed = 0, pack_cap = 32;
     bool loaded = false;
 };
 
@@ -92,6 +95,8 @@ void free_all(sf_ctx* h) {
     h->all_mask = nullptr;
     h->act_buf = nullptr;
     h->surr = nullptr;
+    h->packs_single = h->packs_packed = nullptr;
+    h->n_single = h->n_packed = 0;
     h->loaded = false;
     h->W = h->A = h->NP = 0;
 }
@@ -103,6 +108,9 @@ WorldArgs make_args(sf_ctx* h) {
     a.out = h->out;
     a.num_worlds = h->W;
     a.num_agents = h->A;
+    const bool packed = h->cfg.pack_agents > 0;
+    a.packs = packed ? h->packs_packed : h->packs_single;
+    a.num_packs = packed ? h->n_packed : h->n_single;
     a.flags = h->cfg.flags;
     a.seed = h->cfg.seed;
     a.substeps = 1;
@@ -113,6 +121,23 @@ WorldArgs make_args(sf_ctx* h) {
 int wpb_of(const sf_ctx* h) {
     int w = h->cfg.warps_per_block;
     return (w == 1 || w == 2 || w == 4 || w == 8) ? w : 4;
+}
+
+// blocks of the world kernel: runs of consecutive non-empty worlds whose agents
+// total at most `cap` (cap 0: one world per block)
+std::vector<int4> make_packs(const std::vector<int4>& world, int cap) {
+    std::vector<int4> packs;
+    int4 cur = make_int4(0, 0, 0, 0);
+    bool open = false;
+    for (int w = 0; w < (int)world.size(); ++w) {
+        const int n = world[w].y;
+        if (n <= 0) { if (open) packs.push_back(cur); open = false; continue; }
+        if (open && (cap <= 0 || cur.w + n > cap)) { packs.push_back(cur); open = false; }
+        if (!open) { cur = make_int4(w, 1, world[w].x, n); open = true; }
+        else { cur.y += 1; cur.w += n; }
+    }
+    if (open) packs.push_back(cur);
+    return packs;
 }
 
 bool is_lane_type(int t) { return t == 1 || t == 2; }
@@ -165,8 +190,12 @@ sf_status sf_create(const sf_config* cfg, void* cuda_stream, sf_handle* out) {
     *out = nullptr;
     sf_config c{};
     if (cfg) c = *cfg;
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 7; ++i)
         if (c.reserved[i] != 0) { g_create_error = "sf_create: reserved fields must be zero"; return SF_ERR_INVALID_ARG; }
+    if (c.pack_agents < 0 || c.pack_agents > 32) {
+        g_create_error = "sf_create: pack_agents must be 0..32";
+        return SF_ERR_INVALID_ARG;
+    }
     int dev = 0, count = 0;
     cudaError_t e = cudaGetDeviceCount(&count);
     if (e != cudaSuccess || count == 0) {
@@ -235,7 +264,7 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     std::vector<DevGrid> grid(W);
     std::vector<int32_t> cell_off, sidx(NP);
     std::vector<float4> eall;
-    std::vector<float4> spt(NP);
+    std::vector<float4> sseg(NP);
     std::vector<uint32_t> smeta(NP);
     auto in_box = [](double x, double y) { return std::fabs(x) <= 100.0 && std::fabs(y) <= 100.0; };
     for (int w = 0; w < W; ++w) {
@@ -313,7 +342,8 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
         for (int i = 0; i <= ncell; ++i) cell_off.push_back(q0 + cnt[i]);
         for (int k = q0; k < q1; ++k) {   // stable: input order within a cell
             int slot = q0 + cnt[cy_of(r->py[k]) * nx + cx_of(r->px[k])]++;
-            spt[slot] = pt[k];
+            const bool nxt = (pmeta[k] & sfk::kPtSegNext) != 0;
+            sseg[slot] = make_float4(r->px[k], r->py[k], r->px[nxt ? k + 1 : k], r->py[nxt ? k + 1 : k]);
             smeta[slot] = pmeta[k];
             sidx[slot] = k;
         }
@@ -348,14 +378,14 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     SF_ALLOC(dpmeta, uint32_t, (size_t)NP + 1);
     SF_ALLOC(dpend, int32_t, (size_t)NP + 1);
     SF_ALLOC(dcands, int32_t, cands.size() + 1);
-    DevGrid* dgrid; int32_t *dcoff, *dsidx; float4 *dspt, *deall; uint32_t* dsmeta;
+    DevGrid* dgrid; int32_t *dcoff, *dsidx; float4 *dsseg, *deall; uint32_t* dsmeta;
     SF_ALLOC(dgrid, DevGrid, (size_t)W);
     SF_ALLOC(dcoff, int32_t, cell_off.size());
-    SF_ALLOC(dspt, float4, (size_t)NP + 1);
+    SF_ALLOC(dsseg, float4, (size_t)NP + 1);
     SF_ALLOC(dsmeta, uint32_t, (size_t)NP + 1);
     SF_ALLOC(dsidx, int32_t, (size_t)NP + 1);
     SF_ALLOC(deall, float4, eall.size() + 1);
-    h->rd = DevRoads{dworld, dcand, dpt, dpmeta, dpend, dcands, dgrid, dcoff, dspt, dsmeta, dsidx, deall};
+    h->rd = DevRoads{dworld, dcand, dpt, dpmeta, dpend, dcands, dgrid, dcoff, dsseg, dsmeta, dsidx, deall};
     float *obs, *reward, *drac; uint8_t* done; uint32_t* events; int32_t *lane_seg, *knn_pts, *knn_agents;
     unsigned int* err_word; float* hint;
     SF_ALLOC(obs, float, Aa * SF_OBS_DIM);
@@ -372,6 +402,10 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     SF_ALLOC(h->place_buf, float, Aa * 6);
     SF_ALLOC(h->all_mask, uint8_t, Aa);
     SF_ALLOC(h->act_buf, float, Aa * 3);
+    h->pack_cap = h->cfg.pack_agents > 0 ? h->cfg.pack_agents : 32;
+    const std::vector<int4> ps = make_packs(world, 0), pp = make_packs(world, h->pack_cap);
+    SF_ALLOC(h->packs_single, int4, ps.size());
+    SF_ALLOC(h->packs_packed, int4, pp.size());
 #undef SF_ALLOC
 
     std::vector<uint32_t> meta_h(Aa);
@@ -391,7 +425,7 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     up(dcands, cands.data(), cands.size() * sizeof(int32_t));
     up(dgrid, grid.data(), grid.size() * sizeof(DevGrid));
     up(dcoff, cell_off.data(), cell_off.size() * 4);
-    up(dspt, spt.data(), spt.size() * sizeof(float4));
+    up(dsseg, sseg.data(), sseg.size() * sizeof(float4));
     up(dsmeta, smeta.data(), smeta.size() * 4);
     up(dsidx, sidx.data(), sidx.size() * 4);
     up(deall, eall.data(), eall.size() * sizeof(float4));
@@ -404,6 +438,10 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     if (e == cudaSuccess && Aa) e = cudaMemset(knn_pts, 0xFF, Aa * SF_L_POINTS * 4);
     if (e == cudaSuccess && Aa) e = cudaMemset(knn_agents, 0xFF, Aa * SF_K_AGENTS * 4);
     if (e == cudaSuccess && Aa) e = cudaMemset(h->all_mask, 1, Aa);
+    up(h->packs_single, ps.data(), ps.size() * sizeof(int4));
+    up(h->packs_packed, pp.data(), pp.size() * sizeof(int4));
+    h->n_single = (int)ps.size();
+    h->n_packed = (int)pp.size();
     if (e != cudaSuccess) { free_all(h); return cuda_fail(h, e, "sf_load_roads upload"); }
     h->W = W; h->A = A; h->NP = NP;
     h->loaded = true;
@@ -425,7 +463,7 @@ sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps) {
     return SF_OK;
 }
 
-sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substeps, int iters, int32_t* out_warps,
+sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substeps, int iters, int32_t* out_shape,
                       float* out_ms) {
     if (!h) return SF_ERR_INVALID_ARG;
     if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_autotune: no roads loaded");
@@ -455,40 +493,46 @@ sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substep
         }
         return r;
     };
-    const int shapes[4] = {1, 2, 4, 8};
-    float ms[4] = {0, 0, 0, 0};
-    int best = wpb_of(h);
+    float ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int best = wpb_of(h), best_pack = h->cfg.pack_agents;
     float best_ms = 0.f;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     e = copy_all(true);
     if (e == cudaSuccess) e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    const int saved = h->cfg.warps_per_block;
-    for (int si = 0; si < 4 && e == cudaSuccess; ++si) {
-        h->cfg.warps_per_block = shapes[si];
+    const int saved = h->cfg.warps_per_block, saved_pack = h->cfg.pack_agents;
+    for (int si = 0; si < 8 && e == cudaSuccess; ++si) {
+        const int nw = 1 << (si & 3), pack = si >= 4 ? h->pack_cap : 0;
+        h->cfg.warps_per_block = nw;
+        h->cfg.pack_agents = pack;
         e = copy_all(false);
         WorldArgs a = make_args(h);
         a.actions = d_actions;
         a.h = dt / (float)substeps;
         a.substeps = substeps;
-        if (e == cudaSuccess) e = sf_launch_world(kModeStep, a, shapes[si], h->stream);   // warm
+        if (e == cudaSuccess) e = sf_launch_world(kModeStep, a, nw, h->stream);   // warm
         if (e == cudaSuccess) e = cudaEventRecord(t0, h->stream);
-        for (int it = 0; it < iters && e == cudaSuccess; ++it) e = sf_launch_world(kModeStep, a, shapes[si], h->stream);
+        for (int it = 0; it < iters && e == cudaSuccess; ++it) e = sf_launch_world(kModeStep, a, nw, h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(t1, h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(t1);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[si], t0, t1);
         ms[si] /= (float)iters;
-        if (e == cudaSuccess && (si == 0 || ms[si] < best_ms)) { best_ms = ms[si]; best = shapes[si]; }
+        if (e == cudaSuccess && (si == 0 || ms[si] < best_ms)) { best_ms = ms[si]; best = nw; best_pack = pack; }
     }
     if (e == cudaSuccess) e = copy_all(false);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     cudaFree(snap);
-    if (e != cudaSuccess) { h->cfg.warps_per_block = saved; return cuda_fail(h, e, "sf_autotune"); }
+    if (e != cudaSuccess) {
+        h->cfg.warps_per_block = saved;
+        h->cfg.pack_agents = saved_pack;
+        return cuda_fail(h, e, "sf_autotune");
+    }
     h->cfg.warps_per_block = best;
-    if (out_warps) *out_warps = best;
-    if (out_ms) for (int i = 0; i < 4; ++i) out_ms[i] = ms[i];
+    h->cfg.pack_agents = best_pack;
+    if (out_shape) { out_shape[0] = best; out_shape[1] = best_pack; }
+    if (out_ms) for (int i = 0; i < 8; ++i) out_ms[i] = ms[i];
     return SF_OK;
 }
 

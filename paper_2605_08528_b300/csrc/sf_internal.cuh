@@ -127,7 +127,8 @@ struct DevRoads {
     const int32_t* cands;   // spawn candidate point indices
     const DevGrid* grid;    // per world
     const int32_t* cell_off;// per world nx*ny+1 offsets into the sorted arrays
-    const float4* spt;      // points sorted by cell
+    const float4* sseg;     // points sorted by cell as segment records (x, y, next x, next y);
+                            // (x, y, x, y) where the point starts no segment
     const uint32_t* smeta;  // their meta
     const int32_t* sidx;    // their input-order index
     const float4* eseg;     // every edge segment of a world (ax, ay, bx, by), at grid.eoff
@@ -152,6 +153,8 @@ struct WorldArgs {
     DevState st;
     DevRoads rd;
     DevOutputs out;
+    const int4* packs;      // (first world, worlds, first agent, agents) per thread block
+    int num_packs;
     const float* actions;   // [A][3]   (step mode)
     const uint8_t* mask;    // [A]      (reset mode)
     int num_worlds;

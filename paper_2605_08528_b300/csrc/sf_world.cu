@@ -372,12 +372,13 @@ __device__ __forceinline__ void publish(Exch& E, int lane, const Agent& A, float
 }
 
 // K nearest alive other agents (lexicographic (d^2, index) order); local lane ids
-__device__ __forceinline__ void knn_agents(const Exch& E, int n, int lane, uint32_t alive_bits, float px, float py,
-                                           int nb[kK]) {
+// over the slots [base, base + n) of the lane's own world
+__device__ __forceinline__ void knn_agents(const Exch& E, int base, int n, int lane, uint32_t alive_bits, float px,
+                                           float py, int nb[kK]) {
     float key[kK];
 #pragma unroll
     for (int t = 0; t < kK; ++t) { key[t] = kInf; nb[t] = -1; }
-    for (int j = 0; j < n; ++j) {
+    for (int j = base; j < base + n; ++j) {
         if (j == lane || !((alive_bits >> j) & 1u)) continue;
         float dx = E.px[j] - px, dy = E.py[j] - py;
         float d2 = dx * dx + dy * dy;
@@ -560,34 +561,9 @@ __device__ __forceinline__ Rows rows_covering(const DevGrid& g, float qx, float 
     return w;
 }
 
-// nearest driving-lane segment (App. G), exact: segments whose start point
-// lies in the square of half-size R + 3 m contain every segment within R (no
-// segment is longer than 3 m); R grows until a segment within R is found.
-__device__ Lane coop_nearest_lane(const DevRoads& rd, const DevGrid& g, float qx, float qy, float gx, float gy,
-                                  float R, int lane) {
-    unsigned long long best = kKeyInf;
-    for (;;) {
-        const Rows w = rows_covering(g, qx, qy, R + kSegReach);
-        const float lim = w.all ? kInf : R * R * (1.f - 1e-5f);
-        best = kKeyInf;
-        if (w.cx0 <= w.cx1)
-            for (int cy = w.cy0; cy <= w.cy1; ++cy) {
-                const int row = g.cbase + cy * g.nx;
-                const int s = __ldg(&rd.cell_off[row + w.cx0]), e = __ldg(&rd.cell_off[row + w.cx1 + 1]);
-                for (int i = s + lane; i < e; i += 32) {
-                    const uint32_t m = __ldg(&rd.smeta[i]);
-                    if ((m & (kPtSegNext | kPtLane)) != (kPtSegNext | kPtLane)) continue;
-                    const int k = __ldg(&rd.sidx[i]);
-                    const float4 a = __ldg(&rd.spt[i]);
-                    const float4 b = __ldg(&rd.pt[k + 1]);
-                    const float d2 = seg_dist2(a.x, a.y, b.x, b.y, qx, qy);
-                    if (d2 < lim) best = umin64(best, key_of(d2, k));
-                }
-            }
-        best = warp_min64(best);
-        if (best != kKeyInf || w.all) break;
-        R *= kGrow;
-    }
+// tangent, lateral offset and distance of the nearest lane segment from its key
+__device__ __forceinline__ Lane lane_of(const DevRoads& rd, unsigned long long best, float qx, float qy, float gx,
+                                        float gy) {
     Lane L;
     L.seg = key_idx(best);
     if (L.seg < 0) { L.dist = kInf; L.lat = 0.f; L.tx = L.ty = 0.f; return L; }
@@ -600,6 +576,54 @@ __device__ Lane coop_nearest_lane(const DevRoads& rd, const DevGrid& g, float qx
     if (tx * (gx - qx) + ty * (gy - qy) < 0.f) { tx = -tx; ty = -ty; lat = -lat; }
     L.dist = sqrtf(key_d2(best)); L.lat = lat; L.tx = tx; L.ty = ty;
     return L;
+}
+
+// nearest driving-lane segment (App. G), exact: a segment within D of q starts
+// inside the square of half-size D + 3 m around q (no segment is longer than
+// 3 m), so scanning the cells of the square of half-size S finds every lane
+// segment within S - 3; S grows until one is found.  On the first pass the
+// same scan runs the lane-forbidden test of the footprint's three circles
+// against the road-edge segments (App. G) when `forb` is given: the square
+// then also covers every edge segment that can touch a circle.
+__device__ Lane coop_nearest_lane(const DevRoads& rd, const DevGrid& g, float qx, float qy, float gx, float gy,
+                                  float R, int lane, bool* forb = nullptr, float hx = 1.f, float hy = 0.f) {
+    const float lim_f = (kCircR + kEdgeHalfWidth) * (kCircR + kEdgeHalfWidth);
+    float S = R + kSegReach;
+    if (forb) S = fmaxf(S, kCircD + kCircR + kEdgeHalfWidth + kSegReach);
+    bool edges = forb != nullptr, f = false;
+    unsigned long long best = kKeyInf;
+    for (;;) {
+        const Rows w = rows_covering(g, qx, qy, S);
+        const float Rl = S - kSegReach;
+        const float lim = w.all ? kInf : Rl * Rl * (1.f - 1e-5f);
+        best = kKeyInf;
+        if (w.cx0 <= w.cx1)
+            for (int cy = w.cy0; cy <= w.cy1; ++cy) {
+                const int row = g.cbase + cy * g.nx;
+                const int s = __ldg(&rd.cell_off[row + w.cx0]), e = __ldg(&rd.cell_off[row + w.cx1 + 1]);
+                for (int i = s + lane; i < e; i += 32) {
+                    const uint32_t m = __ldg(&rd.smeta[i]);
+                    if (!(m & kPtSegNext)) continue;
+                    if (m & kPtLane) {
+                        const float4 sg = __ldg(&rd.sseg[i]);
+                        const float d2 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
+                        if (d2 < lim) best = umin64(best, key_of(d2, __ldg(&rd.sidx[i])));
+                    } else if (edges && (m & kPtEdge)) {
+                        const float4 sg = __ldg(&rd.sseg[i]);
+#pragma unroll
+                        for (int c = -1; c <= 1; ++c) {
+                            const float cx_ = qx + (float)c * kCircD * hx, cy_ = qy + (float)c * kCircD * hy;
+                            if (seg_dist2(sg.x, sg.y, sg.z, sg.w, cx_, cy_) < lim_f) f = true;
+                        }
+                    }
+                }
+            }
+        best = warp_min64(best);
+        if (edges) { *forb = __any_sync(kFull, f); edges = false; }
+        if (best != kKeyInf || w.all) break;
+        S = Rl * kGrow + kSegReach;
+    }
+    return lane_of(rd, best, qx, qy, gx, gy);
 }
 
 // the 32 nearest road points (all types), exact; lane t returns the t-th key.
@@ -622,7 +646,7 @@ __device__ unsigned long long coop_knn32(const DevRoads& rd, const DevGrid& g, f
                     const int i = base + lane;
                     unsigned long long key = kKeyInf;
                     if (i < e) {
-                        const float4 P = __ldg(&rd.spt[i]);
+                        const float4 P = __ldg(&rd.sseg[i]);
                         const float dx = P.x - qx, dy = P.y - qy;
                         key = key_of(dx * dx + dy * dy, __ldg(&rd.sidx[i]));
                         if (key >= thr) key = kKeyInf;
@@ -653,32 +677,10 @@ __device__ unsigned long long coop_knn32(const DevRoads& rd, const DevGrid& g, f
     return run;
 }
 
-// road edges seen from one agent: lane-forbidden (any of the three circles
-// within r + half width of an edge segment, App. G) and the time for the
-// constant-velocity ray to reach the nearest edge segment within 40 m
-__device__ void coop_edges(const DevRoads& rd, const DevGrid& g, float px, float py, float hx, float hy, float vx,
-                           float vy, int lane, bool& forb, float& tedge) {
-    const float lim2 = (kCircR + kEdgeHalfWidth) * (kCircR + kEdgeHalfWidth);
-    // circle centres lie within kCircD of p, a touching segment within lim of a centre
-    const Rows w = rows_covering(g, px, py, kCircD + kCircR + kEdgeHalfWidth + kSegReach);
-    bool f = false;
-    if (w.cx0 <= w.cx1)
-        for (int cy = w.cy0; cy <= w.cy1; ++cy) {
-            const int row = g.cbase + cy * g.nx;
-            const int s = __ldg(&rd.cell_off[row + w.cx0]), e = __ldg(&rd.cell_off[row + w.cx1 + 1]);
-            for (int i = s + lane; i < e; i += 32) {
-                const uint32_t m = __ldg(&rd.smeta[i]);
-                if ((m & (kPtSegNext | kPtEdge)) != (kPtSegNext | kPtEdge)) continue;
-                const float4 a = __ldg(&rd.spt[i]);
-                const float4 b = __ldg(&rd.pt[__ldg(&rd.sidx[i]) + 1]);
-#pragma unroll
-                for (int c = -1; c <= 1; ++c) {
-                    float cx_ = px + (float)c * kCircD * hx, cy_ = py + (float)c * kCircD * hy;
-                    if (seg_dist2(a.x, a.y, b.x, b.y, cx_, cy_) < lim2) f = true;
-                }
-            }
-        }
-    forb = __any_sync(kFull, f);
+// time for the constant-velocity ray from an agent to reach the nearest road
+// edge segment within 40 m (App. G)
+__device__ float coop_edge_ray(const DevRoads& rd, const DevGrid& g, float px, float py, float vx, float vy,
+                               int lane) {
     // ray p + v t against every edge segment; the acceptance tests t >= 0,
     // 0 <= s <= 1 and |v| t <= 40 m are evaluated multiplied through by the
     // denominator (sign-aware), and only accepted hits divide.  A segment whose
@@ -698,7 +700,7 @@ __device__ void coop_edges(const DevRoads& rd, const DevGrid& g, float px, float
                                   : (nt <= 0.f && ns <= 0.f && ns >= den && speed * nt >= kEdgeHorizon * den);
         if (ok) t_best = fminf(t_best, nt / den);
     }
-    tedge = warp_min(t_best);
+    return warp_min(t_best);
 }
 
 // ------------------------------------------------------------------ dynamics surrogate
@@ -844,13 +846,13 @@ __device__ void surr_apply(float4 p0, float4 q0, float4 v0, float4 w0, float4 s0
 }
 
 // gate of lane `lane` given the exchange area at the start of the step
-__device__ __forceinline__ bool surr_gate(const Exch& E, int n, int lane, uint32_t alive_bits, const Agent& A,
-                                          float dt) {
+__device__ __forceinline__ bool surr_gate(const Exch& E, int base, int n, int lane, uint32_t alive_bits,
+                                          const Agent& A, float dt) {
     if (!((alive_bits >> lane) & 1u)) return false;
     if (A.mu < kSurrMuMin) return false;
     if (A.vx * A.vx + A.vy * A.vy + A.vz * A.vz > kSurrVMax * kSurrVMax) return false;
     if (1.f - 2.f * (A.qx * A.qx + A.qy * A.qy) < kSurrCosTilt) return false;
-    for (int j = 0; j < n; ++j) {
+    for (int j = base; j < base + n; ++j) {
         if (j == lane || !((alive_bits >> j) & 1u)) continue;
         const float dvx = E.vx[j] - A.vx, dvy = E.vy[j] - A.vy;
         const float reach = kSurrReach + sqrtf(dvx * dvx + dvy * dvy) * dt;
@@ -870,29 +872,48 @@ struct AgentQ {
 }  // namespace
 
 // ====================================================================== the world kernel
-// One CTA per world.  Warp 0 owns the agents (lane l = agent l): physics,
-// events, respawns, neighbours, ego features, state.  All NW warps run the
-// road queries, one agent per warp at a time, and write the road-point block
-// of the observation with coalesced stores.
+// One CTA per pack: consecutive worlds holding at most 32 agents together (one
+// world per pack unless packing is enabled).  Warp 0 owns the agents (lane l =
+// slot l = agent a0 + l): physics, events, respawns, neighbours, ego
+// features, state; a lane only ever interacts with the slots of its own
+// world.  All NW warps run the road queries, one agent per warp at a time, and
+// write the road-point block of the observation with coalesced stores.
 template <int MODE, int NW>
 __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_kernel(const WorldArgs args) {
     __shared__ Exch E;
     __shared__ AgentQ Q[32];
     __shared__ unsigned long long kbuf[NW][64];
-    __shared__ unsigned s_alive, s_any;
+    __shared__ unsigned s_alive, s_any, s_act;
+    __shared__ int s_slot_w[32];                  // pack-local world of each slot
+    __shared__ int s_wid[32], s_wbase[32];        // per pack-local world: world id, first slot
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int w = blockIdx.x;
-    const int4 wd = __ldg(&args.rd.world[w]);
-    const int a0 = wd.x, n = wd.y;
-    if (n <= 0) return;                               // CTA-uniform
-    const DevGrid g = args.rd.grid[w];
+    const int4 pk = __ldg(&args.packs[blockIdx.x]);   // (first world, worlds, first agent, agents)
+    const int a0 = pk.z, m = pk.w;
+    if (m <= 0) return;                               // CTA-uniform
+    if (warp == 0) {
+        if (lane < pk.y) {
+            const int4 wd = __ldg(&args.rd.world[pk.x + lane]);
+            s_wid[lane] = pk.x + lane;
+            s_wbase[lane] = wd.x - a0;
+            for (int k = 0; k < wd.y; ++k) s_slot_w[wd.x - a0 + k] = lane;
+        }
+        __syncwarp();
+    }
     const DevState& st = args.st;
 
     // ---------------- warp 0: agent registers
-    const bool has = warp == 0 && lane < n;
+    const bool has = warp == 0 && lane < m;
     const int a = a0 + (has ? lane : 0);
+    int wl = 0, w = pk.x, base = 0, n = 0;            // the lane's world, its first slot and agent count
+    if (has) {
+        wl = s_slot_w[lane];
+        w = s_wid[wl];
+        base = s_wbase[wl];
+        n = __ldg(&args.rd.world[w]).y;
+    }
     Agent A;
     bool alive = false, respawn = false, parked_now = false, nonfin = false, done = false;
+    bool recompute = false, active_out = false;   // warp 0: neighbours recomputed / outputs written
     uint32_t ev = 0;
     float reward = 0.f, drac = 0.f, hx = 1.f, hy = 0.f;
     int nb[kK];
@@ -930,10 +951,10 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
                 publish(E, lane, A, sx_, sy_);
                 const uint32_t alive_bits = __ballot_sync(kFull, alive);
                 __syncwarp();
-                if (s == 0 && args.surr_mode != 0) gated = surr_gate(E, n, lane, alive_bits, A, args.h * args.substeps);
+                if (s == 0 && args.surr_mode != 0) gated = surr_gate(E, base, n, lane, alive_bits, A, args.h * args.substeps);
                 float fcx = 0.f, fcy = 0.f, tcz = 0.f;
                 if (alive) {
-                    for (int j = 0; j < n; ++j) {
+                    for (int j = base; j < base + n; ++j) {
                         if (j == lane || !((alive_bits >> j) & 1u)) continue;
                         const int lo = min(lane, j), hi = max(lane, j);
                         float fx, fy, tz;
@@ -983,16 +1004,16 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         }
         __syncthreads();
         // ---------------- road queries of the events (all warps, one agent at a time)
-        for (int j = warp; j < n; j += NW) {
+        for (int j = warp; j < m; j += NW) {
             if (!((s_alive >> j) & 1u)) continue;
+            const DevGrid g = args.rd.grid[s_wid[s_slot_w[j]]];
             float* hnt = args.out.hint + 2 * (size_t)(a0 + j);
             const float hl = hnt[1];
+            bool forb = false;
             const Lane L = coop_nearest_lane(args.rd, g, E.px[j], E.py[j], E.gx[j], E.gy[j],
-                                             hl > 0.f ? hl + kHintSlack : kLaneR0, lane);
+                                             hl > 0.f ? hl + kHintSlack : kLaneR0, lane, &forb, E.hx[j], E.hy[j]);
             if (lane == 0) hnt[1] = L.seg >= 0 ? L.dist : 0.f;
-            bool forb;
-            float tedge;
-            coop_edges(args.rd, g, E.px[j], E.py[j], E.hx[j], E.hy[j], E.vx[j], E.vy[j], lane, forb, tedge);
+            const float tedge = coop_edge_ray(args.rd, g, E.px[j], E.py[j], E.vx[j], E.vy[j], lane);
             if (lane == 0) {
                 AgentQ q;
                 q.seg = L.seg; q.dist = L.dist; q.lat = L.lat; q.tx = L.tx; q.ty = L.ty;
@@ -1018,7 +1039,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
                 }
                 if (fabsf(q.lat) > kOffroadLat || q.dist > kOffroadDist) { ev |= kEvOffroad; r -= kWOffroad; }
                 if (speed < kIdleSpeed) { ev |= kEvIdle; r -= kWIdle; }
-                knn_agents(E, n, lane, alive_bits, A.px, A.py, nb);
+                knn_agents(E, base, n, lane, alive_bits, A.px, A.py, nb);
                 float tmin = kTtcMax, dmax = 0.f;
 #pragma unroll
                 for (int t = 0; t < kK; ++t) {
@@ -1035,7 +1056,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
                 drac = dmax;
                 A.peak = fmaxf(A.peak, dmax);
                 bool collided = false;
-                for (int j = 0; j < n && !collided; ++j) {
+                for (int j = base; j < base + n && !collided; ++j) {
                     if (j == lane || !((alive_bits >> j) & 1u)) continue;
                     float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
                     if (dx * dx + dy * dy > kPairCull2) continue;
@@ -1073,14 +1094,15 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         const uint32_t rbits = __ballot_sync(kFull, respawn);
         if (rbits) {
             const unsigned long long seed = args.seed;
-            for (int l = 0; l < n; ++l) {
+            for (int l = 0; l < m; ++l) {
                 if (!((rbits >> l) & 1u)) continue;
                 const int ep = __shfl_sync(kFull, A.episode, l) + 1;
+                const bool same = __shfl_sync(kFull, wl, l) == wl;
                 float bx = 0.f, by = 0.f, bpsi = 0.f, bv = kSpawnVMin, bgx = kSpawnGoalMin, bgy = 0.f, bscore = -1.f;
-                const bool elig = alive && lane != l && !(lane > l && ((rbits >> lane) & 1u));
+                const bool elig = alive && same && lane != l && !(lane > l && ((rbits >> lane) & 1u));
                 for (int r = 0; r < kSpawnTries; ++r) {
                     float x = 0.f, y = 0.f, psi = 0.f, gx = 0.f, gy = 0.f, v0 = 0.f;
-                    if (lane == l) spawn_candidate(args.rd, w, a0 + l, l, ep, r, seed, x, y, psi, gx, gy, v0);
+                    if (lane == l) spawn_candidate(args.rd, w, a, l - base, ep, r, seed, x, y, psi, gx, gy, v0);
                     x = __shfl_sync(kFull, x, l);
                     y = __shfl_sync(kFull, y, l);
                     float d2 = kInf;
@@ -1101,20 +1123,28 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
                 __syncwarp();
             }
         }
-        const bool changed = (MODE != kModeStep) || __ballot_sync(kFull, respawn || parked_now) != 0u;
+        // per world (never per pack, so that packing changes no result): a world
+        // with a respawn or a parked agent republishes and recomputes its
+        // neighbours; a reset leaves the worlds without a masked agent untouched
+        const unsigned chg = __ballot_sync(kFull, respawn || parked_now);
+        const uint32_t wmask = n >= 32 ? 0xFFFFFFFFu : (((1u << n) - 1u) << base);
+        const bool wchanged = (chg & wmask) != 0u;
+        recompute = (MODE != kModeStep) || wchanged;
+        const bool active = (MODE != kModeReset) || wchanged;
+        active_out = active;
         heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
-        if (changed) {
-            __syncwarp();
-            publish(E, lane, A, hx, hy);
-        }
-        const unsigned ab = __ballot_sync(kFull, alive);
-        if (lane == 0) { s_alive = ab; s_any = changed ? 1u : 0u; }
-        if (lane < n && (MODE != kModeStep || respawn)) Q[lane].need = 1;
+        __syncwarp();
+        if (recompute) publish(E, lane, A, hx, hy);
+        const unsigned ab = __ballot_sync(kFull, alive), act = __ballot_sync(kFull, active);
+        if (lane == 0) { s_alive = ab; s_act = act; }
+        if (lane < m && (MODE != kModeStep || respawn)) Q[lane].need = 1;
     }
     __syncthreads();
 
     // ---------------- road-point block of every observation (all warps)
-    for (int j = warp; j < n; j += NW) {
+    for (int j = warp; j < m; j += NW) {
+        if (!((s_act >> j) & 1u)) continue;
+        const DevGrid g = args.rd.grid[s_wid[s_slot_w[j]]];
         float* orow = args.out.obs + (size_t)(a0 + j) * kObsDim + kObsEgo + kK * kObsNbr;
         const bool al = (s_alive >> j) & 1u;
         int kp = -1;
@@ -1156,8 +1186,8 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
 
     // ---------------- neighbours, ego group, outputs, state (warp 0)
     if (warp != 0) return;
-    if (s_any) knn_agents(E, n, lane, s_alive, A.px, A.py, nb);
-    if (has) {
+    if (recompute) knn_agents(E, base, n, lane, s_alive, A.px, A.py, nb);
+    if (has && active_out) {
         float4* o4 = reinterpret_cast<float4*>(args.out.obs + (size_t)a * kObsDim);
         if (alive) {
             const AgentQ q = Q[lane];
@@ -1196,7 +1226,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
                     s[5] = sqrtf(vjx * vjx + vjy * vjy) / 10.f;
                     s[6] = dvx / 10.f;
                     s[7] = dvy / 10.f;
-                    s[8] = (s_any ? ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, pjx, pjy, hjx, hjy, vjx, vjy)
+                    s[8] = (recompute ? ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, pjx, pjy, hjx, hjy, vjx, vjy)
                                   : tt[2 * t2 + u]) / kTtcMax;
                     s[9] = 1.f;
                 }
@@ -1254,7 +1284,7 @@ __global__ void surr_gate_kernel(const WorldArgs args, float dt, uint8_t* __rest
     publish(E, lane, A, hx, hy);
     const uint32_t ab = __ballot_sync(kFull, alive);
     __syncwarp();
-    const bool g = surr_gate(E, n, lane, ab, A, dt);
+    const bool g = surr_gate(E, 0, n, lane, ab, A, dt);
     if (has) elig[a] = g ? 1 : 0;
 }
 
@@ -1334,16 +1364,16 @@ cudaError_t sf_launch_surr_collect(const WorldArgs& a, const float4* snap, const
 template <int MODE>
 static cudaError_t launch_mode(const WorldArgs& a, int nw, cudaStream_t s) {
     switch (nw) {
-        case 1: world_kernel<MODE, 1><<<a.num_worlds, 32, 0, s>>>(a); break;
-        case 2: world_kernel<MODE, 2><<<a.num_worlds, 64, 0, s>>>(a); break;
-        case 8: world_kernel<MODE, 8><<<a.num_worlds, 256, 0, s>>>(a); break;
-        default: world_kernel<MODE, 4><<<a.num_worlds, 128, 0, s>>>(a); break;
+        case 1: world_kernel<MODE, 1><<<a.num_packs, 32, 0, s>>>(a); break;
+        case 2: world_kernel<MODE, 2><<<a.num_packs, 64, 0, s>>>(a); break;
+        case 8: world_kernel<MODE, 8><<<a.num_packs, 256, 0, s>>>(a); break;
+        default: world_kernel<MODE, 4><<<a.num_packs, 128, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t sf_launch_world(int mode, const WorldArgs& a, int nw, cudaStream_t s) {
-    if (a.num_worlds <= 0) return cudaSuccess;
+    if (a.num_packs <= 0) return cudaSuccess;
     switch (mode) {
         case kModeStep: return launch_mode<kModeStep>(a, nw, s);
         case kModeReset: return launch_mode<kModeReset>(a, nw, s);

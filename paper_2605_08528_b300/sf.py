@@ -35,7 +35,7 @@ class SFError(RuntimeError):
 
 class sf_config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("flags", C.c_int32), ("warps_per_block", C.c_int32),
-                ("reserved", C.c_int32 * 8)]
+                ("pack_agents", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class sf_roads(C.Structure):
@@ -118,8 +118,8 @@ def sf_version() -> str:
     return lib().sf_version().decode()
 
 
-def sf_create(seed=0, flags=0, warps_per_block=0, stream=None):
-    cfg = sf_config(seed, flags, warps_per_block)
+def sf_create(seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0):
+    cfg = sf_config(seed, flags, warps_per_block, pack_agents)
     h = C.c_void_p()
     st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().sf_create(C.byref(cfg), C.c_void_p(st), C.byref(h)))
@@ -198,11 +198,12 @@ def sf_sync(h, allow=()):
 
 
 def sf_autotune(h, d_actions, dt=1.0 / 30.0, substeps=4, iters=20):
-    """Pick the fastest world-kernel launch shape; returns (warps per world, ms per shape 1/2/4/8)."""
-    best = C.c_int32()
-    ms = (C.c_float * 4)()
-    _check(lib().sf_autotune(h, _ptr(d_actions), float(dt), int(substeps), int(iters), C.byref(best), ms), h)
-    return int(best.value), list(ms)
+    """Pick the fastest world-kernel launch shape; returns ((warps per block, pack agents),
+    ms per shape: 1/2/4/8 warps unpacked, then 1/2/4/8 warps packed)."""
+    best = (C.c_int32 * 2)()
+    ms = (C.c_float * 8)()
+    _check(lib().sf_autotune(h, _ptr(d_actions), float(dt), int(substeps), int(iters), best, ms), h)
+    return (int(best[0]), int(best[1])), list(ms)
 
 
 def sf_num_agents(h) -> int:
@@ -217,11 +218,11 @@ def sf_num_worlds(h) -> int:
 class World:
     """A handle plus its roads, with torch views of the library-owned outputs."""
 
-    def __init__(self, scene, seed=0, flags=0, warps_per_block=0, stream=None):
+    def __init__(self, scene, seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0):
         import torch
         self.torch = torch
         self.scene = scene
-        self.h = sf_create(seed, flags, warps_per_block, stream)
+        self.h = sf_create(seed, flags, warps_per_block, stream, pack_agents)
         sf_load_roads(self.h, scene)
         self.A = sf_num_agents(self.h)
         self.W = sf_num_worlds(self.h)

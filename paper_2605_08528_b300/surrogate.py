@@ -12,7 +12,7 @@ import numpy as np
 from . import sf, synth
 
 
-def collect_and_train(scene, transitions=10_000_000, train_steps=8000, batch=4096, lr=2e-3, seed=1, stream=None,
+def collect_and_train(scene, transitions=10_000_000, train_steps=60000, batch=8192, lr=3e-3, seed=1, stream=None,
                       max_steps=100_000):
     """Collect up to `transitions` physics transitions of gated agents on `scene`
     (smooth random actions, automatic resets) and train a new surrogate.

@@ -193,10 +193,11 @@ def lane_tie(orc, scene, w, p):
     return len(best) > 1 and best[1] - best[0] < TIE
 
 
-@pytest.mark.parametrize("flags", [sf.FLAG_INVINCIBLE, 0, sf.FLAG_AUTO_RESET])
-def test_discrete_and_observation_parity(flags):
+@pytest.mark.parametrize("flags,pack", [(sf.FLAG_INVINCIBLE, 0), (0, 0), (sf.FLAG_AUTO_RESET, 0),
+                                        (sf.FLAG_AUTO_RESET, 32)])
+def test_discrete_and_observation_parity(flags, pack):
     sc = synth.procedural_scene(6, 16, seed_base=1100)
-    W = sf.World(sc, seed=9, flags=flags | sf.FLAG_RECORD_INDICES)
+    W = sf.World(sc, seed=9, flags=flags | sf.FLAG_RECORD_INDICES, pack_agents=pack)
     spawn_all(W)
     orc = O.Oracle(sc)
     oflags = (O.FLAG_INVINCIBLE if flags & sf.FLAG_INVINCIBLE else 0) | (
@@ -301,7 +302,8 @@ def test_reset_spawns_match_oracle():
 
 
 # ----------------------------------------------------------------------------- edge cases
-def test_ragged_and_degenerate_worlds():
+@pytest.mark.parametrize("pack", [0, 32, 20])
+def test_ragged_and_degenerate_worlds(pack):
     polys_a = synth.procedural_world(5)
     x = np.linspace(-90, 90, 181)
     straight = [(2, np.stack([x, np.full(181, -1.8)], 1)), (2, np.stack([x[::-1], np.full(181, 1.8)], 1)),
@@ -309,7 +311,7 @@ def test_ragged_and_degenerate_worlds():
     worlds = [polys_a, [], straight, polys_a, straight]
     counts = [32, 3, 1, 0, 17]          # a full warp, a world without roads, one agent, an empty world
     sc = synth._assemble(worlds, counts, np.zeros(sum(counts)), np.zeros(sum(counts)))
-    W = sf.World(sc, seed=3, flags=sf.FLAG_AUTO_RESET | sf.FLAG_RECORD_INDICES)
+    W = sf.World(sc, seed=3, flags=sf.FLAG_AUTO_RESET | sf.FLAG_RECORD_INDICES, pack_agents=pack)
     spawn_all(W)
     orc = O.Oracle(sc)
     F, I, _ = sf.sf_get_state(W.h)
@@ -340,6 +342,43 @@ def test_ragged_and_degenerate_worlds():
     ix = W.indices()
     a = 32
     assert ix["lane_seg"][a] == -1 and (ix["knn_pts"][a] == -1).all()
+
+
+def _packing_trace(sc, pack, nw, steps=12):
+    W = sf.World(sc, seed=13, flags=sf.FLAG_AUTO_RESET | sf.FLAG_RECORD_INDICES, warps_per_block=nw,
+                 pack_agents=pack)
+    spawn_all(W)
+    acts = synth.ou_actions(W.A, steps, seed=5)
+    trace = []
+    for t in range(steps):
+        sf.sf_step(W.h, dev(acts[t]))
+        sf.sf_reset(W.h, dev(synth.reset_mask(W.A, t, 0.2, seed=7)))
+        F, I, st = sf.sf_get_state(W.h)
+        assert st == sf.SF_OK
+        obs, rew, done, ev = [x.cpu().numpy() for x in W.outputs()]
+        ix = W.indices()
+        trace.append(dict(F=F, I=I, obs=obs, rew=rew, done=done, ev=ev, lane=ix["lane_seg"], pts=ix["knn_pts"],
+                          agents=ix["knn_agents"]))
+    W.close()
+    return trace
+
+
+@pytest.mark.parametrize("nw", [1, 4, 8])
+def test_world_packing_is_bitwise_invisible(nw):
+    """Packing consecutive worlds into one thread block changes no arithmetic:
+    a ragged batch under random 20% reset masks gives bit-identical state,
+    observations, rewards, events and indices with and without packing (same
+    launch width)."""
+    sc = synth.ragged_scene(48, seed_base=2000, points_hi=1500)
+    ref = _packing_trace(sc, 0, nw)
+    for pack in (32, 11):
+        other = _packing_trace(sc, pack, nw)
+        for t, (a, b) in enumerate(zip(ref, other)):
+            for k in a:
+                if not np.array_equal(a[k], b[k], equal_nan=True):
+                    bad = np.argwhere(~((a[k] == b[k]) | (np.isnan(a[k]) & np.isnan(b[k]))))
+                    r = tuple(bad[0])
+                    raise AssertionError((pack, t, k, len(bad), r, a[k][r], b[k][r]))
 
 
 def test_invalid_roads_rejected():
@@ -427,6 +466,8 @@ def test_full_size_sampled_parity(worlds):
     W = sf.World(sc, seed=4000, flags=sf.FLAG_AUTO_RESET)
     spawn_all(W)
     acts = synth.ou_actions(W.A, 5, seed=6)
+    shape, _ = sf.sf_autotune(W.h, dev(acts[0]), iters=3)      # the launch shape the benchmark times
+    print("launch shape (warps, pack agents):", shape)
     for t in range(4):
         sf.sf_step(W.h, dev(acts[t]))
     F0, I0, _ = sf.sf_get_state(W.h)
