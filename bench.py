@@ -41,7 +41,12 @@ METRIC = "CASPS at 256x16 and 4096x16; surrogate vs plain physics at matched err
 FLUSH_BYTES = 256 << 20
 
 
+RAGGED = (1024, 2000, 0.2)   # worlds, road seed base, per-step reset fraction
+
+
 def make_scene(name: str, rank: int = 0):
+    if name == "ragged1024":
+        return synth.ragged_scene(RAGGED[0], seed_base=RAGGED[1] + rank * RAGGED[0])
     worlds, apw, seed, weather = WORKLOADS[name]
     return synth.procedural_scene(worlds, apw, seed_base=seed + rank * worlds, weather=weather,
                                   weather_seed=seed + 17 + rank)
@@ -117,7 +122,7 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- our arm
 def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, policy_seed=None, surrogate=None,
-                 pack=0):
+                 pack=0, reset_frac=0.0):
     """Time `steps` replays of the captured step graph (policy forward + step
     when policy_seed is given) on the workload `name`."""
     scene = make_scene(name, rank)
@@ -133,14 +138,22 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, p
         acts = torch.as_tensor(acts_h, device=dev)
         act_cur = torch.zeros((A, 3), dtype=torch.float32, device=dev)
         flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        masks = mask_cur = None
+        if reset_frac > 0:                                # a random mask per step, reset inside the graph
+            masks = torch.as_tensor(np.stack([synth.reset_mask(A, t, reset_frac, seed=7 + rank) for t in range(ring)]),
+                                    device=dev)
+            mask_cur = torch.zeros(A, dtype=torch.uint8, device=dev)
         tuned = None
         if nw == 0:                                       # setup: pick the launch shape (state restored)
             tuned = sf.sf_autotune(W.h, acts[0], iters=10)
-        graph = sf.sf_graph_capture(W.h, policy=policy, d_actions=act_cur, surrogate=surrogate)
+        graph = sf.sf_graph_capture(W.h, policy=policy, d_actions=act_cur, d_reset_mask=mask_cur,
+                                    surrogate=surrogate)
         if surrogate is not None:
             sf.sf_surrogate_audit(W.h)                    # reset the usage counter
         for t in range(warmup):
             act_cur.copy_(acts[t % ring])
+            if masks is not None:
+                mask_cur.copy_(masks[t % ring])
             sf.sf_graph_launch(graph)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -148,6 +161,8 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, p
         t0 = time.perf_counter()
         for t in range(steps):
             act_cur.copy_(acts[(warmup + t) % ring])      # stage this step's actions (untimed)
+            if masks is not None:
+                mask_cur.copy_(masks[(warmup + t) % ring])
             flush.fill_(float(t))                         # evict the working set from L2
             starts[t].record(stream)
             sf.sf_graph_launch(graph)
@@ -232,13 +247,20 @@ def main_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     res = {}
-    names = [args.only] if args.only else list(WORKLOADS)
+    names = [args.only] if args.only else list(WORKLOADS) + ["ragged1024"]
     for name in names:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        res[name] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream, e2e=not args.skip_e2e,
-                                 nw=args.nw, pack=args.pack)
+        if name == "4096x16+policy":                  # profiling target: the policy + step graph alone
+            res[name] = run_workload("4096x16", args.steps, args.warmup, rank, torch, sf, stream, e2e=False,
+                                     nw=args.nw, policy_seed=4000, pack=args.pack)
+        elif name == "ragged1024":
+            res[name] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream, e2e=False, nw=args.nw,
+                                     pack=args.pack, reset_frac=RAGGED[2])
+        else:
+            res[name] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream,
+                                     e2e=not args.skip_e2e, nw=args.nw, pack=args.pack)
     surr = None
     surr_info = None
     if not args.only and not args.skip_surrogate:
@@ -292,6 +314,7 @@ def main_ours(args):
 
     a256, a4096 = agg("256x16"), agg("4096x16")
     apol = agg("4096x16+policy") if "4096x16+policy" in res else None
+    arag = agg("ragged1024") if "ragged1024" in res else None
     asur = {k: agg(k + "+surrogate") for k in ("256x16", "4096x16") if k + "+surrogate" in res}
     if rank == 0:
         base = cpu_baseline("256x16") if (world == 1 and not args.skip_cpu) else None
@@ -325,6 +348,14 @@ def main_ours(args):
                                            "algorithmic_bytes_per_launch": a4096["bytes"]["total"],
                                            "traffic": traffic.get("4096x16")},
                               "mean_peak_drac": a4096["peak_drac"]},
+            "scale_ragged1024": None if arag is None else {
+                "value": arag["casps"], "unit": "CASPS", "ms_per_step": arag["ms"], "p50_ms": arag["p50"],
+                "p99_ms": arag["p99"], "agents": arag["A"] * world, "autotune": arag["tuned"],
+                "workload": "1024 worlds, agents floor(exp(U[0, ln 32])), road points exp(U[ln 100, ln 5000]), "
+                            "CSR; a random 20% reset mask every step inside the graph",
+                "roofline": {"bound": "hbm", "achieved": arag["achieved"], "peak": peak, "unit": "GB/s",
+                             "frac": arag["achieved"] / peak,
+                             "algorithmic_bytes_per_launch": arag["bytes"]["total"]}},
             "scale_4096x16_policy": None if apol is None else {
                 "value": apol["casps"], "unit": "CASPS", "ms_per_step": apol["ms"], "p50_ms": apol["p50"],
                 "p99_ms": apol["p99"], "mean_peak_drac": apol["peak_drac"],
@@ -399,7 +430,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--only", default=None, choices=list(WORKLOADS), help="profiling: run one workload only")
+    ap.add_argument("--only", default=None, choices=list(WORKLOADS) + ["ragged1024", "4096x16+policy"],
+                    help="profiling: run one workload only")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling: no end-to-end leg")
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
     ap.add_argument("--nw", type=int, default=0, help="warps per block (1, 2, 4, 8; 0 = autotuned)")

@@ -8,38 +8,50 @@
 
 namespace {
 
-// mean and standard deviation of every column of x [n][k] (two passes in double);
-// one block per column; std floored at 1e-6 of the column's scale
+// compensated (Kahan) float sum of the block's per-thread partials: FP32 only
+__device__ float block_sum(float v, float* red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const float r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// mean and standard deviation of every column of x [n][k] (two passes, each
+// thread a Kahan-compensated float sum); one block per column; std floored at
+// 1e-6 of the column's scale
 __global__ void col_stats_kernel(const float* __restrict__ x, unsigned long long n, int k, float* __restrict__ stats) {
     const int c = blockIdx.x;
-    __shared__ double red[256];
-    double s = 0.0;
-    for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) s += x[i * k + c];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    const double mean = red[0] / (double)(n ? n : 1);
-    __syncthreads();
-    double q = 0.0;
+    __shared__ float red[256];
+    float s = 0.f, comp = 0.f;
     for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) {
-        const double d = x[i * k + c] - mean;
-        q += d * d;
+        const float yv = x[i * k + c] - comp;
+        const float t = s + yv;
+        comp = (t - s) - yv;
+        s = t;
     }
-    red[threadIdx.x] = q;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    const float inv_n = 1.f / (float)(n ? n : 1);
+    const float mean = block_sum(s, red) * inv_n;
+    float q = 0.f;
+    comp = 0.f;
+    for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const float d = x[i * k + c] - mean;
+        const float yv = d * d - comp;
+        const float t = q + yv;
+        comp = (t - q) - yv;
+        q = t;
     }
+    const float var = block_sum(q, red) * inv_n;
     if (threadIdx.x == 0) {
-        double sd = sqrt(red[0] / (double)(n ? n : 1));
-        const double floor_ = 1e-6 * (fabs(mean) + 1e-3);
-        if (!(sd > floor_)) sd = floor_ > 1e-12 ? floor_ : 1.0;
-        stats[c] = (float)mean;
-        stats[k + c] = (float)sd;
+        float sd = sqrtf(var);
+        const float floor_ = 1e-6f * (fabsf(mean) + 1e-3f);
+        if (!(sd > floor_)) sd = floor_ > 1e-12f ? floor_ : 1.f;
+        stats[c] = mean;
+        stats[k + c] = sd;
     }
 }
 
