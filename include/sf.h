@@ -105,7 +105,17 @@ typedef struct {
     int32_t pack_agents;     /* 0: one world per thread block; 1..32: consecutive     *
                               * worlds share a block while their agents total at most *
                               * this many (worlds with more agents get a block alone) */
-    int32_t reserved[7];     /* must be zero                                          */
+    int32_t stage_bytes;     /* shared memory per block (multiple of 16, at most      *
+                              * 163840) into which a block copies its worlds' road    *
+                              * data before querying it; 0 = query global memory.    *
+                              * With staging, blocks also hold at most this many      *
+                              * bytes of road data (a larger world is read from      *
+                              * global memory)                                        */
+    int32_t split_step;      /* 0: a step is one fused kernel; 1: four kernels        *
+                              * (physics and events one warp per block of worlds,     *
+                              * road queries one warp per agent, warps_per_block      *
+                              * warps per query block); bit-identical results        */
+    int32_t reserved[5];     /* must be zero                                          */
 } sf_config;
 
 /* Worlds as CSR (host memory, read during sf_load_roads only).
@@ -147,7 +157,7 @@ typedef struct {
 /* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
  * (NULL = legacy default stream) on which every call of this handle enqueues
  * its work.  *out receives the handle.  Errors: SF_ERR_INVALID_ARG (NULL out,
- * nonzero reserved, pack_agents outside 0..32), SF_ERR_CUDA (no usable device). */
+ * nonzero reserved, pack_agents outside 0..32, bad stage_bytes or split_step), SF_ERR_CUDA (no usable device). */
 sf_status sf_create(const sf_config* cfg, void* cuda_stream, sf_handle* out);
 
 /* Release every device and host resource of h (synchronous).  NULL is a no-op. */
@@ -172,18 +182,21 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* h_roads);
  * substeps outside 1..64), SF_ERR_CUDA (launch failure). */
 sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps);
 
-/* Autotuner: time each launch shape of the world kernel over `iters` steps
- * with the given actions and keep the fastest for this handle.  Shapes are
- * (warps per block in 1, 2, 4, 8) x (world packing off, on): shape s has
- * 1 << (s & 3) warps and packing (s >= 4) groups consecutive worlds into
- * blocks of at most pack_agents agents (32 when the handle was created with
- * 0).  The agent state and every output are saved before and restored after
- * the trials, so the call does not advance the simulation.  Synchronous; uses
- * a temporary device buffer the size of the state and outputs.
- * out_shape (may be NULL, [2]) receives the chosen warps per block and
- * pack_agents (0 = no packing); out_ms (may be NULL, [8]) the mean step time
- * of each shape in ms.
+/* Autotuner: time each launch shape of the step over `iters` steps with the
+ * given actions and keep the fastest for this handle.  Shapes s < 32 are the
+ * fused kernel with 1 << (s & 3) warps per block, world packing when bit 2 is
+ * set (blocks of at most pack_agents agents, 32 when the handle was created
+ * with 0) and road staging budget (s >> 3) of {0, 49152, 98304, the handle's
+ * stage_bytes when it is none of these} bytes; shapes 32 + k (k < 6) are the
+ * split step with 2 << (k % 3) warps per query block, packed when k >= 3.  The agent state and every output are saved
+ * before and restored after the trials, so the call does not advance the
+ * simulation.  Synchronous; uses a temporary device buffer the size of the
+ * state and outputs.  out_shape (may be NULL, [4]) receives the chosen warps
+ * per block, pack_agents (0 = no packing), stage_bytes and split_step; out_ms
+ * (may be NULL, [SF_AUTOTUNE_SHAPES]) the mean step time of each shape in ms
+ * (0 for shapes not tried).
  * Errors: SF_ERR_STATE (no roads), SF_ERR_INVALID_ARG (iters < 1), SF_ERR_OOM. */
+#define SF_AUTOTUNE_SHAPES 38
 sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substeps, int iters, int32_t* out_shape,
                       float* out_ms);
 

@@ -41,9 +41,14 @@ struct sf_ctx {
     uint8_t* all_mask = nullptr;
     float* act_buf = nullptr;   // [A][3] actions written by an attached policy
     void* surr = nullptr;       // surrogate step buffers (allocated on first use)
-    int4* packs_single = nullptr;   // one world per block
-    int4* packs_packed = nullptr;   // consecutive worlds up to pack_cap agents per block
-    int n_single = 0, n_packed = 0, pack_cap = 32;
+    struct PackSet {                // blocks of the world kernel for one (packing, staging) choice
+        int cap, budget;            // agents per block (0: one world), staged bytes per block (0: off)
+        int4* d;
+        int n;
+    };
+    std::vector<PackSet> packsets;
+    int pack_cap = 32;
+    StepScratch sc{};           // scratch of the split step
     bool loaded = false;
 };
 
@@ -95,8 +100,8 @@ void free_all(sf_ctx* h) {
     h->all_mask = nullptr;
     h->act_buf = nullptr;
     h->surr = nullptr;
-    h->packs_single = h->packs_packed = nullptr;
-    h->n_single = h->n_packed = 0;
+    h->packsets.clear();
+    h->sc = StepScratch{};
     h->loaded = false;
     h->W = h->A = h->NP = 0;
 }
@@ -108,9 +113,15 @@ WorldArgs make_args(sf_ctx* h) {
     a.out = h->out;
     a.num_worlds = h->W;
     a.num_agents = h->A;
-    const bool packed = h->cfg.pack_agents > 0;
-    a.packs = packed ? h->packs_packed : h->packs_single;
-    a.num_packs = packed ? h->n_packed : h->n_single;
+    const int cap = h->cfg.pack_agents > 0 ? h->pack_cap : 0;
+    const int budget = h->cfg.split_step ? 0 : h->cfg.stage_bytes;   // the split step does not stage
+    for (const auto& ps : h->packsets)
+        if (ps.cap == cap && ps.budget == budget) {
+            a.packs = ps.d;
+            a.num_packs = ps.n;
+            a.stage_bytes = ps.budget;
+        }
+    a.sc = h->sc;
     a.flags = h->cfg.flags;
     a.seed = h->cfg.seed;
     a.substeps = 1;
@@ -123,22 +134,38 @@ int wpb_of(const sf_ctx* h) {
     return (w == 1 || w == 2 || w == 4 || w == 8) ? w : 4;
 }
 
+// one control step in the handle's launch shape (fused kernel or split step)
+cudaError_t launch_step(const sf_ctx* h, const WorldArgs& a) {
+    return h->cfg.split_step ? sf_launch_step_split(a, wpb_of(h), h->stream)
+                             : sf_launch_world(kModeStep, a, wpb_of(h), h->stream);
+}
+
 // blocks of the world kernel: runs of consecutive non-empty worlds whose agents
-// total at most `cap` (cap 0: one world per block)
-std::vector<int4> make_packs(const std::vector<int4>& world, int cap) {
+// total at most `cap` (cap 0: one world per block) and, with a staging budget,
+// whose road blobs total at most `budget` bytes (a larger world gets a block
+// alone and is read from global memory)
+std::vector<int4> make_packs(const std::vector<int4>& world, const std::vector<DevGrid>& grid, int cap, int budget) {
     std::vector<int4> packs;
     int4 cur = make_int4(0, 0, 0, 0);
+    long long bytes = 0;
     bool open = false;
     for (int w = 0; w < (int)world.size(); ++w) {
         const int n = world[w].y;
         if (n <= 0) { if (open) packs.push_back(cur); open = false; continue; }
-        if (open && (cap <= 0 || cur.w + n > cap)) { packs.push_back(cur); open = false; }
-        if (!open) { cur = make_int4(w, 1, world[w].x, n); open = true; }
-        else { cur.y += 1; cur.w += n; }
+        const long long b = grid[w].bytes;
+        if (open && (cap <= 0 || cur.w + n > cap || (budget > 0 && bytes + b > budget))) {
+            packs.push_back(cur);
+            open = false;
+        }
+        if (!open) { cur = make_int4(w, 1, world[w].x, n); bytes = b; open = true; }
+        else { cur.y += 1; cur.w += n; bytes += b; }
     }
     if (open) packs.push_back(cur);
     return packs;
 }
+
+// staging budgets the autotuner tries (bytes of shared memory per block)
+constexpr int kBudgets[3] = {0, 48 * 1024, 96 * 1024};
 
 bool is_lane_type(int t) { return t == 1 || t == 2; }
 bool is_edge_type(int t) { return t == 15 || t == 16; }
@@ -190,8 +217,16 @@ sf_status sf_create(const sf_config* cfg, void* cuda_stream, sf_handle* out) {
     *out = nullptr;
     sf_config c{};
     if (cfg) c = *cfg;
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 5; ++i)
         if (c.reserved[i] != 0) { g_create_error = "sf_create: reserved fields must be zero"; return SF_ERR_INVALID_ARG; }
+    if (c.split_step != 0 && c.split_step != 1) {
+        g_create_error = "sf_create: split_step must be 0 or 1";
+        return SF_ERR_INVALID_ARG;
+    }
+    if (c.stage_bytes < 0 || c.stage_bytes > sfk::kMaxStageBytes || c.stage_bytes % 16) {
+        g_create_error = "sf_create: stage_bytes must be a multiple of 16 in 0..163840";
+        return SF_ERR_INVALID_ARG;
+    }
     if (c.pack_agents < 0 || c.pack_agents > 32) {
         g_create_error = "sf_create: pack_agents must be 0..32";
         return SF_ERR_INVALID_ARG;
@@ -262,10 +297,8 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     std::vector<int2> cand(W);
     std::vector<int32_t> cands;
     std::vector<DevGrid> grid(W);
-    std::vector<int32_t> cell_off, sidx(NP);
-    std::vector<float4> eall;
-    std::vector<float4> sseg(NP);
-    std::vector<uint32_t> smeta(NP);
+    std::vector<int32_t> pbeg(NP);
+    std::vector<unsigned char> blob;   // every world's road blob, 16-byte aligned sections
     auto in_box = [](double x, double y) { return std::fabs(x) <= 100.0 && std::fabs(y) <= 100.0; };
     for (int w = 0; w < W; ++w) {
         const int p0 = r->poly_off[w], p1 = r->poly_off[w + 1];
@@ -301,6 +334,7 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
                 if (is_edge_type(t)) m |= sfk::kPtEdge;
                 pmeta[k] = m;
                 pend[k] = k1;
+                pbeg[k] = k0;
             }
             if (is_lane_type(t) && k1 > k0) {
                 const double total = arc.back();
@@ -314,7 +348,11 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
         cand[w] = make_int2((int)cands.size(), (int)use.size());
         cands.insert(cands.end(), use.begin(), use.end());
 
-        // ---- uniform grid of the world: points sorted by cell, row-major
+        // ---- the world's road blob: grid cell offsets, cell-sorted segment
+        // records (row-major cells, input order within a cell), info words, edges
+        if (q1 - q0 > sfk::kMaxWorldPoints)
+            return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: world " + std::to_string(w) + " has " +
+                                                   std::to_string(q1 - q0) + " road points (at most 65535)");
         double xmin = 0, xmax = 0, ymin = 0, ymax = 0;
         for (int k = q0; k < q1; ++k) {
             if (k == q0 || r->px[k] < xmin) xmin = r->px[k];
@@ -325,29 +363,47 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
         double c = std::max(sfk::kCellMin, std::max(xmax - xmin, ymax - ymin) / (sfk::kGridMax - 1));
         int nx = std::min(sfk::kGridMax, (int)std::floor((xmax - xmin) / c) + 1);
         int ny = std::min(sfk::kGridMax, (int)std::floor((ymax - ymin) / c) + 1);
-        const int ncell = nx * ny;
+        const int ncell = nx * ny, np = q1 - q0;
         auto cx_of = [&](double x) { return std::min(nx - 1, std::max(0, (int)std::floor((x - xmin) / c))); };
         auto cy_of = [&](double y) { return std::min(ny - 1, std::max(0, (int)std::floor((y - ymin) / c))); };
-        DevGrid g{};
-        g.x0 = (float)xmin; g.y0 = (float)ymin; g.c = (float)c; g.inv_c = (float)(1.0 / c);
-        g.nx = nx; g.ny = ny; g.cbase = (int)cell_off.size();
-        g.eoff = (int)eall.size();
         std::vector<int> cnt(ncell + 1, 0);
+        std::vector<float4> edges;
         for (int k = q0; k < q1; ++k) {
             cnt[cy_of(r->py[k]) * nx + cx_of(r->px[k]) + 1]++;
             if ((pmeta[k] & (sfk::kPtSegNext | sfk::kPtEdge)) == (sfk::kPtSegNext | sfk::kPtEdge))
-                eall.push_back(make_float4(r->px[k], r->py[k], r->px[k + 1], r->py[k + 1]));
+                edges.push_back(make_float4(r->px[k], r->py[k], r->px[k + 1], r->py[k + 1]));
         }
         for (int i = 0; i < ncell; ++i) cnt[i + 1] += cnt[i];
-        for (int i = 0; i <= ncell; ++i) cell_off.push_back(q0 + cnt[i]);
-        for (int k = q0; k < q1; ++k) {   // stable: input order within a cell
-            int slot = q0 + cnt[cy_of(r->py[k]) * nx + cx_of(r->px[k])]++;
-            const bool nxt = (pmeta[k] & sfk::kPtSegNext) != 0;
-            sseg[slot] = make_float4(r->px[k], r->py[k], r->px[nxt ? k + 1 : k], r->py[nxt ? k + 1 : k]);
-            smeta[slot] = pmeta[k];
-            sidx[slot] = k;
+        auto a16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+        const size_t o_seg = a16(2 * (size_t)(ncell + 1)), o_info = o_seg + 16 * (size_t)np,
+                     o_edge = o_info + a16(4 * (size_t)np), bytes = o_edge + 16 * edges.size();
+        const size_t at = blob.size();
+        blob.resize(at + bytes, 0);
+        unsigned char* B = blob.data() + at;
+        for (int i = 0; i <= ncell; ++i) {
+            const uint16_t v = (uint16_t)cnt[i];
+            std::memcpy(B + 2 * i, &v, 2);
         }
-        g.ecnt = (int)eall.size() - g.eoff;
+        for (int k = q0; k < q1; ++k) {   // stable: input order within a cell
+            const int slot = cnt[cy_of(r->py[k]) * nx + cx_of(r->px[k])]++;
+            const bool has_next = k + 1 < pend[k];
+            const int o = has_next ? k + 1 : (k - 1 >= pbeg[k] ? k - 1 : k);
+            const float4 rec = make_float4(r->px[k], r->py[k], r->px[o], r->py[o]);
+            uint32_t info = (uint32_t)(k - q0) | ((pmeta[k] & sfk::kPtTypeMask) << 16);
+            if (pmeta[k] & sfk::kPtSegNext) info |= sfk::kInfoSegNext;
+            if (pmeta[k] & sfk::kPtLane) info |= sfk::kInfoLane;
+            if (pmeta[k] & sfk::kPtEdge) info |= sfk::kInfoEdge;
+            if (has_next) info |= sfk::kInfoHasNext;
+            std::memcpy(B + o_seg + 16 * (size_t)slot, &rec, 16);
+            std::memcpy(B + o_info + 4 * (size_t)slot, &info, 4);
+        }
+        if (!edges.empty()) std::memcpy(B + o_edge, edges.data(), 16 * edges.size());
+        DevGrid g{};
+        g.x0 = (float)xmin; g.y0 = (float)ymin; g.c = (float)c; g.inv_c = (float)(1.0 / c);
+        g.nx = nx; g.ny = ny; g.np = np; g.ecnt = (int)edges.size();
+        g.bytes = (int)bytes; g.o_seg = (int)o_seg; g.o_info = (int)o_info; g.o_edge = (int)o_edge;
+        g.q0 = q0;
+        g.blob = at;
         grid[w] = g;
     }
 
@@ -371,21 +427,16 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     SF_ALLOC(step, int32_t, Aa);
     SF_ALLOC(episode, int32_t, Aa);
     h->st = DevState{pos, quat, vel, angv, spin, goal, peak, meta, step, episode};
-    int4* dworld; int2* dcand; float4* dpt; uint32_t* dpmeta; int32_t *dpend, *dcands;
+    int4* dworld; int2* dcand; float4* dpt; int32_t *dpend, *dcands;
     SF_ALLOC(dworld, int4, (size_t)W);
     SF_ALLOC(dcand, int2, (size_t)W);
     SF_ALLOC(dpt, float4, (size_t)NP + 1);
-    SF_ALLOC(dpmeta, uint32_t, (size_t)NP + 1);
     SF_ALLOC(dpend, int32_t, (size_t)NP + 1);
     SF_ALLOC(dcands, int32_t, cands.size() + 1);
-    DevGrid* dgrid; int32_t *dcoff, *dsidx; float4 *dsseg, *deall; uint32_t* dsmeta;
+    DevGrid* dgrid; unsigned char* dblob;
     SF_ALLOC(dgrid, DevGrid, (size_t)W);
-    SF_ALLOC(dcoff, int32_t, cell_off.size());
-    SF_ALLOC(dsseg, float4, (size_t)NP + 1);
-    SF_ALLOC(dsmeta, uint32_t, (size_t)NP + 1);
-    SF_ALLOC(dsidx, int32_t, (size_t)NP + 1);
-    SF_ALLOC(deall, float4, eall.size() + 1);
-    h->rd = DevRoads{dworld, dcand, dpt, dpmeta, dpend, dcands, dgrid, dcoff, dsseg, dsmeta, dsidx, deall};
+    SF_ALLOC(dblob, unsigned char, blob.size() + 16);
+    h->rd = DevRoads{dworld, dcand, dpt, dpend, dcands, dgrid, dblob};
     float *obs, *reward, *drac; uint8_t* done; uint32_t* events; int32_t *lane_seg, *knn_pts, *knn_agents;
     unsigned int* err_word; float* hint;
     SF_ALLOC(obs, float, Aa * SF_OBS_DIM);
@@ -397,15 +448,33 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     SF_ALLOC(knn_agents, int32_t, Aa * SF_K_AGENTS);
     SF_ALLOC(drac, float, Aa);
     SF_ALLOC(err_word, unsigned int, 1);
-    SF_ALLOC(hint, float, Aa * 2);
+    SF_ALLOC(hint, float, Aa * 4);
     h->out = DevOutputs{obs, reward, done, events, lane_seg, knn_pts, knn_agents, drac, err_word, hint};
     SF_ALLOC(h->place_buf, float, Aa * 6);
     SF_ALLOC(h->all_mask, uint8_t, Aa);
     SF_ALLOC(h->act_buf, float, Aa * 3);
+    AgentQ* scq; float2 *scprev, *schead; uint8_t* scflag; int32_t* scworld;
+    SF_ALLOC(scq, AgentQ, Aa);
+    SF_ALLOC(scprev, float2, Aa);
+    SF_ALLOC(schead, float2, Aa);
+    SF_ALLOC(scflag, uint8_t, Aa);
+    SF_ALLOC(scworld, int32_t, Aa);
+    h->sc = StepScratch{scq, scprev, schead, scflag, scworld};
+    std::vector<int32_t> agent_world(Aa);
+    for (int w = 0; w < W; ++w)
+        for (int k = world[w].x; k < world[w].x + world[w].y; ++k) agent_world[k] = w;
     h->pack_cap = h->cfg.pack_agents > 0 ? h->cfg.pack_agents : 32;
-    const std::vector<int4> ps = make_packs(world, 0), pp = make_packs(world, h->pack_cap);
-    SF_ALLOC(h->packs_single, int4, ps.size());
-    SF_ALLOC(h->packs_packed, int4, pp.size());
+    std::vector<int> budgets(kBudgets, kBudgets + 3);
+    if (std::find(budgets.begin(), budgets.end(), h->cfg.stage_bytes) == budgets.end())
+        budgets.push_back(h->cfg.stage_bytes);
+    std::vector<std::vector<int4>> pack_host;
+    for (int budget : budgets)
+        for (int cap : {0, h->pack_cap}) {
+            pack_host.push_back(make_packs(world, grid, cap, budget));
+            sf_ctx::PackSet ps{cap, budget, nullptr, (int)pack_host.back().size()};
+            SF_ALLOC(ps.d, int4, pack_host.back().size());
+            h->packsets.push_back(ps);
+        }
 #undef SF_ALLOC
 
     std::vector<uint32_t> meta_h(Aa);
@@ -420,28 +489,23 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     up(dworld, world.data(), world.size() * sizeof(int4));
     up(dcand, cand.data(), cand.size() * sizeof(int2));
     up(dpt, pt.data(), pt.size() * sizeof(float4));
-    up(dpmeta, pmeta.data(), pmeta.size() * sizeof(uint32_t));
     up(dpend, pend.data(), pend.size() * sizeof(int32_t));
     up(dcands, cands.data(), cands.size() * sizeof(int32_t));
     up(dgrid, grid.data(), grid.size() * sizeof(DevGrid));
-    up(dcoff, cell_off.data(), cell_off.size() * 4);
-    up(dsseg, sseg.data(), sseg.size() * sizeof(float4));
-    up(dsmeta, smeta.data(), smeta.size() * 4);
-    up(dsidx, sidx.data(), sidx.size() * 4);
-    up(deall, eall.data(), eall.size() * sizeof(float4));
+    up(dblob, blob.data(), blob.size());
     for (float4* p : {pos, quat, vel, angv, spin, goal}) zero(p, Aa * sizeof(float4));
     zero(peak, Aa * 4); zero(step, Aa * 4); zero(episode, Aa * 4);
     up(meta, meta_h.data(), Aa * 4);
+    up(scworld, agent_world.data(), Aa * 4);
+    zero(scflag, Aa);
     zero(obs, Aa * SF_OBS_DIM * 4); zero(reward, Aa * 4); zero(done, Aa); zero(events, Aa * 4);
-    zero(drac, Aa * 4); zero(err_word, 4); zero(hint, Aa * 8);
+    zero(drac, Aa * 4); zero(err_word, 4); zero(hint, Aa * 16);
     if (e == cudaSuccess && Aa) e = cudaMemset(lane_seg, 0xFF, Aa * 4);
     if (e == cudaSuccess && Aa) e = cudaMemset(knn_pts, 0xFF, Aa * SF_L_POINTS * 4);
     if (e == cudaSuccess && Aa) e = cudaMemset(knn_agents, 0xFF, Aa * SF_K_AGENTS * 4);
     if (e == cudaSuccess && Aa) e = cudaMemset(h->all_mask, 1, Aa);
-    up(h->packs_single, ps.data(), ps.size() * sizeof(int4));
-    up(h->packs_packed, pp.data(), pp.size() * sizeof(int4));
-    h->n_single = (int)ps.size();
-    h->n_packed = (int)pp.size();
+    for (size_t i = 0; i < h->packsets.size(); ++i)
+        up(h->packsets[i].d, pack_host[i].data(), pack_host[i].size() * sizeof(int4));
     if (e != cudaSuccess) { free_all(h); return cuda_fail(h, e, "sf_load_roads upload"); }
     h->W = W; h->A = A; h->NP = NP;
     h->loaded = true;
@@ -458,7 +522,7 @@ sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps) {
     a.actions = d_actions;
     a.h = dt / (float)substeps;
     a.substeps = substeps;
-    cudaError_t e = sf_launch_world(kModeStep, a, wpb_of(h), h->stream);
+    cudaError_t e = launch_step(h, a);
     if (e != cudaSuccess) return cuda_fail(h, e, "sf_step launch");
     return SF_OK;
 }
@@ -475,7 +539,7 @@ sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substep
         {h->st.spin, A * 16}, {h->st.goal, A * 16}, {h->st.peak_drac, A * 4}, {h->st.meta, A * 4},
         {h->st.step, A * 4}, {h->st.episode, A * 4}, {h->out.obs, A * SF_OBS_DIM * 4}, {h->out.reward, A * 4},
         {h->out.done, A}, {h->out.events, A * 4}, {h->out.lane_seg, A * 4}, {h->out.knn_pts, A * SF_L_POINTS * 4},
-        {h->out.knn_agents, A * SF_K_AGENTS * 4}, {h->out.drac, A * 4}, {h->out.hint, A * 8},
+        {h->out.knn_agents, A * SF_K_AGENTS * 4}, {h->out.drac, A * 4}, {h->out.hint, A * 16},
         {h->out.error_word, 4}};
     size_t total = 0;
     for (const auto& b : bufs) total += (b.second + 255) & ~(size_t)255;
@@ -493,31 +557,50 @@ sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substep
         }
         return r;
     };
-    float ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int best = wpb_of(h), best_pack = h->cfg.pack_agents;
+    float ms[SF_AUTOTUNE_SHAPES] = {};
+    int best = wpb_of(h), best_pack = h->cfg.pack_agents, best_stage = h->cfg.stage_bytes;
     float best_ms = 0.f;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     e = copy_all(true);
     if (e == cudaSuccess) e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    const int saved = h->cfg.warps_per_block, saved_pack = h->cfg.pack_agents;
-    for (int si = 0; si < 8 && e == cudaSuccess; ++si) {
-        const int nw = 1 << (si & 3), pack = si >= 4 ? h->pack_cap : 0;
+    const int saved = h->cfg.warps_per_block, saved_pack = h->cfg.pack_agents, saved_stage = h->cfg.stage_bytes;
+    const int budgets[4] = {kBudgets[0], kBudgets[1], kBudgets[2], h->cfg.stage_bytes};
+    const int nb = std::find(kBudgets, kBudgets + 3, h->cfg.stage_bytes) == kBudgets + 3 ? 4 : 3;
+    bool first = true;
+    const int saved_split = h->cfg.split_step;
+    int best_split = saved_split;
+    for (int si = 0; si < SF_AUTOTUNE_SHAPES && e == cudaSuccess; ++si) {
+        const bool split = si >= 32;
+        if (!split && si >= 8 * nb) continue;
+        const int k = si - 32;
+        const int nw = split ? 2 << (k % 3) : 1 << (si & 3);
+        const int pack = (split ? k / 3 : (si >> 2) & 1) ? h->pack_cap : 0;
+        const int stage = split ? 0 : budgets[si >> 3];
         h->cfg.warps_per_block = nw;
         h->cfg.pack_agents = pack;
+        h->cfg.stage_bytes = stage;
+        h->cfg.split_step = split ? 1 : 0;
         e = copy_all(false);
         WorldArgs a = make_args(h);
         a.actions = d_actions;
         a.h = dt / (float)substeps;
         a.substeps = substeps;
-        if (e == cudaSuccess) e = sf_launch_world(kModeStep, a, nw, h->stream);   // warm
+        if (e == cudaSuccess) e = launch_step(h, a);   // warm
         if (e == cudaSuccess) e = cudaEventRecord(t0, h->stream);
-        for (int it = 0; it < iters && e == cudaSuccess; ++it) e = sf_launch_world(kModeStep, a, nw, h->stream);
+        for (int it = 0; it < iters && e == cudaSuccess; ++it) e = launch_step(h, a);
         if (e == cudaSuccess) e = cudaEventRecord(t1, h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(t1);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[si], t0, t1);
         ms[si] /= (float)iters;
-        if (e == cudaSuccess && (si == 0 || ms[si] < best_ms)) { best_ms = ms[si]; best = nw; best_pack = pack; }
+        if (e == cudaSuccess && (first || ms[si] < best_ms)) {
+            best_ms = ms[si];
+            best = nw;
+            best_pack = pack;
+            best_stage = stage;
+            best_split = split ? 1 : 0;
+            first = false;
+        }
     }
     if (e == cudaSuccess) e = copy_all(false);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -527,12 +610,18 @@ sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substep
     if (e != cudaSuccess) {
         h->cfg.warps_per_block = saved;
         h->cfg.pack_agents = saved_pack;
+        h->cfg.stage_bytes = saved_stage;
+        h->cfg.split_step = saved_split;
         return cuda_fail(h, e, "sf_autotune");
     }
     h->cfg.warps_per_block = best;
     h->cfg.pack_agents = best_pack;
-    if (out_shape) { out_shape[0] = best; out_shape[1] = best_pack; }
-    if (out_ms) for (int i = 0; i < 8; ++i) out_ms[i] = ms[i];
+    h->cfg.stage_bytes = best_stage;
+    h->cfg.split_step = best_split;
+    if (out_shape) {
+        out_shape[0] = best; out_shape[1] = best_pack; out_shape[2] = best_stage; out_shape[3] = best_split;
+    }
+    if (out_ms) for (int i = 0; i < SF_AUTOTUNE_SHAPES; ++i) out_ms[i] = ms[i];
     return SF_OK;
 }
 
@@ -956,7 +1045,7 @@ sf_status sf_step_surrogate(sf_handle h, sf_surrogate_handle s, const float* d_a
     a.surr_mode = audit ? 2 : 1;
     a.audit_err = b->words;
     a.surr_count = b->words + 1;
-    e = sf_launch_world(kModeStep, a, wpb_of(h), h->stream);
+    e = launch_step(h, a);
     return e == cudaSuccess ? SF_OK : cuda_fail(h, e, "sf_step_surrogate");
 }
 

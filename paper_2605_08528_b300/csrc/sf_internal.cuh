@@ -70,7 +70,8 @@ constexpr int kSpawnTries = 8;
 constexpr double kCellMin = 4.0;   // grid cell edge [m]; larger when a world spans > 128 cells
 constexpr int kGridMax = 128;
 constexpr float kSegReach = 3.0f;  // no segment is longer (App. C gap rule)
-constexpr float kKnnR0 = 10.0f, kLaneR0 = 6.0f, kHintSlack = 2.0f, kGrow = 1.6f;
+constexpr float kKnnR0 = 10.0f, kLaneR0 = 6.0f, kGrow = 1.6f;
+constexpr float kHintJump = 20.0f;   // a hint farther than this from the agent is not used
 
 // ---------------------------------------------------------------- layout
 constexpr int kMaxAgents = 32;
@@ -78,11 +79,19 @@ constexpr int kK = 8, kL = 32;
 constexpr int kObsEgo = 16, kObsNbr = 10, kObsPt = 7;
 constexpr int kObsDim = kObsEgo + kK * kObsNbr + kL * kObsPt;  // 320
 
-// point meta bits
+// point meta bits (input-order store)
 constexpr uint32_t kPtTypeMask = 0xFFu;
 constexpr uint32_t kPtSegNext = 1u << 8;   // point k and k+1 form a segment
 constexpr uint32_t kPtLane = 1u << 9;      // Waymo type 1 or 2
 constexpr uint32_t kPtEdge = 1u << 10;     // Waymo type 15 or 16
+// info word of a cell-sorted record: input index within the world (bits 0-15),
+// Waymo type (16-23) and these bits
+constexpr uint32_t kInfoSegNext = 1u << 24;
+constexpr uint32_t kInfoLane = 1u << 25;
+constexpr uint32_t kInfoEdge = 1u << 26;
+constexpr uint32_t kInfoHasNext = 1u << 27;  // the polyline continues after the point
+constexpr int kMaxWorldPoints = 65535;       // a world's points are indexed by 16 bits
+constexpr int kMaxStageBytes = 160 * 1024;   // dynamic shared memory of a staging block
 
 // status and event bits (same values as the public header)
 constexpr uint32_t kAlive = 1u, kParked = 2u;
@@ -106,32 +115,35 @@ struct DevState {
     int32_t* episode;
 };
 
-// Uniform grid over one world's points (built on the host at load time).
-// The world's points are stored a second time sorted by cell, row-major
-// (cell (cx, cy) = floor((x - x0) / c), clamped), so the cells of one grid row
-// form one contiguous range [cell_off[cbase + cy*nx + cx0], cell_off[cbase +
-// cy*nx + cx1 + 1]).  Segments are found through their start points.
+// One world's road blob (built on the host at load time, 16-byte aligned
+// sections, copied whole into shared memory by a block that stages it):
+//   u16    coff[nx*ny + 1]  cell offsets into the records (relative to the world)
+//   float4 seg[np]          the world's points sorted by grid cell, row-major,
+//                           stable, as (x, y, x', y'): (x', y') the next point of
+//                           the polyline, the previous one at its end, the
+//                           point itself for a one-point polyline
+//   u32    info[np]         input index within the world | type << 16 | kInfo*
+//   float4 edge[ecnt]       the world's road-edge segments (a, b)
+// Cell (cx, cy) = floor((x - x0) / c), clamped; the cells of one grid row form
+// one contiguous range [coff[cy*nx + cx0], coff[cy*nx + cx1 + 1]).  Segments
+// are found through their start points.
 struct DevGrid {
     float x0, y0, c, inv_c;
-    int nx, ny, cbase, eoff;
-    int ecnt, pad0, pad1, pad2;
+    int nx, ny, np, ecnt;
+    int bytes, o_seg, o_info, o_edge;   // blob size and section offsets [bytes]
+    int q0, pad;                        // the world's first point (input order)
+    unsigned long long blob;            // byte offset of the blob in the road store
 };
 
 // Road store of all worlds.
 struct DevRoads {
-    const int4* world;      // (first agent, agent count, first point, point count)
-    const int2* cand;       // (first spawn candidate, candidate count)
-    const float4* pt;       // (x, y, road direction x, y), input order
-    const uint32_t* pmeta;  // type | kPt* bits, input order
-    const int32_t* pend;    // one past the last point of the point's polyline
-    const int32_t* cands;   // spawn candidate point indices
-    const DevGrid* grid;    // per world
-    const int32_t* cell_off;// per world nx*ny+1 offsets into the sorted arrays
-    const float4* sseg;     // points sorted by cell as segment records (x, y, next x, next y);
-                            // (x, y, x, y) where the point starts no segment
-    const uint32_t* smeta;  // their meta
-    const int32_t* sidx;    // their input-order index
-    const float4* eseg;     // every edge segment of a world (ax, ay, bx, by), at grid.eoff
+    const int4* world;          // (first agent, agent count, first point, point count)
+    const int2* cand;           // (first spawn candidate, candidate count)
+    const float4* pt;           // (x, y, road direction x, y), input order
+    const int32_t* pend;        // one past the last point of the point's polyline
+    const int32_t* cands;       // spawn candidate point indices
+    const DevGrid* grid;        // per world
+    const unsigned char* blob;  // every world's road blob
 };
 
 struct DevOutputs {
@@ -144,10 +156,28 @@ struct DevOutputs {
     int32_t* knn_agents;
     float* drac;
     unsigned int* error_word;  // bit0 non-finite seen
-    float* hint;               // [A][2] last query radii (32-NN, nearest lane); 0 = unknown
+    float* hint;               // [A][4] last query: 32nd-point distance, nearest-lane distance (0 = unknown)
+                               // and the position (x, y) they were measured from
 };
 
 enum WorldMode { kModeStep = 0, kModeReset = 1, kModeObserve = 2 };
+
+// results of one agent's road queries for the events
+struct AgentQ {
+    int seg;                     // nearest lane segment (input index), -1 none
+    float dist, lat, tx, ty;     // its distance, signed lateral offset, tangent toward the goal
+    float tedge;                 // edge-ray time (inf: no edge within 40 m)
+    int forb, need;              // lane-forbidden; road block to recompute
+};
+
+// per-agent scratch of the split step (kernels exchange through it)
+struct StepScratch {
+    AgentQ* q;                   // [A] event queries
+    float2* prev;                // [A] start-of-step position
+    float2* head;                // [A] heading after the physics, then after respawns
+    uint8_t* flag;               // [A] bit 0 non-finite this step, bit 1 road block stale
+    const int32_t* agent_world;  // [A] world of each agent
+};
 
 struct WorldArgs {
     DevState st;
@@ -155,6 +185,8 @@ struct WorldArgs {
     DevOutputs out;
     const int4* packs;      // (first world, worlds, first agent, agents) per thread block
     int num_packs;
+    int stage_bytes;        // shared memory per block for staged road blobs (0: read them from global)
+    StepScratch sc;         // split step only
     const float* actions;   // [A][3]   (step mode)
     const uint8_t* mask;    // [A]      (reset mode)
     int num_worlds;
@@ -179,6 +211,8 @@ constexpr int kSurrIn = 30, kSurrInLd = 32, kSurrOut = 16;
 
 // launch wrappers (sf_world.cu)
 cudaError_t sf_launch_world(int mode, const WorldArgs& a, int warps_per_block, cudaStream_t s);
+// one control step as four kernels (physics, road queries, events, fix-up); nwq warps per query block
+cudaError_t sf_launch_step_split(const WorldArgs& a, int nwq, cudaStream_t s);
 cudaError_t sf_launch_place(const WorldArgs& a, const float* d_place, cudaStream_t s);
 // gate of the surrogate per agent (1 = eligible), from the current state
 cudaError_t sf_launch_surr_gate(const WorldArgs& a, float dt, uint8_t* d_elig, cudaStream_t s);

@@ -543,13 +543,56 @@ __device__ __forceinline__ unsigned long long merge32(unsigned long long run, un
     return m;
 }
 
+// One world's road blob as the queries see it: in shared memory when the
+// block staged it, else in global memory (generic pointers either way).
+struct WRoads {
+    const uint16_t* coff;   // [nx*ny + 1] cell offsets into the sorted records
+    const float4* seg;      // sorted segment records (x, y, x', y')
+    const uint32_t* info;   // local input index | type << 16 | kInfo* bits
+    const float4* edge;     // edge segments (a, b)
+    float x0, y0, inv_c;
+    int nx, ny, ecnt, q0;
+};
+
+__device__ __forceinline__ WRoads view_of(const DevGrid& g, const unsigned char* base) {
+    WRoads v;
+    v.coff = reinterpret_cast<const uint16_t*>(base);
+    v.seg = reinterpret_cast<const float4*>(base + g.o_seg);
+    v.info = reinterpret_cast<const uint32_t*>(base + g.o_info);
+    v.edge = reinterpret_cast<const float4*>(base + g.o_edge);
+    v.x0 = g.x0; v.y0 = g.y0; v.inv_c = g.inv_c;
+    v.nx = g.nx; v.ny = g.ny; v.ecnt = g.ecnt; v.q0 = g.q0;
+    return v;
+}
+
+// Starting radius of a query from last step's answer d measured at h: the
+// distance to the k-th nearest object grows by at most |p - h| (triangle
+// inequality), so d + |p - h| (padded for rounding) already holds the previous
+// answer's objects.  Unknown (d = 0) or far hints give the default r0.  The
+// queries stay exact whatever the radius: they grow it until it is enough.
+__device__ __forceinline__ float hint_radius(const float* hnt, int which, float px, float py, float r0) {
+    const float d = hnt[which];
+    const float dx = px - hnt[2], dy = py - hnt[3];
+    const float jump = sqrtf(dx * dx + dy * dy);
+    if (!(d > 0.f) || !(jump < kHintJump)) return r0;
+    return d + jump * 1.0001f + 1e-3f;
+}
+
+// keys of road candidates: (d^2 bits, local input index, sorted position);
+// the order is (d^2, input index), the position only locates the record
+__device__ __forceinline__ unsigned long long rkey(float d2, uint32_t info, int pos) {
+    return key_of(d2, (int)(((info & 0xFFFFu) << 16) | (uint32_t)pos));
+}
+__device__ __forceinline__ int rkey_pos(unsigned long long k) { return (int)(k & 0xFFFFull); }
+__device__ __forceinline__ int rkey_local(unsigned long long k) { return (int)((k >> 16) & 0xFFFFull); }
+
 // Grid rows covering the square [q - R, q + R]^2: every point outside it is
 // at least R away from q.  `all` when the square covers the whole grid.
 struct Rows {
     int cx0, cx1, cy0, cy1;
     bool all;
 };
-__device__ __forceinline__ Rows rows_covering(const DevGrid& g, float qx, float qy, float R) {
+__device__ __forceinline__ Rows rows_covering(const WRoads& g, float qx, float qy, float R) {
     const float fx0 = fminf(fmaxf((qx - R - g.x0) * g.inv_c, -1.f), (float)g.nx);
     const float fx1 = fminf(fmaxf((qx + R - g.x0) * g.inv_c, -1.f), (float)g.nx);
     const float fy0 = fminf(fmaxf((qy - R - g.y0) * g.inv_c, -1.f), (float)g.ny);
@@ -562,17 +605,16 @@ __device__ __forceinline__ Rows rows_covering(const DevGrid& g, float qx, float 
 }
 
 // tangent, lateral offset and distance of the nearest lane segment from its key
-__device__ __forceinline__ Lane lane_of(const DevRoads& rd, unsigned long long best, float qx, float qy, float gx,
+__device__ __forceinline__ Lane lane_of(const WRoads& v, unsigned long long best, float qx, float qy, float gx,
                                         float gy) {
     Lane L;
-    L.seg = key_idx(best);
-    if (L.seg < 0) { L.dist = kInf; L.lat = 0.f; L.tx = L.ty = 0.f; return L; }
-    const float4 a = __ldg(&rd.pt[L.seg]);
-    const float4 b = __ldg(&rd.pt[L.seg + 1]);
-    float ex = b.x - a.x, ey = b.y - a.y;
+    if (best == kKeyInf) { L.seg = -1; L.dist = kInf; L.lat = 0.f; L.tx = L.ty = 0.f; return L; }
+    L.seg = v.q0 + rkey_local(best);
+    const float4 r = v.seg[rkey_pos(best)];            // (a, b) of the segment
+    float ex = r.z - r.x, ey = r.w - r.y;
     float nn = sqrtf(ex * ex + ey * ey);
     float tx = ex / nn, ty = ey / nn;
-    float lat = cross2(tx, ty, qx - a.x, qy - a.y);
+    float lat = cross2(tx, ty, qx - r.x, qy - r.y);
     if (tx * (gx - qx) + ty * (gy - qy) < 0.f) { tx = -tx; ty = -ty; lat = -lat; }
     L.dist = sqrtf(key_d2(best)); L.lat = lat; L.tx = tx; L.ty = ty;
     return L;
@@ -585,31 +627,31 @@ __device__ __forceinline__ Lane lane_of(const DevRoads& rd, unsigned long long b
 // same scan runs the lane-forbidden test of the footprint's three circles
 // against the road-edge segments (App. G) when `forb` is given: the square
 // then also covers every edge segment that can touch a circle.
-__device__ Lane coop_nearest_lane(const DevRoads& rd, const DevGrid& g, float qx, float qy, float gx, float gy,
-                                  float R, int lane, bool* forb = nullptr, float hx = 1.f, float hy = 0.f) {
+__device__ Lane coop_nearest_lane(const WRoads& v, float qx, float qy, float gx, float gy, float R, int lane,
+                                  bool* forb = nullptr, float hx = 1.f, float hy = 0.f) {
     const float lim_f = (kCircR + kEdgeHalfWidth) * (kCircR + kEdgeHalfWidth);
     float S = R + kSegReach;
     if (forb) S = fmaxf(S, kCircD + kCircR + kEdgeHalfWidth + kSegReach);
     bool edges = forb != nullptr, f = false;
     unsigned long long best = kKeyInf;
     for (;;) {
-        const Rows w = rows_covering(g, qx, qy, S);
+        const Rows w = rows_covering(v, qx, qy, S);
         const float Rl = S - kSegReach;
         const float lim = w.all ? kInf : Rl * Rl * (1.f - 1e-5f);
         best = kKeyInf;
         if (w.cx0 <= w.cx1)
             for (int cy = w.cy0; cy <= w.cy1; ++cy) {
-                const int row = g.cbase + cy * g.nx;
-                const int s = __ldg(&rd.cell_off[row + w.cx0]), e = __ldg(&rd.cell_off[row + w.cx1 + 1]);
+                const int row = cy * v.nx;
+                const int s = v.coff[row + w.cx0], e = v.coff[row + w.cx1 + 1];
                 for (int i = s + lane; i < e; i += 32) {
-                    const uint32_t m = __ldg(&rd.smeta[i]);
-                    if (!(m & kPtSegNext)) continue;
-                    if (m & kPtLane) {
-                        const float4 sg = __ldg(&rd.sseg[i]);
+                    const uint32_t m = v.info[i];
+                    if (!(m & kInfoSegNext)) continue;
+                    if (m & kInfoLane) {
+                        const float4 sg = v.seg[i];
                         const float d2 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
-                        if (d2 < lim) best = umin64(best, key_of(d2, __ldg(&rd.sidx[i])));
-                    } else if (edges && (m & kPtEdge)) {
-                        const float4 sg = __ldg(&rd.sseg[i]);
+                        if (d2 < lim) best = umin64(best, rkey(d2, m, i));
+                    } else if (edges && (m & kInfoEdge)) {
+                        const float4 sg = v.seg[i];
 #pragma unroll
                         for (int c = -1; c <= 1; ++c) {
                             const float cx_ = qx + (float)c * kCircD * hx, cy_ = qy + (float)c * kCircD * hy;
@@ -623,32 +665,32 @@ __device__ Lane coop_nearest_lane(const DevRoads& rd, const DevGrid& g, float qx
         if (best != kKeyInf || w.all) break;
         S = Rl * kGrow + kSegReach;
     }
-    return lane_of(rd, best, qx, qy, gx, gy);
+    return lane_of(v, best, qx, qy, gx, gy);
 }
 
 // the 32 nearest road points (all types), exact; lane t returns the t-th key.
 // Only points closer than R compete; if fewer than 32 are, R grows.
 // buf: 64 keys of shared memory owned by the calling warp.
-__device__ unsigned long long coop_knn32(const DevRoads& rd, const DevGrid& g, float qx, float qy, float R, int lane,
+__device__ unsigned long long coop_knn32(const WRoads& v, float qx, float qy, float R, int lane,
                                          unsigned long long* buf) {
     const unsigned lt = (1u << lane) - 1u;
     unsigned long long run = kKeyInf;
     for (;;) {
-        const Rows w = rows_covering(g, qx, qy, R);
+        const Rows w = rows_covering(v, qx, qy, R);
         unsigned long long thr = w.all ? kKeyInf : key_of(R * R * (1.f - 1e-5f), 0);
         run = kKeyInf;
         int cnt = 0;
         if (w.cx0 <= w.cx1)
             for (int cy = w.cy0; cy <= w.cy1; ++cy) {
-                const int row = g.cbase + cy * g.nx;
-                const int s = __ldg(&rd.cell_off[row + w.cx0]), e = __ldg(&rd.cell_off[row + w.cx1 + 1]);
+                const int row = cy * v.nx;
+                const int s = v.coff[row + w.cx0], e = v.coff[row + w.cx1 + 1];
                 for (int base = s; base < e; base += 32) {
                     const int i = base + lane;
                     unsigned long long key = kKeyInf;
                     if (i < e) {
-                        const float4 P = __ldg(&rd.sseg[i]);
+                        const float4 P = v.seg[i];
                         const float dx = P.x - qx, dy = P.y - qy;
-                        key = key_of(dx * dx + dy * dy, __ldg(&rd.sidx[i]));
+                        key = rkey(dx * dx + dy * dy, v.info[i], i);
                         if (key >= thr) key = kKeyInf;
                     }
                     const unsigned m = __ballot_sync(kFull, key != kKeyInf);
@@ -679,8 +721,7 @@ __device__ unsigned long long coop_knn32(const DevRoads& rd, const DevGrid& g, f
 
 // time for the constant-velocity ray from an agent to reach the nearest road
 // edge segment within 40 m (App. G)
-__device__ float coop_edge_ray(const DevRoads& rd, const DevGrid& g, float px, float py, float vx, float vy,
-                               int lane) {
+__device__ float coop_edge_ray(const WRoads& v, float px, float py, float vx, float vy, int lane) {
     // ray p + v t against every edge segment; the acceptance tests t >= 0,
     // 0 <= s <= 1 and |v| t <= 40 m are evaluated multiplied through by the
     // denominator (sign-aware), and only accepted hits divide.  A segment whose
@@ -688,8 +729,8 @@ __device__ float coop_edge_ray(const DevRoads& rd, const DevGrid& g, float px, f
     const float speed = sqrtf(vx * vx + vy * vy);
     const float reach2 = (kEdgeHorizon + kSegReach) * (kEdgeHorizon + kSegReach);
     float t_best = kInf;
-    for (int i = lane; i < g.ecnt; i += 32) {
-        const float4 sg4 = __ldg(&rd.eseg[g.eoff + i]);
+    for (int i = lane; i < v.ecnt; i += 32) {
+        const float4 sg4 = v.edge[i];
         const float apx = sg4.x - px, apy = sg4.y - py;
         if (apx * apx + apy * apy > reach2) continue;
         const float exx = sg4.z - sg4.x, eyy = sg4.w - sg4.y;
@@ -701,6 +742,27 @@ __device__ float coop_edge_ray(const DevRoads& rd, const DevGrid& g, float px, f
         if (ok) t_best = fminf(t_best, nt / den);
     }
     return warp_min(t_best);
+}
+
+// road-point features of the observation (App. D analogue) from a k-NN key
+__device__ __forceinline__ void point_features(const WRoads& v, unsigned long long key, float ehx, float ehy,
+                                               float epx, float epy, float f[kObsPt]) {
+    const int pos = rkey_pos(key);
+    const float4 r = v.seg[pos];
+    const uint32_t m = v.info[pos];
+    // road direction at the point: toward the next point of the polyline,
+    // from the previous one at a polyline's end
+    float ddx = r.z - r.x, ddy = r.w - r.y;
+    if (!(m & kInfoHasNext)) { ddx = -ddx; ddy = -ddy; }
+    const float nn = sqrtf(ddx * ddx + ddy * ddy);
+    if (nn > 0.f) { ddx /= nn; ddy /= nn; } else { ddx = ddy = 0.f; }
+    float bx, by, dbx, dby;
+    to_ego(ehx, ehy, r.x - epx, r.y - epy, bx, by);
+    to_ego(ehx, ehy, ddx, ddy, dbx, dby);
+    f[0] = bx / 10.f; f[1] = by / 10.f; f[2] = dbx; f[3] = dby;
+    f[4] = (float)((m >> 16) & 0xFFu) / 20.f;
+    f[5] = (m & kInfoEdge) ? 1.f : 0.f;
+    f[6] = 1.f;
 }
 
 // ------------------------------------------------------------------ dynamics surrogate
@@ -863,16 +925,408 @@ __device__ __forceinline__ bool surr_gate(const Exch& E, int base, int n, int la
 }
 
 // per-agent results of the cooperative queries
-struct AgentQ {
-    int seg;
-    float dist, lat, tx, ty, tedge;
-    int forb, need;
-};
 
 }  // namespace
 
-// ====================================================================== the world kernel
-// One CTA per pack: consecutive worlds holding at most 32 agents together (one
+// ------------------------------------------------------------------ road staging
+// A block copies the road blobs of its pack's worlds into shared memory with
+// one bulk (TMA) copy per world, completing on an mbarrier; the copy is issued
+// before the physics and waited for before the first road query.  Every wait
+// is bounded (1 s): on expiry the error word gets bit 1 and the queries read
+// the blobs from global memory instead.
+constexpr uint64_t kStageWaitNs = 1000000000ull;
+constexpr uint32_t kStageSpinMax = 1u << 30;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool stage_done(uint64_t* bar) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar))
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ bool stage_wait(uint64_t* bar) {
+    if (stage_done(bar)) return true;
+    const uint64_t t0 = now_ns();
+    for (uint32_t i = 0; i < kStageSpinMax; ++i) {
+        if (stage_done(bar)) return true;
+        if ((i & 63) == 63 && now_ns() - t0 > kStageWaitNs) break;
+    }
+    return false;
+}
+// warp 0: lane 0 arms the barrier for `total` bytes, lane t copies world t
+__device__ void stage_issue(const unsigned char* gblob, const DevGrid* sg, const int* woff, int nworlds, int total,
+                            unsigned char* dst, uint64_t* bar, int lane) {
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(total)
+                     : "memory");
+    }
+    __syncwarp();
+    if (lane < nworlds && sg[lane].bytes > 0)
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_addr(dst + woff[lane])),
+                     "l"(gblob + sg[lane].blob), "r"(sg[lane].bytes), "r"(smem_addr(bar))
+                     : "memory");
+}
+
+// ====================================================================== step building blocks
+// Used by the fused world kernel and by the split step alike (the same inline
+// code, so that both give bit-identical results).
+
+// a lane of the agent warp: its slot in the block's pack and its world
+struct Slot {
+    bool has;       // the lane holds an agent
+    int a;          // agent index (the pack's first agent for lanes without one)
+    int wl, w;      // pack-local world, world id
+    int base, n;    // the world's first slot and its agent count
+};
+
+__device__ __forceinline__ Slot slot_of(const int4& pk, const int* s_slot_w, const int* s_wbase, const int* s_wn,
+                                        int lane, bool warp0) {
+    Slot c;
+    c.has = warp0 && lane < pk.w;
+    c.a = pk.z + (c.has ? lane : 0);
+    c.wl = 0; c.w = pk.x; c.base = 0; c.n = 0;
+    if (c.has) {
+        c.wl = s_slot_w[lane];
+        c.w = pk.x + c.wl;
+        c.base = s_wbase[c.wl];
+        c.n = s_wn[c.wl];
+    }
+    return c;
+}
+
+// the pack's slot tables (warp 0, lanes < worlds of the pack)
+__device__ __forceinline__ void pack_tables(const WorldArgs& args, const int4& pk, int lane, int* s_slot_w,
+                                            int* s_wbase, int* s_wn) {
+    if (lane < pk.y) {
+        const int4 wd = __ldg(&args.rd.world[pk.x + lane]);
+        s_wbase[lane] = wd.x - pk.z;
+        s_wn[lane] = wd.y;
+        for (int k = 0; k < wd.y; ++k) s_slot_w[wd.x - pk.z + k] = lane;
+    }
+    __syncwarp();
+}
+
+// physics of one control step for the lanes of the agent warp (Sec. 4.1,
+// App. F): action decode, substeps with footprint contact through the
+// exchange area every substep, the surrogate for gated agents, the
+// non-finite check; the post-step pose is published in E at the end
+__device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot& c, int lane, Agent& A, bool& alive,
+                                              bool& nonfin, float& prevx, float& prevy, float& hx, float& hy,
+                                              Exch& E) {
+    const DevState& st = args.st;
+    const int a = c.a, base = c.base, n = c.n;
+    float thr = 0.f, dstar = 0.f, brk = 0.f;
+    if (alive) {
+        const float* act = args.actions + 3 * (size_t)a;
+        thr = clampf(act[0], 0.f, 1.f);
+        dstar = kThetaMax * clampf(act[1], -1.f, 1.f);
+        brk = clampf(act[2], 0.f, 1.f);
+    }
+    prevx = A.px; prevy = A.py;
+    bool gated = false;
+    for (int s = 0; s < args.substeps; ++s) {
+        float sx_, sy_;
+        heading_of(A.qw, A.qx, A.qy, A.qz, sx_, sy_);
+        publish(E, lane, A, sx_, sy_);
+        const uint32_t alive_bits = __ballot_sync(kFull, alive);
+        __syncwarp();
+        if (s == 0 && args.surr_mode != 0) gated = surr_gate(E, base, n, lane, alive_bits, A, args.h * args.substeps);
+        float fcx = 0.f, fcy = 0.f, tcz = 0.f;
+        if (alive) {
+            for (int j = base; j < base + n; ++j) {
+                if (j == lane || !((alive_bits >> j) & 1u)) continue;
+                const int lo = min(lane, j), hi = max(lane, j);
+                float fx, fy, tz;
+                pair_force(E.px[lo], E.py[lo], E.dx[lo], E.dy[lo], E.hx[lo], E.hy[lo], E.vx[lo], E.vy[lo],
+                           E.px[hi], E.py[hi], E.dx[hi], E.dy[hi], E.hx[hi], E.hy[hi], E.vx[hi], E.vy[hi],
+                           fx, fy, tz);
+                if (lane == lo) { fcx -= fx; fcy -= fy; } else { fcx += fx; fcy += fy; }
+                tcz += tz;
+            }
+        }
+        __syncwarp();
+        if (alive) {
+            if (gated && args.surr_mode == 1) steer_substep(A, dstar, args.h);   // chassis from the surrogate
+            else body_substep(A, thr, dstar, brk, fcx, fcy, tcz, args.h);
+        }
+    }
+    A.px += A.dpx; A.py += A.dpy; A.pz += A.dpz;
+    A.dpx = A.dpy = A.dpz = 0.f;
+    if (gated) {
+        // the start-of-step state is still in global memory (stored after the physics)
+        const float4 p0 = st.pos[a], q0 = st.quat[a], v0 = st.vel[a], w0 = st.angv[a], s0 = st.spin[a];
+        float d[kSurrOut];
+        const float* yn = args.surr_y + (size_t)a * kSurrOut;
+#pragma unroll
+        for (int k = 0; k < kSurrOut; ++k) d[k] = args.surr_stats[k] + args.surr_stats[kSurrOut + k] * yn[k];
+        const float dt = args.h * args.substeps;
+        if (args.surr_mode == 1) {
+            surr_apply(p0, q0, v0, w0, s0, d, dt, A);
+            atomicAdd(args.surr_count, 1u);
+        } else {
+            Agent P = A;
+            surr_apply(p0, q0, v0, w0, s0, d, dt, P);
+            const float ex = P.px - A.px, ey = P.py - A.py, ez = P.pz - A.pz;
+            atomicMax(args.audit_err, __float_as_uint(sqrtf(ex * ex + ey * ey + ez * ez)));
+        }
+    }
+    if (alive && !finite_agent(A)) {
+        nonfin = true;
+        park_agent(A);
+        alive = false;
+        atomicOr(args.out.error_word, 1u);
+    }
+    heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
+    publish(E, lane, A, hx, hy);
+}
+
+// road queries of the events for one agent (all lanes of a warp): nearest
+// lane with the lane-forbidden test, the edge ray; the lane hint is updated
+__device__ __forceinline__ AgentQ agent_event_queries(const WRoads& v, float px, float py, float gx, float gy,
+                                                      float hx, float hy, float vx, float vy, float* hnt, int lane) {
+    bool forb = false;
+    const Lane L = coop_nearest_lane(v, px, py, gx, gy, hint_radius(hnt, 1, px, py, kLaneR0), lane, &forb, hx, hy);
+    __syncwarp();
+    if (lane == 0) hnt[1] = L.seg >= 0 ? L.dist : 0.f;
+    const float tedge = coop_edge_ray(v, px, py, vx, vy, lane);
+    AgentQ q;
+    q.seg = L.seg; q.dist = L.dist; q.lat = L.lat; q.tx = L.tx; q.ty = L.ty;
+    q.tedge = tedge; q.forb = forb ? 1 : 0; q.need = 0;
+    return q;
+}
+
+// road-point block of one agent's observation (all lanes of a warp).  With
+// `need` (the agent was respawned) the nearest lane is first recomputed from
+// the default radius into *L; the 32 nearest points start from the hinted
+// radius (the default after a respawn); the hints are updated.  orow gets the
+// 32 x 7 features (zeros when !alive), knn_row (may be null) the indices.
+__device__ __forceinline__ void agent_road_block(const WRoads& v, bool alive, bool need, float px, float py,
+                                                 float gx, float gy, float hx, float hy, float* hnt, int lane,
+                                                 unsigned long long* kbuf, float* orow, int32_t* knn_row, Lane* L) {
+    unsigned long long key = kKeyInf;
+    if (alive) {
+        if (need) {
+            *L = coop_nearest_lane(v, px, py, gx, gy, kLaneR0, lane);
+            __syncwarp();
+            if (lane == 0) hnt[1] = L->seg >= 0 ? L->dist : 0.f;
+        }
+        const float r32 = need ? kKnnR0 : hint_radius(hnt, 0, px, py, kKnnR0);
+        __syncwarp();
+        key = coop_knn32(v, px, py, r32, lane, kbuf);
+        const unsigned long long last = shfl64(key, 31);
+        if (lane == 0) {
+            hnt[0] = last != kKeyInf ? sqrtf(key_d2(last)) : 0.f;
+            hnt[2] = px;
+            hnt[3] = py;
+        }
+    }
+    float f[kObsPt] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (key != kKeyInf) point_features(v, key, hx, hy, px, py, f);
+#pragma unroll
+    for (int k = 0; k < kObsPt; ++k) orow[kObsPt * lane + k] = f[k];
+    if (knn_row) knn_row[lane] = key != kKeyInf ? v.q0 + rkey_local(key) : -1;
+}
+
+// events and rewards of the lanes of the agent warp (App. G); done agents are
+// marked for a respawn (auto-reset) or parked
+__device__ __forceinline__ void lanes_events(const WorldArgs& args, const Slot& c, int lane, Agent& A, bool& alive,
+                                             bool nonfin, float prevx, float prevy, float hx, float hy,
+                                             uint32_t alive_bits, const AgentQ* qp, const Exch& E, int (&nb)[kK],
+                                             float (&tt)[kK], uint32_t& ev, float& reward, float& drac, bool& done,
+                                             bool& respawn, bool& parked_now) {
+    const int base = c.base, n = c.n;
+    if (alive) {
+        const AgentQ q = *qp;
+        A.step += 1;
+        const float speed = sqrtf(A.vx * A.vx + A.vy * A.vy);
+        float r = 0.f;
+        if (q.seg >= 0) {
+            float prog = (A.px - prevx) * q.tx + (A.py - prevy) * q.ty;
+            r += kWProgress * clampf(prog, -kProgressClip, kProgressClip);
+            float e = q.lat / kLaneSigma;
+            float cosd = hx * q.tx + hy * q.ty;
+            r += kWLane * (expf(-e * e) * ((1.f - kLaneWh) + kLaneWh * fmaxf(0.f, cosd)));
+        }
+        if (fabsf(q.lat) > kOffroadLat || q.dist > kOffroadDist) { ev |= kEvOffroad; r -= kWOffroad; }
+        if (speed < kIdleSpeed) { ev |= kEvIdle; r -= kWIdle; }
+        knn_agents(E, base, n, lane, alive_bits, A.px, A.py, nb);
+        float tmin = kTtcMax, dmax = 0.f;
+#pragma unroll
+        for (int t = 0; t < kK; ++t) {
+            if (nb[t] < 0) continue;
+            const int j = nb[t];
+            tt[t] = ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j], E.vx[j], E.vy[j]);
+            tmin = fminf(tmin, tt[t]);
+            dmax = fmaxf(dmax, drac_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j],
+                                         E.vx[j], E.vy[j]));
+        }
+        if (tmin < kTtcMax) r -= penalty(kTtcAlphaV, tmin, kTtcPmaxV);
+        r -= kWDrac * fmaxf(0.f, dmax - kDracThresh);
+        drac = dmax;
+        A.peak = fmaxf(A.peak, dmax);
+        bool collided = false;
+        for (int j = base; j < base + n && !collided; ++j) {
+            if (j == lane || !((alive_bits >> j) & 1u)) continue;
+            float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
+            if (dx * dx + dy * dy > kPairCull2) continue;
+            float nx, ny;
+            if (sat2d(A.px, A.py, hx, hy, E.px[j], E.py[j], E.hx[j], E.hy[j], nx, ny) > 0.f) collided = true;
+        }
+        if (collided && A.step > kWarmup) ev |= kEvCollision;
+        if (q.tedge < kInf) r -= penalty(kTtcAlphaE, q.tedge, kTtcPmaxE);
+        if (q.forb) ev |= kEvLaneForb;
+        float gdx = A.gx - A.px, gdy = A.gy - A.py;
+        if (sqrtf(gdx * gdx + gdy * gdy) <= kGoalR) ev |= kEvGoal;
+        float r22 = 1.f - 2.f * (A.qx * A.qx + A.qy * A.qy);
+        float sdx = A.px - A.sx, sdy = A.py - A.sy;
+        if (A.pz < 0.f || sqrtf(sdx * sdx + sdy * sdy) > kDriftMax || -r22 > kTiltGz) ev |= kEvCrash;
+        if (ev & kEvGoal) r += kWGoal;
+        else if (ev & kEvCollision) r -= kWCollision;
+        else if (ev & kEvCrash) r -= kWCrash;
+        else if (ev & kEvLaneForb) r -= kWLaneForb;
+        if (A.step >= kMaxSteps) ev |= kEvTimeout;
+        reward = r;
+    }
+    if (nonfin) { ev = kEvNonfinite; reward = 0.f; }
+    const uint32_t sparse = kEvGoal | kEvCollision | kEvCrash | kEvLaneForb;
+    const bool term = nonfin || (!(args.flags & kFlagInvincible) && (ev & sparse));
+    done = term || (ev & kEvTimeout);
+    if (done) {
+        if (args.flags & kFlagAutoReset) respawn = true;
+        else if (!nonfin) { park_agent(A); alive = false; parked_now = true; }
+    }
+}
+
+// respawns of the marked lanes (App. J), every slot of the pack in index
+// order, each spaced from the other alive agents of its own world
+__device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot& c, int lane, int m, Agent& A,
+                                              bool& alive, bool respawn, uint32_t& ev) {
+    const uint32_t rbits = __ballot_sync(kFull, respawn);
+    if (!rbits) return;
+    const unsigned long long seed = args.seed;
+    for (int l = 0; l < m; ++l) {
+        if (!((rbits >> l) & 1u)) continue;
+        const int ep = __shfl_sync(kFull, A.episode, l) + 1;
+        const bool same = __shfl_sync(kFull, c.wl, l) == c.wl;
+        float bx = 0.f, by = 0.f, bpsi = 0.f, bv = kSpawnVMin, bgx = kSpawnGoalMin, bgy = 0.f, bscore = -1.f;
+        const bool elig = alive && same && lane != l && !(lane > l && ((rbits >> lane) & 1u));
+        for (int r = 0; r < kSpawnTries; ++r) {
+            float x = 0.f, y = 0.f, psi = 0.f, gx = 0.f, gy = 0.f, v0 = 0.f;
+            if (lane == l) spawn_candidate(args.rd, c.w, c.a, l - c.base, ep, r, seed, x, y, psi, gx, gy, v0);
+            x = __shfl_sync(kFull, x, l);
+            y = __shfl_sync(kFull, y, l);
+            float d2 = kInf;
+            if (elig) {
+                float dx = A.px - x, dy = A.py - y;
+                d2 = dx * dx + dy * dy;
+            }
+            const float dmin = warp_min(d2);
+            if (lane == l && dmin > bscore) { bscore = dmin; bx = x; by = y; bpsi = psi; bv = v0; bgx = gx; bgy = gy; }
+            if (dmin >= kSpawnSpacing * kSpawnSpacing) break;
+        }
+        if (lane == l) {
+            place_agent(A, bx, by, bpsi, bv, bgx, bgy);
+            A.episode = ep;
+            alive = true;
+            ev |= kEvRespawned;
+        }
+        __syncwarp();
+    }
+}
+
+// neighbours, ego group, outputs and state of the lanes of the agent warp
+template <int MODE>
+__device__ __forceinline__ void lanes_final(const WorldArgs& args, const Slot& c, int lane, Agent& A, bool alive,
+                                            bool recompute, bool active, uint32_t alive_bits, const AgentQ* qp,
+                                            const Exch& E, int (&nb)[kK], const float (&tt)[kK], float hx, float hy,
+                                            uint32_t ev, float reward, bool done, float drac, bool respawn) {
+    if (recompute) knn_agents(E, c.base, c.n, lane, alive_bits, A.px, A.py, nb);
+    if (!(c.has && active)) return;
+    const int a = c.a;
+    float4* o4 = reinterpret_cast<float4*>(args.out.obs + (size_t)a * kObsDim);
+    AgentQ q;
+    q.seg = -1;
+    if (alive) {
+        q = *qp;
+        float gbx, gby, vbx, vby;
+        to_ego(hx, hy, A.gx - A.px, A.gy - A.py, gbx, gby);
+        to_ego(hx, hy, A.vx, A.vy, vbx, vby);
+        float gn = sqrtf(gbx * gbx + gby * gby);
+        uint32_t pc = A.meta & 0xFFu, sc = (A.meta >> 8) & 0xFFu;
+        o4[0] = make_float4(gbx / kSceneHalf, gby / kSceneHalf, gn > 0.f ? gby / gn : 0.f, gn > 0.f ? gbx / gn : 1.f);
+        o4[1] = make_float4(gn / kSceneHalf, vbx / 10.f, vby / 10.f, (float)pc / 3.f);
+        o4[2] = make_float4(sc == 0 ? 1.f : 0.f, sc == 1 ? 1.f : 0.f, sc == 2 ? 1.f : 0.f, A.wz);
+        o4[3] = make_float4(A.dl / kThetaMax, A.mu, q.seg >= 0 ? q.lat / 3.6f : 0.f,
+                            q.seg >= 0 ? cross2(q.tx, q.ty, hx, hy) : 0.f);
+#pragma unroll
+        for (int t2 = 0; t2 < kK / 2; ++t2) {
+            float f[20];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int j = nb[2 * t2 + u];
+                float* s = f + 10 * u;
+                if (j < 0) {
+#pragma unroll
+                    for (int k = 0; k < 10; ++k) s[k] = 0.f;
+                    continue;
+                }
+                float pjx = E.px[j], pjy = E.py[j], hjx = E.hx[j], hjy = E.hy[j], vjx = E.vx[j], vjy = E.vy[j];
+                float bx, by, dvx, dvy;
+                to_ego(hx, hy, pjx - A.px, pjy - A.py, bx, by);
+                to_ego(hx, hy, vjx - A.vx, vjy - A.vy, dvx, dvy);
+                float dpsi = atan2f(cross2(hx, hy, hjx, hjy), hx * hjx + hy * hjy);
+                s[0] = bx / kSceneHalf;
+                s[1] = by / kSceneHalf;
+                s[2] = 2.f * kHalfLen / kSceneHalf;
+                s[3] = 2.f * kHalfWid / kSceneHalf;
+                s[4] = dpsi / 3.14159265358979323846f;
+                s[5] = sqrtf(vjx * vjx + vjy * vjy) / 10.f;
+                s[6] = dvx / 10.f;
+                s[7] = dvy / 10.f;
+                s[8] = (recompute ? ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, pjx, pjy, hjx, hjy, vjx, vjy)
+                                  : tt[2 * t2 + u]) / kTtcMax;
+                s[9] = 1.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                o4[(kObsEgo + 20 * t2) / 4 + k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < (kObsEgo + kK * kObsNbr) / 4; ++k) o4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (args.flags & kFlagRecord) {
+        args.out.lane_seg[a] = alive ? q.seg : -1;
+#pragma unroll
+        for (int t = 0; t < kK; ++t)
+            args.out.knn_agents[(size_t)a * kK + t] = (alive && nb[t] >= 0) ? (a - lane) + nb[t] : -1;
+    }
+    if (MODE == kModeStep) {
+        args.out.reward[a] = reward;
+        args.out.done[a] = done ? 1 : 0;
+        args.out.events[a] = ev;
+        args.out.drac[a] = drac;
+    } else if (MODE == kModeReset && respawn) {
+        args.out.events[a] = ev;
+    }
+    store_agent(args.st, a, A);
+}
+
+// ====================================================================== the fused world kernel
+// One block per pack: consecutive worlds holding at most 32 agents together (one
 // world per pack unless packing is enabled).  Warp 0 owns the agents (lane l =
 // slot l = agent a0 + l): physics, events, respawns, neighbours, ego
 // features, state; a lane only ever interacts with the slots of its own
@@ -885,35 +1339,46 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     __shared__ unsigned long long kbuf[NW][64];
     __shared__ unsigned s_alive, s_any, s_act;
     __shared__ int s_slot_w[32];                  // pack-local world of each slot
-    __shared__ int s_wid[32], s_wbase[32];        // per pack-local world: world id, first slot
+    __shared__ int s_wbase[32], s_wn[32];         // per pack-local world: first slot, agents
+    __shared__ int s_woff[32];                    // its blob's offset in s_blob, -1: read from global memory
+    __shared__ DevGrid s_grid[32];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ int s_staged;
+    extern __shared__ __align__(128) unsigned char s_blob[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int4 pk = __ldg(&args.packs[blockIdx.x]);   // (first world, worlds, first agent, agents)
     const int a0 = pk.z, m = pk.w;
     if (m <= 0) return;                               // CTA-uniform
+    bool staged = false;                              // warp 0: this block copies its roads to shared memory
+    int stage_total = 0;
     if (warp == 0) {
+        pack_tables(args, pk, lane, s_slot_w, s_wbase, s_wn);
+        int bytes = 0;
         if (lane < pk.y) {
-            const int4 wd = __ldg(&args.rd.world[pk.x + lane]);
-            s_wid[lane] = pk.x + lane;
-            s_wbase[lane] = wd.x - a0;
-            for (int k = 0; k < wd.y; ++k) s_slot_w[wd.x - a0 + k] = lane;
+            const DevGrid gg = args.rd.grid[pk.x + lane];
+            s_grid[lane] = gg;
+            bytes = gg.bytes;
         }
+        int incl = bytes;                             // prefix sum of the blob sizes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        stage_total = __shfl_sync(kFull, incl, 31);
+        staged = args.stage_bytes > 0 && stage_total > 0 && stage_total <= args.stage_bytes;
+        if (lane < pk.y) s_woff[lane] = staged ? incl - bytes : -1;
+        if (lane == 0) s_staged = staged ? 1 : 0;
         __syncwarp();
+        if (staged && MODE != kModeReset)
+            stage_issue(args.rd.blob, s_grid, s_woff, pk.y, stage_total, s_blob, &s_bar, lane);
     }
-    const DevState& st = args.st;
 
     // ---------------- warp 0: agent registers
-    const bool has = warp == 0 && lane < m;
-    const int a = a0 + (has ? lane : 0);
-    int wl = 0, w = pk.x, base = 0, n = 0;            // the lane's world, its first slot and agent count
-    if (has) {
-        wl = s_slot_w[lane];
-        w = s_wid[wl];
-        base = s_wbase[wl];
-        n = __ldg(&args.rd.world[w]).y;
-    }
+    const Slot c = slot_of(pk, s_slot_w, s_wbase, s_wn, lane, warp == 0);
     Agent A;
     bool alive = false, respawn = false, parked_now = false, nonfin = false, done = false;
-    bool recompute = false, active_out = false;   // warp 0: neighbours recomputed / outputs written
+    bool recompute = false, active = false;       // warp 0: neighbours recomputed / outputs written
     uint32_t ev = 0;
     float reward = 0.f, drac = 0.f, hx = 1.f, hy = 0.f;
     int nb[kK];
@@ -921,217 +1386,61 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
 #pragma unroll
     for (int t = 0; t < kK; ++t) { nb[t] = -1; tt[t] = kTtcMax; }
     if (warp == 0) {
-        load_agent(st, a, A);
-        if (!has) A.meta = 0;
-        alive = has && (status_of(A.meta) & kAlive);
-        if (MODE == kModeReset) respawn = has && args.mask[a] != 0;
+        load_agent(args.st, c.a, A);
+        if (!c.has) A.meta = 0;
+        alive = c.has && (status_of(A.meta) & kAlive);
+        if (MODE == kModeReset) respawn = c.has && args.mask[c.a] != 0;
         const unsigned anyr = __ballot_sync(kFull, respawn);
         if (lane == 0) s_any = anyr;
     }
     if (MODE == kModeReset) {
         __syncthreads();
-        if (s_any == 0u) return;                      // CTA-uniform: no masked agent in this world
+        if (s_any == 0u) return;                      // CTA-uniform: no masked agent in this pack
+        if (warp == 0 && staged)
+            stage_issue(args.rd.blob, s_grid, s_woff, pk.y, stage_total, s_blob, &s_bar, lane);
     }
+    bool stg = false;                                 // this thread reads the staged copies
 
     if (MODE == kModeStep) {
         float prevx = 0.f, prevy = 0.f;
         if (warp == 0) {
-            float thr = 0.f, dstar = 0.f, brk = 0.f;
-            if (alive) {
-                const float* act = args.actions + 3 * (size_t)a;
-                thr = clampf(act[0], 0.f, 1.f);
-                dstar = kThetaMax * clampf(act[1], -1.f, 1.f);
-                brk = clampf(act[2], 0.f, 1.f);
-            }
-            prevx = A.px; prevy = A.py;
-            bool gated = false;
-            for (int s = 0; s < args.substeps; ++s) {
-                float sx_, sy_;
-                heading_of(A.qw, A.qx, A.qy, A.qz, sx_, sy_);
-                publish(E, lane, A, sx_, sy_);
-                const uint32_t alive_bits = __ballot_sync(kFull, alive);
-                __syncwarp();
-                if (s == 0 && args.surr_mode != 0) gated = surr_gate(E, base, n, lane, alive_bits, A, args.h * args.substeps);
-                float fcx = 0.f, fcy = 0.f, tcz = 0.f;
-                if (alive) {
-                    for (int j = base; j < base + n; ++j) {
-                        if (j == lane || !((alive_bits >> j) & 1u)) continue;
-                        const int lo = min(lane, j), hi = max(lane, j);
-                        float fx, fy, tz;
-                        pair_force(E.px[lo], E.py[lo], E.dx[lo], E.dy[lo], E.hx[lo], E.hy[lo], E.vx[lo], E.vy[lo],
-                                   E.px[hi], E.py[hi], E.dx[hi], E.dy[hi], E.hx[hi], E.hy[hi], E.vx[hi], E.vy[hi],
-                                   fx, fy, tz);
-                        if (lane == lo) { fcx -= fx; fcy -= fy; } else { fcx += fx; fcy += fy; }
-                        tcz += tz;
-                    }
-                }
-                __syncwarp();
-                if (alive) {
-                    if (gated && args.surr_mode == 1) steer_substep(A, dstar, args.h);   // chassis from the surrogate
-                    else body_substep(A, thr, dstar, brk, fcx, fcy, tcz, args.h);
-                }
-            }
-            A.px += A.dpx; A.py += A.dpy; A.pz += A.dpz;
-            A.dpx = A.dpy = A.dpz = 0.f;
-            if (gated) {
-                // the start-of-step state is still in global memory (stored at the end of the kernel)
-                const float4 p0 = st.pos[a], q0 = st.quat[a], v0 = st.vel[a], w0 = st.angv[a], s0 = st.spin[a];
-                float d[kSurrOut];
-                const float* yn = args.surr_y + (size_t)a * kSurrOut;
-#pragma unroll
-                for (int k = 0; k < kSurrOut; ++k) d[k] = args.surr_stats[k] + args.surr_stats[kSurrOut + k] * yn[k];
-                const float dt = args.h * args.substeps;
-                if (args.surr_mode == 1) {
-                    surr_apply(p0, q0, v0, w0, s0, d, dt, A);
-                    atomicAdd(args.surr_count, 1u);
-                } else {
-                    Agent P = A;
-                    surr_apply(p0, q0, v0, w0, s0, d, dt, P);
-                    const float ex = P.px - A.px, ey = P.py - A.py, ez = P.pz - A.pz;
-                    atomicMax(args.audit_err, __float_as_uint(sqrtf(ex * ex + ey * ey + ez * ez)));
-                }
-            }
-            if (alive && !finite_agent(A)) {
-                nonfin = true;
-                park_agent(A);
-                alive = false;
-                atomicOr(args.out.error_word, 1u);
-            }
-            heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
-            publish(E, lane, A, hx, hy);
+            lanes_physics(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E);
             const unsigned ab = __ballot_sync(kFull, alive);
             if (lane == 0) s_alive = ab;
         }
         __syncthreads();
+        if (s_staged) {
+            stg = stage_wait(&s_bar);
+            if (!stg) atomicOr(args.out.error_word, 2u);
+        }
         // ---------------- road queries of the events (all warps, one agent at a time)
         for (int j = warp; j < m; j += NW) {
             if (!((s_alive >> j) & 1u)) continue;
-            const DevGrid g = args.rd.grid[s_wid[s_slot_w[j]]];
-            float* hnt = args.out.hint + 2 * (size_t)(a0 + j);
-            const float hl = hnt[1];
-            bool forb = false;
-            const Lane L = coop_nearest_lane(args.rd, g, E.px[j], E.py[j], E.gx[j], E.gy[j],
-                                             hl > 0.f ? hl + kHintSlack : kLaneR0, lane, &forb, E.hx[j], E.hy[j]);
-            if (lane == 0) hnt[1] = L.seg >= 0 ? L.dist : 0.f;
-            const float tedge = coop_edge_ray(args.rd, g, E.px[j], E.py[j], E.vx[j], E.vy[j], lane);
-            if (lane == 0) {
-                AgentQ q;
-                q.seg = L.seg; q.dist = L.dist; q.lat = L.lat; q.tx = L.tx; q.ty = L.ty;
-                q.tedge = tedge; q.forb = forb ? 1 : 0; q.need = 0;
-                Q[j] = q;
-            }
+            const int t = s_slot_w[j];
+            const WRoads v = view_of(s_grid[t], (stg && s_woff[t] >= 0) ? s_blob + s_woff[t]
+                                                                         : args.rd.blob + s_grid[t].blob);
+            const AgentQ q = agent_event_queries(v, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j], E.vx[j],
+                                                 E.vy[j], args.out.hint + 4 * (size_t)(a0 + j), lane);
+            if (lane == 0) Q[j] = q;
         }
         __syncthreads();
         // ---------------- events and rewards (App. G), warp 0
-        if (warp == 0) {
-            const uint32_t alive_bits = s_alive;
-            if (alive) {
-                const AgentQ q = Q[lane];
-                A.step += 1;
-                const float speed = sqrtf(A.vx * A.vx + A.vy * A.vy);
-                float r = 0.f;
-                if (q.seg >= 0) {
-                    float prog = (A.px - prevx) * q.tx + (A.py - prevy) * q.ty;
-                    r += kWProgress * clampf(prog, -kProgressClip, kProgressClip);
-                    float e = q.lat / kLaneSigma;
-                    float cosd = hx * q.tx + hy * q.ty;
-                    r += kWLane * (expf(-e * e) * ((1.f - kLaneWh) + kLaneWh * fmaxf(0.f, cosd)));
-                }
-                if (fabsf(q.lat) > kOffroadLat || q.dist > kOffroadDist) { ev |= kEvOffroad; r -= kWOffroad; }
-                if (speed < kIdleSpeed) { ev |= kEvIdle; r -= kWIdle; }
-                knn_agents(E, base, n, lane, alive_bits, A.px, A.py, nb);
-                float tmin = kTtcMax, dmax = 0.f;
-#pragma unroll
-                for (int t = 0; t < kK; ++t) {
-                    if (nb[t] < 0) continue;
-                    const int j = nb[t];
-                    tt[t] = ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j], E.vx[j],
-                                     E.vy[j]);
-                    tmin = fminf(tmin, tt[t]);
-                    dmax = fmaxf(dmax, drac_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j],
-                                                 E.vx[j], E.vy[j]));
-                }
-                if (tmin < kTtcMax) r -= penalty(kTtcAlphaV, tmin, kTtcPmaxV);
-                r -= kWDrac * fmaxf(0.f, dmax - kDracThresh);
-                drac = dmax;
-                A.peak = fmaxf(A.peak, dmax);
-                bool collided = false;
-                for (int j = base; j < base + n && !collided; ++j) {
-                    if (j == lane || !((alive_bits >> j) & 1u)) continue;
-                    float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
-                    if (dx * dx + dy * dy > kPairCull2) continue;
-                    float nx, ny;
-                    if (sat2d(A.px, A.py, hx, hy, E.px[j], E.py[j], E.hx[j], E.hy[j], nx, ny) > 0.f) collided = true;
-                }
-                if (collided && A.step > kWarmup) ev |= kEvCollision;
-                if (q.tedge < kInf) r -= penalty(kTtcAlphaE, q.tedge, kTtcPmaxE);
-                if (q.forb) ev |= kEvLaneForb;
-                float gdx = A.gx - A.px, gdy = A.gy - A.py;
-                if (sqrtf(gdx * gdx + gdy * gdy) <= kGoalR) ev |= kEvGoal;
-                float r22 = 1.f - 2.f * (A.qx * A.qx + A.qy * A.qy);
-                float sdx = A.px - A.sx, sdy = A.py - A.sy;
-                if (A.pz < 0.f || sqrtf(sdx * sdx + sdy * sdy) > kDriftMax || -r22 > kTiltGz) ev |= kEvCrash;
-                if (ev & kEvGoal) r += kWGoal;
-                else if (ev & kEvCollision) r -= kWCollision;
-                else if (ev & kEvCrash) r -= kWCrash;
-                else if (ev & kEvLaneForb) r -= kWLaneForb;
-                if (A.step >= kMaxSteps) ev |= kEvTimeout;
-                reward = r;
-            }
-            if (nonfin) { ev = kEvNonfinite; reward = 0.f; }
-            const uint32_t sparse = kEvGoal | kEvCollision | kEvCrash | kEvLaneForb;
-            const bool term = nonfin || (!(args.flags & kFlagInvincible) && (ev & sparse));
-            done = term || (ev & kEvTimeout);
-            if (done) {
-                if (args.flags & kFlagAutoReset) respawn = true;
-                else if (!nonfin) { park_agent(A); alive = false; parked_now = true; }
-            }
-        }
+        if (warp == 0)
+            lanes_events(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, s_alive, &Q[lane], E, nb, tt, ev,
+                         reward, drac, done, respawn, parked_now);
     }
 
     // ---------------- respawns (warp 0, agents in index order), then the post-reset exchange
     if (warp == 0) {
-        const uint32_t rbits = __ballot_sync(kFull, respawn);
-        if (rbits) {
-            const unsigned long long seed = args.seed;
-            for (int l = 0; l < m; ++l) {
-                if (!((rbits >> l) & 1u)) continue;
-                const int ep = __shfl_sync(kFull, A.episode, l) + 1;
-                const bool same = __shfl_sync(kFull, wl, l) == wl;
-                float bx = 0.f, by = 0.f, bpsi = 0.f, bv = kSpawnVMin, bgx = kSpawnGoalMin, bgy = 0.f, bscore = -1.f;
-                const bool elig = alive && same && lane != l && !(lane > l && ((rbits >> lane) & 1u));
-                for (int r = 0; r < kSpawnTries; ++r) {
-                    float x = 0.f, y = 0.f, psi = 0.f, gx = 0.f, gy = 0.f, v0 = 0.f;
-                    if (lane == l) spawn_candidate(args.rd, w, a, l - base, ep, r, seed, x, y, psi, gx, gy, v0);
-                    x = __shfl_sync(kFull, x, l);
-                    y = __shfl_sync(kFull, y, l);
-                    float d2 = kInf;
-                    if (elig) {
-                        float dx = A.px - x, dy = A.py - y;
-                        d2 = dx * dx + dy * dy;
-                    }
-                    const float dmin = warp_min(d2);
-                    if (lane == l && dmin > bscore) { bscore = dmin; bx = x; by = y; bpsi = psi; bv = v0; bgx = gx; bgy = gy; }
-                    if (dmin >= kSpawnSpacing * kSpawnSpacing) break;
-                }
-                if (lane == l) {
-                    place_agent(A, bx, by, bpsi, bv, bgx, bgy);
-                    A.episode = ep;
-                    alive = true;
-                    ev |= kEvRespawned;
-                }
-                __syncwarp();
-            }
-        }
+        lanes_respawn(args, c, lane, m, A, alive, respawn, ev);
         // per world (never per pack, so that packing changes no result): a world
         // with a respawn or a parked agent republishes and recomputes its
         // neighbours; a reset leaves the worlds without a masked agent untouched
         const unsigned chg = __ballot_sync(kFull, respawn || parked_now);
-        const uint32_t wmask = n >= 32 ? 0xFFFFFFFFu : (((1u << n) - 1u) << base);
+        const uint32_t wmask = c.n >= 32 ? 0xFFFFFFFFu : (((1u << c.n) - 1u) << c.base);
         const bool wchanged = (chg & wmask) != 0u;
         recompute = (MODE != kModeStep) || wchanged;
-        const bool active = (MODE != kModeReset) || wchanged;
-        active_out = active;
+        active = (MODE != kModeReset) || wchanged;
         heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
         __syncwarp();
         if (recompute) publish(E, lane, A, hx, hy);
@@ -1142,117 +1451,169 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     __syncthreads();
 
     // ---------------- road-point block of every observation (all warps)
+    if (MODE != kModeStep && s_staged) {
+        stg = stage_wait(&s_bar);
+        if (!stg) atomicOr(args.out.error_word, 2u);
+    }
     for (int j = warp; j < m; j += NW) {
         if (!((s_act >> j) & 1u)) continue;
-        const DevGrid g = args.rd.grid[s_wid[s_slot_w[j]]];
-        float* orow = args.out.obs + (size_t)(a0 + j) * kObsDim + kObsEgo + kK * kObsNbr;
-        const bool al = (s_alive >> j) & 1u;
-        int kp = -1;
-        if (al) {
-            float* hnt = args.out.hint + 2 * (size_t)(a0 + j);
-            if (Q[j].need) {
-                const Lane L = coop_nearest_lane(args.rd, g, E.px[j], E.py[j], E.gx[j], E.gy[j], kLaneR0, lane);
-                __syncwarp();
-                if (lane == 0) {
-                    Q[j].seg = L.seg; Q[j].dist = L.dist; Q[j].lat = L.lat; Q[j].tx = L.tx; Q[j].ty = L.ty;
-                    hnt[1] = L.seg >= 0 ? L.dist : 0.f;
-                }
-            }
-            const float h32 = hnt[0];
-            const unsigned long long key =
-                coop_knn32(args.rd, g, E.px[j], E.py[j], h32 > 0.f ? h32 + kHintSlack : kKnnR0, lane, kbuf[warp]);
-            kp = key_idx(key);
-            const unsigned long long last = shfl64(key, 31);
-            if (lane == 0) hnt[0] = last != kKeyInf ? sqrtf(key_d2(last)) : 0.f;
+        const int t = s_slot_w[j];
+        const WRoads v = view_of(s_grid[t], (stg && s_woff[t] >= 0) ? s_blob + s_woff[t]
+                                                                     : args.rd.blob + s_grid[t].blob);
+        const bool al = (s_alive >> j) & 1u, need = Q[j].need != 0;
+        Lane L;
+        agent_road_block(v, al, need, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j],
+                         args.out.hint + 4 * (size_t)(a0 + j), lane, kbuf[warp],
+                         args.out.obs + (size_t)(a0 + j) * kObsDim + kObsEgo + kK * kObsNbr,
+                         (args.flags & kFlagRecord) ? args.out.knn_pts + (size_t)(a0 + j) * kL : nullptr, &L);
+        if (al && need && lane == 0) {
+            Q[j].seg = L.seg; Q[j].dist = L.dist; Q[j].lat = L.lat; Q[j].tx = L.tx; Q[j].ty = L.ty;
         }
-        float f[kObsPt] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (kp >= 0) {
-            const float4 P = __ldg(&args.rd.pt[kp]);
-            const uint32_t m = __ldg(&args.rd.pmeta[kp]);
-            const float ehx = E.hx[j], ehy = E.hy[j];
-            float bx, by, dbx, dby;
-            to_ego(ehx, ehy, P.x - E.px[j], P.y - E.py[j], bx, by);
-            to_ego(ehx, ehy, P.z, P.w, dbx, dby);
-            f[0] = bx / 10.f; f[1] = by / 10.f; f[2] = dbx; f[3] = dby;
-            f[4] = (float)(m & kPtTypeMask) / 20.f;
-            f[5] = (m & kPtEdge) ? 1.f : 0.f;
-            f[6] = 1.f;
-        }
-#pragma unroll
-        for (int c = 0; c < kObsPt; ++c) orow[kObsPt * lane + c] = f[c];
-        if (args.flags & kFlagRecord) args.out.knn_pts[(size_t)(a0 + j) * kL + lane] = kp;
     }
     __syncthreads();
 
     // ---------------- neighbours, ego group, outputs, state (warp 0)
     if (warp != 0) return;
-    if (recompute) knn_agents(E, base, n, lane, s_alive, A.px, A.py, nb);
-    if (has && active_out) {
-        float4* o4 = reinterpret_cast<float4*>(args.out.obs + (size_t)a * kObsDim);
-        if (alive) {
-            const AgentQ q = Q[lane];
-            float gbx, gby, vbx, vby;
-            to_ego(hx, hy, A.gx - A.px, A.gy - A.py, gbx, gby);
-            to_ego(hx, hy, A.vx, A.vy, vbx, vby);
-            float gn = sqrtf(gbx * gbx + gby * gby);
-            uint32_t pc = A.meta & 0xFFu, sc = (A.meta >> 8) & 0xFFu;
-            o4[0] = make_float4(gbx / kSceneHalf, gby / kSceneHalf, gn > 0.f ? gby / gn : 0.f, gn > 0.f ? gbx / gn : 1.f);
-            o4[1] = make_float4(gn / kSceneHalf, vbx / 10.f, vby / 10.f, (float)pc / 3.f);
-            o4[2] = make_float4(sc == 0 ? 1.f : 0.f, sc == 1 ? 1.f : 0.f, sc == 2 ? 1.f : 0.f, A.wz);
-            o4[3] = make_float4(A.dl / kThetaMax, A.mu, q.seg >= 0 ? q.lat / 3.6f : 0.f,
-                                q.seg >= 0 ? cross2(q.tx, q.ty, hx, hy) : 0.f);
+    if (lane == 0 && s_staged && !stg) stage_wait(&s_bar);   // no copy may outlive the block
+    lanes_final<MODE>(args, c, lane, A, alive, recompute, active, s_alive, &Q[lane], E, nb, tt, hx, hy, ev, reward,
+                      done, drac, respawn);
+}
+
+// ====================================================================== the split step
+// The same step as four kernels: the lane-per-agent phases (physics; events,
+// respawns and the ego / neighbour groups) run one warp per pack, the road
+// queries one warp per agent in blocks of NWQ warps, so that the query kernels
+// keep a small register footprint and many warps resident.  Results are
+// bit-identical to the fused kernel (the same inline code).
+
+// physics; writes the state, the start-of-step position, the heading and the
+// non-finite flag
+__global__ void __launch_bounds__(32, 16) phys_kernel(const WorldArgs args) {
+    __shared__ Exch E;
+    __shared__ int s_slot_w[32], s_wbase[32], s_wn[32];
+    const int lane = threadIdx.x;
+    const int4 pk = __ldg(&args.packs[blockIdx.x]);
+    if (pk.w <= 0) return;
+    pack_tables(args, pk, lane, s_slot_w, s_wbase, s_wn);
+    const Slot c = slot_of(pk, s_slot_w, s_wbase, s_wn, lane, true);
+    Agent A;
+    load_agent(args.st, c.a, A);
+    if (!c.has) A.meta = 0;
+    bool alive = c.has && (status_of(A.meta) & kAlive), nonfin = false;
+    float prevx = 0.f, prevy = 0.f, hx = 1.f, hy = 0.f;
+    lanes_physics(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E);
+    if (c.has) {
+        store_agent(args.st, c.a, A);
+        args.sc.prev[c.a] = make_float2(prevx, prevy);
+        args.sc.head[c.a] = make_float2(hx, hy);
+        args.sc.flag[c.a] = nonfin ? 1 : 0;
+    }
+}
+
+// road queries of one agent per warp: the events' queries (into sc.q) and the
+// road-point block of the observation at the post-physics pose
+template <int NWQ>
+__global__ void __launch_bounds__(32 * NWQ) query_kernel(const WorldArgs args) {
+    __shared__ unsigned long long kbuf[NWQ][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int a = blockIdx.x * NWQ + warp;
+    if (a >= args.num_agents) return;                 // warp-uniform
+    float* orow = args.out.obs + (size_t)a * kObsDim + kObsEgo + kK * kObsNbr;
+    int32_t* krow = (args.flags & kFlagRecord) ? args.out.knn_pts + (size_t)a * kL : nullptr;
+    if (!(status_of(args.st.meta[a]) & kAlive)) {
 #pragma unroll
-            for (int t2 = 0; t2 < kK / 2; ++t2) {
-                float f[20];
+        for (int k = 0; k < kObsPt; ++k) orow[kObsPt * lane + k] = 0.f;
+        if (krow) krow[lane] = -1;
+        return;
+    }
+    const DevGrid g = args.rd.grid[args.sc.agent_world[a]];
+    const WRoads v = view_of(g, args.rd.blob + g.blob);
+    const float4 p = args.st.pos[a], vel = args.st.vel[a], goal = args.st.goal[a];
+    const float2 h = args.sc.head[a];
+    float* hnt = args.out.hint + 4 * (size_t)a;
+    const AgentQ q = agent_event_queries(v, p.x, p.y, goal.x, goal.y, h.x, h.y, vel.x, vel.y, hnt, lane);
+    if (lane == 0) args.sc.q[a] = q;
+    agent_road_block(v, true, false, p.x, p.y, goal.x, goal.y, h.x, h.y, hnt, lane, kbuf[warp], orow, krow, nullptr);
+}
+
+// events, rewards, respawns, neighbours, ego group, outputs and state; marks
+// the agents whose road-point block is stale (respawned or parked)
+__global__ void __launch_bounds__(32, 16) events_kernel(const WorldArgs args) {
+    __shared__ Exch E;
+    __shared__ int s_slot_w[32], s_wbase[32], s_wn[32];
+    const int lane = threadIdx.x;
+    const int4 pk = __ldg(&args.packs[blockIdx.x]);
+    const int m = pk.w;
+    if (m <= 0) return;
+    pack_tables(args, pk, lane, s_slot_w, s_wbase, s_wn);
+    const Slot c = slot_of(pk, s_slot_w, s_wbase, s_wn, lane, true);
+    Agent A;
+    load_agent(args.st, c.a, A);
+    if (!c.has) A.meta = 0;
+    bool alive = c.has && (status_of(A.meta) & kAlive);
+    const bool nonfin = c.has && (args.sc.flag[c.a] & 1u);
+    float prevx = 0.f, prevy = 0.f, hx = 1.f, hy = 0.f;
+    if (c.has) {
+        const float2 pv = args.sc.prev[c.a], hd = args.sc.head[c.a];
+        prevx = pv.x; prevy = pv.y; hx = hd.x; hy = hd.y;
+    }
+    publish(E, lane, A, hx, hy);
+    const uint32_t alive_bits = __ballot_sync(kFull, alive);
+    __syncwarp();
+    bool respawn = false, parked_now = false, done = false;
+    uint32_t ev = 0;
+    float reward = 0.f, drac = 0.f;
+    int nb[kK];
+    float tt[kK];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int j = nb[2 * t2 + u];
-                    float* s = f + 10 * u;
-                    if (j < 0) {
+    for (int t = 0; t < kK; ++t) { nb[t] = -1; tt[t] = kTtcMax; }
+    lanes_events(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, alive_bits, args.sc.q + c.a, E, nb, tt, ev,
+                 reward, drac, done, respawn, parked_now);
+    lanes_respawn(args, c, lane, m, A, alive, respawn, ev);
+    const unsigned chg = __ballot_sync(kFull, respawn || parked_now);
+    const uint32_t wmask = c.n >= 32 ? 0xFFFFFFFFu : (((1u << c.n) - 1u) << c.base);
+    const bool recompute = (chg & wmask) != 0u;
+    heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
+    __syncwarp();
+    if (recompute) publish(E, lane, A, hx, hy);
+    const uint32_t alive_now = __ballot_sync(kFull, alive);
+    __syncwarp();
+    if (c.has) {
+        args.sc.head[c.a] = make_float2(hx, hy);
+        args.sc.flag[c.a] = (respawn || parked_now) ? 2 : 0;
+    }
+    lanes_final<kModeStep>(args, c, lane, A, alive, recompute, true, alive_now, args.sc.q + c.a, E, nb, tt, hx, hy,
+                           ev, reward, done, drac, respawn);
+}
+
+// road-point blocks of the agents the events kernel respawned (nearest lane
+// and 32 points from the default radii, the ego lane features) or parked (zeros)
+template <int NWQ>
+__global__ void __launch_bounds__(32 * NWQ) fix_kernel(const WorldArgs args) {
+    __shared__ unsigned long long kbuf[NWQ][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int a = blockIdx.x * NWQ + warp;
+    if (a >= args.num_agents || !(args.sc.flag[a] & 2u)) return;   // warp-uniform
+    float* orow = args.out.obs + (size_t)a * kObsDim + kObsEgo + kK * kObsNbr;
+    int32_t* krow = (args.flags & kFlagRecord) ? args.out.knn_pts + (size_t)a * kL : nullptr;
+    if (!(status_of(args.st.meta[a]) & kAlive)) {
 #pragma unroll
-                        for (int c = 0; c < 10; ++c) s[c] = 0.f;
-                        continue;
-                    }
-                    float pjx = E.px[j], pjy = E.py[j], hjx = E.hx[j], hjy = E.hy[j], vjx = E.vx[j], vjy = E.vy[j];
-                    float bx, by, dvx, dvy;
-                    to_ego(hx, hy, pjx - A.px, pjy - A.py, bx, by);
-                    to_ego(hx, hy, vjx - A.vx, vjy - A.vy, dvx, dvy);
-                    float dpsi = atan2f(cross2(hx, hy, hjx, hjy), hx * hjx + hy * hjy);
-                    s[0] = bx / kSceneHalf;
-                    s[1] = by / kSceneHalf;
-                    s[2] = 2.f * kHalfLen / kSceneHalf;
-                    s[3] = 2.f * kHalfWid / kSceneHalf;
-                    s[4] = dpsi / 3.14159265358979323846f;
-                    s[5] = sqrtf(vjx * vjx + vjy * vjy) / 10.f;
-                    s[6] = dvx / 10.f;
-                    s[7] = dvy / 10.f;
-                    s[8] = (recompute ? ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, pjx, pjy, hjx, hjy, vjx, vjy)
-                                  : tt[2 * t2 + u]) / kTtcMax;
-                    s[9] = 1.f;
-                }
-#pragma unroll
-                for (int c = 0; c < 5; ++c)
-                    o4[(kObsEgo + 20 * t2) / 4 + c] = make_float4(f[4 * c], f[4 * c + 1], f[4 * c + 2], f[4 * c + 3]);
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < (kObsEgo + kK * kObsNbr) / 4; ++c) o4[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        if (args.flags & kFlagRecord) {
-            args.out.lane_seg[a] = alive ? Q[lane].seg : -1;
-#pragma unroll
-            for (int t = 0; t < kK; ++t)
-                args.out.knn_agents[(size_t)a * kK + t] = (alive && nb[t] >= 0) ? a0 + nb[t] : -1;
-        }
-        if (MODE == kModeStep) {
-            args.out.reward[a] = reward;
-            args.out.done[a] = done ? 1 : 0;
-            args.out.events[a] = ev;
-            args.out.drac[a] = drac;
-        } else if (MODE == kModeReset && respawn) {
-            args.out.events[a] = ev;
-        }
-        store_agent(st, a, A);
+        for (int k = 0; k < kObsPt; ++k) orow[kObsPt * lane + k] = 0.f;
+        if (krow) krow[lane] = -1;
+        return;
+    }
+    const DevGrid g = args.rd.grid[args.sc.agent_world[a]];
+    const WRoads v = view_of(g, args.rd.blob + g.blob);
+    const float4 p = args.st.pos[a], goal = args.st.goal[a];
+    const float2 h = args.sc.head[a];
+    Lane L;
+    agent_road_block(v, true, true, p.x, p.y, goal.x, goal.y, h.x, h.y, args.out.hint + 4 * (size_t)a, lane,
+                     kbuf[warp], orow, krow, &L);
+    if (lane == 0) {
+        float* ego = args.out.obs + (size_t)a * kObsDim;
+        ego[14] = L.seg >= 0 ? L.lat / 3.6f : 0.f;
+        ego[15] = L.seg >= 0 ? cross2(L.tx, L.ty, h.x, h.y) : 0.f;
+        if (args.flags & kFlagRecord) args.out.lane_seg[a] = L.seg;
     }
 }
 
@@ -1361,15 +1722,44 @@ cudaError_t sf_launch_surr_collect(const WorldArgs& a, const float4* snap, const
     return cudaGetLastError();
 }
 
+template <int NWQ>
+static cudaError_t launch_split(const WorldArgs& a, cudaStream_t s) {
+    const int qb = (a.num_agents + NWQ - 1) / NWQ;
+    phys_kernel<<<a.num_packs, 32, 0, s>>>(a);
+    query_kernel<NWQ><<<qb, 32 * NWQ, 0, s>>>(a);
+    events_kernel<<<a.num_packs, 32, 0, s>>>(a);
+    fix_kernel<NWQ><<<qb, 32 * NWQ, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t sf_launch_step_split(const WorldArgs& a, int nwq, cudaStream_t s) {
+    if (a.num_packs <= 0 || a.num_agents <= 0) return cudaSuccess;
+    switch (nwq) {
+        case 2: return launch_split<2>(a, s);
+        case 8: return launch_split<8>(a, s);
+        default: return launch_split<4>(a, s);
+    }
+}
+
+template <int MODE, int NW>
+static cudaError_t launch_shape(const WorldArgs& a, cudaStream_t s) {
+    // allow up to kMaxStageBytes of dynamic shared memory, once per instantiation
+    static const cudaError_t attr = cudaFuncSetAttribute(world_kernel<MODE, NW>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStageBytes);
+    if (attr != cudaSuccess) return attr;
+    if (a.stage_bytes < 0 || a.stage_bytes > kMaxStageBytes || a.stage_bytes % 16) return cudaErrorInvalidValue;
+    world_kernel<MODE, NW><<<a.num_packs, 32 * NW, a.stage_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int MODE>
 static cudaError_t launch_mode(const WorldArgs& a, int nw, cudaStream_t s) {
     switch (nw) {
-        case 1: world_kernel<MODE, 1><<<a.num_packs, 32, 0, s>>>(a); break;
-        case 2: world_kernel<MODE, 2><<<a.num_packs, 64, 0, s>>>(a); break;
-        case 8: world_kernel<MODE, 8><<<a.num_packs, 256, 0, s>>>(a); break;
-        default: world_kernel<MODE, 4><<<a.num_packs, 128, 0, s>>>(a); break;
+        case 1: return launch_shape<MODE, 1>(a, s);
+        case 2: return launch_shape<MODE, 2>(a, s);
+        case 8: return launch_shape<MODE, 8>(a, s);
+        default: return launch_shape<MODE, 4>(a, s);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t sf_launch_world(int mode, const WorldArgs& a, int nw, cudaStream_t s) {

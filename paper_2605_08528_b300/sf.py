@@ -35,7 +35,8 @@ class SFError(RuntimeError):
 
 class sf_config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("flags", C.c_int32), ("warps_per_block", C.c_int32),
-                ("pack_agents", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("pack_agents", C.c_int32), ("stage_bytes", C.c_int32), ("split_step", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class sf_roads(C.Structure):
@@ -118,8 +119,8 @@ def sf_version() -> str:
     return lib().sf_version().decode()
 
 
-def sf_create(seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0):
-    cfg = sf_config(seed, flags, warps_per_block, pack_agents)
+def sf_create(seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0, stage_bytes=0, split_step=0):
+    cfg = sf_config(seed, flags, warps_per_block, pack_agents, stage_bytes, split_step)
     h = C.c_void_p()
     st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().sf_create(C.byref(cfg), C.c_void_p(st), C.byref(h)))
@@ -197,13 +198,18 @@ def sf_sync(h, allow=()):
     return _check(lib().sf_sync(h), h, allow=allow)
 
 
+AUTOTUNE_SHAPES = 38
+
+
 def sf_autotune(h, d_actions, dt=1.0 / 30.0, substeps=4, iters=20):
-    """Pick the fastest world-kernel launch shape; returns ((warps per block, pack agents),
-    ms per shape: 1/2/4/8 warps unpacked, then 1/2/4/8 warps packed)."""
-    best = (C.c_int32 * 2)()
-    ms = (C.c_float * 8)()
+    """Pick the fastest launch shape of the step; returns ((warps per block, pack agents,
+    stage bytes, split step), ms per shape: s < 32 the fused kernel with 1 << (s & 3) warps,
+    packed if s & 4, staging budget s >> 3; s = 32 + k the split step with 2 << (k % 3)
+    warps per query block, packed if k >= 3)."""
+    best = (C.c_int32 * 4)()
+    ms = (C.c_float * AUTOTUNE_SHAPES)()
     _check(lib().sf_autotune(h, _ptr(d_actions), float(dt), int(substeps), int(iters), best, ms), h)
-    return (int(best[0]), int(best[1])), list(ms)
+    return (int(best[0]), int(best[1]), int(best[2]), int(best[3])), list(ms)
 
 
 def sf_num_agents(h) -> int:
@@ -218,11 +224,12 @@ def sf_num_worlds(h) -> int:
 class World:
     """A handle plus its roads, with torch views of the library-owned outputs."""
 
-    def __init__(self, scene, seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0):
+    def __init__(self, scene, seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0, stage_bytes=0,
+                 split_step=0):
         import torch
         self.torch = torch
         self.scene = scene
-        self.h = sf_create(seed, flags, warps_per_block, stream, pack_agents)
+        self.h = sf_create(seed, flags, warps_per_block, stream, pack_agents, stage_bytes, split_step)
         sf_load_roads(self.h, scene)
         self.A = sf_num_agents(self.h)
         self.W = sf_num_worlds(self.h)

@@ -193,11 +193,13 @@ def lane_tie(orc, scene, w, p):
     return len(best) > 1 and best[1] - best[0] < TIE
 
 
-@pytest.mark.parametrize("flags,pack", [(sf.FLAG_INVINCIBLE, 0), (0, 0), (sf.FLAG_AUTO_RESET, 0),
-                                        (sf.FLAG_AUTO_RESET, 32)])
-def test_discrete_and_observation_parity(flags, pack):
+@pytest.mark.parametrize("flags,pack,stage,split", [(sf.FLAG_INVINCIBLE, 0, 0, 0), (0, 0, 0, 0),
+                                                    (sf.FLAG_AUTO_RESET, 0, 0, 0), (sf.FLAG_AUTO_RESET, 32, 48 << 10, 0),
+                                                    (0, 32, 96 << 10, 0), (0, 32, 0, 1), (sf.FLAG_AUTO_RESET, 0, 0, 1)])
+def test_discrete_and_observation_parity(flags, pack, stage, split):
     sc = synth.procedural_scene(6, 16, seed_base=1100)
-    W = sf.World(sc, seed=9, flags=flags | sf.FLAG_RECORD_INDICES, pack_agents=pack)
+    W = sf.World(sc, seed=9, flags=flags | sf.FLAG_RECORD_INDICES, pack_agents=pack, stage_bytes=stage,
+                 split_step=split)
     spawn_all(W)
     orc = O.Oracle(sc)
     oflags = (O.FLAG_INVINCIBLE if flags & sf.FLAG_INVINCIBLE else 0) | (
@@ -302,8 +304,9 @@ def test_reset_spawns_match_oracle():
 
 
 # ----------------------------------------------------------------------------- edge cases
-@pytest.mark.parametrize("pack", [0, 32, 20])
-def test_ragged_and_degenerate_worlds(pack):
+@pytest.mark.parametrize("pack,stage,split", [(0, 0, 0), (32, 0, 0), (20, 0, 0), (32, 96 << 10, 0), (0, 48 << 10, 0),
+                                              (32, 0, 1), (0, 0, 1)])
+def test_ragged_and_degenerate_worlds(pack, stage, split):
     polys_a = synth.procedural_world(5)
     x = np.linspace(-90, 90, 181)
     straight = [(2, np.stack([x, np.full(181, -1.8)], 1)), (2, np.stack([x[::-1], np.full(181, 1.8)], 1)),
@@ -311,7 +314,8 @@ def test_ragged_and_degenerate_worlds(pack):
     worlds = [polys_a, [], straight, polys_a, straight]
     counts = [32, 3, 1, 0, 17]          # a full warp, a world without roads, one agent, an empty world
     sc = synth._assemble(worlds, counts, np.zeros(sum(counts)), np.zeros(sum(counts)))
-    W = sf.World(sc, seed=3, flags=sf.FLAG_AUTO_RESET | sf.FLAG_RECORD_INDICES, pack_agents=pack)
+    W = sf.World(sc, seed=3, flags=sf.FLAG_AUTO_RESET | sf.FLAG_RECORD_INDICES, pack_agents=pack,
+                 stage_bytes=stage, split_step=split)
     spawn_all(W)
     orc = O.Oracle(sc)
     F, I, _ = sf.sf_get_state(W.h)
@@ -344,9 +348,9 @@ def test_ragged_and_degenerate_worlds(pack):
     assert ix["lane_seg"][a] == -1 and (ix["knn_pts"][a] == -1).all()
 
 
-def _packing_trace(sc, pack, nw, steps=12):
+def _packing_trace(sc, pack, nw, stage=0, split=0, steps=12):
     W = sf.World(sc, seed=13, flags=sf.FLAG_AUTO_RESET | sf.FLAG_RECORD_INDICES, warps_per_block=nw,
-                 pack_agents=pack)
+                 pack_agents=pack, stage_bytes=stage, split_step=split)
     spawn_all(W)
     acts = synth.ou_actions(W.A, steps, seed=5)
     trace = []
@@ -365,20 +369,23 @@ def _packing_trace(sc, pack, nw, steps=12):
 
 @pytest.mark.parametrize("nw", [1, 4, 8])
 def test_world_packing_is_bitwise_invisible(nw):
-    """Packing consecutive worlds into one thread block changes no arithmetic:
-    a ragged batch under random 20% reset masks gives bit-identical state,
-    observations, rewards, events and indices with and without packing (same
-    launch width)."""
+    """Packing consecutive worlds into one thread block, staging their roads in
+    shared memory and splitting the step into four kernels change no
+    arithmetic: a ragged batch under random 20% reset masks gives bit-identical
+    state, observations, rewards, events and indices for every (packing,
+    staging budget, split) at the same launch width; the 16 KB budget stages
+    some worlds and reads the larger ones from global memory."""
     sc = synth.ragged_scene(48, seed_base=2000, points_hi=1500)
     ref = _packing_trace(sc, 0, nw)
-    for pack in (32, 11):
-        other = _packing_trace(sc, pack, nw)
+    for pack, stage, split in [(32, 0, 0), (11, 0, 0), (0, 48 << 10, 0), (32, 48 << 10, 0), (32, 96 << 10, 0),
+                               (32, 16 << 10, 0), (0, 0, 1), (32, 0, 1), (11, 0, 1)]:
+        other = _packing_trace(sc, pack, nw, stage, split)
         for t, (a, b) in enumerate(zip(ref, other)):
             for k in a:
                 if not np.array_equal(a[k], b[k], equal_nan=True):
                     bad = np.argwhere(~((a[k] == b[k]) | (np.isnan(a[k]) & np.isnan(b[k]))))
                     r = tuple(bad[0])
-                    raise AssertionError((pack, t, k, len(bad), r, a[k][r], b[k][r]))
+                    raise AssertionError((pack, stage, split, t, k, len(bad), r, a[k][r], b[k][r]))
 
 
 def test_invalid_roads_rejected():
