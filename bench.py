@@ -122,12 +122,12 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- our arm
 def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, policy_seed=None, surrogate=None,
-                 pack=0, reset_frac=0.0):
+                 pack=0, reset_frac=0.0, stage=0, split=0):
     """Time `steps` replays of the captured step graph (policy forward + step
     when policy_seed is given) on the workload `name`."""
     scene = make_scene(name, rank)
     W = sf.World(scene, seed=4242 + rank, flags=sf.FLAG_AUTO_RESET, warps_per_block=nw, stream=stream,
-                 pack_agents=pack)
+                 pack_agents=pack, stage_bytes=stage, split_step=split)
     A = W.A
     dev = torch.device("cuda")
     policy = sf.init_policy(seed=policy_seed, stream=stream) if policy_seed is not None else None
@@ -254,13 +254,16 @@ def main_ours(args):
         torch.cuda.synchronize()
         if name == "4096x16+policy":                  # profiling target: the policy + step graph alone
             res[name] = run_workload("4096x16", args.steps, args.warmup, rank, torch, sf, stream, e2e=False,
-                                     nw=args.nw, policy_seed=4000, pack=args.pack)
+                                     nw=args.nw, policy_seed=4000, pack=args.pack, stage=args.stage,
+                                     split=args.split)
         elif name == "ragged1024":
             res[name] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream, e2e=False, nw=args.nw,
-                                     pack=args.pack, reset_frac=RAGGED[2])
+                                     pack=args.pack, reset_frac=RAGGED[2], stage=args.stage,
+                                     split=args.split)
         else:
             res[name] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream,
-                                     e2e=not args.skip_e2e, nw=args.nw, pack=args.pack)
+                                     e2e=not args.skip_e2e, nw=args.nw, pack=args.pack, stage=args.stage,
+                                     split=args.split)
     surr = None
     surr_info = None
     if not args.only and not args.skip_surrogate:
@@ -279,12 +282,14 @@ def main_ours(args):
             if world > 1:
                 dist.barrier()
             res[name + "+surrogate"] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream,
-                                                    e2e=False, nw=args.nw, surrogate=surr, pack=args.pack)
+                                                    e2e=False, nw=args.nw, surrogate=surr, pack=args.pack,
+                                                    stage=args.stage, split=args.split)
     if not args.only and not args.skip_policy:
         if world > 1:
             dist.barrier()
         res["4096x16+policy"] = run_workload("4096x16", args.steps, args.warmup, rank, torch, sf, stream, e2e=False,
-                                             nw=args.nw, policy_seed=4000, surrogate=surr, pack=args.pack)
+                                             nw=args.nw, policy_seed=4000, surrogate=surr, pack=args.pack,
+                                             stage=args.stage, split=args.split)
     if surr is not None:
         sf.sf_surrogate_destroy(surr)
     clk = clocks.stop()
@@ -436,6 +441,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
     ap.add_argument("--nw", type=int, default=0, help="warps per block (1, 2, 4, 8; 0 = autotuned)")
     ap.add_argument("--pack", type=int, default=0, help="with --nw: agents per packed block (0 = one world)")
+    ap.add_argument("--stage", type=int, default=0, help="with --nw: road staging bytes per block (0 = off)")
+    ap.add_argument("--split", type=int, default=0, help="with --nw: 1 = the step as four kernels")
     ap.add_argument("--skip-policy", action="store_true", help="no 4096x16 + policy leg")
     ap.add_argument("--skip-surrogate", action="store_true", help="no surrogate training / legs")
     ap.add_argument("--surr-rows", type=int, default=10_000_000, help="surrogate training transitions")

@@ -298,6 +298,7 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     std::vector<int32_t> cands;
     std::vector<DevGrid> grid(W);
     std::vector<int32_t> pbeg(NP);
+    std::vector<float> arcl(NP);
     std::vector<unsigned char> blob;   // every world's road blob, 16-byte aligned sections
     auto in_box = [](double x, double y) { return std::fabs(x) <= 100.0 && std::fabs(y) <= 100.0; };
     for (int w = 0; w < W; ++w) {
@@ -335,6 +336,7 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
                 pmeta[k] = m;
                 pend[k] = k1;
                 pbeg[k] = k0;
+                arcl[k] = (float)arc[k - k0];
             }
             if (is_lane_type(t) && k1 > k0) {
                 const double total = arc.back();
@@ -427,16 +429,17 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     SF_ALLOC(step, int32_t, Aa);
     SF_ALLOC(episode, int32_t, Aa);
     h->st = DevState{pos, quat, vel, angv, spin, goal, peak, meta, step, episode};
-    int4* dworld; int2* dcand; float4* dpt; int32_t *dpend, *dcands;
+    int4* dworld; int2* dcand; float4* dpt; int32_t *dpend, *dcands; float* darc;
     SF_ALLOC(dworld, int4, (size_t)W);
     SF_ALLOC(dcand, int2, (size_t)W);
     SF_ALLOC(dpt, float4, (size_t)NP + 1);
     SF_ALLOC(dpend, int32_t, (size_t)NP + 1);
+    SF_ALLOC(darc, float, (size_t)NP + 1);
     SF_ALLOC(dcands, int32_t, cands.size() + 1);
     DevGrid* dgrid; unsigned char* dblob;
     SF_ALLOC(dgrid, DevGrid, (size_t)W);
     SF_ALLOC(dblob, unsigned char, blob.size() + 16);
-    h->rd = DevRoads{dworld, dcand, dpt, dpend, dcands, dgrid, dblob};
+    h->rd = DevRoads{dworld, dcand, dpt, dpend, darc, dcands, dgrid, dblob};
     float *obs, *reward, *drac; uint8_t* done; uint32_t* events; int32_t *lane_seg, *knn_pts, *knn_agents;
     unsigned int* err_word; float* hint;
     SF_ALLOC(obs, float, Aa * SF_OBS_DIM);
@@ -490,6 +493,7 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     up(dcand, cand.data(), cand.size() * sizeof(int2));
     up(dpt, pt.data(), pt.size() * sizeof(float4));
     up(dpend, pend.data(), pend.size() * sizeof(int32_t));
+    up(darc, arcl.data(), arcl.size() * sizeof(float));
     up(dcands, cands.data(), cands.size() * sizeof(int32_t));
     up(dgrid, grid.data(), grid.size() * sizeof(DevGrid));
     up(dblob, blob.data(), blob.size());

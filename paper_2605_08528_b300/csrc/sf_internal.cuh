@@ -141,6 +141,7 @@ struct DevRoads {
     const int2* cand;           // (first spawn candidate, candidate count)
     const float4* pt;           // (x, y, road direction x, y), input order
     const int32_t* pend;        // one past the last point of the point's polyline
+    const float* arc;           // arc length from the polyline's first point (summed in double)
     const int32_t* cands;       // spawn candidate point indices
     const DevGrid* grid;        // per world
     const unsigned char* blob;  // every world's road blob

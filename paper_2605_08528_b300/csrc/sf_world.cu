@@ -476,17 +476,16 @@ __device__ void spawn_candidate(const DevRoads& rd, int w, int a, int slot, int 
         x = p.x; y = p.y;
         psi = atan2f(p.w, p.z);
         float dg = kSpawnGoalMin + (kSpawnGoalMax - kSpawnGoalMin) * u24(reset_draw(seed, a, ep, r, 1));
-        int k1 = __ldg(&rd.pend[k]);
-        int g = k1 - 1;
-        float s = 0.f;
-        float prx = p.x, pry = p.y;
-        for (int j = k + 1; j < k1; ++j) {
-            float4 q = __ldg(&rd.pt[j]);
-            float dx = q.x - prx, dy = q.y - pry;
-            s += sqrtf(dx * dx + dy * dy);
-            prx = q.x; pry = q.y;
-            if (s >= dg) { g = j; break; }
+        // the first point j after k with arc(k, j) >= dg (the polyline's last point
+        // if none): binary search over the cumulative arc lengths
+        const int k1 = __ldg(&rd.pend[k]);
+        const float ak = __ldg(&rd.arc[k]);
+        int lo = k + 1, hi = k1;                      // answer in [lo, hi], hi = none
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(&rd.arc[mid]) - ak >= dg) hi = mid; else lo = mid + 1;
         }
+        const int g = lo < k1 ? lo : k1 - 1;
         float4 G = __ldg(&rd.pt[g]);
         gx = G.x; gy = G.y;
     }
@@ -1140,19 +1139,24 @@ __device__ __forceinline__ void agent_road_block(const WRoads& v, bool alive, bo
     if (knn_row) knn_row[lane] = key != kKeyInf ? v.q0 + rkey_local(key) : -1;
 }
 
-// events and rewards of the lanes of the agent warp (App. G); done agents are
-// marked for a respawn (auto-reset) or parked
-__device__ __forceinline__ void lanes_events(const WorldArgs& args, const Slot& c, int lane, Agent& A, bool& alive,
-                                             bool nonfin, float prevx, float prevy, float hx, float hy,
-                                             uint32_t alive_bits, const AgentQ* qp, const Exch& E, int (&nb)[kK],
-                                             float (&tt)[kK], uint32_t& ev, float& reward, float& drac, bool& done,
-                                             bool& respawn, bool& parked_now) {
-    const int base = c.base, n = c.n;
+// Neighbour tables of a block: the 8 nearest agents of every slot and, per
+// (slot, neighbour) pair, TTC and DRAC; the pairs are spread over every warp.
+struct Nbr {
+    int8_t nb[32][kK];
+    float tt[32][kK], dr[32][kK];
+    float hx[32], hy[32];     // heading of each slot for the observation (after respawns)
+};
+
+// events and rewards (App. G), first part, lanes of the agent warp: lane terms,
+// off-road, idle, the 8 nearest agents (into N.nb); returns the partial reward
+__device__ __forceinline__ float lanes_events_a(const Slot& c, int lane, Agent& A, bool alive, float prevx,
+                                                float prevy, float hx, float hy, uint32_t alive_bits, const AgentQ* qp,
+                                                const Exch& E, int (&nb)[kK], uint32_t& ev, Nbr& N) {
+    float r = 0.f;
     if (alive) {
         const AgentQ q = *qp;
         A.step += 1;
         const float speed = sqrtf(A.vx * A.vx + A.vy * A.vy);
-        float r = 0.f;
         if (q.seg >= 0) {
             float prog = (A.px - prevx) * q.tx + (A.py - prevy) * q.ty;
             r += kWProgress * clampf(prog, -kProgressClip, kProgressClip);
@@ -1162,16 +1166,43 @@ __device__ __forceinline__ void lanes_events(const WorldArgs& args, const Slot& 
         }
         if (fabsf(q.lat) > kOffroadLat || q.dist > kOffroadDist) { ev |= kEvOffroad; r -= kWOffroad; }
         if (speed < kIdleSpeed) { ev |= kEvIdle; r -= kWIdle; }
-        knn_agents(E, base, n, lane, alive_bits, A.px, A.py, nb);
+        knn_agents(E, c.base, c.n, lane, alive_bits, A.px, A.py, nb);
+    }
+#pragma unroll
+    for (int t = 0; t < kK; ++t) N.nb[lane][t] = (int8_t)nb[t];
+    return r;
+}
+
+// TTC and DRAC of every (slot, neighbour) pair of the block (all threads);
+// the pair's own pose comes from the exchange area (published from the lane)
+__device__ __forceinline__ void pairs_ttc_drac(const Exch& E, Nbr& N, int m, int tid, int nthreads) {
+    for (int p = tid; p < m * kK; p += nthreads) {
+        const int i = p / kK, t = p % kK, j = N.nb[i][t];
+        if (j < 0) continue;
+        N.tt[i][t] = ttc_pair(E.px[i], E.py[i], E.hx[i], E.hy[i], E.vx[i], E.vy[i], E.px[j], E.py[j], E.hx[j],
+                              E.hy[j], E.vx[j], E.vy[j]);
+        N.dr[i][t] = drac_pair(E.px[i], E.py[i], E.hx[i], E.hy[i], E.vx[i], E.vy[i], E.px[j], E.py[j], E.hx[j],
+                               E.hy[j], E.vx[j], E.vy[j]);
+    }
+}
+
+// events and rewards, second part: TTC / DRAC penalties, collision, edge,
+// sparse events; done agents are marked for a respawn (auto-reset) or parked
+__device__ __forceinline__ void lanes_events_b(const WorldArgs& args, const Slot& c, int lane, Agent& A, bool& alive,
+                                               bool nonfin, float hx, float hy, uint32_t alive_bits,
+                                               const AgentQ* qp, const Exch& E, const int (&nb)[kK],
+                                               float (&tt)[kK], float r, const Nbr& N, uint32_t& ev, float& reward,
+                                               float& drac, bool& done, bool& respawn, bool& parked_now) {
+    const int base = c.base, n = c.n;
+    if (alive) {
+        const AgentQ q = *qp;
         float tmin = kTtcMax, dmax = 0.f;
 #pragma unroll
         for (int t = 0; t < kK; ++t) {
             if (nb[t] < 0) continue;
-            const int j = nb[t];
-            tt[t] = ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j], E.vx[j], E.vy[j]);
+            tt[t] = N.tt[lane][t];
             tmin = fminf(tmin, tt[t]);
-            dmax = fmaxf(dmax, drac_pair(A.px, A.py, hx, hy, A.vx, A.vy, E.px[j], E.py[j], E.hx[j], E.hy[j],
-                                         E.vx[j], E.vy[j]));
+            dmax = fmaxf(dmax, N.dr[lane][t]);
         }
         if (tmin < kTtcMax) r -= penalty(kTtcAlphaV, tmin, kTtcPmaxV);
         r -= kWDrac * fmaxf(0.f, dmax - kDracThresh);
@@ -1211,32 +1242,42 @@ __device__ __forceinline__ void lanes_events(const WorldArgs& args, const Slot& 
 }
 
 // respawns of the marked lanes (App. J), every slot of the pack in index
-// order, each spaced from the other alive agents of its own world
+// order, each spaced from the other alive agents of its own world.  The
+// candidate draws of the up to kSpawnTries attempts are independent, so lane
+// r computes attempt r (its global loads overlap); the attempts are then
+// scored in order exactly as a sequential loop would: the first one at least
+// the spacing away is taken, else the one with the largest clearance (first
+// on ties).
 __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot& c, int lane, int m, Agent& A,
                                               bool& alive, bool respawn, uint32_t& ev) {
+    static_assert(kSpawnTries <= 32, "one lane per attempt");
     const uint32_t rbits = __ballot_sync(kFull, respawn);
     if (!rbits) return;
     const unsigned long long seed = args.seed;
     for (int l = 0; l < m; ++l) {
         if (!((rbits >> l) & 1u)) continue;
         const int ep = __shfl_sync(kFull, A.episode, l) + 1;
-        const bool same = __shfl_sync(kFull, c.wl, l) == c.wl;
-        float bx = 0.f, by = 0.f, bpsi = 0.f, bv = kSpawnVMin, bgx = kSpawnGoalMin, bgy = 0.f, bscore = -1.f;
-        const bool elig = alive && same && lane != l && !(lane > l && ((rbits >> lane) & 1u));
+        const int wl = __shfl_sync(kFull, c.wl, l), wid = __shfl_sync(kFull, c.w, l);
+        const int al = __shfl_sync(kFull, c.a, l), slot = l - __shfl_sync(kFull, c.base, l);
+        const bool elig = alive && c.wl == wl && lane != l && !(lane > l && ((rbits >> lane) & 1u));
+        float x = 0.f, y = 0.f, psi = 0.f, gx = 0.f, gy = 0.f, v0 = 0.f;
+        if (lane < kSpawnTries) spawn_candidate(args.rd, wid, al, slot, ep, lane, seed, x, y, psi, gx, gy, v0);
+        int pick = 0;
+        float bscore = -1.f;
         for (int r = 0; r < kSpawnTries; ++r) {
-            float x = 0.f, y = 0.f, psi = 0.f, gx = 0.f, gy = 0.f, v0 = 0.f;
-            if (lane == l) spawn_candidate(args.rd, c.w, c.a, l - c.base, ep, r, seed, x, y, psi, gx, gy, v0);
-            x = __shfl_sync(kFull, x, l);
-            y = __shfl_sync(kFull, y, l);
+            const float xr = __shfl_sync(kFull, x, r), yr = __shfl_sync(kFull, y, r);
             float d2 = kInf;
             if (elig) {
-                float dx = A.px - x, dy = A.py - y;
+                float dx = A.px - xr, dy = A.py - yr;
                 d2 = dx * dx + dy * dy;
             }
             const float dmin = warp_min(d2);
-            if (lane == l && dmin > bscore) { bscore = dmin; bx = x; by = y; bpsi = psi; bv = v0; bgx = gx; bgy = gy; }
+            if (dmin > bscore) { bscore = dmin; pick = r; }
             if (dmin >= kSpawnSpacing * kSpawnSpacing) break;
         }
+        const float bx = __shfl_sync(kFull, x, pick), by = __shfl_sync(kFull, y, pick);
+        const float bpsi = __shfl_sync(kFull, psi, pick), bv = __shfl_sync(kFull, v0, pick);
+        const float bgx = __shfl_sync(kFull, gx, pick), bgy = __shfl_sync(kFull, gy, pick);
         if (lane == l) {
             place_agent(A, bx, by, bpsi, bv, bgx, bgy);
             A.episode = ep;
@@ -1247,13 +1288,60 @@ __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot&
     }
 }
 
-// neighbours, ego group, outputs and state of the lanes of the agent warp
-template <int MODE>
-__device__ __forceinline__ void lanes_final(const WorldArgs& args, const Slot& c, int lane, Agent& A, bool alive,
-                                            bool recompute, bool active, uint32_t alive_bits, const AgentQ* qp,
-                                            const Exch& E, int (&nb)[kK], const float (&tt)[kK], float hx, float hy,
-                                            uint32_t ev, float reward, bool done, float drac, bool respawn) {
+// neighbours of the final observation (lanes of the agent warp): recomputed
+// after a respawn in the world; the tables get each slot's heading
+__device__ __forceinline__ void lanes_final_a(const Slot& c, int lane, const Agent& A, bool recompute,
+                                              uint32_t alive_bits, const Exch& E, int (&nb)[kK], float hx, float hy,
+                                              Nbr& N) {
     if (recompute) knn_agents(E, c.base, c.n, lane, alive_bits, A.px, A.py, nb);
+#pragma unroll
+    for (int t = 0; t < kK; ++t) N.nb[lane][t] = (int8_t)nb[t];
+    N.hx[lane] = hx;
+    N.hy[lane] = hy;
+}
+
+// neighbour rows of the observations (App. D analogue), one (slot, neighbour)
+// pair per thread: 10 features relative to the slot's pose, zeros for an
+// empty neighbour or a slot without an alive agent; TTC recomputed in a world
+// that changed, else the events' value
+__device__ __forceinline__ void pairs_nbr_rows(const WorldArgs& args, const Exch& E, const Nbr& N, int a0, int m,
+                                               uint32_t alive_bits, uint32_t recompute_bits, uint32_t active_bits,
+                                               int tid, int nthreads) {
+    for (int p = tid; p < m * kK; p += nthreads) {
+        const int i = p / kK, t = p % kK;
+        if (!((active_bits >> i) & 1u)) continue;
+        float s[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const int j = N.nb[i][t];
+        if (((alive_bits >> i) & 1u) && j >= 0) {
+            const float hx = N.hx[i], hy = N.hy[i], px = E.px[i], py = E.py[i], vx = E.vx[i], vy = E.vy[i];
+            const float pjx = E.px[j], pjy = E.py[j], hjx = E.hx[j], hjy = E.hy[j], vjx = E.vx[j], vjy = E.vy[j];
+            float bx, by, dvx, dvy;
+            to_ego(hx, hy, pjx - px, pjy - py, bx, by);
+            to_ego(hx, hy, vjx - vx, vjy - vy, dvx, dvy);
+            const float dpsi = atan2f(cross2(hx, hy, hjx, hjy), hx * hjx + hy * hjy);
+            s[0] = bx / kSceneHalf;
+            s[1] = by / kSceneHalf;
+            s[2] = 2.f * kHalfLen / kSceneHalf;
+            s[3] = 2.f * kHalfWid / kSceneHalf;
+            s[4] = dpsi / 3.14159265358979323846f;
+            s[5] = sqrtf(vjx * vjx + vjy * vjy) / 10.f;
+            s[6] = dvx / 10.f;
+            s[7] = dvy / 10.f;
+            s[8] = (((recompute_bits >> i) & 1u) ? ttc_pair(px, py, hx, hy, vx, vy, pjx, pjy, hjx, hjy, vjx, vjy)
+                                                  : N.tt[i][t]) / kTtcMax;
+            s[9] = 1.f;
+        }
+        float2* row = reinterpret_cast<float2*>(args.out.obs + (size_t)(a0 + i) * kObsDim + kObsEgo + kObsNbr * t);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) row[k] = make_float2(s[2 * k], s[2 * k + 1]);
+    }
+}
+
+// ego group, outputs and state of the lanes of the agent warp
+template <int MODE>
+__device__ __forceinline__ void lanes_final_b(const WorldArgs& args, const Slot& c, int lane, Agent& A, bool alive,
+                                              bool active, const AgentQ* qp, const int (&nb)[kK], float hx, float hy,
+                                              uint32_t ev, float reward, bool done, float drac, bool respawn) {
     if (!(c.has && active)) return;
     const int a = c.a;
     float4* o4 = reinterpret_cast<float4*>(args.out.obs + (size_t)a * kObsDim);
@@ -1271,48 +1359,14 @@ __device__ __forceinline__ void lanes_final(const WorldArgs& args, const Slot& c
         o4[2] = make_float4(sc == 0 ? 1.f : 0.f, sc == 1 ? 1.f : 0.f, sc == 2 ? 1.f : 0.f, A.wz);
         o4[3] = make_float4(A.dl / kThetaMax, A.mu, q.seg >= 0 ? q.lat / 3.6f : 0.f,
                             q.seg >= 0 ? cross2(q.tx, q.ty, hx, hy) : 0.f);
-#pragma unroll
-        for (int t2 = 0; t2 < kK / 2; ++t2) {
-            float f[20];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int j = nb[2 * t2 + u];
-                float* s = f + 10 * u;
-                if (j < 0) {
-#pragma unroll
-                    for (int k = 0; k < 10; ++k) s[k] = 0.f;
-                    continue;
-                }
-                float pjx = E.px[j], pjy = E.py[j], hjx = E.hx[j], hjy = E.hy[j], vjx = E.vx[j], vjy = E.vy[j];
-                float bx, by, dvx, dvy;
-                to_ego(hx, hy, pjx - A.px, pjy - A.py, bx, by);
-                to_ego(hx, hy, vjx - A.vx, vjy - A.vy, dvx, dvy);
-                float dpsi = atan2f(cross2(hx, hy, hjx, hjy), hx * hjx + hy * hjy);
-                s[0] = bx / kSceneHalf;
-                s[1] = by / kSceneHalf;
-                s[2] = 2.f * kHalfLen / kSceneHalf;
-                s[3] = 2.f * kHalfWid / kSceneHalf;
-                s[4] = dpsi / 3.14159265358979323846f;
-                s[5] = sqrtf(vjx * vjx + vjy * vjy) / 10.f;
-                s[6] = dvx / 10.f;
-                s[7] = dvy / 10.f;
-                s[8] = (recompute ? ttc_pair(A.px, A.py, hx, hy, A.vx, A.vy, pjx, pjy, hjx, hjy, vjx, vjy)
-                                  : tt[2 * t2 + u]) / kTtcMax;
-                s[9] = 1.f;
-            }
-#pragma unroll
-            for (int k = 0; k < 5; ++k)
-                o4[(kObsEgo + 20 * t2) / 4 + k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
-        }
     } else {
 #pragma unroll
-        for (int k = 0; k < (kObsEgo + kK * kObsNbr) / 4; ++k) o4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < kObsEgo / 4; ++k) o4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (args.flags & kFlagRecord) {
         args.out.lane_seg[a] = alive ? q.seg : -1;
 #pragma unroll
-        for (int t = 0; t < kK; ++t)
-            args.out.knn_agents[(size_t)a * kK + t] = (alive && nb[t] >= 0) ? (a - lane) + nb[t] : -1;
+        for (int t = 0; t < kK; ++t) args.out.knn_agents[(size_t)a * kK + t] = (alive && nb[t] >= 0) ? (a - lane) + nb[t] : -1;
     }
     if (MODE == kModeStep) {
         args.out.reward[a] = reward;
@@ -1336,8 +1390,9 @@ template <int MODE, int NW>
 __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_kernel(const WorldArgs args) {
     __shared__ Exch E;
     __shared__ AgentQ Q[32];
+    __shared__ Nbr N;
     __shared__ unsigned long long kbuf[NW][64];
-    __shared__ unsigned s_alive, s_any, s_act;
+    __shared__ unsigned s_alive, s_any, s_act, s_rec;
     __shared__ int s_slot_w[32];                  // pack-local world of each slot
     __shared__ int s_wbase[32], s_wn[32];         // per pack-local world: first slot, agents
     __shared__ int s_woff[32];                    // its blob's offset in s_blob, -1: read from global memory
@@ -1424,10 +1479,15 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
             if (lane == 0) Q[j] = q;
         }
         __syncthreads();
-        // ---------------- events and rewards (App. G), warp 0
+        // ---------------- events and rewards (App. G): lanes, pairs, lanes
+        float r = 0.f;
+        if (warp == 0) r = lanes_events_a(c, lane, A, alive, prevx, prevy, hx, hy, s_alive, &Q[lane], E, nb, ev, N);
+        __syncthreads();
+        pairs_ttc_drac(E, N, m, threadIdx.x, 32 * NW);
+        __syncthreads();
         if (warp == 0)
-            lanes_events(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, s_alive, &Q[lane], E, nb, tt, ev,
-                         reward, drac, done, respawn, parked_now);
+            lanes_events_b(args, c, lane, A, alive, nonfin, hx, hy, s_alive, &Q[lane], E, nb, tt, r, N, ev, reward,
+                           drac, done, respawn, parked_now);
     }
 
     // ---------------- respawns (warp 0, agents in index order), then the post-reset exchange
@@ -1472,11 +1532,17 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     }
     __syncthreads();
 
-    // ---------------- neighbours, ego group, outputs, state (warp 0)
+    // ---------------- neighbours (warp 0), their rows (all warps), ego group, outputs, state (warp 0)
+    if (warp == 0) {
+        if (lane == 0 && s_staged && !stg) stage_wait(&s_bar);   // no copy may outlive the block
+        lanes_final_a(c, lane, A, recompute, s_alive, E, nb, hx, hy, N);
+        const unsigned rb = __ballot_sync(kFull, recompute);
+        if (lane == 0) s_rec = rb;
+    }
+    __syncthreads();
+    pairs_nbr_rows(args, E, N, a0, m, s_alive, s_rec, s_act, threadIdx.x, 32 * NW);
     if (warp != 0) return;
-    if (lane == 0 && s_staged && !stg) stage_wait(&s_bar);   // no copy may outlive the block
-    lanes_final<MODE>(args, c, lane, A, alive, recompute, active, s_alive, &Q[lane], E, nb, tt, hx, hy, ev, reward,
-                      done, drac, respawn);
+    lanes_final_b<MODE>(args, c, lane, A, alive, active, &Q[lane], nb, hx, hy, ev, reward, done, drac, respawn);
 }
 
 // ====================================================================== the split step
@@ -1537,53 +1603,71 @@ __global__ void __launch_bounds__(32 * NWQ) query_kernel(const WorldArgs args) {
 }
 
 // events, rewards, respawns, neighbours, ego group, outputs and state; marks
-// the agents whose road-point block is stale (respawned or parked)
-__global__ void __launch_bounds__(32, 16) events_kernel(const WorldArgs args) {
+// the agents whose road-point block is stale (respawned or parked).  Warp 0
+// holds the agents; the (agent, neighbour) pairs are spread over NWE warps.
+template <int NWE>
+__global__ void __launch_bounds__(32 * NWE) events_kernel(const WorldArgs args) {
     __shared__ Exch E;
+    __shared__ Nbr N;
     __shared__ int s_slot_w[32], s_wbase[32], s_wn[32];
-    const int lane = threadIdx.x;
+    __shared__ unsigned s_alive, s_rec;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int4 pk = __ldg(&args.packs[blockIdx.x]);
     const int m = pk.w;
     if (m <= 0) return;
-    pack_tables(args, pk, lane, s_slot_w, s_wbase, s_wn);
-    const Slot c = slot_of(pk, s_slot_w, s_wbase, s_wn, lane, true);
+    if (warp == 0) pack_tables(args, pk, lane, s_slot_w, s_wbase, s_wn);
+    __syncthreads();
+    const Slot c = slot_of(pk, s_slot_w, s_wbase, s_wn, lane, warp == 0);
     Agent A;
-    load_agent(args.st, c.a, A);
-    if (!c.has) A.meta = 0;
-    bool alive = c.has && (status_of(A.meta) & kAlive);
-    const bool nonfin = c.has && (args.sc.flag[c.a] & 1u);
-    float prevx = 0.f, prevy = 0.f, hx = 1.f, hy = 0.f;
-    if (c.has) {
-        const float2 pv = args.sc.prev[c.a], hd = args.sc.head[c.a];
-        prevx = pv.x; prevy = pv.y; hx = hd.x; hy = hd.y;
-    }
-    publish(E, lane, A, hx, hy);
-    const uint32_t alive_bits = __ballot_sync(kFull, alive);
-    __syncwarp();
-    bool respawn = false, parked_now = false, done = false;
-    uint32_t ev = 0;
-    float reward = 0.f, drac = 0.f;
+    bool alive = false, nonfin = false, respawn = false, parked_now = false, done = false, recompute = false;
+    float prevx = 0.f, prevy = 0.f, hx = 1.f, hy = 0.f, reward = 0.f, drac = 0.f, r = 0.f;
+    uint32_t ev = 0, alive_bits = 0;
     int nb[kK];
     float tt[kK];
 #pragma unroll
     for (int t = 0; t < kK; ++t) { nb[t] = -1; tt[t] = kTtcMax; }
-    lanes_events(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, alive_bits, args.sc.q + c.a, E, nb, tt, ev,
-                 reward, drac, done, respawn, parked_now);
-    lanes_respawn(args, c, lane, m, A, alive, respawn, ev);
-    const unsigned chg = __ballot_sync(kFull, respawn || parked_now);
-    const uint32_t wmask = c.n >= 32 ? 0xFFFFFFFFu : (((1u << c.n) - 1u) << c.base);
-    const bool recompute = (chg & wmask) != 0u;
-    heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
-    __syncwarp();
-    if (recompute) publish(E, lane, A, hx, hy);
-    const uint32_t alive_now = __ballot_sync(kFull, alive);
-    __syncwarp();
-    if (c.has) {
-        args.sc.head[c.a] = make_float2(hx, hy);
-        args.sc.flag[c.a] = (respawn || parked_now) ? 2 : 0;
+    if (warp == 0) {
+        load_agent(args.st, c.a, A);
+        if (!c.has) A.meta = 0;
+        alive = c.has && (status_of(A.meta) & kAlive);
+        nonfin = c.has && (args.sc.flag[c.a] & 1u);
+        if (c.has) {
+            const float2 pv = args.sc.prev[c.a], hd = args.sc.head[c.a];
+            prevx = pv.x; prevy = pv.y; hx = hd.x; hy = hd.y;
+        }
+        publish(E, lane, A, hx, hy);
+        alive_bits = __ballot_sync(kFull, alive);
+        __syncwarp();
+        r = lanes_events_a(c, lane, A, alive, prevx, prevy, hx, hy, alive_bits, args.sc.q + c.a, E, nb, ev, N);
     }
-    lanes_final<kModeStep>(args, c, lane, A, alive, recompute, true, alive_now, args.sc.q + c.a, E, nb, tt, hx, hy,
-                           ev, reward, done, drac, respawn);
+    __syncthreads();
+    pairs_ttc_drac(E, N, m, threadIdx.x, 32 * NWE);
+    __syncthreads();
+    if (warp == 0) {
+        lanes_events_b(args, c, lane, A, alive, nonfin, hx, hy, alive_bits, args.sc.q + c.a, E, nb, tt, r, N, ev,
+                       reward, drac, done, respawn, parked_now);
+        lanes_respawn(args, c, lane, m, A, alive, respawn, ev);
+        const unsigned chg = __ballot_sync(kFull, respawn || parked_now);
+        const uint32_t wmask = c.n >= 32 ? 0xFFFFFFFFu : (((1u << c.n) - 1u) << c.base);
+        recompute = (chg & wmask) != 0u;
+        heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
+        __syncwarp();
+        if (recompute) publish(E, lane, A, hx, hy);
+        const uint32_t alive_now = __ballot_sync(kFull, alive);
+        __syncwarp();
+        if (c.has) {
+            args.sc.head[c.a] = make_float2(hx, hy);
+            args.sc.flag[c.a] = (respawn || parked_now) ? 2 : 0;
+        }
+        lanes_final_a(c, lane, A, recompute, alive_now, E, nb, hx, hy, N);
+        const unsigned rb = __ballot_sync(kFull, recompute);
+        if (lane == 0) { s_alive = alive_now; s_rec = rb; }
+    }
+    __syncthreads();
+    pairs_nbr_rows(args, E, N, pk.z, m, s_alive, s_rec, 0xFFFFFFFFu, threadIdx.x, 32 * NWE);
+    if (warp != 0) return;
+    lanes_final_b<kModeStep>(args, c, lane, A, alive, true, args.sc.q + c.a, nb, hx, hy, ev, reward, done, drac,
+                             respawn);
 }
 
 // road-point blocks of the agents the events kernel respawned (nearest lane
@@ -1727,7 +1811,7 @@ static cudaError_t launch_split(const WorldArgs& a, cudaStream_t s) {
     const int qb = (a.num_agents + NWQ - 1) / NWQ;
     phys_kernel<<<a.num_packs, 32, 0, s>>>(a);
     query_kernel<NWQ><<<qb, 32 * NWQ, 0, s>>>(a);
-    events_kernel<<<a.num_packs, 32, 0, s>>>(a);
+    events_kernel<4><<<a.num_packs, 128, 0, s>>>(a);
     fix_kernel<NWQ><<<qb, 32 * NWQ, 0, s>>>(a);
     return cudaGetLastError();
 }
