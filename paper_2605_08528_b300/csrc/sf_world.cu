@@ -718,6 +718,81 @@ __device__ unsigned long long coop_knn32(const WRoads& v, float qx, float qy, fl
     return run;
 }
 
+// One pass over the cells around q for the three point queries of an agent
+// at once: the 32 nearest road points (radius R32), the nearest driving-lane
+// segment (radius Rl) and the lane-forbidden test of the footprint's circles.
+// The scanned square covers all three; each answer is exact when its own
+// radius held enough candidates, else that query is redone alone with a
+// growing radius (coop_knn32 / coop_nearest_lane).  Returns the lane; lane t
+// of the warp gets the t-th nearest point's key in *key.
+__device__ Lane coop_point_queries(const WRoads& v, float qx, float qy, float gx, float gy, float hx, float hy,
+                                   float R32, float Rl, int lane, unsigned long long* buf, bool* forb,
+                                   unsigned long long* key) {
+    const unsigned lt = (1u << lane) - 1u;
+    const float lim_f = (kCircR + kEdgeHalfWidth) * (kCircR + kEdgeHalfWidth);
+    const float S = fmaxf(fmaxf(Rl + kSegReach, kCircD + kCircR + kEdgeHalfWidth + kSegReach), R32);
+    const Rows w = rows_covering(v, qx, qy, S);
+    const float Rle = S - kSegReach;                  // every lane segment within Rle is seen
+    const float lim_l = w.all ? kInf : Rle * Rle * (1.f - 1e-5f);
+    unsigned long long thr = w.all ? kKeyInf : key_of(R32 * R32 * (1.f - 1e-5f), 0);
+    unsigned long long run = kKeyInf, best = kKeyInf;
+    bool f = false;
+    int cnt = 0;
+    if (w.cx0 <= w.cx1)
+        for (int cy = w.cy0; cy <= w.cy1; ++cy) {
+            const int row = cy * v.nx;
+            const int s = v.coff[row + w.cx0], e = v.coff[row + w.cx1 + 1];
+            for (int base = s; base < e; base += 32) {
+                const int i = base + lane;
+                unsigned long long k = kKeyInf;
+                if (i < e) {
+                    const float4 sg = v.seg[i];
+                    const uint32_t m = v.info[i];
+                    const float dx = sg.x - qx, dy = sg.y - qy;
+                    k = rkey(dx * dx + dy * dy, m, i);
+                    if (k >= thr) k = kKeyInf;
+                    if (m & kInfoSegNext) {
+                        if (m & kInfoLane) {
+                            const float d2 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
+                            if (d2 < lim_l) best = umin64(best, rkey(d2, m, i));
+                        } else if (m & kInfoEdge) {
+#pragma unroll
+                            for (int c = -1; c <= 1; ++c) {
+                                const float cx_ = qx + (float)c * kCircD * hx, cy_ = qy + (float)c * kCircD * hy;
+                                if (seg_dist2(sg.x, sg.y, sg.z, sg.w, cx_, cy_) < lim_f) f = true;
+                            }
+                        }
+                    }
+                }
+                const unsigned mk = __ballot_sync(kFull, k != kKeyInf);
+                if (k != kKeyInf) buf[cnt + __popc(mk & lt)] = k;
+                cnt += __popc(mk);
+                __syncwarp();
+                if (cnt >= 32) {
+                    run = merge32(run, buf[lane], lane);
+                    const unsigned long long rest = lane < cnt - 32 ? buf[32 + lane] : kKeyInf;
+                    __syncwarp();
+                    if (lane < cnt - 32) buf[lane] = rest;
+                    cnt -= 32;
+                    thr = umin64(thr, shfl64(run, 31));
+                    __syncwarp();
+                }
+            }
+        }
+    if (cnt > 0) {
+        const unsigned long long c = lane < cnt ? buf[lane] : kKeyInf;
+        run = merge32(run, c, lane);
+    }
+    __syncwarp();
+    *forb = __any_sync(kFull, f);
+    best = warp_min64(best);
+    // too few points within R32: the 32 nearest alone, from a larger radius
+    *key = (shfl64(run, 31) != kKeyInf || w.all) ? run : coop_knn32(v, qx, qy, R32 * kGrow, lane, buf);
+    if (best == kKeyInf && !w.all)                   // no lane within Rle: the nearest lane alone
+        return coop_nearest_lane(v, qx, qy, gx, gy, Rle * kGrow, lane);
+    return lane_of(v, best, qx, qy, gx, gy);
+}
+
 // time for the constant-velocity ray from an agent to reach the nearest road
 // edge segment within 40 m (App. G)
 __device__ float coop_edge_ray(const WRoads& v, float px, float py, float vx, float vy, int lane) {
@@ -1597,9 +1672,28 @@ __global__ void __launch_bounds__(32 * NWQ) query_kernel(const WorldArgs args) {
     const float4 p = args.st.pos[a], vel = args.st.vel[a], goal = args.st.goal[a];
     const float2 h = args.sc.head[a];
     float* hnt = args.out.hint + 4 * (size_t)a;
-    const AgentQ q = agent_event_queries(v, p.x, p.y, goal.x, goal.y, h.x, h.y, vel.x, vel.y, hnt, lane);
-    if (lane == 0) args.sc.q[a] = q;
-    agent_road_block(v, true, false, p.x, p.y, goal.x, goal.y, h.x, h.y, hnt, lane, kbuf[warp], orow, krow, nullptr);
+    bool forb = false;
+    unsigned long long key = kKeyInf;
+    const Lane L = coop_point_queries(v, p.x, p.y, goal.x, goal.y, h.x, h.y, hint_radius(hnt, 0, p.x, p.y, kKnnR0),
+                                      hint_radius(hnt, 1, p.x, p.y, kLaneR0), lane, kbuf[warp], &forb, &key);
+    const float tedge = coop_edge_ray(v, p.x, p.y, vel.x, vel.y, lane);
+    const unsigned long long last = shfl64(key, 31);
+    __syncwarp();
+    if (lane == 0) {
+        AgentQ q;
+        q.seg = L.seg; q.dist = L.dist; q.lat = L.lat; q.tx = L.tx; q.ty = L.ty;
+        q.tedge = tedge; q.forb = forb ? 1 : 0; q.need = 0;
+        args.sc.q[a] = q;
+        hnt[0] = last != kKeyInf ? sqrtf(key_d2(last)) : 0.f;
+        hnt[1] = L.seg >= 0 ? L.dist : 0.f;
+        hnt[2] = p.x;
+        hnt[3] = p.y;
+    }
+    float f[kObsPt] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (key != kKeyInf) point_features(v, key, h.x, h.y, p.x, p.y, f);
+#pragma unroll
+    for (int k = 0; k < kObsPt; ++k) orow[kObsPt * lane + k] = f[k];
+    if (krow) krow[lane] = key != kKeyInf ? v.q0 + rkey_local(key) : -1;
 }
 
 // events, rewards, respawns, neighbours, ego group, outputs and state; marks
