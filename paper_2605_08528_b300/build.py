@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr",
+         "-prec-div=false", "-prec-sqrt=false"]   # FP32 divide and square root to within 2 ulp
 
 
 def sources():
@@ -19,7 +20,7 @@ def sources():
 
 def deps():
     return sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
-        os.path.join(os.path.dirname(HERE), "include", "sf.h")]
+        os.path.join(os.path.dirname(HERE), "include", "sf.h"), os.path.abspath(__file__)]
 
 
 def stale() -> bool:

@@ -43,6 +43,7 @@ constexpr float kWheelbase = 2.6f;
 constexpr float kZStar = (float)(0.25 + (0.3 - kMassD * 9.81 / (4.0 * 35000.0)) + 0.33);
 // bounding-circle cull of footprint pairs: 2 * sqrt(hl^2 + hw^2), squared
 constexpr float kPairCull2 = (float)(4.0 * (2.25 * 2.25 + 0.9 * 0.9));
+constexpr float kPairCullR = 4.8466483f;   // sqrt(kPairCull2), rounded up
 
 // ---------------------------------------------------------------- rewards / events (App. G)
 constexpr float kGoalR = 3.0f, kWGoal = 45.0f, kWCollision = 6.0f, kWCrash = 10.0f, kWLaneForb = 20.0f;

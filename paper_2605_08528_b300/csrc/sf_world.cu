@@ -619,6 +619,24 @@ __device__ __forceinline__ Lane lane_of(const WRoads& v, unsigned long long best
     return L;
 }
 
+// lane-forbidden test of one edge segment against the footprint's three
+// circles, given d0 = its squared distance from the centre circle's centre q:
+// the side circles (kCircD from q) can only touch a segment closer to q than
+// kCircD + the touch distance, tested first (a conservative bound)
+constexpr float kForbLim = (kCircR + kEdgeHalfWidth) * (kCircR + kEdgeHalfWidth);
+constexpr float kForbSide = (kCircD + kCircR + kEdgeHalfWidth) * (kCircD + kCircR + kEdgeHalfWidth) * 1.0001f + 1e-4f;
+__device__ __forceinline__ bool forb_touch(const float4& sg, float d0, float qx, float qy, float hx, float hy) {
+    if (d0 < kForbLim) return true;
+    if (!(d0 < kForbSide)) return false;
+    bool f = false;
+#pragma unroll
+    for (int c = -1; c <= 1; c += 2) {
+        const float cx_ = qx + (float)c * kCircD * hx, cy_ = qy + (float)c * kCircD * hy;
+        if (seg_dist2(sg.x, sg.y, sg.z, sg.w, cx_, cy_) < kForbLim) f = true;
+    }
+    return f;
+}
+
 // nearest driving-lane segment (App. G), exact: a segment within D of q starts
 // inside the square of half-size D + 3 m around q (no segment is longer than
 // 3 m), so scanning the cells of the square of half-size S finds every lane
@@ -628,7 +646,6 @@ __device__ __forceinline__ Lane lane_of(const WRoads& v, unsigned long long best
 // then also covers every edge segment that can touch a circle.
 __device__ Lane coop_nearest_lane(const WRoads& v, float qx, float qy, float gx, float gy, float R, int lane,
                                   bool* forb = nullptr, float hx = 1.f, float hy = 0.f) {
-    const float lim_f = (kCircR + kEdgeHalfWidth) * (kCircR + kEdgeHalfWidth);
     float S = R + kSegReach;
     if (forb) S = fmaxf(S, kCircD + kCircR + kEdgeHalfWidth + kSegReach);
     bool edges = forb != nullptr, f = false;
@@ -644,18 +661,13 @@ __device__ Lane coop_nearest_lane(const WRoads& v, float qx, float qy, float gx,
                 const int s = v.coff[row + w.cx0], e = v.coff[row + w.cx1 + 1];
                 for (int i = s + lane; i < e; i += 32) {
                     const uint32_t m = v.info[i];
-                    if (!(m & kInfoSegNext)) continue;
+                    if (!(m & kInfoSegNext) || !(m & (kInfoLane | (edges ? kInfoEdge : 0u)))) continue;
+                    const float4 sg = v.seg[i];
+                    const float d0 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
                     if (m & kInfoLane) {
-                        const float4 sg = v.seg[i];
-                        const float d2 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
-                        if (d2 < lim) best = umin64(best, rkey(d2, m, i));
-                    } else if (edges && (m & kInfoEdge)) {
-                        const float4 sg = v.seg[i];
-#pragma unroll
-                        for (int c = -1; c <= 1; ++c) {
-                            const float cx_ = qx + (float)c * kCircD * hx, cy_ = qy + (float)c * kCircD * hy;
-                            if (seg_dist2(sg.x, sg.y, sg.z, sg.w, cx_, cy_) < lim_f) f = true;
-                        }
+                        if (d0 < lim) best = umin64(best, rkey(d0, m, i));
+                    } else if (forb_touch(sg, d0, qx, qy, hx, hy)) {
+                        f = true;
                     }
                 }
             }
@@ -729,7 +741,6 @@ __device__ Lane coop_point_queries(const WRoads& v, float qx, float qy, float gx
                                    float R32, float Rl, int lane, unsigned long long* buf, bool* forb,
                                    unsigned long long* key) {
     const unsigned lt = (1u << lane) - 1u;
-    const float lim_f = (kCircR + kEdgeHalfWidth) * (kCircR + kEdgeHalfWidth);
     const float S = fmaxf(fmaxf(Rl + kSegReach, kCircD + kCircR + kEdgeHalfWidth + kSegReach), R32);
     const Rows w = rows_covering(v, qx, qy, S);
     const float Rle = S - kSegReach;                  // every lane segment within Rle is seen
@@ -751,16 +762,12 @@ __device__ Lane coop_point_queries(const WRoads& v, float qx, float qy, float gx
                     const float dx = sg.x - qx, dy = sg.y - qy;
                     k = rkey(dx * dx + dy * dy, m, i);
                     if (k >= thr) k = kKeyInf;
-                    if (m & kInfoSegNext) {
+                    if ((m & kInfoSegNext) && (m & (kInfoLane | kInfoEdge))) {
+                        const float d0 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
                         if (m & kInfoLane) {
-                            const float d2 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
-                            if (d2 < lim_l) best = umin64(best, rkey(d2, m, i));
-                        } else if (m & kInfoEdge) {
-#pragma unroll
-                            for (int c = -1; c <= 1; ++c) {
-                                const float cx_ = qx + (float)c * kCircD * hx, cy_ = qy + (float)c * kCircD * hy;
-                                if (seg_dist2(sg.x, sg.y, sg.z, sg.w, cx_, cy_) < lim_f) f = true;
-                            }
+                            if (d0 < lim_l) best = umin64(best, rkey(d0, m, i));
+                        } else if (forb_touch(sg, d0, qx, qy, hx, hy)) {
+                            f = true;
                         }
                     }
                 }
@@ -1111,6 +1118,17 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
     }
     prevx = A.px; prevy = A.py;
     bool gated = false;
+    // contact candidates: the pairs of the world that can come within the cull
+    // distance during this control step.  Lane i may move |v_i| T + 1 m (its
+    // budget) before the set is rebuilt, so a pair farther apart at the start
+    // than the cull distance + both budgets is culled at every substep, and
+    // skipping it is exact (a culled pair adds +0, and a force sum that starts
+    // at +0 is never -0).  A lane that exceeds its budget rebuilds the set as
+    // all pairs of its world for the remaining substeps.
+    const float T = args.h * args.substeps;
+    const float budget = sqrtf(A.vx * A.vx + A.vy * A.vy) * T + 1.f;
+    uint32_t near = 0u;
+    bool wide = false;
     for (int s = 0; s < args.substeps; ++s) {
         float sx_, sy_;
         heading_of(A.qw, A.qx, A.qy, A.qz, sx_, sy_);
@@ -1118,10 +1136,21 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
         const uint32_t alive_bits = __ballot_sync(kFull, alive);
         __syncwarp();
         if (s == 0 && args.surr_mode != 0) gated = surr_gate(E, base, n, lane, alive_bits, A, args.h * args.substeps);
+        if (s == 0) {
+            for (int j = base; j < base + n; ++j) {
+                if (j == lane) continue;
+                const float bj = sqrtf(E.vx[j] * E.vx[j] + E.vy[j] * E.vy[j]) * T + 1.f;
+                const float reach = kPairCullR + budget + bj + 0.01f;
+                const float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
+                if (dx * dx + dy * dy <= reach * reach) near |= 1u << j;
+            }
+        }
+        if (!wide && __any_sync(kFull, alive && A.dpx * A.dpx + A.dpy * A.dpy > budget * budget)) wide = true;
+        const uint32_t cand = (wide ? 0xFFFFFFFFu : near) & alive_bits;
         float fcx = 0.f, fcy = 0.f, tcz = 0.f;
         if (alive) {
             for (int j = base; j < base + n; ++j) {
-                if (j == lane || !((alive_bits >> j) & 1u)) continue;
+                if (j == lane || !((cand >> j) & 1u)) continue;
                 const int lo = min(lane, j), hi = max(lane, j);
                 float fx, fy, tz;
                 pair_force(E.px[lo], E.py[lo], E.dx[lo], E.dy[lo], E.hx[lo], E.hy[lo], E.vx[lo], E.vy[lo],
