@@ -254,7 +254,10 @@ sf_status sf_sync(sf_handle h);
  * An MLP of L dense layers y = act(W x + b), W [out, in] fp32 masters with
  * bf16 copies for the tcgen05 GEMMs, fp32 accumulation.  Hidden layers use
  * hidden_act, the last layer out_act (SF_ACT_*).  All device work runs on
- * the stream given to sf_mlp_create.
+ * the stream given to sf_mlp_create (or, for a step that uses the MLP, on the
+ * world handle's stream).  An MLP keeps its activations in buffers of its
+ * own: work that uses one MLP (or one surrogate) must not overlap on two
+ * streams.
  * ---------------------------------------------------------------------- */
 typedef struct sf_mlp* sf_mlp_handle;
 #define SF_ACT_NONE 0

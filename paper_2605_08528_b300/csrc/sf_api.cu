@@ -456,13 +456,15 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     SF_ALLOC(h->place_buf, float, Aa * 6);
     SF_ALLOC(h->all_mask, uint8_t, Aa);
     SF_ALLOC(h->act_buf, float, Aa * 3);
-    AgentQ* scq; float2 *scprev, *schead; uint8_t* scflag; int32_t* scworld;
+    AgentQ* scq; float2 *scprev, *schead; uint8_t* scflag; int32_t *scworld, *scfix; unsigned* sccount;
     SF_ALLOC(scq, AgentQ, Aa);
     SF_ALLOC(scprev, float2, Aa);
     SF_ALLOC(schead, float2, Aa);
     SF_ALLOC(scflag, uint8_t, Aa);
     SF_ALLOC(scworld, int32_t, Aa);
-    h->sc = StepScratch{scq, scprev, schead, scflag, scworld};
+    SF_ALLOC(scfix, int32_t, Aa);
+    SF_ALLOC(sccount, unsigned, 1);
+    h->sc = StepScratch{scq, scprev, schead, scflag, scworld, scfix, sccount};
     std::vector<int32_t> agent_world(Aa);
     for (int w = 0; w < W; ++w)
         for (int k = world[w].x; k < world[w].x + world[w].y; ++k) agent_world[k] = w;
@@ -502,6 +504,7 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     up(meta, meta_h.data(), Aa * 4);
     up(scworld, agent_world.data(), Aa * 4);
     zero(scflag, Aa);
+    zero(sccount, 4);
     zero(obs, Aa * SF_OBS_DIM * 4); zero(reward, Aa * 4); zero(done, Aa); zero(events, Aa * 4);
     zero(drac, Aa * 4); zero(err_word, 4); zero(hint, Aa * 16);
     if (e == cudaSuccess && Aa) e = cudaMemset(lane_seg, 0xFF, Aa * 4);

@@ -179,6 +179,8 @@ struct StepScratch {
     float2* head;                // [A] heading after the physics, then after respawns
     uint8_t* flag;               // [A] bit 0 non-finite this step, bit 1 road block stale
     const int32_t* agent_world;  // [A] world of each agent
+    int32_t* fix_list;           // [A] agents whose road block is stale, in arrival order
+    unsigned* fix_count;         // [1] their number (reset by the physics kernel)
 };
 
 struct WorldArgs {

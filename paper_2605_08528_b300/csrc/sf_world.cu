@@ -1671,6 +1671,7 @@ __global__ void __launch_bounds__(32, 16) phys_kernel(const WorldArgs args) {
     if (!c.has) A.meta = 0;
     bool alive = c.has && (status_of(A.meta) & kAlive), nonfin = false;
     float prevx = 0.f, prevy = 0.f, hx = 1.f, hy = 0.f;
+    if (blockIdx.x == 0 && lane == 0) *args.sc.fix_count = 0u;   // the events kernel appends after this kernel
     lanes_physics(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E);
     if (c.has) {
         store_agent(args.st, c.a, A);
@@ -1781,6 +1782,7 @@ __global__ void __launch_bounds__(32 * NWE) events_kernel(const WorldArgs args) 
         if (c.has) {
             args.sc.head[c.a] = make_float2(hx, hy);
             args.sc.flag[c.a] = (respawn || parked_now) ? 2 : 0;
+            if (respawn || parked_now) args.sc.fix_list[atomicAdd(args.sc.fix_count, 1u)] = c.a;
         }
         lanes_final_a(c, lane, A, recompute, alive_now, E, nb, hx, hy, N);
         const unsigned rb = __ballot_sync(kFull, recompute);
@@ -1794,33 +1796,37 @@ __global__ void __launch_bounds__(32 * NWE) events_kernel(const WorldArgs args) 
 }
 
 // road-point blocks of the agents the events kernel respawned (nearest lane
-// and 32 points from the default radii, the ego lane features) or parked (zeros)
+// and 32 points from the default radii, the ego lane features) or parked
+// (zeros): the warps of a small grid walk the events kernel's list
 template <int NWQ>
 __global__ void __launch_bounds__(32 * NWQ) fix_kernel(const WorldArgs args) {
     __shared__ unsigned long long kbuf[NWQ][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int a = blockIdx.x * NWQ + warp;
-    if (a >= args.num_agents || !(args.sc.flag[a] & 2u)) return;   // warp-uniform
-    float* orow = args.out.obs + (size_t)a * kObsDim + kObsEgo + kK * kObsNbr;
-    int32_t* krow = (args.flags & kFlagRecord) ? args.out.knn_pts + (size_t)a * kL : nullptr;
-    if (!(status_of(args.st.meta[a]) & kAlive)) {
+    const unsigned count = *args.sc.fix_count;
+    for (unsigned i = blockIdx.x * NWQ + warp; i < count; i += gridDim.x * NWQ) {   // warp-uniform
+        const int a = args.sc.fix_list[i];
+        float* orow = args.out.obs + (size_t)a * kObsDim + kObsEgo + kK * kObsNbr;
+        int32_t* krow = (args.flags & kFlagRecord) ? args.out.knn_pts + (size_t)a * kL : nullptr;
+        if (!(status_of(args.st.meta[a]) & kAlive)) {
 #pragma unroll
-        for (int k = 0; k < kObsPt; ++k) orow[kObsPt * lane + k] = 0.f;
-        if (krow) krow[lane] = -1;
-        return;
-    }
-    const DevGrid g = args.rd.grid[args.sc.agent_world[a]];
-    const WRoads v = view_of(g, args.rd.blob + g.blob);
-    const float4 p = args.st.pos[a], goal = args.st.goal[a];
-    const float2 h = args.sc.head[a];
-    Lane L;
-    agent_road_block(v, true, true, p.x, p.y, goal.x, goal.y, h.x, h.y, args.out.hint + 4 * (size_t)a, lane,
-                     kbuf[warp], orow, krow, &L);
-    if (lane == 0) {
-        float* ego = args.out.obs + (size_t)a * kObsDim;
-        ego[14] = L.seg >= 0 ? L.lat / 3.6f : 0.f;
-        ego[15] = L.seg >= 0 ? cross2(L.tx, L.ty, h.x, h.y) : 0.f;
-        if (args.flags & kFlagRecord) args.out.lane_seg[a] = L.seg;
+            for (int k = 0; k < kObsPt; ++k) orow[kObsPt * lane + k] = 0.f;
+            if (krow) krow[lane] = -1;
+            continue;
+        }
+        const DevGrid g = args.rd.grid[args.sc.agent_world[a]];
+        const WRoads v = view_of(g, args.rd.blob + g.blob);
+        const float4 p = args.st.pos[a], goal = args.st.goal[a];
+        const float2 h = args.sc.head[a];
+        Lane L;
+        agent_road_block(v, true, true, p.x, p.y, goal.x, goal.y, h.x, h.y, args.out.hint + 4 * (size_t)a, lane,
+                         kbuf[warp], orow, krow, &L);
+        if (lane == 0) {
+            float* ego = args.out.obs + (size_t)a * kObsDim;
+            ego[14] = L.seg >= 0 ? L.lat / 3.6f : 0.f;
+            ego[15] = L.seg >= 0 ? cross2(L.tx, L.ty, h.x, h.y) : 0.f;
+            if (args.flags & kFlagRecord) args.out.lane_seg[a] = L.seg;
+        }
+        __syncwarp();
     }
 }
 
@@ -1934,8 +1940,11 @@ static cudaError_t launch_split(const WorldArgs& a, cudaStream_t s) {
     const int qb = (a.num_agents + NWQ - 1) / NWQ;
     phys_kernel<<<a.num_packs, 32, 0, s>>>(a);
     query_kernel<NWQ><<<qb, 32 * NWQ, 0, s>>>(a);
-    events_kernel<4><<<a.num_packs, 128, 0, s>>>(a);
-    fix_kernel<NWQ><<<qb, 32 * NWQ, 0, s>>>(a);
+    // blocks of about 32 agents keep one warp for their pairs (more blocks
+    // resident); blocks of one small world spread them over four
+    if (a.num_agents > 16 * a.num_packs) events_kernel<1><<<a.num_packs, 32, 0, s>>>(a);
+    else events_kernel<4><<<a.num_packs, 128, 0, s>>>(a);
+    fix_kernel<NWQ><<<min(qb, 4 * 148), 32 * NWQ, 0, s>>>(a);
     return cudaGetLastError();
 }
 

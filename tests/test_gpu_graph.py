@@ -82,12 +82,16 @@ def test_graph_with_surrogate_matches_individual_calls():
     act_buf = torch.zeros((W1.A, 3), device="cuda")
     torch.cuda.synchronize()
     g = sf.sf_graph_capture(W1.h, d_actions=act_buf, surrogate=sur)
+    # one surrogate object: its MLP's activation buffers serve one stream at a time
     for t in range(8):
         with torch.cuda.stream(s1):
             act_buf.copy_(acts[t])
             sf.sf_graph_launch(g)
+    torch.cuda.synchronize()
+    for t in range(8):
         with torch.cuda.stream(s2):
             sf.sf_step_surrogate(W2.h, sur, acts[t])
+    torch.cuda.synchronize()
     F1, I1, _ = sf.sf_get_state(W1.h)
     F2, I2, _ = sf.sf_get_state(W2.h)
     assert np.array_equal(F1, F2) and np.array_equal(I1, I2)
