@@ -339,26 +339,28 @@ def main_ours(args):
                     "d2h_bytes_per_step": a256["d2h"]},
             "gpu_launches": args.steps,
             "graph": "each timed step is one CUDA-graph replay",
-            "roofline": {"bound": "hbm", "kernel": "world_kernel<step>", "achieved": a256["achieved"],
+            "roofline": {"bound": "hbm", "kernel": step_kernels(a256["tuned"]), "achieved": a256["achieved"],
                          "peak": peak, "unit": "GB/s", "frac": a256["achieved"] / peak,
                          "peak_source": peak_kind, "algorithmic_bytes_per_launch": a256["bytes"]["total"],
-                         "traffic": traffic.get("256x16")},
+                         "traffic": traffic_of(traffic, "256x16", a256["tuned"])},
             "scale_4096x16": {"value": a4096["casps"], "unit": "CASPS", "ms_per_step": a4096["ms"],
                               "p50_ms": a4096["p50"], "p99_ms": a4096["p99"],
                               "agents": a4096["A"] * world, "autotune": a4096["tuned"],
                               "e2e": {"value": a4096["e2e"], "unit": "CASPS", "h2d_bytes_per_step": a4096["h2d"],
                                       "d2h_bytes_per_step": a4096["d2h"]},
-                              "roofline": {"bound": "hbm", "achieved": a4096["achieved"], "peak": peak,
+                              "roofline": {"bound": "hbm", "kernel": step_kernels(a4096["tuned"]),
+                                           "achieved": a4096["achieved"], "peak": peak,
                                            "unit": "GB/s", "frac": a4096["achieved"] / peak,
                                            "algorithmic_bytes_per_launch": a4096["bytes"]["total"],
-                                           "traffic": traffic.get("4096x16")},
+                                           "traffic": traffic_of(traffic, "4096x16", a4096["tuned"])},
                               "mean_peak_drac": a4096["peak_drac"]},
             "scale_ragged1024": None if arag is None else {
                 "value": arag["casps"], "unit": "CASPS", "ms_per_step": arag["ms"], "p50_ms": arag["p50"],
                 "p99_ms": arag["p99"], "agents": arag["A"] * world, "autotune": arag["tuned"],
                 "workload": "1024 worlds, agents floor(exp(U[0, ln 32])), road points exp(U[ln 100, ln 5000]), "
                             "CSR; a random 20% reset mask every step inside the graph",
-                "roofline": {"bound": "hbm", "achieved": arag["achieved"], "peak": peak, "unit": "GB/s",
+                "roofline": {"bound": "hbm", "kernel": step_kernels(arag["tuned"]), "achieved": arag["achieved"],
+                             "peak": peak, "unit": "GB/s",
                              "frac": arag["achieved"] / peak,
                              "algorithmic_bytes_per_launch": arag["bytes"]["total"]}},
             "scale_4096x16_policy": None if apol is None else {
@@ -386,15 +388,39 @@ def main_ours(args):
         dist.destroy_process_group()
 
 
+def step_kernels(tuned) -> str:
+    """The kernels one timed step launches, from the autotuned launch shape."""
+    if not tuned:
+        return "world_kernel<step>"
+    nw, pack, stage, split = tuned[0]
+    if split:
+        return "split step: phys, query<%d>, events, fix kernels (pack %d)" % (nw, pack)
+    return "world_kernel<step, %d warps> (pack %d, staged %d B)" % (nw, pack, stage)
+
+
 def load_traffic():
-    """DRAM bytes per launch of the world kernel from the committed ncu summary
-    (null when no capture of the current kernel exists)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch of the kernel a roofline describes, from the
+    committed ncu summary (lines "workload bytes ..."); none when the current
+    kernel has no capture."""
+    out = {}
     try:
-        with open(p) as f:
-            return json.load(f)
-    except Exception:
-        return {}
+        with open(os.path.join(ROOT, "profiles", "world_kernel_traffic.txt")) as f:
+            for line in f:
+                parts = line.split()
+                if parts and not parts[0].startswith("#") and len(parts) >= 3:
+                    out[parts[0]] = (int(parts[1]), [int(x) for x in parts[2].split(",")])
+    except (OSError, ValueError):
+        pass
+    return out
+
+
+def traffic_of(traffic, name, tuned):
+    """Captured DRAM bytes per launch for this workload when the timed launch
+    shape is the captured one, else None."""
+    t = traffic.get(name)
+    if t is None or not tuned or list(tuned[0]) != t[1]:
+        return None
+    return t[0]
 
 
 # --------------------------------------------------------------------------- reference arm
