@@ -30,6 +30,10 @@ EV = dict(goal=1, collision=2, crash=4, lane_forbidden=8, offroad=16, idle=32, t
           nonfinite=128, respawned=256)
 FLAG_INVINCIBLE, FLAG_AUTO_RESET = 1, 2
 K_AGENTS, L_POINTS, OBS = 8, 32, 320
+FULL_EGO, FULL_KR, FULL_PT, FULL_KV, FULL_NB = 11, 350, 5, 24, 7
+FULL_OBS = FULL_EGO + FULL_KR * FULL_PT + FULL_KV * FULL_NB   # 1929 (App. D)
+FULL_ROAD0, FULL_VEH0 = FULL_EGO, FULL_EGO + FULL_KR * FULL_PT
+FULL_RADIUS = 10.0
 
 
 def build(force: bool = False) -> str:
@@ -88,6 +92,7 @@ def lib():
         L.or_step.restype = i
         L.or_events.argtypes = [vp, vp, vp, vp, vp, i, vp]
         L.or_observe.argtypes = [vp, vp, vp, vp, vp]
+        L.or_observe_full.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.or_reset.argtypes = [vp, vp, vp, vp, vp, u64, vp]
         L.or_place_agent.argtypes = [vp, vp, vp, i, d, d, d, d, d, d, i, i]
         L.or_sat.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -182,6 +187,17 @@ class Oracle:
         self._chk(F, I)
         o, s = self._outs(True)
         lib().or_observe(C.byref(self.P), C.byref(self.S), _p(F), _p(I), C.byref(s))
+        return o
+
+    def observe_full(self, F, I):
+        """The paper's 1,929-value observation of every agent (App. D) with the
+        filled-slot counts and the selected segment / agent indices."""
+        self._chk(F, I)
+        A = self.A
+        o = dict(obs=np.zeros((A, FULL_OBS)), n_road=np.zeros(A, np.int32), n_veh=np.zeros(A, np.int32),
+                 road_idx=np.zeros((A, FULL_KR), np.int32), veh_idx=np.zeros((A, FULL_KV), np.int32))
+        lib().or_observe_full(C.byref(self.P), C.byref(self.S), _p(F), _p(I), _p(o["obs"]), _p(o["n_road"]),
+                              _p(o["n_veh"]), _p(o["road_idx"]), _p(o["veh_idx"]))
         return o
 
     def reset(self, F, I, mask, seed=0):

@@ -637,6 +637,119 @@ void or_observe(const or_params* P, const or_scene* S, const double* F, const in
         for (int a = S->agent_off[w]; a < S->agent_off[w + 1]; ++a) observe_agent(P, S, w, F, I, a, out);
 }
 
+/* ------------------------------------------------------------------ full observation (App. D) */
+/* One agent's 1,929 values.  Road context: App. D selects the road points within
+ * r = 10 m of the ego and orders them by their original polyline index; the points
+ * are the segment midpoints baked at world build time (App. C "Segment generation",
+ * "Metadata baking"), so the candidates are the world's valid segments k -> k+1 in
+ * ascending k (polyline order, then point order), the test is |m - p|^2 <= r^2 on the
+ * midpoint m, and the first 350 are kept.  Neighbours: the 24 nearest alive others
+ * with self and dead agents at infinity (App. D). */
+static void observe_full_agent(const or_params* P, const or_scene* S, int w, const double* F, const int32_t* I,
+                               int a, double* o, int32_t* n_road, int32_t* n_veh, int32_t* road_idx,
+                               int32_t* veh_idx) {
+    if (o) memset(o, 0, sizeof(double) * OR_FULL_OBS);
+    if (n_road) n_road[a] = 0;
+    if (n_veh) n_veh[a] = 0;
+    if (road_idx) for (int t = 0; t < OR_FULL_KR; ++t) road_idx[(size_t)a * OR_FULL_KR + t] = -1;
+    if (veh_idx) for (int t = 0; t < OR_FULL_KV; ++t) veh_idx[(size_t)a * OR_FULL_KV + t] = -1;
+    if (!alive(I, a)) return;
+    const double* f = F + (size_t)a * OR_NF;
+    double hd[2];
+    heading_of(f, hd);
+    double p[2] = {f[OR_F_PX], f[OR_F_PY]};
+    double v[2] = {f[OR_F_VX], f[OR_F_VY]};
+
+    /* ego group: App. D items 1-4, then the weather token analogue (four values) */
+    if (o) {
+        double gbx, gby, vbx, vby;
+        to_ego(hd, f[OR_F_GX] - p[0], f[OR_F_GY] - p[1], &gbx, &gby);
+        to_ego(hd, v[0], v[1], &vbx, &vby);
+        double gn = sqrt(gbx * gbx + gby * gby);
+        int pc = I[a * OR_NI + OR_I_PRECIP], sc = I[a * OR_NI + OR_I_SURFACE];
+        o[0] = gbx / P->scene_half;
+        o[1] = gby / P->scene_half;
+        o[2] = gn > 0 ? gby / gn : 0.0;
+        o[3] = gn > 0 ? gbx / gn : 1.0;
+        o[4] = gn / P->scene_half;
+        o[5] = vbx / 10.0;
+        o[6] = vby / 10.0;
+        o[7] = pc / 3.0;
+        o[8] = sc == 0; o[9] = sc == 1; o[10] = sc == 2;
+    }
+
+    /* road context: every valid segment of the world, in index order */
+    const double r = OR_FULL_RADIUS;
+    int nr = 0;
+    for (int pl = S->poly_off[w]; pl < S->poly_off[w + 1] && nr < OR_FULL_KR; ++pl) {
+        for (int k = S->point_off[pl]; k < S->point_off[pl + 1] && nr < OR_FULL_KR; ++k) {
+            if (!seg_valid(P, S, pl, k)) continue;
+            double mx = 0.5 * (S->px[k] + S->px[k + 1]), my = 0.5 * (S->py[k] + S->py[k + 1]);
+            double dx = mx - p[0], dy = my - p[1];
+            if (dx * dx + dy * dy > r * r) continue;
+            if (road_idx) road_idx[(size_t)a * OR_FULL_KR + nr] = k;
+            if (o) {
+                double ex = S->px[k + 1] - S->px[k], ey = S->py[k + 1] - S->py[k];
+                double n = sqrt(ex * ex + ey * ey);
+                double ux = n > 0 ? ex / n : 0.0, uy = n > 0 ? ey / n : 0.0;
+                double bx, by, ubx, uby;
+                to_ego(hd, dx, dy, &bx, &by);
+                to_ego(hd, ux, uy, &ubx, &uby);
+                double* s = o + OR_FULL_EGO + nr * OR_FULL_PT;
+                s[0] = bx / r;
+                s[1] = by / r;
+                s[2] = S->poly_type[pl] / 20.0;
+                s[3] = ubx;
+                s[4] = uby;
+            }
+            ++nr;
+        }
+    }
+    if (n_road) n_road[a] = nr;
+
+    /* neighbour context: full sort of the alive others by (squared distance, index) */
+    int a0 = S->agent_off[w], a1 = S->agent_off[w + 1];
+    keyed* buf = (keyed*)malloc(sizeof(keyed) * (size_t)(a1 - a0 + 1));
+    int m = 0;
+    for (int j = a0; j < a1; ++j) {
+        if (j == a || !alive(I, j)) continue;
+        double dx = F[(size_t)j * OR_NF + OR_F_PX] - p[0], dy = F[(size_t)j * OR_NF + OR_F_PY] - p[1];
+        buf[m].key = dx * dx + dy * dy; buf[m].idx = j; ++m;
+    }
+    qsort(buf, (size_t)m, sizeof(keyed), cmp_keyed);
+    int nv = m < OR_FULL_KV ? m : OR_FULL_KV;
+    for (int t = 0; t < nv; ++t) {
+        int j = buf[t].idx;
+        if (veh_idx) veh_idx[(size_t)a * OR_FULL_KV + t] = j;
+        if (!o) continue;
+        const double* g = F + (size_t)j * OR_NF;
+        double hj[2];
+        heading_of(g, hj);
+        double pj[2] = {g[OR_F_PX], g[OR_F_PY]}, vj[2] = {g[OR_F_VX], g[OR_F_VY]};
+        double bx, by;
+        to_ego(hd, pj[0] - p[0], pj[1] - p[1], &bx, &by);
+        double dpsi = atan2(cross2(hd[0], hd[1], hj[0], hj[1]), hd[0] * hj[0] + hd[1] * hj[1]);
+        double* s = o + OR_FULL_EGO + OR_FULL_KR * OR_FULL_PT + t * OR_FULL_NB;
+        s[0] = bx / P->scene_half;
+        s[1] = by / P->scene_half;
+        s[2] = 2 * P->half_len / P->scene_half;
+        s[3] = 2 * P->half_wid / P->scene_half;
+        s[4] = dpsi / M_PI;
+        s[5] = sqrt(vj[0] * vj[0] + vj[1] * vj[1]) / 10.0;
+        s[6] = or_ttc(P, p, hd, v, pj, hj, vj) / P->ttc_max;
+    }
+    free(buf);
+    if (n_veh) n_veh[a] = nv;
+}
+
+void or_observe_full(const or_params* P, const or_scene* S, const double* F, const int32_t* I, double* obs,
+                     int32_t* n_road, int32_t* n_veh, int32_t* road_idx, int32_t* veh_idx) {
+    for (int w = 0; w < S->num_worlds; ++w)
+        for (int a = S->agent_off[w]; a < S->agent_off[w + 1]; ++a)
+            observe_full_agent(P, S, w, F, I, a, obs ? obs + (size_t)a * OR_FULL_OBS : NULL, n_road, n_veh,
+                               road_idx, veh_idx);
+}
+
 /* ------------------------------------------------------------------ events and rewards */
 static void events_agent(const or_params* P, const or_scene* S, int w, double* F, int32_t* I, int a,
                          const double prev[2], int flags, double* reward, uint32_t* ev, double* drac_out,

@@ -164,6 +164,31 @@ void or_reset(const or_params* P, const or_scene* S, double* F, int32_t* I, cons
 void or_place_agent(const or_params* P, double* F, int32_t* I, int a, double x, double y, double psi,
                     double v0, double gx, double gy, int precip, int surface);
 
+/* --- the paper's full observation (App. D, 1,929 values per agent) --------------------
+ * ego (11):    goal in the body frame / 100 (2), sin and cos of the goal bearing, goal
+ *              distance / 100, body-frame velocity / 10 (2), then the weather token
+ *              (precip / 3, one-hot asphalt, concrete, gravel) in place of Eq. weather_obs
+ * road (350 x 5): midpoints of the world's road segments (App. C segment rule) within
+ *              10 m of the CoM, in ascending segment index (polyline order), first 350:
+ *              body-frame offset / 10 (2), polyline type / 20, body-frame unit direction (2)
+ * vehicles (24 x 7): the 24 nearest alive other agents (ascending squared distance,
+ *              ties lowest index): body-frame offset / 100 (2), length / 100, width / 100,
+ *              relative heading / pi, speed / 10, swept-circle TTC / 10
+ * Padding slots are zero; n_road / n_veh give the number of filled slots (a prefix). */
+#define OR_FULL_EGO 11
+#define OR_FULL_KR 350
+#define OR_FULL_PT 5
+#define OR_FULL_KV 24
+#define OR_FULL_NB 7
+#define OR_FULL_OBS (OR_FULL_EGO + OR_FULL_KR * OR_FULL_PT + OR_FULL_KV * OR_FULL_NB) /* 1929 */
+#define OR_FULL_RADIUS 10.0
+
+/* obs [A][OR_FULL_OBS]; n_road, n_veh [A]; road_idx [A][OR_FULL_KR] (segment start point,
+ * global index) and veh_idx [A][OR_FULL_KV] (agent index), -1 padded; any may be NULL.
+ * Parked / inactive agents get zeros and counts 0. */
+void or_observe_full(const or_params* P, const or_scene* S, const double* F, const int32_t* I, double* obs,
+                     int32_t* n_road, int32_t* n_veh, int32_t* road_idx, int32_t* veh_idx);
+
 /* --- pieces exported for the pins ------------------------------------------------- */
 /* 2-D SAT of two footprints; returns penetration depth (0 when separated), normal i->j. */
 double or_sat(const or_params* P, const double ci[2], const double hi[2], const double cj[2],

@@ -1,0 +1,103 @@
+"""Pins of the late-fusion actor-critic oracle (App. E).
+
+The masked max-pool is pinned by the properties that define a set encoder:
+invariance to the order of the valid slots, to the contents of padded slots and
+to a duplicated slot; the whole network by a second formulation written as
+plain loops over the valid slots only (no padding, no -inf), including empty
+groups; and the actor / critic split by their independence.
+"""
+import numpy as np
+import pytest
+
+from oracle import lf as LF
+
+
+def params(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    P = []
+    for net in ("actor", "critic"):
+        for _, o, i in LF.net_layers(net):
+            P.append(rng.normal(0, scale / np.sqrt(i), o * i))
+            P.append(rng.normal(0, 0.1, o))
+    P.append(np.full(3, -0.5))
+    return np.concatenate(P)
+
+
+def observations(seed, A, n_road, n_veh):
+    rng = np.random.default_rng(seed)
+    obs = rng.normal(0, 1, (A, LF.OBS))
+    for a in range(A):   # padding slots are zero, as the observation writes them
+        obs[a, LF.ROAD0 + n_road[a] * LF.PT:LF.VEH0] = 0
+        obs[a, LF.VEH0 + n_veh[a] * LF.NB:] = 0
+    return obs
+
+
+def test_parameter_count():
+    per = lambda out: (11 * 64 + 64 + 64 * 64 + 64 + 5 * 96 + 96 + 96 * 96 + 96 + 7 * 96 + 96 + 96 * 96 + 96
+                       + 256 * 128 + 128 + 128 * 64 + 64 + 64 * out + out)
+    assert LF.num_params() == per(3) + per(1) + 3
+
+
+def test_loop_formulation_agrees_including_empty_groups():
+    p = params(1)
+    n_road = np.array([0, 1, 3, 7])
+    n_veh = np.array([2, 0, 1, 24])
+    obs = observations(2, 4, n_road, n_veh)
+    mean, value = LF.forward(p, obs, n_road, n_veh)
+    for a in range(4):
+        m, v = LF.forward_loops(p, obs[a], int(n_road[a]), int(n_veh[a]))
+        np.testing.assert_allclose(mean[a], m, rtol=1e-12, atol=1e-12)
+        assert abs(value[a] - v) < 1e-12
+
+
+def test_set_invariances():
+    p = params(3)
+    rng = np.random.default_rng(4)
+    n_road = np.array([40, 350, 5])
+    n_veh = np.array([15, 3, 24])
+    obs = observations(5, 3, n_road, n_veh)
+    mean, value = LF.forward(p, obs, n_road, n_veh)
+    # order of the valid slots
+    o2 = obs.copy()
+    for a in range(3):
+        r = o2[a, LF.ROAD0:LF.VEH0].reshape(LF.KR, LF.PT)
+        r[:n_road[a]] = r[rng.permutation(n_road[a])]
+        v = o2[a, LF.VEH0:].reshape(LF.KV, LF.NB)
+        v[:n_veh[a]] = v[rng.permutation(n_veh[a])]
+    m2, v2 = LF.forward(p, o2, n_road, n_veh)
+    np.testing.assert_allclose(m2, mean, atol=1e-12)
+    np.testing.assert_allclose(v2, value, atol=1e-12)
+    # contents of the padded slots
+    o3 = obs.copy()
+    for a in range(3):
+        o3[a, LF.ROAD0 + n_road[a] * LF.PT:LF.VEH0] = rng.normal(0, 50, (LF.KR - n_road[a]) * LF.PT)
+        o3[a, LF.VEH0 + n_veh[a] * LF.NB:] = rng.normal(0, 50, (LF.KV - n_veh[a]) * LF.NB)
+    m3, v3 = LF.forward(p, o3, n_road, n_veh)
+    np.testing.assert_allclose(m3, mean, atol=1e-12)
+    np.testing.assert_allclose(v3, value, atol=1e-12)
+    # a duplicated valid slot (max is idempotent)
+    o4 = obs.copy()
+    o4[2, LF.ROAD0 + 5 * LF.PT:LF.ROAD0 + 6 * LF.PT] = o4[2, LF.ROAD0:LF.ROAD0 + LF.PT]
+    n4 = n_road.copy(); n4[2] = 6
+    m4, v4 = LF.forward(p, o4, n4, n_veh)
+    np.testing.assert_allclose(m4, mean, atol=1e-12)
+    # ... while a new, different slot does change the output
+    o4[2, LF.ROAD0 + 5 * LF.PT:LF.ROAD0 + 6 * LF.PT] = [3.0, -3.0, 1.0, 0.0, 1.0]
+    m5, _ = LF.forward(p, o4, n4, n_veh)
+    assert np.abs(m5[2] - mean[2]).max() > 1e-6
+
+
+def test_actor_and_critic_are_independent():
+    p = params(6)
+    n_road, n_veh = np.array([10, 0]), np.array([4, 1])
+    obs = observations(7, 2, n_road, n_veh)
+    mean, value = LF.forward(p, obs, n_road, n_veh)
+    half = sum(o * i + o for _, o, i in LF.net_layers("actor"))
+    pa, pc = p.copy(), p.copy()
+    pa[:half] += 0.3           # actor changed
+    pc[half:-3] += 0.3         # critic changed
+    ma, va = LF.forward(pa, obs, n_road, n_veh)
+    mc, vc = LF.forward(pc, obs, n_road, n_veh)
+    np.testing.assert_array_equal(va, value)
+    np.testing.assert_array_equal(mc, mean)
+    assert np.abs(ma - mean).max() > 1e-3 and np.abs(vc - value).max() > 1e-3
