@@ -214,6 +214,44 @@ sf_status sf_get_obs(sf_handle h, float* d_obs, float* d_reward, uint8_t* d_done
 sf_status sf_get_indices(sf_handle h, int32_t* d_lane_seg, int32_t* d_knn_points, int32_t* d_knn_agents,
                          float* d_drac);
 
+/* The paper's full observation (SceneFactory App. D), 1,929 values per agent,
+ * computed from the current state (after any sf_step / sf_reset / placement):
+ *   [0, 11)       ego: goal in the body frame / 100 (x, y), sin and cos of the
+ *                 goal bearing, goal distance / 100, body-frame velocity / 10
+ *                 (x, y), then the weather token of Eq. weather_obs in this
+ *                 library's weather cells: precip / 3, one-hot asphalt,
+ *                 concrete, gravel;
+ *   [11, 1761)    road context, 350 slots x 5: the midpoints of the world's
+ *                 road segments (App. C: consecutive points of a polyline at
+ *                 most 3 m apart, both inside the 200 m box) within 10 m of the
+ *                 agent's centre, in ascending segment index (polyline order,
+ *                 then point order), the first 350; per slot the body-frame
+ *                 offset / 10 (x, y), polyline type / 20 and the body-frame
+ *                 unit direction (x, y);
+ *   [1761, 1929)  vehicle context, 24 slots x 7: the 24 nearest alive other
+ *                 agents of the world (squared distance, ties to the lower
+ *                 index); per slot the body-frame offset / 100 (x, y), length
+ *                 / 100, width / 100, relative heading / pi, speed / 10 and the
+ *                 swept three-circle time to collision / 10.
+ * Slots beyond the filled ones are zero, and a parked agent's row is all zeros.
+ * d_obs [A][SF_FULL_OBS_DIM] float32 (required); d_n_road, d_n_veh [A] int32
+ * receive the number of filled road / vehicle slots (the slots are a prefix;
+ * these counts are the masks of the policy's max-pool); d_road_idx
+ * [A][SF_FULL_KR] and d_veh_idx [A][SF_FULL_KV] int32 receive the global
+ * start-point index of each selected segment and the global index of each
+ * selected agent, -1 past the end.  The optional pointers may be NULL.  All
+ * buffers are caller-owned device memory.  Asynchronous on the handle's stream.
+ * Errors: SF_ERR_STATE (no roads), SF_ERR_INVALID_ARG (NULL d_obs),
+ * SF_ERR_CUDA. */
+#define SF_FULL_EGO 11
+#define SF_FULL_KR 350
+#define SF_FULL_PT 5
+#define SF_FULL_KV 24
+#define SF_FULL_NB 7
+#define SF_FULL_OBS_DIM (SF_FULL_EGO + SF_FULL_KR * SF_FULL_PT + SF_FULL_KV * SF_FULL_NB) /* 1929 */
+sf_status sf_observe_full(sf_handle h, float* d_obs, int32_t* d_n_road, int32_t* d_n_veh, int32_t* d_road_idx,
+                          int32_t* d_veh_idx);
+
 /* Device pointers of the library-owned outputs (zero-copy). */
 sf_status sf_output_ptrs(sf_handle h, sf_outputs* out);
 
@@ -402,6 +440,58 @@ sf_status sf_step_surrogate(sf_handle h, sf_surrogate_handle s, const float* d_a
 /* Synchronous: the largest audit error since the last call [m] and the number
  * of agent-steps that used the surrogate; both counters are reset. */
 sf_status sf_surrogate_audit(sf_handle h, float* h_max_err, unsigned long long* h_used);
+
+/* ------------------------------------------------------------------------
+ * The paper's late-fusion actor-critic network (SceneFactory App. E) on the
+ * full observation (sf_observe_full).  Two networks without shared weights,
+ * the actor and the critic, each:
+ *   ego encoder      11 -> 64 -> 64 (ELU) on observation values [0, 11)
+ *   road encoder     5 -> 96 -> 96 (ELU) on each road slot, then a masked
+ *                    max-pool over the first n_road slots
+ *   vehicle encoder  7 -> 96 -> 96 (ELU) on each vehicle slot, masked
+ *                    max-pool over the first n_veh slots
+ *   trunk            [ego | road | vehicles] 256 -> 128 -> 64 (ELU)
+ *   head             actor: 3 action means; critic: 1 value (linear)
+ * The masked max-pool is the paper's "fill padding with -inf, then max"; a
+ * group without a filled slot pools to zeros.  Weights and activations are
+ * bf16 on the tensor cores with fp32 accumulation; biases are fp32.
+ * Parameters (fp32, host) are one flat vector: for the actor then the critic,
+ * for each layer in the order ego0, ego1, road0, road1, veh0, veh1, trunk0,
+ * trunk1, head, the weight [out][in] row-major then the bias [out]; then the
+ * 3 log standard deviations of the diagonal Gaussian policy (kept, not used by
+ * the forward pass).  sf_lf_num_params() gives the length.
+ * ---------------------------------------------------------------------- */
+typedef struct sf_lf* sf_lf_handle;
+
+size_t sf_lf_num_params(void);
+
+/* A network with all parameters zero on cuda_stream (NULL = legacy default
+ * stream).  Errors: SF_ERR_INVALID_ARG (NULL out), SF_ERR_CUDA. */
+sf_status sf_lf_create(void* cuda_stream, sf_lf_handle* out);
+sf_status sf_lf_destroy(sf_lf_handle m);
+const char* sf_lf_last_error(sf_lf_handle m);
+
+/* Set / read every parameter (h_params has n == sf_lf_num_params() floats;
+ * set rejects non-finite values).  Synchronous.  Errors: SF_ERR_INVALID_ARG. */
+sf_status sf_lf_set_params(sf_lf_handle m, const float* h_params, size_t n);
+sf_status sf_lf_get_params(sf_lf_handle m, float* h_params, size_t n);
+
+/* Forward pass of both networks on num_agents observation rows:
+ * d_obs [num_agents][SF_FULL_OBS_DIM] float32, d_n_road / d_n_veh [num_agents]
+ * int32 filled-slot counts (clamped to 0..350 / 0..24), all as written by
+ * sf_observe_full; d_mean [num_agents][3] receives the actor's action means,
+ * d_value [num_agents] (may be NULL) the critic's values, d_embed (may be NULL)
+ * [num_agents][512] the trunk inputs of the actor (256) then the critic (256).
+ * Caller-owned device buffers.  The network keeps its activation buffers and
+ * grows them (cudaMalloc, after synchronising its stream) when num_agents
+ * exceeds every earlier call's.  Asynchronous on the network's stream.
+ * Errors: SF_ERR_INVALID_ARG, SF_ERR_OOM, SF_ERR_CUDA. */
+sf_status sf_lf_forward(sf_lf_handle m, const float* d_obs, const int32_t* d_n_road, const int32_t* d_n_veh,
+                        int num_agents, float* d_mean, float* d_value, float* d_embed);
+
+/* Wait for the network's stream; SF_ERR_TIMEOUT if a bounded tensor-core wait
+ * gave up since the last sync. */
+sf_status sf_lf_sync(sf_lf_handle m);
 
 /* Number of agents and worlds of the loaded roads (0 before sf_load_roads). */
 int32_t sf_num_agents(sf_handle h);

@@ -299,6 +299,8 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     std::vector<DevGrid> grid(W);
     std::vector<int32_t> pbeg(NP);
     std::vector<float> arcl(NP);
+    std::vector<float4> mid(NP);       // segment k -> k+1: midpoint (double, rounded) and unit direction
+    std::vector<uint8_t> ptype(NP);
     std::vector<unsigned char> blob;   // every world's road blob, 16-byte aligned sections
     auto in_box = [](double x, double y) { return std::fabs(x) <= 100.0 && std::fabs(y) <= 100.0; };
     for (int w = 0; w < W; ++w) {
@@ -334,6 +336,14 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
                 if (is_lane_type(t)) m |= sfk::kPtLane;
                 if (is_edge_type(t)) m |= sfk::kPtEdge;
                 pmeta[k] = m;
+                ptype[k] = (uint8_t)t;
+                mid[k] = make_float4(INFINITY, 0.f, 0.f, 0.f);
+                if (m & sfk::kPtSegNext) {
+                    const double ax = r->px[k], ay = r->py[k], bx = r->px[k + 1], by = r->py[k + 1];
+                    const double n = std::sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+                    mid[k] = make_float4((float)(0.5 * (ax + bx)), (float)(0.5 * (ay + by)),
+                                         n > 0 ? (float)((bx - ax) / n) : 0.f, n > 0 ? (float)((by - ay) / n) : 0.f);
+                }
                 pend[k] = k1;
                 pbeg[k] = k0;
                 arcl[k] = (float)arc[k - k0];
@@ -439,7 +449,10 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     DevGrid* dgrid; unsigned char* dblob;
     SF_ALLOC(dgrid, DevGrid, (size_t)W);
     SF_ALLOC(dblob, unsigned char, blob.size() + 16);
-    h->rd = DevRoads{dworld, dcand, dpt, dpend, darc, dcands, dgrid, dblob};
+    float4* dmid; uint8_t* dptype;
+    SF_ALLOC(dmid, float4, (size_t)NP + 1);
+    SF_ALLOC(dptype, uint8_t, (size_t)NP + 1);
+    h->rd = DevRoads{dworld, dcand, dpt, dpend, darc, dcands, dgrid, dblob, dmid, dptype};
     float *obs, *reward, *drac; uint8_t* done; uint32_t* events; int32_t *lane_seg, *knn_pts, *knn_agents;
     unsigned int* err_word; float* hint;
     SF_ALLOC(obs, float, Aa * SF_OBS_DIM);
@@ -499,6 +512,8 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     up(dcands, cands.data(), cands.size() * sizeof(int32_t));
     up(dgrid, grid.data(), grid.size() * sizeof(DevGrid));
     up(dblob, blob.data(), blob.size());
+    up(dmid, mid.data(), mid.size() * sizeof(float4));
+    up(dptype, ptype.data(), ptype.size());
     for (float4* p : {pos, quat, vel, angv, spin, goal}) zero(p, Aa * sizeof(float4));
     zero(peak, Aa * 4); zero(step, Aa * 4); zero(episode, Aa * 4);
     up(meta, meta_h.data(), Aa * 4);
@@ -668,6 +683,25 @@ sf_status sf_get_indices(sf_handle h, int32_t* d_lane_seg, int32_t* d_knn_points
         SF_CUDA(h, cudaMemcpyAsync(d_knn_agents, h->out.knn_agents, A * SF_K_AGENTS * 4, cudaMemcpyDeviceToDevice,
                                    h->stream));
     if (d_drac) SF_CUDA(h, cudaMemcpyAsync(d_drac, h->out.drac, A * 4, cudaMemcpyDeviceToDevice, h->stream));
+    return SF_OK;
+}
+
+sf_status sf_observe_full(sf_handle h, float* d_obs, int32_t* d_n_road, int32_t* d_n_veh, int32_t* d_road_idx,
+                          int32_t* d_veh_idx) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_observe_full: no roads loaded");
+    if (!d_obs) return fail(h, SF_ERR_INVALID_ARG, "sf_observe_full: NULL observation buffer");
+    FullObsArgs f{};
+    f.st = h->st;
+    f.rd = h->rd;
+    f.agent_world = h->sc.agent_world;
+    f.num_agents = h->A;
+    f.obs = d_obs;
+    f.n_road = d_n_road;
+    f.n_veh = d_n_veh;
+    f.road_idx = d_road_idx;
+    f.veh_idx = d_veh_idx;
+    SF_CUDA(h, sf_launch_full_obs(f, h->stream));
     return SF_OK;
 }
 

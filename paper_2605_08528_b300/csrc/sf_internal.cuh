@@ -79,6 +79,11 @@ constexpr int kMaxAgents = 32;
 constexpr int kK = 8, kL = 32;
 constexpr int kObsEgo = 16, kObsNbr = 10, kObsPt = 7;
 constexpr int kObsDim = kObsEgo + kK * kObsNbr + kL * kObsPt;  // 320
+// the paper's full observation (App. D): ego 11, 350 road slots x 5, 24 vehicle slots x 7
+constexpr int kFullEgo = 11, kFullKR = 350, kFullPt = 5, kFullKV = 24, kFullNb = 7;
+constexpr int kFullRoad0 = kFullEgo, kFullVeh0 = kFullEgo + kFullKR * kFullPt;
+constexpr int kFullObs = kFullVeh0 + kFullKV * kFullNb;         // 1929
+constexpr float kFullR2 = 100.0f;                               // road radius 10 m, squared
 
 // point meta bits (input-order store)
 constexpr uint32_t kPtTypeMask = 0xFFu;
@@ -146,6 +151,9 @@ struct DevRoads {
     const int32_t* cands;       // spawn candidate point indices
     const DevGrid* grid;        // per world
     const unsigned char* blob;  // every world's road blob
+    const float4* mid;          // per point k: midpoint and unit direction of segment k -> k+1
+                                // (App. C rule), x = +inf when k starts no segment
+    const uint8_t* ptype;       // per point: Waymo type of its polyline
 };
 
 struct DevOutputs {
@@ -213,7 +221,21 @@ struct WorldArgs {
 // surrogate feature / target layout (dynamics surrogate of the step)
 constexpr int kSurrIn = 30, kSurrInLd = 32, kSurrOut = 16;
 
+// the full observation (App. D) of every agent from the current state
+struct FullObsArgs {
+    DevState st;
+    DevRoads rd;
+    const int32_t* agent_world;  // [A]
+    int num_agents;
+    float* obs;                  // [A][kFullObs]
+    int32_t* n_road;             // [A] or null
+    int32_t* n_veh;              // [A] or null
+    int32_t* road_idx;           // [A][kFullKR] or null
+    int32_t* veh_idx;            // [A][kFullKV] or null
+};
+
 // launch wrappers (sf_world.cu)
+cudaError_t sf_launch_full_obs(const FullObsArgs& f, cudaStream_t s);
 cudaError_t sf_launch_world(int mode, const WorldArgs& a, int warps_per_block, cudaStream_t s);
 // one control step as four kernels (physics, road queries, events, fix-up); nwq warps per query block
 cudaError_t sf_launch_step_split(const WorldArgs& a, int nwq, cudaStream_t s);

@@ -1,0 +1,589 @@
+// sf_lf.cu -- the paper's late-fusion actor-critic network (SceneFactory App. E)
+// on the sm_103a tensor cores.
+//
+// Each of the two networks (actor, critic; no shared weights) encodes the
+// 1,929-value observation (App. D) by groups:
+//   ego      11 -> 64 -> 64 (ELU)                          tc GEMMs (sf_gemm.cu)
+//   road     5 -> 96 -> 96 (ELU) per slot, masked max-pool  lf_set_kernel below
+//   vehicles 7 -> 96 -> 96 (ELU) per slot, masked max-pool  lf_set_kernel below
+//   trunk    [ego | road | vehicles] 256 -> 128 -> 64 (ELU), then the actor's
+//            3 action means or the critic's value (linear)    tc GEMMs
+// The max-pool is masked by the group's count (the observation fills a prefix
+// of the slots); an empty group pools to zeros.
+//
+// lf_set_kernel (one persistent CTA of 8 warps per SM) runs both networks'
+// encoders of one group over work items of 32 consecutive agents.  An item's
+// valid slots are concatenated (no padding) into tiles of 128 rows:
+//   gather   rows -> bf16 A1 [128 slots][16 features] (swizzled smem), the
+//            next tile's global loads issued before this tile's epilogues
+//   MMA 1    D1[128 slots][192] = A1 . W1^T             (both nets, K = 16)
+//   epi 1    bias + ELU -> bf16 H1[net][128 slots][96]  (K-major for MMA 2)
+//   MMA 2    D2[net][128 features][128 slots] = W2 . H1^T  (K = 96; features
+//            96..127 are zero rows of the weight image)
+//   epi 2    each thread owns one feature and walks the tile's slot columns:
+//            a running max, flushed to the item's pool (shared atomicMax on
+//            order-preserving integer keys) at every agent boundary
+// after the item: pooled max + bias -> ELU -> bf16 into the trunk inputs.
+// ELU is monotone and the bias is constant per feature, so max-then-activate
+// equals the paper's activate-then-max.  Every mbarrier wait is bounded (1 s).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sf.h"
+#include "sf_gemm.cuh"
+#include "sf_tc.cuh"
+
+namespace {
+
+using namespace sftc;
+
+constexpr int kEgo = 11, kKR = 350, kPT = 5, kKV = 24, kNB = 7;
+constexpr int kObs = kEgo + kKR * kPT + kKV * kNB;   // 1929
+constexpr int kRoad0 = kEgo, kVeh0 = kEgo + kKR * kPT;
+constexpr int kHid = 96;                             // set-encoder width
+constexpr int kG = 32;                               // agents per work item
+constexpr int kThreads = 256;
+constexpr unsigned kLfTimeout = 4u;                  // error-word bit: a bounded wait gave up
+
+// shared memory (offsets from a 1024-byte aligned base)
+constexpr int kOffW1 = 0;                           // [192 rows][128 B]: layer 1 of both nets, K 0..15 used
+constexpr int kW2Net = 2 * 128 * 128;               // per net: 2 K-atoms of [128 rows][128 B]
+constexpr int kOffW2 = kOffW1 + 192 * 128;          // 24576
+constexpr int kImgBytes = kOffW2 + 2 * kW2Net;      // 90112: the weight image copied from global
+constexpr int kOffA1 = kImgBytes;                   // [128 slots][128 B]
+constexpr int kH1Net = 2 * 128 * 128;               // per net: 2 K-atoms of [128 slots][128 B]
+constexpr int kOffH1 = kOffA1 + 128 * 128;          // 106496
+constexpr int kOffPool = kOffH1 + 2 * kH1Net;       // 172032: u32 [kG][192]
+constexpr int kOffMisc = kOffPool + kG * 192 * 4;   // 196608
+constexpr int kMiscBytes = 2048;
+constexpr int kSmemBytes = kOffMisc + kMiscBytes + 1024;
+
+struct SetArgs {
+    const float* obs;          // [A][ld]
+    int ld, off, F, K;         // row stride, group offset, features per slot, slots
+    const int32_t* count;      // [A] filled slots
+    int num_agents;
+    const uint4* wimg;         // kImgBytes: W1 and W2 images (bf16, swizzled)
+    const float* b1;           // [192] layer-1 bias (actor 96, critic 96)
+    const float* b2;           // [192] layer-2 bias
+    __nv_bfloat16* xa;         // [A][ldx] actor trunk input
+    __nv_bfloat16* xc;         // [A][ldx] critic trunk input
+    int ldx, xoff;             // columns [xoff, xoff + 96) receive the pooled embedding
+    unsigned* err;
+};
+
+__device__ __forceinline__ uint32_t fkey(float f) {   // order-preserving float -> u32 (0 is below every key)
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float funkey(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+__device__ __forceinline__ float elu(float x) { return x > 0.f ? x : __expf(x) - 1.f; }
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// the agent (item-local) whose rows contain item row r: last s with rs[s] <= r
+__device__ __forceinline__ int agent_of_row(const int* rs, int r) {
+    int lo = 0, hi = kG - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rs[mid] <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// features of item row (tile * 128 + row) into v[0..7] (zeros past F or past the item)
+__device__ __forceinline__ void gather_row(const SetArgs& a, const int* rs, int a0, int total, int tile, int row,
+                                           float (&v)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = 0.f;
+    const int r = tile * 128 + row;
+    if (r >= total) return;
+    const int al = agent_of_row(rs, r);
+    const float* src = a.obs + (size_t)(a0 + al) * a.ld + a.off + (size_t)(r - rs[al]) * a.F;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (i < a.F) v[i] = __ldg(src + i);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) lf_set_kernel(const SetArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                         ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(sm);
+    uint32_t* pool = reinterpret_cast<uint32_t*>(sm + kOffPool);
+    int* rs = reinterpret_cast<int*>(sm + kOffMisc);                       // [kG + 1] item row starts
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kOffMisc + 192);     // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffMisc + 208);
+    float* sb1 = reinterpret_cast<float*>(sm + kOffMisc + 256);           // [192]
+    float* sb2 = reinterpret_cast<float*>(sm + kOffMisc + 1024);          // [192]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // ---- weights, biases, pool, barriers, TMEM
+    for (int i = tid; i < kImgBytes / 16; i += kThreads) reinterpret_cast<uint4*>(sm)[i] = __ldg(a.wimg + i);
+    for (int i = tid; i < 192; i += kThreads) { sb1[i] = __ldg(a.b1 + i); sb2[i] = __ldg(a.b2 + i); }
+    for (int i = tid; i < kG * 192; i += kThreads) pool[i] = 0u;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t kIdesc1 = instr_desc(128, 192), kIdesc2 = instr_desc(128, 128);
+    uint32_t phase1 = 0, phase2 = 0;
+    bool ok = true;
+    const int q = warp & 3, net = warp >> 2;                // TMEM lane quarter, network of this warp
+    const int num_items = (a.num_agents + kG - 1) / kG;
+
+    for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
+        const int a0 = item * kG;
+        const int na = min(kG, a.num_agents - a0);
+        if (warp == 0) {
+            int n = lane < na ? min(max(__ldg(a.count + a0 + lane), 0), a.K) : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xFFFFFFFFu, n, o);
+                if (lane >= o) n += t;
+            }
+            rs[lane + 1] = n;
+            if (lane == 0) rs[0] = 0;
+        }
+        __syncthreads();
+        const int total = rs[kG];
+        const int ntiles = (total + 127) / 128;
+        float v8[8];
+        gather_row(a, rs, a0, total, 0, tid >> 1, v8);
+        for (int t = 0; t < ntiles; ++t) {
+            // ---- A1: the tile's 128 slots x 16 features (bf16), two threads per row
+            {
+                const int row = tid >> 1, half = tid & 1;
+                uint4 w = make_uint4(0u, 0u, 0u, 0u);
+                if (half == 0) w = make_uint4(pack_bf16(v8[0], v8[1]), pack_bf16(v8[2], v8[3]), pack_bf16(v8[4], v8[5]),
+                                              pack_bf16(v8[6], v8[7]));
+                *reinterpret_cast<uint4*>(sm + kOffA1 + swz128(row, half)) = w;
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc_after();
+                umma_bf16(tmem, smem_desc(sbase + kOffA1), smem_desc(sbase + kOffW1), kIdesc1, 0u);
+                umma_commit(&bar[0]);
+            }
+            if (t + 1 < ntiles) gather_row(a, rs, a0, total, t + 1, tid >> 1, v8);   // in flight meanwhile
+
+            // ---- epilogue 1: bias + ELU, bf16 rows of H1 (this warp: its 32 slots, its net's 96 columns)
+            ok = __syncthreads_and(mbar_wait(&bar[0], phase1, a.err, kLfTimeout) ? 1 : 0) != 0;
+            phase1 ^= 1u;
+            if (!ok) break;
+            tc_after();
+            {
+                const int row = 32 * q + lane;
+                unsigned char* h1 = sm + kOffH1 + net * kH1Net;
+#pragma unroll 1
+                for (int c = 0; c < 3; ++c) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kHid * net + 32 * c), v);
+                    const float* b = sb1 + kHid * net + 32 * c;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {   // 8 columns -> one 16-byte chunk of the K-major row
+                        uint32_t p[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            p[e] = pack_bf16(elu(v[8 * m + 2 * e] + b[8 * m + 2 * e]),
+                                             elu(v[8 * m + 2 * e + 1] + b[8 * m + 2 * e + 1]));
+                        const int j = 4 * c + m;                 // chunk of the 96-wide row
+                        *reinterpret_cast<uint4*>(h1 + (j >> 3) * 16384 + swz128(row, j & 7)) =
+                            make_uint4(p[0], p[1], p[2], p[3]);
+                    }
+                }
+            }
+            fence_async_smem();
+            tc_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_after();
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int kk = 0; kk < 6; ++kk) {
+                        const uint64_t ad = smem_desc(sbase + kOffW2 + h * kW2Net + (kk >> 2) * 16384) + 2 * (kk & 3);
+                        const uint64_t bd = smem_desc(sbase + kOffH1 + h * kH1Net + (kk >> 2) * 16384) + 2 * (kk & 3);
+                        umma_bf16(tmem + 256 + 128 * h, ad, bd, kIdesc2, kk > 0 ? 1u : 0u);
+                    }
+                umma_commit(&bar[1]);
+            }
+
+            // ---- epilogue 2: per feature, running max over the tile's slot columns
+            ok = __syncthreads_and(mbar_wait(&bar[1], phase2, a.err, kLfTimeout) ? 1 : 0) != 0;
+            phase2 ^= 1u;
+            if (!ok) break;
+            tc_after();
+            if (q < 3) {
+                const int f = 32 * q + lane;
+                const int r0 = 128 * t;
+                int s = agent_of_row(rs, r0);            // agent holding the tile's first row
+                int bnd = rs[s + 1];                     // row where it ends
+                float m = -INFINITY;
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(256 + 128 * net + 32 * c), v);
+                    const int base = r0 + 32 * c;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        if (base + i == bnd) {           // warp-uniform: every lane walks the same rows
+                            if (s < kG) atomicMax(&pool[s * 192 + kHid * net + f], fkey(m));
+                            while (s < kG && rs[s + 1] <= base + i) ++s;
+                            bnd = s < kG ? rs[s + 1] : 0x7FFFFFFF;
+                            m = -INFINITY;
+                        }
+                        m = fmaxf(m, v[i]);
+                    }
+                }
+                if (s < kG) atomicMax(&pool[s * 192 + kHid * net + f], fkey(m));   // continues in the next tile
+            }
+            tc_before();
+            __syncthreads();
+            tc_after();
+        }
+        if (!ok) break;
+        __syncthreads();
+        // ---- the item's pooled embeddings: + bias, ELU, bf16 into the trunk inputs
+        for (int i = tid; i < na * 192; i += kThreads) {
+            const int al = i / 192, col = i - al * 192;
+            const uint32_t k = pool[i];
+            pool[i] = 0u;
+            const float y = k ? elu(funkey(k) + sb2[col]) : 0.f;
+            __nv_bfloat16* X = col < kHid ? a.xa : a.xc;
+            X[(size_t)(a0 + al) * a.ldx + a.xoff + (col % kHid)] = __float2bfloat16_rn(y);
+        }
+        __syncthreads();
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+// ego features -> bf16 [A][16] (11 used)
+__global__ void lf_ego_kernel(const float* __restrict__ obs, int ld, int A, __nv_bfloat16* __restrict__ x) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A * 16) return;
+    const int a = i >> 4, j = i & 15;
+    x[i] = __float2bfloat16_rn(j < kEgo ? obs[(size_t)a * ld + j] : 0.f);
+}
+
+// bf16 trunk inputs of both nets -> fp32 [A][512]
+__global__ void lf_embed_kernel(const __nv_bfloat16* __restrict__ xa, const __nv_bfloat16* __restrict__ xc, int A,
+                                float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A * 512) return;
+    const int a = i >> 9, j = i & 511;
+    out[i] = __bfloat162float(j < 256 ? xa[(size_t)a * 256 + j] : xc[(size_t)a * 256 + j - 256]);
+}
+
+// ------------------------------------------------------------------ host side
+struct Layer {   // one dense layer of a net in the oracle's parameter order
+    int out, in;
+};
+const Layer kLayers[9] = {{64, 11}, {64, 64}, {96, 5}, {96, 96}, {96, 7}, {96, 96}, {128, 256}, {64, 128}, {0, 64}};
+enum { L_EGO0, L_EGO1, L_ROAD0, L_ROAD1, L_VEH0, L_VEH1, L_TRUNK0, L_TRUNK1, L_HEAD };
+
+size_t net_params(int head) {
+    size_t n = 0;
+    for (int l = 0; l < 9; ++l) {
+        const int o = l == L_HEAD ? head : kLayers[l].out;
+        n += (size_t)o * kLayers[l].in + o;
+    }
+    return n;
+}
+size_t total_params() { return net_params(3) + net_params(1) + 3; }
+
+uint16_t to_bf16(float f) {   // round to nearest even
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    if ((b & 0x7F800000u) == 0x7F800000u) return (uint16_t)(b >> 16);
+    b += 0x7FFFu + ((b >> 16) & 1u);
+    return (uint16_t)(b >> 16);
+}
+
+}  // namespace
+
+struct sf_lf {
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::vector<float> params;           // oracle layout, fp32
+    std::vector<void*> allocs;           // parameters and the error word
+    std::vector<void*> acts;             // activation buffers (grown on demand)
+    // device parameters
+    uint4* img[2] = {nullptr, nullptr};  // road, vehicles: kImgBytes each
+    float* sb[2] = {nullptr, nullptr};   // road, vehicles: b1[192], b2[192]
+    __nv_bfloat16* w[2][6] = {};         // per net: ego0 [64][16], ego1, trunk0, trunk1, head [out][64] (bf16)
+    float* b[2][6] = {};                 // their biases
+    // activations (grown on demand)
+    int cap = 0;
+    __nv_bfloat16 *xego = nullptr, *he1[2] = {nullptr, nullptr}, *x[2] = {nullptr, nullptr};
+    __nv_bfloat16 *t1 = nullptr, *t2 = nullptr;
+    unsigned* d_err = nullptr;
+};
+
+namespace {
+
+sf_status lfail(sf_lf* m, sf_status s, const std::string& msg) {
+    if (m) m->err = msg;
+    return s;
+}
+
+template <class T>
+bool lalloc(sf_lf* m, T** p, size_t count, bool act = false) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess) return false;
+    (act ? m->acts : m->allocs).push_back(q);
+    *p = static_cast<T*>(q);
+    return true;
+}
+
+// swizzled bf16 image of a [rows][k_used] weight block as K-major 128-byte atoms of 64 columns
+void put_swizzled(std::vector<uint16_t>& img, size_t base, int rows_total, int r, int k, float v) {
+    const int atom = k / 64, kk = k % 64;
+    const size_t off = base + (size_t)atom * rows_total * 128 + (size_t)r * 128 +
+                       (size_t)((((kk / 8) ^ (r & 7)) * 16) + (kk % 8) * 2);
+    img[off / 2] = to_bf16(v);
+}
+
+sf_status upload(sf_lf* m) {
+    const float* P = m->params.data();
+    size_t k = 0;
+    std::vector<const float*> W[2], B[2];
+    for (int n = 0; n < 2; ++n)
+        for (int l = 0; l < 9; ++l) {
+            const int o = l == L_HEAD ? (n == 0 ? 3 : 1) : kLayers[l].out, i = kLayers[l].in;
+            W[n].push_back(P + k); k += (size_t)o * i;
+            B[n].push_back(P + k); k += o;
+        }
+    cudaError_t e = cudaSuccess;
+    // set-encoder images: group g (0 road, 1 vehicles) uses layers (ROAD0, ROAD1) / (VEH0, VEH1)
+    for (int g = 0; g < 2; ++g) {
+        const int l0 = g == 0 ? L_ROAD0 : L_VEH0, l1 = l0 + 1, F = kLayers[l0].in;
+        std::vector<uint16_t> img(kImgBytes / 2, 0);
+        for (int n = 0; n < 2; ++n)
+            for (int j = 0; j < kHid; ++j) {
+                for (int f = 0; f < F; ++f) put_swizzled(img, kOffW1, 192, n * kHid + j, f, W[n][l0][j * F + f]);
+                for (int f = 0; f < kHid; ++f)
+                    put_swizzled(img, kOffW2 + n * kW2Net, 128, j, f, W[n][l1][j * kHid + f]);
+            }
+        std::vector<float> bb(384);
+        for (int n = 0; n < 2; ++n)
+            for (int j = 0; j < kHid; ++j) {
+                bb[n * kHid + j] = B[n][l0][j];
+                bb[192 + n * kHid + j] = B[n][l1][j];
+            }
+        if (e == cudaSuccess) e = cudaMemcpy(m->img[g], img.data(), kImgBytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(m->sb[g], bb.data(), 384 * 4, cudaMemcpyHostToDevice);
+    }
+    // dense layers (bf16 [out][in_padded]) of the tc GEMMs
+    const int dl[5] = {L_EGO0, L_EGO1, L_TRUNK0, L_TRUNK1, L_HEAD};
+    for (int n = 0; n < 2; ++n)
+        for (int t = 0; t < 5; ++t) {
+            const int l = dl[t], o = l == L_HEAD ? (n == 0 ? 3 : 1) : kLayers[l].out, i = kLayers[l].in;
+            const int ip = l == L_EGO0 ? 16 : (i + 7) / 8 * 8;   // ego input padded to 16
+            std::vector<uint16_t> wb((size_t)o * ip, 0);
+            for (int r = 0; r < o; ++r)
+                for (int c = 0; c < i; ++c) wb[(size_t)r * ip + c] = to_bf16(W[n][l][(size_t)r * i + c]);
+            if (e == cudaSuccess) e = cudaMemcpy(m->w[n][t], wb.data(), wb.size() * 2, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(m->b[n][t], B[n][l], (size_t)o * 4, cudaMemcpyHostToDevice);
+        }
+    if (e != cudaSuccess) return lfail(m, SF_ERR_CUDA, std::string("sf_lf_set_params: ") + cudaGetErrorString(e));
+    return SF_OK;
+}
+
+sf_status ensure(sf_lf* m, int A) {
+    if (A <= m->cap) return SF_OK;
+    cudaStreamSynchronize(m->stream);
+    for (void* p : m->acts) cudaFree(p);
+    m->acts.clear();
+    m->cap = 0;
+    const size_t Aa = (size_t)A;
+    bool okk = lalloc(m, &m->xego, Aa * 16, true) && lalloc(m, &m->he1[0], Aa * 64, true) &&
+               lalloc(m, &m->he1[1], Aa * 64, true) && lalloc(m, &m->x[0], Aa * 256, true) &&
+               lalloc(m, &m->x[1], Aa * 256, true) && lalloc(m, &m->t1, Aa * 128, true) &&
+               lalloc(m, &m->t2, Aa * 64, true);
+    if (!okk) return lfail(m, SF_ERR_OOM, "sf_lf_forward: cudaMalloc of the activations failed");
+    m->cap = A;
+    return SF_OK;
+}
+
+cudaError_t gemm(sf_lf* m, const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, int M, int N, int K,
+                 int act, float* out_f32, __nv_bfloat16* out_bf16, int ldc) {
+    GemmArgs g{};
+    g.A = A; g.B = B; g.bias = bias;
+    g.out_f32 = out_f32; g.out_bf16 = out_bf16;
+    g.M = M; g.N = N; g.Nb = N; g.K = K;
+    g.ldc = ldc; g.ldt = 0;
+    g.act = act;
+    g.bn = N > 64 ? 128 : 64;
+    g.err = m->d_err;
+    return sf_gemm_launch(g, m->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t sf_lf_num_params(void) { return total_params(); }
+
+sf_status sf_lf_create(void* cuda_stream, sf_lf_handle* out) {
+    if (!out) return SF_ERR_INVALID_ARG;
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SF_ERR_CUDA;
+    sf_lf* m = new sf_lf();
+    m->stream = static_cast<cudaStream_t>(cuda_stream);
+    m->params.assign(total_params(), 0.f);
+    bool okk = true;
+    for (int g = 0; g < 2; ++g) okk = okk && lalloc(m, &m->img[g], kImgBytes / 16) && lalloc(m, &m->sb[g], 384);
+    for (int n = 0; n < 2; ++n)
+        for (int t = 0; t < 5; ++t) {
+            const int l = t == 0 ? L_EGO0 : t == 1 ? L_EGO1 : t == 2 ? L_TRUNK0 : t == 3 ? L_TRUNK1 : L_HEAD;
+            const int o = l == L_HEAD ? (n == 0 ? 3 : 1) : kLayers[l].out;
+            const int ip = l == L_EGO0 ? 16 : (kLayers[l].in + 7) / 8 * 8;
+            okk = okk && lalloc(m, &m->w[n][t], (size_t)o * ip) && lalloc(m, &m->b[n][t], (size_t)o);
+        }
+    okk = okk && lalloc(m, &m->d_err, 1);
+    static bool attr = false;
+    if (okk && !attr) {
+        okk = cudaFuncSetAttribute(lf_set_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) ==
+              cudaSuccess;
+        attr = okk;
+    }
+    if (!okk || cudaMemset(m->d_err, 0, 4) != cudaSuccess || upload(m) != SF_OK) {
+        for (void* p : m->allocs) cudaFree(p);
+        delete m;
+        return SF_ERR_CUDA;
+    }
+    *out = m;
+    return SF_OK;
+}
+
+sf_status sf_lf_destroy(sf_lf_handle m) {
+    if (!m) return SF_OK;
+    cudaStreamSynchronize(m->stream);
+    for (void* p : m->allocs) cudaFree(p);
+    for (void* p : m->acts) cudaFree(p);
+    delete m;
+    return SF_OK;
+}
+
+const char* sf_lf_last_error(sf_lf_handle m) { return m ? m->err.c_str() : "NULL handle"; }
+
+sf_status sf_lf_set_params(sf_lf_handle m, const float* h_params, size_t n) {
+    if (!m) return SF_ERR_INVALID_ARG;
+    if (!h_params || n != total_params())
+        return lfail(m, SF_ERR_INVALID_ARG, "sf_lf_set_params: expected " + std::to_string(total_params()) +
+                                                " parameters, got " + std::to_string(n));
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(h_params[i])) return lfail(m, SF_ERR_INVALID_ARG, "sf_lf_set_params: non-finite value");
+    cudaStreamSynchronize(m->stream);
+    m->params.assign(h_params, h_params + n);
+    return upload(m);
+}
+
+sf_status sf_lf_get_params(sf_lf_handle m, float* h_params, size_t n) {
+    if (!m) return SF_ERR_INVALID_ARG;
+    if (!h_params || n != total_params()) return lfail(m, SF_ERR_INVALID_ARG, "sf_lf_get_params: wrong size");
+    std::memcpy(h_params, m->params.data(), n * 4);
+    return SF_OK;
+}
+
+sf_status sf_lf_forward(sf_lf_handle m, const float* d_obs, const int32_t* d_n_road, const int32_t* d_n_veh,
+                        int num_agents, float* d_mean, float* d_value, float* d_embed) {
+    if (!m) return SF_ERR_INVALID_ARG;
+    if (num_agents < 0 || (num_agents > 0 && (!d_obs || !d_n_road || !d_n_veh || !d_mean)))
+        return lfail(m, SF_ERR_INVALID_ARG, "sf_lf_forward: NULL buffer or negative agent count");
+    if (num_agents == 0) return SF_OK;
+    sf_status s = ensure(m, num_agents);
+    if (s != SF_OK) return s;
+    const int A = num_agents;
+    cudaError_t e = cudaSuccess;
+    lf_ego_kernel<<<(A * 16 + 255) / 256, 256, 0, m->stream>>>(d_obs, kObs, A, m->xego);
+    e = cudaGetLastError();
+    for (int n = 0; n < 2 && e == cudaSuccess; ++n) {
+        e = gemm(m, m->xego, m->w[n][0], m->b[n][0], A, 64, 16, SF_ACT_ELU, nullptr, m->he1[n], 64);
+        if (e == cudaSuccess) e = gemm(m, m->he1[n], m->w[n][1], m->b[n][1], A, 64, 64, SF_ACT_ELU, nullptr, m->x[n], 256);
+    }
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    for (int g = 0; g < 2 && e == cudaSuccess; ++g) {
+        SetArgs sa{};
+        sa.obs = d_obs; sa.ld = kObs;
+        sa.off = g == 0 ? kRoad0 : kVeh0;
+        sa.F = g == 0 ? kPT : kNB;
+        sa.K = g == 0 ? kKR : kKV;
+        sa.count = g == 0 ? d_n_road : d_n_veh;
+        sa.num_agents = A;
+        sa.wimg = m->img[g];
+        sa.b1 = m->sb[g];
+        sa.b2 = m->sb[g] + 192;
+        sa.xa = m->x[0]; sa.xc = m->x[1];
+        sa.ldx = 256;
+        sa.xoff = g == 0 ? 64 : 160;
+        sa.err = m->d_err;
+        const int items = (A + kG - 1) / kG;
+        lf_set_kernel<<<items < sms ? items : sms, kThreads, kSmemBytes, m->stream>>>(sa);
+        e = cudaGetLastError();
+    }
+    for (int n = 0; n < 2 && e == cudaSuccess; ++n) {
+        e = gemm(m, m->x[n], m->w[n][2], m->b[n][2], A, 128, 256, SF_ACT_ELU, nullptr, m->t1, 128);
+        if (e == cudaSuccess) e = gemm(m, m->t1, m->w[n][3], m->b[n][3], A, 64, 128, SF_ACT_ELU, nullptr, m->t2, 64);
+        if (e == cudaSuccess) {
+            if (n == 0) e = gemm(m, m->t2, m->w[0][4], m->b[0][4], A, 3, 64, SF_ACT_NONE, d_mean, nullptr, 3);
+            else if (d_value) e = gemm(m, m->t2, m->w[1][4], m->b[1][4], A, 1, 64, SF_ACT_NONE, d_value, nullptr, 1);
+        }
+    }
+    if (e == cudaSuccess && d_embed) {
+        lf_embed_kernel<<<(A * 512 + 255) / 256, 256, 0, m->stream>>>(m->x[0], m->x[1], A, d_embed);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return lfail(m, SF_ERR_CUDA, std::string("sf_lf_forward: ") + cudaGetErrorString(e));
+    return SF_OK;
+}
+
+sf_status sf_lf_sync(sf_lf_handle m) {
+    if (!m) return SF_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return lfail(m, SF_ERR_CUDA, std::string("sf_lf_sync: ") + cudaGetErrorString(e));
+    unsigned w = 0;
+    if (cudaMemcpy(&w, m->d_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return lfail(m, SF_ERR_CUDA, "sf_lf_sync");
+    if (w) {
+        cudaMemset(m->d_err, 0, 4);
+        return lfail(m, SF_ERR_TIMEOUT, "sf_lf_sync: a bounded tensor-core wait gave up");
+    }
+    return SF_OK;
+}
+
+}  // extern "C"

@@ -1992,3 +1992,139 @@ cudaError_t sf_launch_place(const WorldArgs& a, const float* d_place, cudaStream
     place_kernel<<<(a.num_agents + 127) / 128, 128, 0, s>>>(a, d_place);
     return cudaGetLastError();
 }
+
+// ====================================================================== the full observation (App. D)
+// One warp per agent.  Ego group and weather token; road context: the world's
+// segment midpoints within 10 m, scanned in ascending point index (polyline
+// order) 32 at a time, each lane testing one midpoint, a ballot and a prefix
+// count placing the hits in order, stopping once 350 slots are filled;
+// neighbour context: a bitonic sort of the (squared distance, index) keys of
+// the world's other alive agents, one lane per slot.  Every slot that is not
+// filled is written as zeros, so the row is complete after the call.
+template <int NW>
+__global__ void __launch_bounds__(32 * NW) full_obs_kernel(const FullObsArgs f) {
+    const int lane = threadIdx.x & 31;
+    const int a = blockIdx.x * NW + (threadIdx.x >> 5);
+    if (a >= f.num_agents) return;
+    float* o = f.obs + (size_t)a * kFullObs;
+    const uint32_t meta = f.st.meta[a];
+    if (!(status_of(meta) & kAlive)) {
+        for (int i = lane; i < kFullObs; i += 32) o[i] = 0.f;
+        if (lane == 0) {
+            if (f.n_road) f.n_road[a] = 0;
+            if (f.n_veh) f.n_veh[a] = 0;
+        }
+        if (f.road_idx) for (int t = lane; t < kFullKR; t += 32) f.road_idx[(size_t)a * kFullKR + t] = -1;
+        if (f.veh_idx && lane < kFullKV) f.veh_idx[(size_t)a * kFullKV + lane] = -1;
+        return;
+    }
+    const float4 p = f.st.pos[a], q = f.st.quat[a], v = f.st.vel[a], g = f.st.goal[a];
+    float hx, hy;
+    heading_of(q.x, q.y, q.z, q.w, hx, hy);
+
+    // ---- ego group (11)
+    {
+        float gbx, gby, vbx, vby;
+        to_ego(hx, hy, g.x - p.x, g.y - p.y, gbx, gby);
+        to_ego(hx, hy, v.x, v.y, vbx, vby);
+        const float gn = sqrtf(gbx * gbx + gby * gby);
+        const uint32_t pc = meta & 0xFFu, sc = (meta >> 8) & 0xFFu;
+        float e = 0.f;
+        switch (lane) {
+            case 0: e = gbx / kSceneHalf; break;
+            case 1: e = gby / kSceneHalf; break;
+            case 2: e = gn > 0.f ? gby / gn : 0.f; break;
+            case 3: e = gn > 0.f ? gbx / gn : 1.f; break;
+            case 4: e = gn / kSceneHalf; break;
+            case 5: e = vbx / 10.f; break;
+            case 6: e = vby / 10.f; break;
+            case 7: e = (float)pc / 3.f; break;
+            case 8: e = sc == 0 ? 1.f : 0.f; break;
+            case 9: e = sc == 1 ? 1.f : 0.f; break;
+            case 10: e = sc == 2 ? 1.f : 0.f; break;
+            default: break;
+        }
+        if (lane < kFullEgo) o[lane] = e;
+    }
+
+    // ---- road context (350 x 5)
+    const int w = f.agent_world[a];
+    const int4 wd = f.rd.world[w];   // first agent, agents, first point, points
+    const int kend = wd.z + wd.w;
+    int nr = 0;
+    for (int base = wd.z; base < kend && nr < kFullKR; base += 32) {
+        const int k = base + lane;
+        float4 m = make_float4(kInf, 0.f, 0.f, 0.f);
+        if (k < kend) m = __ldg(f.rd.mid + k);
+        const float dx = m.x - p.x, dy = m.y - p.y;
+        const bool in = dx * dx + dy * dy <= kFullR2;
+        const unsigned bal = __ballot_sync(kFull, in);
+        const int slot = nr + __popc(bal & ((1u << lane) - 1u));
+        if (in && slot < kFullKR) {
+            float bx, by, ux, uy;
+            to_ego(hx, hy, dx, dy, bx, by);
+            to_ego(hx, hy, m.z, m.w, ux, uy);
+            float* s = o + kFullRoad0 + kFullPt * slot;
+            s[0] = bx / 10.f;
+            s[1] = by / 10.f;
+            s[2] = (float)__ldg(f.rd.ptype + k) / 20.f;
+            s[3] = ux;
+            s[4] = uy;
+            if (f.road_idx) f.road_idx[(size_t)a * kFullKR + slot] = k;
+        }
+        nr += __popc(bal);
+    }
+    nr = min(nr, kFullKR);
+    for (int i = kFullRoad0 + kFullPt * nr + lane; i < kFullVeh0; i += 32) o[i] = 0.f;
+    if (f.road_idx)
+        for (int t = nr + lane; t < kFullKR; t += 32) f.road_idx[(size_t)a * kFullKR + t] = -1;
+
+    // ---- vehicle context (24 x 7)
+    const int self = a - wd.x;
+    unsigned long long key = kKeyInf;
+    if (lane < wd.y && lane != self) {
+        const int b = wd.x + lane;
+        if (status_of(f.st.meta[b]) & kAlive) {
+            const float4 pb = f.st.pos[b];
+            const float dx = pb.x - p.x, dy = pb.y - p.y;
+            key = key_of(dx * dx + dy * dy, lane);
+        }
+    }
+    const int nv = min(__popc(__ballot_sync(kFull, key != kKeyInf)), kFullKV);
+    key = warp_sort32(key, lane);
+    if (lane < kFullKV) {
+        float s[kFullNb] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int jdx = -1;
+        if (lane < nv) {
+            const int b = wd.x + key_idx(key);
+            const float4 pb = f.st.pos[b], qb = f.st.quat[b], vb = f.st.vel[b];
+            float hjx, hjy, bx, by;
+            heading_of(qb.x, qb.y, qb.z, qb.w, hjx, hjy);
+            to_ego(hx, hy, pb.x - p.x, pb.y - p.y, bx, by);
+            const float dpsi = atan2f(cross2(hx, hy, hjx, hjy), hx * hjx + hy * hjy);
+            s[0] = bx / kSceneHalf;
+            s[1] = by / kSceneHalf;
+            s[2] = 2.f * kHalfLen / kSceneHalf;
+            s[3] = 2.f * kHalfWid / kSceneHalf;
+            s[4] = dpsi / 3.14159265358979323846f;
+            s[5] = sqrtf(vb.x * vb.x + vb.y * vb.y) / 10.f;
+            s[6] = ttc_pair(p.x, p.y, hx, hy, v.x, v.y, pb.x, pb.y, hjx, hjy, vb.x, vb.y) / kTtcMax;
+            jdx = b;
+        }
+        float* r = o + kFullVeh0 + kFullNb * lane;
+#pragma unroll
+        for (int i = 0; i < kFullNb; ++i) r[i] = s[i];
+        if (f.veh_idx) f.veh_idx[(size_t)a * kFullKV + lane] = jdx;
+    }
+    if (lane == 0) {
+        if (f.n_road) f.n_road[a] = nr;
+        if (f.n_veh) f.n_veh[a] = nv;
+    }
+}
+
+cudaError_t sf_launch_full_obs(const FullObsArgs& f, cudaStream_t s) {
+    if (f.num_agents <= 0) return cudaSuccess;
+    constexpr int NW = 8;
+    full_obs_kernel<NW><<<(f.num_agents + NW - 1) / NW, 32 * NW, 0, s>>>(f);
+    return cudaGetLastError();
+}

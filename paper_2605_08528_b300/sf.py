@@ -23,6 +23,8 @@ SF_OK, SF_ERR_INVALID_ARG, SF_ERR_CUDA, SF_ERR_OOM, SF_ERR_NONFINITE, SF_ERR_TIM
 STATUS_NAMES = {0: "SF_OK", 1: "SF_ERR_INVALID_ARG", 2: "SF_ERR_CUDA", 3: "SF_ERR_OOM", 4: "SF_ERR_NONFINITE",
                 5: "SF_ERR_TIMEOUT", 6: "SF_ERR_STATE"}
 NF, NI, OBS_DIM, K_AGENTS, L_POINTS = 25, 6, 320, 8, 32
+FULL_EGO, FULL_KR, FULL_PT, FULL_KV, FULL_NB = 11, 350, 5, 24, 7
+FULL_OBS_DIM = FULL_EGO + FULL_KR * FULL_PT + FULL_KV * FULL_NB   # 1929
 FLAG_INVINCIBLE, FLAG_AUTO_RESET, FLAG_RECORD_INDICES = 1, 2, 4
 ACT_NONE, ACT_ELU, ACT_SILU, ACT_TANH = 0, 1, 2, 3
 
@@ -66,7 +68,7 @@ def lib():
         sig = {
             "sf_create": ([vp, vp, vp], i32), "sf_destroy": ([vp], i32), "sf_load_roads": ([vp, vp], i32),
             "sf_step": ([vp, vp, f32, C.c_int], i32), "sf_get_obs": ([vp, vp, vp, vp, vp], i32),
-            "sf_output_ptrs": ([vp, vp], i32), "sf_get_indices": ([vp, vp, vp, vp, vp], i32), "sf_reset": ([vp, vp], i32), "sf_place_agents": ([vp, vp], i32),
+            "sf_output_ptrs": ([vp, vp], i32), "sf_observe_full": ([vp, vp, vp, vp, vp, vp], i32), "sf_get_indices": ([vp, vp, vp, vp, vp], i32), "sf_reset": ([vp, vp], i32), "sf_place_agents": ([vp, vp], i32),
             "sf_get_state": ([vp, vp, vp], i32), "sf_set_state": ([vp, vp, vp], i32),
             "sf_save_state": ([vp, C.c_char_p], i32), "sf_load_state": ([vp, C.c_char_p], i32),
             "sf_sync": ([vp], i32), "sf_autotune": ([vp, vp, f32, C.c_int, C.c_int, vp, vp], i32), "sf_num_agents": ([vp], i32), "sf_num_worlds": ([vp], i32),
@@ -90,6 +92,10 @@ def lib():
             "sf_surrogate_set_stats": ([vp, vp], i32),
             "sf_step_surrogate": ([vp, vp, vp, f32, C.c_int, C.c_int], i32),
             "sf_surrogate_audit": ([vp, vp, vp], i32),
+            "sf_lf_num_params": ([], C.c_size_t), "sf_lf_create": ([vp, vp], i32), "sf_lf_destroy": ([vp], i32),
+            "sf_lf_last_error": ([vp], C.c_char_p), "sf_lf_set_params": ([vp, vp, C.c_size_t], i32),
+            "sf_lf_get_params": ([vp, vp, C.c_size_t], i32),
+            "sf_lf_forward": ([vp, vp, vp, vp, C.c_int, vp, vp, vp], i32), "sf_lf_sync": ([vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -155,6 +161,11 @@ def sf_get_obs(h, d_obs=None, d_reward=None, d_done=None, d_events=None):
 
 def sf_get_indices(h, d_lane_seg=None, d_knn_points=None, d_knn_agents=None, d_drac=None):
     _check(lib().sf_get_indices(h, _ptr(d_lane_seg), _ptr(d_knn_points), _ptr(d_knn_agents), _ptr(d_drac)), h)
+
+
+def sf_observe_full(h, d_obs, d_n_road=None, d_n_veh=None, d_road_idx=None, d_veh_idx=None):
+    _check(lib().sf_observe_full(h, _ptr(d_obs), _ptr(d_n_road), _ptr(d_n_veh), _ptr(d_road_idx), _ptr(d_veh_idx)),
+           h)
 
 
 def sf_output_ptrs(h) -> sf_outputs:
@@ -255,6 +266,21 @@ class World:
         ev = t.empty(self.A, dtype=t.int32, device=dev)
         sf_get_obs(self.h, obs, rew, done, ev)
         return obs, rew, done, ev
+
+    def full_obs(self):
+        """Host copies of the paper's full observation (sf_observe_full) of the
+        current state: obs [A][1929], n_road, n_veh [A], road_idx [A][350],
+        veh_idx [A][24]."""
+        t = self.torch
+        obs = t.empty((self.A, FULL_OBS_DIM), dtype=t.float32, device="cuda")
+        nr = t.empty(self.A, dtype=t.int32, device="cuda")
+        nv = t.empty(self.A, dtype=t.int32, device="cuda")
+        ri = t.empty((self.A, FULL_KR), dtype=t.int32, device="cuda")
+        vi = t.empty((self.A, FULL_KV), dtype=t.int32, device="cuda")
+        sf_observe_full(self.h, obs, nr, nv, ri, vi)
+        sf_sync(self.h, allow=(SF_ERR_NONFINITE,))
+        return dict(obs=obs.cpu().numpy(), n_road=nr.cpu().numpy(), n_veh=nv.cpu().numpy(),
+                    road_idx=ri.cpu().numpy(), veh_idx=vi.cpu().numpy())
 
     def indices(self):
         """Host copies of the recorded nearest-lane / k-NN indices (SF_FLAG_RECORD_INDICES) and step DRAC."""
@@ -431,3 +457,66 @@ def sf_surrogate_audit(h):
     n = C.c_uint64()
     _check(lib().sf_surrogate_audit(h, C.byref(e), C.byref(n)), h)
     return float(e.value), int(n.value)
+
+
+# --------------------------------------------------------------------------- late-fusion actor-critic (App. E)
+def _lcheck(status, m):
+    if status != SF_OK:
+        raise SFError(status, lib().sf_lf_last_error(m).decode())
+    return status
+
+
+def sf_lf_num_params() -> int:
+    return int(lib().sf_lf_num_params())
+
+
+def sf_lf_create(stream=None):
+    m = C.c_void_p()
+    st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().sf_lf_create(C.c_void_p(st), C.byref(m)))
+    return m
+
+
+def sf_lf_destroy(m):
+    _lcheck(lib().sf_lf_destroy(m), m)
+
+
+def sf_lf_set_params(m, params):
+    p = np.ascontiguousarray(params, np.float32)
+    _lcheck(lib().sf_lf_set_params(m, p.ctypes.data, p.size), m)
+
+
+def sf_lf_get_params(m):
+    p = np.zeros(sf_lf_num_params(), np.float32)
+    _lcheck(lib().sf_lf_get_params(m, p.ctypes.data, p.size), m)
+    return p
+
+
+def sf_lf_forward(m, d_obs, d_n_road, d_n_veh, num_agents, d_mean, d_value=None, d_embed=None):
+    _lcheck(lib().sf_lf_forward(m, _ptr(d_obs), _ptr(d_n_road), _ptr(d_n_veh), int(num_agents), _ptr(d_mean),
+                                _ptr(d_value), _ptr(d_embed)), m)
+
+
+def sf_lf_sync(m):
+    _lcheck(lib().sf_lf_sync(m), m)
+
+
+# layer shapes (out, in) of one network in parameter order; the head has 3
+# outputs in the actor and 1 in the critic
+LF_LAYERS = [(64, 11), (64, 64), (96, 5), (96, 96), (96, 7), (96, 96), (128, 256), (64, 128), (None, 64)]
+
+
+def init_lf(seed=0, log_std=-0.5):
+    """Seeded initial parameters of the late-fusion network: weights
+    N(0, 1/fan_in), biases N(0, 0.05^2), log standard deviations log_std."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for head in (3, 1):
+        for o, i in LF_LAYERS:
+            o = head if o is None else o
+            out.append(rng.normal(0, 1 / np.sqrt(i), o * i))
+            out.append(rng.normal(0, 0.05, o))
+    out.append(np.full(3, log_std))
+    p = np.concatenate(out).astype(np.float32)
+    assert p.size == sf_lf_num_params()
+    return p
