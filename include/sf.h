@@ -493,6 +493,36 @@ sf_status sf_lf_forward(sf_lf_handle m, const float* d_obs, const int32_t* d_n_r
  * gave up since the last sync. */
 sf_status sf_lf_sync(sf_lf_handle m);
 
+/* The paper's control loop (Alg. 1: observe, act, simulate) with this
+ * network: the full observation of the current state, the actor's action
+ * means (and the critic's values) from it, then one sf_step on those actions
+ * (throttle and brake rectified, steer scaled, as for any action).  Buffers of
+ * the observation, counts and values are allocated by the first call on h.
+ * Asynchronous on h's stream; lf must not run elsewhere meanwhile.
+ * Errors: SF_ERR_STATE, SF_ERR_INVALID_ARG, SF_ERR_OOM, SF_ERR_CUDA. */
+sf_status sf_step_lf(sf_handle h, sf_lf_handle lf, float dt, int substeps);
+
+/* Device pointers to what the last sf_step_lf (or its captured graph) used:
+ * the full observation [A][SF_FULL_OBS_DIM], its counts [A], the actions [A][3]
+ * and the critic values [A] (library-owned, valid until sf_destroy / the next
+ * sf_load_roads). */
+typedef struct {
+    float* obs;
+    int32_t* n_road;
+    int32_t* n_veh;
+    float* actions;
+    float* value;
+    int32_t num_agents;
+} sf_lf_outputs;
+sf_status sf_lf_step_outputs(sf_handle h, sf_lf_outputs* out);
+
+/* Capture sf_step_lf (then sf_reset(d_reset_mask) if not NULL) into a CUDA
+ * graph on h's stream (not the legacy default stream); replay with
+ * sf_graph_launch.  Buffers are allocated before the capture.
+ * Errors: SF_ERR_STATE, SF_ERR_INVALID_ARG, SF_ERR_OOM, SF_ERR_CUDA. */
+sf_status sf_graph_capture_lf(sf_handle h, sf_lf_handle lf, const uint8_t* d_reset_mask, float dt, int substeps,
+                              sf_graph_handle* out);
+
 /* Number of agents and worlds of the loaded roads (0 before sf_load_roads). */
 int32_t sf_num_agents(sf_handle h);
 int32_t sf_num_worlds(sf_handle h);

@@ -41,6 +41,7 @@ struct sf_ctx {
     uint8_t* all_mask = nullptr;
     float* act_buf = nullptr;   // [A][3] actions written by an attached policy
     void* surr = nullptr;       // surrogate step buffers (allocated on first use)
+    void* lfb = nullptr;        // full observation and critic values of the late-fusion policy step
     struct PackSet {                // blocks of the world kernel for one (packing, staging) choice
         int cap, budget;            // agents per block (0: one world), staged bytes per block (0: off)
         int4* d;
@@ -91,6 +92,7 @@ sf_status dalloc(sf_ctx* h, T** p, size_t count) {
 
 void free_all(sf_ctx* h) {
     if (h->surr) { ::operator delete(h->surr); h->surr = nullptr; }
+    if (h->lfb) { ::operator delete(h->lfb); h->lfb = nullptr; }
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     h->st = DevState{};
@@ -100,6 +102,7 @@ void free_all(sf_ctx* h) {
     h->all_mask = nullptr;
     h->act_buf = nullptr;
     h->surr = nullptr;
+    h->lfb = nullptr;
     h->packsets.clear();
     h->sc = StepScratch{};
     h->loaded = false;
@@ -202,6 +205,24 @@ static SurrBufs* surr_bufs(sf_ctx* h) {
               dalloc(h, &b->words, 2) == SF_OK;
     if (!ok || cudaMemset(b->words, 0, 8) != cudaSuccess) { delete b; return nullptr; }
     h->surr = b;
+    return b;
+}
+
+struct LfBufs {                   // per-world-handle buffers of the late-fusion policy step
+    float* obs = nullptr;         // [A][SF_FULL_OBS_DIM]
+    int32_t* n_road = nullptr;    // [A]
+    int32_t* n_veh = nullptr;     // [A]
+    float* value = nullptr;       // [A]
+};
+
+static LfBufs* lf_bufs(sf_ctx* h) {
+    if (h->lfb) return static_cast<LfBufs*>(h->lfb);
+    const size_t A = (size_t)h->A;
+    LfBufs* b = new LfBufs();
+    bool ok = dalloc(h, &b->obs, A * SF_FULL_OBS_DIM) == SF_OK && dalloc(h, &b->n_road, A) == SF_OK &&
+              dalloc(h, &b->n_veh, A) == SF_OK && dalloc(h, &b->value, A) == SF_OK;
+    if (!ok) { delete b; return nullptr; }
+    h->lfb = b;
     return b;
 }
 
@@ -878,6 +899,78 @@ sf_status sf_step_policy(sf_handle h, sf_mlp_handle policy, float dt, int subste
     sf_status s = sf_mlp_forward_on(policy, h->stream, h->out.obs, SF_OBS_DIM, h->A, h->act_buf, 3);
     if (s != SF_OK) return fail(h, s, std::string("sf_step_policy: ") + sf_mlp_last_error(policy));
     return sf_step(h, h->act_buf, dt, substeps);
+}
+
+// observe (full), act (late-fusion actor mean, critic value), step
+static sf_status lf_step_body(sf_handle h, sf_lf_handle lf, LfBufs* b, float dt, int substeps) {
+    sf_status s = sf_observe_full(h, b->obs, b->n_road, b->n_veh, nullptr, nullptr);
+    if (s != SF_OK) return s;
+    s = sf_lf_forward_on(lf, h->stream, b->obs, b->n_road, b->n_veh, h->A, h->act_buf, b->value, nullptr);
+    if (s != SF_OK) return fail(h, s, std::string("late-fusion forward: ") + sf_lf_last_error(lf));
+    return sf_step(h, h->act_buf, dt, substeps);
+}
+
+sf_status sf_step_lf(sf_handle h, sf_lf_handle lf, float dt, int substeps) {
+    if (!h || !lf) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_step_lf: no roads loaded");
+    LfBufs* b = lf_bufs(h);
+    if (!b) return fail(h, SF_ERR_OOM, "sf_step_lf: observation buffers");
+    return lf_step_body(h, lf, b, dt, substeps);
+}
+
+sf_status sf_lf_step_outputs(sf_handle h, sf_lf_outputs* o) {
+    if (!h || !o) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_lf_step_outputs: no roads loaded");
+    LfBufs* b = lf_bufs(h);
+    if (!b) return fail(h, SF_ERR_OOM, "sf_lf_step_outputs: observation buffers");
+    o->obs = b->obs;
+    o->n_road = b->n_road;
+    o->n_veh = b->n_veh;
+    o->actions = h->act_buf;
+    o->value = b->value;
+    o->num_agents = h->A;
+    return SF_OK;
+}
+
+sf_status sf_graph_capture_lf(sf_handle h, sf_lf_handle lf, const uint8_t* d_reset_mask, float dt, int substeps,
+                              sf_graph_handle* out) {
+    if (!h || !lf || !out) return SF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_graph_capture_lf: no roads loaded");
+    if (!h->stream) return fail(h, SF_ERR_INVALID_ARG, "sf_graph_capture_lf: needs a non-default stream");
+    LfBufs* b = lf_bufs(h);
+    if (!b || sf_lf_reserve(lf, h->A) != SF_OK) return fail(h, SF_ERR_OOM, "sf_graph_capture_lf: buffers");
+    // one uncaptured forward: first-use work (kernel attributes) happens outside the capture
+    sf_status s0 = sf_observe_full(h, b->obs, b->n_road, b->n_veh, nullptr, nullptr);
+    if (s0 == SF_OK) s0 = sf_lf_forward_on(lf, h->stream, b->obs, b->n_road, b->n_veh, h->A, h->act_buf, b->value, nullptr);
+    if (s0 != SF_OK) return fail(h, s0, "sf_graph_capture_lf: warm-up forward");
+    SF_CUDA(h, cudaStreamSynchronize(h->stream));
+    sf_graph* g = new sf_graph();
+    g->h = h;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    sf_status st = SF_OK;
+    if (e == cudaSuccess) {
+        st = lf_step_body(h, lf, b, dt, substeps);
+        g->launches = 16;
+        if (st == SF_OK && d_reset_mask) { st = sf_reset(h, d_reset_mask); g->launches += 1; }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+        if (e2 == cudaSuccess && st == SF_OK) {
+            g->graph = graph;
+            e = cudaGraphInstantiate(&g->exec, graph, 0);
+        } else {
+            if (graph) cudaGraphDestroy(graph);
+            e = e2 != cudaSuccess ? e2 : cudaErrorUnknown;
+        }
+    }
+    if (e != cudaSuccess || st != SF_OK) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return st != SF_OK ? st : cuda_fail(h, e, "sf_graph_capture_lf");
+    }
+    *out = g;
+    return SF_OK;
 }
 
 sf_status sf_graph_capture(sf_handle h, sf_mlp_handle policy, sf_surrogate_handle surrogate, const float* d_actions,

@@ -37,6 +37,7 @@
 
 #include "../../include/sf.h"
 #include "sf_gemm.cuh"
+#include "sf_mlp_internal.cuh"
 #include "sf_tc.cuh"
 
 namespace {
@@ -51,27 +52,25 @@ constexpr int kG = 32;                               // agents per work item
 constexpr int kThreads = 256;
 constexpr unsigned kLfTimeout = 4u;                  // error-word bit: a bounded wait gave up
 
-// shared memory (offsets from a 1024-byte aligned base)
-constexpr int kOffW1 = 0;                           // [192 rows][128 B]: layer 1 of both nets, K 0..15 used
-constexpr int kW2Net = 2 * 128 * 128;               // per net: 2 K-atoms of [128 rows][128 B]
-constexpr int kOffW2 = kOffW1 + 192 * 128;          // 24576
-constexpr int kImgBytes = kOffW2 + 2 * kW2Net;      // 90112: the weight image copied from global
+// shared memory of one CTA (one network), offsets from a 1024-byte aligned base
+constexpr int kOffW1 = 0;                           // [96 rows][128 B]: layer 1, K 0..15 used (bias at K 15)
+constexpr int kOffW2 = kOffW1 + 96 * 128;           // 12288: 2 K-atoms of [128 rows][128 B], rows 96..127 zero
+constexpr int kImgBytes = kOffW2 + 2 * 128 * 128;   // 45056: one network's weight image
 constexpr int kOffA1 = kImgBytes;                   // [128 slots][128 B]
-constexpr int kH1Net = 2 * 128 * 128;               // per net: 2 K-atoms of [128 slots][128 B]
-constexpr int kOffH1 = kOffA1 + 128 * 128;          // 106496
-constexpr int kOffPool = kOffH1 + 2 * kH1Net;       // 172032: u32 [kG][192]
-constexpr int kOffMisc = kOffPool + kG * 192 * 4;   // 196608
-constexpr int kMiscBytes = 2048;
-constexpr int kSmemBytes = kOffMisc + kMiscBytes + 1024;
+constexpr int kOffH1 = kOffA1 + 128 * 128;          // 61440: 2 K-atoms of [128 slots][128 B]
+constexpr int kOffPool = kOffH1 + 2 * 128 * 128;    // 94208: u32 [kG][96]
+constexpr int kOffMisc = kOffPool + kG * kHid * 4;  // 106496
+constexpr int kMiscBytes = 1024;
+constexpr int kSmemBytes = kOffMisc + kMiscBytes + 1024;   // 108544: two CTAs per SM
+constexpr uint32_t kTmemCols = 256;                 // D1 at column 0 (96), D2 at column 128 (128)
 
 struct SetArgs {
     const float* obs;          // [A][ld]
     int ld, off, F, K;         // row stride, group offset, features per slot, slots
     const int32_t* count;      // [A] filled slots
     int num_agents;
-    const uint4* wimg;         // kImgBytes: W1 and W2 images (bf16, swizzled)
-    const float* b1;           // [192] layer-1 bias (actor 96, critic 96)
-    const float* b2;           // [192] layer-2 bias
+    const uint4* wimg;         // 2 x kImgBytes: actor then critic weight images (bf16, swizzled)
+    const float* b2;           // [2][96] layer-2 biases (layer-1 biases are in the images)
     __nv_bfloat16* xa;         // [A][ldx] actor trunk input
     __nv_bfloat16* xc;         // [A][ldx] critic trunk input
     int ldx, xoff;             // columns [xoff, xoff + 96) receive the pooled embedding
@@ -94,6 +93,21 @@ __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// ELU of two fp32 accumulators, in packed bf16: the positive part is the
+// rounded input, the negative part 2^(x log2 e) - 1 from the two-lane bf16
+// exp2; one of the two parts is zero, so their sum is exact
+__device__ __forceinline__ uint32_t elu_bf16x2(uint32_t a, uint32_t b) {
+    uint32_t x, pos, neg, e, t, y;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(x) : "f"(__uint_as_float(b)), "f"(__uint_as_float(a)));
+    asm("max.bf16x2 %0, %1, %2;" : "=r"(pos) : "r"(x), "r"(0u));
+    asm("min.bf16x2 %0, %1, %2;" : "=r"(neg) : "r"(x), "r"(0u));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(neg) : "r"(neg), "r"(0x3FB93FB9u));   // log2(e) in bf16
+    asm("ex2.approx.ftz.bf16x2 %0, %1;" : "=r"(e) : "r"(neg));
+    asm("sub.rn.bf16x2 %0, %1, %2;" : "=r"(t) : "r"(e), "r"(0x3F803F80u));       // e - 1 (exact for e >= 1/2)
+    asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(y) : "r"(pos), "r"(t));
+    return y;
 }
 
 // the agent (item-local) whose rows contain item row r: last s with rs[s] <= r
@@ -120,7 +134,8 @@ __device__ __forceinline__ void gather_row(const SetArgs& a, const int* rs, int 
         if (i < a.F) v[i] = __ldg(src + i);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) lf_set_kernel(const SetArgs a) {
+// Two CTAs per SM; even CTAs run the actor's encoder, odd ones the critic's.
+__global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~(uintptr_t)1023);
@@ -129,21 +144,25 @@ __global__ void __launch_bounds__(kThreads, 1) lf_set_kernel(const SetArgs a) {
     int* rs = reinterpret_cast<int*>(sm + kOffMisc);                       // [kG + 1] item row starts
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kOffMisc + 192);     // [2]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffMisc + 208);
-    float* sb1 = reinterpret_cast<float*>(sm + kOffMisc + 256);           // [192]
-    float* sb2 = reinterpret_cast<float*>(sm + kOffMisc + 1024);          // [192]
+    float* sb2 = reinterpret_cast<float*>(sm + kOffMisc + 256);           // [96]
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kOffMisc + 212);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int net = blockIdx.x & 1, cta = blockIdx.x >> 1, ncta = gridDim.x >> 1;
 
-    // ---- weights, biases, pool, barriers, TMEM
-    for (int i = tid; i < kImgBytes / 16; i += kThreads) reinterpret_cast<uint4*>(sm)[i] = __ldg(a.wimg + i);
-    for (int i = tid; i < 192; i += kThreads) { sb1[i] = __ldg(a.b1 + i); sb2[i] = __ldg(a.b2 + i); }
-    for (int i = tid; i < kG * 192; i += kThreads) pool[i] = 0u;
+    // ---- weights, bias, pool, barriers, TMEM
+    const uint4* img = a.wimg + (size_t)net * (kImgBytes / 16);
+    for (int i = tid; i < kImgBytes / 16; i += kThreads) reinterpret_cast<uint4*>(sm)[i] = __ldg(img + i);
+    for (int i = tid; i < kHid; i += kThreads) sb2[i] = __ldg(a.b2 + net * kHid + i);
+    for (int i = tid; i < kG * kHid; i += kThreads) pool[i] = 0u;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -152,13 +171,15 @@ __global__ void __launch_bounds__(kThreads, 1) lf_set_kernel(const SetArgs a) {
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tmem_slot;
-    constexpr uint32_t kIdesc1 = instr_desc(128, 192), kIdesc2 = instr_desc(128, 128);
+    constexpr uint32_t kIdesc1 = instr_desc(128, kHid), kIdesc2 = instr_desc(128, 128);
     uint32_t phase1 = 0, phase2 = 0;
-    bool ok = true;
-    const int q = warp & 3, net = warp >> 2;                // TMEM lane quarter, network of this warp
+    bool ok = true;   // false once any thread's bounded wait gave up (checked once per tile)
+    const int q = warp & 3, hh = warp >> 2;                 // TMEM lane quarter, column half of this warp
+    const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    __nv_bfloat16* X = net ? a.xc : a.xa;
     const int num_items = (a.num_agents + kG - 1) / kG;
 
-    for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
+    for (int item = cta; item < num_items && ok; item += ncta) {
         const int a0 = item * kG;
         const int na = min(kG, a.num_agents - a0);
         if (warp == 0) {
@@ -177,47 +198,48 @@ __global__ void __launch_bounds__(kThreads, 1) lf_set_kernel(const SetArgs a) {
         float v8[8];
         gather_row(a, rs, a0, total, 0, tid >> 1, v8);
         for (int t = 0; t < ntiles; ++t) {
-            // ---- A1: the tile's 128 slots x 16 features (bf16), two threads per row
+            // ---- A1: 128 slots x 16 inputs (features, zeros, 1 at K 15 for the bias), two threads per row
             {
                 const int row = tid >> 1, half = tid & 1;
-                uint4 w = make_uint4(0u, 0u, 0u, 0u);
-                if (half == 0) w = make_uint4(pack_bf16(v8[0], v8[1]), pack_bf16(v8[2], v8[3]), pack_bf16(v8[4], v8[5]),
-                                              pack_bf16(v8[6], v8[7]));
+                const bool live = t * 128 + row < total;
+                const uint4 w = half == 0 ? make_uint4(pack_bf16(v8[0], v8[1]), pack_bf16(v8[2], v8[3]),
+                                                       pack_bf16(v8[4], v8[5]), pack_bf16(v8[6], v8[7]))
+                                          : make_uint4(0u, 0u, 0u, live ? 0x3F800000u : 0u);
                 *reinterpret_cast<uint4*>(sm + kOffA1 + swz128(row, half)) = w;
             }
             fence_async_smem();
-            __syncthreads();
+            ok = __syncthreads_and(*abort_flag == 0) != 0;   // also: the last tile's TMEM reads are done
+            if (!ok) break;
+            tc_after();
             if (tid == 0) {
-                tc_after();
                 umma_bf16(tmem, smem_desc(sbase + kOffA1), smem_desc(sbase + kOffW1), kIdesc1, 0u);
                 umma_commit(&bar[0]);
             }
             if (t + 1 < ntiles) gather_row(a, rs, a0, total, t + 1, tid >> 1, v8);   // in flight meanwhile
 
-            // ---- epilogue 1: bias + ELU, bf16 rows of H1 (this warp: its 32 slots, its net's 96 columns)
-            ok = __syncthreads_and(mbar_wait(&bar[0], phase1, a.err, kLfTimeout) ? 1 : 0) != 0;
+            // ---- epilogue 1: ELU -> bf16 rows of H1 (this warp: its 32 slots, 48 of the 96 columns)
+            if (!mbar_wait(&bar[0], phase1, a.err, kLfTimeout)) *abort_flag = 1;
             phase1 ^= 1u;
-            if (!ok) break;
             tc_after();
             {
+                uint32_t r0[32], r1[16];
+                tmem_ld32_async(tmem + lanes + (uint32_t)(48 * hh), r0);
+                tmem_ld16_async(tmem + lanes + (uint32_t)(48 * hh + 32), r1);
+                tmem_wait();
+                tmem_hold(r0);
+                tmem_hold(r1);
                 const int row = 32 * q + lane;
-                unsigned char* h1 = sm + kOffH1 + net * kH1Net;
-#pragma unroll 1
-                for (int c = 0; c < 3; ++c) {
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kHid * net + 32 * c), v);
-                    const float* b = sb1 + kHid * net + 32 * c;
+                unsigned char* h1 = sm + kOffH1;
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {   // 8 columns -> one 16-byte chunk of the K-major row
-                        uint32_t p[4];
+                for (int u = 0; u < 6; ++u) {    // 8 columns -> one 16-byte chunk of the K-major row
+                    uint32_t p[4];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            p[e] = pack_bf16(elu(v[8 * m + 2 * e] + b[8 * m + 2 * e]),
-                                             elu(v[8 * m + 2 * e + 1] + b[8 * m + 2 * e + 1]));
-                        const int j = 4 * c + m;                 // chunk of the 96-wide row
-                        *reinterpret_cast<uint4*>(h1 + (j >> 3) * 16384 + swz128(row, j & 7)) =
-                            make_uint4(p[0], p[1], p[2], p[3]);
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = 8 * u + 2 * e;
+                        p[e] = c < 32 ? elu_bf16x2(r0[c], r0[c + 1]) : elu_bf16x2(r1[c - 32], r1[c - 31]);
                     }
+                    const int j = 6 * hh + u;    // chunk of the 96-wide row
+                    *reinterpret_cast<uint4*>(h1 + (j >> 3) * 16384 + swz128(row, j & 7)) = make_uint4(p[0], p[1], p[2], p[3]);
                 }
             }
             fence_async_smem();
@@ -226,59 +248,69 @@ __global__ void __launch_bounds__(kThreads, 1) lf_set_kernel(const SetArgs a) {
             if (tid == 0) {
                 tc_after();
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int kk = 0; kk < 6; ++kk) {
-                        const uint64_t ad = smem_desc(sbase + kOffW2 + h * kW2Net + (kk >> 2) * 16384) + 2 * (kk & 3);
-                        const uint64_t bd = smem_desc(sbase + kOffH1 + h * kH1Net + (kk >> 2) * 16384) + 2 * (kk & 3);
-                        umma_bf16(tmem + 256 + 128 * h, ad, bd, kIdesc2, kk > 0 ? 1u : 0u);
-                    }
+                for (int kk = 0; kk < 6; ++kk) {
+                    const uint64_t ad = smem_desc(sbase + kOffW2 + (kk >> 2) * 16384) + 2 * (kk & 3);
+                    const uint64_t bd = smem_desc(sbase + kOffH1 + (kk >> 2) * 16384) + 2 * (kk & 3);
+                    umma_bf16(tmem + 128, ad, bd, kIdesc2, kk > 0 ? 1u : 0u);
+                }
                 umma_commit(&bar[1]);
             }
 
-            // ---- epilogue 2: per feature, running max over the tile's slot columns
-            ok = __syncthreads_and(mbar_wait(&bar[1], phase2, a.err, kLfTimeout) ? 1 : 0) != 0;
+            // ---- epilogue 2: per feature, running max over 64 of the tile's slot columns
+            if (!mbar_wait(&bar[1], phase2, a.err, kLfTimeout)) *abort_flag = 1;
             phase2 ^= 1u;
-            if (!ok) break;
             tc_after();
-            if (q < 3) {
+            const int rbase = 128 * t + 64 * hh;
+            if (q < 3 && rbase < total) {
+                uint32_t r[2][32];
+                tmem_ld32_async(tmem + lanes + (uint32_t)(128 + 64 * hh), r[0]);
+                tmem_ld32_async(tmem + lanes + (uint32_t)(128 + 64 * hh + 32), r[1]);
+                tmem_wait();
+                tmem_hold(r[0]);
+                tmem_hold(r[1]);
                 const int f = 32 * q + lane;
-                const int r0 = 128 * t;
-                int s = agent_of_row(rs, r0);            // agent holding the tile's first row
+                int s = agent_of_row(rs, rbase);         // agent holding the first row
                 int bnd = rs[s + 1];                     // row where it ends
                 float m = -INFINITY;
-#pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(256 + 128 * net + 32 * c), v);
-                    const int base = r0 + 32 * c;
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        if (base + i == bnd) {           // warp-uniform: every lane walks the same rows
-                            if (s < kG) atomicMax(&pool[s * 192 + kHid * net + f], fkey(m));
-                            while (s < kG && rs[s + 1] <= base + i) ++s;
-                            bnd = s < kG ? rs[s + 1] : 0x7FFFFFFF;
-                            m = -INFINITY;
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        const int base = rbase + 32 * c + 8 * g;
+                        const uint32_t* v = r[c] + 8 * g;
+                        if (bnd >= base + 8) {           // warp-uniform: no agent boundary in these 8 rows
+                            const float m4 = fmaxf(fmaxf(__uint_as_float(v[0]), __uint_as_float(v[1])),
+                                                   fmaxf(__uint_as_float(v[2]), __uint_as_float(v[3])));
+                            const float n4 = fmaxf(fmaxf(__uint_as_float(v[4]), __uint_as_float(v[5])),
+                                                   fmaxf(__uint_as_float(v[6]), __uint_as_float(v[7])));
+                            m = fmaxf(m, fmaxf(m4, n4));
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                if (base + i == bnd) {   // warp-uniform
+                                    if (s < kG) atomicMax(&pool[s * kHid + f], fkey(m));
+                                    while (s < kG && rs[s + 1] <= base + i) ++s;
+                                    bnd = s < kG ? rs[s + 1] : 0x7FFFFFFF;
+                                    m = -INFINITY;
+                                }
+                                m = fmaxf(m, __uint_as_float(v[i]));
+                            }
                         }
-                        m = fmaxf(m, v[i]);
                     }
-                }
-                if (s < kG) atomicMax(&pool[s * 192 + kHid * net + f], fkey(m));   // continues in the next tile
+                if (s < kG) atomicMax(&pool[s * kHid + f], fkey(m));   // continues past these rows
             }
-            tc_before();
-            __syncthreads();
-            tc_after();
+            tc_before();   // this tile's TMEM reads before the next tile's barrier and MMAs
         }
         if (!ok) break;
         __syncthreads();
+        if (*abort_flag) break;
         // ---- the item's pooled embeddings: + bias, ELU, bf16 into the trunk inputs
-        for (int i = tid; i < na * 192; i += kThreads) {
-            const int al = i / 192, col = i - al * 192;
+        for (int i = tid; i < na * kHid; i += kThreads) {
+            const int al = i / kHid, col = i - al * kHid;
             const uint32_t k = pool[i];
             pool[i] = 0u;
             const float y = k ? elu(funkey(k) + sb2[col]) : 0.f;
-            __nv_bfloat16* X = col < kHid ? a.xa : a.xc;
-            X[(size_t)(a0 + al) * a.ldx + a.xoff + (col % kHid)] = __float2bfloat16_rn(y);
+            X[(size_t)(a0 + al) * a.ldx + a.xoff + col] = __float2bfloat16_rn(y);
         }
         __syncthreads();
     }
@@ -286,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1) lf_set_kernel(const SetArgs a) {
     __syncthreads();
     if (warp == 0) {
         tc_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
 }
 
@@ -341,8 +373,8 @@ struct sf_lf {
     std::vector<void*> allocs;           // parameters and the error word
     std::vector<void*> acts;             // activation buffers (grown on demand)
     // device parameters
-    uint4* img[2] = {nullptr, nullptr};  // road, vehicles: kImgBytes each
-    float* sb[2] = {nullptr, nullptr};   // road, vehicles: b1[192], b2[192]
+    uint4* img[2] = {nullptr, nullptr};  // road, vehicles: 2 x kImgBytes each (actor, critic)
+    float* sb[2] = {nullptr, nullptr};   // road, vehicles: layer-2 biases [2][96]
     __nv_bfloat16* w[2][6] = {};         // per net: ego0 [64][16], ego1, trunk0, trunk1, head [out][64] (bf16)
     float* b[2][6] = {};                 // their biases
     // activations (grown on demand)
@@ -387,24 +419,23 @@ sf_status upload(sf_lf* m) {
             B[n].push_back(P + k); k += o;
         }
     cudaError_t e = cudaSuccess;
-    // set-encoder images: group g (0 road, 1 vehicles) uses layers (ROAD0, ROAD1) / (VEH0, VEH1)
+    // set-encoder images: group g (0 road, 1 vehicles) uses layers (ROAD0, ROAD1) / (VEH0, VEH1); per
+    // network, layer 1 as [96 rows][K 16] with the bias at K 15 and layer 2 as [128 rows][K 96]
     for (int g = 0; g < 2; ++g) {
         const int l0 = g == 0 ? L_ROAD0 : L_VEH0, l1 = l0 + 1, F = kLayers[l0].in;
-        std::vector<uint16_t> img(kImgBytes / 2, 0);
-        for (int n = 0; n < 2; ++n)
+        std::vector<uint16_t> img(kImgBytes, 0);   // two networks of kImgBytes bytes
+        std::vector<float> bb(2 * kHid);
+        for (int n = 0; n < 2; ++n) {
+            const size_t base = (size_t)n * kImgBytes;
             for (int j = 0; j < kHid; ++j) {
-                for (int f = 0; f < F; ++f) put_swizzled(img, kOffW1, 192, n * kHid + j, f, W[n][l0][j * F + f]);
-                for (int f = 0; f < kHid; ++f)
-                    put_swizzled(img, kOffW2 + n * kW2Net, 128, j, f, W[n][l1][j * kHid + f]);
+                for (int f = 0; f < F; ++f) put_swizzled(img, base + kOffW1, 96, j, f, W[n][l0][j * F + f]);
+                put_swizzled(img, base + kOffW1, 96, j, 15, B[n][l0][j]);
+                for (int f = 0; f < kHid; ++f) put_swizzled(img, base + kOffW2, 128, j, f, W[n][l1][j * kHid + f]);
+                bb[n * kHid + j] = B[n][l1][j];
             }
-        std::vector<float> bb(384);
-        for (int n = 0; n < 2; ++n)
-            for (int j = 0; j < kHid; ++j) {
-                bb[n * kHid + j] = B[n][l0][j];
-                bb[192 + n * kHid + j] = B[n][l1][j];
-            }
-        if (e == cudaSuccess) e = cudaMemcpy(m->img[g], img.data(), kImgBytes, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(m->sb[g], bb.data(), 384 * 4, cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(m->img[g], img.data(), 2 * kImgBytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(m->sb[g], bb.data(), 2 * kHid * 4, cudaMemcpyHostToDevice);
     }
     // dense layers (bf16 [out][in_padded]) of the tc GEMMs
     const int dl[5] = {L_EGO0, L_EGO1, L_TRUNK0, L_TRUNK1, L_HEAD};
@@ -424,7 +455,7 @@ sf_status upload(sf_lf* m) {
 
 sf_status ensure(sf_lf* m, int A) {
     if (A <= m->cap) return SF_OK;
-    cudaStreamSynchronize(m->stream);
+    cudaDeviceSynchronize();   // the buffers may be in use on any stream the network ran on
     for (void* p : m->acts) cudaFree(p);
     m->acts.clear();
     m->cap = 0;
@@ -438,8 +469,8 @@ sf_status ensure(sf_lf* m, int A) {
     return SF_OK;
 }
 
-cudaError_t gemm(sf_lf* m, const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, int M, int N, int K,
-                 int act, float* out_f32, __nv_bfloat16* out_bf16, int ldc) {
+cudaError_t gemm(sf_lf* m, cudaStream_t st, const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, int M,
+                 int N, int K, int act, float* out_f32, __nv_bfloat16* out_bf16, int ldc) {
     GemmArgs g{};
     g.A = A; g.B = B; g.bias = bias;
     g.out_f32 = out_f32; g.out_bf16 = out_bf16;
@@ -448,7 +479,7 @@ cudaError_t gemm(sf_lf* m, const __nv_bfloat16* A, const __nv_bfloat16* B, const
     g.act = act;
     g.bn = N > 64 ? 128 : 64;
     g.err = m->d_err;
-    return sf_gemm_launch(g, m->stream);
+    return sf_gemm_launch(g, st);
 }
 
 }  // namespace
@@ -466,7 +497,7 @@ sf_status sf_lf_create(void* cuda_stream, sf_lf_handle* out) {
     m->stream = static_cast<cudaStream_t>(cuda_stream);
     m->params.assign(total_params(), 0.f);
     bool okk = true;
-    for (int g = 0; g < 2; ++g) okk = okk && lalloc(m, &m->img[g], kImgBytes / 16) && lalloc(m, &m->sb[g], 384);
+    for (int g = 0; g < 2; ++g) okk = okk && lalloc(m, &m->img[g], 2 * kImgBytes / 16) && lalloc(m, &m->sb[g], 2 * kHid);
     for (int n = 0; n < 2; ++n)
         for (int t = 0; t < 5; ++t) {
             const int l = t == 0 ? L_EGO0 : t == 1 ? L_EGO1 : t == 2 ? L_TRUNK0 : t == 3 ? L_TRUNK1 : L_HEAD;
@@ -499,6 +530,12 @@ sf_status sf_lf_destroy(sf_lf_handle m) {
     return SF_OK;
 }
 
+}  // extern "C"
+
+sf_status sf_lf_reserve(sf_lf_handle m, int batch) { return m ? ensure(m, batch) : SF_ERR_INVALID_ARG; }
+
+extern "C" {
+
 const char* sf_lf_last_error(sf_lf_handle m) { return m ? m->err.c_str() : "NULL handle"; }
 
 sf_status sf_lf_set_params(sf_lf_handle m, const float* h_params, size_t n) {
@@ -520,8 +557,10 @@ sf_status sf_lf_get_params(sf_lf_handle m, float* h_params, size_t n) {
     return SF_OK;
 }
 
-sf_status sf_lf_forward(sf_lf_handle m, const float* d_obs, const int32_t* d_n_road, const int32_t* d_n_veh,
-                        int num_agents, float* d_mean, float* d_value, float* d_embed) {
+}  // extern "C"
+
+sf_status sf_lf_forward_on(sf_lf_handle m, cudaStream_t st, const float* d_obs, const int32_t* d_n_road,
+                           const int32_t* d_n_veh, int num_agents, float* d_mean, float* d_value, float* d_embed) {
     if (!m) return SF_ERR_INVALID_ARG;
     if (num_agents < 0 || (num_agents > 0 && (!d_obs || !d_n_road || !d_n_veh || !d_mean)))
         return lfail(m, SF_ERR_INVALID_ARG, "sf_lf_forward: NULL buffer or negative agent count");
@@ -530,11 +569,11 @@ sf_status sf_lf_forward(sf_lf_handle m, const float* d_obs, const int32_t* d_n_r
     if (s != SF_OK) return s;
     const int A = num_agents;
     cudaError_t e = cudaSuccess;
-    lf_ego_kernel<<<(A * 16 + 255) / 256, 256, 0, m->stream>>>(d_obs, kObs, A, m->xego);
+    lf_ego_kernel<<<(A * 16 + 255) / 256, 256, 0, st>>>(d_obs, kObs, A, m->xego);
     e = cudaGetLastError();
     for (int n = 0; n < 2 && e == cudaSuccess; ++n) {
-        e = gemm(m, m->xego, m->w[n][0], m->b[n][0], A, 64, 16, SF_ACT_ELU, nullptr, m->he1[n], 64);
-        if (e == cudaSuccess) e = gemm(m, m->he1[n], m->w[n][1], m->b[n][1], A, 64, 64, SF_ACT_ELU, nullptr, m->x[n], 256);
+        e = gemm(m, st, m->xego, m->w[n][0], m->b[n][0], A, 64, 16, SF_ACT_ELU, nullptr, m->he1[n], 64);
+        if (e == cudaSuccess) e = gemm(m, st, m->he1[n], m->w[n][1], m->b[n][1], A, 64, 64, SF_ACT_ELU, nullptr, m->x[n], 256);
     }
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
@@ -547,30 +586,37 @@ sf_status sf_lf_forward(sf_lf_handle m, const float* d_obs, const int32_t* d_n_r
         sa.count = g == 0 ? d_n_road : d_n_veh;
         sa.num_agents = A;
         sa.wimg = m->img[g];
-        sa.b1 = m->sb[g];
-        sa.b2 = m->sb[g] + 192;
+        sa.b2 = m->sb[g];
         sa.xa = m->x[0]; sa.xc = m->x[1];
         sa.ldx = 256;
         sa.xoff = g == 0 ? 64 : 160;
         sa.err = m->d_err;
         const int items = (A + kG - 1) / kG;
-        lf_set_kernel<<<items < sms ? items : sms, kThreads, kSmemBytes, m->stream>>>(sa);
+        lf_set_kernel<<<2 * (items < sms ? items : sms), kThreads, kSmemBytes, st>>>(sa);
         e = cudaGetLastError();
     }
     for (int n = 0; n < 2 && e == cudaSuccess; ++n) {
-        e = gemm(m, m->x[n], m->w[n][2], m->b[n][2], A, 128, 256, SF_ACT_ELU, nullptr, m->t1, 128);
-        if (e == cudaSuccess) e = gemm(m, m->t1, m->w[n][3], m->b[n][3], A, 64, 128, SF_ACT_ELU, nullptr, m->t2, 64);
+        e = gemm(m, st, m->x[n], m->w[n][2], m->b[n][2], A, 128, 256, SF_ACT_ELU, nullptr, m->t1, 128);
+        if (e == cudaSuccess) e = gemm(m, st, m->t1, m->w[n][3], m->b[n][3], A, 64, 128, SF_ACT_ELU, nullptr, m->t2, 64);
         if (e == cudaSuccess) {
-            if (n == 0) e = gemm(m, m->t2, m->w[0][4], m->b[0][4], A, 3, 64, SF_ACT_NONE, d_mean, nullptr, 3);
-            else if (d_value) e = gemm(m, m->t2, m->w[1][4], m->b[1][4], A, 1, 64, SF_ACT_NONE, d_value, nullptr, 1);
+            if (n == 0) e = gemm(m, st, m->t2, m->w[0][4], m->b[0][4], A, 3, 64, SF_ACT_NONE, d_mean, nullptr, 3);
+            else if (d_value) e = gemm(m, st, m->t2, m->w[1][4], m->b[1][4], A, 1, 64, SF_ACT_NONE, d_value, nullptr, 1);
         }
     }
     if (e == cudaSuccess && d_embed) {
-        lf_embed_kernel<<<(A * 512 + 255) / 256, 256, 0, m->stream>>>(m->x[0], m->x[1], A, d_embed);
+        lf_embed_kernel<<<(A * 512 + 255) / 256, 256, 0, st>>>(m->x[0], m->x[1], A, d_embed);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return lfail(m, SF_ERR_CUDA, std::string("sf_lf_forward: ") + cudaGetErrorString(e));
     return SF_OK;
+}
+
+extern "C" {
+
+sf_status sf_lf_forward(sf_lf_handle m, const float* d_obs, const int32_t* d_n_road, const int32_t* d_n_veh,
+                        int num_agents, float* d_mean, float* d_value, float* d_embed) {
+    if (!m) return SF_ERR_INVALID_ARG;
+    return sf_lf_forward_on(m, m->stream, d_obs, d_n_road, d_n_veh, num_agents, d_mean, d_value, d_embed);
 }
 
 sf_status sf_lf_sync(sf_lf_handle m) {

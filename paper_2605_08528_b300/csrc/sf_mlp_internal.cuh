@@ -9,3 +9,8 @@ sf_status sf_mlp_reserve(sf_mlp_handle m, int batch);
 // sf_mlp_forward on `stream` instead of the MLP's own stream (no allocation if reserved)
 sf_status sf_mlp_forward_on(sf_mlp_handle m, cudaStream_t stream, const float* d_x, int ldx, int batch, float* d_y,
                             int ldy);
+
+// the late-fusion actor-critic on an explicit stream (used by the policy step and its graph)
+sf_status sf_lf_reserve(sf_lf_handle m, int batch);
+sf_status sf_lf_forward_on(sf_lf_handle m, cudaStream_t stream, const float* d_obs, const int32_t* d_n_road,
+                           const int32_t* d_n_veh, int num_agents, float* d_mean, float* d_value, float* d_embed);

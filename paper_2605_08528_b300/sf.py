@@ -96,6 +96,8 @@ def lib():
             "sf_lf_last_error": ([vp], C.c_char_p), "sf_lf_set_params": ([vp, vp, C.c_size_t], i32),
             "sf_lf_get_params": ([vp, vp, C.c_size_t], i32),
             "sf_lf_forward": ([vp, vp, vp, vp, C.c_int, vp, vp, vp], i32), "sf_lf_sync": ([vp], i32),
+            "sf_step_lf": ([vp, vp, f32, C.c_int], i32), "sf_lf_step_outputs": ([vp, vp], i32),
+            "sf_graph_capture_lf": ([vp, vp, vp, f32, C.c_int, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -499,6 +501,43 @@ def sf_lf_forward(m, d_obs, d_n_road, d_n_veh, num_agents, d_mean, d_value=None,
 
 def sf_lf_sync(m):
     _lcheck(lib().sf_lf_sync(m), m)
+
+
+class sf_lf_outputs(C.Structure):
+    _fields_ = [("obs", C.c_void_p), ("n_road", C.c_void_p), ("n_veh", C.c_void_p), ("actions", C.c_void_p),
+                ("value", C.c_void_p), ("num_agents", C.c_int32)]
+
+
+class _DevArray:
+    """A library-owned device buffer exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = dict(shape=tuple(shape), typestr=typestr, data=(int(ptr), False),
+                                             version=2, strides=None)
+
+
+def device_view(ptr, shape, dtype="float32"):
+    """Zero-copy torch view of a library-owned device buffer (e.g. a pointer
+    from sf_output_ptrs or sf_lf_step_outputs)."""
+    import torch
+    typestr = {"float32": "<f4", "int32": "<i4", "uint8": "|u1", "uint32": "<u4"}[dtype]
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")
+
+
+def sf_step_lf(h, lf, dt=1.0 / 30.0, substeps=4):
+    _check(lib().sf_step_lf(h, lf, dt, substeps), h)
+
+
+def sf_lf_step_outputs(h) -> sf_lf_outputs:
+    o = sf_lf_outputs()
+    _check(lib().sf_lf_step_outputs(h, C.byref(o)), h)
+    return o
+
+
+def sf_graph_capture_lf(h, lf, d_reset_mask=None, dt=1.0 / 30.0, substeps=4):
+    g = C.c_void_p()
+    _check(lib().sf_graph_capture_lf(h, lf, _ptr(d_reset_mask), dt, substeps, C.byref(g)), h)
+    return g
 
 
 # layer shapes (out, in) of one network in parameter order; the head has 3

@@ -124,3 +124,59 @@ def test_lf_rejects_bad_arguments():
     with pytest.raises(sf.SFError):
         sf.sf_lf_forward(m, None, None, None, 4, None)
     sf.sf_lf_destroy(m)
+
+
+def lf_world(sc, stream, seed=5):
+    W = sf.World(sc, seed=seed, flags=sf.FLAG_AUTO_RESET, stream=stream)
+    with torch.cuda.stream(stream):
+        sf.sf_reset(W.h, torch.ones(W.A, dtype=torch.uint8, device="cuda"))
+    return W
+
+
+def test_lf_policy_step_and_its_graph_match_the_individual_calls():
+    """sf_step_lf = full observation -> actor means -> sf_step, and its captured
+    graph (with a reset mask) replays bit-identically to those calls."""
+    sc = synth.procedural_scene(6, 16, seed_base=900)
+    s1, s2, s3 = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    W1, W2, W3 = lf_world(sc, s1), lf_world(sc, s2), lf_world(sc, s3)
+    p = sf.init_lf(seed=11)
+    lf1, lf2, lf3 = sf.sf_lf_create(s1), sf.sf_lf_create(s2), sf.sf_lf_create(s3)
+    for m in (lf1, lf2, lf3):
+        sf.sf_lf_set_params(m, p)
+    A = W1.A
+    obs = torch.zeros((A, sf.FULL_OBS_DIM), device="cuda")
+    nr = torch.zeros(A, dtype=torch.int32, device="cuda")
+    nv = torch.zeros_like(nr)
+    mean = torch.zeros((A, 3), device="cuda")
+    val = torch.zeros(A, device="cuda")
+    mask = torch.zeros(A, dtype=torch.uint8, device="cuda")
+    masks = torch.as_tensor(np.stack([synth.reset_mask(A, t, 0.2) for t in range(8)]), device="cuda")
+    torch.cuda.synchronize()
+    g = sf.sf_graph_capture_lf(W3.h, lf3, d_reset_mask=mask)
+    for t in range(8):
+        with torch.cuda.stream(s1):
+            sf.sf_step_lf(W1.h, lf1)
+            sf.sf_reset(W1.h, masks[t])
+        with torch.cuda.stream(s2):
+            sf.sf_observe_full(W2.h, obs, nr, nv)
+            sf.sf_lf_forward(lf2, obs, nr, nv, A, mean, val)
+            sf.sf_step(W2.h, mean)
+            sf.sf_reset(W2.h, masks[t])
+        with torch.cuda.stream(s3):
+            mask.copy_(masks[t])
+            sf.sf_graph_launch(g)
+        torch.cuda.synchronize()
+    o = sf.sf_lf_step_outputs(W3.h)
+    F1, I1, _ = sf.sf_get_state(W1.h)
+    F2, I2, _ = sf.sf_get_state(W2.h)
+    F3, I3, _ = sf.sf_get_state(W3.h)
+    assert np.array_equal(F1, F2) and np.array_equal(I1, I2)
+    assert np.array_equal(F1, F3) and np.array_equal(I1, I3)
+    assert o.num_agents == A and o.value and o.actions
+    v3 = sf.device_view(o.value, (A,)).clone()
+    a3 = sf.device_view(o.actions, (A, 3)).clone()
+    assert torch.isfinite(v3).all()
+    assert torch.equal(v3, val) and torch.equal(a3, mean)   # the last step's critic values and actions
+    sf.sf_graph_destroy(g)
+    for m in (lf1, lf2, lf3):
+        sf.sf_lf_destroy(m)
