@@ -218,7 +218,8 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
             if (t + 1 < ntiles) gather_row(a, rs, a0, total, t + 1, tid >> 1, v8);   // in flight meanwhile
 
             // ---- epilogue 1: ELU -> bf16 rows of H1 (this warp: its 32 slots, 48 of the 96 columns)
-            if (!mbar_wait(&bar[0], phase1, a.err, kLfTimeout)) *abort_flag = 1;
+            // every lane waits, then the warp reconverges (the tcgen05.ld that follows is warp-synchronous)
+            if (!__all_sync(0xFFFFFFFFu, mbar_wait(&bar[0], phase1, a.err, kLfTimeout))) *abort_flag = 1;
             phase1 ^= 1u;
             tc_after();
             {
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
             }
 
             // ---- epilogue 2: per feature, running max over 64 of the tile's slot columns
-            if (!mbar_wait(&bar[1], phase2, a.err, kLfTimeout)) *abort_flag = 1;
+            if (!__all_sync(0xFFFFFFFFu, mbar_wait(&bar[1], phase2, a.err, kLfTimeout))) *abort_flag = 1;
             phase2 ^= 1u;
             tc_after();
             const int rbase = 128 * t + 64 * hh;
