@@ -28,7 +28,7 @@ I_PRECIP, I_SURFACE, I_STEP, I_EPISODE, I_STATUS, I_EVENTS = range(6)
 ALIVE, PARKED = 1, 2
 EV = dict(goal=1, collision=2, crash=4, lane_forbidden=8, offroad=16, idle=32, timeout=64,
           nonfinite=128, respawned=256)
-FLAG_INVINCIBLE, FLAG_AUTO_RESET = 1, 2
+FLAG_INVINCIBLE, FLAG_AUTO_RESET, FLAG_BICYCLE = 1, 2, 4
 K_AGENTS, L_POINTS, OBS = 8, 32, 320
 FULL_EGO, FULL_KR, FULL_PT, FULL_KV, FULL_NB = 11, 350, 5, 24, 7
 FULL_OBS = FULL_EGO + FULL_KR * FULL_PT + FULL_KV * FULL_NB   # 1929 (App. D)
@@ -62,7 +62,8 @@ class Params(C.Structure):
             "edge_half_width")] + [("warmup_steps", C.c_int), ("max_steps", C.c_int)] + [
         (n, C.c_double) for n in (
             "spawn_goal_min", "spawn_goal_max", "spawn_v_min", "spawn_v_max", "spawn_spacing",
-            "park_x")] + [("spawn_tries", C.c_int), ("mu_table", (C.c_double * 3) * 4)]
+            "park_x")] + [("spawn_tries", C.c_int), ("mu_table", (C.c_double * 3) * 4)] + [
+        (n, C.c_double) for n in ("bike_theta_max", "bike_a_drive", "bike_a_brake")]
 
 
 class _Scene(C.Structure):
@@ -95,6 +96,7 @@ def lib():
         L.or_observe_full.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.or_reset.argtypes = [vp, vp, vp, vp, vp, u64, vp]
         L.or_place_agent.argtypes = [vp, vp, vp, i, d, d, d, d, d, d, i, i]
+        L.or_bicycle_agent.argtypes = [vp, vp, vp, d]
         L.or_sat.argtypes = [vp, vp, vp, vp, vp, vp]
         L.or_sat.restype = d
         L.or_nearest_lane.argtypes = [vp, vp, i, vp, vp, vp, vp]
@@ -218,6 +220,14 @@ class Oracle:
         k = lib().or_nearest_lane(C.byref(self.P), C.byref(self.S), int(w), _p(qq), C.byref(dist),
                                   C.byref(lat), _p(tan))
         return k, dist.value, lat.value, tan
+
+
+def bicycle_agent(f_row, action, dt=1.0 / 30.0, params=None):
+    """One kinematic-bicycle control step of one state row (modified in place)."""
+    P = params or default_params()
+    assert f_row.dtype == np.float64 and f_row.flags.c_contiguous and f_row.shape == (NF,)
+    act = np.ascontiguousarray(action, dtype=np.float64)
+    lib().or_bicycle_agent(C.byref(P), _p(f_row), _p(act), float(dt))
 
 
 # -- free functions on the pair geometry ---------------------------------------------------

@@ -92,6 +92,12 @@ void or_default_params(or_params* P) {
                                     {0.50, 0.45, 0.40},
                                     {0.30, 0.25, 0.20}};
     memcpy(P->mu_table, mu, sizeof(mu));
+    /* bicycle backend: the 30 degree steering limit of Sec. 4.4; accelerations
+     * from the vehicle's actuator limits (App. F): 2 x 600.7 N m and
+     * 2 x 1090.5 + 2 x 980.7 N m at r_w = 0.33 m on 1500 kg (a reading) */
+    P->bike_theta_max = M_PI / 6.0;
+    P->bike_a_drive = 2.0 * P->tau_drive / (P->wheel_r * P->mass);
+    P->bike_a_brake = 2.0 * (P->tau_brk_f + P->tau_brk_r) / (P->wheel_r * P->mass);
 }
 
 uint64_t or_splitmix64(uint64_t x) {
@@ -1011,6 +1017,27 @@ static int finite_state(const double* f) {
     return 1;
 }
 
+void or_bicycle_agent(const or_params* P, double* f, const double* act, double dt) {
+    double thr = clampd(act[0], 0.0, 1.0), brk = clampd(act[2], 0.0, 1.0);
+    double delta = P->bike_theta_max * clampd(act[1], -1.0, 1.0);
+    double lr = 0.5 * P->wheelbase;
+    double beta = atan(0.5 * tan(delta));
+    double psi = 2.0 * atan2(f[OR_F_QZ], f[OR_F_QW]);
+    double v = sqrt(f[OR_F_VX] * f[OR_F_VX] + f[OR_F_VY] * f[OR_F_VY]);
+    double a = P->bike_a_drive * thr - P->bike_a_brake * brk;
+    double v1 = fmax(0.0, v + a * dt);
+    double r = v1 / lr * sin(beta);
+    f[OR_F_PX] += v1 * cos(psi + beta) * dt;
+    f[OR_F_PY] += v1 * sin(psi + beta) * dt;
+    double psi1 = psi + r * dt;
+    f[OR_F_PZ] = -P->hard_z + (P->rest_len - P->mass * P->g / (4 * P->k_susp)) + P->wheel_r;
+    f[OR_F_QW] = cos(0.5 * psi1); f[OR_F_QX] = 0; f[OR_F_QY] = 0; f[OR_F_QZ] = sin(0.5 * psi1);
+    f[OR_F_VX] = v1 * cos(psi1 + beta); f[OR_F_VY] = v1 * sin(psi1 + beta); f[OR_F_VZ] = 0;
+    f[OR_F_WX] = 0; f[OR_F_WY] = 0; f[OR_F_WZ] = r;
+    for (int i = 0; i < 4; ++i) f[OR_F_S0 + i] = v1 / P->wheel_r;
+    f[OR_F_DELTA] = delta; f[OR_F_DDELTA] = 0;
+}
+
 int or_step(const or_params* P, const or_scene* S, double* F, int32_t* I, const double* actions, double dt,
             int substeps, uint64_t seed, int flags, or_out* out) {
     int A = S->agent_off[S->num_worlds];
@@ -1024,8 +1051,13 @@ int or_step(const or_params* P, const or_scene* S, double* F, int32_t* I, const 
         prev[2 * a] = F[(size_t)a * OR_NF + OR_F_PX];
         prev[2 * a + 1] = F[(size_t)a * OR_NF + OR_F_PY];
     }
-    for (int w = 0; w < S->num_worlds; ++w)
-        for (int s = 0; s < substeps; ++s) or_substep_world(P, S, w, F, I, actions, h);
+    if (flags & OR_FLAG_BICYCLE) {
+        for (int a = 0; a < A; ++a)
+            if (alive(I, a)) or_bicycle_agent(P, F + (size_t)a * OR_NF, actions + 3 * (size_t)a, dt);
+    } else {
+        for (int w = 0; w < S->num_worlds; ++w)
+            for (int s = 0; s < substeps; ++s) or_substep_world(P, S, w, F, I, actions, h);
+    }
     /* non-finite guard: such agents leave the world before events are computed */
     uint8_t* nonfin = (uint8_t*)calloc((size_t)A + 1, 1);
     for (int a = 0; a < A; ++a)

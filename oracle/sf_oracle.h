@@ -68,6 +68,7 @@ enum {
 /* step flags */
 #define OR_FLAG_INVINCIBLE 1
 #define OR_FLAG_AUTO_RESET 2
+#define OR_FLAG_BICYCLE    4   /* kinematic bicycle dynamics instead of the raycast vehicle */
 
 #define OR_K_AGENTS 8
 #define OR_L_POINTS 32
@@ -105,6 +106,10 @@ typedef struct {
     double spawn_spacing, park_x;
     int spawn_tries;
     double mu_table[4][3];        /* [precip][surface] */
+    /* kinematic bicycle backend (Sec. 4.4 vehicle dynamics ablation) */
+    double bike_theta_max;        /* steering limit, 30 degrees                                  */
+    double bike_a_drive;          /* full-throttle acceleration: both front drive torques / (r m) */
+    double bike_a_brake;          /* full-brake deceleration: all four brake torques / (r m)      */
 } or_params;
 
 /* Roads and agents of all worlds, as CSR (world -> polylines -> points). */
@@ -188,6 +193,20 @@ void or_place_agent(const or_params* P, double* F, int32_t* I, int a, double x, 
  * Parked / inactive agents get zeros and counts 0. */
 void or_observe_full(const or_params* P, const or_scene* S, const double* F, const int32_t* I, double* obs,
                      int32_t* n_road, int32_t* n_veh, int32_t* road_idx, int32_t* veh_idx);
+
+/* One control step of the kinematic bicycle for one agent's state row f (the
+ * drop-in backend of Sec. 4.4): front-wheel steer delta = theta_bike * steer,
+ * acceleration a = a_drive * throttle - a_brake * brake (both rectified), and
+ * with the centre of mass midway between the axles (l_r = WB / 2) the slip angle
+ * beta = atan(tan(delta) / 2); then
+ *   v'   = max(0, |v| + a dt)
+ *   x'   = x + v' cos(psi + beta) dt,   y' = y + v' sin(psi + beta) dt
+ *   psi' = psi + (v' / l_r) sin(beta) dt
+ * The row is rewritten level at the static ride height with velocity
+ * v' (cos(psi' + beta), sin(psi' + beta)), yaw rate (v' / l_r) sin(beta),
+ * rolling wheels v' / r_w and steer angle delta.  No suspension, contact
+ * response or lateral slip. */
+void or_bicycle_agent(const or_params* P, double* f, const double* act, double dt);
 
 /* --- pieces exported for the pins ------------------------------------------------- */
 /* 2-D SAT of two footprints; returns penetration depth (0 when separated), normal i->j. */
