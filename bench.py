@@ -131,12 +131,12 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- our arm
 def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, policy_seed=None, surrogate=None,
-                 pack=0, reset_frac=0.0, stage=0, split=0):
+                 pack=0, reset_frac=0.0, stage=0, split=0, dynamics=0):
     """Time `steps` replays of the captured step graph (policy forward + step
     when policy_seed is given) on the workload `name`."""
     scene = make_scene(name, rank)
     W = sf.World(scene, seed=4242 + rank, flags=sf.FLAG_AUTO_RESET, warps_per_block=nw, stream=stream,
-                 pack_agents=pack, stage_bytes=stage, split_step=split)
+                 pack_agents=pack, stage_bytes=stage, split_step=split, dynamics=dynamics)
     A = W.A
     dev = torch.device("cuda")
     policy = sf.init_policy(seed=policy_seed, stream=stream) if policy_seed is not None else None
@@ -371,6 +371,14 @@ def main_ours(args):
                                              stage=args.stage, split=args.split)
     if surr is not None:
         sf.sf_surrogate_destroy(surr)
+    bikes = {}
+    if not args.only and not args.skip_bicycle:
+        for name in ("256x16", "4096x16"):
+            if world > 1:
+                dist.barrier()
+            bikes[name] = run_workload(name, max(args.steps // 4, 50), args.warmup, rank, torch, sf, stream,
+                                       e2e=False, nw=args.nw, pack=args.pack, stage=args.stage, split=args.split,
+                                       dynamics=sf.DYN_BICYCLE)
     loops = {}
     if not args.only and not args.skip_paper_loop:
         for name in ("256x16", "4096x16"):
@@ -462,6 +470,13 @@ def main_ours(args):
                 **{"speedup_vs_physics_" + k: v["casps"] / (a256 if k == "256x16" else a4096)["casps"]
                    for k, v in asur.items()},
                 **{"gated_fraction_" + k: v["surr_frac"] for k, v in asur.items()}),
+            "bicycle": {k: {
+                "value": v["alive"] * world * len(v["ms"]) / (float(v["ms"].sum()) / 1e3), "unit": "CASPS",
+                "ms_per_step": float(v["ms"].mean()), "p50_ms": float(np.percentile(v["ms"], 50)),
+                "p99_ms": float(np.percentile(v["ms"], 99)), "agents": v["A"] * world, "autotune": v["tuned"],
+                "dynamics": "kinematic bicycle (Sec. 4.4 ablation backend): one update per control step, same "
+                            "events, rewards, observations and resets"}
+                for k, v in bikes.items()} or None,
             "paper_loop": {k: {
                 "value": v["A"] * world * len(v["ms"]) / (float(v["ms"].sum()) / 1e3), "unit": "CASPS",
                 "ms_per_step": float(v["ms"].mean()), "p50_ms": float(np.percentile(v["ms"], 50)),
@@ -571,6 +586,7 @@ def main():
     ap.add_argument("--skip-policy", action="store_true", help="no 4096x16 + policy leg")
     ap.add_argument("--skip-surrogate", action="store_true", help="no surrogate training / legs")
     ap.add_argument("--skip-paper-loop", action="store_true", help="no full-observation + late-fusion legs")
+    ap.add_argument("--skip-bicycle", action="store_true", help="no kinematic-bicycle legs")
     ap.add_argument("--surr-rows", type=int, default=10_000_000, help="surrogate training transitions")
     ap.add_argument("--surr-steps", type=int, default=60000, help="surrogate Adam steps")
     args = ap.parse_args()

@@ -115,8 +115,20 @@ typedef struct {
                               * (physics and events one warp per block of worlds,     *
                               * road queries one warp per agent, warps_per_block      *
                               * warps per query block); bit-identical results        */
-    int32_t reserved[5];     /* must be zero                                          */
+    int32_t dynamics;        /* SF_DYN_VEHICLE (default): the raycast spring-damper   *
+                              * vehicle over `substeps` substeps with footprint       *
+                              * contact; SF_DYN_BICYCLE: the kinematic bicycle of the *
+                              * paper's dynamics ablation (Sec. 4.4), one update per  *
+                              * control step: steer 30 deg x a1, acceleration         *
+                              * 2.43 m/s^2 x throttle - 8.37 m/s^2 x brake (the       *
+                              * vehicle's actuator limits), no reversing, slip angle  *
+                              * atan(tan(delta) / 2), no suspension, contact response *
+                              * or lateral slip.  Events, rewards, observations and  *
+                              * resets are the same for both                          */
+    int32_t reserved[4];     /* must be zero                                          */
 } sf_config;
+#define SF_DYN_VEHICLE 0
+#define SF_DYN_BICYCLE 1
 
 /* Worlds as CSR (host memory, read during sf_load_roads only).
  * World w holds agents [agent_off[w], agent_off[w+1]) (at most 32) and
@@ -157,7 +169,8 @@ typedef struct {
 /* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
  * (NULL = legacy default stream) on which every call of this handle enqueues
  * its work.  *out receives the handle.  Errors: SF_ERR_INVALID_ARG (NULL out,
- * nonzero reserved, pack_agents outside 0..32, bad stage_bytes or split_step), SF_ERR_CUDA (no usable device). */
+ * nonzero reserved, pack_agents outside 0..32, bad stage_bytes, split_step or dynamics), SF_ERR_CUDA (no usable
+ * device). */
 sf_status sf_create(const sf_config* cfg, void* cuda_stream, sf_handle* out);
 
 /* Release every device and host resource of h (synchronous).  NULL is a no-op. */
@@ -433,7 +446,9 @@ sf_status sf_surrogate_set_stats(sf_surrogate_handle s, const float* h_stats);
  * MLP's prediction instead of the substep loop.  With audit != 0 every agent
  * runs the physics instead and the largest distance between the surrogate's
  * and the physics' end position over gated agents is recorded (the periodic
- * audit).  Asynchronous. */
+ * audit).  Asynchronous.  SF_ERR_STATE on a handle with SF_DYN_BICYCLE dynamics
+ * (the surrogate stands in for the raycast vehicle only; so does
+ * sf_surrogate_collect). */
 sf_status sf_step_surrogate(sf_handle h, sf_surrogate_handle s, const float* d_actions, float dt, int substeps,
                             int audit);
 

@@ -127,6 +127,7 @@ WorldArgs make_args(sf_ctx* h) {
     a.sc = h->sc;
     a.flags = h->cfg.flags;
     a.seed = h->cfg.seed;
+    a.dynamics = h->cfg.dynamics;
     a.substeps = 1;
     a.h = 0.f;
     return a;
@@ -238,8 +239,12 @@ sf_status sf_create(const sf_config* cfg, void* cuda_stream, sf_handle* out) {
     *out = nullptr;
     sf_config c{};
     if (cfg) c = *cfg;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
         if (c.reserved[i] != 0) { g_create_error = "sf_create: reserved fields must be zero"; return SF_ERR_INVALID_ARG; }
+    if (c.dynamics != SF_DYN_VEHICLE && c.dynamics != SF_DYN_BICYCLE) {
+        g_create_error = "sf_create: dynamics must be SF_DYN_VEHICLE or SF_DYN_BICYCLE";
+        return SF_ERR_INVALID_ARG;
+    }
     if (c.split_step != 0 && c.split_step != 1) {
         g_create_error = "sf_create: split_step must be 0 or 1";
         return SF_ERR_INVALID_ARG;
@@ -1098,6 +1103,8 @@ sf_status sf_surrogate_collect(sf_handle h, sf_surrogate_handle s, const float* 
                                float* d_x, float* d_y, unsigned long long cap, unsigned long long* d_count) {
     if (!h || !s || !d_actions || !d_x || !d_y || !d_count) return SF_ERR_INVALID_ARG;
     if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_surrogate_collect: no roads loaded");
+    if (h->cfg.dynamics != SF_DYN_VEHICLE)
+        return fail(h, SF_ERR_STATE, "sf_surrogate_collect: the surrogate learns the raycast vehicle only");
     SurrBufs* b = surr_bufs(h);
     if (!b) return fail(h, SF_ERR_OOM, "sf_surrogate_collect: buffers");
     WorldArgs a = make_args(h);
@@ -1163,6 +1170,8 @@ sf_status sf_step_surrogate(sf_handle h, sf_surrogate_handle s, const float* d_a
                             int audit) {
     if (!h || !s || !d_actions) return SF_ERR_INVALID_ARG;
     if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_step_surrogate: no roads loaded");
+    if (h->cfg.dynamics != SF_DYN_VEHICLE)
+        return fail(h, SF_ERR_STATE, "sf_step_surrogate: the surrogate replaces the raycast vehicle only");
     if (!(dt > 0.f) || substeps < 1 || substeps > 64) return fail(h, SF_ERR_INVALID_ARG, "sf_step_surrogate: dt");
     SurrBufs* b = surr_bufs(h);
     if (!b) return fail(h, SF_ERR_OOM, "sf_step_surrogate: buffers");

@@ -45,6 +45,11 @@ constexpr float kZStar = (float)(0.25 + (0.3 - kMassD * 9.81 / (4.0 * 35000.0)) 
 constexpr float kPairCull2 = (float)(4.0 * (2.25 * 2.25 + 0.9 * 0.9));
 constexpr float kPairCullR = 4.8466483f;   // sqrt(kPairCull2), rounded up
 
+// ---------------------------------------------------------------- kinematic bicycle backend (Sec. 4.4)
+constexpr float kBikeThetaMax = 0.52359877559829887f;                          // 30 degrees
+constexpr float kBikeADrive = (float)(2.0 * 600.7 / (0.33 * 1500.0));          // both front drive torques / (r m)
+constexpr float kBikeABrake = (float)(2.0 * (1090.5 + 980.7) / (0.33 * 1500.0));  // all four brakes / (r m)
+
 // ---------------------------------------------------------------- rewards / events (App. G)
 constexpr float kGoalR = 3.0f, kWGoal = 45.0f, kWCollision = 6.0f, kWCrash = 10.0f, kWLaneForb = 20.0f;
 constexpr float kWProgress = 2.0f, kProgressClip = 2.0f;
@@ -203,6 +208,7 @@ struct WorldArgs {
     const uint8_t* mask;    // [A]      (reset mode)
     int num_worlds;
     int num_agents;
+    int dynamics;           // 0 raycast vehicle (substeps), 1 kinematic bicycle (one update per step)
     float h;                // substep length
     int substeps;
     int flags;

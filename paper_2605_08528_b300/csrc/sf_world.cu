@@ -1104,6 +1104,33 @@ __device__ __forceinline__ void pack_tables(const WorldArgs& args, const int4& p
 // App. F): action decode, substeps with footprint contact through the
 // exchange area every substep, the surrogate for gated agents, the
 // non-finite check; the post-step pose is published in E at the end
+// One control step of the kinematic bicycle (Sec. 4.4 ablation backend): the
+// front wheel steers delta = 30 deg x steer, the speed follows the rectified
+// throttle / brake accelerations and never reverses, and with the centre of
+// mass midway between the axles the slip angle is beta = atan(tan(delta) / 2):
+//   v' = max(0, |v| + a dt), p' = p + v' (cos, sin)(psi + beta) dt,
+//   psi' = psi + v' sin(beta) / (WB / 2) dt.
+// The chassis stays level at the static ride height; no suspension, contact
+// response or lateral slip.
+__device__ __forceinline__ void bicycle_step(Agent& A, const float* act, float dt) {
+    const float thr = clampf(act[0], 0.f, 1.f), brk = clampf(act[2], 0.f, 1.f);
+    const float delta = kBikeThetaMax * clampf(act[1], -1.f, 1.f);
+    const float beta = atanf(0.5f * tanf(delta));
+    const float psi = 2.f * atan2f(A.qz, A.qw);
+    const float v = sqrtf(A.vx * A.vx + A.vy * A.vy);
+    const float v1 = fmaxf(0.f, v + (kBikeADrive * thr - kBikeABrake * brk) * dt);
+    const float r = v1 / (0.5f * kWheelbase) * sinf(beta);
+    A.px += v1 * cosf(psi + beta) * dt;
+    A.py += v1 * sinf(psi + beta) * dt;
+    const float psi1 = psi + r * dt;
+    A.pz = kZStar;
+    A.qw = cosf(0.5f * psi1); A.qx = 0.f; A.qy = 0.f; A.qz = sinf(0.5f * psi1);
+    A.vx = v1 * cosf(psi1 + beta); A.vy = v1 * sinf(psi1 + beta); A.vz = 0.f;
+    A.wx = 0.f; A.wy = 0.f; A.wz = r;
+    A.s0 = A.s1 = A.s2 = A.s3 = v1 / kWheelR;
+    A.dl = delta; A.dd = 0.f;
+}
+
 __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot& c, int lane, Agent& A, bool& alive,
                                               bool& nonfin, float& prevx, float& prevy, float& hx, float& hy,
                                               Exch& E) {
@@ -1118,6 +1145,19 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
     }
     prevx = A.px; prevy = A.py;
     bool gated = false;
+    if (args.dynamics == 1) {   // the bicycle backend replaces the substeps (no contact response)
+        if (alive) bicycle_step(A, args.actions + 3 * (size_t)a, args.h * args.substeps);
+        if (alive && !finite_agent(A)) {
+            nonfin = true;
+            park_agent(A);
+            alive = false;
+            atomicOr(args.out.error_word, 1u);
+        }
+        heading_of(A.qw, A.qx, A.qy, A.qz, hx, hy);
+        publish(E, lane, A, hx, hy);
+        __syncwarp();
+        return;
+    }
     // contact candidates: the pairs of the world that can come within the cull
     // distance during this control step.  Lane i may move |v_i| T + 1 m (its
     // budget) before the set is rebuilt, so a pair farther apart at the start

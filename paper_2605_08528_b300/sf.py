@@ -26,6 +26,7 @@ NF, NI, OBS_DIM, K_AGENTS, L_POINTS = 25, 6, 320, 8, 32
 FULL_EGO, FULL_KR, FULL_PT, FULL_KV, FULL_NB = 11, 350, 5, 24, 7
 FULL_OBS_DIM = FULL_EGO + FULL_KR * FULL_PT + FULL_KV * FULL_NB   # 1929
 FLAG_INVINCIBLE, FLAG_AUTO_RESET, FLAG_RECORD_INDICES = 1, 2, 4
+DYN_VEHICLE, DYN_BICYCLE = 0, 1
 ACT_NONE, ACT_ELU, ACT_SILU, ACT_TANH = 0, 1, 2, 3
 
 
@@ -38,7 +39,7 @@ class SFError(RuntimeError):
 class sf_config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("flags", C.c_int32), ("warps_per_block", C.c_int32),
                 ("pack_agents", C.c_int32), ("stage_bytes", C.c_int32), ("split_step", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("dynamics", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class sf_roads(C.Structure):
@@ -127,8 +128,9 @@ def sf_version() -> str:
     return lib().sf_version().decode()
 
 
-def sf_create(seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0, stage_bytes=0, split_step=0):
-    cfg = sf_config(seed, flags, warps_per_block, pack_agents, stage_bytes, split_step)
+def sf_create(seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0, stage_bytes=0, split_step=0,
+              dynamics=DYN_VEHICLE):
+    cfg = sf_config(seed, flags, warps_per_block, pack_agents, stage_bytes, split_step, dynamics)
     h = C.c_void_p()
     st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().sf_create(C.byref(cfg), C.c_void_p(st), C.byref(h)))
@@ -238,11 +240,11 @@ class World:
     """A handle plus its roads, with torch views of the library-owned outputs."""
 
     def __init__(self, scene, seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0, stage_bytes=0,
-                 split_step=0):
+                 split_step=0, dynamics=DYN_VEHICLE):
         import torch
         self.torch = torch
         self.scene = scene
-        self.h = sf_create(seed, flags, warps_per_block, stream, pack_agents, stage_bytes, split_step)
+        self.h = sf_create(seed, flags, warps_per_block, stream, pack_agents, stage_bytes, split_step, dynamics)
         sf_load_roads(self.h, scene)
         self.A = sf_num_agents(self.h)
         self.W = sf_num_worlds(self.h)
