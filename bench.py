@@ -227,19 +227,21 @@ def lf_flops(n_road, n_veh):
         2 * 64 * 4 * len(n_road)
 
 
-def run_paper_loop(name, steps, warmup, rank, torch, sf, stream):
+def run_paper_loop(name, steps, warmup, rank, torch, sf, stream, nw=0, pack=0, stage=0, split=0):
     """The paper's control loop on the full observation: sf_observe_full ->
     late-fusion actor-critic (seeded random weights) -> sf_step, captured in one
     graph, auto-reset; plus the observation and network timed alone."""
     scene = make_scene(name, rank)
-    W = sf.World(scene, seed=4242 + rank, flags=sf.FLAG_AUTO_RESET, stream=stream)
+    W = sf.World(scene, seed=4242 + rank, flags=sf.FLAG_AUTO_RESET, stream=stream, warps_per_block=nw,
+                 pack_agents=pack, stage_bytes=stage, split_step=split)
     A = W.A
     dev = torch.device("cuda")
     lf = sf.sf_lf_create(stream)
     sf.sf_lf_set_params(lf, sf.init_lf(seed=4000 + rank))
     with torch.cuda.stream(stream):
         sf.sf_reset(W.h, torch.ones(A, dtype=torch.uint8, device=dev))
-        sf.sf_autotune(W.h, torch.zeros((A, 3), device=dev), iters=10)
+        if nw == 0:                                   # setup: pick the step's launch shape (state restored)
+            sf.sf_autotune(W.h, torch.zeros((A, 3), device=dev), iters=10)
         flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
         graph = sf.sf_graph_capture_lf(W.h, lf)
         for t in range(warmup):
@@ -331,6 +333,14 @@ def main_ours(args):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        if name.startswith("paper"):                  # profiling target: the paper loop alone
+            r = run_paper_loop(name[5:], args.steps, args.warmup, rank, torch, sf, stream, nw=args.nw, pack=args.pack,
+                               stage=args.stage, split=args.split)
+            if rank == 0:
+                print(json.dumps({"profile_run": name, "ms_per_step": float(r["ms"].mean()), "agents": r["A"],
+                                  "observation_ms": r["obs_ms"], "network_ms": r["lf_ms"]}))
+            clocks.stop()
+            return
         if name == "4096x16+policy":                  # profiling target: the policy + step graph alone
             res[name] = run_workload("4096x16", args.steps, args.warmup, rank, torch, sf, stream, e2e=False,
                                      nw=args.nw, policy_seed=4000, pack=args.pack, stage=args.stage,
@@ -575,8 +585,9 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--only", default=None, choices=list(WORKLOADS) + ["ragged1024", "4096x16+policy"],
-                    help="profiling: run one workload only")
+    ap.add_argument("--only", default=None,
+                    choices=list(WORKLOADS) + ["ragged1024", "4096x16+policy", "paper256x16", "paper4096x16"],
+                    help="profiling: run one workload only (paper*: the full-observation + late-fusion loop)")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling: no end-to-end leg")
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
     ap.add_argument("--nw", type=int, default=0, help="warps per block (1, 2, 4, 8; 0 = autotuned)")

@@ -2092,27 +2092,38 @@ __global__ void __launch_bounds__(32 * NW) full_obs_kernel(const FullObsArgs f) 
     const int4 wd = f.rd.world[w];   // first agent, agents, first point, points
     const int kend = wd.z + wd.w;
     int nr = 0;
-    for (int base = wd.z; base < kend && nr < kFullKR; base += 32) {
-        const int k = base + lane;
-        float4 m = make_float4(kInf, 0.f, 0.f, 0.f);
-        if (k < kend) m = __ldg(f.rd.mid + k);
-        const float dx = m.x - p.x, dy = m.y - p.y;
-        const bool in = dx * dx + dy * dy <= kFullR2;
-        const unsigned bal = __ballot_sync(kFull, in);
-        const int slot = nr + __popc(bal & ((1u << lane) - 1u));
-        if (in && slot < kFullKR) {
-            float bx, by, ux, uy;
-            to_ego(hx, hy, dx, dy, bx, by);
-            to_ego(hx, hy, m.z, m.w, ux, uy);
-            float* s = o + kFullRoad0 + kFullPt * slot;
-            s[0] = bx / 10.f;
-            s[1] = by / 10.f;
-            s[2] = (float)__ldg(f.rd.ptype + k) / 20.f;
-            s[3] = ux;
-            s[4] = uy;
-            if (f.road_idx) f.road_idx[(size_t)a * kFullKR + slot] = k;
+    // four chunks of 32 midpoints (and their types) are loaded before any is used: memory-level
+    // parallelism for a scan whose every step otherwise waits on one L2 round trip
+    for (int base = wd.z; base < kend && nr < kFullKR; base += 128) {
+        float4 m[4];
+        uint32_t ty[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = base + 32 * u + lane;
+            m[u] = k < kend ? __ldg(f.rd.mid + k) : make_float4(kInf, 0.f, 0.f, 0.f);
+            ty[u] = k < kend ? (uint32_t)__ldg(f.rd.ptype + k) : 0u;
         }
-        nr += __popc(bal);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = base + 32 * u + lane;
+            const float dx = m[u].x - p.x, dy = m[u].y - p.y;
+            const bool in = dx * dx + dy * dy <= kFullR2;
+            const unsigned bal = __ballot_sync(kFull, in);
+            const int slot = nr + __popc(bal & ((1u << lane) - 1u));
+            if (in && slot < kFullKR) {
+                float bx, by, ux, uy;
+                to_ego(hx, hy, dx, dy, bx, by);
+                to_ego(hx, hy, m[u].z, m[u].w, ux, uy);
+                float* s = o + kFullRoad0 + kFullPt * slot;
+                s[0] = bx / 10.f;
+                s[1] = by / 10.f;
+                s[2] = (float)ty[u] / 20.f;
+                s[3] = ux;
+                s[4] = uy;
+                if (f.road_idx) f.road_idx[(size_t)a * kFullKR + slot] = k;
+            }
+            nr += __popc(bal);
+        }
     }
     nr = min(nr, kFullKR);
     for (int i = kFullRoad0 + kFullPt * nr + lane; i < kFullVeh0; i += 32) o[i] = 0.f;
