@@ -120,18 +120,22 @@ __device__ __forceinline__ int agent_of_row(const int* rs, int r) {
     return lo;
 }
 
-// features of item row (tile * 128 + row) into v[0..7] (zeros past F or past the item)
-__device__ __forceinline__ void gather_row(const SetArgs& a, const int* rs, int a0, int total, int tile, int row,
-                                           float (&v)[8]) {
+// features of item row (tile * 128 + row) into v[0..7] (zeros past F, past the agent's filled
+// slots or past the item); returns whether the row is a filled slot
+__device__ __forceinline__ bool gather_row(const SetArgs& a, const int* rs, const int* cnt, int a0, int total,
+                                           int tile, int row, float (&v)[8]) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = 0.f;
     const int r = tile * 128 + row;
-    if (r >= total) return;
+    if (r >= total) return false;
     const int al = agent_of_row(rs, r);
-    const float* src = a.obs + (size_t)(a0 + al) * a.ld + a.off + (size_t)(r - rs[al]) * a.F;
+    const int slot = r - rs[al];
+    if (slot >= cnt[al]) return false;
+    const float* src = a.obs + (size_t)(a0 + al) * a.ld + a.off + (size_t)slot * a.F;
 #pragma unroll
     for (int i = 0; i < 8; ++i)
         if (i < a.F) v[i] = __ldg(src + i);
+    return true;
 }
 
 // Two CTAs per SM; even CTAs run the actor's encoder, odd ones the critic's.
@@ -141,7 +145,8 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
                                                          ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(sm);
     uint32_t* pool = reinterpret_cast<uint32_t*>(sm + kOffPool);
-    int* rs = reinterpret_cast<int*>(sm + kOffMisc);                       // [kG + 1] item row starts
+    int* rs = reinterpret_cast<int*>(sm + kOffMisc);                       // [kG + 1] item row starts (x8)
+    int* cnt = reinterpret_cast<int*>(sm + kOffMisc + 640);               // [kG] filled slots per agent
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kOffMisc + 192);     // [2]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffMisc + 208);
     float* sb2 = reinterpret_cast<float*>(sm + kOffMisc + 256);           // [96]
@@ -182,26 +187,27 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
     for (int item = cta; item < num_items && ok; item += ncta) {
         const int a0 = item * kG;
         const int na = min(kG, a.num_agents - a0);
-        if (warp == 0) {
-            int n = lane < na ? min(max(__ldg(a.count + a0 + lane), 0), a.K) : 0;
+        if (warp == 0) {   // each agent's slots take a multiple of 8 rows: an 8-row group is one agent's
+            const int n = lane < na ? min(max(__ldg(a.count + a0 + lane), 0), a.K) : 0;
+            int n8 = (n + 7) & ~7;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xFFFFFFFFu, n, o);
-                if (lane >= o) n += t;
+                const int t = __shfl_up_sync(0xFFFFFFFFu, n8, o);
+                if (lane >= o) n8 += t;
             }
-            rs[lane + 1] = n;
+            rs[lane + 1] = n8;
+            cnt[lane] = n;
             if (lane == 0) rs[0] = 0;
         }
         __syncthreads();
         const int total = rs[kG];
         const int ntiles = (total + 127) / 128;
         float v8[8];
-        gather_row(a, rs, a0, total, 0, tid >> 1, v8);
+        bool live = gather_row(a, rs, cnt, a0, total, 0, tid >> 1, v8);
         for (int t = 0; t < ntiles; ++t) {
             // ---- A1: 128 slots x 16 inputs (features, zeros, 1 at K 15 for the bias), two threads per row
             {
                 const int row = tid >> 1, half = tid & 1;
-                const bool live = t * 128 + row < total;
                 const uint4 w = half == 0 ? make_uint4(pack_bf16(v8[0], v8[1]), pack_bf16(v8[2], v8[3]),
                                                        pack_bf16(v8[4], v8[5]), pack_bf16(v8[6], v8[7]))
                                           : make_uint4(0u, 0u, 0u, live ? 0x3F800000u : 0u);
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
                 umma_bf16(tmem, smem_desc(sbase + kOffA1), smem_desc(sbase + kOffW1), kIdesc1, 0u);
                 umma_commit(&bar[0]);
             }
-            if (t + 1 < ntiles) gather_row(a, rs, a0, total, t + 1, tid >> 1, v8);   // in flight meanwhile
+            if (t + 1 < ntiles) live = gather_row(a, rs, cnt, a0, total, t + 1, tid >> 1, v8);   // in flight meanwhile
 
             // ---- epilogue 1: ELU -> bf16 rows of H1 (this warp: its 32 slots, 48 of the 96 columns)
             // every lane waits, then the warp reconverges (the tcgen05.ld that follows is warp-synchronous)
@@ -271,32 +277,31 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
                 tmem_hold(r[1]);
                 const int f = 32 * q + lane;
                 int s = agent_of_row(rs, rbase);         // agent holding the first row
-                int bnd = rs[s + 1];                     // row where it ends
+                int bnd = rs[s + 1];                     // row where its 8-row groups end
                 float m = -INFINITY;
 #pragma unroll
                 for (int c = 0; c < 2; ++c)
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
                         const int base = rbase + 32 * c + 8 * g;
-                        const uint32_t* v = r[c] + 8 * g;
-                        if (bnd >= base + 8) {           // warp-uniform: no agent boundary in these 8 rows
-                            const float m4 = fmaxf(fmaxf(__uint_as_float(v[0]), __uint_as_float(v[1])),
-                                                   fmaxf(__uint_as_float(v[2]), __uint_as_float(v[3])));
-                            const float n4 = fmaxf(fmaxf(__uint_as_float(v[4]), __uint_as_float(v[5])),
-                                                   fmaxf(__uint_as_float(v[6]), __uint_as_float(v[7])));
-                            m = fmaxf(m, fmaxf(m4, n4));
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                if (base + i == bnd) {   // warp-uniform
-                                    if (s < kG) atomicMax(&pool[s * kHid + f], fkey(m));
-                                    while (s < kG && rs[s + 1] <= base + i) ++s;
-                                    bnd = s < kG ? rs[s + 1] : 0x7FFFFFFF;
-                                    m = -INFINITY;
-                                }
-                                m = fmaxf(m, __uint_as_float(v[i]));
-                            }
+                        if (base >= bnd) {               // warp-uniform: the group starts the next agent
+                            if (s < kG) atomicMax(&pool[s * kHid + f], fkey(m));
+                            while (s < kG && rs[s + 1] <= base) ++s;
+                            bnd = s < kG ? rs[s + 1] : 0x7FFFFFFF;
+                            m = -INFINITY;
                         }
+                        if (s >= kG) continue;           // rows past the item
+                        const int valid = cnt[s] - (base - rs[s]);   // filled slots among these 8 rows
+                        const uint32_t* v = r[c] + 8 * g;
+                        float x[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) x[i] = __uint_as_float(v[i]);
+                        if (valid < 8) {                 // warp-uniform: the agent's last, partly filled group
+#pragma unroll
+                            for (int i = 1; i < 8; ++i) x[i] = i < valid ? x[i] : x[0];
+                        }
+                        m = fmaxf(m, fmaxf(fmaxf(fmaxf(x[0], x[1]), fmaxf(x[2], x[3])),
+                                           fmaxf(fmaxf(x[4], x[5]), fmaxf(x[6], x[7]))));
                     }
                 if (s < kG) atomicMax(&pool[s * kHid + f], fkey(m));   // continues past these rows
             }

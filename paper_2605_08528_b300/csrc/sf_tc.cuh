@@ -30,6 +30,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// the same with a suspend-time hint: the waiting thread sleeps (up to `ns`) instead of
+// spinning, leaving the issue slots to the other warps of the SM
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -134,6 +146,17 @@ template <int N>
 __device__ __forceinline__ void tmem_hold(uint32_t (&r)[N]) {
 #pragma unroll
     for (int i = 0; i < N; ++i) asm volatile("" : "+r"(r[i]));
+}
+
+// bounded wait that sleeps between polls (1 s of wall time at most)
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, unsigned* err, unsigned flag) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try_wait_sleep(bar, parity, 2000u)) return true;
+        if (global_ns() - t0 > kWaitNs) break;
+    }
+    if (err) atomicOr(err, flag);
+    return false;
 }
 
 // UMMA shared-memory descriptor of a K-major bf16 operand stored in 128-byte
