@@ -288,6 +288,50 @@ def run_paper_loop(name, steps, warmup, rank, torch, sf, stream, nw=0, pack=0, s
                 mean_road=float(n_road.mean()), mean_veh=float(n_veh.mean()))
 
 
+def run_ppo(name, iters, rank, torch, sf, stream):
+    """On-device PPO with the paper's hyperparameters (App. L: horizon 128, 16
+    minibatches, 5 epochs): per iteration one rollout (policy and value forward,
+    Gaussian sampling, the step) and one update (GAE and 80 minibatch steps),
+    timed with CUDA events; the training CASPS counts the rollout's agent-steps
+    over the whole iteration, as the paper's CASPS includes the PPO update."""
+    scene = make_scene(name, rank)
+    W = sf.World(scene, seed=4242 + rank, flags=sf.FLAG_AUTO_RESET, stream=stream)
+    A = W.A
+    with torch.cuda.stream(stream):
+        sf.sf_reset(W.h, torch.ones(A, dtype=torch.uint8, device="cuda"))
+        sf.sf_autotune(W.h, torch.zeros((A, 3), device="cuda"), iters=10)
+    actor = sf.init_policy(seed=5000 + rank, stream=stream, out_scale=0.1)
+    critic = sf.init_value(seed=6000 + rank, stream=stream)
+    cfg = sf.sf_ppo_default_config(init_log_std=-0.5, seed=77 + rank)
+    ppo = sf.sf_ppo_create(W.h, actor, critic, cfg)
+    sf.sf_ppo_collect(ppo)                        # warm-up iteration (buffers, kernel attributes)
+    sf.sf_ppo_update(ppo)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(iters)]
+    stats = []
+    torch.cuda.synchronize()
+    for i in range(iters):
+        ev[i][0].record(stream)
+        sf.sf_ppo_collect(ppo)
+        ev[i][1].record(stream)
+        sf.sf_ppo_update(ppo, want_stats=False)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    collect_ms = np.array([e[0].elapsed_time(e[1]) for e in ev])
+    update_ms = np.array([e[1].elapsed_time(e[2]) for e in ev])
+    for i in range(3):                            # learning statistics (untimed iterations)
+        sf.sf_ppo_collect(ppo)
+        stats.append(sf.sf_ppo_update(ppo).tolist())
+    log_std = sf.sf_ppo_log_std(ppo).tolist()
+    sf.sf_ppo_destroy(ppo)
+    sf.sf_mlp_destroy(actor)
+    sf.sf_mlp_destroy(critic)
+    W.close()
+    steps = A * cfg.horizon
+    return dict(A=A, horizon=cfg.horizon, collect_ms=float(collect_ms.mean()), update_ms=float(update_ms.mean()),
+                casps_train=steps / ((collect_ms + update_ms).mean() / 1e3),
+                casps_collect=steps / (collect_ms.mean() / 1e3), stats=stats, log_std=log_std)
+
+
 def cpu_baseline(name, seconds=12.0):
     """The FP64 oracle as it stands, single thread, on a bounded sample of the
     workload: the first worlds of the same scene, stepped until ~`seconds`."""
@@ -389,6 +433,11 @@ def main_ours(args):
             bikes[name] = run_workload(name, max(args.steps // 4, 50), args.warmup, rank, torch, sf, stream,
                                        e2e=False, nw=args.nw, pack=args.pack, stage=args.stage, split=args.split,
                                        dynamics=sf.DYN_BICYCLE)
+    ppo = None
+    if not args.only and not args.skip_ppo:
+        if world > 1:
+            dist.barrier()
+        ppo = run_ppo("256x16", 3, rank, torch, sf, stream)
     loops = {}
     if not args.only and not args.skip_paper_loop:
         for name in ("256x16", "4096x16"):
@@ -487,6 +536,16 @@ def main_ours(args):
                 "dynamics": "kinematic bicycle (Sec. 4.4 ablation backend): one update per control step, same "
                             "events, rewards, observations and resets"}
                 for k, v in bikes.items()} or None,
+            "ppo": None if ppo is None else {
+                "value": ppo["casps_train"] * world, "unit": "CASPS (training: rollout + PPO update)",
+                "workload": "256 worlds x 16 agents, App. L hyperparameters (horizon 128, 16 minibatches, 5 epochs, "
+                            "clip 0.15, gamma 0.99, lambda 0.98, adaptive KL 0.01); actor 320-512-512-3 and critic "
+                            "320-512-512-1 BF16 tcgen05 MLPs",
+                "rollout_ms": ppo["collect_ms"], "update_ms": ppo["update_ms"],
+                "rollout_casps": ppo["casps_collect"] * world,
+                "stats_columns": ["mean reward", "policy loss", "value loss", "kl", "lr", "grad norm"],
+                "stats_last_iterations": ppo["stats"], "log_std": ppo["log_std"],
+                "paper_context": "19,250 CASPS during PPO training at 256 x 16 (RTX PRO 6000, Isaac Sim/PhysX)"},
             "paper_loop": {k: {
                 "value": v["A"] * world * len(v["ms"]) / (float(v["ms"].sum()) / 1e3), "unit": "CASPS",
                 "ms_per_step": float(v["ms"].mean()), "p50_ms": float(np.percentile(v["ms"], 50)),
@@ -598,6 +657,7 @@ def main():
     ap.add_argument("--skip-surrogate", action="store_true", help="no surrogate training / legs")
     ap.add_argument("--skip-paper-loop", action="store_true", help="no full-observation + late-fusion legs")
     ap.add_argument("--skip-bicycle", action="store_true", help="no kinematic-bicycle legs")
+    ap.add_argument("--skip-ppo", action="store_true", help="no on-device PPO leg")
     ap.add_argument("--surr-rows", type=int, default=10_000_000, help="surrogate training transitions")
     ap.add_argument("--surr-steps", type=int, default=60000, help="surrogate Adam steps")
     args = ap.parse_args()

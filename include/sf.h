@@ -538,6 +538,104 @@ sf_status sf_lf_step_outputs(sf_handle h, sf_lf_outputs* out);
 sf_status sf_graph_capture_lf(sf_handle h, sf_lf_handle lf, const uint8_t* d_reset_mask, float dt, int substeps,
                               sf_graph_handle* out);
 
+/* ------------------------------------------------------------------------
+ * On-device PPO (SceneFactory App. L, Tab. app_ppo_hparams; the training
+ * loop of Alg. 1) with the tensor-core MLPs: an actor (320 inputs, 3 outputs:
+ * the mean of a diagonal Gaussian policy whose log standard deviation is a
+ * free 3-vector) and a critic (320 inputs, 1 output), both sf_mlp handles.
+ * A rollout of `horizon` control steps of the world handle (which must be
+ * created with SF_FLAG_AUTO_RESET so that done agents respawn) records per
+ * step and agent the 320-value observation, the sampled action (mean + sigma
+ * times a standard normal from a counter-hashed Box-Muller draw), its
+ * log-probability, the mean, the critic's value, the reward and the done
+ * flag.  An update computes GAE advantages and returns
+ * (delta_t = r_t + gamma (1 - d_t) V_{t+1} - V_t, A_t = delta_t +
+ * gamma lambda (1 - d_t) A_{t+1}), normalises the advantages over the
+ * rollout, and runs `epochs` x `minibatches` steps of: the clipped surrogate
+ * -min(ratio A, clip(ratio, 1 - clip, 1 + clip) A) + vf_coef (V - R)^2 -
+ * ent_coef H, its gradients through both MLPs, the mean Gaussian KL to the
+ * rollout policy (learning rate halved when KL > 2 kl_target, doubled when
+ * KL < kl_target / 2, within [1e-6, 1e-2]), gradient clipping to a global
+ * norm of max_grad_norm, and Adam.  Minibatch rows are an affine bijection
+ * of the rollout rows, drawn per epoch from the seed.  All of it runs on the
+ * world handle's stream; the MLPs must not be used elsewhere meanwhile.
+ * ---------------------------------------------------------------------- */
+typedef struct sf_ppo* sf_ppo_handle;
+typedef struct {
+    int32_t horizon;         /* rollout steps per update (App. L: 128)     */
+    int32_t minibatches;     /* minibatches per epoch (16)                  */
+    int32_t epochs;          /* learning epochs (5)                         */
+    float lr;                /* initial learning rate (2.09e-4)             */
+    float kl_target;         /* adaptive learning-rate KL target (0.01)     */
+    float gamma;             /* discount (0.99)                             */
+    float lam;               /* GAE lambda (0.98)                           */
+    float clip;              /* clip epsilon (0.15)                         */
+    float ent_coef;          /* entropy coefficient (3e-5)                  */
+    float vf_coef;           /* value loss coefficient (1.0)                */
+    float max_grad_norm;     /* gradient norm limit (1.0)                   */
+    float init_log_std;      /* initial log standard deviation (0)          */
+    float dt;                /* control step (1/30 s)                       */
+    int32_t substeps;        /* physics substeps per control step (4)       */
+    uint64_t seed;           /* sampling and minibatch draws                */
+} sf_ppo_config;
+
+/* The paper's values above. */
+void sf_ppo_default_config(sf_ppo_config* cfg);
+
+/* Rollout buffers (library-owned device memory, valid until sf_ppo_destroy),
+ * indexed [t][agent]: obs [T][A][320], actions and mean [T][A][3], logp,
+ * reward, advantage, ret [T][A] float32, done [T][A] uint8, value [T + 1][A]
+ * (the last row bootstraps GAE).  advantage / ret hold the last update's
+ * normalised advantages and returns. */
+typedef struct {
+    float* obs;
+    float* actions;
+    float* mean;
+    float* logp;
+    float* value;
+    float* reward;
+    uint8_t* done;
+    float* advantage;
+    float* ret;
+    int32_t horizon;
+    int32_t num_agents;
+    int32_t minibatch_rows;  /* floor(horizon * agents / minibatches) rounded down to a multiple of 8 */
+} sf_ppo_rollout;
+
+/* Allocates the rollout (horizon x agents rows) and the minibatch buffers.
+ * Errors: SF_ERR_INVALID_ARG (MLP shapes, configuration), SF_ERR_STATE (no
+ * roads), SF_ERR_OOM. */
+sf_status sf_ppo_create(sf_handle h, sf_mlp_handle actor, sf_mlp_handle critic, const sf_ppo_config* cfg,
+                        sf_ppo_handle* out);
+sf_status sf_ppo_destroy(sf_ppo_handle p);
+const char* sf_ppo_last_error(sf_ppo_handle p);
+
+/* One rollout of `horizon` steps from the world's current state.  Asynchronous. */
+sf_status sf_ppo_collect(sf_ppo_handle p);
+
+/* GAE and the epochs of minibatch updates on the last rollout.  h_stats (may
+ * be NULL; synchronous when given) [6] receives the rollout's mean reward per
+ * agent-step and, averaged over the minibatches, the policy loss, the value
+ * loss, the KL, then the current learning rate and the mean gradient norm
+ * before clipping.  Errors: SF_ERR_STATE (no rollout), SF_ERR_CUDA. */
+sf_status sf_ppo_update(sf_ppo_handle p, float* h_stats);
+
+/* The policy's log standard deviations [3] (synchronous). */
+sf_status sf_ppo_log_std(sf_ppo_handle p, float* h_log_std);
+sf_status sf_ppo_rollout_ptrs(sf_ppo_handle p, sf_ppo_rollout* out);
+
+/* The loss and its gradients for `rows` given rows (rows % 8 == 0, at most
+ * minibatch_rows) with the current parameters, without updating anything:
+ * d_obs [rows][320], d_small [rows][12] = (action 3, rollout mean 3, rollout
+ * log-probability, normalised advantage, return, 3 unused); d_mean [rows][3]
+ * and d_value [rows] receive the actor / critic outputs, d_dmean [rows][3] and
+ * d_dvalue [rows] the loss gradients with respect to them (any of these four
+ * may be NULL), h_out [6] the gradient with respect to the three log-stds,
+ * then the policy loss, the value loss (mean squared error, without vf_coef)
+ * and the mean KL to the last rollout's policy.  Synchronous. */
+sf_status sf_ppo_loss_grads(sf_ppo_handle p, const float* d_obs, const float* d_small, int rows, float* d_mean,
+                            float* d_value, float* d_dmean, float* d_dvalue, float* h_out);
+
 /* Number of agents and worlds of the loaded roads (0 before sf_load_roads). */
 int32_t sf_num_agents(sf_handle h);
 int32_t sf_num_worlds(sf_handle h);

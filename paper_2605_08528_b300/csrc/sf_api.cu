@@ -227,6 +227,8 @@ static LfBufs* lf_bufs(sf_ctx* h) {
     return b;
 }
 
+cudaStream_t sf_handle_stream(sf_handle h) { return h ? h->stream : nullptr; }
+
 extern "C" {
 
 const char* sf_version(void) { return "sf 0.1 (sm_103a)"; }

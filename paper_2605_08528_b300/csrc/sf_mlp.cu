@@ -206,11 +206,11 @@ int tile_for(int n) { return n >= 256 ? 256 : (n > 64 ? 128 : 64); }
 
 cudaError_t gemm(sf_mlp* m, const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, int M, int N, int Nb,
                  int K, int act, float* pre, float* out_f32, __nv_bfloat16* out_bf16, __nv_bfloat16* out_t, int ldc,
-                 int ldt) {
+                 int ldt, cudaStream_t st = nullptr, bool use_st = false) {
     GemmArgs g{};
     g.A = A; g.B = B; g.bias = bias; g.pre = pre; g.out_f32 = out_f32; g.out_bf16 = out_bf16; g.out_bf16_t = out_t;
     g.M = M; g.N = N; g.Nb = Nb; g.K = K; g.ldc = ldc; g.ldt = ldt; g.act = act; g.bn = tile_for(N); g.err = m->errw;
-    return sf_gemm_launch(g, m->stream);
+    return sf_gemm_launch(g, use_st ? st : m->stream);
 }
 
 cudaError_t ensure_batch(sf_mlp* m, int B) {
@@ -234,15 +234,87 @@ cudaError_t ensure_batch(sf_mlp* m, int B) {
 
 // forward of a batch already converted into x[0] (and xt[0] when training); the
 // last layer writes y_out [B][ldy] (m->y with its padded width when null)
-cudaError_t forward_core(sf_mlp* m, int B, bool train, float* y_out = nullptr, int ldy = 0) {
+cudaError_t forward_core(sf_mlp* m, int B, bool train, float* y_out = nullptr, int ldy = 0,
+                         cudaStream_t st = nullptr, bool use_st = false) {
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < m->L && e == cudaSuccess; ++l) {
         const bool last = l == m->L - 1;
         e = gemm(m, m->x[l], m->wb[l], m->b[l], B, m->dim[l + 1], m->dim[l + 1], m->ld[l], act_of(m, l),
                  train ? m->z[l] : nullptr, last ? (y_out ? y_out : m->y) : nullptr, last ? nullptr : m->x[l + 1],
-                 (train && !last) ? m->xt[l + 1] : nullptr, (last && y_out) ? ldy : m->ld[l + 1], B);
+                 (train && !last) ? m->xt[l + 1] : nullptr, (last && y_out) ? ldy : m->ld[l + 1], B, st, use_st);
     }
     return e;
+}
+
+// upstream gradient dy [B, n] (row stride ldy) -> dA [B, ld] with zero padding
+__global__ void dy_in_kernel(const float* __restrict__ dy, int B, int n, int ldy, int ld, float* __restrict__ dA) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)B * ld) return;
+    const int b = (int)(i / ld), c = (int)(i % ld);
+    dA[i] = c < n ? dy[(size_t)b * ldy + c] : 0.f;
+}
+
+// backward of the activations kept by the last training forward, from dA (holding dL/dy)
+cudaError_t backward_core(sf_mlp* m, int B, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    for (int l = m->L - 1; l >= 0 && e == cudaSuccess; --l) {
+        const int o = m->dim[l + 1], lo = m->ld[l + 1], li = m->ld[l], i = m->dim[l];
+        act_back_kernel<<<(unsigned)(((size_t)B * lo + 255) / 256), 256, 0, st>>>(m->dA, m->z[l], B, o, lo,
+                                                                                  act_of(m, l), m->dz, m->dzt);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = gemm(m, m->dzt, m->xt[l], nullptr, o, li, li, B, SF_ACT_NONE, nullptr, m->gwfull, nullptr, nullptr,
+                     li, 0, st, true);
+        if (e == cudaSuccess) {
+            compact_kernel<<<(unsigned)(((size_t)o * i + 255) / 256), 256, 0, st>>>(m->gwfull, o, i, li, m->gw[l]);
+            bias_grad_kernel<<<(o + 7) / 8, 256, 0, st>>>(m->dzt, B, o, m->gb[l]);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && l > 0)
+            e = gemm(m, m->dz, m->wbt[l], nullptr, B, li, li, lo, SF_ACT_NONE, nullptr, m->dA, nullptr, nullptr, li,
+                     0, st, true);
+    }
+    return e;
+}
+
+// sum of squares of n values added into *acc (one block reduction, one atomic per block)
+__global__ void sumsq_kernel(const float* __restrict__ g, int n, float* __restrict__ acc) {
+    __shared__ float red[8];
+    float sacc = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) sacc += g[i] * g[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xFFFFFFFFu, sacc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sacc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        if (threadIdx.x == 0) atomicAdd(acc, v);
+    }
+}
+
+// Adam with the learning rate and a gradient scale read from device memory
+__global__ void adam_dev_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                                float* __restrict__ v, int n, const float* __restrict__ lr_p,
+                                const float* __restrict__ scale_p, float b1, float b2, float eps, float c1, float c2,
+                                int out, int in, int ldi, int ldo, __nv_bfloat16* __restrict__ wb,
+                                __nv_bfloat16* __restrict__ wbt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i] * *scale_p;
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - *lr_p * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (wb) {
+        const int o = i / in, k = i % in;
+        const __nv_bfloat16 hb = __float2bfloat16_rn(wi);
+        wb[(size_t)o * ldi + k] = hb;
+        wbt[(size_t)k * ldo + o] = hb;
+    }
 }
 
 }  // namespace
@@ -497,6 +569,63 @@ sf_status sf_mlp_train_step(sf_mlp_handle m, const float* d_x, const float* d_t,
     }
     return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("sf_mlp_train_step: ") + cudaGetErrorString(e));
 }
+
+}  // extern "C"
+
+sf_status sf_mlp_forward_train_on(sf_mlp_handle m, cudaStream_t st, const float* d_x, int ldx, int batch, float* d_y,
+                                  int ldy) {
+    if (!m || !d_x || !d_y || batch < 8 || batch % 8 != 0 || ldx < m->dim[0] || ldy < m->dim[m->L])
+        return SF_ERR_INVALID_ARG;
+    cudaError_t e = ensure_batch(m, batch);
+    if (e != cudaSuccess) return mfail(m, SF_ERR_OOM, "batch buffers");
+    to_bf16_kernel<<<grid1((size_t)batch * m->ld[0]), 256, 0, st>>>(d_x, batch, m->dim[0], ldx, m->x[0], m->ld[0],
+                                                                    m->xt[0]);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = forward_core(m, batch, true, d_y, ldy, st, true);
+    return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("forward_train: ") + cudaGetErrorString(e));
+}
+
+sf_status sf_mlp_backward_on(sf_mlp_handle m, cudaStream_t st, const float* d_dy, int ldy, int batch) {
+    if (!m || !d_dy || batch < 8 || batch > m->cap || ldy < m->dim[m->L]) return SF_ERR_INVALID_ARG;
+    const int L = m->L;
+    dy_in_kernel<<<grid1((size_t)batch * m->ld[L]), 256, 0, st>>>(d_dy, batch, m->dim[L], ldy, m->ld[L], m->dA);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = backward_core(m, batch, st);
+    return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("backward: ") + cudaGetErrorString(e));
+}
+
+sf_status sf_mlp_grad_sumsq_on(sf_mlp_handle m, cudaStream_t st, float* d_acc) {
+    if (!m || !d_acc) return SF_ERR_INVALID_ARG;
+    for (int l = 0; l < m->L; ++l) {
+        const int n = m->dim[l + 1] * m->dim[l];
+        sumsq_kernel<<<std::min(256u, grid1(n)), 256, 0, st>>>(m->gw[l], n, d_acc);
+        sumsq_kernel<<<1, 256, 0, st>>>(m->gb[l], m->dim[l + 1], d_acc);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, cudaGetErrorString(e));
+}
+
+sf_status sf_mlp_adam_on(sf_mlp_handle m, cudaStream_t st, const float* d_lr, const float* d_scale) {
+    if (!m || !d_lr || !d_scale) return SF_ERR_INVALID_ARG;
+    ++m->adam_t;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - std::pow(b1, (float)m->adam_t), c2 = 1.f - std::pow(b2, (float)m->adam_t);
+    for (int l = 0; l < m->L; ++l) {
+        const int o = m->dim[l + 1], i = m->dim[l];
+        adam_dev_kernel<<<grid1((size_t)o * i), 256, 0, st>>>(m->w[l], m->gw[l], m->mw[l], m->vw[l], o * i, d_lr,
+                                                              d_scale, b1, b2, eps, c1, c2, o, i, m->ld[l],
+                                                              m->ld[l + 1], m->wb[l], m->wbt[l]);
+        adam_dev_kernel<<<grid1(o), 256, 0, st>>>(m->b[l], m->gb[l], m->mb[l], m->vb[l], o, d_lr, d_scale, b1, b2, eps,
+                                                  c1, c2, 0, 1, 0, 0, nullptr, nullptr);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, cudaGetErrorString(e));
+}
+
+int sf_mlp_out_dim(sf_mlp_handle m) { return m ? m->dim[m->L] : 0; }
+int sf_mlp_in_dim(sf_mlp_handle m) { return m ? m->dim[0] : 0; }
+
+extern "C" {
 
 sf_status sf_mlp_sync(sf_mlp_handle m) {
     if (!m) return SF_ERR_INVALID_ARG;

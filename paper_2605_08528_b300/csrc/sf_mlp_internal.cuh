@@ -14,3 +14,16 @@ sf_status sf_mlp_forward_on(sf_mlp_handle m, cudaStream_t stream, const float* d
 sf_status sf_lf_reserve(sf_lf_handle m, int batch);
 sf_status sf_lf_forward_on(sf_lf_handle m, cudaStream_t stream, const float* d_obs, const int32_t* d_n_road,
                            const int32_t* d_n_veh, int num_agents, float* d_mean, float* d_value, float* d_embed);
+
+// training pieces on an explicit stream (used by the PPO engine)
+// forward of `batch` rows keeping the activations the backward needs; outputs d_y [batch][ldy]
+sf_status sf_mlp_forward_train_on(sf_mlp_handle m, cudaStream_t stream, const float* d_x, int ldx, int batch,
+                                  float* d_y, int ldy);
+// weight and bias gradients of the last training forward from the upstream gradient d_dy [batch][ldy]
+sf_status sf_mlp_backward_on(sf_mlp_handle m, cudaStream_t stream, const float* d_dy, int ldy, int batch);
+// adds the sum of squares of every gradient into *d_acc
+sf_status sf_mlp_grad_sumsq_on(sf_mlp_handle m, cudaStream_t stream, float* d_acc);
+// Adam (0.9, 0.999, 1e-8) with learning rate *d_lr and gradients scaled by *d_scale
+sf_status sf_mlp_adam_on(sf_mlp_handle m, cudaStream_t stream, const float* d_lr, const float* d_scale);
+int sf_mlp_out_dim(sf_mlp_handle m);
+int sf_mlp_in_dim(sf_mlp_handle m);

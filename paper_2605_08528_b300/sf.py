@@ -99,6 +99,11 @@ def lib():
             "sf_lf_forward": ([vp, vp, vp, vp, C.c_int, vp, vp, vp], i32), "sf_lf_sync": ([vp], i32),
             "sf_step_lf": ([vp, vp, f32, C.c_int], i32), "sf_lf_step_outputs": ([vp, vp], i32),
             "sf_graph_capture_lf": ([vp, vp, vp, f32, C.c_int, vp], i32),
+            "sf_ppo_default_config": ([vp], None), "sf_ppo_create": ([vp, vp, vp, vp, vp], i32),
+            "sf_ppo_destroy": ([vp], i32), "sf_ppo_last_error": ([vp], C.c_char_p), "sf_ppo_collect": ([vp], i32),
+            "sf_ppo_update": ([vp, vp], i32), "sf_ppo_log_std": ([vp, vp], i32),
+            "sf_ppo_rollout_ptrs": ([vp, vp], i32),
+            "sf_ppo_loss_grads": ([vp, vp, vp, C.c_int, vp, vp, vp, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -395,12 +400,14 @@ def sf_graph_destroy(g):
     lib().sf_graph_destroy(g)
 
 
-def init_policy(seed=0, dims=(320, 512, 512, 3), stream=None):
-    """A policy MLP with seeded random (untrained) weights: ELU hidden layers, tanh actions."""
-    m = sf_mlp_create(list(dims), ACT_ELU, ACT_TANH, stream)
+def init_policy(seed=0, dims=(320, 512, 512, 3), stream=None, out_act=ACT_TANH, out_scale=1.0):
+    """A policy MLP with seeded random (untrained) weights: ELU hidden layers,
+    tanh actions (or out_act); the last layer's weights scaled by out_scale."""
+    m = sf_mlp_create(list(dims), ACT_ELU, out_act, stream)
     rng = np.random.default_rng(seed)
     for l, (i, o) in enumerate(zip(dims[:-1], dims[1:])):
-        sf_mlp_set_layer(m, l, rng.normal(0, 1 / np.sqrt(i), (o, i)), np.zeros(o))
+        w = rng.normal(0, 1 / np.sqrt(i), (o, i)) * (out_scale if l == len(dims) - 2 else 1.0)
+        sf_mlp_set_layer(m, l, w, np.zeros(o))
     return m
 
 
@@ -561,3 +568,77 @@ def init_lf(seed=0, log_std=-0.5):
     p = np.concatenate(out).astype(np.float32)
     assert p.size == sf_lf_num_params()
     return p
+
+
+# --------------------------------------------------------------------------- on-device PPO (App. L)
+class sf_ppo_config(C.Structure):
+    _fields_ = [("horizon", C.c_int32), ("minibatches", C.c_int32), ("epochs", C.c_int32), ("lr", C.c_float),
+                ("kl_target", C.c_float), ("gamma", C.c_float), ("lam", C.c_float), ("clip", C.c_float),
+                ("ent_coef", C.c_float), ("vf_coef", C.c_float), ("max_grad_norm", C.c_float),
+                ("init_log_std", C.c_float), ("dt", C.c_float), ("substeps", C.c_int32), ("seed", C.c_uint64)]
+
+
+class sf_ppo_rollout(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("obs", "actions", "mean", "logp", "value", "reward", "done", "advantage",
+                                          "ret")] + [("horizon", C.c_int32), ("num_agents", C.c_int32),
+                                                     ("minibatch_rows", C.c_int32)]
+
+
+def _pcheck(status, p):
+    if status != SF_OK:
+        raise SFError(status, lib().sf_ppo_last_error(p).decode() if p else "sf_ppo")
+    return status
+
+
+def sf_ppo_default_config(**overrides):
+    c = sf_ppo_config()
+    lib().sf_ppo_default_config(C.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def sf_ppo_create(h, actor, critic, cfg=None):
+    cfg = cfg if cfg is not None else sf_ppo_default_config()
+    p = C.c_void_p()
+    _check(lib().sf_ppo_create(h, actor, critic, C.byref(cfg), C.byref(p)), h)
+    return p
+
+
+def sf_ppo_destroy(p):
+    _pcheck(lib().sf_ppo_destroy(p), p)
+
+
+def sf_ppo_collect(p):
+    _pcheck(lib().sf_ppo_collect(p), p)
+
+
+def sf_ppo_update(p, want_stats=True):
+    """Returns (mean reward, policy loss, value loss, KL, learning rate, gradient norm) when want_stats."""
+    st = np.zeros(6, np.float32)
+    _pcheck(lib().sf_ppo_update(p, st.ctypes.data if want_stats else None), p)
+    return st if want_stats else None
+
+
+def sf_ppo_log_std(p):
+    s = np.zeros(3, np.float32)
+    _pcheck(lib().sf_ppo_log_std(p, s.ctypes.data), p)
+    return s
+
+
+def sf_ppo_rollout_ptrs(p) -> sf_ppo_rollout:
+    r = sf_ppo_rollout()
+    _pcheck(lib().sf_ppo_rollout_ptrs(p, C.byref(r)), p)
+    return r
+
+
+def sf_ppo_loss_grads(p, d_obs, d_small, rows, d_mean=None, d_value=None, d_dmean=None, d_dvalue=None):
+    out = np.zeros(6, np.float32)
+    _pcheck(lib().sf_ppo_loss_grads(p, _ptr(d_obs), _ptr(d_small), int(rows), _ptr(d_mean), _ptr(d_value),
+                                    _ptr(d_dmean), _ptr(d_dvalue), out.ctypes.data), p)
+    return out
+
+
+def init_value(seed=0, dims=(320, 512, 512, 1), stream=None):
+    """A critic MLP with seeded weights (ELU hidden layers, linear output)."""
+    return init_policy(seed=seed, dims=dims, stream=stream, out_act=ACT_NONE, out_scale=0.1)

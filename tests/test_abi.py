@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_binding_names_match_the_abi():
     for n in declared("sf.h"):
-        if n in ("sf_last_error", "sf_mlp_last_error", "sf_lf_last_error"):   # message accessors, used inside the binding
+        if n.endswith("last_error"):   # message accessors, used inside the binding
             continue
         assert hasattr(sf, n), n
 
