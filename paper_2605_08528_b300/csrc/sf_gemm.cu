@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "sf_gemm.cuh"
@@ -66,6 +67,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
     const int nk = (args.K + kBK - 1) / kBK;
+    // split K: CTA z of gridDim.z takes K tiles [kb, kb + nkz) and writes its partial sum to the workspace
+    const int z = blockIdx.z, nsplit = gridDim.z;
+    const int kb = (int)(((long long)nk * z) / nsplit), nkz = (int)(((long long)nk * (z + 1)) / nsplit) - kb;
+    float* const out_f32 = args.ws ? args.ws + (size_t)z * args.M * args.ldc : args.out_f32;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) { mbar_init(&S.full[s], 1); mbar_init(&S.empty[s], 1); }
@@ -86,9 +91,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
-        for (int kt = 0; kt < nk; ++kt) {
-            const int s = kt % kStages;
-            if (kt >= kStages && !mbar_wait(&S.empty[s], ((kt / kStages) & 1) ^ 1, args.err)) break;
+        for (int j = 0; j < nkz; ++j) {
+            const int s = j % kStages, kt = kb + j;
+            if (j >= kStages && !mbar_wait(&S.empty[s], ((j / kStages) & 1) ^ 1, args.err)) break;
             mbar_expect_tx(&S.full[s], kTxBytes);
             tma_load_2d(S.a[s], &map_a, kt * kBK, m0, &S.full[s]);
             tma_load_2d(S.b[s], &map_b, kt * kBK, n0, &S.full[s]);
@@ -97,15 +102,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- MMA issuer
         constexpr uint32_t idesc = instr_desc(kBM, BN);
         bool ok = true;
-        for (int kt = 0; kt < nk && ok; ++kt) {
-            const int s = kt % kStages;
-            ok = mbar_wait(&S.full[s], (kt / kStages) & 1, args.err);
+        for (int j = 0; j < nkz && ok; ++j) {
+            const int s = j % kStages;
+            ok = mbar_wait(&S.full[s], (j / kStages) & 1, args.err);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint64_t ad = smem_desc(smem_u32(S.a[s])), bd = smem_desc(smem_u32(S.b[s]));
 #pragma unroll
             for (int k = 0; k < kBK / 16; ++k)    // advance 16 bf16 (32 B) along K inside the swizzle atom
-                umma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kt > 0 || k > 0) ? 1u : 0u);
+                umma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (j > 0 || k > 0) ? 1u : 0u);
             umma_commit(&S.empty[s]);
         }
         umma_commit(&S.done);                  // arrives when every issued MMA has completed
@@ -117,7 +122,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int r = m0 + (warp & 3) * 32 + lane;   // TMEM lane slice of this warp
     // 16-byte vector stores when rows are aligned for them
-    const bool vf = args.ldc % 4 == 0 && ((reinterpret_cast<uintptr_t>(args.out_f32) |
+    const bool vf = args.ldc % 4 == 0 && ((reinterpret_cast<uintptr_t>(out_f32) |
                                           reinterpret_cast<uintptr_t>(args.pre)) & 15) == 0;
     const bool vb = args.ldc % 8 == 0 && (reinterpret_cast<uintptr_t>(args.out_bf16) & 15) == 0;
     if (have) {
@@ -155,15 +160,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             activate32(v, args.act);
-            if (args.out_f32) {
+            if (out_f32) {
                 if (full && vf) {
-                    float4* p4 = reinterpret_cast<float4*>(args.out_f32 + row);
+                    float4* p4 = reinterpret_cast<float4*>(out_f32 + row);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) p4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
-                        if (nb + i < args.N) args.out_f32[row + i] = v[i];
+                        if (nb + i < args.N) out_f32[row + i] = v[i];
                 }
             }
             if (args.out_bf16) {
@@ -200,8 +205,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     // a stage still holding TMA bytes after a timeout must land before exit
     if (threadIdx.x == 0 && !have) {
-        for (int s = 0; s < kStages && s < nk; ++s) {
-            const int last = ((nk - 1 - s) / kStages) * kStages + s;   // last K tile loaded into stage s
+        for (int s = 0; s < kStages && s < nkz; ++s) {
+            const int last = ((nkz - 1 - s) / kStages) * kStages + s;   // last K tile loaded into stage s
             mbar_wait(&S.full[s], (last / kStages) & 1, nullptr);
         }
     }
@@ -249,7 +254,9 @@ cudaError_t launch_bn(const GemmArgs& g, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid((g.N + BN - 1) / BN, (g.M + kBM - 1) / kBM);
+    const int nk = (g.K + kBK - 1) / kBK;
+    const int splits = g.ws ? std::max(1, std::min(g.splits, nk)) : 1;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + kBM - 1) / kBM, splits);
     tc_gemm_kernel<BN><<<grid, kThreads, smem, s>>>(ma, mb, g);
     return cudaGetLastError();
 }
@@ -259,6 +266,9 @@ cudaError_t launch_bn(const GemmArgs& g, cudaStream_t s) {
 cudaError_t sf_gemm_launch(const GemmArgs& g, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
     if (g.K <= 0 || g.K % 8 != 0 || g.Nb < 1) return cudaErrorInvalidValue;
+    // split-K partial sums are plain products: no bias, activation or extra outputs
+    if (g.ws && (g.bias || g.pre || g.out_bf16 || g.out_bf16_t || g.act != SF_ACT_NONE || g.splits < 1))
+        return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(g.A) | reinterpret_cast<uintptr_t>(g.B)) & 15) return cudaErrorInvalidValue;
     switch (g.bn) {
         case 64: return launch_bn<64>(g, s);

@@ -23,6 +23,11 @@ struct GemmArgs {
     int act;
     int bn;                   // tile width 64, 128 or 256
     unsigned* err;            // device error word (SF_GEMM_TIMEOUT)
+    // split K (optional): with ws set, `splits` CTAs share each output tile's K range and
+    // split z writes its partial product to ws + z * M * ldc (no bias, activation or other
+    // outputs); the caller sums the partials.  splits is capped at the number of K tiles.
+    int splits;
+    float* ws;
 };
 
 cudaError_t sf_gemm_launch(const GemmArgs& g, cudaStream_t s);

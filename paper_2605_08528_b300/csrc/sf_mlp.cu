@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -27,6 +28,7 @@
 namespace {
 
 constexpr int kMaxLayers = 8;
+constexpr int kSplitMax = 16;   // split-K partials of a weight gradient (K = the batch rows)
 
 int pad8(int x) { return (x + 7) & ~7; }
 
@@ -56,27 +58,54 @@ __global__ void to_bf16_vec8_kernel(const float* __restrict__ x, size_t n8, __nv
 }
 
 // x [B, n] f32 -> bf16 [B, ld] (zero padded) and optionally bf16^T [ld, B]
+// x [B, n] f32 (row stride ldx) -> bf16 y [B, ld] (zero padded) and, when yt is set, y^T [ld, B]:
+// 32 x 32 tiles through shared memory so that both the rows and the transpose are written
+// coalesced (block 32 x 8, grid (ld / 32, B / 32) rounded up)
 __global__ void to_bf16_kernel(const float* __restrict__ x, int B, int n, int ldx, __nv_bfloat16* __restrict__ y,
                                int ld, __nv_bfloat16* __restrict__ yt) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)B * ld) return;
-    const int b = (int)(i / ld), c = (int)(i % ld);
-    const __nv_bfloat16 v = __float2bfloat16_rn(c < n ? x[(size_t)b * ldx + c] : 0.f);
-    y[i] = v;
-    if (yt) yt[(size_t)c * B + b] = v;
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int c0 = blockIdx.x * 32, b0 = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int b = b0 + ty + 8 * j, c = c0 + tx;
+        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+        if (b < B && c < ld) {
+            v = __float2bfloat16_rn(c < n ? x[(size_t)b * ldx + c] : 0.f);
+            y[(size_t)b * ld + c] = v;
+        }
+        tile[ty + 8 * j][tx] = v;
+    }
+    if (!yt) return;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = c0 + ty + 8 * j, b = b0 + tx;
+        if (b < B && c < ld) yt[(size_t)c * B + b] = tile[tx][ty + 8 * j];
+    }
 }
-
-// dZ = dA * act'(Z), written as bf16 [B, ld] and bf16^T [ld, B]
+// dZ = dA * act'(Z) as bf16 [B, ld] and its transpose [ld, B] (tiled like to_bf16_kernel)
 __global__ void act_back_kernel(const float* __restrict__ dA, const float* __restrict__ Z, int B, int n, int ld,
                                 int act, __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)B * ld) return;
-    const int b = (int)(i / ld), c = (int)(i % ld);
-    float g = 0.f;
-    if (c < n) g = dA[(size_t)b * ld + c] * act_grad(Z[(size_t)b * ld + c], act);
-    const __nv_bfloat16 v = __float2bfloat16_rn(g);
-    dz[i] = v;
-    dzt[(size_t)c * B + b] = v;
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int c0 = blockIdx.x * 32, b0 = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int b = b0 + ty + 8 * j, c = c0 + tx;
+        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+        if (b < B && c < ld) {
+            float g = 0.f;
+            if (c < n) g = dA[(size_t)b * ld + c] * act_grad(Z[(size_t)b * ld + c], act);
+            v = __float2bfloat16_rn(g);
+            dz[(size_t)b * ld + c] = v;
+        }
+        tile[ty + 8 * j][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = c0 + ty + 8 * j, b = b0 + tx;
+        if (b < B && c < ld) dzt[(size_t)c * B + b] = tile[tx][ty + 8 * j];
+    }
 }
 
 // mean-squared-error gradient of the output: dY = 2 (y - t) / (B n), loss partial sums
@@ -133,6 +162,17 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
     }
 }
 
+// sum of the split-K partials [S][out][ldi] into the dense [out, in] weight gradient (fixed order)
+__global__ void reduce_compact_kernel(const float* __restrict__ ws, int S, int out, int in, int ldi,
+                                      float* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= out * in) return;
+    const size_t src = (size_t)(i / in) * ldi + (i % in), stride = (size_t)out * ldi;
+    float acc = 0.f;
+    for (int z = 0; z < S; ++z) acc += ws[z * stride + src];
+    dst[i] = acc;
+}
+
 // gather the fp32 weight gradient [out, ldi] into the dense [out, in] layout
 __global__ void compact_kernel(const float* __restrict__ src, int out, int in, int ldi, float* __restrict__ dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -151,6 +191,9 @@ __global__ void weights_to_bf16_kernel(const float* __restrict__ w, int out, int
 }
 
 unsigned grid1(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+// launch shape of the tiled [B, ld] kernels (to_bf16_kernel, act_back_kernel)
+dim3 tgrid(int B, int ld) { return dim3((unsigned)((ld + 31) / 32), (unsigned)((B + 31) / 32)); }
+const dim3 kTBlock(32, 8);
 
 }  // namespace
 
@@ -179,6 +222,7 @@ struct sf_mlp {
     float* dA = nullptr;                     // [cap, max ld] f32
     __nv_bfloat16 *dz = nullptr, *dzt = nullptr;
     float* gwfull = nullptr;                 // [max out, max ld] f32 (padded gradient)
+    float* ws = nullptr;                     // [kSplitMax][max out][max ld] f32 split-K partials of dW
     float* loss = nullptr;
     unsigned* errw = nullptr;
 };
@@ -254,19 +298,36 @@ __global__ void dy_in_kernel(const float* __restrict__ dy, int B, int n, int ldy
     dA[i] = c < n ? dy[(size_t)b * ldy + c] : 0.f;
 }
 
+// dW_l = dZ_l^T X_l [out, in] with K = B rows: the output has few tiles, so the K range is split over
+// up to kSplitMax CTAs per tile (enough to fill the GPU) and the partials summed in a fixed order
+cudaError_t weight_grad(sf_mlp* m, int l, int B, cudaStream_t st) {
+    const int o = m->dim[l + 1], li = m->ld[l], i = m->dim[l];
+    const int bn = tile_for(li);
+    const int tiles = ((o + 127) / 128) * ((li + bn - 1) / bn), nk = (B + 63) / 64;
+    const int S = std::max(1, std::min(std::min(kSplitMax, nk), 296 / std::max(1, tiles)));
+    GemmArgs g{};
+    g.A = m->dzt; g.B = m->xt[l]; g.M = o; g.N = li; g.Nb = li; g.K = B; g.ldc = li; g.act = SF_ACT_NONE;
+    g.bn = bn; g.err = m->errw;
+    if (S > 1) { g.ws = m->ws; g.splits = S; } else { g.out_f32 = m->gwfull; }
+    cudaError_t e = sf_gemm_launch(g, st);
+    if (e != cudaSuccess) return e;
+    if (S > 1)
+        reduce_compact_kernel<<<(unsigned)(((size_t)o * i + 255) / 256), 256, 0, st>>>(m->ws, S, o, i, li, m->gw[l]);
+    else
+        compact_kernel<<<(unsigned)(((size_t)o * i + 255) / 256), 256, 0, st>>>(m->gwfull, o, i, li, m->gw[l]);
+    return cudaGetLastError();
+}
+
 // backward of the activations kept by the last training forward, from dA (holding dL/dy)
 cudaError_t backward_core(sf_mlp* m, int B, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     for (int l = m->L - 1; l >= 0 && e == cudaSuccess; --l) {
         const int o = m->dim[l + 1], lo = m->ld[l + 1], li = m->ld[l], i = m->dim[l];
-        act_back_kernel<<<(unsigned)(((size_t)B * lo + 255) / 256), 256, 0, st>>>(m->dA, m->z[l], B, o, lo,
+        act_back_kernel<<<tgrid(B, lo), kTBlock, 0, st>>>(m->dA, m->z[l], B, o, lo,
                                                                                   act_of(m, l), m->dz, m->dzt);
         e = cudaGetLastError();
-        if (e == cudaSuccess)
-            e = gemm(m, m->dzt, m->xt[l], nullptr, o, li, li, B, SF_ACT_NONE, nullptr, m->gwfull, nullptr, nullptr,
-                     li, 0, st, true);
+        if (e == cudaSuccess) e = weight_grad(m, l, B, st);
         if (e == cudaSuccess) {
-            compact_kernel<<<(unsigned)(((size_t)o * i + 255) / 256), 256, 0, st>>>(m->gwfull, o, i, li, m->gw[l]);
             bias_grad_kernel<<<(o + 7) / 8, 256, 0, st>>>(m->dzt, B, o, m->gb[l]);
             e = cudaGetLastError();
         }
@@ -382,7 +443,7 @@ sf_status sf_mlp_forward_static(sf_mlp_handle m, const float* d_x, int ldx, int 
     float* y = reinterpret_cast<float*>(p);
     e = cudaMemsetAsync(base, 0, need, m->stream);
     if (e == cudaSuccess) {
-        to_bf16_kernel<<<grid1((size_t)batch * m->ld[0]), 256, 0, m->stream>>>(d_x, batch, m->dim[0], ldx, xs[0],
+        to_bf16_kernel<<<tgrid(batch, m->ld[0]), kTBlock, 0, m->stream>>>(d_x, batch, m->dim[0], ldx, xs[0],
                                                                                m->ld[0], nullptr);
         e = cudaGetLastError();
     }
@@ -432,6 +493,7 @@ sf_status sf_mlp_create(int num_layers, const int32_t* dims, int hidden_act, int
         if (e == cudaSuccess) e = malloc_zero(m, &m->vb[l], (size_t)o);
     }
     if (e == cudaSuccess) e = malloc_zero(m, &m->gwfull, (size_t)maxo * maxi);
+    if (e == cudaSuccess) e = malloc_zero(m, &m->ws, (size_t)kSplitMax * maxo * maxi);
     if (e != cudaSuccess) {
         for (void* p : m->allocs) cudaFree(p);
         delete m;
@@ -503,7 +565,7 @@ sf_status sf_mlp_forward_on(sf_mlp_handle m, cudaStream_t stream, const float* d
         const size_t n8 = (size_t)batch * m->ld[0] / 8;
         to_bf16_vec8_kernel<<<grid1(n8), 256, 0, stream>>>(d_x, n8, m->x[0]);
     } else {
-        to_bf16_kernel<<<grid1((size_t)batch * m->ld[0]), 256, 0, stream>>>(d_x, batch, m->dim[0], ldx, m->x[0],
+        to_bf16_kernel<<<tgrid(batch, m->ld[0]), kTBlock, 0, stream>>>(d_x, batch, m->dim[0], ldx, m->x[0],
                                                                             m->ld[0], nullptr);
     }
     e = cudaGetLastError();
@@ -520,7 +582,7 @@ sf_status sf_mlp_train_step(sf_mlp_handle m, const float* d_x, const float* d_t,
     cudaError_t e = ensure_batch(m, batch);
     if (e != cudaSuccess) return mfail(m, SF_ERR_OOM, "batch buffers");
     const int L = m->L, B = batch;
-    to_bf16_kernel<<<grid1((size_t)B * m->ld[0]), 256, 0, m->stream>>>(d_x, B, m->dim[0], m->dim[0], m->x[0], m->ld[0],
+    to_bf16_kernel<<<tgrid(B, m->ld[0]), kTBlock, 0, m->stream>>>(d_x, B, m->dim[0], m->dim[0], m->x[0], m->ld[0],
                                                                        m->xt[0]);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = forward_core(m, B, true);
@@ -530,25 +592,7 @@ sf_status sf_mlp_train_step(sf_mlp_handle m, const float* d_x, const float* d_t,
                                                                             m->dim[L], m->dA, m->loss);
         e = cudaGetLastError();
     }
-    for (int l = L - 1; l >= 0 && e == cudaSuccess; --l) {
-        const int o = m->dim[l + 1], lo = m->ld[l + 1], li = m->ld[l], i = m->dim[l];
-        act_back_kernel<<<grid1((size_t)B * lo), 256, 0, m->stream>>>(m->dA, m->z[l], B, o, lo, act_of(m, l), m->dz,
-                                                                      m->dzt);
-        e = cudaGetLastError();
-        // dW = dZ^T X  ([o, B] x [li, B]^T), padded gradient then compacted
-        if (e == cudaSuccess)
-            e = gemm(m, m->dzt, m->xt[l], nullptr, o, li, li, B, SF_ACT_NONE, nullptr, m->gwfull, nullptr, nullptr,
-                     li, 0);
-        if (e == cudaSuccess) {
-            compact_kernel<<<grid1((size_t)o * i), 256, 0, m->stream>>>(m->gwfull, o, i, li, m->gw[l]);
-            bias_grad_kernel<<<(o + 7) / 8, 256, 0, m->stream>>>(m->dzt, B, o, m->gb[l]);
-            e = cudaGetLastError();
-        }
-        // dX = dZ W ([B, lo] x [li, lo]^T) -> the next (lower) layer's dA
-        if (e == cudaSuccess && l > 0)
-            e = gemm(m, m->dz, m->wbt[l], nullptr, B, li, li, lo, SF_ACT_NONE, nullptr, m->dA, nullptr, nullptr, li,
-                     0);
-    }
+    if (e == cudaSuccess) e = backward_core(m, B, m->stream);
     if (e == cudaSuccess && update) {
         ++m->adam_t;
         const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -578,7 +622,7 @@ sf_status sf_mlp_forward_train_on(sf_mlp_handle m, cudaStream_t st, const float*
         return SF_ERR_INVALID_ARG;
     cudaError_t e = ensure_batch(m, batch);
     if (e != cudaSuccess) return mfail(m, SF_ERR_OOM, "batch buffers");
-    to_bf16_kernel<<<grid1((size_t)batch * m->ld[0]), 256, 0, st>>>(d_x, batch, m->dim[0], ldx, m->x[0], m->ld[0],
+    to_bf16_kernel<<<tgrid(batch, m->ld[0]), kTBlock, 0, st>>>(d_x, batch, m->dim[0], ldx, m->x[0], m->ld[0],
                                                                     m->xt[0]);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = forward_core(m, batch, true, d_y, ldy, st, true);
