@@ -581,8 +581,8 @@ sf_status sf_lf_forward_on(sf_lf_handle m, cudaStream_t st, const float* d_obs, 
         e = gemm(m, st, m->xego, m->w[n][0], m->b[n][0], A, 64, 16, SF_ACT_ELU, nullptr, m->he1[n], 64);
         if (e == cudaSuccess) e = gemm(m, st, m->he1[n], m->w[n][1], m->b[n][1], A, 64, 64, SF_ACT_ELU, nullptr, m->x[n], 256);
     }
-    int sms = 148;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    int sms = 148, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (int g = 0; g < 2 && e == cudaSuccess; ++g) {
         SetArgs sa{};
         sa.obs = d_obs; sa.ld = kObs;
