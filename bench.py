@@ -130,6 +130,18 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- our arm
+def combine_over_ranks(t_seconds, e2e_seconds, alive, steps, e2e_steps, dist, torch, device):
+    """Whole-job CASPS over all ranks: the agents every rank stepped, summed,
+    over the slowest rank's time (the max over ranks of each timed region).
+    dist is torch.distributed (initialised) or None for one rank."""
+    tt = torch.tensor([t_seconds, e2e_seconds], dtype=torch.float64, device=device)
+    n = torch.tensor([float(alive)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(n[0]) * steps / float(tt[0]), float(n[0]) * e2e_steps / float(tt[1])
+
+
 def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, policy_seed=None, surrogate=None,
                  pack=0, reset_frac=0.0, stage=0, split=0, dynamics=0):
     """Time `steps` replays of the captured step graph (policy forward + step
@@ -453,15 +465,8 @@ def main_ours(args):
 
     def agg(name):
         r = res[name]
-        t = float(r["ms"].sum()) / 1e3
-        tt = torch.tensor([t, r["e2e_wall"]], dtype=torch.float64, device="cuda")
-        n = torch.tensor([r["alive"]], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dist.all_reduce(n, op=dist.ReduceOp.SUM)
-        t, e2e = float(tt[0]), float(tt[1])
-        casps = float(n[0]) * args.steps / t
-        e2e_casps = float(n[0]) * r["e2e_steps"] / e2e
+        casps, e2e_casps = combine_over_ranks(float(r["ms"].sum()) / 1e3, r["e2e_wall"], r["alive"], args.steps,
+                                              r["e2e_steps"], dist if world > 1 else None, torch, "cuda")
         ab = algorithmic_bytes(r["scene"])
         mean_s = float(r["ms"].mean()) / 1e3
         ach = ab["total"] / mean_s / 1e9
