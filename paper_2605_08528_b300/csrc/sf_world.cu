@@ -359,8 +359,15 @@ __device__ __forceinline__ float penalty(float alpha, float tau, float pmax) {
 }
 
 // exchange area of one world: footprints, velocities, goals of its agents
+constexpr int kMaxPairs = 64;   // candidate contact pairs of a warp handled pair-parallel per substep
 struct Exch {
     float px[32], py[32], hx[32], hy[32], vx[32], vy[32], dx[32], dy[32], gx[32], gy[32];
+    // one substep's candidate contact pairs (lo < hi): per lane the first pair id and the mask of its
+    // partners above it; the pair list and each pair's force (fx, fy, tz)
+    int poff[32];
+    uint32_t pmask[32];
+    int plist[kMaxPairs];
+    float4 pf[kMaxPairs];
 };
 
 __device__ __forceinline__ void publish(Exch& E, int lane, const Agent& A, float hx, float hy) {
@@ -1188,7 +1195,45 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
         if (!wide && __any_sync(kFull, alive && A.dpx * A.dpx + A.dpy * A.dpy > budget * budget)) wide = true;
         const uint32_t cand = (wide ? 0xFFFFFFFFu : near) & alive_bits;
         float fcx = 0.f, fcy = 0.f, tcz = 0.f;
-        if (alive) {
+        // candidate pairs (lo < hi) of the world, compacted over the warp: each pair's force is
+        // computed once, by one lane, then every lane sums its partners in ascending order (the
+        // order, and so the rounding, of a per-lane loop over its partners)
+        const uint32_t wmask = (n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u)) << base;
+        const uint32_t above = lane < 31 ? (0xFFFFFFFFu << (lane + 1)) : 0u;
+        const uint32_t mine = alive ? (cand & above & wmask) : 0u;
+        const int pc = __popc(mine);
+        int poff = pc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, poff, o);
+            if (lane >= o) poff += t;
+        }
+        const int npairs = __shfl_sync(kFull, poff, 31);
+        poff -= pc;
+        if (npairs <= kMaxPairs) {
+            E.poff[lane] = poff;
+            E.pmask[lane] = mine;
+            for (uint32_t mm = mine, k = (uint32_t)poff; mm; mm &= mm - 1u, ++k) E.plist[k] = (lane << 8) | (__ffs(mm) - 1);
+            __syncwarp();
+            for (int p = lane; p < npairs; p += 32) {
+                const int lo = E.plist[p] >> 8, hi = E.plist[p] & 0xFF;
+                float fx, fy, tz;
+                pair_force(E.px[lo], E.py[lo], E.dx[lo], E.dy[lo], E.hx[lo], E.hy[lo], E.vx[lo], E.vy[lo],
+                           E.px[hi], E.py[hi], E.dx[hi], E.dy[hi], E.hx[hi], E.hy[hi], E.vx[hi], E.vy[hi],
+                           fx, fy, tz);
+                E.pf[p] = make_float4(fx, fy, tz, 0.f);
+            }
+            __syncwarp();
+            if (alive) {
+                for (int j = base; j < base + n; ++j) {
+                    if (j == lane || !((cand >> j) & 1u)) continue;
+                    const int lo = min(lane, j), hi = max(lane, j);
+                    const float4 f = E.pf[E.poff[lo] + __popc(E.pmask[lo] & ((1u << hi) - 1u))];
+                    if (lane == lo) { fcx -= f.x; fcy -= f.y; } else { fcx += f.x; fcy += f.y; }
+                    tcz += f.z;
+                }
+            }
+        } else if (alive) {   // many candidates (all pairs of a crowded world): a loop per lane
             for (int j = base; j < base + n; ++j) {
                 if (j == lane || !((cand >> j) & 1u)) continue;
                 const int lo = min(lane, j), hi = max(lane, j);
