@@ -610,6 +610,59 @@ __device__ __forceinline__ Rows rows_covering(const WRoads& g, float qx, float q
     return w;
 }
 
+// The records of the cells in columns cx0..cx1 of rows cy0..cy1, in batches of
+// 32 (lane t takes one record of each batch): the rows' bounds are read in one
+// step (one row per lane, up to 32 rows at a time) and their ranges flattened
+// by a prefix sum, so a batch can span rows, and the next batch's loads are
+// issued before `body` runs on the current one.  body(sg, m, i, has) is called
+// by every lane, `has` false past the last record; the queries built on it
+// keep the order-independent answers (a minimum, a set of smallest keys, an
+// any), so the batching does not change them.
+template <class F>
+__device__ __forceinline__ void scan_cells(const WRoads& v, const Rows& w, int lane, F&& body) {
+    if (w.cx0 > w.cx1) return;
+    for (int r0 = w.cy0; r0 <= w.cy1; r0 += 32) {
+        int s = 0, n = 0;
+        if (r0 + lane <= w.cy1) {
+            const int row = (r0 + lane) * v.nx;
+            s = v.coff[row + w.cx0];
+            n = v.coff[row + w.cx1 + 1] - s;
+        }
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int shift = s - (incl - n);          // record index of flattened j in this row: j + shift
+        // record index of flattened candidate j: its row is the number of rows
+        // whose inclusive end is <= j (incl is non-decreasing over the lanes)
+        auto locate = [&](int j) {
+            int r = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1)
+                if (__shfl_sync(kFull, incl, r + st - 1) <= j) r += st;
+            return j + __shfl_sync(kFull, shift, r);
+        };
+        int i = locate(lane);
+        bool has = lane < total;
+        float4 sg = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t m = 0u;
+        if (has) { sg = v.seg[i]; m = v.info[i]; }
+        for (int base = 0; base < total; base += 32) {
+            const int jn = base + 32 + lane;
+            const int in = locate(jn);
+            const bool hn = jn < total;
+            float4 sgn = make_float4(0.f, 0.f, 0.f, 0.f);
+            uint32_t mn = 0u;
+            if (hn) { sgn = v.seg[in]; mn = v.info[in]; }
+            body(sg, m, i, has);
+            sg = sgn; m = mn; i = in; has = hn;
+        }
+    }
+}
+
 // tangent, lateral offset and distance of the nearest lane segment from its key
 __device__ __forceinline__ Lane lane_of(const WRoads& v, unsigned long long best, float qx, float qy, float gx,
                                         float gy) {
@@ -662,28 +715,42 @@ __device__ Lane coop_nearest_lane(const WRoads& v, float qx, float qy, float gx,
         const float Rl = S - kSegReach;
         const float lim = w.all ? kInf : Rl * Rl * (1.f - 1e-5f);
         best = kKeyInf;
-        if (w.cx0 <= w.cx1)
-            for (int cy = w.cy0; cy <= w.cy1; ++cy) {
-                const int row = cy * v.nx;
-                const int s = v.coff[row + w.cx0], e = v.coff[row + w.cx1 + 1];
-                for (int i = s + lane; i < e; i += 32) {
-                    const uint32_t m = v.info[i];
-                    if (!(m & kInfoSegNext) || !(m & (kInfoLane | (edges ? kInfoEdge : 0u)))) continue;
-                    const float4 sg = v.seg[i];
-                    const float d0 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
-                    if (m & kInfoLane) {
-                        if (d0 < lim) best = umin64(best, rkey(d0, m, i));
-                    } else if (forb_touch(sg, d0, qx, qy, hx, hy)) {
-                        f = true;
-                    }
-                }
+        const uint32_t want = kInfoLane | (edges ? kInfoEdge : 0u);
+        scan_cells(v, w, lane, [&](const float4& sg, uint32_t m, int i, bool has) {
+            if (!has || !(m & kInfoSegNext) || !(m & want)) return;
+            const float d0 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
+            if (m & kInfoLane) {
+                if (d0 < lim) best = umin64(best, rkey(d0, m, i));
+            } else if (forb_touch(sg, d0, qx, qy, hx, hy)) {
+                f = true;
             }
+        });
         best = warp_min64(best);
         if (edges) { *forb = __any_sync(kFull, f); edges = false; }
         if (best != kKeyInf || w.all) break;
         S = Rl * kGrow + kSegReach;
     }
     return lane_of(v, best, qx, qy, gx, gy);
+}
+
+// Candidate keys (kKeyInf: none) of a batch into the warp's buffer; every 32
+// collected are merged into the running 32 smallest, whose largest then tightens
+// the admission threshold.
+__device__ __forceinline__ void collect32(unsigned long long key, int lane, unsigned lt, unsigned long long* buf,
+                                          int& cnt, unsigned long long& run, unsigned long long& thr) {
+    const unsigned mk = __ballot_sync(kFull, key != kKeyInf);
+    if (key != kKeyInf) buf[cnt + __popc(mk & lt)] = key;
+    cnt += __popc(mk);
+    __syncwarp();
+    if (cnt >= 32) {
+        run = merge32(run, buf[lane], lane);
+        const unsigned long long rest = lane < cnt - 32 ? buf[32 + lane] : kKeyInf;
+        __syncwarp();
+        if (lane < cnt - 32) buf[lane] = rest;
+        cnt -= 32;
+        thr = umin64(thr, shfl64(run, 31));
+        __syncwarp();
+    }
 }
 
 // the 32 nearest road points (all types), exact; lane t returns the t-th key.
@@ -698,34 +765,15 @@ __device__ unsigned long long coop_knn32(const WRoads& v, float qx, float qy, fl
         unsigned long long thr = w.all ? kKeyInf : key_of(R * R * (1.f - 1e-5f), 0);
         run = kKeyInf;
         int cnt = 0;
-        if (w.cx0 <= w.cx1)
-            for (int cy = w.cy0; cy <= w.cy1; ++cy) {
-                const int row = cy * v.nx;
-                const int s = v.coff[row + w.cx0], e = v.coff[row + w.cx1 + 1];
-                for (int base = s; base < e; base += 32) {
-                    const int i = base + lane;
-                    unsigned long long key = kKeyInf;
-                    if (i < e) {
-                        const float4 P = v.seg[i];
-                        const float dx = P.x - qx, dy = P.y - qy;
-                        key = rkey(dx * dx + dy * dy, v.info[i], i);
-                        if (key >= thr) key = kKeyInf;
-                    }
-                    const unsigned m = __ballot_sync(kFull, key != kKeyInf);
-                    if (key != kKeyInf) buf[cnt + __popc(m & lt)] = key;
-                    cnt += __popc(m);
-                    __syncwarp();
-                    if (cnt >= 32) {
-                        run = merge32(run, buf[lane], lane);
-                        const unsigned long long rest = lane < cnt - 32 ? buf[32 + lane] : kKeyInf;
-                        __syncwarp();
-                        if (lane < cnt - 32) buf[lane] = rest;
-                        cnt -= 32;
-                        thr = umin64(thr, shfl64(run, 31));
-                        __syncwarp();
-                    }
-                }
+        scan_cells(v, w, lane, [&](const float4& P, uint32_t m, int i, bool has) {
+            unsigned long long key = kKeyInf;
+            if (has) {
+                const float dx = P.x - qx, dy = P.y - qy;
+                key = rkey(dx * dx + dy * dy, m, i);
+                if (key >= thr) key = kKeyInf;
             }
+            collect32(key, lane, lt, buf, cnt, run, thr);
+        });
         if (cnt > 0) {
             const unsigned long long c = lane < cnt ? buf[lane] : kKeyInf;
             run = merge32(run, c, lane);
@@ -756,43 +804,23 @@ __device__ Lane coop_point_queries(const WRoads& v, float qx, float qy, float gx
     unsigned long long run = kKeyInf, best = kKeyInf;
     bool f = false;
     int cnt = 0;
-    if (w.cx0 <= w.cx1)
-        for (int cy = w.cy0; cy <= w.cy1; ++cy) {
-            const int row = cy * v.nx;
-            const int s = v.coff[row + w.cx0], e = v.coff[row + w.cx1 + 1];
-            for (int base = s; base < e; base += 32) {
-                const int i = base + lane;
-                unsigned long long k = kKeyInf;
-                if (i < e) {
-                    const float4 sg = v.seg[i];
-                    const uint32_t m = v.info[i];
-                    const float dx = sg.x - qx, dy = sg.y - qy;
-                    k = rkey(dx * dx + dy * dy, m, i);
-                    if (k >= thr) k = kKeyInf;
-                    if ((m & kInfoSegNext) && (m & (kInfoLane | kInfoEdge))) {
-                        const float d0 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
-                        if (m & kInfoLane) {
-                            if (d0 < lim_l) best = umin64(best, rkey(d0, m, i));
-                        } else if (forb_touch(sg, d0, qx, qy, hx, hy)) {
-                            f = true;
-                        }
-                    }
-                }
-                const unsigned mk = __ballot_sync(kFull, k != kKeyInf);
-                if (k != kKeyInf) buf[cnt + __popc(mk & lt)] = k;
-                cnt += __popc(mk);
-                __syncwarp();
-                if (cnt >= 32) {
-                    run = merge32(run, buf[lane], lane);
-                    const unsigned long long rest = lane < cnt - 32 ? buf[32 + lane] : kKeyInf;
-                    __syncwarp();
-                    if (lane < cnt - 32) buf[lane] = rest;
-                    cnt -= 32;
-                    thr = umin64(thr, shfl64(run, 31));
-                    __syncwarp();
+    scan_cells(v, w, lane, [&](const float4& sg, uint32_t m, int i, bool has) {
+        unsigned long long k = kKeyInf;
+        if (has) {
+            const float dx = sg.x - qx, dy = sg.y - qy;
+            k = rkey(dx * dx + dy * dy, m, i);
+            if (k >= thr) k = kKeyInf;
+            if ((m & kInfoSegNext) && (m & (kInfoLane | kInfoEdge))) {
+                const float d0 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
+                if (m & kInfoLane) {
+                    if (d0 < lim_l) best = umin64(best, rkey(d0, m, i));
+                } else if (forb_touch(sg, d0, qx, qy, hx, hy)) {
+                    f = true;
                 }
             }
         }
+        collect32(k, lane, lt, buf, cnt, run, thr);
+    });
     if (cnt > 0) {
         const unsigned long long c = lane < cnt ? buf[lane] : kKeyInf;
         run = merge32(run, c, lane);
@@ -817,17 +845,27 @@ __device__ float coop_edge_ray(const WRoads& v, float px, float py, float vx, fl
     const float speed = sqrtf(vx * vx + vy * vy);
     const float reach2 = (kEdgeHorizon + kSegReach) * (kEdgeHorizon + kSegReach);
     float t_best = kInf;
-    for (int i = lane; i < v.ecnt; i += 32) {
-        const float4 sg4 = v.edge[i];
+    auto hit = [&](const float4& sg4) {
         const float apx = sg4.x - px, apy = sg4.y - py;
-        if (apx * apx + apy * apy > reach2) continue;
+        if (apx * apx + apy * apy > reach2) return;
         const float exx = sg4.z - sg4.x, eyy = sg4.w - sg4.y;
         const float den = cross2(vx, vy, exx, eyy);
-        if (den == 0.f) continue;
+        if (den == 0.f) return;
         const float nt = cross2(apx, apy, exx, eyy), ns = cross2(apx, apy, vx, vy);
         const bool ok = den > 0.f ? (nt >= 0.f && ns >= 0.f && ns <= den && speed * nt <= kEdgeHorizon * den)
                                   : (nt <= 0.f && ns <= 0.f && ns >= den && speed * nt >= kEdgeHorizon * den);
         if (ok) t_best = fminf(t_best, nt / den);
+    };
+    // four segments per lane in flight: the loads are issued before the tests
+    constexpr int kU = 4;
+    for (int i0 = lane; i0 < v.ecnt; i0 += 32 * kU) {
+        float4 e[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + 32 * u < v.ecnt) e[u] = v.edge[i0 + 32 * u];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + 32 * u < v.ecnt) hit(e[u]);
     }
     return warp_min(t_best);
 }
