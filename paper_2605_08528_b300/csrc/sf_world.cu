@@ -43,7 +43,12 @@ struct Agent {
 };
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return x < lo ? lo : (x > hi ? hi : x); }
-__device__ __forceinline__ float cross2(float ax, float ay, float bx, float by) { return ax * by - ay * bx; }
+// a*b + c*d rounded one fixed way (c*d rounded, then one fused multiply-add):
+// the step's kernels inline the same geometry in different contexts, and a
+// contraction left to the compiler could round them differently
+__device__ __forceinline__ float dot2(float a, float b, float c, float d) { return __fmaf_rn(a, b, __fmul_rn(c, d)); }
+__device__ __forceinline__ float norm2(float x, float y) { return dot2(x, x, y, y); }
+__device__ __forceinline__ float cross2(float ax, float ay, float bx, float by) { return dot2(ax, by, -ay, bx); }
 __device__ __forceinline__ uint32_t status_of(uint32_t meta) { return (meta >> 16) & 0xFFu; }
 __device__ __forceinline__ uint32_t with_status(uint32_t meta, uint32_t st) { return (meta & 0xFFFFu) | (st << 16); }
 
@@ -81,17 +86,17 @@ __device__ __forceinline__ void heading_of(float qw, float qx, float qy, float q
 }
 
 __device__ __forceinline__ void to_ego(float hx, float hy, float x, float y, float& bx, float& by) {
-    bx = hx * x + hy * y;
-    by = -hy * x + hx * y;
+    bx = dot2(hx, x, hy, y);
+    by = dot2(hx, y, -hy, x);
 }
 
 __device__ __forceinline__ float seg_dist2(float ax, float ay, float bx, float by, float qx, float qy) {
     float ex = bx - ax, ey = by - ay;
-    float l2 = ex * ex + ey * ey;
-    float t = l2 > 0.f ? ((qx - ax) * ex + (qy - ay) * ey) / l2 : 0.f;
+    float l2 = norm2(ex, ey);
+    float t = l2 > 0.f ? dot2(qx - ax, ex, qy - ay, ey) / l2 : 0.f;
     t = clampf(t, 0.f, 1.f);
-    float dx = qx - ax - t * ex, dy = qy - ay - t * ey;
-    return dx * dx + dy * dy;
+    float dx = __fmaf_rn(-t, ex, qx - ax), dy = __fmaf_rn(-t, ey, qy - ay);
+    return norm2(dx, dy);
 }
 
 // ------------------------------------------------------------------ footprint contact
@@ -579,7 +584,7 @@ __device__ __forceinline__ WRoads view_of(const DevGrid& g, const unsigned char*
 __device__ __forceinline__ float hint_radius(const float* hnt, int which, float px, float py, float r0) {
     const float d = hnt[which];
     const float dx = px - hnt[2], dy = py - hnt[3];
-    const float jump = sqrtf(dx * dx + dy * dy);
+    const float jump = sqrtf(norm2(dx, dy));
     if (!(d > 0.f) || !(jump < kHintJump)) return r0;
     return d + jump * 1.0001f + 1e-3f;
 }
@@ -663,18 +668,29 @@ __device__ __forceinline__ void scan_cells(const WRoads& v, const Rows& w, int l
     }
 }
 
-// tangent, lateral offset and distance of the nearest lane segment from its key
-__device__ __forceinline__ Lane lane_of(const WRoads& v, unsigned long long best, float qx, float qy, float gx,
-                                        float gy) {
+// the warp's smallest key, and in r the record of the lane that held it (keys
+// are unique: they carry the record's position)
+__device__ __forceinline__ unsigned long long warp_min_rec(unsigned long long k, float4& r) {
+    const unsigned long long m = warp_min64(k);
+    const unsigned win = __ballot_sync(kFull, k == m);
+    const int src = win ? __ffs(win) - 1 : 0;
+    r.x = __shfl_sync(kFull, r.x, src); r.y = __shfl_sync(kFull, r.y, src);
+    r.z = __shfl_sync(kFull, r.z, src); r.w = __shfl_sync(kFull, r.w, src);
+    return m;
+}
+
+// tangent, lateral offset and distance of the nearest lane segment from its
+// key and its record r = (a, b)
+__device__ __forceinline__ Lane lane_of(const WRoads& v, unsigned long long best, const float4& r, float qx, float qy,
+                                        float gx, float gy) {
     Lane L;
     if (best == kKeyInf) { L.seg = -1; L.dist = kInf; L.lat = 0.f; L.tx = L.ty = 0.f; return L; }
     L.seg = v.q0 + rkey_local(best);
-    const float4 r = v.seg[rkey_pos(best)];            // (a, b) of the segment
     float ex = r.z - r.x, ey = r.w - r.y;
     float nn = sqrtf(ex * ex + ey * ey);
     float tx = ex / nn, ty = ey / nn;
     float lat = cross2(tx, ty, qx - r.x, qy - r.y);
-    if (tx * (gx - qx) + ty * (gy - qy) < 0.f) { tx = -tx; ty = -ty; lat = -lat; }
+    if (dot2(tx, gx - qx, ty, gy - qy) < 0.f) { tx = -tx; ty = -ty; lat = -lat; }
     L.dist = sqrtf(key_d2(best)); L.lat = lat; L.tx = tx; L.ty = ty;
     return L;
 }
@@ -710,6 +726,7 @@ __device__ Lane coop_nearest_lane(const WRoads& v, float qx, float qy, float gx,
     if (forb) S = fmaxf(S, kCircD + kCircR + kEdgeHalfWidth + kSegReach);
     bool edges = forb != nullptr, f = false;
     unsigned long long best = kKeyInf;
+    float4 brec = make_float4(0.f, 0.f, 0.f, 0.f);
     for (;;) {
         const Rows w = rows_covering(v, qx, qy, S);
         const float Rl = S - kSegReach;
@@ -720,17 +737,18 @@ __device__ Lane coop_nearest_lane(const WRoads& v, float qx, float qy, float gx,
             if (!has || !(m & kInfoSegNext) || !(m & want)) return;
             const float d0 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
             if (m & kInfoLane) {
-                if (d0 < lim) best = umin64(best, rkey(d0, m, i));
+                const unsigned long long k = rkey(d0, m, i);
+                if (d0 < lim && k < best) { best = k; brec = sg; }
             } else if (forb_touch(sg, d0, qx, qy, hx, hy)) {
                 f = true;
             }
         });
-        best = warp_min64(best);
+        best = warp_min_rec(best, brec);
         if (edges) { *forb = __any_sync(kFull, f); edges = false; }
         if (best != kKeyInf || w.all) break;
         S = Rl * kGrow + kSegReach;
     }
-    return lane_of(v, best, qx, qy, gx, gy);
+    return lane_of(v, best, brec, qx, qy, gx, gy);
 }
 
 // Candidate keys (kKeyInf: none) of a batch into the warp's buffer; every 32
@@ -769,7 +787,7 @@ __device__ unsigned long long coop_knn32(const WRoads& v, float qx, float qy, fl
             unsigned long long key = kKeyInf;
             if (has) {
                 const float dx = P.x - qx, dy = P.y - qy;
-                key = rkey(dx * dx + dy * dy, m, i);
+                key = rkey(norm2(dx, dy), m, i);
                 if (key >= thr) key = kKeyInf;
             }
             collect32(key, lane, lt, buf, cnt, run, thr);
@@ -802,18 +820,20 @@ __device__ Lane coop_point_queries(const WRoads& v, float qx, float qy, float gx
     const float lim_l = w.all ? kInf : Rle * Rle * (1.f - 1e-5f);
     unsigned long long thr = w.all ? kKeyInf : key_of(R32 * R32 * (1.f - 1e-5f), 0);
     unsigned long long run = kKeyInf, best = kKeyInf;
+    float4 brec = make_float4(0.f, 0.f, 0.f, 0.f);
     bool f = false;
     int cnt = 0;
     scan_cells(v, w, lane, [&](const float4& sg, uint32_t m, int i, bool has) {
         unsigned long long k = kKeyInf;
         if (has) {
             const float dx = sg.x - qx, dy = sg.y - qy;
-            k = rkey(dx * dx + dy * dy, m, i);
+            k = rkey(norm2(dx, dy), m, i);
             if (k >= thr) k = kKeyInf;
             if ((m & kInfoSegNext) && (m & (kInfoLane | kInfoEdge))) {
                 const float d0 = seg_dist2(sg.x, sg.y, sg.z, sg.w, qx, qy);
                 if (m & kInfoLane) {
-                    if (d0 < lim_l) best = umin64(best, rkey(d0, m, i));
+                    const unsigned long long kl = rkey(d0, m, i);
+                    if (d0 < lim_l && kl < best) { best = kl; brec = sg; }
                 } else if (forb_touch(sg, d0, qx, qy, hx, hy)) {
                     f = true;
                 }
@@ -827,12 +847,12 @@ __device__ Lane coop_point_queries(const WRoads& v, float qx, float qy, float gx
     }
     __syncwarp();
     *forb = __any_sync(kFull, f);
-    best = warp_min64(best);
+    best = warp_min_rec(best, brec);
     // too few points within R32: the 32 nearest alone, from a larger radius
     *key = (shfl64(run, 31) != kKeyInf || w.all) ? run : coop_knn32(v, qx, qy, R32 * kGrow, lane, buf);
     if (best == kKeyInf && !w.all)                   // no lane within Rle: the nearest lane alone
         return coop_nearest_lane(v, qx, qy, gx, gy, Rle * kGrow, lane);
-    return lane_of(v, best, qx, qy, gx, gy);
+    return lane_of(v, best, brec, qx, qy, gx, gy);
 }
 
 // time for the constant-velocity ray from an agent to reach the nearest road
@@ -847,7 +867,7 @@ __device__ float coop_edge_ray(const WRoads& v, float px, float py, float vx, fl
     float t_best = kInf;
     auto hit = [&](const float4& sg4) {
         const float apx = sg4.x - px, apy = sg4.y - py;
-        if (apx * apx + apy * apy > reach2) return;
+        if (norm2(apx, apy) > reach2) return;
         const float exx = sg4.z - sg4.x, eyy = sg4.w - sg4.y;
         const float den = cross2(vx, vy, exx, eyy);
         if (den == 0.f) return;
@@ -871,16 +891,14 @@ __device__ float coop_edge_ray(const WRoads& v, float px, float py, float vx, fl
 }
 
 // road-point features of the observation (App. D analogue) from a k-NN key
-__device__ __forceinline__ void point_features(const WRoads& v, unsigned long long key, float ehx, float ehy,
-                                               float epx, float epy, float f[kObsPt]) {
-    const int pos = rkey_pos(key);
-    const float4 r = v.seg[pos];
-    const uint32_t m = v.info[pos];
+// and the point's record (r, m)
+__device__ __forceinline__ void point_features_of(const float4& r, uint32_t m, float ehx, float ehy, float epx,
+                                                  float epy, float f[kObsPt]) {
     // road direction at the point: toward the next point of the polyline,
     // from the previous one at a polyline's end
     float ddx = r.z - r.x, ddy = r.w - r.y;
     if (!(m & kInfoHasNext)) { ddx = -ddx; ddy = -ddy; }
-    const float nn = sqrtf(ddx * ddx + ddy * ddy);
+    const float nn = sqrtf(norm2(ddx, ddy));
     if (nn > 0.f) { ddx /= nn; ddy /= nn; } else { ddx = ddy = 0.f; }
     float bx, by, dbx, dby;
     to_ego(ehx, ehy, r.x - epx, r.y - epy, bx, by);
@@ -889,6 +907,11 @@ __device__ __forceinline__ void point_features(const WRoads& v, unsigned long lo
     f[4] = (float)((m >> 16) & 0xFFu) / 20.f;
     f[5] = (m & kInfoEdge) ? 1.f : 0.f;
     f[6] = 1.f;
+}
+__device__ __forceinline__ void point_features(const WRoads& v, unsigned long long key, float ehx, float ehy,
+                                               float epx, float epy, float f[kObsPt]) {
+    const int pos = rkey_pos(key);
+    point_features_of(v.seg[pos], v.info[pos], ehx, ehy, epx, epy, f);
 }
 
 // ------------------------------------------------------------------ dynamics surrogate
@@ -1045,7 +1068,7 @@ __device__ __forceinline__ bool surr_gate(const Exch& E, int base, int n, int la
         const float dvx = E.vx[j] - A.vx, dvy = E.vy[j] - A.vy;
         const float reach = kSurrReach + sqrtf(dvx * dvx + dvy * dvy) * dt;
         const float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
-        if (dx * dx + dy * dy <= reach * reach) return false;
+        if (norm2(dx, dy) <= reach * reach) return false;
     }
     return true;
 }
@@ -1227,7 +1250,7 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
                 const float bj = sqrtf(E.vx[j] * E.vx[j] + E.vy[j] * E.vy[j]) * T + 1.f;
                 const float reach = kPairCullR + budget + bj + 0.01f;
                 const float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
-                if (dx * dx + dy * dy <= reach * reach) near |= 1u << j;
+                if (norm2(dx, dy) <= reach * reach) near |= 1u << j;
             }
         }
         if (!wide && __any_sync(kFull, alive && A.dpx * A.dpx + A.dpy * A.dpy > budget * budget)) wide = true;
@@ -1439,7 +1462,7 @@ __device__ __forceinline__ void lanes_events_b(const WorldArgs& args, const Slot
         for (int j = base; j < base + n && !collided; ++j) {
             if (j == lane || !((alive_bits >> j) & 1u)) continue;
             float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
-            if (dx * dx + dy * dy > kPairCull2) continue;
+            if (norm2(dx, dy) > kPairCull2) continue;
             float nx, ny;
             if (sat2d(A.px, A.py, hx, hy, E.px[j], E.py[j], E.hx[j], E.hy[j], nx, ny) > 0.f) collided = true;
         }
@@ -1496,7 +1519,7 @@ __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot&
             float d2 = kInf;
             if (elig) {
                 float dx = A.px - xr, dy = A.py - yr;
-                d2 = dx * dx + dy * dy;
+                d2 = norm2(dx, dy);
             }
             const float dmin = warp_min(d2);
             if (dmin > bscore) { bscore = dmin; pick = r; }
@@ -1807,28 +1830,37 @@ __global__ void __launch_bounds__(32, 16) phys_kernel(const WorldArgs args) {
 // road queries of one agent per warp: the events' queries (into sc.q) and the
 // road-point block of the observation at the post-physics pose
 template <int NWQ>
-__global__ void __launch_bounds__(32 * NWQ) query_kernel(const WorldArgs args) {
+__global__ void __launch_bounds__(32 * NWQ, 32 / NWQ) query_kernel(const WorldArgs args) {
     __shared__ unsigned long long kbuf[NWQ][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * NWQ + warp;
     if (a >= args.num_agents) return;                 // warp-uniform
     float* orow = args.out.obs + (size_t)a * kObsDim + kObsEgo + kK * kObsNbr;
     int32_t* krow = (args.flags & kFlagRecord) ? args.out.knn_pts + (size_t)a * kL : nullptr;
-    if (!(status_of(args.st.meta[a]) & kAlive)) {
+    // every per-agent load at once (one memory round trip), then the world's grid
+    const uint32_t meta = args.st.meta[a];
+    const int wid = args.sc.agent_world[a];
+    const float4 p = args.st.pos[a], vel = args.st.vel[a], goal = args.st.goal[a];
+    const float2 h = args.sc.head[a];
+    float* hnt = args.out.hint + 4 * (size_t)a;
+    const float4 h4 = *reinterpret_cast<const float4*>(hnt);
+    if (!(status_of(meta) & kAlive)) {
 #pragma unroll
         for (int k = 0; k < kObsPt; ++k) orow[kObsPt * lane + k] = 0.f;
         if (krow) krow[lane] = -1;
         return;
     }
-    const DevGrid g = args.rd.grid[args.sc.agent_world[a]];
+    const DevGrid g = args.rd.grid[wid];
     const WRoads v = view_of(g, args.rd.blob + g.blob);
-    const float4 p = args.st.pos[a], vel = args.st.vel[a], goal = args.st.goal[a];
-    const float2 h = args.sc.head[a];
-    float* hnt = args.out.hint + 4 * (size_t)a;
+    const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
     bool forb = false;
     unsigned long long key = kKeyInf;
-    const Lane L = coop_point_queries(v, p.x, p.y, goal.x, goal.y, h.x, h.y, hint_radius(hnt, 0, p.x, p.y, kKnnR0),
-                                      hint_radius(hnt, 1, p.x, p.y, kLaneR0), lane, kbuf[warp], &forb, &key);
+    const Lane L = coop_point_queries(v, p.x, p.y, goal.x, goal.y, h.x, h.y, hint_radius(hv, 0, p.x, p.y, kKnnR0),
+                                      hint_radius(hv, 1, p.x, p.y, kLaneR0), lane, kbuf[warp], &forb, &key);
+    // the observation's point records are fetched while the edge ray runs
+    float4 prec = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t pm = 0u;
+    if (key != kKeyInf) { prec = v.seg[rkey_pos(key)]; pm = v.info[rkey_pos(key)]; }
     const float tedge = coop_edge_ray(v, p.x, p.y, vel.x, vel.y, lane);
     const unsigned long long last = shfl64(key, 31);
     __syncwarp();
@@ -1843,7 +1875,7 @@ __global__ void __launch_bounds__(32 * NWQ) query_kernel(const WorldArgs args) {
         hnt[3] = p.y;
     }
     float f[kObsPt] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (key != kKeyInf) point_features(v, key, h.x, h.y, p.x, p.y, f);
+    if (key != kKeyInf) point_features_of(prec, pm, h.x, h.y, p.x, p.y, f);
 #pragma unroll
     for (int k = 0; k < kObsPt; ++k) orow[kObsPt * lane + k] = f[k];
     if (krow) krow[lane] = key != kKeyInf ? v.q0 + rkey_local(key) : -1;
