@@ -49,6 +49,9 @@ __device__ __forceinline__ float clampf(float x, float lo, float hi) { return x 
 __device__ __forceinline__ float dot2(float a, float b, float c, float d) { return __fmaf_rn(a, b, __fmul_rn(c, d)); }
 __device__ __forceinline__ float norm2(float x, float y) { return dot2(x, x, y, y); }
 __device__ __forceinline__ float cross2(float ax, float ay, float bx, float by) { return dot2(ax, by, -ay, bx); }
+// named barrier `id` over n threads (a multiple of 32): arrive without waiting / wait
+__device__ __forceinline__ void named_bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void named_bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 __device__ __forceinline__ uint32_t status_of(uint32_t meta) { return (meta >> 16) & 0xFFu; }
 __device__ __forceinline__ uint32_t with_status(uint32_t meta, uint32_t st) { return (meta & 0xFFFFu) | (st << 16); }
 
@@ -1498,8 +1501,26 @@ __device__ __forceinline__ void lanes_events_b(const WorldArgs& args, const Slot
 // scored in order exactly as a sequential loop would: the first one at least
 // the spacing away is taken, else the one with the largest clearance (first
 // on ties).
+// spawn candidates (x, y, psi, goal x, goal y, v0) of every try of every slot
+// of a pack for the slot's next episode, drawn ahead of the respawns by threads
+// t = 0..nt-1 (the draws depend on the slot, its episode and the try only)
+constexpr int kSpawnDraws = 32 * kSpawnTries;
+__device__ __forceinline__ void draw_spawns(const WorldArgs& args, const int4& pk, const int* s_slot_w,
+                                            const int* s_wbase, int t, int nt, float (*sp)[kSpawnDraws]) {
+    for (int i = t; i < pk.w * kSpawnTries; i += nt) {
+        const int j = i / kSpawnTries, r = i % kSpawnTries;
+        const int wl = s_slot_w[j], a = pk.z + j;
+        float x, y, psi, gx, gy, v0;
+        spawn_candidate(args.rd, pk.x + wl, a, j - s_wbase[wl], args.st.episode[a] + 1, r, args.seed, x, y, psi, gx,
+                        gy, v0);
+        sp[0][i] = x; sp[1][i] = y; sp[2][i] = psi; sp[3][i] = gx; sp[4][i] = gy; sp[5][i] = v0;
+    }
+}
+
+// respawns in slot order; `pre` (may be null) holds the candidates drawn ahead
 __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot& c, int lane, int m, Agent& A,
-                                              bool& alive, bool respawn, uint32_t& ev) {
+                                              bool& alive, bool respawn, uint32_t& ev,
+                                              const float (*pre)[kSpawnDraws] = nullptr) {
     static_assert(kSpawnTries <= 32, "one lane per attempt");
     const uint32_t rbits = __ballot_sync(kFull, respawn);
     if (!rbits) return;
@@ -1511,7 +1532,14 @@ __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot&
         const int al = __shfl_sync(kFull, c.a, l), slot = l - __shfl_sync(kFull, c.base, l);
         const bool elig = alive && c.wl == wl && lane != l && !(lane > l && ((rbits >> lane) & 1u));
         float x = 0.f, y = 0.f, psi = 0.f, gx = 0.f, gy = 0.f, v0 = 0.f;
-        if (lane < kSpawnTries) spawn_candidate(args.rd, wid, al, slot, ep, lane, seed, x, y, psi, gx, gy, v0);
+        if (lane < kSpawnTries) {
+            if (pre) {
+                const int i = l * kSpawnTries + lane;
+                x = pre[0][i]; y = pre[1][i]; psi = pre[2][i]; gx = pre[3][i]; gy = pre[4][i]; v0 = pre[5][i];
+            } else {
+                spawn_candidate(args.rd, wid, al, slot, ep, lane, seed, x, y, psi, gx, gy, v0);
+            }
+        }
         int pick = 0;
         float bscore = -1.f;
         for (int r = 0; r < kSpawnTries; ++r) {
@@ -1649,7 +1677,12 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     __shared__ DevGrid s_grid[32];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ int s_staged;
+    __shared__ float s_sp[6][kSpawnDraws];       // spawn candidates drawn ahead (kDraw)
     extern __shared__ __align__(128) unsigned char s_blob[];
+    // with spare warps, warps 1..NW-1 draw the spawn candidates of every slot
+    // while warp 0 runs the physics (a step) or right after the masks (a reset),
+    // so that the in-order respawns only pick among them
+    constexpr bool kDraw = NW >= 4 && MODE != kModeObserve;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int4 pk = __ldg(&args.packs[blockIdx.x]);   // (first world, worlds, first agent, agents)
     const int a0 = pk.z, m = pk.w;
@@ -1677,6 +1710,10 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         __syncwarp();
         if (staged && MODE != kModeReset)
             stage_issue(args.rd.blob, s_grid, s_woff, pk.y, stage_total, s_blob, &s_bar, lane);
+        if (kDraw && MODE == kModeStep) named_bar_arrive(1, 32 * NW);   // the pack tables are written
+    } else if (kDraw && MODE == kModeStep) {
+        named_bar_sync(1, 32 * NW);
+        draw_spawns(args, pk, s_slot_w, s_wbase, threadIdx.x - 32, 32 * (NW - 1), s_sp);
     }
 
     // ---------------- warp 0: agent registers
@@ -1703,6 +1740,10 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         if (s_any == 0u) return;                      // CTA-uniform: no masked agent in this pack
         if (warp == 0 && staged)
             stage_issue(args.rd.blob, s_grid, s_woff, pk.y, stage_total, s_blob, &s_bar, lane);
+        if (kDraw) {
+            if (warp != 0) draw_spawns(args, pk, s_slot_w, s_wbase, threadIdx.x - 32, 32 * (NW - 1), s_sp);
+            __syncthreads();
+        }
     }
     bool stg = false;                                 // this thread reads the staged copies
 
@@ -1742,7 +1783,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
 
     // ---------------- respawns (warp 0, agents in index order), then the post-reset exchange
     if (warp == 0) {
-        lanes_respawn(args, c, lane, m, A, alive, respawn, ev);
+        lanes_respawn(args, c, lane, m, A, alive, respawn, ev, kDraw ? s_sp : nullptr);
         // per world (never per pack, so that packing changes no result): a world
         // with a respawn or a parked agent republishes and recomputes its
         // neighbours; a reset leaves the worlds without a masked agent untouched
