@@ -322,7 +322,7 @@ cudaError_t weight_grad(sf_mlp* m, int l, int B, cudaStream_t st) {
 cudaError_t backward_core(sf_mlp* m, int B, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     for (int l = m->L - 1; l >= 0 && e == cudaSuccess; --l) {
-        const int o = m->dim[l + 1], lo = m->ld[l + 1], li = m->ld[l], i = m->dim[l];
+        const int o = m->dim[l + 1], lo = m->ld[l + 1], li = m->ld[l];
         act_back_kernel<<<tgrid(B, lo), kTBlock, 0, st>>>(m->dA, m->z[l], B, o, lo,
                                                                                   act_of(m, l), m->dz, m->dzt);
         e = cudaGetLastError();

@@ -1540,18 +1540,27 @@ __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot&
                 spawn_candidate(args.rd, wid, al, slot, ep, lane, seed, x, y, psi, gx, gy, v0);
             }
         }
-        int pick = 0;
-        float bscore = -1.f;
+        // every try's squared clearance from the eligible agents (the warp minima
+        // interleaved over the tries), then the first try at least the spacing
+        // away from everyone, else the first of the largest clearance
+        float dmin[kSpawnTries];
+#pragma unroll
         for (int r = 0; r < kSpawnTries; ++r) {
             const float xr = __shfl_sync(kFull, x, r), yr = __shfl_sync(kFull, y, r);
-            float d2 = kInf;
-            if (elig) {
-                float dx = A.px - xr, dy = A.py - yr;
-                d2 = norm2(dx, dy);
-            }
-            const float dmin = warp_min(d2);
-            if (dmin > bscore) { bscore = dmin; pick = r; }
-            if (dmin >= kSpawnSpacing * kSpawnSpacing) break;
+            dmin[r] = elig ? norm2(A.px - xr, A.py - yr) : kInf;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int r = 0; r < kSpawnTries; ++r) dmin[r] = fminf(dmin[r], __shfl_xor_sync(kFull, dmin[r], o));
+        int pick = 0;
+        float bscore = -1.f;
+        bool found = false;
+#pragma unroll
+        for (int r = 0; r < kSpawnTries; ++r) {
+            if (found) continue;
+            if (dmin[r] > bscore) { bscore = dmin[r]; pick = r; }
+            if (dmin[r] >= kSpawnSpacing * kSpawnSpacing) found = true;
         }
         const float bx = __shfl_sync(kFull, x, pick), by = __shfl_sync(kFull, y, pick);
         const float bpsi = __shfl_sync(kFull, psi, pick), bv = __shfl_sync(kFull, v0, pick);
