@@ -1505,6 +1505,7 @@ __device__ __forceinline__ void lanes_events_b(const WorldArgs& args, const Slot
 // of a pack for the slot's next episode, drawn ahead of the respawns by threads
 // t = 0..nt-1 (the draws depend on the slot, its episode and the try only)
 constexpr int kSpawnDraws = 32 * kSpawnTries;
+constexpr int kSpawnGroup = 4;   // respawning slots whose tries are drawn together (one lane each)
 __device__ __forceinline__ void draw_spawns(const WorldArgs& args, const int4& pk, const int* s_slot_w,
                                             const int* s_wbase, int t, int nt, float (*sp)[kSpawnDraws]) {
     for (int i = t; i < pk.w * kSpawnTries; i += nt) {
@@ -1518,60 +1519,77 @@ __device__ __forceinline__ void draw_spawns(const WorldArgs& args, const int4& p
 }
 
 // respawns in slot order; `pre` (may be null) holds the candidates drawn ahead
-__device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot& c, int lane, int m, Agent& A,
+__device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot& c, int lane, Agent& A,
                                               bool& alive, bool respawn, uint32_t& ev,
                                               const float (*pre)[kSpawnDraws] = nullptr) {
-    static_assert(kSpawnTries <= 32, "one lane per attempt");
+    static_assert(kSpawnTries * kSpawnGroup == 32, "one lane per (slot, try) of a group");
     const uint32_t rbits = __ballot_sync(kFull, respawn);
     if (!rbits) return;
     const unsigned long long seed = args.seed;
-    for (int l = 0; l < m; ++l) {
-        if (!((rbits >> l) & 1u)) continue;
-        const int ep = __shfl_sync(kFull, A.episode, l) + 1;
-        const int wl = __shfl_sync(kFull, c.wl, l), wid = __shfl_sync(kFull, c.w, l);
-        const int al = __shfl_sync(kFull, c.a, l), slot = l - __shfl_sync(kFull, c.base, l);
-        const bool elig = alive && c.wl == wl && lane != l && !(lane > l && ((rbits >> lane) & 1u));
+    const int q = lane / kSpawnTries, r = lane % kSpawnTries;
+    for (uint32_t todo = rbits; todo;) {
+        // the next kSpawnGroup respawning slots (ascending): lane (q, r) holds try r
+        // of the group's q-th slot, read from `pre` or drawn here, all at once
+        uint32_t group = 0u;
+        for (int k = 0; k < kSpawnGroup && todo; ++k) {
+            group |= todo & (~todo + 1u);
+            todo &= todo - 1u;
+        }
+        uint32_t t = group;
+        for (int k = 0; k < q && t; ++k) t &= t - 1u;
+        const int lq = t ? __ffs(t) - 1 : 0;
+        const int ep_q = __shfl_sync(kFull, A.episode, lq) + 1, w_q = __shfl_sync(kFull, c.w, lq);
+        const int a_q = __shfl_sync(kFull, c.a, lq), base_q = __shfl_sync(kFull, c.base, lq);
         float x = 0.f, y = 0.f, psi = 0.f, gx = 0.f, gy = 0.f, v0 = 0.f;
-        if (lane < kSpawnTries) {
+        if (t) {
             if (pre) {
-                const int i = l * kSpawnTries + lane;
+                const int i = lq * kSpawnTries + r;
                 x = pre[0][i]; y = pre[1][i]; psi = pre[2][i]; gx = pre[3][i]; gy = pre[4][i]; v0 = pre[5][i];
             } else {
-                spawn_candidate(args.rd, wid, al, slot, ep, lane, seed, x, y, psi, gx, gy, v0);
+                spawn_candidate(args.rd, w_q, a_q, lq - base_q, ep_q, r, seed, x, y, psi, gx, gy, v0);
             }
         }
-        // every try's squared clearance from the eligible agents (the warp minima
-        // interleaved over the tries), then the first try at least the spacing
-        // away from everyone, else the first of the largest clearance
-        float dmin[kSpawnTries];
+        // the group's slots in order: each takes the first try at least the spacing
+        // away from every eligible agent, else the first of the largest clearance
+        // (the warp minima interleaved over the tries); the eligible agents are the
+        // alive ones of its world, without the slots still waiting to respawn
+        int g = 0;
+        for (uint32_t gg = group; gg; gg &= gg - 1u, ++g) {
+            const int l = __ffs(gg) - 1;
+            const int ep = __shfl_sync(kFull, A.episode, l) + 1, wl = __shfl_sync(kFull, c.wl, l);
+            const bool elig = alive && c.wl == wl && lane != l && !(lane > l && ((rbits >> lane) & 1u));
+            const int s0 = g * kSpawnTries;
+            float dmin[kSpawnTries];
 #pragma unroll
-        for (int r = 0; r < kSpawnTries; ++r) {
-            const float xr = __shfl_sync(kFull, x, r), yr = __shfl_sync(kFull, y, r);
-            dmin[r] = elig ? norm2(A.px - xr, A.py - yr) : kInf;
+            for (int k = 0; k < kSpawnTries; ++k) {
+                const float xr = __shfl_sync(kFull, x, s0 + k), yr = __shfl_sync(kFull, y, s0 + k);
+                dmin[k] = elig ? norm2(A.px - xr, A.py - yr) : kInf;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int k = 0; k < kSpawnTries; ++k) dmin[k] = fminf(dmin[k], __shfl_xor_sync(kFull, dmin[k], o));
+            int pick = 0;
+            float bscore = -1.f;
+            bool found = false;
+#pragma unroll
+            for (int k = 0; k < kSpawnTries; ++k) {
+                if (found) continue;
+                if (dmin[k] > bscore) { bscore = dmin[k]; pick = k; }
+                if (dmin[k] >= kSpawnSpacing * kSpawnSpacing) found = true;
+            }
+            const int src = s0 + pick;
+            const float bx = __shfl_sync(kFull, x, src), by = __shfl_sync(kFull, y, src);
+            const float bpsi = __shfl_sync(kFull, psi, src), bv = __shfl_sync(kFull, v0, src);
+            const float bgx = __shfl_sync(kFull, gx, src), bgy = __shfl_sync(kFull, gy, src);
+            if (lane == l) {
+                place_agent(A, bx, by, bpsi, bv, bgx, bgy);
+                A.episode = ep;
+                alive = true;
+                ev |= kEvRespawned;
+            }
+            __syncwarp();
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int r = 0; r < kSpawnTries; ++r) dmin[r] = fminf(dmin[r], __shfl_xor_sync(kFull, dmin[r], o));
-        int pick = 0;
-        float bscore = -1.f;
-        bool found = false;
-#pragma unroll
-        for (int r = 0; r < kSpawnTries; ++r) {
-            if (found) continue;
-            if (dmin[r] > bscore) { bscore = dmin[r]; pick = r; }
-            if (dmin[r] >= kSpawnSpacing * kSpawnSpacing) found = true;
-        }
-        const float bx = __shfl_sync(kFull, x, pick), by = __shfl_sync(kFull, y, pick);
-        const float bpsi = __shfl_sync(kFull, psi, pick), bv = __shfl_sync(kFull, v0, pick);
-        const float bgx = __shfl_sync(kFull, gx, pick), bgy = __shfl_sync(kFull, gy, pick);
-        if (lane == l) {
-            place_agent(A, bx, by, bpsi, bv, bgx, bgy);
-            A.episode = ep;
-            alive = true;
-            ev |= kEvRespawned;
-        }
-        __syncwarp();
     }
 }
 
@@ -1792,7 +1810,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
 
     // ---------------- respawns (warp 0, agents in index order), then the post-reset exchange
     if (warp == 0) {
-        lanes_respawn(args, c, lane, m, A, alive, respawn, ev, kDraw ? s_sp : nullptr);
+        lanes_respawn(args, c, lane, A, alive, respawn, ev, kDraw ? s_sp : nullptr);
         // per world (never per pack, so that packing changes no result): a world
         // with a respawn or a parked agent republishes and recomputes its
         // neighbours; a reset leaves the worlds without a masked agent untouched
@@ -1975,7 +1993,7 @@ __global__ void __launch_bounds__(32 * NWE) events_kernel(const WorldArgs args) 
     if (warp == 0) {
         lanes_events_b(args, c, lane, A, alive, nonfin, hx, hy, alive_bits, args.sc.q + c.a, E, nb, tt, r, N, ev,
                        reward, drac, done, respawn, parked_now);
-        lanes_respawn(args, c, lane, m, A, alive, respawn, ev);
+        lanes_respawn(args, c, lane, A, alive, respawn, ev);
         const unsigned chg = __ballot_sync(kFull, respawn || parked_now);
         const uint32_t wmask = c.n >= 32 ? 0xFFFFFFFFu : (((1u << c.n) - 1u) << c.base);
         recompute = (chg & wmask) != 0u;
