@@ -586,16 +586,28 @@ def step_kernels(tuned) -> str:
     return "world_kernel<step, %d warps> (pack %d, staged %d B)" % (nw, pack, stage)
 
 
+def kernel_source_tag():
+    """First 12 hex digits of the SHA-1 of the step kernels' sources: a DRAM
+    traffic figure holds only for the source it was captured on."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("sf_world.cu", "sf_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2605_08528_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def load_traffic():
     """DRAM bytes per launch of the kernel a roofline describes, from the
-    committed ncu summary (lines "workload bytes ..."); none when the current
-    kernel has no capture."""
+    committed ncu summary (lines "workload bytes shape source-tag ..."); an
+    entry captured on another source than the current one is dropped."""
     out = {}
     try:
+        tag = kernel_source_tag()
         with open(os.path.join(ROOT, "profiles", "world_kernel_traffic.txt")) as f:
             for line in f:
                 parts = line.split()
-                if parts and not parts[0].startswith("#") and len(parts) >= 3:
+                if parts and not parts[0].startswith("#") and len(parts) >= 4 and parts[3] == tag:
                     out[parts[0]] = (int(parts[1]), [int(x) for x in parts[2].split(",")])
     except (OSError, ValueError):
         pass
@@ -604,7 +616,7 @@ def load_traffic():
 
 def traffic_of(traffic, name, tuned):
     """Captured DRAM bytes per launch for this workload when the timed launch
-    shape is the captured one, else None."""
+    shape and the kernel source are the captured ones, else None."""
     t = traffic.get(name)
     if t is None or not tuned or list(tuned[0]) != t[1]:
         return None
