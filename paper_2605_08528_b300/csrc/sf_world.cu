@@ -374,6 +374,7 @@ struct Exch {
     // partners above it; the pair list and each pair's force (fx, fy, tz)
     int poff[32];
     uint32_t pmask[32];
+    float bud[32];            // each agent's displacement budget for the control step
     int plist[kMaxPairs];
     float4 pf[kMaxPairs];
 };
@@ -1248,10 +1249,11 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
         __syncwarp();
         if (s == 0 && args.surr_mode != 0) gated = surr_gate(E, base, n, lane, alive_bits, A, args.h * args.substeps);
         if (s == 0) {
+            E.bud[lane] = budget;
+            __syncwarp();
             for (int j = base; j < base + n; ++j) {
                 if (j == lane) continue;
-                const float bj = sqrtf(E.vx[j] * E.vx[j] + E.vy[j] * E.vy[j]) * T + 1.f;
-                const float reach = kPairCullR + budget + bj + 0.01f;
+                const float reach = kPairCullR + budget + E.bud[j] + 0.01f;
                 const float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
                 if (norm2(dx, dy) <= reach * reach) near |= 1u << j;
             }
@@ -1289,8 +1291,8 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
             }
             __syncwarp();
             if (alive) {
-                for (int j = base; j < base + n; ++j) {
-                    if (j == lane || !((cand >> j) & 1u)) continue;
+                for (uint32_t pm = cand & wmask & ~(1u << lane); pm; pm &= pm - 1u) {   // ascending j
+                    const int j = __ffs(pm) - 1;
                     const int lo = min(lane, j), hi = max(lane, j);
                     const float4 f = E.pf[E.poff[lo] + __popc(E.pmask[lo] & ((1u << hi) - 1u))];
                     if (lane == lo) { fcx -= f.x; fcy -= f.y; } else { fcx += f.x; fcy += f.y; }
@@ -1298,8 +1300,8 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
                 }
             }
         } else if (alive) {   // many candidates (all pairs of a crowded world): a loop per lane
-            for (int j = base; j < base + n; ++j) {
-                if (j == lane || !((cand >> j) & 1u)) continue;
+            for (uint32_t pm = cand & wmask & ~(1u << lane); pm; pm &= pm - 1u) {   // ascending j
+                const int j = __ffs(pm) - 1;
                 const int lo = min(lane, j), hi = max(lane, j);
                 float fx, fy, tz;
                 pair_force(E.px[lo], E.py[lo], E.dx[lo], E.dy[lo], E.hx[lo], E.hy[lo], E.vx[lo], E.vy[lo],
