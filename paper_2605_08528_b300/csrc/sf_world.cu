@@ -396,8 +396,7 @@ __device__ __forceinline__ void knn_agents(const Exch& E, int base, int n, int l
     for (int t = 0; t < kK; ++t) { key[t] = kInf; nb[t] = -1; }
     for (int j = base; j < base + n; ++j) {
         if (j == lane || !((alive_bits >> j) & 1u)) continue;
-        float dx = E.px[j] - px, dy = E.py[j] - py;
-        float d2 = dx * dx + dy * dy;
+        const float d2 = norm2(E.px[j] - px, E.py[j] - py);
         if (!(d2 < key[kK - 1])) continue;
         float ck = d2;
         int ci = j;

@@ -303,6 +303,50 @@ def test_reset_spawns_match_oracle():
     assert ties <= 2
 
 
+@pytest.mark.parametrize("agents", [16, 32])
+def test_whole_world_respawn_in_one_step(agents):
+    """Every agent reaches the episode limit in the same step, so every world
+    respawns all of its agents inside one auto-reset step: 4 or 8 groups of
+    four respawning slots, drawn ahead by the spare warps (8 warps) or by the
+    lanes (1 warp, and the split events kernel).  With the whole world
+    respawning, a slot only avoids the slots placed before it, so the spawns
+    equal the oracle's reset of every agent at the same episode counters, and
+    every launch form gives the same bits."""
+    sc = synth.procedural_scene(4, agents, seed_base=1500)
+    max_steps = O.default_params().max_steps
+    acts = synth.ou_actions(sc.num_agents, 3, seed=2)
+    first = None
+    for nw, pack, split in [(8, 0, 0), (1, 0, 0), (2, 32, 0), (4, 32, 1)]:
+        W = sf.World(sc, seed=31, flags=sf.FLAG_AUTO_RESET, warps_per_block=nw, pack_agents=pack,
+                     split_step=split)
+        spawn_all(W)
+        for t in range(2):
+            sf.sf_step(W.h, dev(acts[t]))
+        F, I, _ = sf.sf_get_state(W.h)
+        I[:, O.I_STEP] = max_steps - 1
+        sf.sf_set_state(W.h, F, I)
+        sf.sf_step(W.h, dev(acts[2]))
+        F1, I1, _ = sf.sf_get_state(W.h)
+        _, _, done, ev = [x.cpu().numpy() for x in W.outputs()]
+        W.close()
+        assert done.all() and ((ev & O.EV["timeout"]) != 0).all() and ((ev & O.EV["respawned"]) != 0).all()
+        Fr, Ir = F.astype(np.float64), I.copy()
+        O.Oracle(sc).reset(Fr, Ir, np.ones(sc.num_agents, np.uint8), seed=31)
+        assert np.array_equal(I1[:, O.I_EPISODE], Ir[:, O.I_EPISODE])
+        assert (I1[:, O.I_STEP] == 0).all() and (I1[:, O.I_STATUS] == O.ALIVE).all()
+        ties = 0
+        for a in range(sc.num_agents):
+            if not np.array_equal(F1[a, :2].astype(np.float64), Fr[a, :2]):
+                ties += 1      # a spacing test within rounding of 10 m
+                continue
+            assert np.abs(F1[a] - Fr[a]).max() < 2e-5, (nw, pack, split, a)
+        assert ties <= 2
+        if first is None:
+            first = (F1, I1)
+        else:
+            assert np.array_equal(first[0], F1) and np.array_equal(first[1], I1), (nw, pack, split)
+
+
 # ----------------------------------------------------------------------------- edge cases
 @pytest.mark.parametrize("pack,stage,split", [(0, 0, 0), (32, 0, 0), (20, 0, 0), (32, 96 << 10, 0), (0, 48 << 10, 0),
                                               (32, 0, 1), (0, 0, 1)])
