@@ -47,6 +47,7 @@ __device__ __forceinline__ float act_grad(float z, int act) {
     }
 }
 
+
 // x [B, n] f32 -> bf16 [B, ld] with n == ld, ld % 8 == 0 and 16-byte rows: 8 elements per thread
 __global__ void to_bf16_vec8_kernel(const float* __restrict__ x, size_t n8, __nv_bfloat16* __restrict__ y) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,15 +130,54 @@ __global__ void mse_grad_kernel(const float* __restrict__ y, const float* __rest
     }
 }
 
-// column sums of the bf16 dZ^T rows: db[c] = sum_b dZ[b, c] (one warp per column)
-__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ dzt, int B, int n, float* __restrict__ db) {
-    const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (c >= n) return;
-    float s = 0.f;
-    for (int b = lane; b < B; b += 32) s += __bfloat162float(dzt[(size_t)c * B + b]);
+// column sums of dZ [B, ld] (bf16, row-major): db[c] = sum_b dZ[b, c], in two
+// deterministic passes.  Pass 1: block (x, s) sums columns [64 x, 64 x + 64)
+// over rows split s (a lane holds a column pair, so a warp reads whole 128-byte
+// rows; warp w takes rows w, w + 8, ...; the 8 warps are added in order).
+// Pass 2: each column adds its S split sums in order.
+constexpr int kBiasSplitMax = 32;
+__global__ void bias_part_kernel(const __nv_bfloat16* __restrict__ dz, int B, int ld, int n, int S,
+                                 float* __restrict__ part) {
+    __shared__ float2 red[8][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 64 + 2 * lane, s = blockIdx.y;
+    const int R = (B + S - 1) / S, r0 = s * R, r1 = min(B, r0 + R);
+    float2 acc = make_float2(0.f, 0.f);
+    if (c < ld) {
+        const __nv_bfloat162* col = reinterpret_cast<const __nv_bfloat162*>(dz + c);
+        int b = r0 + warp;
+        for (; b + 24 < r1; b += 32) {     // four rows in flight
+            const float2 v0 = __bfloat1622float2(col[(size_t)b * (ld / 2)]);
+            const float2 v1 = __bfloat1622float2(col[(size_t)(b + 8) * (ld / 2)]);
+            const float2 v2 = __bfloat1622float2(col[(size_t)(b + 16) * (ld / 2)]);
+            const float2 v3 = __bfloat1622float2(col[(size_t)(b + 24) * (ld / 2)]);
+            acc.x += v0.x; acc.y += v0.y;
+            acc.x += v1.x; acc.y += v1.y;
+            acc.x += v2.x; acc.y += v2.y;
+            acc.x += v3.x; acc.y += v3.y;
+        }
+        for (; b < r1; b += 8) {
+            const float2 v = __bfloat1622float2(col[(size_t)b * (ld / 2)]);
+            acc.x += v.x; acc.y += v.y;
+        }
+    }
+    red[warp][lane] = acc;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        const int l = threadIdx.x >> 1, k = threadIdx.x & 1;
+        float t = 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-    if (lane == 0) db[c] = s;
+        for (int w = 0; w < 8; ++w) t += k ? red[w][l].y : red[w][l].x;
+        const int cc = blockIdx.x * 64 + threadIdx.x;
+        if (cc < n) part[(size_t)s * n + cc] = t;
+    }
+}
+__global__ void bias_sum_kernel(const float* __restrict__ part, int n, int S, float* __restrict__ db) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    float t = 0.f;
+    for (int s = 0; s < S; ++s) t += part[(size_t)s * n + c];
+    db[c] = t;
 }
 
 // Adam (Kingma & Ba) on fp32 masters; refresh bf16 W [out, ldi] and W^T [ldi, ldo]
@@ -224,6 +264,7 @@ struct sf_mlp {
     float* gwfull = nullptr;                 // [max out, max ld] f32 (padded gradient)
     float* ws = nullptr;                     // [kSplitMax][max out][max ld] f32 split-K partials of dW
     float* loss = nullptr;
+    float* red = nullptr;                    // [kSumsqBlocks] partial sums of the gradient norm
     unsigned* errw = nullptr;
 };
 
@@ -300,13 +341,13 @@ __global__ void dy_in_kernel(const float* __restrict__ dy, int B, int n, int ldy
 
 // dW_l = dZ_l^T X_l [out, in] with K = B rows: the output has few tiles, so the K range is split over
 // up to kSplitMax CTAs per tile (enough to fill the GPU) and the partials summed in a fixed order
-cudaError_t weight_grad(sf_mlp* m, int l, int B, cudaStream_t st) {
+cudaError_t weight_grad(sf_mlp* m, int l, int B, const __nv_bfloat16* dzt, cudaStream_t st) {
     const int o = m->dim[l + 1], li = m->ld[l], i = m->dim[l];
     const int bn = tile_for(li);
     const int tiles = ((o + 127) / 128) * ((li + bn - 1) / bn), nk = (B + 63) / 64;
     const int S = std::max(1, std::min(std::min(kSplitMax, nk), 296 / std::max(1, tiles)));
     GemmArgs g{};
-    g.A = m->dzt; g.B = m->xt[l]; g.M = o; g.N = li; g.Nb = li; g.K = B; g.ldc = li; g.act = SF_ACT_NONE;
+    g.A = dzt; g.B = m->xt[l]; g.M = o; g.N = li; g.Nb = li; g.K = B; g.ldc = li; g.act = SF_ACT_NONE;
     g.bn = bn; g.err = m->errw;
     if (S > 1) { g.ws = m->ws; g.splits = S; } else { g.out_f32 = m->gwfull; }
     cudaError_t e = sf_gemm_launch(g, st);
@@ -323,12 +364,14 @@ cudaError_t backward_core(sf_mlp* m, int B, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     for (int l = m->L - 1; l >= 0 && e == cudaSuccess; --l) {
         const int o = m->dim[l + 1], lo = m->ld[l + 1], li = m->ld[l];
-        act_back_kernel<<<tgrid(B, lo), kTBlock, 0, st>>>(m->dA, m->z[l], B, o, lo,
-                                                                                  act_of(m, l), m->dz, m->dzt);
+        act_back_kernel<<<tgrid(B, lo), kTBlock, 0, st>>>(m->dA, m->z[l], B, o, lo, act_of(m, l), m->dz, m->dzt);
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = weight_grad(m, l, B, st);
+        if (e == cudaSuccess) e = weight_grad(m, l, B, m->dzt, st);
         if (e == cudaSuccess) {
-            bias_grad_kernel<<<(o + 7) / 8, 256, 0, st>>>(m->dzt, B, o, m->gb[l]);
+            // the split-K partials of dW are consumed: their workspace holds the bias partials
+            const int S = std::max(1, std::min(kBiasSplitMax, B / 256));
+            bias_part_kernel<<<dim3((unsigned)((o + 63) / 64), (unsigned)S), 256, 0, st>>>(m->dz, B, lo, o, S, m->ws);
+            bias_sum_kernel<<<(unsigned)((o + 255) / 256), 256, 0, st>>>(m->ws, o, S, m->gb[l]);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && l > 0)
@@ -338,44 +381,101 @@ cudaError_t backward_core(sf_mlp* m, int B, cudaStream_t st) {
     return e;
 }
 
-// sum of squares of n values added into *acc (one block reduction, one atomic per block)
-__global__ void sumsq_kernel(const float* __restrict__ g, int n, float* __restrict__ acc) {
+// every parameter tensor of a network as one index space: segment k holds
+// n = off[k + 1] - off[k] values; weight segments also carry their bf16 copies
+constexpr int kSegMax = 2 * kMaxLayers;
+struct Segs {
+    float* w[kSegMax];
+    const float* g[kSegMax];
+    float* m[kSegMax];
+    float* v[kSegMax];
+    __nv_bfloat16* wb[kSegMax];    // null for a bias
+    __nv_bfloat16* wbt[kSegMax];
+    int in[kSegMax], ldi[kSegMax], ldo[kSegMax];
+    long long off[kSegMax + 1];
+    int nseg;
+};
+__device__ __forceinline__ int seg_of(const Segs& S, long long i) {
+    int k = 0;
+    while (k + 1 < S.nseg && S.off[k + 1] <= i) ++k;
+    return k;
+}
+
+// sum of squares of the gradients, deterministic: block j sums its fixed chunk
+// of the index space (each thread a fixed stride, the warps added in order)
+// into part[j]; sumsq_final adds the parts in order into *acc
+constexpr int kSumsqBlocks = 148;
+__global__ void sumsq_part_kernel(const Segs S, float* __restrict__ part) {
     __shared__ float red[8];
-    float sacc = 0.f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) sacc += g[i] * g[i];
+    const long long total = S.off[S.nseg];
+    const long long chunk = (total + gridDim.x - 1) / gridDim.x;
+    const long long i0 = (long long)blockIdx.x * chunk, i1 = min(total, i0 + chunk);
+    float acc = 0.f;
+    long long i = i0 + threadIdx.x;
+    int k = i < i1 ? seg_of(S, i) : 0;
+    for (; i < i1; i += blockDim.x) {
+        while (S.off[k + 1] <= i) ++k;
+        const float gi = S.g[k][i - S.off[k]];
+        acc += gi * gi;
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xFFFFFFFFu, sacc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sacc;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        if (threadIdx.x == 0) atomicAdd(acc, v);
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+__global__ void sumsq_final_kernel(const float* __restrict__ part, int P, float* __restrict__ acc) {
+    if (threadIdx.x != 0) return;
+    float t = 0.f;
+    for (int j = 0; j < P; ++j) t += part[j];
+    *acc += t;
+}
+
+// Adam (Kingma & Ba) over every tensor of a network in one launch, with the
+// learning rate and a gradient scale read from device memory; weight elements
+// (o, k) of [out, in] refresh their bf16 copies W [out, ldi] and W^T [ldi, ldo]
+__global__ void adam_all_kernel(const Segs S, const float* __restrict__ lr_p, const float* __restrict__ scale_p,
+                                float b1, float b2, float eps, float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.off[S.nseg]) return;
+    const int k = seg_of(S, i);
+    const long long j = i - S.off[k];
+    const float gi = S.g[k][j] * *scale_p;
+    const float mi = b1 * S.m[k][j] + (1.f - b1) * gi;
+    const float vi = b2 * S.v[k][j] + (1.f - b2) * gi * gi;
+    S.m[k][j] = mi;
+    S.v[k][j] = vi;
+    const float wi = S.w[k][j] - *lr_p * (mi / c1) / (sqrtf(vi / c2) + eps);
+    S.w[k][j] = wi;
+    if (S.wb[k]) {
+        const int o = (int)(j / S.in[k]), c = (int)(j % S.in[k]);
+        const __nv_bfloat16 hb = __float2bfloat16_rn(wi);
+        S.wb[k][(size_t)o * S.ldi[k] + c] = hb;
+        S.wbt[k][(size_t)c * S.ldo[k] + o] = hb;
     }
 }
 
-// Adam with the learning rate and a gradient scale read from device memory
-__global__ void adam_dev_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
-                                float* __restrict__ v, int n, const float* __restrict__ lr_p,
-                                const float* __restrict__ scale_p, float b1, float b2, float eps, float c1, float c2,
-                                int out, int in, int ldi, int ldo, __nv_bfloat16* __restrict__ wb,
-                                __nv_bfloat16* __restrict__ wbt) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float gi = g[i] * *scale_p;
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float wi = w[i] - *lr_p * (mi / c1) / (sqrtf(vi / c2) + eps);
-    w[i] = wi;
-    if (wb) {
-        const int o = i / in, k = i % in;
-        const __nv_bfloat16 hb = __float2bfloat16_rn(wi);
-        wb[(size_t)o * ldi + k] = hb;
-        wbt[(size_t)k * ldo + o] = hb;
+// the segment table of network m: per layer its weights, then its biases
+Segs segs_of(const sf_mlp* m) {
+    Segs S{};
+    long long off = 0;
+    int k = 0;
+    for (int l = 0; l < m->L; ++l) {
+        const int o = m->dim[l + 1], i = m->dim[l];
+        S.w[k] = m->w[l]; S.g[k] = m->gw[l]; S.m[k] = m->mw[l]; S.v[k] = m->vw[l];
+        S.wb[k] = m->wb[l]; S.wbt[k] = m->wbt[l]; S.in[k] = i; S.ldi[k] = m->ld[l]; S.ldo[k] = m->ld[l + 1];
+        S.off[k] = off; off += (long long)o * i; ++k;
+        S.w[k] = m->b[l]; S.g[k] = m->gb[l]; S.m[k] = m->mb[l]; S.v[k] = m->vb[l];
+        S.wb[k] = nullptr; S.wbt[k] = nullptr; S.in[k] = 1; S.ldi[k] = 0; S.ldo[k] = 0;
+        S.off[k] = off; off += o; ++k;
     }
+    S.off[k] = off;
+    S.nseg = k;
+    return S;
 }
 
 }  // namespace
@@ -476,6 +576,7 @@ sf_status sf_mlp_create(int num_layers, const int32_t* dims, int hidden_act, int
     m->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = malloc_zero(m, &m->errw, 1);
     if (e == cudaSuccess) e = malloc_zero(m, &m->loss, 1);
+    if (e == cudaSuccess) e = malloc_zero(m, &m->red, 256);
     int maxo = 0, maxi = 0;
     for (int l = 0; l < num_layers && e == cudaSuccess; ++l) {
         const int o = dims[l + 1], i = dims[l];
@@ -640,11 +741,8 @@ sf_status sf_mlp_backward_on(sf_mlp_handle m, cudaStream_t st, const float* d_dy
 
 sf_status sf_mlp_grad_sumsq_on(sf_mlp_handle m, cudaStream_t st, float* d_acc) {
     if (!m || !d_acc) return SF_ERR_INVALID_ARG;
-    for (int l = 0; l < m->L; ++l) {
-        const int n = m->dim[l + 1] * m->dim[l];
-        sumsq_kernel<<<std::min(256u, grid1(n)), 256, 0, st>>>(m->gw[l], n, d_acc);
-        sumsq_kernel<<<1, 256, 0, st>>>(m->gb[l], m->dim[l + 1], d_acc);
-    }
+    sumsq_part_kernel<<<kSumsqBlocks, 256, 0, st>>>(segs_of(m), m->red);
+    sumsq_final_kernel<<<1, 32, 0, st>>>(m->red, kSumsqBlocks, d_acc);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, cudaGetErrorString(e));
 }
@@ -654,14 +752,8 @@ sf_status sf_mlp_adam_on(sf_mlp_handle m, cudaStream_t st, const float* d_lr, co
     ++m->adam_t;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.f - std::pow(b1, (float)m->adam_t), c2 = 1.f - std::pow(b2, (float)m->adam_t);
-    for (int l = 0; l < m->L; ++l) {
-        const int o = m->dim[l + 1], i = m->dim[l];
-        adam_dev_kernel<<<grid1((size_t)o * i), 256, 0, st>>>(m->w[l], m->gw[l], m->mw[l], m->vw[l], o * i, d_lr,
-                                                              d_scale, b1, b2, eps, c1, c2, o, i, m->ld[l],
-                                                              m->ld[l + 1], m->wb[l], m->wbt[l]);
-        adam_dev_kernel<<<grid1(o), 256, 0, st>>>(m->b[l], m->gb[l], m->mb[l], m->vb[l], o, d_lr, d_scale, b1, b2, eps,
-                                                  c1, c2, 0, 1, 0, 0, nullptr, nullptr);
-    }
+    const Segs S = segs_of(m);
+    adam_all_kernel<<<grid1((size_t)S.off[S.nseg]), 256, 0, st>>>(S, d_lr, d_scale, b1, b2, eps, c1, c2);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, cudaGetErrorString(e));
 }
