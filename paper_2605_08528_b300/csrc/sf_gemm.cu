@@ -23,9 +23,22 @@
 #include "sf_gemm.cuh"
 #include "sf_tc.cuh"
 
+
+
+
+
+
+
 namespace {
 
-constexpr int kBM = 128, kBK = 64, kStages = 4, kThreads = 256;   // 8 warps: 2 per TMEM lane slice
+constexpr int kBM = 128, kBK = 64, kThreads = 256;   // 8 warps: 2 per TMEM lane slice
+// Pipeline depth: a deep ring (4 stages, one CTA per SM) for long K; for short K
+// (few K tiles per CTA) a shallow ring that lets two CTAs share an SM (shared
+// memory and TMEM columns), so one CTA's epilogue overlaps the other's main loop
+constexpr int kDeep = 4;
+template <int BN>
+constexpr int shallow_for() { return BN >= 256 ? 2 : (BN >= 128 ? 3 : 4); }
+constexpr int kShallowMaxK = 8;   // K tiles per CTA up to which the shallow ring is used
 using namespace sftc;
 
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err) {
@@ -47,7 +60,7 @@ __device__ __forceinline__ void activate32(float (&v)[32], int act) {
     }
 }
 
-template <int BN>
+template <int BN, int kStages>
 struct alignas(1024) GemmSmem {
     __nv_bfloat16 a[kStages][kBM * kBK];
     __nv_bfloat16 b[kStages][BN * kBK];
@@ -57,12 +70,12 @@ struct alignas(1024) GemmSmem {
     uint32_t tmem_base;
 };
 
-template <int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int BN, int kStages>
+__global__ void __launch_bounds__(kThreads, kStages == kDeep ? 1 : 2)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                    const GemmArgs args) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    GemmSmem<BN>& S = *reinterpret_cast<GemmSmem<BN>*>(
+    GemmSmem<BN, kStages>& S = *reinterpret_cast<GemmSmem<BN, kStages>*>(
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
@@ -243,22 +256,29 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+template <int BN, int ST>
+cudaError_t launch_st(const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& g, dim3 grid, cudaStream_t s) {
+    const size_t smem = sizeof(GemmSmem<BN, ST>) + 1024;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(tc_gemm_kernel<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    tc_gemm_kernel<BN, ST><<<grid, kThreads, smem, s>>>(ma, mb, g);
+    return cudaGetLastError();
+}
+
 template <int BN>
 cudaError_t launch_bn(const GemmArgs& g, cudaStream_t s) {
     CUtensorMap ma, mb;
     if (!make_map(&ma, g.A, g.M, g.K, kBM) || !make_map(&mb, g.B, g.Nb, g.K, BN)) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(GemmSmem<BN>) + 1024;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
     const int nk = (g.K + kBK - 1) / kBK;
     const int splits = g.ws ? std::max(1, std::min(g.splits, nk)) : 1;
     dim3 grid((g.N + BN - 1) / BN, (g.M + kBM - 1) / kBM, splits);
-    tc_gemm_kernel<BN><<<grid, kThreads, smem, s>>>(ma, mb, g);
-    return cudaGetLastError();
+    if ((nk + splits - 1) / splits <= kShallowMaxK) return launch_st<BN, shallow_for<BN>()>(ma, mb, g, grid, s);
+    return launch_st<BN, kDeep>(ma, mb, g, grid, s);
 }
 
 }  // namespace
