@@ -195,6 +195,21 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* h_roads);
  * substeps outside 1..64), SF_ERR_CUDA (launch failure). */
 sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps);
 
+/* The same control step end to end from host memory: h_actions [A][3] float32
+ * is copied to the device, the step runs, and the rewards [A] float32 and done
+ * flags [A] uint8 are copied into h_reward and h_done; returns when they are in
+ * host memory (synchronous).  With a non-default stream and page-locked buffers
+ * (cudaHostAlloc / cudaHostRegister) the copies and the step are captured into
+ * one CUDA graph that later calls with the same dt and substeps replay (other
+ * page-locked buffers retarget its copies); the graph is re-captured after
+ * sf_load_roads or sf_autotune.  Pageable buffers or the legacy stream run the
+ * copies and the step without a graph.  The buffers are caller-owned and must
+ * stay valid during the call.
+ * Errors: SF_ERR_STATE (no roads), SF_ERR_INVALID_ARG (NULL buffer, dt <= 0,
+ * substeps outside 1..64), SF_ERR_OOM, SF_ERR_CUDA. */
+sf_status sf_step_host(sf_handle h, const float* h_actions, float* h_reward, uint8_t* h_done, float dt,
+                       int substeps);
+
 /* Autotuner: time each launch shape of the step over `iters` steps with the
  * given actions and keep the fastest for this handle.  Shapes s < 32 are the
  * fused kernel with 1 << (s & 3) warps per block, world packing when bit 2 is

@@ -51,6 +51,19 @@ struct sf_ctx {
     int pack_cap = 32;
     StepScratch sc{};           // scratch of the split step
     bool loaded = false;
+    unsigned gen = 0;           // bumped when a captured step would go stale (roads, launch shape)
+    struct HostStep {           // the captured step of sf_step_host: copy in, step, copies out
+        float dt = 0.f;
+        int substeps = 0;
+        unsigned gen = 0;
+        const float* ha = nullptr;
+        float* hr = nullptr;
+        uint8_t* hd = nullptr;
+        float* d_act = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphNode_t n_act = nullptr, n_rew = nullptr, n_done = nullptr;
+    } hs;
 };
 
 struct sf_graph {
@@ -90,7 +103,18 @@ sf_status dalloc(sf_ctx* h, T** p, size_t count) {
     return SF_OK;
 }
 
+void drop_host_step(sf_ctx* h) {
+    if (h->hs.exec) cudaGraphExecDestroy(h->hs.exec);
+    if (h->hs.graph) cudaGraphDestroy(h->hs.graph);
+    float* d_act = h->hs.d_act;   // in h->allocs
+    h->hs = sf_ctx::HostStep{};
+    h->hs.d_act = d_act;
+}
+
 void free_all(sf_ctx* h) {
+    drop_host_step(h);
+    h->hs.d_act = nullptr;
+    ++h->gen;
     if (h->surr) { ::operator delete(h->surr); h->surr = nullptr; }
     if (h->lfb) { ::operator delete(h->lfb); h->lfb = nullptr; }
     for (void* p : h->allocs) cudaFree(p);
@@ -577,9 +601,113 @@ sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps) {
     return SF_OK;
 }
 
+namespace {
+
+bool page_locked(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+// the copy nodes of a captured host step, told apart by their host pointers
+void find_copy_nodes(sf_ctx* h) {
+    size_t n = 0;
+    cudaGraphGetNodes(h->hs.graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    cudaGraphGetNodes(h->hs.graph, nodes.data(), &n);
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeMemcpy) continue;
+        cudaMemcpy3DParms prm{};
+        if (cudaGraphMemcpyNodeGetParams(nd, &prm) != cudaSuccess) continue;
+        if (prm.srcPtr.ptr == h->hs.ha) h->hs.n_act = nd;
+        else if (prm.dstPtr.ptr == h->hs.hr) h->hs.n_rew = nd;
+        else if (prm.dstPtr.ptr == h->hs.hd) h->hs.n_done = nd;
+    }
+}
+
+}  // namespace
+
+sf_status sf_step_host(sf_handle h, const float* h_actions, float* h_reward, uint8_t* h_done, float dt,
+                       int substeps) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_step_host: no roads loaded");
+    if (h->A > 0 && (!h_actions || !h_reward || !h_done)) return fail(h, SF_ERR_INVALID_ARG, "sf_step_host: NULL buffer");
+    if (!(dt > 0.f) || !std::isfinite(dt)) return fail(h, SF_ERR_INVALID_ARG, "sf_step_host: dt must be > 0");
+    if (substeps < 1 || substeps > 64) return fail(h, SF_ERR_INVALID_ARG, "sf_step_host: substeps must be 1..64");
+    const size_t A = (size_t)h->A;
+    sf_ctx::HostStep& c = h->hs;
+    if (!c.d_act) {
+        void* p = nullptr;
+        SF_CUDA(h, cudaMalloc(&p, A * 12 + 16));
+        h->allocs.push_back(p);
+        c.d_act = static_cast<float*>(p);
+    }
+    const bool same = c.exec && c.dt == dt && c.substeps == substeps && c.gen == h->gen;
+    if (same && c.ha == h_actions && c.hr == h_reward && c.hd == h_done) {   // replay
+        SF_CUDA(h, cudaGraphLaunch(c.exec, h->stream));
+        SF_CUDA(h, cudaStreamSynchronize(h->stream));
+        return SF_OK;
+    }
+    const bool pinned = page_locked(h_actions) && page_locked(h_reward) && page_locked(h_done);
+    if (!h->stream || !pinned) {   // no graph: plain copies around the step
+        SF_CUDA(h, cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream));
+        sf_status st = sf_step(h, c.d_act, dt, substeps);
+        if (st != SF_OK) return st;
+        SF_CUDA(h, cudaMemcpyAsync(h_reward, h->out.reward, A * 4, cudaMemcpyDeviceToHost, h->stream));
+        SF_CUDA(h, cudaMemcpyAsync(h_done, h->out.done, A, cudaMemcpyDeviceToHost, h->stream));
+        SF_CUDA(h, cudaStreamSynchronize(h->stream));
+        return SF_OK;
+    }
+    if (same && c.n_act && c.n_rew && c.n_done) {   // other page-locked buffers: retarget the copies
+        SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_act, c.d_act, h_actions, A * 12,
+                                                      cudaMemcpyHostToDevice));
+        SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_rew, h_reward, h->out.reward, A * 4,
+                                                      cudaMemcpyDeviceToHost));
+        SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_done, h_done, h->out.done, A,
+                                                      cudaMemcpyDeviceToHost));
+        c.ha = h_actions; c.hr = h_reward; c.hd = h_done;
+        SF_CUDA(h, cudaGraphLaunch(c.exec, h->stream));
+        SF_CUDA(h, cudaStreamSynchronize(h->stream));
+        return SF_OK;
+    }
+    drop_host_step(h);
+    SF_CUDA(h, cudaStreamSynchronize(h->stream));
+    SF_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream);
+    sf_status st = e == cudaSuccess ? sf_step(h, c.d_act, dt, substeps) : SF_ERR_CUDA;
+    if (e == cudaSuccess && st == SF_OK)
+        e = cudaMemcpyAsync(h_reward, h->out.reward, A * 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && st == SF_OK)
+        e = cudaMemcpyAsync(h_done, h->out.done, A, cudaMemcpyDeviceToHost, h->stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess || st != SF_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        if (st != SF_OK) return st;
+        return cuda_fail(h, e != cudaSuccess ? e : e2, "sf_step_host capture");
+    }
+    c.graph = graph;
+    e = cudaGraphInstantiate(&c.exec, graph, 0);
+    if (e != cudaSuccess) {
+        drop_host_step(h);
+        return cuda_fail(h, e, "sf_step_host instantiate");
+    }
+    c.dt = dt; c.substeps = substeps; c.gen = h->gen;
+    c.ha = h_actions; c.hr = h_reward; c.hd = h_done;
+    find_copy_nodes(h);
+    SF_CUDA(h, cudaGraphLaunch(c.exec, h->stream));
+    SF_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SF_OK;
+}
+
 sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substeps, int iters, int32_t* out_shape,
                       float* out_ms) {
     if (!h) return SF_ERR_INVALID_ARG;
+    ++h->gen;   // a step captured by sf_step_host re-captures with the tuned shape
     if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_autotune: no roads loaded");
     if (iters < 1) return fail(h, SF_ERR_INVALID_ARG, "sf_autotune: iters must be >= 1");
     const size_t A = (size_t)h->A;

@@ -69,6 +69,7 @@ def lib():
         sig = {
             "sf_create": ([vp, vp, vp], i32), "sf_destroy": ([vp], i32), "sf_load_roads": ([vp, vp], i32),
             "sf_step": ([vp, vp, f32, C.c_int], i32), "sf_get_obs": ([vp, vp, vp, vp, vp], i32),
+            "sf_step_host": ([vp, vp, vp, vp, f32, C.c_int], i32),
             "sf_output_ptrs": ([vp, vp], i32), "sf_observe_full": ([vp, vp, vp, vp, vp, vp], i32), "sf_get_indices": ([vp, vp, vp, vp, vp], i32), "sf_reset": ([vp, vp], i32), "sf_place_agents": ([vp, vp], i32),
             "sf_get_state": ([vp, vp, vp], i32), "sf_set_state": ([vp, vp, vp], i32),
             "sf_save_state": ([vp, C.c_char_p], i32), "sf_load_state": ([vp, C.c_char_p], i32),
@@ -162,6 +163,13 @@ def sf_load_roads(h, scene):
 
 def sf_step(h, d_actions, dt=1.0 / 30.0, substeps=4):
     _check(lib().sf_step(h, _ptr(d_actions), float(dt), int(substeps)), h)
+
+
+def sf_step_host(h, h_actions, h_reward, h_done, dt=1.0 / 30.0, substeps=4):
+    """One step end to end from host buffers (numpy arrays or CPU tensors,
+    page-locked for the captured-graph path): actions in, rewards and done
+    flags out; returns when they are in host memory."""
+    _check(lib().sf_step_host(h, _ptr(h_actions), _ptr(h_reward), _ptr(h_done), float(dt), int(substeps)), h)
 
 
 def sf_get_obs(h, d_obs=None, d_reward=None, d_done=None, d_events=None):

@@ -98,3 +98,46 @@ def test_graph_with_surrogate_matches_individual_calls():
     assert sf.sf_surrogate_audit(W1.h)[1] == sf.sf_surrogate_audit(W2.h)[1] > 0
     sf.sf_graph_destroy(g)
     sf.sf_surrogate_destroy(sur)
+
+
+def test_step_from_host_buffers_equals_device_step():
+    """sf_step_host (copy in, step, copies out, one captured graph for
+    page-locked buffers) gives the device step's rewards, done flags and state
+    bit for bit: replays, a ring of page-locked action buffers (the graph's
+    copies are retargeted), pageable numpy buffers (no graph) and a re-capture
+    after sf_autotune."""
+    sc = synth.procedural_scene(6, 16, seed_base=720)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    W1, W2 = world(sc, s1), world(sc, s2)
+    A = W1.A
+    acts = synth.ou_actions(A, 24, seed=6)
+    ring = [torch.as_tensor(acts[t]).pin_memory() for t in range(3)]
+    rew_h = torch.empty(A, dtype=torch.float32).pin_memory()
+    done_h = torch.empty(A, dtype=torch.uint8).pin_memory()
+    rew_np, done_np = np.zeros(A, np.float32), np.zeros(A, np.uint8)
+    act_dev = torch.empty((A, 3), device="cuda")
+    rew_dev = torch.empty(A, device="cuda")
+    done_dev = torch.empty(A, dtype=torch.uint8, device="cuda")
+    for t in range(24):
+        if t == 12:
+            with torch.cuda.stream(s2):
+                sf.sf_autotune(W2.h, torch.zeros((A, 3), device="cuda"), iters=2)
+            torch.cuda.synchronize()
+        if t < 16:
+            a_h = ring[t % 3]
+            a_h.copy_(torch.as_tensor(acts[t]))
+            sf.sf_step_host(W2.h, a_h, rew_h, done_h)
+            r2, d2 = rew_h.numpy().copy(), done_h.numpy().copy()
+        else:
+            sf.sf_step_host(W2.h, np.ascontiguousarray(acts[t]), rew_np, done_np)
+            r2, d2 = rew_np.copy(), done_np.copy()
+        with torch.cuda.stream(s1):
+            act_dev.copy_(torch.as_tensor(acts[t]))
+            sf.sf_step(W1.h, act_dev)
+            sf.sf_get_obs(W1.h, None, rew_dev, done_dev, None)
+        torch.cuda.synchronize()
+        assert np.array_equal(rew_dev.cpu().numpy(), r2), t
+        assert np.array_equal(done_dev.cpu().numpy(), d2), t
+    F1, I1, _ = sf.sf_get_state(W1.h)
+    F2, I2, _ = sf.sf_get_state(W2.h)
+    assert np.array_equal(F1, F2) and np.array_equal(I1, I2)
