@@ -293,7 +293,7 @@ def run_paper_loop(name, steps, warmup, rank, torch, sf, stream, nw=0, pack=0, s
                 mean_road=float(n_road.mean()), mean_veh=float(n_veh.mean()))
 
 
-def run_ppo(name, iters, rank, torch, sf, stream):
+def run_ppo(name, iters, rank, torch, sf, stream, profile_update=False):
     """On-device PPO with the paper's hyperparameters (App. L: horizon 128, 16
     minibatches, 5 epochs): per iteration one rollout (policy and value forward,
     Gaussian sampling, the step) and one update (GAE and 80 minibatch steps),
@@ -318,8 +318,14 @@ def run_ppo(name, iters, rank, torch, sf, stream):
         ev[i][0].record(stream)
         sf.sf_ppo_collect(ppo)
         ev[i][1].record(stream)
+        if profile_update:                        # an external profiler captures this update only
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
         sf.sf_ppo_update(ppo, want_stats=False)
         ev[i][2].record(stream)
+        if profile_update:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
     torch.cuda.synchronize()
     collect_ms = np.array([e[0].elapsed_time(e[1]) for e in ev])
     update_ms = np.array([e[1].elapsed_time(e[2]) for e in ev])
@@ -382,6 +388,13 @@ def main_ours(args):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        if name == "ppo":                             # profiling target: the PPO leg alone
+            r = run_ppo("256x16", 1 if args.profile_update else 3, rank, torch, sf, stream,
+                        profile_update=args.profile_update)
+            if rank == 0:
+                print(json.dumps({"profile_run": name, "rollout_ms": r["collect_ms"], "update_ms": r["update_ms"]}))
+            clocks.stop()
+            return
         if name.startswith("paper"):                  # profiling target: the paper loop alone
             r = run_paper_loop(name[5:], args.steps, args.warmup, rank, torch, sf, stream, nw=args.nw, pack=args.pack,
                                stage=args.stage, split=args.split)
@@ -655,8 +668,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--only", default=None,
-                    choices=list(WORKLOADS) + ["ragged1024", "4096x16+policy", "paper256x16", "paper4096x16"],
-                    help="profiling: run one workload only (paper*: the full-observation + late-fusion loop)")
+                    choices=list(WORKLOADS) + ["ragged1024", "4096x16+policy", "paper256x16", "paper4096x16", "ppo"],
+                    help="profiling: run one workload only (paper*: the full-observation + late-fusion loop; "
+                         "ppo: the on-device PPO leg)")
+    ap.add_argument("--profile-update", action="store_true",
+                    help="with --only ppo: one iteration, its update bracketed by cudaProfilerStart / Stop")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling: no end-to-end leg")
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
     ap.add_argument("--nw", type=int, default=0, help="warps per block (1, 2, 4, 8; 0 = autotuned)")
