@@ -593,13 +593,17 @@ def step_kernels(tuned) -> str:
 
 
 def kernel_source_tag():
-    """First 12 hex digits of the SHA-1 of the step kernels' sources: a DRAM
-    traffic figure holds only for the source it was captured on."""
+    """First 12 hex digits of the SHA-1 of the step kernels' code (sf_world.cu
+    then sf_internal.cuh, comments dropped and white space collapsed): a DRAM
+    traffic figure holds only for the code it was captured on."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for f in ("sf_world.cu", "sf_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2605_08528_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2605_08528_b300", "csrc", f)) as fh:
+            code = re.sub(r"/\*.*?\*/", " ", fh.read(), flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(re.sub(r"\s+", " ", code).strip().encode())
     return h.hexdigest()[:12]
 
 

@@ -1495,13 +1495,6 @@ __device__ __forceinline__ void lanes_events_b(const WorldArgs& args, const Slot
     }
 }
 
-// respawns of the marked lanes (App. J), every slot of the pack in index
-// order, each spaced from the other alive agents of its own world.  The
-// candidate draws of the up to kSpawnTries attempts are independent, so lane
-// r computes attempt r (its global loads overlap); the attempts are then
-// scored in order exactly as a sequential loop would: the first one at least
-// the spacing away is taken, else the one with the largest clearance (first
-// on ties).
 // spawn candidates (x, y, psi, goal x, goal y, v0) of every try of every slot
 // of a pack for the slot's next episode, drawn ahead of the respawns by threads
 // t = 0..nt-1 (the draws depend on the slot, its episode and the try only)
@@ -1519,7 +1512,13 @@ __device__ __forceinline__ void draw_spawns(const WorldArgs& args, const int4& p
     }
 }
 
-// respawns in slot order; `pre` (may be null) holds the candidates drawn ahead
+// respawns of the marked lanes (App. J), every slot of the pack in index
+// order, each spaced from the other alive agents of its own world.  A slot's
+// kSpawnTries candidate draws depend on the slot, its episode and the try
+// only, so they are read from `pre` (drawn ahead; may be null) or drawn for up
+// to kSpawnGroup slots at once, one lane per (slot, try); the tries are then
+// scored as a sequential loop would: the first one at least the spacing away
+// is taken, else the one with the largest clearance (first on ties).
 __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot& c, int lane, Agent& A,
                                               bool& alive, bool respawn, uint32_t& ev,
                                               const float (*pre)[kSpawnDraws] = nullptr) {
