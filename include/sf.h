@@ -199,12 +199,14 @@ sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps);
  * is copied to the device, the step runs, and the rewards [A] float32 and done
  * flags [A] uint8 are copied into h_reward and h_done; returns when they are in
  * host memory (synchronous).  With a non-default stream and page-locked buffers
- * (cudaHostAlloc / cudaHostRegister) the copies and the step are captured into
- * one CUDA graph that later calls with the same dt and substeps replay (other
- * page-locked buffers retarget its copies); the graph is re-captured after
- * sf_load_roads or sf_autotune.  Pageable buffers or the legacy stream run the
- * copies and the step without a graph.  The buffers are caller-owned and must
- * stay valid during the call.
+ * (cudaHostAlloc / cudaHostRegister) the transfers and the step are captured
+ * into one CUDA graph that later calls with the same dt and substeps replay
+ * (other page-locked buffers retarget its transfers); buffers with a device
+ * mapping are read and written in place by two small kernels of the graph,
+ * others by copy nodes.  The graph is re-captured after sf_load_roads or
+ * sf_autotune.  Pageable buffers or the legacy stream run copies and the step
+ * without a graph.  The buffers are caller-owned and must stay valid during the
+ * call.
  * Errors: SF_ERR_STATE (no roads), SF_ERR_INVALID_ARG (NULL buffer, dt <= 0,
  * substeps outside 1..64), SF_ERR_OOM, SF_ERR_CUDA. */
 sf_status sf_step_host(sf_handle h, const float* h_actions, float* h_reward, uint8_t* h_done, float dt,

@@ -62,7 +62,9 @@ struct sf_ctx {
         float* d_act = nullptr;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
-        cudaGraphNode_t n_act = nullptr, n_rew = nullptr, n_done = nullptr;
+        bool mapped = false;    // the kernels read / write the host buffers through their device mapping
+        cudaGraphNode_t n_act = nullptr, n_rew = nullptr, n_done = nullptr;   // copy nodes (not mapped)
+        cudaGraphNode_t n_in = nullptr, n_out = nullptr;                      // kernel nodes (mapped)
     } hs;
 };
 
@@ -603,6 +605,29 @@ sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps) {
 
 namespace {
 
+// the actions of a step from (device-mapped) host memory, and its rewards and
+// done flags back to it: plain loads and stores over the host link, one
+// element per thread, instead of copy operations
+__global__ void host_in_kernel(const float* __restrict__ src, float* __restrict__ dst, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i];
+}
+__global__ void host_out_kernel(const float* __restrict__ rew, const uint8_t* __restrict__ done,
+                                float* __restrict__ hrew, uint8_t* __restrict__ hdone, int A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < A) { hrew[i] = rew[i]; hdone[i] = done[i]; }
+}
+
+// the device address of a page-locked host buffer, or null when it has none
+void* device_view(const void* p) {
+    void* d = nullptr;
+    if (cudaHostGetDevicePointer(&d, const_cast<void*>(p), 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return d;
+}
+
 bool page_locked(const void* p) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -620,7 +645,15 @@ void find_copy_nodes(sf_ctx* h) {
     cudaGraphGetNodes(h->hs.graph, nodes.data(), &n);
     for (cudaGraphNode_t nd : nodes) {
         cudaGraphNodeType t;
-        if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeMemcpy) continue;
+        if (cudaGraphNodeGetType(nd, &t) != cudaSuccess) continue;
+        if (t == cudaGraphNodeTypeKernel) {
+            cudaKernelNodeParams kp{};
+            if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+            if (kp.func == reinterpret_cast<void*>(host_in_kernel)) h->hs.n_in = nd;
+            else if (kp.func == reinterpret_cast<void*>(host_out_kernel)) h->hs.n_out = nd;
+            continue;
+        }
+        if (t != cudaGraphNodeTypeMemcpy) continue;
         cudaMemcpy3DParms prm{};
         if (cudaGraphMemcpyNodeGetParams(nd, &prm) != cudaSuccess) continue;
         if (prm.srcPtr.ptr == h->hs.ha) h->hs.n_act = nd;
@@ -653,36 +686,76 @@ sf_status sf_step_host(sf_handle h, const float* h_actions, float* h_reward, uin
         return SF_OK;
     }
     const bool pinned = page_locked(h_actions) && page_locked(h_reward) && page_locked(h_done);
-    if (!h->stream || !pinned) {   // no graph: plain copies around the step
-        SF_CUDA(h, cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream));
+    if (!h->stream || !pinned || A == 0) {   // no graph: plain copies around the step
+        if (A > 0) SF_CUDA(h, cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream));
         sf_status st = sf_step(h, c.d_act, dt, substeps);
         if (st != SF_OK) return st;
-        SF_CUDA(h, cudaMemcpyAsync(h_reward, h->out.reward, A * 4, cudaMemcpyDeviceToHost, h->stream));
-        SF_CUDA(h, cudaMemcpyAsync(h_done, h->out.done, A, cudaMemcpyDeviceToHost, h->stream));
+        if (A > 0) {
+            SF_CUDA(h, cudaMemcpyAsync(h_reward, h->out.reward, A * 4, cudaMemcpyDeviceToHost, h->stream));
+            SF_CUDA(h, cudaMemcpyAsync(h_done, h->out.done, A, cudaMemcpyDeviceToHost, h->stream));
+        }
         SF_CUDA(h, cudaStreamSynchronize(h->stream));
         return SF_OK;
     }
-    if (same && c.n_act && c.n_rew && c.n_done) {   // other page-locked buffers: retarget the copies
-        SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_act, c.d_act, h_actions, A * 12,
-                                                      cudaMemcpyHostToDevice));
-        SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_rew, h_reward, h->out.reward, A * 4,
-                                                      cudaMemcpyDeviceToHost));
-        SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_done, h_done, h->out.done, A,
-                                                      cudaMemcpyDeviceToHost));
+    // page-locked buffers with device addresses are read and written by two small
+    // kernels inside the graph; others get copy nodes
+    const float* da = static_cast<const float*>(device_view(h_actions));
+    float* dr = static_cast<float*>(device_view(h_reward));
+    uint8_t* dd = static_cast<uint8_t*>(device_view(h_done));
+    const bool mapped = da && dr && dd;
+    const int n3 = (int)(3 * A), nA = (int)A;
+    if (same && c.mapped == mapped) {   // other buffers: retarget the graph's transfers
+        if (mapped && c.n_in && c.n_out) {
+            cudaKernelNodeParams kp{};
+            SF_CUDA(h, cudaGraphKernelNodeGetParams(c.n_in, &kp));
+            float* dst = c.d_act;
+            void* in_args[] = {&da, &dst, const_cast<int*>(&n3)};
+            kp.kernelParams = in_args;
+            kp.extra = nullptr;
+            SF_CUDA(h, cudaGraphExecKernelNodeSetParams(c.exec, c.n_in, &kp));
+            SF_CUDA(h, cudaGraphKernelNodeGetParams(c.n_out, &kp));
+            const float* rew = h->out.reward;
+            const uint8_t* dn = h->out.done;
+            void* out_args[] = {&rew, &dn, &dr, &dd, const_cast<int*>(&nA)};
+            kp.kernelParams = out_args;
+            kp.extra = nullptr;
+            SF_CUDA(h, cudaGraphExecKernelNodeSetParams(c.exec, c.n_out, &kp));
+        } else if (!mapped && c.n_act && c.n_rew && c.n_done) {
+            SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_act, c.d_act, h_actions, A * 12,
+                                                          cudaMemcpyHostToDevice));
+            SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_rew, h_reward, h->out.reward, A * 4,
+                                                          cudaMemcpyDeviceToHost));
+            SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_done, h_done, h->out.done, A,
+                                                          cudaMemcpyDeviceToHost));
+        } else {
+            goto capture;
+        }
         c.ha = h_actions; c.hr = h_reward; c.hd = h_done;
         SF_CUDA(h, cudaGraphLaunch(c.exec, h->stream));
         SF_CUDA(h, cudaStreamSynchronize(h->stream));
         return SF_OK;
     }
+capture:
     drop_host_step(h);
     SF_CUDA(h, cudaStreamSynchronize(h->stream));
     SF_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream);
+    cudaError_t e = cudaSuccess;
+    if (mapped) {
+        host_in_kernel<<<(n3 + 255) / 256, 256, 0, h->stream>>>(da, c.d_act, n3);
+        e = cudaGetLastError();
+    } else {
+        e = cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream);
+    }
     sf_status st = e == cudaSuccess ? sf_step(h, c.d_act, dt, substeps) : SF_ERR_CUDA;
-    if (e == cudaSuccess && st == SF_OK)
-        e = cudaMemcpyAsync(h_reward, h->out.reward, A * 4, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess && st == SF_OK)
-        e = cudaMemcpyAsync(h_done, h->out.done, A, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && st == SF_OK) {
+        if (mapped) {
+            host_out_kernel<<<(nA + 255) / 256, 256, 0, h->stream>>>(h->out.reward, h->out.done, dr, dd, nA);
+            e = cudaGetLastError();
+        } else {
+            e = cudaMemcpyAsync(h_reward, h->out.reward, A * 4, cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h_done, h->out.done, A, cudaMemcpyDeviceToHost, h->stream);
+        }
+    }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess || st != SF_OK) {
@@ -696,7 +769,7 @@ sf_status sf_step_host(sf_handle h, const float* h_actions, float* h_reward, uin
         drop_host_step(h);
         return cuda_fail(h, e, "sf_step_host instantiate");
     }
-    c.dt = dt; c.substeps = substeps; c.gen = h->gen;
+    c.dt = dt; c.substeps = substeps; c.gen = h->gen; c.mapped = mapped;
     c.ha = h_actions; c.hr = h_reward; c.hd = h_done;
     find_copy_nodes(h);
     SF_CUDA(h, cudaGraphLaunch(c.exec, h->stream));
