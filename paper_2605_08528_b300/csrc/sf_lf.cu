@@ -11,14 +11,18 @@
 // The max-pool is masked by the group's count (the observation fills a prefix
 // of the slots); an empty group pools to zeros.
 //
-// lf_set_kernel (one persistent CTA of 8 warps per SM) runs both networks'
-// encoders of one group over work items of 32 consecutive agents.  An item's
-// valid slots are concatenated (no padding) into tiles of 128 rows:
-//   gather   rows -> bf16 A1 [128 slots][16 features] (swizzled smem), the
-//            next tile's global loads issued before this tile's epilogues
-//   MMA 1    D1[128 slots][192] = A1 . W1^T             (both nets, K = 16)
-//   epi 1    bias + ELU -> bf16 H1[net][128 slots][96]  (K-major for MMA 2)
-//   MMA 2    D2[net][128 features][128 slots] = W2 . H1^T  (K = 96; features
+// lf_set_kernel runs the encoder of one group over work items of 32
+// consecutive agents: two persistent CTAs of 8 warps per SM, even CTAs the
+// actor's network, odd ones the critic's (each holds its network's weights in
+// shared memory and 256 TMEM columns).  An item's slots are concatenated into
+// tiles of 128 rows, each agent's filled slots padded to a multiple of 8 rows
+// (an 8-row group belongs to one agent):
+//   gather   rows -> bf16 A1 [128 slots][16 inputs] (swizzled smem; the
+//            layer-1 bias rides on input 15 = 1), the next tile's global loads
+//            issued before this tile's epilogues
+//   MMA 1    D1[128 slots][96] = A1 . W1^T              (K = 16)
+//   epi 1    ELU -> bf16 H1[128 slots][96]              (K-major for MMA 2)
+//   MMA 2    D2[128 features][128 slots] = W2 . H1^T    (K = 96; features
 //            96..127 are zero rows of the weight image)
 //   epi 2    each thread owns one feature and walks the tile's slot columns:
 //            a running max, flushed to the item's pool (shared atomicMax on
