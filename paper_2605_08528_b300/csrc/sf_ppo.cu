@@ -93,25 +93,63 @@ __global__ void sample_kernel(const float* __restrict__ mu, const float* __restr
     logp[a] = logp3(x, m, s);
 }
 
-// rewards [T][A] and done flags, one step at a time; reward sum for the statistics
+// rewards [T][A] and done flags, one step at a time
 __global__ void record_step_kernel(const float* __restrict__ rew_in, const uint8_t* __restrict__ done_in, int A,
-                                   float* __restrict__ rew, uint8_t* __restrict__ done, float* __restrict__ scal) {
+                                   float* __restrict__ rew, uint8_t* __restrict__ done) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    float r = 0.f;
     if (a < A) {
-        r = rew_in[a];
-        rew[a] = r;
+        rew[a] = rew_in[a];
         done[a] = done_in[a];
     }
+}
+
+// Deterministic sums: every reduction of the update adds per-block partial
+// sums (warps and then the block's warps in a fixed order) and then the
+// partials in order on one thread, so repeated runs agree bit for bit.
+template <int K, class T>
+__device__ __forceinline__ void block_sums(T (&v)[K], T* out) {   // 256 threads; out[K] on thread 0
+    __shared__ T red[8][K];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xFFFFFFFFu, r, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&scal[S_REW], r);
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xFFFFFFFFu, v[k], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[threadIdx.x >> 5][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            T t = 0;
+            for (int w = 0; w < 8; ++w) t += red[w][k];
+            out[k] = t;
+        }
+}
+
+// sum of n values: block j sums the j-th of gridDim.x contiguous chunks
+constexpr int kSumBlocks = 148;
+__global__ void sum_part_kernel(const float* __restrict__ x, size_t n, float* __restrict__ part) {
+    const size_t chunk = (n + gridDim.x - 1) / gridDim.x, i0 = (size_t)blockIdx.x * chunk;
+    const size_t i1 = i0 + chunk < n ? i0 + chunk : n;
+    float v[1] = {0.f};
+    for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) v[0] += x[i];
+    block_sums<1>(v, part + blockIdx.x);
+}
+// out[k] (op) sum over j of part[j * stride + k], k < K, in order of j
+template <class T>
+__global__ void parts_final_kernel(const T* __restrict__ part, int P, int stride, int K, T* __restrict__ out,
+                                   bool accumulate) {
+    const int k = threadIdx.x;
+    if (k >= K) return;
+    T t = 0;
+    for (int j = 0; j < P; ++j) t += part[(size_t)j * stride + k];
+    out[k] = accumulate ? out[k] + t : t;
 }
 
 // GAE per agent (one thread): delta_t = r_t + g (1 - d_t) V_{t+1} - V_t, A_t = delta_t + g l (1 - d_t) A_{t+1}
 __global__ void gae_kernel(const float* __restrict__ rew, const uint8_t* __restrict__ done,
                            const float* __restrict__ val, int T, int A, float gamma, float lam,
-                           float* __restrict__ adv, float* __restrict__ ret, double* __restrict__ moments) {
+                           float* __restrict__ adv, float* __restrict__ ret, double* __restrict__ mpart) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     double s1 = 0.0, s2 = 0.0;
     if (a < A) {
@@ -129,15 +167,8 @@ __global__ void gae_kernel(const float* __restrict__ rew, const uint8_t* __restr
             s2 += (double)na * na;
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
-        s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&moments[0], s1);
-        atomicAdd(&moments[1], s2);
-    }
+    double v[2] = {s1, s2};
+    block_sums<2>(v, mpart + 2 * (size_t)blockIdx.x);   // summed in order into the moments
 }
 
 // advantages -> (A - mean) / (std + 1e-8) over the rollout (population std)
@@ -180,8 +211,7 @@ __global__ void gather_kernel(Perm p, size_t i0, int B, const float* __restrict_
 __global__ void loss_grad_kernel(int B, const float* __restrict__ g_small, const float* __restrict__ mu_new,
                                  const float* __restrict__ v_new, const float* __restrict__ log_std,
                                  const float* __restrict__ log_std_old, float clip, float vf_coef,
-                                 float* __restrict__ d_mu, float* __restrict__ d_v, float* __restrict__ d_std,
-                                 float* __restrict__ scal) {
+                                 float* __restrict__ d_mu, float* __restrict__ d_v, float* __restrict__ lpart) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     float ds[3] = {0.f, 0.f, 0.f}, pol = 0.f, vl = 0.f, kl = 0.f;
     if (row < B) {
@@ -212,18 +242,20 @@ __global__ void loss_grad_kernel(int B, const float* __restrict__ g_small, const
         vl = dv * dv;
     }
     float vals[6] = {ds[0], ds[1], ds[2], pol, vl, kl};
+    block_sums<6>(vals, lpart + 8 * (size_t)blockIdx.x);   // summed in order by loss_sums
+}
+
+// the loss block sums in order: log-std gradient into d_std[0..2], policy loss,
+// value loss and KL into their minibatch sums
+__global__ void loss_sums_kernel(const float* __restrict__ lpart, int P, float* __restrict__ d_std,
+                                 float* __restrict__ scal) {
+    if (threadIdx.x != 0) return;
+    float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int j = 0; j < P; ++j)
 #pragma unroll
-    for (int k = 0; k < 6; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) vals[k] += __shfl_xor_sync(0xFFFFFFFFu, vals[k], o);
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&d_std[0], vals[0]);
-        atomicAdd(&d_std[1], vals[1]);
-        atomicAdd(&d_std[2], vals[2]);
-        atomicAdd(&scal[S_POL], vals[3]);
-        atomicAdd(&scal[S_VAL], vals[4]);
-        atomicAdd(&scal[S_KL], vals[5]);
-    }
+        for (int k = 0; k < 6; ++k) t[k] += lpart[8 * (size_t)j + k];
+    d_std[0] += t[0]; d_std[1] += t[1]; d_std[2] += t[2];
+    scal[S_POL] += t[3]; scal[S_VAL] += t[4]; scal[S_KL] += t[5];
 }
 
 // minibatch scalars: mean KL -> learning rate (App. L rule), entropy term of the log-std gradient,
@@ -284,6 +316,9 @@ struct sf_ppo {
     float *log_std = nullptr, *log_std_old = nullptr, *g_std = nullptr, *m_std = nullptr, *v_std = nullptr;
     float* scal = nullptr;
     double* moments = nullptr;
+    float* lpart = nullptr;     // [blocks of a minibatch][8] loss block sums
+    double* mpart = nullptr;    // [blocks of the agents][2] advantage moment block sums
+    float* rpart = nullptr;     // [kSumBlocks] rollout reward block sums
     float *g_obs = nullptr, *g_small = nullptr, *mu_new = nullptr, *v_new = nullptr, *d_mu = nullptr, *d_v = nullptr;
     bool collected = false;
 };
@@ -366,6 +401,8 @@ sf_status sf_ppo_create(sf_handle h, sf_mlp_handle actor, sf_mlp_handle critic, 
               palloc(p, &p->log_std, 3) && palloc(p, &p->log_std_old, 3) && palloc(p, &p->g_std, 3) &&
               palloc(p, &p->m_std, 3) && palloc(p, &p->v_std, 3) && palloc(p, &p->scal, S_COUNT) &&
               palloc(p, &p->moments, 2) && palloc(p, &p->g_obs, (size_t)B * kObsW) &&
+              palloc(p, &p->lpart, (size_t)grid_for(B) * 8) && palloc(p, &p->mpart, (size_t)grid_for(A) * 2) &&
+              palloc(p, &p->rpart, (size_t)kSumBlocks) &&
               palloc(p, &p->g_small, (size_t)B * 12) && palloc(p, &p->mu_new, (size_t)B * 3) &&
               palloc(p, &p->v_new, (size_t)B) && palloc(p, &p->d_mu, (size_t)B * 3) && palloc(p, &p->d_v, (size_t)B);
     if (ok) ok = sf_mlp_reserve(actor, std::max(A, B)) == SF_OK && sf_mlp_reserve(critic, std::max(A, B)) == SF_OK;
@@ -399,8 +436,6 @@ sf_status sf_ppo_collect(sf_ppo_handle p) {
     if (s != SF_OK) return pfail(p, s, "sf_ppo_collect: world outputs");
     const int A = p->A;
     cudaError_t e = cudaMemcpyAsync(p->log_std_old, p->log_std, 12, cudaMemcpyDeviceToDevice, p->st);
-    const float zero = 0.f;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->scal + S_REW, &zero, 4, cudaMemcpyHostToDevice, p->st);
     for (int t = 0; t < p->T && e == cudaSuccess; ++t) {
         float* obs_t = p->obs + (size_t)t * A * kObsW;
         e = cudaMemcpyAsync(obs_t, o.obs, (size_t)A * kObsW * 4, cudaMemcpyDeviceToDevice, p->st);
@@ -416,7 +451,7 @@ sf_status sf_ppo_collect(sf_ppo_handle p) {
         s = sf_step(p->h, p->act + (size_t)t * A * 3, p->cfg.dt, p->cfg.substeps);
         if (s != SF_OK) return pfail(p, s, std::string("sf_ppo_collect: step: ") + sf_last_error(p->h));
         record_step_kernel<<<grid_for(A), 256, 0, p->st>>>(o.reward, o.done, A, p->rew + (size_t)t * A,
-                                                           p->done + (size_t)t * A, p->scal);
+                                                           p->done + (size_t)t * A);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {   // the value of the state after the last step bootstraps GAE
@@ -434,12 +469,14 @@ sf_status sf_ppo_update(sf_ppo_handle p, float* h_stats) {
     const int A = p->A, T = p->T, B = p->B;
     const size_t N = (size_t)A * T;
     const sf_ppo_config& c = p->cfg;
-    cudaError_t e = cudaMemsetAsync(p->moments, 0, 16, p->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->scal + S_ACC_POL, 0, 4 * 4, p->st);
+    cudaError_t e = cudaMemsetAsync(p->scal + S_ACC_POL, 0, 4 * 4, p->st);
     if (e == cudaSuccess) {
         gae_kernel<<<grid_for(A), 256, 0, p->st>>>(p->rew, p->done, p->val, T, A, c.gamma, c.lam, p->adv, p->ret,
-                                                    p->moments);
+                                                    p->mpart);
+        parts_final_kernel<double><<<1, 32, 0, p->st>>>(p->mpart, (int)grid_for(A), 2, 2, p->moments, false);
         normalise_kernel<<<grid_for(N), 256, 0, p->st>>>(p->adv, N, p->moments);
+        sum_part_kernel<<<kSumBlocks, 256, 0, p->st>>>(p->rew, N, p->rpart);   // the rollout's reward sum
+        parts_final_kernel<float><<<1, 32, 0, p->st>>>(p->rpart, kSumBlocks, 1, 1, p->scal + S_REW, false);
         e = cudaGetLastError();
     }
     int nmb = 0;
@@ -468,7 +505,8 @@ sf_status sf_ppo_update(sf_ppo_handle p, float* h_stats) {
             if (s != SF_OK) return pfail(p, s, "sf_ppo_update: forward");
             loss_grad_kernel<<<grid_for(B), 256, 0, p->st>>>(B, p->g_small, p->mu_new, p->v_new, p->log_std,
                                                               p->log_std_old, c.clip, c.vf_coef, p->d_mu, p->d_v,
-                                                              p->g_std, p->scal);
+                                                              p->lpart);
+            loss_sums_kernel<<<1, 32, 0, p->st>>>(p->lpart, (int)grid_for(B), p->g_std, p->scal);
             e = cudaGetLastError();
             if (e != cudaSuccess) break;
             s = sf_mlp_backward_on(p->actor, p->st, p->d_mu, 3, B);
@@ -534,7 +572,8 @@ sf_status sf_ppo_loss_grads(sf_ppo_handle p, const float* d_obs, const float* d_
     if (e == cudaSuccess) {
         loss_grad_kernel<<<grid_for(rows), 256, 0, p->st>>>(rows, d_small, mu, v, p->log_std, p->log_std_old, c.clip,
                                                              c.vf_coef, d_dmean ? d_dmean : p->d_mu,
-                                                             d_dvalue ? d_dvalue : p->d_v, p->g_std, p->scal);
+                                                             d_dvalue ? d_dvalue : p->d_v, p->lpart);
+        loss_sums_kernel<<<1, 32, 0, p->st>>>(p->lpart, (int)grid_for(rows), p->g_std, p->scal);
         e = cudaGetLastError();
     }
     float sc[S_COUNT], gs[3];

@@ -84,8 +84,13 @@ def test_mlp_forward_against_fp64(dims, hidden, out, batch):
     sf.sf_mlp_destroy(m)
 
 
-def test_mlp_gradients_against_fp64():
-    dims, hidden, out, batch = [30, 256, 256, 256, 16], sf.ACT_SILU, sf.ACT_NONE, 1024
+@pytest.mark.parametrize("dims,hidden,out,batch", [([30, 256, 256, 256, 16], sf.ACT_SILU, sf.ACT_NONE, 1024),
+                                                   ([320, 512, 512, 3], sf.ACT_ELU, sf.ACT_TANH, 1736),
+                                                   ([30, 64, 5], sf.ACT_ELU, sf.ACT_NONE, 200)])
+def test_mlp_gradients_against_fp64(dims, hidden, out, batch):
+    """Weight and bias gradients against the FP64 oracle: the bias sums run in
+    batch // 256 row splits, at least one (four even ones; six with a short
+    last one; one), over column groups wider than some layers (3, 5 outputs)."""
     rng = np.random.default_rng(3)
     m, params = make_mlp(dims, hidden, out, rng)
     x = rng.normal(0, 1, (batch, dims[0])).astype(np.float32)

@@ -121,3 +121,29 @@ def test_training_fits_the_value_function():
     assert min(vals[3:]) < vals[0]
     sf.sf_ppo_destroy(p)
     W.close()
+
+
+def test_updates_are_deterministic():
+    """Two PPO runs from the same seeds give bit-identical statistics, log
+    standard deviations and weights: every reduction of the update (GAE
+    moments, loss sums, split-K weight gradients, bias gradients, the gradient
+    norm) runs in a fixed order."""
+    out = []
+    for _ in range(2):
+        W, actor, critic, p, cfg, stream = setup(horizon=16, minibatches=4, epochs=2, worlds=4)
+        stats = []
+        for it in range(2):
+            sf.sf_ppo_collect(p)
+            stats.append(np.asarray(sf.sf_ppo_update(p)))
+        torch.cuda.synchronize()
+        weights = [sf.sf_mlp_get_layer(m, l, o, i)[0]
+                   for m, dims in ((actor, (320, 512, 512, 3)), (critic, (320, 512, 512, 1)))
+                   for l, (i, o) in enumerate(zip(dims[:-1], dims[1:]))]
+        out.append((np.stack(stats), np.asarray(sf.sf_ppo_log_std(p)), weights))
+        sf.sf_ppo_destroy(p)
+        sf.sf_mlp_destroy(actor)
+        sf.sf_mlp_destroy(critic)
+        W.close()
+    (s1, l1, w1), (s2, l2, w2) = out
+    assert np.array_equal(s1, s2) and np.array_equal(l1, l2)
+    assert all(np.array_equal(a, b) for a, b in zip(w1, w2))
