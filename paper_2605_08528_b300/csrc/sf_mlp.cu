@@ -265,6 +265,7 @@ struct sf_mlp {
     float* ws = nullptr;                     // [kSplitMax][max out][max ld] f32 split-K partials of dW
     float* loss = nullptr;
     float* red = nullptr;                    // [kSumsqBlocks] partial sums of the gradient norm
+    const sf_mlp* share = nullptr;           // while set: layer 0 reads its bf16 input (and its transpose) from it
     unsigned* errw = nullptr;
 };
 
@@ -317,6 +318,10 @@ cudaError_t ensure_batch(sf_mlp* m, int B) {
     return e;
 }
 
+// the bf16 input of layer l and its transpose (layer 0 may borrow another network's)
+const __nv_bfloat16* x_in(const sf_mlp* m, int l) { return l == 0 && m->share ? m->share->x[0] : m->x[l]; }
+const __nv_bfloat16* xt_in(const sf_mlp* m, int l) { return l == 0 && m->share ? m->share->xt[0] : m->xt[l]; }
+
 // forward of a batch already converted into x[0] (and xt[0] when training); the
 // last layer writes y_out [B][ldy] (m->y with its padded width when null)
 cudaError_t forward_core(sf_mlp* m, int B, bool train, float* y_out = nullptr, int ldy = 0,
@@ -324,7 +329,7 @@ cudaError_t forward_core(sf_mlp* m, int B, bool train, float* y_out = nullptr, i
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < m->L && e == cudaSuccess; ++l) {
         const bool last = l == m->L - 1;
-        e = gemm(m, m->x[l], m->wb[l], m->b[l], B, m->dim[l + 1], m->dim[l + 1], m->ld[l], act_of(m, l),
+        e = gemm(m, x_in(m, l), m->wb[l], m->b[l], B, m->dim[l + 1], m->dim[l + 1], m->ld[l], act_of(m, l),
                  train ? m->z[l] : nullptr, last ? (y_out ? y_out : m->y) : nullptr, last ? nullptr : m->x[l + 1],
                  (train && !last) ? m->xt[l + 1] : nullptr, (last && y_out) ? ldy : m->ld[l + 1], B, st, use_st);
     }
@@ -347,7 +352,7 @@ cudaError_t weight_grad(sf_mlp* m, int l, int B, const __nv_bfloat16* dzt, cudaS
     const int tiles = ((o + 127) / 128) * ((li + bn - 1) / bn), nk = (B + 63) / 64;
     const int S = std::max(1, std::min(std::min(kSplitMax, nk), 296 / std::max(1, tiles)));
     GemmArgs g{};
-    g.A = dzt; g.B = m->xt[l]; g.M = o; g.N = li; g.Nb = li; g.K = B; g.ldc = li; g.act = SF_ACT_NONE;
+    g.A = dzt; g.B = xt_in(m, l); g.M = o; g.N = li; g.Nb = li; g.K = B; g.ldc = li; g.act = SF_ACT_NONE;
     g.bn = bn; g.err = m->errw;
     if (S > 1) { g.ws = m->ws; g.splits = S; } else { g.out_f32 = m->gwfull; }
     cudaError_t e = sf_gemm_launch(g, st);
@@ -662,6 +667,7 @@ sf_status sf_mlp_forward_on(sf_mlp_handle m, cudaStream_t stream, const float* d
     if (e != cudaSuccess) return mfail(m, e == cudaErrorMemoryAllocation ? SF_ERR_OOM : SF_ERR_CUDA, "batch buffers");
     cudaStream_t saved = m->stream;
     m->stream = stream;
+    m->share = nullptr;   // the network's own input from here on
     if (m->dim[0] == m->ld[0] && ldx == m->dim[0] && (reinterpret_cast<uintptr_t>(d_x) & 15) == 0) {
         const size_t n8 = (size_t)batch * m->ld[0] / 8;
         to_bf16_vec8_kernel<<<grid1(n8), 256, 0, stream>>>(d_x, n8, m->x[0]);
@@ -683,6 +689,7 @@ sf_status sf_mlp_train_step(sf_mlp_handle m, const float* d_x, const float* d_t,
     cudaError_t e = ensure_batch(m, batch);
     if (e != cudaSuccess) return mfail(m, SF_ERR_OOM, "batch buffers");
     const int L = m->L, B = batch;
+    m->share = nullptr;
     to_bf16_kernel<<<tgrid(B, m->ld[0]), kTBlock, 0, m->stream>>>(d_x, B, m->dim[0], m->dim[0], m->x[0], m->ld[0],
                                                                        m->xt[0]);
     e = cudaGetLastError();
@@ -723,10 +730,23 @@ sf_status sf_mlp_forward_train_on(sf_mlp_handle m, cudaStream_t st, const float*
         return SF_ERR_INVALID_ARG;
     cudaError_t e = ensure_batch(m, batch);
     if (e != cudaSuccess) return mfail(m, SF_ERR_OOM, "batch buffers");
+    m->share = nullptr;
     to_bf16_kernel<<<tgrid(batch, m->ld[0]), kTBlock, 0, st>>>(d_x, batch, m->dim[0], ldx, m->x[0], m->ld[0],
                                                                     m->xt[0]);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = forward_core(m, batch, true, d_y, ldy, st, true);
+    return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("forward_train: ") + cudaGetErrorString(e));
+}
+
+sf_status sf_mlp_forward_train_shared_on(sf_mlp_handle m, sf_mlp_handle src, cudaStream_t st, int batch, float* d_y,
+                                         int ldy) {
+    if (!m || !src || m == src || !d_y || batch < 8 || batch % 8 != 0 || batch > src->cap ||
+        m->dim[0] != src->dim[0] || ldy < m->dim[m->L])
+        return SF_ERR_INVALID_ARG;
+    cudaError_t e = ensure_batch(m, batch);
+    if (e != cudaSuccess) return mfail(m, SF_ERR_OOM, "batch buffers");
+    m->share = src;   // until the next forward_train of m with its own input
+    e = forward_core(m, batch, true, d_y, ldy, st, true);
     return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("forward_train: ") + cudaGetErrorString(e));
 }
 

@@ -19,6 +19,10 @@ sf_status sf_lf_forward_on(sf_lf_handle m, cudaStream_t stream, const float* d_o
 // forward of `batch` rows keeping the activations the backward needs; outputs d_y [batch][ldy]
 sf_status sf_mlp_forward_train_on(sf_mlp_handle m, cudaStream_t stream, const float* d_x, int ldx, int batch,
                                   float* d_y, int ldy);
+// the same on the input src's last training forward converted (same input width): m's layer 0
+// reads src's bf16 copies, which must stay unchanged until m's backward has run
+sf_status sf_mlp_forward_train_shared_on(sf_mlp_handle m, sf_mlp_handle src, cudaStream_t stream, int batch,
+                                         float* d_y, int ldy);
 // weight and bias gradients of the last training forward from the upstream gradient d_dy [batch][ldy]
 sf_status sf_mlp_backward_on(sf_mlp_handle m, cudaStream_t stream, const float* d_dy, int ldy, int batch);
 // adds the sum of squares of every gradient into *d_acc

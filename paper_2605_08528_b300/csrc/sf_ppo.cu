@@ -500,8 +500,9 @@ sf_status sf_ppo_update(sf_ppo_handle p, float* h_stats) {
                                                                         p->g_small);
             e = cudaGetLastError();
             if (e != cudaSuccess) break;
+            // the critic reads the actor's bf16 copy of the minibatch (converted once)
             sf_status s = sf_mlp_forward_train_on(p->actor, p->st, p->g_obs, kObsW, B, p->mu_new, 3);
-            if (s == SF_OK) s = sf_mlp_forward_train_on(p->critic, p->st, p->g_obs, kObsW, B, p->v_new, 1);
+            if (s == SF_OK) s = sf_mlp_forward_train_shared_on(p->critic, p->actor, p->st, B, p->v_new, 1);
             if (s != SF_OK) return pfail(p, s, "sf_ppo_update: forward");
             loss_grad_kernel<<<grid_for(B), 256, 0, p->st>>>(B, p->g_small, p->mu_new, p->v_new, p->log_std,
                                                               p->log_std_old, c.clip, c.vf_coef, p->d_mu, p->d_v,
