@@ -1202,6 +1202,15 @@ __device__ __forceinline__ void bicycle_step(Agent& A, const float* act, float d
     A.dl = delta; A.dd = 0.f;
 }
 
+// the physics a step kernel is compiled with: the raycast vehicle, the vehicle
+// with the learned surrogate's gate, or the kinematic bicycle (the variants not
+// launched stay out of the kernel's code)
+enum PhysKind { kPhysVehicle = 0, kPhysSurrogate = 1, kPhysBicycle = 2 };
+__host__ __device__ inline int phys_of(const WorldArgs& a) {
+    return a.dynamics == 1 ? kPhysBicycle : (a.surr_mode != 0 ? kPhysSurrogate : kPhysVehicle);
+}
+
+template <int PHYS>
 __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot& c, int lane, Agent& A, bool& alive,
                                               bool& nonfin, float& prevx, float& prevy, float& hx, float& hy,
                                               Exch& E) {
@@ -1216,7 +1225,7 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
     }
     prevx = A.px; prevy = A.py;
     bool gated = false;
-    if (args.dynamics == 1) {   // the bicycle backend replaces the substeps (no contact response)
+    if (PHYS == kPhysBicycle) {   // the bicycle backend replaces the substeps (no contact response)
         if (alive) bicycle_step(A, args.actions + 3 * (size_t)a, args.h * args.substeps);
         if (alive && !finite_agent(A)) {
             nonfin = true;
@@ -1246,7 +1255,8 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
         publish(E, lane, A, sx_, sy_);
         const uint32_t alive_bits = __ballot_sync(kFull, alive);
         __syncwarp();
-        if (s == 0 && args.surr_mode != 0) gated = surr_gate(E, base, n, lane, alive_bits, A, args.h * args.substeps);
+        if (PHYS == kPhysSurrogate && s == 0 && args.surr_mode != 0)
+            gated = surr_gate(E, base, n, lane, alive_bits, A, args.h * args.substeps);
         if (s == 0) {
             E.bud[lane] = budget;
             __syncwarp();
@@ -1691,7 +1701,7 @@ __device__ __forceinline__ void lanes_final_b(const WorldArgs& args, const Slot&
 // features, state; a lane only ever interacts with the slots of its own
 // world.  All NW warps run the road queries, one agent per warp at a time, and
 // write the road-point block of the observation with coalesced stores.
-template <int MODE, int NW>
+template <int MODE, int NW, int PHYS>
 __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_kernel(const WorldArgs args) {
     __shared__ Exch E;
     __shared__ AgentQ Q[32];
@@ -1777,7 +1787,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     if (MODE == kModeStep) {
         float prevx = 0.f, prevy = 0.f;
         if (warp == 0) {
-            lanes_physics(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E);
+            lanes_physics<PHYS>(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E);
             const unsigned ab = __ballot_sync(kFull, alive);
             if (lane == 0) s_alive = ab;
         }
@@ -1872,6 +1882,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
 
 // physics; writes the state, the start-of-step position, the heading and the
 // non-finite flag
+template <int PHYS>
 __global__ void __launch_bounds__(32, 16) phys_kernel(const WorldArgs args) {
     __shared__ Exch E;
     __shared__ int s_slot_w[32], s_wbase[32], s_wn[32];
@@ -1886,7 +1897,7 @@ __global__ void __launch_bounds__(32, 16) phys_kernel(const WorldArgs args) {
     bool alive = c.has && (status_of(A.meta) & kAlive), nonfin = false;
     float prevx = 0.f, prevy = 0.f, hx = 1.f, hy = 0.f;
     if (blockIdx.x == 0 && lane == 0) *args.sc.fix_count = 0u;   // the events kernel appends after this kernel
-    lanes_physics(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E);
+    lanes_physics<PHYS>(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E);
     if (c.has) {
         store_agent(args.st, c.a, A);
         args.sc.prev[c.a] = make_float2(prevx, prevy);
@@ -2161,7 +2172,11 @@ cudaError_t sf_launch_surr_collect(const WorldArgs& a, const float4* snap, const
 template <int NWQ>
 static cudaError_t launch_split(const WorldArgs& a, cudaStream_t s) {
     const int qb = (a.num_agents + NWQ - 1) / NWQ;
-    phys_kernel<<<a.num_packs, 32, 0, s>>>(a);
+    switch (phys_of(a)) {
+        case kPhysBicycle: phys_kernel<kPhysBicycle><<<a.num_packs, 32, 0, s>>>(a); break;
+        case kPhysSurrogate: phys_kernel<kPhysSurrogate><<<a.num_packs, 32, 0, s>>>(a); break;
+        default: phys_kernel<kPhysVehicle><<<a.num_packs, 32, 0, s>>>(a); break;
+    }
     query_kernel<NWQ><<<qb, 32 * NWQ, 0, s>>>(a);
     // blocks of about 32 agents keep one warp for their pairs (more blocks
     // resident); blocks of one small world spread them over four
@@ -2180,24 +2195,35 @@ cudaError_t sf_launch_step_split(const WorldArgs& a, int nwq, cudaStream_t s) {
     }
 }
 
-template <int MODE, int NW>
+template <int MODE, int NW, int PHYS>
 static cudaError_t launch_shape(const WorldArgs& a, cudaStream_t s) {
     // allow up to kMaxStageBytes of dynamic shared memory, once per instantiation
-    static const cudaError_t attr = cudaFuncSetAttribute(world_kernel<MODE, NW>,
+    static const cudaError_t attr = cudaFuncSetAttribute(world_kernel<MODE, NW, PHYS>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStageBytes);
     if (attr != cudaSuccess) return attr;
     if (a.stage_bytes < 0 || a.stage_bytes > kMaxStageBytes || a.stage_bytes % 16) return cudaErrorInvalidValue;
-    world_kernel<MODE, NW><<<a.num_packs, 32 * NW, a.stage_bytes, s>>>(a);
+    world_kernel<MODE, NW, PHYS><<<a.num_packs, 32 * NW, a.stage_bytes, s>>>(a);
     return cudaGetLastError();
 }
 
+template <int MODE, int PHYS>
+static cudaError_t launch_nw(const WorldArgs& a, int nw, cudaStream_t s) {
+    switch (nw) {
+        case 1: return launch_shape<MODE, 1, PHYS>(a, s);
+        case 2: return launch_shape<MODE, 2, PHYS>(a, s);
+        case 8: return launch_shape<MODE, 8, PHYS>(a, s);
+        default: return launch_shape<MODE, 4, PHYS>(a, s);
+    }
+}
+
+// a step's kernel carries only its physics variant; resets and observations run none
 template <int MODE>
 static cudaError_t launch_mode(const WorldArgs& a, int nw, cudaStream_t s) {
-    switch (nw) {
-        case 1: return launch_shape<MODE, 1>(a, s);
-        case 2: return launch_shape<MODE, 2>(a, s);
-        case 8: return launch_shape<MODE, 8>(a, s);
-        default: return launch_shape<MODE, 4>(a, s);
+    if (MODE != kModeStep) return launch_nw<MODE, kPhysVehicle>(a, nw, s);
+    switch (phys_of(a)) {
+        case kPhysBicycle: return launch_nw<MODE, kPhysBicycle>(a, nw, s);
+        case kPhysSurrogate: return launch_nw<MODE, kPhysSurrogate>(a, nw, s);
+        default: return launch_nw<MODE, kPhysVehicle>(a, nw, s);
     }
 }
 
