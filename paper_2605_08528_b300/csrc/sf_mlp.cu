@@ -738,6 +738,10 @@ sf_status sf_mlp_forward_train_on(sf_mlp_handle m, cudaStream_t st, const float*
     return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("forward_train: ") + cudaGetErrorString(e));
 }
 
+void sf_mlp_end_share(sf_mlp_handle m) {
+    if (m) m->share = nullptr;
+}
+
 sf_status sf_mlp_forward_train_shared_on(sf_mlp_handle m, sf_mlp_handle src, cudaStream_t st, int batch, float* d_y,
                                          int ldy) {
     if (!m || !src || m == src || !d_y || batch < 8 || batch % 8 != 0 || batch > src->cap ||

@@ -23,6 +23,8 @@ sf_status sf_mlp_forward_train_on(sf_mlp_handle m, cudaStream_t stream, const fl
 // reads src's bf16 copies, which must stay unchanged until m's backward has run
 sf_status sf_mlp_forward_train_shared_on(sf_mlp_handle m, sf_mlp_handle src, cudaStream_t stream, int batch,
                                          float* d_y, int ldy);
+// ends m's borrow of another network's input (after its backward)
+void sf_mlp_end_share(sf_mlp_handle m);
 // weight and bias gradients of the last training forward from the upstream gradient d_dy [batch][ldy]
 sf_status sf_mlp_backward_on(sf_mlp_handle m, cudaStream_t stream, const float* d_dy, int ldy, int batch);
 // adds the sum of squares of every gradient into *d_acc

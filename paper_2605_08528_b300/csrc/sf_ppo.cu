@@ -465,6 +465,10 @@ sf_status sf_ppo_collect(sf_ppo_handle p) {
 
 sf_status sf_ppo_update(sf_ppo_handle p, float* h_stats) {
     if (!p) return SF_ERR_INVALID_ARG;
+    struct EndShare {   // on every exit: the critic stops reading the actor's input copy
+        sf_mlp_handle m;
+        ~EndShare() { sf_mlp_end_share(m); }
+    } end_share{p->critic};
     if (!p->collected) return pfail(p, SF_ERR_STATE, "sf_ppo_update: no rollout collected");
     const int A = p->A, T = p->T, B = p->B;
     const size_t N = (size_t)A * T;
