@@ -63,9 +63,11 @@ constexpr int kImgBytes = kOffW2 + 2 * 128 * 128;   // 45056: one network's weig
 constexpr int kOffA1 = kImgBytes;                   // [128 slots][128 B]
 constexpr int kOffH1 = kOffA1 + 128 * 128;          // 61440: 2 K-atoms of [128 slots][128 B]
 constexpr int kOffPool = kOffH1 + 2 * 128 * 128;    // 94208: u32 [kG][96]
-constexpr int kOffMisc = kOffPool + kG * kHid * 4;  // 106496
+constexpr int kMaxGroups = kG * ((kKR + 7) / 8);    // 1408 8-row groups of an item at most
+constexpr int kOffMeta = kOffPool + kG * kHid * 4;  // 106496: u32 [kMaxGroups] group words
+constexpr int kOffMisc = kOffMeta + kMaxGroups * 4; // 112128
 constexpr int kMiscBytes = 1024;
-constexpr int kSmemBytes = kOffMisc + kMiscBytes + 1024;   // 108544: two CTAs per SM
+constexpr int kSmemBytes = kOffMisc + kMiscBytes + 1024;   // 114176: two CTAs per SM
 constexpr uint32_t kTmemCols = 256;                 // D1 at column 0 (96), D2 at column 128 (128)
 
 struct SetArgs {
@@ -124,17 +126,27 @@ __device__ __forceinline__ int agent_of_row(const int* rs, int r) {
     return lo;
 }
 
+// the word of an item's 8-row group: filled rows (1..8) in bits 0-7, the agent
+// (item-local; kG past the item) in bits 8-15, the agent's slot of the group's
+// first row in bits 16-31; written once per item, read by the gathers and the
+// max-pool of every tile
+__device__ __forceinline__ uint32_t group_word(int s, int slot0, int valid) {
+    return (uint32_t)valid | ((uint32_t)s << 8) | ((uint32_t)slot0 << 16);
+}
+constexpr uint32_t kPastItem = (uint32_t)kG << 8;
+
 // features of item row (tile * 128 + row) into v[0..7] (zeros past F, past the agent's filled
 // slots or past the item); returns whether the row is a filled slot
-__device__ __forceinline__ bool gather_row(const SetArgs& a, const int* rs, const int* cnt, int a0, int total,
-                                           int tile, int row, float (&v)[8]) {
+__device__ __forceinline__ bool gather_row(const SetArgs& a, const uint32_t* meta, int a0, int total, int tile,
+                                           int row, float (&v)[8]) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = 0.f;
     const int r = tile * 128 + row;
     if (r >= total) return false;
-    const int al = agent_of_row(rs, r);
-    const int slot = r - rs[al];
-    if (slot >= cnt[al]) return false;
+    const uint32_t md = meta[r >> 3];
+    const int k = r & 7;
+    if (k >= (int)(md & 0xFFu)) return false;
+    const int al = (int)((md >> 8) & 0xFFu), slot = (int)(md >> 16) + k;
     const float* src = a.obs + (size_t)(a0 + al) * a.ld + a.off + (size_t)slot * a.F;
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -149,6 +161,7 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
                                                          ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(sm);
     uint32_t* pool = reinterpret_cast<uint32_t*>(sm + kOffPool);
+    uint32_t* meta = reinterpret_cast<uint32_t*>(sm + kOffMeta);
     int* rs = reinterpret_cast<int*>(sm + kOffMisc);                       // [kG + 1] item row starts (x8)
     int* cnt = reinterpret_cast<int*>(sm + kOffMisc + 640);               // [kG] filled slots per agent
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kOffMisc + 192);     // [2]
@@ -206,8 +219,13 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
         __syncthreads();
         const int total = rs[kG];
         const int ntiles = (total + 127) / 128;
+        for (int g = tid; g < total / 8; g += kThreads) {
+            const int s = agent_of_row(rs, 8 * g), slot0 = 8 * g - rs[s];
+            meta[g] = group_word(s, slot0, min(8, cnt[s] - slot0));
+        }
+        __syncthreads();
         float v8[8];
-        bool live = gather_row(a, rs, cnt, a0, total, 0, tid >> 1, v8);
+        bool live = gather_row(a, meta, a0, total, 0, tid >> 1, v8);
         for (int t = 0; t < ntiles; ++t) {
             // ---- A1: 128 slots x 16 inputs (features, zeros, 1 at K 15 for the bias), two threads per row
             {
@@ -225,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
                 umma_bf16(tmem, smem_desc(sbase + kOffA1), smem_desc(sbase + kOffW1), kIdesc1, 0u);
                 umma_commit(&bar[0]);
             }
-            if (t + 1 < ntiles) live = gather_row(a, rs, cnt, a0, total, t + 1, tid >> 1, v8);   // in flight meanwhile
+            if (t + 1 < ntiles) live = gather_row(a, meta, a0, total, t + 1, tid >> 1, v8);   // in flight meanwhile
 
             // ---- epilogue 1: ELU -> bf16 rows of H1 (this warp: its 32 slots, 48 of the 96 columns)
             // every lane waits, then the warp reconverges (the tcgen05.ld that follows is warp-synchronous)
@@ -276,38 +294,38 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
                 uint32_t r[2][32];
                 tmem_ld32_async(tmem + lanes + (uint32_t)(128 + 64 * hh), r[0]);
                 tmem_ld32_async(tmem + lanes + (uint32_t)(128 + 64 * hh + 32), r[1]);
+                // the words of these columns' eight 8-row groups, read while the TMEM loads run
+                const int g0 = rbase >> 3, ng = total >> 3;
+                uint32_t md[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) md[i] = g0 + i < ng ? meta[g0 + i] : kPastItem;
                 tmem_wait();
                 tmem_hold(r[0]);
                 tmem_hold(r[1]);
                 const int f = 32 * q + lane;
-                int s = agent_of_row(rs, rbase);         // agent holding the first row
-                int bnd = rs[s + 1];                     // row where its 8-row groups end
+                int cur = -1;                            // agent of the running max
                 float m = -INFINITY;
 #pragma unroll
-                for (int c = 0; c < 2; ++c)
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        const int base = rbase + 32 * c + 8 * g;
-                        if (base >= bnd) {               // warp-uniform: the group starts the next agent
-                            if (s < kG) atomicMax(&pool[s * kHid + f], fkey(m));
-                            while (s < kG && rs[s + 1] <= base) ++s;
-                            bnd = s < kG ? rs[s + 1] : 0x7FFFFFFF;
-                            m = -INFINITY;
-                        }
-                        if (s >= kG) continue;           // rows past the item
-                        const int valid = cnt[s] - (base - rs[s]);   // filled slots among these 8 rows
-                        const uint32_t* v = r[c] + 8 * g;
-                        float x[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) x[i] = __uint_as_float(v[i]);
-                        if (valid < 8) {                 // warp-uniform: the agent's last, partly filled group
-#pragma unroll
-                            for (int i = 1; i < 8; ++i) x[i] = i < valid ? x[i] : x[0];
-                        }
-                        m = fmaxf(m, fmaxf(fmaxf(fmaxf(x[0], x[1]), fmaxf(x[2], x[3])),
-                                           fmaxf(fmaxf(x[4], x[5]), fmaxf(x[6], x[7]))));
+                for (int i = 0; i < 8; ++i) {
+                    const int s = (int)((md[i] >> 8) & 0xFFu), valid = (int)(md[i] & 0xFFu);
+                    if (s != cur) {                      // warp-uniform: the group starts the next agent
+                        if (cur >= 0 && cur < kG) atomicMax(&pool[cur * kHid + f], fkey(m));
+                        cur = s;
+                        m = -INFINITY;
                     }
-                if (s < kG) atomicMax(&pool[s * kHid + f], fkey(m));   // continues past these rows
+                    if (s >= kG) continue;               // rows past the item
+                    const uint32_t* v = r[i >> 2] + 8 * (i & 3);
+                    float x[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) x[k] = __uint_as_float(v[k]);
+                    if (valid < 8) {                     // warp-uniform: the agent's last, partly filled group
+#pragma unroll
+                        for (int k = 1; k < 8; ++k) x[k] = k < valid ? x[k] : x[0];
+                    }
+                    m = fmaxf(m, fmaxf(fmaxf(fmaxf(x[0], x[1]), fmaxf(x[2], x[3])),
+                                       fmaxf(fmaxf(x[4], x[5]), fmaxf(x[6], x[7]))));
+                }
+                if (cur >= 0 && cur < kG) atomicMax(&pool[cur * kHid + f], fkey(m));   // continues past these rows
             }
             tc_before();   // this tile's TMEM reads before the next tile's barrier and MMAs
         }
