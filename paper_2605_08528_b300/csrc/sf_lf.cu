@@ -91,6 +91,12 @@ __device__ __forceinline__ float funkey(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 __device__ __forceinline__ float elu(float x) { return x > 0.f ? x : __expf(x) - 1.f; }
+// maximum of three values in one instruction (NaN inputs are ignored as by fmaxf)
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -322,8 +328,7 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
 #pragma unroll
                         for (int k = 1; k < 8; ++k) x[k] = k < valid ? x[k] : x[0];
                     }
-                    m = fmaxf(m, fmaxf(fmaxf(fmaxf(x[0], x[1]), fmaxf(x[2], x[3])),
-                                       fmaxf(fmaxf(x[4], x[5]), fmaxf(x[6], x[7]))));
+                    m = max3f(max3f(m, x[0], x[1]), max3f(x[2], x[3], x[4]), max3f(x[5], x[6], x[7]));
                 }
                 if (cur >= 0 && cur < kG) atomicMax(&pool[cur * kHid + f], fkey(m));   // continues past these rows
             }
