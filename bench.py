@@ -366,6 +366,55 @@ def cpu_baseline(name, seconds=12.0):
                     len(worlds), scene.num_worlds, sub.num_agents, n, name))
 
 
+def _oracle_worker(job):
+    """One host process of the all-cores oracle timing: worlds [w0, w0 + nw) of
+    the workload, `warmup` untimed steps, then `steps` timed steps (or as many
+    as fit in `seconds` when steps is None); returns (agents, steps, elapsed)."""
+    name, w0, nw, warmup, steps, seconds = job
+    from oracle import oracle as O
+    scene = make_scene(name)
+    sub, _ = synth.subscene(scene, list(range(w0, w0 + nw)))
+    orc = O.Oracle(sub)
+    F, I = orc.empty_state()
+    I[:, O.I_PRECIP], I[:, O.I_SURFACE] = sub.precip, sub.surface
+    orc.reset(F, I, np.ones(sub.num_agents, np.uint8), seed=4242)
+    acts = synth.ou_actions(sub.num_agents, 64, seed=11 + w0).astype(np.float64)
+    for t in range(warmup):
+        orc.step(F, I, acts[t % 64], flags=O.FLAG_AUTO_RESET, seed=4242)
+    t0 = time.perf_counter()
+    n = 0
+    while (n < steps) if steps is not None else (time.perf_counter() - t0 < seconds):
+        orc.step(F, I, acts[(warmup + n) % 64], flags=O.FLAG_AUTO_RESET, seed=4242)
+        n += 1
+    return sub.num_agents, n, time.perf_counter() - t0
+
+
+def oracle_on_all_cores(name, warmup=0, steps=None, seconds=12.0):
+    """The oracle on every host core: one process per core (started with
+    spawn), each on its own consecutive worlds of the workload (8, or fewer
+    when the cores outnumber the worlds / 8); returns (agent-steps per second
+    over the slowest process, processes, agents, worlds per process)."""
+    import multiprocessing as mp
+    worlds = WORKLOADS[name][0]
+    cores = os.cpu_count() or 1
+    per = max(1, min(8, worlds // cores))
+    procs = min(cores, worlds // per)
+    jobs = [(name, per * k, per, warmup, steps, seconds) for k in range(procs)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    agent_steps = sum(a * n for a, n, _ in res)
+    return agent_steps / max(t for _, _, t in res), procs, sum(a for a, _, _ in res), per
+
+
+def cpu_baseline_all_cores(name, seconds=12.0):
+    """The same oracle on every host core (after the GPU work), each process on
+    its own 8 worlds of the workload."""
+    v, cores, agents, per = oracle_on_all_cores(name, seconds=seconds)
+    return dict(value=v, unit="CASPS", cores=cores, kind="oracle",
+                sample="%d processes x %d worlds (%d agents in all) of the %s workload, FP64, %.0f s each" % (
+                    cores, per, agents, name, seconds))
+
+
 def main_ours(args):
     import torch
     import torch.distributed as dist
@@ -486,6 +535,8 @@ def main_ours(args):
     asur = {k: agg(k + "+surrogate") for k in ("256x16", "4096x16") if k + "+surrogate" in res}
     if rank == 0:
         base = cpu_baseline("256x16") if (world == 1 and not args.skip_cpu) else None
+        base_all = cpu_baseline_all_cores("256x16") if (world == 1 and not args.skip_cpu) else None
+        fp32_peak = sf.sf_fp32_fma_peak(stream)
         traffic = load_traffic()
         line = {
             "metric": METRIC, "value": a256["casps"], "unit": "CASPS", "n_gpus": world, "steps": args.steps,
@@ -577,6 +628,12 @@ def main_ours(args):
         }
         if base is not None:
             line["cpu_baseline"] = base
+        if base_all is not None:
+            line["cpu_baseline_all_cores"] = base_all
+        # the denominator of the step's ALU roofline (its FP32 pipe use is in profiles/)
+        line["fp32_fma_peak"] = {"value": fp32_peak, "unit": "TFLOP/s", "kind": "measured",
+                                 "nominal": 2.0 * 128 * torch.cuda.get_device_properties(0).multi_processor_count
+                                 * clk["sm_max_mhz"] * 1e6 / 1e12 if clk["sm_max_mhz"] else None}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -636,31 +693,21 @@ def traffic_of(traffic, name, tuned):
 # --------------------------------------------------------------------------- reference arm
 def main_reference(args):
     """The FP64 oracle as it stands on the host cores, for the same metric and
-    workload; each step a bounded sample (8 of the 256 worlds)."""
+    workload: one process per core, each stepping its own 8 of the 256 worlds."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import oracle as O
-    scene = make_scene("256x16")
-    sub, rows = synth.subscene(scene, range(8))
-    orc = O.Oracle(sub)
-    F, I = orc.empty_state()
-    I[:, O.I_PRECIP], I[:, O.I_SURFACE] = sub.precip, sub.surface
-    orc.reset(F, I, np.ones(sub.num_agents, np.uint8), seed=4242)
-    acts = synth.ou_actions(sub.num_agents, 64, seed=11).astype(np.float64)
-    for t in range(args.warmup):
-        orc.step(F, I, acts[t % 64], flags=O.FLAG_AUTO_RESET, seed=4242)
-    t0 = time.perf_counter()
-    for t in range(args.steps):
-        orc.step(F, I, acts[(args.warmup + t) % 64], flags=O.FLAG_AUTO_RESET, seed=4242)
-    dt = time.perf_counter() - t0
-    v = sub.num_agents * args.steps / dt
+    v, cores, agents, per = oracle_on_all_cores("256x16", warmup=args.warmup, steps=args.steps)
+    dt = agents * args.steps / v
+
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "CASPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "256 worlds x 16 agents (sample: 8 worlds, 128 agents per step)"},
-            "cpu_baseline": {"value": v, "unit": "CASPS", "cores": 1, "kind": "oracle",
-                             "sample": "8 of 256 worlds (128 agents) per step, FP64, 1 thread"},
+            "config": {"workload": "256 worlds x 16 agents (sample: %d worlds per host process, %d agents per "
+                                   "step)" % (per, agents)},
+            "cpu_baseline": {"value": v, "unit": "CASPS", "cores": cores, "kind": "oracle",
+                             "sample": "%d processes x %d of the 256 worlds (%d agents in all) per step, FP64" % (
+                                 cores, per, agents)},
             "e2e": {"value": v, "unit": "CASPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

@@ -404,6 +404,14 @@ sf_status sf_gemm_bf16(const void* d_a, const void* d_b, const float* d_bias, in
  * Both run on the handle's stream.  Asynchronous. */
 sf_status sf_step_policy(sf_handle h, sf_mlp_handle policy, float dt, int substeps);
 
+/* The device's FP32 fused multiply-add throughput, measured: `iters` rounds of
+ * eight independent FMA chains per thread, eight 256-thread blocks per SM, one
+ * timed launch after a warm-up on `stream` (a cudaStream_t, NULL: the legacy
+ * stream); *out_tflops = 2 x FMAs / elapsed time / 1e12.  The denominator of
+ * the step's ALU roofline.  Synchronous.  Errors: SF_ERR_INVALID_ARG (NULL
+ * out_tflops, iters < 1), SF_ERR_OOM, SF_ERR_CUDA. */
+sf_status sf_fp32_fma_peak(void* stream, int iters, double* out_tflops);
+
 /* Capture a whole control step into a CUDA graph on the handle's stream
  * (which must not be the legacy default stream): [policy forward if policy
  * != NULL] -> [surrogate features and MLP if surrogate != NULL] -> the step

@@ -70,6 +70,7 @@ def lib():
             "sf_create": ([vp, vp, vp], i32), "sf_destroy": ([vp], i32), "sf_load_roads": ([vp, vp], i32),
             "sf_step": ([vp, vp, f32, C.c_int], i32), "sf_get_obs": ([vp, vp, vp, vp, vp], i32),
             "sf_step_host": ([vp, vp, vp, vp, f32, C.c_int], i32),
+            "sf_fp32_fma_peak": ([vp, C.c_int, C.POINTER(C.c_double)], i32),
             "sf_output_ptrs": ([vp, vp], i32), "sf_observe_full": ([vp, vp, vp, vp, vp, vp], i32), "sf_get_indices": ([vp, vp, vp, vp, vp], i32), "sf_reset": ([vp, vp], i32), "sf_place_agents": ([vp, vp], i32),
             "sf_get_state": ([vp, vp, vp], i32), "sf_set_state": ([vp, vp, vp], i32),
             "sf_save_state": ([vp, C.c_char_p], i32), "sf_load_state": ([vp, C.c_char_p], i32),
@@ -170,6 +171,16 @@ def sf_step_host(h, h_actions, h_reward, h_done, dt=1.0 / 30.0, substeps=4):
     page-locked for the captured-graph path): actions in, rewards and done
     flags out; returns when they are in host memory."""
     _check(lib().sf_step_host(h, _ptr(h_actions), _ptr(h_reward), _ptr(h_done), float(dt), int(substeps)), h)
+
+
+def sf_fp32_fma_peak(stream=None, iters=20000):
+    """Measured FP32 FMA throughput of the device in TFLOP/s."""
+    out = C.c_double(0.0)
+    st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    s = lib().sf_fp32_fma_peak(st or None, int(iters), C.byref(out))
+    if s != SF_OK:
+        raise SFError(s, "sf_fp32_fma_peak")
+    return out.value
 
 
 def sf_get_obs(h, d_obs=None, d_reward=None, d_done=None, d_events=None):
