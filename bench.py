@@ -209,13 +209,14 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, p
     acts_pin = [torch.as_tensor(acts_h[k]).pin_memory() for k in range(ring)]
     rew_h = torch.empty(A, dtype=torch.float32).pin_memory()
     done_h = torch.empty(A, dtype=torch.uint8).pin_memory()
+    rew_np = rew_h.numpy()                               # host views of the page-locked results
     e2e_steps = max(50, steps // 4)
     sf.sf_step_host(W.h, acts_pin[0], rew_h, done_h)   # capture outside the timed region
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for t in range(e2e_steps):
         sf.sf_step_host(W.h, acts_pin[t % ring], rew_h, done_h)
-        float(rew_h[0])                                  # the host consumes the result
+        float(rew_np[0])                                 # the host consumes the result
     e2e_wall = time.perf_counter() - t0
     W.close()
     return dict(scene=scene, A=A, alive=alive, ms=ms, wall=wall, status=st, e2e_wall=e2e_wall,
