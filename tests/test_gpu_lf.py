@@ -92,6 +92,25 @@ def test_lf_forward_random_observations(A):
     sf.sf_lf_destroy(m)
 
 
+def test_lf_empty_items_between_full_ones():
+    """Items (32 consecutive agents) whose groups have no filled slot at all,
+    among full ones, with more items than the set encoder's persistent CTAs
+    (150 items, one CTA per SM and network): CTAs 0 and 1 take an empty item
+    and then a full one, whose tiles must not see barrier phases or pool
+    entries left by the empty one.  Every output against the oracle."""
+    A = 150 * 32
+    obs, nr, nv = random_obs(11, A)
+    for it in [0, 1] + list(range(7, 150, 7)):
+        nr[32 * it:32 * it + 32] = 0
+        nv[32 * it:32 * it + 32] = 0
+        obs[32 * it:32 * it + 32, LF.ROAD0:] = 0
+    p = sf.init_lf(seed=11)
+    m = sf.sf_lf_create()
+    sf.sf_lf_set_params(m, p)
+    check(p, obs, nr, nv, run(m, obs, nr, nv))
+    sf.sf_lf_destroy(m)
+
+
 def test_lf_forward_on_full_observations():
     """The network on the library's own full observations: paper-shaped worlds,
     a ragged batch (up to 32 agents and 5,000 points a world) and parked agents."""
