@@ -449,8 +449,10 @@ sf_status sf_surrogate_destroy(sf_surrogate_handle s);
 /* One plain physics step of h with d_actions, recording a training
  * transition for every gated agent that stayed alive and neither respawned,
  * collided nor crashed: raw inputs appended to d_x [cap][30], raw outputs to
- * d_y [cap][16] at the device counter *d_count (incremented; rows beyond cap
- * are dropped).  Asynchronous on h's stream. */
+ * d_y [cap][16] at the device counter *d_count (advanced by the number of
+ * transitions; rows beyond cap are dropped).  The rows of one call follow the
+ * agents' order, so a seeded collection yields the same rows on every run.
+ * Asynchronous on h's stream. */
 sf_status sf_surrogate_collect(sf_handle h, sf_surrogate_handle s, const float* d_actions, float dt, int substeps,
                                float* d_x, float* d_y, unsigned long long cap, unsigned long long* d_count);
 

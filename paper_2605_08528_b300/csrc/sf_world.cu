@@ -2123,26 +2123,60 @@ __global__ void surr_snapshot_kernel(const WorldArgs args, float4* __restrict__ 
     snap[4 * A + a] = args.st.spin[a];
 }
 
-__global__ void surr_collect_kernel(const WorldArgs args, const float4* __restrict__ snap,
-                                    const uint8_t* __restrict__ elig, const float* __restrict__ x, float dt,
-                                    float* __restrict__ out_x, float* __restrict__ out_y, unsigned long long cap,
-                                    unsigned long long* __restrict__ count) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+// One block walks the agents in order, kCollectThreads at a time, and gives
+// each kept transition the next row: row i of the training set is the i-th
+// kept transition in (step, agent) order, so the rows, the normalisation
+// fitted to them and the trained weights repeat from run to run (an atomic
+// ticket per row would order them by scheduling).
+constexpr int kCollectThreads = 512;
+
+__global__ void __launch_bounds__(kCollectThreads, 1)
+    surr_collect_kernel(const WorldArgs args, const float4* __restrict__ snap, const uint8_t* __restrict__ elig,
+                        const float* __restrict__ x, float dt, float* __restrict__ out_x, float* __restrict__ out_y,
+                        unsigned long long cap, unsigned long long* __restrict__ count) {
+    __shared__ unsigned s_cnt[kCollectThreads / 32];
+    __shared__ unsigned long long s_base;
     const int A = args.num_agents;
-    if (a >= A || !elig[a]) return;
-    const uint32_t ev = args.out.events[a];
-    if (ev & (kEvRespawned | kEvNonfinite | kEvCollision | kEvCrash)) return;
-    Agent S;
-    load_agent(args.st, a, S);
-    if (!(status_of(S.meta) & kAlive)) return;
-    float y[kSurrOut];
-    surr_targets(snap[a], snap[A + a], snap[2 * A + a], snap[3 * A + a], snap[4 * A + a], S, dt, y);
-    const unsigned long long i = atomicAdd(count, 1ull);
-    if (i >= cap) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_base = *count;
+    __syncthreads();
+    unsigned long long base = s_base;
+    for (int a0 = 0; a0 < A; a0 += kCollectThreads) {
+        const int a = a0 + (int)threadIdx.x;
+        bool keep = false;
+        float y[kSurrOut];
+        if (a < A && elig[a] &&
+            !(args.out.events[a] & (kEvRespawned | kEvNonfinite | kEvCollision | kEvCrash))) {
+            Agent S;
+            load_agent(args.st, a, S);
+            if (status_of(S.meta) & kAlive) {
+                keep = true;
+                surr_targets(snap[a], snap[A + a], snap[2 * A + a], snap[3 * A + a], snap[4 * A + a], S, dt, y);
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) s_cnt[w] = __popc(m);
+        __syncthreads();
+        unsigned before = 0, total = 0;
 #pragma unroll
-    for (int k = 0; k < kSurrIn; ++k) out_x[i * kSurrIn + k] = x[(size_t)a * kSurrInLd + k];
+        for (int j = 0; j < kCollectThreads / 32; ++j) {
+            const unsigned c = s_cnt[j];
+            before += j < w ? c : 0u;
+            total += c;
+        }
+        __syncthreads();
+        if (keep) {
+            const unsigned long long i = base + before + __popc(m & ((1u << lane) - 1u));
+            if (i < cap) {
 #pragma unroll
-    for (int k = 0; k < kSurrOut; ++k) out_y[i * kSurrOut + k] = y[k];
+                for (int k = 0; k < kSurrIn; ++k) out_x[i * kSurrIn + k] = x[(size_t)a * kSurrInLd + k];
+#pragma unroll
+                for (int k = 0; k < kSurrOut; ++k) out_y[i * kSurrOut + k] = y[k];
+            }
+        }
+        base += total;
+    }
+    if (threadIdx.x == 0) *count = base;
 }
 
 cudaError_t sf_launch_surr_gate(const WorldArgs& a, float dt, uint8_t* d_elig, cudaStream_t s) {
@@ -2165,7 +2199,7 @@ cudaError_t sf_launch_surr_collect(const WorldArgs& a, const float4* snap, const
                                    float dt, float* out_x, float* out_y, unsigned long long cap,
                                    unsigned long long* count, cudaStream_t s) {
     if (a.num_agents <= 0) return cudaSuccess;
-    surr_collect_kernel<<<(a.num_agents + 127) / 128, 128, 0, s>>>(a, snap, d_elig, d_x, dt, out_x, out_y, cap, count);
+    surr_collect_kernel<<<1, kCollectThreads, 0, s>>>(a, snap, d_elig, d_x, dt, out_x, out_y, cap, count);
     return cudaGetLastError();
 }
 

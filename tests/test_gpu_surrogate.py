@@ -76,15 +76,66 @@ def test_collected_rows_match_the_oracle():
         assert abs(n - int(keep.sum())) <= 1, (t, n, int(keep.sum()))     # a gate decision within rounding
         X = dx[before:before + n].cpu().numpy()
         Y = dy[before:before + n].cpu().numpy()
+        rows = []
         for a in np.nonzero(keep)[0]:
             xo = OS.features(F0[a], acts[t][a])
             yo = OS.targets(F0[a], F1[a], DT)
             k = int(np.argmin(np.abs(X - xo).sum(1)))
+            rows.append(k)
             assert np.abs(X[k] - xo).max() <= 1e-5 * max(1.0, np.abs(xo).max()), (t, a)
             assert np.abs(Y[k] - yo).max() <= 5e-5, (t, a, float(np.abs(Y[k] - yo).max()))
             checked += 1
+        if n == int(keep.sum()):
+            assert rows == list(range(n)), t       # one call's rows follow the agents' order
     assert checked > 50
     sf.sf_surrogate_destroy(s)
+
+
+def collect(sc, steps, cap, seed=3):
+    W = sf.World(sc, seed=seed, flags=sf.FLAG_AUTO_RESET)
+    sf.sf_reset(W.h, dev(np.ones(W.A, np.uint8)))
+    s = sf.sf_surrogate_create()
+    dx = torch.zeros((cap, 30), device="cuda")
+    dy = torch.zeros((cap, 16), device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    acts = dev(synth.ou_actions(W.A, steps, seed=7))
+    for t in range(steps):
+        sf.sf_surrogate_collect(W.h, s, acts[t], dx, dy, cap, cnt)
+    torch.cuda.synchronize()
+    out = int(cnt.item()), dx.cpu().numpy(), dy.cpu().numpy()
+    sf.sf_surrogate_destroy(s)
+    W.close()
+    return out
+
+
+def test_collection_repeats_and_cap_keeps_the_first_rows():
+    """Two collections from the same seeded worlds give the same rows bit for
+    bit (the training set, its normalisation and the trained weights repeat
+    from run to run); a collection cut at a small cap keeps exactly the first
+    rows of the uncut one, and its counter still counts every transition."""
+    sc = synth.procedural_scene(40, 16, seed_base=910)       # 640 agents: two 512-agent chunks
+    n1, x1, y1 = collect(sc, 24, 20000)
+    n2, x2, y2 = collect(sc, 24, 20000)
+    assert n1 == n2 and 1000 < n1 <= 20000
+    assert np.array_equal(x1.view(np.uint32), x2.view(np.uint32))
+    assert np.array_equal(y1.view(np.uint32), y2.view(np.uint32))
+    cap = 777
+    n3, x3, y3 = collect(sc, 24, cap)
+    assert n3 == n1
+    assert np.array_equal(x3.view(np.uint32), x1[:cap].view(np.uint32))
+    assert np.array_equal(y3.view(np.uint32), y1[:cap].view(np.uint32))
+    # training on the same rows with the same seed gives the same statistics and weights
+    dims = [30, 256, 256, 256, 16]
+    got = []
+    for _ in range(2):
+        s = sf.sf_surrogate_create()
+        sf.sf_surrogate_train(s, dev(x1[:n1]), dev(y1[:n1]), n1, batch=1024, steps=200, lr=3e-3, seed=11)
+        m = sf.sf_surrogate_mlp(s)
+        got.append([sf.sf_surrogate_stats(s)] +
+                   [a for l in range(4) for a in sf.sf_mlp_get_layer(m, l, dims[l + 1], dims[l])[:2]])
+        sf.sf_surrogate_destroy(s)
+    for a, b in zip(*got):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
 
 
 def train_small(sc_train, steps=1500, collect_steps=120):
