@@ -362,7 +362,7 @@ def cpu_baseline(name, seconds=12.0):
         orc.step(F, I, acts[n % 64], flags=O.FLAG_AUTO_RESET, seed=4242)
         n += 1
     dt = time.perf_counter() - t0
-    return dict(value=sub.num_agents * n / dt, unit="CASPS", cores=1, kind="oracle",
+    return dict(value=sub.num_agents * n / dt, unit="CASPS", cores=1, kind="oracle", cpu_model=host_cpu_model(),
                 sample="%d of %d worlds (%d agents) x %d steps of the %s workload, FP64, 1 thread" % (
                     len(worlds), scene.num_worlds, sub.num_agents, n, name))
 
@@ -407,11 +407,24 @@ def oracle_on_all_cores(name, warmup=0, steps=None, seconds=12.0):
     return agent_steps / max(t for _, _, t in res), procs, sum(a for a, _, _ in res), per
 
 
+def host_cpu_model():
+    """The host CPU's model name (Linux), or the platform's processor string."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
+
+
 def cpu_baseline_all_cores(name, seconds=12.0):
     """The same oracle on every host core (after the GPU work), each process on
     its own 8 worlds of the workload."""
     v, cores, agents, per = oracle_on_all_cores(name, seconds=seconds)
-    return dict(value=v, unit="CASPS", cores=cores, kind="oracle",
+    return dict(value=v, unit="CASPS", cores=cores, kind="oracle", cpu_model=host_cpu_model(),
                 sample="%d processes x %d worlds (%d agents in all) of the %s workload, FP64, %.0f s each" % (
                     cores, per, agents, name, seconds))
 
@@ -473,12 +486,13 @@ def main_ours(args):
         surr, rows, loss = SU.collect_and_train(make_scene("256x16", rank), transitions=args.surr_rows,
                                                 train_steps=args.surr_steps, seed=31 + rank, stream=stream)
         t_train = time.perf_counter() - t0
-        lone = synth.procedural_scene(512, 1, seed_base=9000 + 512 * rank)
+        lone = synth.procedural_scene(2048, 1, seed_base=9000 + 2048 * rank)
         lone.precip[:] = np.minimum(lone.precip, 2)       # mu >= 0.3 cells (the gate's range)
-        err, frac = SU.rollout_error(surr, lone, stream=stream)
+        err, frac = SU.rollout_error(surr, lone, stream=stream, segments=5)    # 10,240 held-out start states
         surr_info = dict(rows=rows, train_steps=args.surr_steps, final_loss=loss, train_s=t_train,
                          err_mean_m=float(err.mean()), err_p90_m=float(np.percentile(err, 90)),
-                         err_max_m=float(err.max()), gated_fraction_lone=frac)
+                         err_p99_m=float(np.percentile(err, 99)),
+                         err_max_m=float(err.max()), eval_states=int(err.size), gated_fraction_lone=frac)
         for name in ("256x16", "4096x16"):
             if world > 1:
                 dist.barrier()
@@ -707,7 +721,7 @@ def main_reference(args):
             "config": {"workload": "256 worlds x 16 agents (sample: %d worlds per host process, %d agents per "
                                    "step)" % (per, agents)},
             "cpu_baseline": {"value": v, "unit": "CASPS", "cores": cores, "kind": "oracle",
-                             "sample": "%d processes x %d of the 256 worlds (%d agents in all) per step, FP64" % (
+                             "cpu_model": host_cpu_model(), "sample": "%d processes x %d of the 256 worlds (%d agents in all) per step, FP64" % (
                                  cores, per, agents)},
             "e2e": {"value": v, "unit": "CASPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

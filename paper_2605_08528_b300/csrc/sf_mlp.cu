@@ -109,25 +109,36 @@ __global__ void act_back_kernel(const float* __restrict__ dA, const float* __res
     }
 }
 
-// mean-squared-error gradient of the output: dY = 2 (y - t) / (B n), loss partial sums
+// mean-squared-error gradient of the output: dY = 2 (y - t) / (B n)
 __global__ void mse_grad_kernel(const float* __restrict__ y, const float* __restrict__ t, int B, int n, int ld,
-                                int ldt, float* __restrict__ dy, float* __restrict__ loss) {
+                                int ldt, float* __restrict__ dy) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float l = 0.f;
     if (i < (size_t)B * ld) {
         const int b = (int)(i / ld), c = (int)(i % ld);
-        float d = 0.f;
-        if (c < n) {
-            d = y[i] - t[(size_t)b * ldt + c];
-            l = d * d;
-        }
+        const float d = c < n ? y[i] - t[(size_t)b * ldt + c] : 0.f;
         dy[i] = 2.f * d / ((float)B * (float)n);
     }
-    if (loss) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o);
-        if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss, l / ((float)B * (float)n));
+}
+
+// the loss mean (y - t)^2 over the B x n outputs, in a fixed order: thread k
+// sums elements k, k + 256, ... and the 256 sums meet in a tree (one block;
+// launched only for the step whose loss is read)
+__global__ void mse_loss_kernel(const float* __restrict__ y, const float* __restrict__ t, int B, int n, int ld,
+                                int ldt, float* __restrict__ loss) {
+    __shared__ float red[256];
+    float l = 0.f;
+    for (size_t i = threadIdx.x; i < (size_t)B * n; i += 256) {
+        const int b = (int)(i / n), c = (int)(i % n);
+        const float d = y[(size_t)b * ld + c] - t[(size_t)b * ldt + c];
+        l += d * d;
     }
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0] / ((float)B * (float)n);
 }
 
 // column sums of dZ [B, ld] (bf16, row-major): db[c] = sum_b dZ[b, c], in two
@@ -694,10 +705,11 @@ sf_status sf_mlp_train_step(sf_mlp_handle m, const float* d_x, const float* d_t,
                                                                        m->xt[0]);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = forward_core(m, B, true);
-    if (e == cudaSuccess) e = cudaMemsetAsync(m->loss, 0, 4, m->stream);
     if (e == cudaSuccess) {
         mse_grad_kernel<<<grid1((size_t)B * m->ld[L]), 256, 0, m->stream>>>(m->y, d_t, B, m->dim[L], m->ld[L],
-                                                                            m->dim[L], m->dA, m->loss);
+                                                                            m->dim[L], m->dA);
+        if (h_loss)
+            mse_loss_kernel<<<1, 256, 0, m->stream>>>(m->y, d_t, B, m->dim[L], m->ld[L], m->dim[L], m->loss);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = backward_core(m, B, m->stream);

@@ -41,29 +41,37 @@ def collect_and_train(scene, transitions=10_000_000, train_steps=60000, batch=81
     return s, n, loss
 
 
-def rollout_error(s, scene, steps=30, warm=10, seed=5, stream=None):
+def rollout_error(s, scene, steps=30, warm=10, seed=5, stream=None, segments=1):
     """Position error after `steps` control steps between the surrogate path and
     the FP32 physics path started from identical states with identical actions
-    (lone agents).  Returns (errors [A], fraction of agent-steps on the surrogate)."""
+    (lone agents).  The physics world runs on through `segments` back-to-back
+    windows; each window starts the surrogate world from a copy of the physics
+    world's state, so every agent gives `segments` start states.  Returns
+    (errors [segments * A], fraction of agent-steps on the surrogate)."""
     import torch
     dev = torch.device("cuda")
     W1 = sf.World(scene, seed=seed, flags=sf.FLAG_INVINCIBLE, stream=stream)
     W2 = sf.World(scene, seed=seed, flags=sf.FLAG_INVINCIBLE, stream=stream)
-    acts = torch.as_tensor(synth.ou_actions(W1.A, warm + steps, seed=seed + 1), device=dev)
-    for W in (W1, W2):
-        sf.sf_reset(W.h, torch.ones(W.A, dtype=torch.uint8, device=dev))
-        for t in range(warm):
-            sf.sf_step(W.h, acts[t])
+    acts = torch.as_tensor(synth.ou_actions(W1.A, warm + segments * steps, seed=seed + 1), device=dev)
+    sf.sf_reset(W1.h, torch.ones(W1.A, dtype=torch.uint8, device=dev))
+    for t in range(warm):
+        sf.sf_step(W1.h, acts[t])
     used = 0
-    for t in range(steps):
-        sf.sf_step(W1.h, acts[warm + t])
-        sf.sf_step_surrogate(W2.h, s, acts[warm + t])
-        used += sf.sf_surrogate_audit(W2.h)[1]
-    F1, _, _ = sf.sf_get_state(W1.h)
-    F2, _, _ = sf.sf_get_state(W2.h)
+    errs = []
+    for k in range(segments):
+        F, I, _ = sf.sf_get_state(W1.h)
+        sf.sf_set_state(W2.h, F, I)
+        for t in range(steps):
+            a = acts[warm + k * steps + t]
+            sf.sf_step(W1.h, a)
+            sf.sf_step_surrogate(W2.h, s, a)
+            used += sf.sf_surrogate_audit(W2.h)[1]
+        F1, _, _ = sf.sf_get_state(W1.h)
+        F2, _, _ = sf.sf_get_state(W2.h)
+        errs.append(np.linalg.norm(F1[:, :3] - F2[:, :3], axis=1))
     W1.close()
     W2.close()
-    return np.linalg.norm(F1[:, :3] - F2[:, :3], axis=1), used / float(steps * F1.shape[0])
+    return np.concatenate(errs), used / float(segments * steps * W1.A)
 
 
 class _null:

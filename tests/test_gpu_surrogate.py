@@ -124,14 +124,14 @@ def test_collection_repeats_and_cap_keeps_the_first_rows():
     assert n3 == n1
     assert np.array_equal(x3.view(np.uint32), x1[:cap].view(np.uint32))
     assert np.array_equal(y3.view(np.uint32), y1[:cap].view(np.uint32))
-    # training on the same rows with the same seed gives the same statistics and weights
+    # training on the same rows with the same seed gives the same loss, statistics and weights
     dims = [30, 256, 256, 256, 16]
     got = []
     for _ in range(2):
         s = sf.sf_surrogate_create()
-        sf.sf_surrogate_train(s, dev(x1[:n1]), dev(y1[:n1]), n1, batch=1024, steps=200, lr=3e-3, seed=11)
+        loss = sf.sf_surrogate_train(s, dev(x1[:n1]), dev(y1[:n1]), n1, batch=1024, steps=200, lr=3e-3, seed=11)
         m = sf.sf_surrogate_mlp(s)
-        got.append([sf.sf_surrogate_stats(s)] +
+        got.append([np.array([loss], np.float32), sf.sf_surrogate_stats(s)] +
                    [a for l in range(4) for a in sf.sf_mlp_get_layer(m, l, dims[l + 1], dims[l])[:2]])
         sf.sf_surrogate_destroy(s)
     for a, b in zip(*got):
