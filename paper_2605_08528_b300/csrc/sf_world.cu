@@ -1660,9 +1660,11 @@ __device__ __forceinline__ void lanes_final_b(const WorldArgs& args, const Slot&
     if (!(c.has && active)) return;
     const int a = c.a;
     float4* o4 = reinterpret_cast<float4*>(args.out.obs + (size_t)a * kObsDim);
+    // an agent a reset did not move keeps its ego group and nearest lane
+    const bool keep = MODE == kModeReset && alive && !respawn;
     AgentQ q;
     q.seg = -1;
-    if (alive) {
+    if (alive && !keep) {
         q = *qp;
         float gbx, gby, vbx, vby;
         to_ego(hx, hy, A.gx - A.px, A.gy - A.py, gbx, gby);
@@ -1674,12 +1676,12 @@ __device__ __forceinline__ void lanes_final_b(const WorldArgs& args, const Slot&
         o4[2] = make_float4(sc == 0 ? 1.f : 0.f, sc == 1 ? 1.f : 0.f, sc == 2 ? 1.f : 0.f, A.wz);
         o4[3] = make_float4(A.dl / kThetaMax, A.mu, q.seg >= 0 ? q.lat / 3.6f : 0.f,
                             q.seg >= 0 ? cross2(q.tx, q.ty, hx, hy) : 0.f);
-    } else {
+    } else if (!alive) {
 #pragma unroll
         for (int k = 0; k < kObsEgo / 4; ++k) o4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (args.flags & kFlagRecord) {
-        args.out.lane_seg[a] = alive ? q.seg : -1;
+        if (!keep) args.out.lane_seg[a] = alive ? q.seg : -1;
 #pragma unroll
         for (int t = 0; t < kK; ++t) args.out.knn_agents[(size_t)a * kK + t] = (alive && nb[t] >= 0) ? (a - lane) + nb[t] : -1;
     }
@@ -1834,7 +1836,13 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         if (recompute) publish(E, lane, A, hx, hy);
         const unsigned ab = __ballot_sync(kFull, alive), act = __ballot_sync(kFull, active);
         if (lane == 0) { s_alive = ab; s_act = act; }
-        if (lane < m && (MODE != kModeStep || respawn)) Q[lane].need = 1;
+        // road-point blocks to compute: every agent when observing, the respawned
+        // ones otherwise (a reset moves only its masked agents, so the others'
+        // blocks and ego groups, computed at the same pose, stand)
+        if (lane < m) {
+            if (MODE == kModeObserve || respawn) Q[lane].need = 1;
+            else if (MODE == kModeReset) Q[lane].need = 0;
+        }
     }
     __syncthreads();
 
@@ -1849,6 +1857,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         const WRoads v = view_of(s_grid[t], (stg && s_woff[t] >= 0) ? s_blob + s_woff[t]
                                                                      : args.rd.blob + s_grid[t].blob);
         const bool al = (s_alive >> j) & 1u, need = Q[j].need != 0;
+        if (MODE == kModeReset && al && !need) continue;   // unmoved by the reset
         Lane L;
         agent_road_block(v, al, need, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j],
                          args.out.hint + 4 * (size_t)(a0 + j), lane, kbuf[warp],

@@ -300,6 +300,12 @@ def test_reset_spawns_match_oracle():
                 continue
             assert np.abs(F1[a] - Fr[a]).max() < 2e-5
         assert np.array_equal(I1[:, O.I_EPISODE], Ir[:, O.I_EPISODE])
+        # the reset recomputes only what moved: its observations equal, bit for
+        # bit, those computed afresh for every agent from the same state
+        obs_r = W.outputs()[0].cpu().numpy().copy()
+        sf.sf_set_state(W.h, F1, I1)
+        obs_f = W.outputs()[0].cpu().numpy()
+        assert np.array_equal(obs_r.view(np.uint32), obs_f.view(np.uint32)), t
     assert ties <= 2
 
 
