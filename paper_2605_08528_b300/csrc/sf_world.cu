@@ -1372,17 +1372,22 @@ __device__ __forceinline__ AgentQ agent_event_queries(const WRoads& v, float px,
 }
 
 // road-point block of one agent's observation (all lanes of a warp).  With
-// `need` (the agent was respawned) the nearest lane is first recomputed from
-// the default radius into *L; the 32 nearest points start from the hinted
+// `need` (the agent was respawned, or every agent is observed afresh) the
+// nearest lane is first recomputed from radius rlane into *L; the 32 nearest points start from the hinted
 // radius (the default after a respawn); the hints are updated.  orow gets the
 // 32 x 7 features (zeros when !alive), knn_row (may be null) the indices.
+// A respawned agent sits on a lane point, so its lane query starts from
+// kSpawnLaneR (the query still grows its radius until the answer is exact).
+constexpr float kSpawnLaneR = 1.0f;
+
 __device__ __forceinline__ void agent_road_block(const WRoads& v, bool alive, bool need, float px, float py,
                                                  float gx, float gy, float hx, float hy, float* hnt, int lane,
-                                                 unsigned long long* kbuf, float* orow, int32_t* knn_row, Lane* L) {
+                                                 unsigned long long* kbuf, float* orow, int32_t* knn_row, Lane* L,
+                                                 float rlane = kLaneR0) {
     unsigned long long key = kKeyInf;
     if (alive) {
         if (need) {
-            *L = coop_nearest_lane(v, px, py, gx, gy, kLaneR0, lane);
+            *L = coop_nearest_lane(v, px, py, gx, gy, rlane, lane);
             __syncwarp();
             if (lane == 0) hnt[1] = L->seg >= 0 ? L->dist : 0.f;
         }
@@ -1862,7 +1867,8 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         agent_road_block(v, al, need, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j],
                          args.out.hint + 4 * (size_t)(a0 + j), lane, kbuf[warp],
                          args.out.obs + (size_t)(a0 + j) * kObsDim + kObsEgo + kK * kObsNbr,
-                         (args.flags & kFlagRecord) ? args.out.knn_pts + (size_t)(a0 + j) * kL : nullptr, &L);
+                         (args.flags & kFlagRecord) ? args.out.knn_pts + (size_t)(a0 + j) * kL : nullptr, &L,
+                         MODE == kModeObserve ? kLaneR0 : kSpawnLaneR);
         if (al && need && lane == 0) {
             Q[j].seg = L.seg; Q[j].dist = L.dist; Q[j].lat = L.lat; Q[j].tx = L.tx; Q[j].ty = L.ty;
         }
@@ -2062,7 +2068,7 @@ __global__ void __launch_bounds__(32 * NWQ) fix_kernel(const WorldArgs args) {
         const float2 h = args.sc.head[a];
         Lane L;
         agent_road_block(v, true, true, p.x, p.y, goal.x, goal.y, h.x, h.y, args.out.hint + 4 * (size_t)a, lane,
-                         kbuf[warp], orow, krow, &L);
+                         kbuf[warp], orow, krow, &L, kSpawnLaneR);
         if (lane == 0) {
             float* ego = args.out.obs + (size_t)a * kObsDim;
             ego[14] = L.seg >= 0 ? L.lat / 3.6f : 0.f;
