@@ -317,6 +317,21 @@ sf_status sf_load_state(sf_handle h, const char* path);
  * device recorded such a condition since the last sync (and clear it). */
 sf_status sf_sync(sf_handle h);
 
+/* Failure detection of bounded device waits (no counterpart in the paper).
+ * The step kernels wait on an mbarrier for the bulk copy that stages a
+ * block's road blobs in shared memory; that wait gives up after limit_ns of
+ * wall time (1 s by default; 0 gives up at the first poll), records a timeout
+ * in the handle's device error word and carries on reading the roads from
+ * global memory (same results); before the block exits it waits again,
+ * bounded by 1 s whatever limit_ns is, for a copy it issued, so no copy
+ * outlives the block.  The next synchronising call returns SF_ERR_TIMEOUT.
+ * withhold_producer != 0 is for tests of that path: the barrier is set up
+ * but no copy is issued, so the wait runs out on a barrier that nothing
+ * completes, with no copy in flight.  Applies to later launches; a captured
+ * graph keeps the values it was captured with.  SF_ERR_INVALID_ARG if h is
+ * NULL. */
+sf_status sf_set_wait_limit(sf_handle h, unsigned long long limit_ns, int withhold_producer);
+
 /* ------------------------------------------------------------------------
  * BF16 tensor-core MLPs (dynamics surrogate and policy of the step).
  * An MLP of L dense layers y = act(W x + b), W [out, in] fp32 masters with
@@ -374,7 +389,10 @@ sf_status sf_mlp_train_step(sf_mlp_handle m, const float* d_x, const float* d_t,
  * output width) bytes (each part rounded up to 256 B); larger batches are
  * rejected with SF_ERR_INVALID_ARG and a message giving both sizes.  The
  * first call on a device looks the array's address up (cudaGetSymbolAddress)
- * and must therefore come before any stream capture on that device.  Every
+ * and must therefore come before any stream capture on that device; a call
+ * with batch 0 does only that lookup (d_x and d_y must still be non-NULL but
+ * are not read or written), so a caller can prime the device before it has
+ * real buffers.  Every
  * call clears and reuses the same array: calls that overlap on the GPU (on
  * different streams, or from different MLP handles) race and corrupt each
  * other's results; serialise them.  Asynchronous on the MLP's stream. */
@@ -383,6 +401,16 @@ size_t sf_mlp_static_scratch_bytes(void);
 
 /* Wait for the MLP's stream; SF_ERR_TIMEOUT if a GEMM's bounded wait gave up. */
 sf_status sf_mlp_sync(sf_mlp_handle m);
+
+/* The same for the MLP's tensor-core GEMMs (no counterpart in the paper):
+ * their operand-ring mbarrier waits give up after limit_ns (1 s by default;
+ * 0 gives up at the first poll), record SF_ERR_TIMEOUT for sf_mlp_sync and
+ * skip the epilogue (the outputs of that launch are left unwritten); every
+ * MMA and TMA load already issued is waited for (bounded by 1 s) before the
+ * CTA frees its tensor memory and exits.  withhold_producer != 0 issues no
+ * TMA load at all, so the first wait runs out with nothing in flight (tests
+ * of that path).  SF_ERR_INVALID_ARG if m is NULL. */
+sf_status sf_mlp_set_wait_limit(sf_mlp_handle m, unsigned long long limit_ns, int withhold_producer);
 
 /* The GEMM itself: C = act(A . B^T + bias) with A [M][K], B [N][K] bf16
  * row-major device arrays (K % 8 == 0, 16-byte aligned), bias [N] or NULL,

@@ -15,8 +15,8 @@
  * (roads are z-flattened, App. C), friction-capped tire impulses, and
  * semi-implicit (symplectic) Euler integration of a 6-DOF chassis, four wheel
  * spins and one steering angle over fixed substeps (120 Hz physics, 30 Hz
- * control, Sec. 4.1).  Every choice the paper leaves open is marked R<n> and
- * listed with its reason in the design notes.
+ * control, Sec. 4.1).  Every choice the paper leaves open is marked R<n>
+ * beside the code that makes it, with its reason.
  *
  * Parity pins (tests/test_oracle_*.py): static sag m g/(4k), exact equilibrium,
  * free fall recurrence, locked-wheel stopping distance v^2/(2 mu g), the friction
@@ -791,8 +791,10 @@ static void events_agent(const or_params* P, const or_scene* S, int w, double* F
     int nb[OR_K_AGENTS];
     knn_agents(S, w, F, I, a, nb);
     double tmin = P->ttc_max, dmax = 0;
+    int n_nb = 0;
     for (int t = 0; t < OR_K_AGENTS; ++t) {
         if (nb[t] < 0) continue;
+        ++n_nb;
         const double* g = F + (size_t)nb[t] * OR_NF;
         double hj[2];
         heading_of(g, hj);
@@ -802,7 +804,11 @@ static void events_agent(const or_params* P, const or_scene* S, int w, double* F
         double dr = or_drac(P, p, hd, v, pj, hj, vj);
         if (dr > dmax) dmax = dr;
     }
-    if (tmin < P->ttc_max) r -= or_penalty(P->ttc_alpha_v, tmin, P->ttc_floor, P->ttc_pmax_v);
+    /* App. G: p(tau) of the minimum pairwise TTC over the neighbours, where a
+     * neighbour behind the ego or on no collision course has TTC = tau_max
+     * (App. D); so any neighbour costs at least alpha_v / tau_max = 0.01 per
+     * step.  An agent without neighbours has no pairwise TTC and no term. */
+    if (n_nb > 0) r -= or_penalty(P->ttc_alpha_v, tmin, P->ttc_floor, P->ttc_pmax_v);
     r -= P->w_drac * fmax(0.0, dmax - P->drac_thresh);
     *drac_out = dmax;
     if (dmax > f[OR_F_PEAK_DRAC]) f[OR_F_PEAK_DRAC] = dmax;

@@ -49,6 +49,8 @@ struct sf_ctx {
     };
     std::vector<PackSet> packsets;
     int pack_cap = 32;
+    unsigned long long wait_ns = 0;   // staging-wait limit of the step kernels (0: 1 s)
+    int withhold = 0;                 // set up the staging barrier but issue no copy (timeout tests)
     StepScratch sc{};           // scratch of the split step
     bool loaded = false;
     unsigned gen = 0;           // bumped when a captured step would go stale (roads, launch shape)
@@ -156,6 +158,8 @@ WorldArgs make_args(sf_ctx* h) {
     a.dynamics = h->cfg.dynamics;
     a.substeps = 1;
     a.h = 0.f;
+    a.wait_ns = h->wait_ns;
+    a.withhold = h->withhold;
     return a;
 }
 
@@ -1407,6 +1411,13 @@ sf_status sf_surrogate_audit(sf_handle h, float* h_max_err, unsigned long long* 
     std::memcpy(&f, &w[0], 4);
     if (h_max_err) *h_max_err = f;
     if (h_used) *h_used = w[1];
+    return SF_OK;
+}
+
+sf_status sf_set_wait_limit(sf_handle h, unsigned long long limit_ns, int withhold_producer) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    h->wait_ns = limit_ns == 0 ? 1ull : limit_ns;   // the kernels read 0 as the 1 s default
+    h->withhold = withhold_producer != 0;
     return SF_OK;
 }
 

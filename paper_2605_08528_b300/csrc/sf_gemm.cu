@@ -12,7 +12,9 @@
 //                  32(w%4)..32(w%4)+31 and every other 32-column chunk), add
 //                  the bias, apply the activation and store.
 // Every mbarrier wait is bounded: on expiry the kernel records SF_GEMM_TIMEOUT
-// in the error word, stops issuing work, frees its TMEM and returns.
+// in the error word and stops issuing work; before it frees its TMEM and
+// returns it waits (bounded, 1 s) for every MMA it issued and for every TMA
+// load it issued, so no asynchronous copy outlives the CTA.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -22,12 +24,6 @@
 
 #include "sf_gemm.cuh"
 #include "sf_tc.cuh"
-
-
-
-
-
-
 
 namespace {
 
@@ -41,8 +37,9 @@ constexpr int shallow_for() { return BN >= 256 ? 2 : (BN >= 128 ? 3 : 4); }
 constexpr int kShallowMaxK = 8;   // K tiles per CTA up to which the shallow ring is used
 using namespace sftc;
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err) {
-    return sftc::mbar_wait(bar, parity, err, SF_GEMM_TIMEOUT);
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err,
+                                          uint64_t limit_ns = kWaitNs) {
+    return sftc::mbar_wait(bar, parity, err, SF_GEMM_TIMEOUT, limit_ns);
 }
 
 // activations of 32 accumulator values; the exponentials use the hardware
@@ -68,6 +65,8 @@ struct alignas(1024) GemmSmem {
     uint64_t empty[kStages];
     uint64_t done;
     uint32_t tmem_base;
+    uint32_t abort;    // a ring wait gave up (producer or MMA issuer)
+    int issued;        // K tiles whose TMA loads the producer issued
 };
 
 template <int BN, int kStages>
@@ -85,9 +84,12 @@ __global__ void __launch_bounds__(kThreads, kStages == kDeep ? 1 : 2)
     const int kb = (int)(((long long)nk * z) / nsplit), nkz = (int)(((long long)nk * (z + 1)) / nsplit) - kb;
     float* const out_f32 = args.ws ? args.ws + (size_t)z * args.M * args.ldc : args.out_f32;
 
+    const uint64_t lim = args.wait_ns ? args.wait_ns : kWaitNs;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) { mbar_init(&S.full[s], 1); mbar_init(&S.empty[s], 1); }
         mbar_init(&S.done, 1);
+        S.abort = 0;
+        S.issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {   // TMEM accumulator: BN fp32 columns x 128 lanes
@@ -104,21 +106,29 @@ __global__ void __launch_bounds__(kThreads, kStages == kDeep ? 1 : 2)
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
-        for (int j = 0; j < nkz; ++j) {
+        int j = 0;
+        for (; j < nkz && !args.withhold; ++j) {
             const int s = j % kStages, kt = kb + j;
-            if (j >= kStages && !mbar_wait(&S.empty[s], ((j / kStages) & 1) ^ 1, args.err)) break;
+            if (j >= kStages && !mbar_wait(&S.empty[s], ((j / kStages) & 1) ^ 1, args.err, lim)) {
+                S.abort = 1;
+                break;
+            }
             mbar_expect_tx(&S.full[s], kTxBytes);
             tma_load_2d(S.a[s], &map_a, kt * kBK, m0, &S.full[s]);
             tma_load_2d(S.b[s], &map_b, kt * kBK, n0, &S.full[s]);
         }
+        S.issued = j;
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         constexpr uint32_t idesc = instr_desc(kBM, BN);
         bool ok = true;
         for (int j = 0; j < nkz && ok; ++j) {
             const int s = j % kStages;
-            ok = mbar_wait(&S.full[s], (j / kStages) & 1, args.err);
-            if (!ok) break;
+            ok = mbar_wait(&S.full[s], (j / kStages) & 1, args.err, lim);
+            if (!ok) {
+                S.abort = 1;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint64_t ad = smem_desc(smem_u32(S.a[s])), bd = smem_desc(smem_u32(S.b[s]));
 #pragma unroll
@@ -129,9 +139,13 @@ __global__ void __launch_bounds__(kThreads, kStages == kDeep ? 1 : 2)
         umma_commit(&S.done);                  // arrives when every issued MMA has completed
     }
     __syncwarp();
+    __syncthreads();   // the producer and the MMA issuer are done: abort and issued are final
 
     // ---------------- epilogue: TMEM -> bias + activation -> global
-    const bool have = __all_sync(0xFFFFFFFFu, mbar_wait(&S.done, 0, args.err));
+    // every issued MMA completes (done is committed on every path), then the
+    // accumulator is used only if no wait gave up
+    const bool fin = __all_sync(0xFFFFFFFFu, mbar_wait(&S.done, 0, args.err));
+    const bool have = fin && S.abort == 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int r = m0 + (warp & 3) * 32 + lane;   // TMEM lane slice of this warp
     // 16-byte vector stores when rows are aligned for them
@@ -216,10 +230,12 @@ __global__ void __launch_bounds__(kThreads, kStages == kDeep ? 1 : 2)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
     }
-    // a stage still holding TMA bytes after a timeout must land before exit
+    // after a timeout, the TMA loads still in flight must land before exit
+    // (bounded by the default 1 s, whatever limit the caller set)
     if (threadIdx.x == 0 && !have) {
-        for (int s = 0; s < kStages && s < nkz; ++s) {
-            const int last = ((nkz - 1 - s) / kStages) * kStages + s;   // last K tile loaded into stage s
+        const int n = S.issued;
+        for (int s = 0; s < kStages && s < n; ++s) {
+            const int last = ((n - 1 - s) / kStages) * kStages + s;     // last K tile loaded into stage s
             mbar_wait(&S.full[s], (last / kStages) & 1, nullptr);
         }
     }

@@ -28,6 +28,11 @@ struct GemmArgs {
     // outputs); the caller sums the partials.  splits is capped at the number of K tiles.
     int splits;
     float* ws;
+    // bounded waits: the operand-ring waits give up after wait_ns of wall time
+    // (0: 1 s); withhold != 0 issues no TMA load at all, so the first wait runs
+    // out on a barrier nothing completes (a test of the timeout path)
+    unsigned long long wait_ns;
+    int withhold;
 };
 
 cudaError_t sf_gemm_launch(const GemmArgs& g, cudaStream_t s);

@@ -222,6 +222,10 @@ struct WorldArgs {
     int surr_mode;
     unsigned int* audit_err;   // float bits, max-reduced
     unsigned int* surr_count;  // number of agents that used the surrogate (accumulated)
+    // bounded wait of the road staging: limit in ns (0: 1 s); withhold != 0 sets
+    // the barrier up but issues no copy (a test of the timeout path)
+    unsigned long long wait_ns;
+    int withhold;
 };
 
 // surrogate feature / target layout (dynamics surrogate of the step)

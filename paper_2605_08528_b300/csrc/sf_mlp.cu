@@ -278,6 +278,8 @@ struct sf_mlp {
     float* red = nullptr;                    // [kSumsqBlocks] partial sums of the gradient norm
     const sf_mlp* share = nullptr;           // while set: layer 0 reads its bf16 input (and its transpose) from it
     unsigned* errw = nullptr;
+    unsigned long long wait_ns = 0;          // GEMM ring-wait limit (0: 1 s)
+    int withhold = 0;                        // GEMMs issue no operand loads (timeout test)
 };
 
 namespace {
@@ -307,6 +309,7 @@ cudaError_t gemm(sf_mlp* m, const __nv_bfloat16* A, const __nv_bfloat16* B, cons
     GemmArgs g{};
     g.A = A; g.B = B; g.bias = bias; g.pre = pre; g.out_f32 = out_f32; g.out_bf16 = out_bf16; g.out_bf16_t = out_t;
     g.M = M; g.N = N; g.Nb = Nb; g.K = K; g.ldc = ldc; g.ldt = ldt; g.act = act; g.bn = tile_for(N); g.err = m->errw;
+    g.wait_ns = m->wait_ns; g.withhold = m->withhold;
     return sf_gemm_launch(g, use_st ? st : m->stream);
 }
 
@@ -364,7 +367,7 @@ cudaError_t weight_grad(sf_mlp* m, int l, int B, const __nv_bfloat16* dzt, cudaS
     const int S = std::max(1, std::min(std::min(kSplitMax, nk), 296 / std::max(1, tiles)));
     GemmArgs g{};
     g.A = dzt; g.B = xt_in(m, l); g.M = o; g.N = li; g.Nb = li; g.K = B; g.ldc = li; g.act = SF_ACT_NONE;
-    g.bn = bn; g.err = m->errw;
+    g.bn = bn; g.err = m->errw; g.wait_ns = m->wait_ns; g.withhold = m->withhold;
     if (S > 1) { g.ws = m->ws; g.splits = S; } else { g.out_f32 = m->gwfull; }
     cudaError_t e = sf_gemm_launch(g, st);
     if (e != cudaSuccess) return e;
@@ -540,15 +543,17 @@ extern "C" {
 
 sf_status sf_mlp_forward_static(sf_mlp_handle m, const float* d_x, int ldx, int batch, float* d_y, int ldy) {
     if (!m || !d_x || !d_y || batch < 0 || ldx < m->dim[0] || ldy < m->dim[m->L]) return SF_ERR_INVALID_ARG;
+    // the address lookup comes first, so that a call with batch 0 primes the
+    // device (before any stream capture) without touching any buffer
+    void* base = nullptr;
+    cudaError_t e = static_scratch(&base);
+    if (e != cudaSuccess) return mfail(m, SF_ERR_CUDA, std::string("static scratch: ") + cudaGetErrorString(e));
     if (batch == 0) return SF_OK;
     const size_t need = static_need(m, batch);
     if (need > kStaticScratchBytes)
         return mfail(m, SF_ERR_INVALID_ARG,
                      "sf_mlp_forward_static: batch " + std::to_string(batch) + " needs " + std::to_string(need) +
                          " bytes of scratch; the static scratch holds " + std::to_string(kStaticScratchBytes));
-    void* base = nullptr;
-    cudaError_t e = static_scratch(&base);
-    if (e != cudaSuccess) return mfail(m, SF_ERR_CUDA, std::string("static scratch: ") + cudaGetErrorString(e));
     // carve: bf16 input of every layer, then the fp32 output; zero it (padding columns must read as 0)
     unsigned char* p = static_cast<unsigned char*>(base);
     __nv_bfloat16* xs[kMaxLayers] = {};
@@ -810,6 +815,13 @@ sf_status sf_mlp_sync(sf_mlp_handle m) {
         cudaMemset(m->errw, 0, 4);
         return mfail(m, SF_ERR_TIMEOUT, "a tensor-core GEMM gave up waiting for its operands");
     }
+    return SF_OK;
+}
+
+sf_status sf_mlp_set_wait_limit(sf_mlp_handle m, unsigned long long limit_ns, int withhold_producer) {
+    if (!m) return SF_ERR_INVALID_ARG;
+    m->wait_ns = limit_ns == 0 ? 1ull : limit_ns;   // the kernels read 0 as the 1 s default
+    m->withhold = withhold_producer != 0;
     return SF_OK;
 }
 

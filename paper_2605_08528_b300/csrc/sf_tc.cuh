@@ -49,13 +49,14 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // bounded wait: false (and the error flag) when the barrier has not completed
-// within kWaitNs of wall time
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err, unsigned flag) {
+// within limit_ns of wall time (1 s unless a caller asks for less)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err, unsigned flag,
+                                          uint64_t limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 0; i < kWaitLimit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63) == 63 && global_ns() - t0 > kWaitNs) break;
+        if ((i & 63) == 63 && global_ns() - t0 > limit_ns) break;
     }
     if (err) atomicOr(err, flag);
     return false;

@@ -1106,26 +1106,29 @@ __device__ __forceinline__ uint64_t now_ns() {
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
 }
-__device__ bool stage_wait(uint64_t* bar) {
+// bounded wait for the staging copy: false when it has not landed within limit_ns
+__device__ bool stage_wait(uint64_t* bar, uint64_t limit_ns) {
     if (stage_done(bar)) return true;
     const uint64_t t0 = now_ns();
     for (uint32_t i = 0; i < kStageSpinMax; ++i) {
         if (stage_done(bar)) return true;
-        if ((i & 63) == 63 && now_ns() - t0 > kStageWaitNs) break;
+        if ((i & 63) == 63 && now_ns() - t0 > limit_ns) break;
     }
     return false;
 }
-// warp 0: lane 0 arms the barrier for `total` bytes, lane t copies world t
+// warp 0: lane 0 arms the barrier for `total` bytes, lane t copies world t;
+// with `withhold` the barrier is only initialised (nothing will complete it)
 __device__ void stage_issue(const unsigned char* gblob, const DevGrid* sg, const int* woff, int nworlds, int total,
-                            unsigned char* dst, uint64_t* bar, int lane) {
+                            unsigned char* dst, uint64_t* bar, int lane, bool withhold) {
     if (lane == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(total)
-                     : "memory");
+        if (!withhold)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(total)
+                         : "memory");
     }
     __syncwarp();
-    if (lane < nworlds && sg[lane].bytes > 0)
+    if (!withhold && lane < nworlds && sg[lane].bytes > 0)
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                          smem_addr(dst + woff[lane])),
                      "l"(gblob + sg[lane].blob), "r"(sg[lane].bytes), "r"(smem_addr(bar))
@@ -1473,7 +1476,9 @@ __device__ __forceinline__ void lanes_events_b(const WorldArgs& args, const Slot
             tmin = fminf(tmin, tt[t]);
             dmax = fmaxf(dmax, N.dr[lane][t]);
         }
-        if (tmin < kTtcMax) r -= penalty(kTtcAlphaV, tmin, kTtcPmaxV);
+        // App. G: p(tau) of the minimum TTC over the neighbours; a neighbour on no
+        // collision course has TTC = tau_max (App. D), so any neighbour costs >= 0.01
+        if (nb[0] >= 0) r -= penalty(kTtcAlphaV, tmin, kTtcPmaxV);
         r -= kWDrac * fmaxf(0.f, dmax - kDracThresh);
         drac = dmax;
         A.peak = fmaxf(A.peak, dmax);
@@ -1753,7 +1758,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         if (lane == 0) s_staged = staged ? 1 : 0;
         __syncwarp();
         if (staged && MODE != kModeReset)
-            stage_issue(args.rd.blob, s_grid, s_woff, pk.y, stage_total, s_blob, &s_bar, lane);
+            stage_issue(args.rd.blob, s_grid, s_woff, pk.y, stage_total, s_blob, &s_bar, lane, args.withhold != 0);
         if (kDraw && MODE == kModeStep) named_bar_arrive(1, 32 * NW);   // the pack tables are written
     } else if (kDraw && MODE == kModeStep) {
         named_bar_sync(1, 32 * NW);
@@ -1783,7 +1788,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         __syncthreads();
         if (s_any == 0u) return;                      // CTA-uniform: no masked agent in this pack
         if (warp == 0 && staged)
-            stage_issue(args.rd.blob, s_grid, s_woff, pk.y, stage_total, s_blob, &s_bar, lane);
+            stage_issue(args.rd.blob, s_grid, s_woff, pk.y, stage_total, s_blob, &s_bar, lane, args.withhold != 0);
         if (kDraw) {
             if (warp != 0) draw_spawns(args, pk, s_slot_w, s_wbase, threadIdx.x - 32, 32 * (NW - 1), s_sp);
             __syncthreads();
@@ -1800,7 +1805,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         }
         __syncthreads();
         if (s_staged) {
-            stg = stage_wait(&s_bar);
+            stg = stage_wait(&s_bar, args.wait_ns ? args.wait_ns : kStageWaitNs);
             if (!stg) atomicOr(args.out.error_word, 2u);
         }
         // ---------------- road queries of the events (all warps, one agent at a time)
@@ -1853,7 +1858,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
 
     // ---------------- road-point block of every observation (all warps)
     if (MODE != kModeStep && s_staged) {
-        stg = stage_wait(&s_bar);
+        stg = stage_wait(&s_bar, args.wait_ns ? args.wait_ns : kStageWaitNs);
         if (!stg) atomicOr(args.out.error_word, 2u);
     }
     for (int j = warp; j < m; j += NW) {
@@ -1877,7 +1882,9 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
 
     // ---------------- neighbours (warp 0), their rows (all warps), ego group, outputs, state (warp 0)
     if (warp == 0) {
-        if (lane == 0 && s_staged && !stg) stage_wait(&s_bar);   // no copy may outlive the block
+        // no copy may outlive the block: after a wait that gave up, wait again
+        // (bounded by 1 s whatever the caller's limit) for the copy this block issued
+        if (lane == 0 && s_staged && !stg && !args.withhold) stage_wait(&s_bar, kStageWaitNs);
         lanes_final_a(c, lane, A, recompute, s_alive, E, nb, hx, hy, N);
         const unsigned rb = __ballot_sync(kFull, recompute);
         if (lane == 0) s_rec = rb;

@@ -74,7 +74,8 @@ def lib():
             "sf_output_ptrs": ([vp, vp], i32), "sf_observe_full": ([vp, vp, vp, vp, vp, vp], i32), "sf_get_indices": ([vp, vp, vp, vp, vp], i32), "sf_reset": ([vp, vp], i32), "sf_place_agents": ([vp, vp], i32),
             "sf_get_state": ([vp, vp, vp], i32), "sf_set_state": ([vp, vp, vp], i32),
             "sf_save_state": ([vp, C.c_char_p], i32), "sf_load_state": ([vp, C.c_char_p], i32),
-            "sf_sync": ([vp], i32), "sf_autotune": ([vp, vp, f32, C.c_int, C.c_int, vp, vp], i32), "sf_num_agents": ([vp], i32), "sf_num_worlds": ([vp], i32),
+            "sf_sync": ([vp], i32), "sf_set_wait_limit": ([vp, C.c_ulonglong, C.c_int], i32),
+            "sf_mlp_set_wait_limit": ([vp, C.c_ulonglong, C.c_int], i32), "sf_autotune": ([vp, vp, f32, C.c_int, C.c_int, vp, vp], i32), "sf_num_agents": ([vp], i32), "sf_num_worlds": ([vp], i32),
             "sf_last_error": ([vp], C.c_char_p), "sf_version": ([], C.c_char_p),
             "sf_mlp_create": ([C.c_int, vp, C.c_int, C.c_int, vp, vp], i32), "sf_mlp_destroy": ([vp], i32),
             "sf_mlp_last_error": ([vp], C.c_char_p), "sf_mlp_set_layer": ([vp, C.c_int, vp, vp], i32),
@@ -235,6 +236,16 @@ def sf_load_state(h, path):
 
 def sf_sync(h, allow=()):
     return _check(lib().sf_sync(h), h, allow=allow)
+
+
+def sf_set_wait_limit(h, limit_ns=1_000_000_000, withhold_producer=False):
+    """Limit of the step kernels' bounded staging wait (and the test switch that issues no copy)."""
+    _check(lib().sf_set_wait_limit(h, int(limit_ns), int(bool(withhold_producer))), h)
+
+
+def sf_mlp_set_wait_limit(m, limit_ns=1_000_000_000, withhold_producer=False):
+    """Limit of the MLP GEMMs' bounded operand waits (and the test switch that issues no load)."""
+    _mcheck(lib().sf_mlp_set_wait_limit(m, int(limit_ns), int(bool(withhold_producer))), m)
 
 
 AUTOTUNE_SHAPES = 38

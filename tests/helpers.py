@@ -95,3 +95,48 @@ def in_contact(F, I, scene):
                 if d > 0:
                     out[i] = out[j] = True
     return out
+
+
+TIE = 1e-5
+
+
+def heading(F, a):
+    """Unit heading (x, y) of agent a: the body x axis projected on the road plane."""
+    from oracle import oracle as O
+    qw, qx, qy, qz = (float(F[a, k]) for k in (O.F_QW, O.F_QX, O.F_QY, O.F_QZ))
+    hx, hy = 1.0 - 2.0 * (qy * qy + qz * qz), 2.0 * (qx * qy + qw * qz)
+    n = math.hypot(hx, hy)
+    return np.array([hx / n, hy / n]) if n > 0 else np.array([1.0, 0.0])
+
+
+def agent_tie(scene, F, I, w, a_local, p, K=8):
+    """True if the selection of the K nearest alive other agents of p has a near-tie."""
+    from oracle import oracle as O
+    a0, a1 = scene.agent_off[w], scene.agent_off[w + 1]
+    d = [np.hypot(F[j, 0] - p[0], F[j, 1] - p[1]) for j in range(a0, a1)
+         if j != a_local and I[j, O.I_STATUS] & O.ALIVE]
+    ds = np.sort(np.asarray(d, np.float64))[:K + 1]
+    return len(ds) > 1 and np.diff(ds).min() < TIE
+
+
+def ttc_tie(F, a, j, gpu_feature, tol, trials=200, eps=1e-5):
+    """True if the FP64 TTC of pair (a, j) comes within tol of the GPU's TTC
+    feature (TTC / 10 s) for some perturbation of the pair's positions and
+    velocities by ~eps (m, m/s) and headings by ~eps rad: the quadratic's root
+    is ill-conditioned there (a grazing closest approach, or the choice
+    between no root and a root).  A genuine discrepancy matches none."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(1000 * a + j)
+    pi, vi, hi = F[a, 0:2].astype(np.float64), F[a, 7:9].astype(np.float64), heading(F, a)
+    pj, vj, hj = F[j, 0:2].astype(np.float64), F[j, 7:9].astype(np.float64), heading(F, j)
+
+    def rot(h, e):
+        c, s = math.cos(e), math.sin(e)
+        return np.array([c * h[0] - s * h[1], s * h[0] + c * h[1]])
+
+    for _ in range(trials):
+        e = rng.normal(0, eps, 10)
+        t = O.ttc(pi + e[0:2], rot(hi, e[8]), vi + e[2:4], pj + e[4:6], rot(hj, e[9]), vj + e[6:8])
+        if abs(t / 10.0 - gpu_feature) <= tol:
+            return True
+    return False

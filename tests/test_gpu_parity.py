@@ -1,7 +1,7 @@
 """GPU parity: the CUDA step through the C-ABI against the FP64 oracle on the
 same seeded inputs.
 
-Tolerances (written here, derived in the design notes):
+Tolerances:
   * single step, per state block: ||gpu - oracle|| / max(||x||, floor) <= 1e-5
     (floors: 1 m, 1 m/s, 1 rad/s, 1 rad/s spin, 1e-2 rad steer; attitude angle
     relative to max(angle, 0.1 rad)) for agents not in footprint contact; an
@@ -10,9 +10,14 @@ Tolerances (written here, derived in the design notes):
     and ~1.3e-5 rad/s per step;
   * 100-step non-contact rollouts: |dp| <= 1e-3 m and |dv| <= 1e-3 m/s;
   * indices and event flags: bit-exact when the oracle is fed the GPU's FP32
-    state, except near-ties (selection margins below 1e-5 m), which are counted
-    and reported;
-  * observation floats: |d| <= 2e-5 absolute on features of unit scale.
+    state, except near-ties (selection margins below 1e-5 m, or a state
+    perturbation of 1e-5 under which the oracle reproduces the GPU), which are
+    counted and reported;
+  * observation floats: |d| <= 2e-5 absolute on features of unit scale (FP32
+    rounding of O(100 m) positions is ~1e-5 m, divided by the 10-100 m
+    normalisers), every neighbour's TTC feature included unless a 1e-5
+    perturbation of the pair's state moves the FP64 TTC onto the GPU's value
+    (a grazing closest approach, where the quadratic's root is ill-conditioned).
 """
 import math
 
@@ -23,14 +28,14 @@ torch = pytest.importorskip("torch")
 
 from oracle import oracle as O
 from paper_2605_08528_b300 import sf, synth
-from tests.helpers import block_errors, in_contact, subscene
+from tests.helpers import TIE, agent_tie, block_errors, in_contact, subscene, ttc_tie
 
 pytestmark = pytest.mark.gpu
 
 TOL_STEP = 1e-5
 TOL_CONTACT = 5e-5
 TOL_OBS = 2e-5
-TIE = 1e-5
+TTC_COLS = [16 + 10 * k + 8 for k in range(8)]
 
 
 def dev(x, dtype=None):
@@ -205,8 +210,8 @@ def test_discrete_and_observation_parity(flags, pack, stage, split):
     oflags = (O.FLAG_INVINCIBLE if flags & sf.FLAG_INVINCIBLE else 0) | (
         O.FLAG_AUTO_RESET if flags & sf.FLAG_AUTO_RESET else 0)
     acts = synth.ou_actions(W.A, 30, seed=4, sigma=0.5)
-    ties = dict(lane=0, knn_pts=0, knn_agents=0, events=0)
-    checked = 0
+    ties = dict(lane=0, knn_pts=0, knn_agents=0, ttc=0, events=0)
+    checked = obs_rows = 0
     for t in range(30):
         F0, I0, _ = sf.sf_get_state(W.h)
         sf.sf_step(W.h, dev(acts[t]))
@@ -255,18 +260,24 @@ def test_discrete_and_observation_parity(flags, pack, stage, split):
                 ties["knn_pts"] += 1
                 continue
             if not np.array_equal(ix["knn_agents"][a], oo["knn_agents"][a]):
+                assert agent_tie(sc, F1, I1, w, a, p), (t, a)
                 ties["knn_agents"] += 1
                 continue
             d = np.abs(obs[a] - oo["obs"][a])
             for k in range(8):          # relative heading / pi wraps at +-1
                 c = 16 + 10 * k + 4
                 d[c] = min(d[c], abs(2.0 - d[c]))
-            ttc_cols = [16 + 10 * k + 8 for k in range(8)]
-            dd = np.delete(d, ttc_cols)
+            dd = np.delete(d, TTC_COLS)
             assert dd.max() <= TOL_OBS, (t, a, int(np.argmax(dd)), float(dd.max()))
-            assert (d[ttc_cols] <= 1e-3).sum() >= 7
-    print("near-ties counted:", ties, "event rows checked:", checked)
-    assert sum(ties.values()) <= 0.01 * 30 * W.A + 3
+            for k, c in enumerate(TTC_COLS):     # every neighbour's TTC, to the observation tolerance
+                if d[c] > TOL_OBS:
+                    j = int(ix["knn_agents"][a][k])
+                    assert j >= 0 and ttc_tie(F1, a, j, float(obs[a][c]), TOL_OBS), (t, a, k, float(d[c]))
+                    ties["ttc"] += 1
+            obs_rows += 1
+    print("near-ties counted:", ties, "event rows checked:", checked, "observation rows checked:", obs_rows)
+    assert ties["lane"] + ties["knn_pts"] + ties["knn_agents"] <= 4
+    assert ties["ttc"] <= 4 and ties["events"] <= 4
 
 
 # ----------------------------------------------------------------------------- resets
@@ -514,15 +525,6 @@ def test_nonfinite_state_is_reported_and_contained():
 
 
 # ----------------------------------------------------------------------------- full-size sampled parity
-def agent_tie(scene, F, I, w, a_local, p, K=8):
-    """True if the selection of the K nearest alive other agents of p has a near-tie."""
-    a0, a1 = scene.agent_off[w], scene.agent_off[w + 1]
-    d = [np.hypot(F[j, 0] - p[0], F[j, 1] - p[1]) for j in range(a0, a1)
-         if j != a_local and I[j, O.I_STATUS] & O.ALIVE]
-    ds = np.sort(np.asarray(d, np.float64))[:K + 1]
-    return len(ds) > 1 and np.diff(ds).min() < TIE
-
-
 # (warps per block, pack agents, stage bytes, split step) the benchmark has timed
 # on each workload; None: the autotuner's pick, as in the benchmark
 @pytest.mark.parametrize("name,shape", [("256x16", (8, 0, 48 << 10, 0)), ("256x16", None),
@@ -567,8 +569,7 @@ def test_full_size_sampled_parity(name, shape):
         assert e.max() <= TOL_STEP, (k, float(e.max()))
     Fs, Is = F1[rows].astype(np.float64), I1[rows].copy()
     oo = orc.observe(Fs, Is)
-    ttc_cols = [16 + 10 * k + 8 for k in range(8)]
-    checked = ties = 0
+    checked = ties = ttc_ties = 0
     for i, a in enumerate(rows):
         if not I1[a, O.I_STATUS] & O.ALIVE:
             assert not obs[a].any()
@@ -577,7 +578,7 @@ def test_full_size_sampled_parity(name, shape):
         for k in range(8):          # relative heading / pi wraps at +-1
             c = 16 + 10 * k + 4
             d[c] = min(d[c], abs(2.0 - d[c]))
-        dd = np.delete(d, ttc_cols)
+        dd = np.delete(d, TTC_COLS)
         if dd.max() > TOL_OBS:
             w = int(np.searchsorted(sub.agent_off, i, side="right") - 1)
             p = Fs[i, :2]
@@ -585,7 +586,11 @@ def test_full_size_sampled_parity(name, shape):
                     or agent_tie(sub, Fs, Is, w, i, p)), (i, int(np.argmax(dd)), float(dd.max()))
             ties += 1
             continue
-        assert (d[ttc_cols] <= 1e-3).sum() >= 7
+        for k, c in enumerate(TTC_COLS):     # same neighbours (features agree): every TTC slot
+            if d[c] > TOL_OBS:
+                j = int(oo["knn_agents"][i][k])
+                assert j >= 0 and ttc_tie(Fs, i, j, float(obs[a][c]), TOL_OBS), (i, k, float(d[c]))
+                ttc_ties += 1
         checked += 1
-    print("observation rows checked:", checked, "near-ties:", ties)
-    assert checked >= 20 and ties <= 0.02 * len(rows) + 2
+    print("observation rows checked:", checked, "near-ties:", ties, "grazing TTC roots:", ttc_ties)
+    assert checked >= 20 and ties <= 3 and ttc_ties <= 3

@@ -6,7 +6,7 @@
   differences of FP32 states), and the gate selects the same agents;
 * agents the gate leaves to the physics evolve bit-identically to a plain step;
 * the trained surrogate's 1 s (30-step) rollout position error against the
-  FP64 oracle physics is measured and reported (target: 1 cm);
+  FP64 oracle physics: mean <= 1 cm (the target), p90 / p99 / max printed;
 * a seeded collection gives the same rows on every run, a cap keeps the first
   rows, and training on the same rows gives the same loss and weights.
 """
@@ -140,23 +140,6 @@ def test_collection_repeats_and_cap_keeps_the_first_rows():
         assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
 
 
-def train_small(sc_train, steps=1500, collect_steps=120):
-    W = sf.World(sc_train, seed=11, flags=sf.FLAG_AUTO_RESET)
-    sf.sf_reset(W.h, dev(np.ones(W.A, np.uint8)))
-    s = sf.sf_surrogate_create()
-    cap = W.A * collect_steps
-    dx = torch.zeros((cap, 30), device="cuda")
-    dy = torch.zeros((cap, 16), device="cuda")
-    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-    acts = dev(synth.ou_actions(W.A, collect_steps, seed=13))
-    for t in range(collect_steps):
-        sf.sf_surrogate_collect(W.h, s, acts[t], dx, dy, cap, cnt)
-    n = min(int(cnt.item()), cap)
-    loss = sf.sf_surrogate_train(s, dx, dy, n, batch=4096, steps=steps, lr=2e-3, seed=7)
-    W.close()
-    return s, n, loss
-
-
 def test_ungated_agents_follow_the_physics_exactly():
     sc = synth.procedural_scene(8, 16, seed_base=950, weather="uniform")
     s = sf.sf_surrogate_create()
@@ -181,9 +164,11 @@ def test_ungated_agents_follow_the_physics_exactly():
 
 
 def test_trained_surrogate_rollout_error_against_the_oracle():
-    s, n, loss = train_small(synth.procedural_scene(64, 8, seed_base=3000))
+    from paper_2605_08528_b300 import surrogate as SU
+    s, n, loss = SU.collect_and_train(synth.procedural_scene(128, 16, seed_base=3000), transitions=4_000_000,
+                                      train_steps=40000, seed=31)
     print("training rows", n, "final normalised loss %.4f" % loss)
-    assert n > 20000 and loss < 0.5
+    assert n > 1_000_000 and loss < 0.1
     # 1 s rollouts of lone agents (one per world, mu >= 0.3 cells only) against the FP64 physics
     scw = synth.procedural_scene(96, 1, seed_base=3500)
     scw.precip[:] = np.minimum(scw.precip, 2)                  # keep mu >= 0.3 (no snow)
@@ -204,11 +189,11 @@ def test_trained_surrogate_rollout_error_against_the_oracle():
         orc.step(Fo, Io, a.astype(np.float64), flags=O.FLAG_INVINCIBLE, want_obs=False)
     F1, _, _ = sf.sf_get_state(W.h)
     err = np.linalg.norm(F1[:, :3] - Fo[:, :3], axis=1)
-    print("surrogate 1 s rollout position error vs FP64 oracle: mean %.4f m, p90 %.4f m, max %.4f m "
-          "(agent-steps on the surrogate %d of %d)" % (err.mean(), np.percentile(err, 90), err.max(), used_total,
-                                                       30 * W.A))
+    print("surrogate 1 s rollout position error vs FP64 oracle: mean %.4f m, p90 %.4f m, p99 %.4f m, max %.4f m "
+          "(agent-steps on the surrogate %d of %d)" % (err.mean(), np.percentile(err, 90), np.percentile(err, 99),
+                                                       err.max(), used_total, 30 * W.A))
     assert used_total > 0.8 * 30 * W.A
-    assert np.isfinite(err).all() and err.mean() < 1.0
+    assert np.isfinite(err).all() and err.mean() <= 1e-2
     # the audit measures the same kind of error on one step
     sf.sf_step_surrogate(W.h, s, dev(warm[0]), audit=True)
     e1, used = sf.sf_surrogate_audit(W.h)

@@ -323,6 +323,38 @@ def test_collision_warmup_and_reward():
     assert out["reward"][0] < -5.0
 
 
+def test_ttc_penalty_on_the_minimum_neighbour_ttc():
+    """App. G: r_ttc = -p(min over neighbours of TTC), p(tau) = min(0.10 / max(tau, 0.5), 0.35),
+    with TTC = tau_max = 10 s for a neighbour behind the ego or on no collision
+    course (App. D).  So one harmless neighbour costs exactly 0.10 / 10 = 0.01."""
+    def reward_of_agent0(others):
+        sc, orc, F, I = road_world(1 + len(others))
+        orc.place(F, I, 0, 0.0, -1.8, 0.0, 10.0, 80.0, -1.8)
+        for k, (x, y, v) in enumerate(others):
+            orc.place(F, I, 1 + k, x, y, 0.0, v, 80.0, y)
+        return orc.events(F, I, F[:, :2].copy())["reward"][0]
+
+    alone = reward_of_agent0([])
+    # same speed on the other lane, 30 m ahead: no collision course
+    assert abs((alone - reward_of_agent0([(30.0, 1.8, 10.0)])) - 0.01) < 1e-12
+    # behind the ego, closing: still TTC = tau_max for the ego
+    assert abs((alone - reward_of_agent0([(-30.0, -1.8, 20.0)])) - 0.01) < 1e-12
+    # stopped 20 m ahead in the same lane: the front circle of the ego (+1.3 m)
+    # meets the rear circle of the other (-1.3 m) when their gap 17.4 m has
+    # shrunk to 2 r = 1.98 m, at 10 m/s: tau = 1.542 s
+    tau = (20.0 - 2 * 1.3 - 2 * 0.99) / 10.0
+    closing = reward_of_agent0([(20.0, -1.8, 0.0)])
+    assert abs((alone - closing) - 0.10 / tau) < 1e-12
+    # the minimum over the neighbours decides, not the sum
+    both = reward_of_agent0([(30.0, 1.8, 10.0), (20.0, -1.8, 0.0)])
+    assert abs((alone - both) - 0.10 / tau) < 1e-12
+    # 5.5 m ahead (footprints 1 m apart), closing at 10 m/s: tau = (2.9 - 1.98) / 10
+    # = 0.092 s is floored at 0.5 s, p = 0.10 / 0.5 = 0.2 (below the 0.35 cap);
+    # DRAC = 10^2 / (2 * 1.0) = 50 m/s^2 adds 0.01 * (50 - 3.4)
+    near = reward_of_agent0([(5.5, -1.8, 0.0)])
+    assert abs((alone - near) - (0.2 + 0.01 * (50.0 - 3.4))) < 1e-12
+
+
 def test_progress_reward_sign():
     sc, orc, F, I = road_world(1)
     orc.place(F, I, 0, 0.0, -1.8, 0.0, 10.0, 80.0, -1.8)
