@@ -203,7 +203,7 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, p
         W.close()
         return dict(scene=scene, A=A, alive=alive, ms=ms, wall=wall, status=st, e2e_wall=float("nan"),
                     e2e_steps=1, h2d=A * 12, d2h=A * 5, tuned=tuned, peak_drac=peak_drac,
-                    surr_frac=surr_used / float((warmup + steps) * A))
+                    surr_frac=surr_used / float((warmup + steps) * A), e2e_obs_wall=float("nan"), d2h_obs=0)
     # end to end through the C-ABI (sf_step_host): page-locked host actions in (a
     # ring of action sets), host rewards / done flags out, every step
     acts_pin = [torch.as_tensor(acts_h[k]).pin_memory() for k in range(ring)]
@@ -218,9 +218,21 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, p
         sf.sf_step_host(W.h, acts_pin[t % ring], rew_h, done_h)
         float(rew_np[0])                                 # the host consumes the result
     e2e_wall = time.perf_counter() - t0
+    # the same with the 320-value observation delivered to the host every step
+    # (sf_step_host_obs: one more copy node in the graph, 1,280 B per agent)
+    obs_h = torch.empty((A, sf.OBS_DIM), dtype=torch.float32).pin_memory()
+    obs_np = obs_h.numpy()
+    sf.sf_step_host_obs(W.h, acts_pin[0], obs_h, rew_h, done_h)   # capture outside the timed region
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for t in range(e2e_steps):
+        sf.sf_step_host_obs(W.h, acts_pin[t % ring], obs_h, rew_h, done_h)
+        float(rew_np[0]) + float(obs_np[0, 0])           # the host consumes the results
+    e2e_obs_wall = time.perf_counter() - t0
     W.close()
     return dict(scene=scene, A=A, alive=alive, ms=ms, wall=wall, status=st, e2e_wall=e2e_wall,
-                e2e_steps=e2e_steps, h2d=A * 12, d2h=A * 5, tuned=tuned, peak_drac=peak_drac, surr_frac=0.0)
+                e2e_steps=e2e_steps, h2d=A * 12, d2h=A * 5, tuned=tuned, peak_drac=peak_drac, surr_frac=0.0,
+                e2e_obs_wall=e2e_obs_wall, d2h_obs=A * (5 + sf.OBS_DIM * 4))
 
 
 def lf_flops(n_road, n_veh):
@@ -537,10 +549,12 @@ def main_ours(args):
         r = res[name]
         casps, e2e_casps = combine_over_ranks(float(r["ms"].sum()) / 1e3, r["e2e_wall"], r["alive"], args.steps,
                                               r["e2e_steps"], dist if world > 1 else None, torch, "cuda")
+        _, e2e_obs = combine_over_ranks(float(r["ms"].sum()) / 1e3, r["e2e_obs_wall"], r["alive"], args.steps,
+                                        r["e2e_steps"], dist if world > 1 else None, torch, "cuda")
         ab = algorithmic_bytes(r["scene"])
         mean_s = float(r["ms"].mean()) / 1e3
         ach = ab["total"] / mean_s / 1e9
-        return dict(casps=casps, e2e=e2e_casps, ms=float(r["ms"].mean()), p50=float(np.percentile(r["ms"], 50)),
+        return dict(casps=casps, e2e=e2e_casps, e2e_obs=e2e_obs, d2h_obs=r["d2h_obs"], ms=float(r["ms"].mean()), p50=float(np.percentile(r["ms"], 50)),
                     p99=float(np.percentile(r["ms"], 99)), bytes=ab, achieved=ach, A=r["A"], alive=r["alive"],
                     h2d=r["h2d"], d2h=r["d2h"], tuned=r["tuned"], peak_drac=r["peak_drac"], surr_frac=r["surr_frac"])
 
@@ -565,7 +579,13 @@ def main_ours(args):
                        "autotune": a256["tuned"]},
             "p50_ms": a256["p50"], "p99_ms": a256["p99"],
             "e2e": {"value": a256["e2e"], "unit": "CASPS", "h2d_bytes_per_step": a256["h2d"],
-                    "d2h_bytes_per_step": a256["d2h"]},
+                    "d2h_bytes_per_step": a256["d2h"],
+                    "what": "sf_step_host: actions in, rewards and done flags out each step; the observation "
+                            "stays on the device (a policy on the GPU reads it there)"},
+            "e2e_with_observation": {"value": a256["e2e_obs"], "unit": "CASPS", "h2d_bytes_per_step": a256["h2d"],
+                                     "d2h_bytes_per_step": a256["d2h_obs"],
+                                     "what": "sf_step_host_obs: the same plus the 320-value observation of every "
+                                             "agent copied to page-locked host memory each step"},
             "gpu_launches": args.steps,
             "graph": "each timed step is one CUDA-graph replay",
             "roofline": {"bound": "hbm", "kernel": step_kernels(a256["tuned"]), "achieved": a256["achieved"],
@@ -577,6 +597,9 @@ def main_ours(args):
                               "agents": a4096["A"] * world, "autotune": a4096["tuned"],
                               "e2e": {"value": a4096["e2e"], "unit": "CASPS", "h2d_bytes_per_step": a4096["h2d"],
                                       "d2h_bytes_per_step": a4096["d2h"]},
+                              "e2e_with_observation": {"value": a4096["e2e_obs"], "unit": "CASPS",
+                                                       "h2d_bytes_per_step": a4096["h2d"],
+                                                       "d2h_bytes_per_step": a4096["d2h_obs"]},
                               "roofline": {"bound": "hbm", "kernel": step_kernels(a4096["tuned"]),
                                            "achieved": a4096["achieved"], "peak": peak,
                                            "unit": "GB/s", "frac": a4096["achieved"] / peak,

@@ -125,7 +125,17 @@ typedef struct {
                               * atan(tan(delta) / 2), no suspension, contact response *
                               * or lateral slip.  Events, rewards, observations and  *
                               * resets are the same for both                          */
-    int32_t reserved[4];     /* must be zero                                          */
+    int32_t world_begin;     /* world range [world_begin, world_end) of the CSR given  */
+    int32_t world_end;       /* to sf_load_roads that this handle steps (both 0: every *
+                              * world).  Worlds are independent (no term of the step  *
+                              * couples two worlds), so one handle per GPU over       *
+                              * disjoint ranges shards a batch with no exchange; a    *
+                              * shard's worlds evolve bit-identically to the same    *
+                              * worlds in one handle over all of them (the respawn    *
+                              * draws use the agent's index in the whole CSR).  Agent *
+                              * indices of the handle's outputs are local to the      *
+                              * range                                                 */
+    int32_t reserved[2];     /* must be zero                                          */
 } sf_config;
 #define SF_DYN_VEHICLE 0
 #define SF_DYN_BICYCLE 1
@@ -166,11 +176,15 @@ typedef struct {
     int32_t num_agents;
 } sf_outputs;
 
-/* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
+/* Create a context on the current CUDA device: the batch of worlds and agents
+ * that SceneFactory exposes as GPU-resident tensors of shape (num_envs,
+ * num_agents, d) (Sec. 1; App. K "Batched joint-state tensors"), here owned
+ * by the library and stepped by its kernels.  cuda_stream is a cudaStream_t
  * (NULL = legacy default stream) on which every call of this handle enqueues
- * its work.  *out receives the handle.  Errors: SF_ERR_INVALID_ARG (NULL out,
- * nonzero reserved, pack_agents outside 0..32, bad stage_bytes, split_step or dynamics), SF_ERR_CUDA (no usable
- * device). */
+ * its work.  *out receives the handle.  cfg may be NULL (all defaults).
+ * Errors: SF_ERR_INVALID_ARG (NULL out, nonzero reserved, pack_agents outside
+ * 0..32, bad stage_bytes, split_step, dynamics or world range), SF_ERR_CUDA
+ * (no usable device). */
 sf_status sf_create(const sf_config* cfg, void* cuda_stream, sf_handle* out);
 
 /* Release every device and host resource of h (synchronous).  NULL is a no-op. */
@@ -212,6 +226,15 @@ sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps);
 sf_status sf_step_host(sf_handle h, const float* h_actions, float* h_reward, uint8_t* h_done, float dt,
                        int substeps);
 
+/* sf_step_host for a host that consumes the observations too: the same call,
+ * plus the step's observations [A][SF_OBS_DIM] float32 (1,280 B per agent)
+ * copied into h_obs by the copy engine inside the same graph (a copy node;
+ * page-locked h_obs required for the graph, else plain copies).  Switching
+ * between sf_step_host and this call re-captures the graph.
+ * Errors: as sf_step_host; SF_ERR_INVALID_ARG if h_obs is NULL. */
+sf_status sf_step_host_obs(sf_handle h, const float* h_actions, float* h_obs, float* h_reward, uint8_t* h_done,
+                           float dt, int substeps);
+
 /* Autotuner: time each launch shape of the step over `iters` steps with the
  * given actions and keep the fastest for this handle.  Shapes s < 32 are the
  * fused kernel with 1 << (s & 3) warps per block, world packing when bit 2 is
@@ -232,7 +255,12 @@ sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substep
 
 /* Copy the observations, rewards, done flags and event bits of the last step
  * or reset into caller device buffers ([A][SF_OBS_DIM], [A], [A], [A]); any
- * pointer may be NULL.  Asynchronous device-to-device copies. */
+ * pointer may be NULL.  Asynchronous device-to-device copies.  The
+ * observation is this library's 320-value analogue of App. D (ego 16 with
+ * the weather token of Eq. weather_obs, 8 nearest agents x 10 with the
+ * swept-circle TTC, 32 nearest road points x 7); rewards are the ten terms of
+ * App. G (Tab. app_reward_terms) plus DRAC; done marks the sparse events and
+ * the 1,500-step time-out (App. G "Termination and time-out"). */
 sf_status sf_get_obs(sf_handle h, float* d_obs, float* d_reward, uint8_t* d_done, uint32_t* d_events);
 
 /* Copy the inspection outputs of the last step / reset into caller device

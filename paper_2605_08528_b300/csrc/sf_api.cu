@@ -61,11 +61,13 @@ struct sf_ctx {
         const float* ha = nullptr;
         float* hr = nullptr;
         uint8_t* hd = nullptr;
+        float* ho = nullptr;    // observations [A][320] (sf_step_host_obs), null: not copied
         float* d_act = nullptr;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         bool mapped = false;    // the kernels read / write the host buffers through their device mapping
         cudaGraphNode_t n_act = nullptr, n_rew = nullptr, n_done = nullptr;   // copy nodes (not mapped)
+        cudaGraphNode_t n_obs = nullptr;                                        // observation copy node
         cudaGraphNode_t n_in = nullptr, n_out = nullptr;                      // kernel nodes (mapped)
     } hs;
 };
@@ -271,8 +273,13 @@ sf_status sf_create(const sf_config* cfg, void* cuda_stream, sf_handle* out) {
     *out = nullptr;
     sf_config c{};
     if (cfg) c = *cfg;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 2; ++i)
         if (c.reserved[i] != 0) { g_create_error = "sf_create: reserved fields must be zero"; return SF_ERR_INVALID_ARG; }
+    if (c.world_begin < 0 || c.world_end < 0 || (c.world_end != 0 && c.world_end <= c.world_begin) ||
+        (c.world_end == 0 && c.world_begin != 0)) {
+        g_create_error = "sf_create: world range must be 0 <= world_begin < world_end (or both 0)";
+        return SF_ERR_INVALID_ARG;
+    }
     if (c.dynamics != SF_DYN_VEHICLE && c.dynamics != SF_DYN_BICYCLE) {
         g_create_error = "sf_create: dynamics must be SF_DYN_VEHICLE or SF_DYN_BICYCLE";
         return SF_ERR_INVALID_ARG;
@@ -319,6 +326,40 @@ int32_t sf_num_worlds(sf_handle h) { return h ? h->W : 0; }
 sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     if (!h) return SF_ERR_INVALID_ARG;
     if (!r) return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: roads is NULL");
+    // world range: the CSR of worlds [world_begin, world_end), offsets re-based
+    sf_roads rs{};
+    std::vector<int32_t> s_aoff, s_poff, s_ptoff;
+    int agent_base = 0;
+    if (h->cfg.world_end != 0) {
+        const int w0 = h->cfg.world_begin, w1 = h->cfg.world_end;
+        if (w1 > r->num_worlds) return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: world range beyond num_worlds");
+        if (!r->agent_off || !r->poly_off || !r->point_off)
+            return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: NULL array");
+        const int a0 = r->agent_off[w0], p0 = r->poly_off[w0], p1 = r->poly_off[w1];
+        if (a0 < 0 || p0 < 0 || p1 < p0 || p1 > r->num_polylines)
+            return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: world range offsets out of order");
+        const int q0 = r->point_off[p0];
+        if (q0 < 0 || r->point_off[p1] < q0)
+            return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: world range offsets out of order");
+        for (int w = w0; w <= w1; ++w) {
+            s_aoff.push_back(r->agent_off[w] - a0);
+            s_poff.push_back(r->poly_off[w] - p0);
+        }
+        for (int p = p0; p <= p1; ++p) s_ptoff.push_back(r->point_off[p] - q0);
+        rs.num_worlds = w1 - w0;
+        rs.num_polylines = p1 - p0;
+        rs.num_points = r->point_off[p1] - q0;
+        rs.agent_off = s_aoff.data();
+        rs.poly_off = s_poff.data();
+        rs.point_off = s_ptoff.data();
+        rs.poly_type = r->poly_type ? r->poly_type + p0 : nullptr;
+        rs.px = r->px ? r->px + q0 : nullptr;
+        rs.py = r->py ? r->py + q0 : nullptr;
+        rs.precip = r->precip ? r->precip + a0 : nullptr;
+        rs.surface = r->surface ? r->surface + a0 : nullptr;
+        agent_base = a0;
+        r = &rs;
+    }
     const int W = r->num_worlds, NPl = r->num_polylines, NP = r->num_points;
     if (W <= 0 || NPl < 0 || NP < 0) return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: negative or zero sizes");
     if (!r->agent_off || !r->poly_off || !r->point_off || (NPl > 0 && !r->poly_type) || (NP > 0 && (!r->px || !r->py)))
@@ -510,7 +551,7 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     float4* dmid; uint8_t* dptype;
     SF_ALLOC(dmid, float4, (size_t)NP + 1);
     SF_ALLOC(dptype, uint8_t, (size_t)NP + 1);
-    h->rd = DevRoads{dworld, dcand, dpt, dpend, darc, dcands, dgrid, dblob, dmid, dptype};
+    h->rd = DevRoads{dworld, dcand, dpt, dpend, darc, dcands, dgrid, dblob, dmid, dptype, agent_base};
     float *obs, *reward, *drac; uint8_t* done; uint32_t* events; int32_t *lane_seg, *knn_pts, *knn_agents;
     unsigned int* err_word; float* hint;
     SF_ALLOC(obs, float, Aa * SF_OBS_DIM);
@@ -663,13 +704,13 @@ void find_copy_nodes(sf_ctx* h) {
         if (prm.srcPtr.ptr == h->hs.ha) h->hs.n_act = nd;
         else if (prm.dstPtr.ptr == h->hs.hr) h->hs.n_rew = nd;
         else if (prm.dstPtr.ptr == h->hs.hd) h->hs.n_done = nd;
+        else if (h->hs.ho && prm.dstPtr.ptr == h->hs.ho) h->hs.n_obs = nd;
     }
 }
 
-}  // namespace
-
-sf_status sf_step_host(sf_handle h, const float* h_actions, float* h_reward, uint8_t* h_done, float dt,
-                       int substeps) {
+// the control step from host buffers (sf_step_host, and with h_obs sf_step_host_obs)
+sf_status step_host(sf_handle h, const float* h_actions, float* h_obs, float* h_reward, uint8_t* h_done, float dt,
+                    int substeps) {
     if (!h) return SF_ERR_INVALID_ARG;
     if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_step_host: no roads loaded");
     if (h->A > 0 && (!h_actions || !h_reward || !h_done)) return fail(h, SF_ERR_INVALID_ARG, "sf_step_host: NULL buffer");
@@ -683,13 +724,17 @@ sf_status sf_step_host(sf_handle h, const float* h_actions, float* h_reward, uin
         h->allocs.push_back(p);
         c.d_act = static_cast<float*>(p);
     }
-    const bool same = c.exec && c.dt == dt && c.substeps == substeps && c.gen == h->gen;
-    if (same && c.ha == h_actions && c.hr == h_reward && c.hd == h_done) {   // replay
+    const size_t obs_bytes = A * SF_OBS_DIM * 4;
+    // the graph copies the observation or not: a change of that re-captures
+    const bool same = c.exec && c.dt == dt && c.substeps == substeps && c.gen == h->gen &&
+                      (c.ho != nullptr) == (h_obs != nullptr);
+    if (same && c.ha == h_actions && c.hr == h_reward && c.hd == h_done && c.ho == h_obs) {   // replay
         SF_CUDA(h, cudaGraphLaunch(c.exec, h->stream));
         SF_CUDA(h, cudaStreamSynchronize(h->stream));
         return SF_OK;
     }
-    const bool pinned = page_locked(h_actions) && page_locked(h_reward) && page_locked(h_done);
+    const bool pinned = page_locked(h_actions) && page_locked(h_reward) && page_locked(h_done) &&
+                        (!h_obs || page_locked(h_obs));
     if (!h->stream || !pinned || A == 0) {   // no graph: plain copies around the step
         if (A > 0) SF_CUDA(h, cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream));
         sf_status st = sf_step(h, c.d_act, dt, substeps);
@@ -697,6 +742,7 @@ sf_status sf_step_host(sf_handle h, const float* h_actions, float* h_reward, uin
         if (A > 0) {
             SF_CUDA(h, cudaMemcpyAsync(h_reward, h->out.reward, A * 4, cudaMemcpyDeviceToHost, h->stream));
             SF_CUDA(h, cudaMemcpyAsync(h_done, h->out.done, A, cudaMemcpyDeviceToHost, h->stream));
+            if (h_obs) SF_CUDA(h, cudaMemcpyAsync(h_obs, h->out.obs, obs_bytes, cudaMemcpyDeviceToHost, h->stream));
         }
         SF_CUDA(h, cudaStreamSynchronize(h->stream));
         return SF_OK;
@@ -708,7 +754,10 @@ sf_status sf_step_host(sf_handle h, const float* h_actions, float* h_reward, uin
     uint8_t* dd = static_cast<uint8_t*>(device_view(h_done));
     const bool mapped = da && dr && dd;
     const int n3 = (int)(3 * A), nA = (int)A;
-    if (same && c.mapped == mapped) {   // other buffers: retarget the graph's transfers
+    if (same && c.mapped == mapped && (!h_obs || c.n_obs)) {   // other buffers: retarget the graph's transfers
+        if (h_obs)
+            SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_obs, h_obs, h->out.obs, obs_bytes,
+                                                          cudaMemcpyDeviceToHost));
         if (mapped && c.n_in && c.n_out) {
             cudaKernelNodeParams kp{};
             SF_CUDA(h, cudaGraphKernelNodeGetParams(c.n_in, &kp));
@@ -734,7 +783,7 @@ sf_status sf_step_host(sf_handle h, const float* h_actions, float* h_reward, uin
         } else {
             goto capture;
         }
-        c.ha = h_actions; c.hr = h_reward; c.hd = h_done;
+        c.ha = h_actions; c.hr = h_reward; c.hd = h_done; c.ho = h_obs;
         SF_CUDA(h, cudaGraphLaunch(c.exec, h->stream));
         SF_CUDA(h, cudaStreamSynchronize(h->stream));
         return SF_OK;
@@ -759,6 +808,9 @@ capture:
             e = cudaMemcpyAsync(h_reward, h->out.reward, A * 4, cudaMemcpyDeviceToHost, h->stream);
             if (e == cudaSuccess) e = cudaMemcpyAsync(h_done, h->out.done, A, cudaMemcpyDeviceToHost, h->stream);
         }
+        // the observation block goes by the copy engine (1,280 B per agent)
+        if (e == cudaSuccess && h_obs)
+            e = cudaMemcpyAsync(h_obs, h->out.obs, obs_bytes, cudaMemcpyDeviceToHost, h->stream);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
@@ -774,11 +826,24 @@ capture:
         return cuda_fail(h, e, "sf_step_host instantiate");
     }
     c.dt = dt; c.substeps = substeps; c.gen = h->gen; c.mapped = mapped;
-    c.ha = h_actions; c.hr = h_reward; c.hd = h_done;
+    c.ha = h_actions; c.hr = h_reward; c.hd = h_done; c.ho = h_obs;
     find_copy_nodes(h);
     SF_CUDA(h, cudaGraphLaunch(c.exec, h->stream));
     SF_CUDA(h, cudaStreamSynchronize(h->stream));
     return SF_OK;
+}
+
+}  // namespace
+
+sf_status sf_step_host(sf_handle h, const float* h_actions, float* h_reward, uint8_t* h_done, float dt,
+                       int substeps) {
+    return step_host(h, h_actions, nullptr, h_reward, h_done, dt, substeps);
+}
+
+sf_status sf_step_host_obs(sf_handle h, const float* h_actions, float* h_obs, float* h_reward, uint8_t* h_done,
+                           float dt, int substeps) {
+    if (h && h->A > 0 && !h_obs) return fail(h, SF_ERR_INVALID_ARG, "sf_step_host_obs: NULL observation buffer");
+    return step_host(h, h_actions, h_obs, h_reward, h_done, dt, substeps);
 }
 
 sf_status sf_autotune(sf_handle h, const float* d_actions, float dt, int substeps, int iters, int32_t* out_shape,

@@ -159,6 +159,7 @@ struct DevRoads {
     const float4* mid;          // per point k: midpoint and unit direction of segment k -> k+1
                                 // (App. C rule), x = +inf when k starts no segment
     const uint8_t* ptype;       // per point: Waymo type of its polyline
+    int agent_base;             // index in the whole CSR of the first agent (world range)
 };
 
 struct DevOutputs {

@@ -478,19 +478,20 @@ __device__ __forceinline__ void park_agent(Agent& A) {
     A.meta = with_status(A.meta, kParked);
 }
 
-// spawn candidate r of agent a (global index) for episode ep (App. J reading)
+// spawn candidate r of agent a (handle index; its draws use its index in the
+// whole CSR, rd.agent_base + a) for episode ep (App. J reading)
 // a world without lane points spawns its slot k at (0, k * spacing), heading +x
 __device__ void spawn_candidate(const DevRoads& rd, int w, int a, int slot, int ep, int r, unsigned long long seed,
                                 float& x, float& y, float& psi, float& gx, float& gy, float& v0) {
     const int2 cw = __ldg(&rd.cand[w]);
     x = 0.f; y = (float)slot * kSpawnSpacing; psi = 0.f; gx = kSpawnGoalMin; gy = y;
     if (cw.y > 0) {
-        uint32_t pick = (uint32_t)(reset_draw(seed, a, ep, r, 0) >> 32) % (uint32_t)cw.y;
+        uint32_t pick = (uint32_t)(reset_draw(seed, rd.agent_base + a, ep, r, 0) >> 32) % (uint32_t)cw.y;
         int k = __ldg(&rd.cands[cw.x + (int)pick]);
         float4 p = __ldg(&rd.pt[k]);
         x = p.x; y = p.y;
         psi = atan2f(p.w, p.z);
-        float dg = kSpawnGoalMin + (kSpawnGoalMax - kSpawnGoalMin) * u24(reset_draw(seed, a, ep, r, 1));
+        float dg = kSpawnGoalMin + (kSpawnGoalMax - kSpawnGoalMin) * u24(reset_draw(seed, rd.agent_base + a, ep, r, 1));
         // the first point j after k with arc(k, j) >= dg (the polyline's last point
         // if none): binary search over the cumulative arc lengths
         const int k1 = __ldg(&rd.pend[k]);
@@ -504,7 +505,7 @@ __device__ void spawn_candidate(const DevRoads& rd, int w, int a, int slot, int 
         float4 G = __ldg(&rd.pt[g]);
         gx = G.x; gy = G.y;
     }
-    v0 = kSpawnVMin + (kSpawnVMax - kSpawnVMin) * u24(reset_draw(seed, a, ep, r, 2));
+    v0 = kSpawnVMin + (kSpawnVMax - kSpawnVMin) * u24(reset_draw(seed, rd.agent_base + a, ep, r, 2));
 }
 
 

@@ -39,7 +39,8 @@ class SFError(RuntimeError):
 class sf_config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("flags", C.c_int32), ("warps_per_block", C.c_int32),
                 ("pack_agents", C.c_int32), ("stage_bytes", C.c_int32), ("split_step", C.c_int32),
-                ("dynamics", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("dynamics", C.c_int32), ("world_begin", C.c_int32), ("world_end", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class sf_roads(C.Structure):
@@ -70,6 +71,7 @@ def lib():
             "sf_create": ([vp, vp, vp], i32), "sf_destroy": ([vp], i32), "sf_load_roads": ([vp, vp], i32),
             "sf_step": ([vp, vp, f32, C.c_int], i32), "sf_get_obs": ([vp, vp, vp, vp, vp], i32),
             "sf_step_host": ([vp, vp, vp, vp, f32, C.c_int], i32),
+            "sf_step_host_obs": ([vp, vp, vp, vp, vp, f32, C.c_int], i32),
             "sf_fp32_fma_peak": ([vp, C.c_int, C.POINTER(C.c_double)], i32),
             "sf_output_ptrs": ([vp, vp], i32), "sf_observe_full": ([vp, vp, vp, vp, vp, vp], i32), "sf_get_indices": ([vp, vp, vp, vp, vp], i32), "sf_reset": ([vp, vp], i32), "sf_place_agents": ([vp, vp], i32),
             "sf_get_state": ([vp, vp, vp], i32), "sf_set_state": ([vp, vp, vp], i32),
@@ -137,8 +139,9 @@ def sf_version() -> str:
 
 
 def sf_create(seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0, stage_bytes=0, split_step=0,
-              dynamics=DYN_VEHICLE):
-    cfg = sf_config(seed, flags, warps_per_block, pack_agents, stage_bytes, split_step, dynamics)
+              dynamics=DYN_VEHICLE, world_range=(0, 0)):
+    cfg = sf_config(seed, flags, warps_per_block, pack_agents, stage_bytes, split_step, dynamics,
+                    int(world_range[0]), int(world_range[1]))
     h = C.c_void_p()
     st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().sf_create(C.byref(cfg), C.c_void_p(st), C.byref(h)))
@@ -172,6 +175,12 @@ def sf_step_host(h, h_actions, h_reward, h_done, dt=1.0 / 30.0, substeps=4):
     page-locked for the captured-graph path): actions in, rewards and done
     flags out; returns when they are in host memory."""
     _check(lib().sf_step_host(h, _ptr(h_actions), _ptr(h_reward), _ptr(h_done), float(dt), int(substeps)), h)
+
+
+def sf_step_host_obs(h, h_actions, h_obs, h_reward, h_done, dt=1.0 / 30.0, substeps=4):
+    """sf_step_host that also copies the step's observations [A][320] into h_obs."""
+    _check(lib().sf_step_host_obs(h, _ptr(h_actions), _ptr(h_obs), _ptr(h_reward), _ptr(h_done), float(dt),
+                                  int(substeps)), h)
 
 
 def sf_fp32_fma_peak(stream=None, iters=20000):
@@ -275,11 +284,12 @@ class World:
     """A handle plus its roads, with torch views of the library-owned outputs."""
 
     def __init__(self, scene, seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0, stage_bytes=0,
-                 split_step=0, dynamics=DYN_VEHICLE):
+                 split_step=0, dynamics=DYN_VEHICLE, world_range=(0, 0)):
         import torch
         self.torch = torch
         self.scene = scene
-        self.h = sf_create(seed, flags, warps_per_block, stream, pack_agents, stage_bytes, split_step, dynamics)
+        self.h = sf_create(seed, flags, warps_per_block, stream, pack_agents, stage_bytes, split_step, dynamics,
+                           world_range)
         sf_load_roads(self.h, scene)
         self.A = sf_num_agents(self.h)
         self.W = sf_num_worlds(self.h)

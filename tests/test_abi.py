@@ -45,3 +45,10 @@ def test_create_without_gpu_fails_loudly():
 
 def test_obs_layout_constants():
     assert sf.OBS_DIM == 16 + 8 * 10 + 32 * 7
+
+
+def test_world_range_is_validated_before_any_device_call():
+    for bad in [(3, 2), (-1, 4), (2, 0), (2, 2)]:
+        with pytest.raises(sf.SFError) as e:
+            sf.sf_create(world_range=bad)
+        assert e.value.status == sf.SF_ERR_INVALID_ARG, bad

@@ -129,7 +129,7 @@ def test_full_observation_parity(name):
     print("full observation near-ties:", ties, "capped rows:", capped)
     if name == "dense":
         assert capped > 0            # the 350-slot cap was exercised
-    assert ties["road"] + ties["veh"] <= 0.01 * 12 * W.A + 2 and ties["ttc"] <= 4
+    assert ties["road"] + ties["veh"] <= 4 and ties["ttc"] <= 4      # observed: at most 2 and 2
     W.close()
 
 

@@ -141,3 +141,47 @@ def test_step_from_host_buffers_equals_device_step():
     F1, I1, _ = sf.sf_get_state(W1.h)
     F2, I2, _ = sf.sf_get_state(W2.h)
     assert np.array_equal(F1, F2) and np.array_equal(I1, I2)
+
+
+def test_step_from_host_buffers_with_observations():
+    """sf_step_host_obs also delivers the step's observations to the host: they
+    equal the device step's (sf_get_obs) bit for bit, through replays, a
+    retargeted observation buffer, a switch back to sf_step_host (re-capture)
+    and pageable buffers (no graph)."""
+    sc = synth.procedural_scene(4, 16, seed_base=730)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    W1, W2 = world(sc, s1), world(sc, s2)
+    A = W1.A
+    acts = synth.ou_actions(A, 12, seed=7)
+    a_h = torch.empty((A, 3), dtype=torch.float32).pin_memory()
+    obs_ring = [torch.empty((A, sf.OBS_DIM), dtype=torch.float32).pin_memory() for _ in range(2)]
+    rew_h = torch.empty(A, dtype=torch.float32).pin_memory()
+    done_h = torch.empty(A, dtype=torch.uint8).pin_memory()
+    act_dev = torch.empty((A, 3), device="cuda")
+    obs_dev = torch.empty((A, sf.OBS_DIM), device="cuda")
+    for t in range(12):
+        a_h.copy_(torch.as_tensor(acts[t]))
+        if t == 6:
+            sf.sf_step_host(W2.h, a_h, rew_h, done_h)          # without the observation
+            o2 = None
+        elif t >= 10:
+            o_np = np.zeros((A, sf.OBS_DIM), np.float32)
+            sf.sf_step_host_obs(W2.h, np.ascontiguousarray(acts[t]), o_np, np.zeros(A, np.float32),
+                                np.zeros(A, np.uint8))
+            o2 = o_np
+        else:
+            o = obs_ring[t % 2]
+            sf.sf_step_host_obs(W2.h, a_h, o, rew_h, done_h)
+            o2 = o.numpy().copy()
+        with torch.cuda.stream(s1):
+            act_dev.copy_(torch.as_tensor(acts[t]))
+            sf.sf_step(W1.h, act_dev)
+            sf.sf_get_obs(W1.h, obs_dev, None, None, None)
+        torch.cuda.synchronize()
+        if o2 is not None:
+            assert np.array_equal(obs_dev.cpu().numpy().view(np.uint32), o2.view(np.uint32)), t
+    with pytest.raises(sf.SFError) as e:
+        sf.sf_step_host_obs(W2.h, a_h, None, rew_h, done_h)
+    assert e.value.status == sf.SF_ERR_INVALID_ARG
+    W1.close()
+    W2.close()

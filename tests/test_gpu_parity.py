@@ -276,7 +276,10 @@ def test_discrete_and_observation_parity(flags, pack, stage, split):
                     ties["ttc"] += 1
             obs_rows += 1
     print("near-ties counted:", ties, "event rows checked:", checked, "observation rows checked:", obs_rows)
-    assert ties["lane"] + ties["knn_pts"] + ties["knn_agents"] <= 4
+    # respawned agents sit exactly on a lane point: a vertex shared by two lane
+    # segments and points spaced evenly along the polyline tie exactly (7 of
+    # ~2,900 rows with auto-reset); the runs are deterministic
+    assert ties["lane"] + ties["knn_pts"] + ties["knn_agents"] <= 12
     assert ties["ttc"] <= 4 and ties["events"] <= 4
 
 
@@ -447,6 +450,44 @@ def test_world_packing_is_bitwise_invisible(nw):
                     bad = np.argwhere(~((a[k] == b[k]) | (np.isnan(a[k]) & np.isnan(b[k]))))
                     r = tuple(bad[0])
                     raise AssertionError((pack, stage, split, t, k, len(bad), r, a[k][r], b[k][r]))
+
+
+def test_world_range_shards_bit_identically():
+    """Worlds are independent, so handles over disjoint world ranges of one CSR
+    (one per GPU when sharded) evolve bit-identically to the same worlds of a
+    handle over all of them, respawns under auto-reset and masked resets
+    included: the respawn draws use the agent's index in the whole CSR."""
+    sc = synth.procedural_scene(8, 16, seed_base=1600)
+    A = sc.num_agents
+    acts = synth.ou_actions(A, 20, seed=3)
+    full = sf.World(sc, seed=5, flags=sf.FLAG_AUTO_RESET)
+    ranges = [(0, 3), (3, 8)]
+    parts = [sf.World(sc, seed=5, flags=sf.FLAG_AUTO_RESET, world_range=r) for r in ranges]
+    rows = [slice(int(sc.agent_off[w0]), int(sc.agent_off[w1])) for w0, w1 in ranges]
+    assert [P.A for P in parts] == [r.stop - r.start for r in rows] and parts[0].W == 3
+    spawn_all(full)
+    for P in parts:
+        spawn_all(P)
+    for t in range(20):
+        sf.sf_step(full.h, dev(acts[t]))
+        for P, r in zip(parts, rows):
+            sf.sf_step(P.h, dev(acts[t][r]))
+        if t % 5 == 4:
+            m = synth.reset_mask(A, t, 0.3, seed=7)
+            sf.sf_reset(full.h, dev(m))
+            for P, r in zip(parts, rows):
+                sf.sf_reset(P.h, dev(m[r]))
+    F, I, _ = sf.sf_get_state(full.h)
+    out = [x.cpu().numpy() for x in full.outputs()]
+    assert (I[:, O.I_EPISODE] > 1).any()                    # respawns happened
+    for P, r in zip(parts, rows):
+        Fp, Ip, _ = sf.sf_get_state(P.h)
+        assert np.array_equal(F[r].view(np.uint32), Fp.view(np.uint32))
+        assert np.array_equal(I[r], Ip)
+        for a, b in zip(out, [x.cpu().numpy() for x in P.outputs()]):
+            assert np.array_equal(a[r].view(np.uint8), b.view(np.uint8))
+        P.close()
+    full.close()
 
 
 def test_invalid_roads_rejected():
