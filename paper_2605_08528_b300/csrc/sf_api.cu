@@ -551,7 +551,12 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     float4* dmid; uint8_t* dptype;
     SF_ALLOC(dmid, float4, (size_t)NP + 1);
     SF_ALLOC(dptype, uint8_t, (size_t)NP + 1);
-    h->rd = DevRoads{dworld, dcand, dpt, dpend, darc, dcands, dgrid, dblob, dmid, dptype, agent_base};
+    // spawn table (one entry per spawn candidate) and each candidate's world, for its build
+    const int ncand = (int)cands.size();
+    SpawnQ* dspawnq; int32_t* dcand_world;
+    SF_ALLOC(dspawnq, SpawnQ, (size_t)ncand + 1);
+    SF_ALLOC(dcand_world, int32_t, (size_t)ncand + 1);
+    h->rd = DevRoads{dworld, dcand, dpt, dpend, darc, dcands, dgrid, dblob, dmid, dptype, agent_base, dspawnq};
     float *obs, *reward, *drac; uint8_t* done; uint32_t* events; int32_t *lane_seg, *knn_pts, *knn_agents;
     unsigned int* err_word; float* hint;
     SF_ALLOC(obs, float, Aa * SF_OBS_DIM);
@@ -627,6 +632,13 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     if (e == cudaSuccess && Aa) e = cudaMemset(h->all_mask, 1, Aa);
     for (size_t i = 0; i < h->packsets.size(); ++i)
         up(h->packsets[i].d, pack_host[i].data(), pack_host[i].size() * sizeof(int4));
+    // the spawn table: the road answers at every spawn candidate, by the step's exact queries
+    std::vector<int32_t> cand_world(ncand);
+    for (int w = 0; w < W; ++w)
+        for (int k = cand[w].x; k < cand[w].x + cand[w].y; ++k) cand_world[k] = w;
+    up(dcand_world, cand_world.data(), (size_t)ncand * 4);
+    if (e == cudaSuccess) e = sf_launch_spawn_table(h->rd, dcand_world, ncand, dspawnq, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) { free_all(h); return cuda_fail(h, e, "sf_load_roads upload"); }
     h->W = W; h->A = A; h->NP = NP;
     h->loaded = true;

@@ -147,6 +147,19 @@ struct DevGrid {
 };
 
 // Road store of all worlds.
+// Road answers at one spawn candidate (a lane point), computed once when the
+// roads are loaded by the step's own exact queries: a respawned agent stands
+// exactly on its candidate, so its nearest lane and 32 nearest road points
+// are these, and no query runs at respawn time.
+struct SpawnQ {
+    uint16_t pos[32];            // sorted record positions of the 32 nearest points (0xFFFF: none)
+    int seg;                     // nearest lane segment (input index), -1 none
+    float dist, lat, tx, ty;     // its distance; lateral offset and tangent before the goal orientation
+    float d32;                   // distance of the 32nd point (0: fewer than 32)
+    int pad[2];
+};
+static_assert(sizeof(SpawnQ) == 96, "spawn table entry layout");
+
 struct DevRoads {
     const int4* world;          // (first agent, agent count, first point, point count)
     const int2* cand;           // (first spawn candidate, candidate count)
@@ -160,6 +173,7 @@ struct DevRoads {
                                 // (App. C rule), x = +inf when k starts no segment
     const uint8_t* ptype;       // per point: Waymo type of its polyline
     int agent_base;             // index in the whole CSR of the first agent (world range)
+    const SpawnQ* spawnq;       // per spawn candidate (indexed like cands), null: none built
 };
 
 struct DevOutputs {
@@ -246,6 +260,9 @@ struct FullObsArgs {
 };
 
 // launch wrappers (sf_world.cu)
+// the spawn table: one entry per spawn candidate c of rd.cands (its world cand_world[c])
+cudaError_t sf_launch_spawn_table(const DevRoads& rd, const int32_t* cand_world, int ncand, SpawnQ* out,
+                                  cudaStream_t s);
 cudaError_t sf_launch_full_obs(const FullObsArgs& f, cudaStream_t s);
 cudaError_t sf_launch_world(int mode, const WorldArgs& a, int warps_per_block, cudaStream_t s);
 // one control step as four kernels (physics, road queries, events, fix-up); nwq warps per query block

@@ -68,11 +68,6 @@ __device__ __forceinline__ unsigned long long reset_draw(unsigned long long seed
 }
 __device__ __forceinline__ float u24(unsigned long long h) { return (float)(uint32_t)(h >> 40) * (1.0f / 16777216.0f); }
 
-__device__ __forceinline__ float warp_min(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
 
 __device__ __forceinline__ void quat_to_mat(float w, float x, float y, float z, float R[3][3]) {
     R[0][0] = 1.f - 2.f * (y * y + z * z); R[0][1] = 2.f * (x * y - w * z);       R[0][2] = 2.f * (x * z + w * y);
@@ -84,8 +79,13 @@ __device__ __forceinline__ void quat_to_mat(float w, float x, float y, float z, 
 __device__ __forceinline__ void heading_of(float qw, float qx, float qy, float qz, float& hx, float& hy) {
     float r00 = 1.f - 2.f * (qy * qy + qz * qz);
     float r10 = 2.f * (qx * qy + qw * qz);
-    float n = sqrtf(r00 * r00 + r10 * r10);
-    if (n > 0.f) { hx = r00 / n; hy = r10 / n; } else { hx = 1.f; hy = 0.f; }
+    const float n2 = norm2(r00, r10);
+    if (n2 > 0.f) {
+        const float rn = rsqrtf(n2);
+        hx = __fmul_rn(r00, rn); hy = __fmul_rn(r10, rn);
+    } else {
+        hx = 1.f; hy = 0.f;
+    }
 }
 
 __device__ __forceinline__ void to_ego(float hx, float hy, float x, float y, float& bx, float& by) {
@@ -165,18 +165,17 @@ __device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, f
     // 1. steering
     steer_substep(A, dstar, h);
 
-    // 2. rotation, world inverse inertia (symmetric), world inertia
+    // 2. rotation, world inverse inertia (symmetric)
     float R[3][3];
     quat_to_mat(A.qw, A.qx, A.qy, A.qz, R);
-    float Ii[3][3], Iw[3][3];
+    float Ii[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
+        for (int b = 0; b < 3; ++b)
             Ii[a][b] = R[a][0] * R[b][0] * kInvIxx + R[a][1] * R[b][1] * kInvIyy + R[a][2] * R[b][2] * kInvIzz;
-            Iw[a][b] = R[a][0] * R[b][0] * kIxx + R[a][1] * R[b][1] * kIyy + R[a][2] * R[b][2] * kIzz;
-        }
     const float ux = R[0][2], uy = R[1][2], uz = R[2][2];
+    const float inv_uz = uz > kUzMin ? 1.f / uz : 0.f;   // shared by the four rays
 
     // 3. suspension rays from the hardpoints along -u to the plane z = 0
     float N[4], rcx[4], rcy[4], rcz[4];
@@ -191,12 +190,12 @@ __device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, f
         N[i] = 0.f; rcx[i] = rcy[i] = rcz[i] = 0.f;
         if (uz > kUzMin) {
             float az = (A.pz + A.dpz) + rbz;
-            float t = az / uz;
+            float t = __fmul_rn(az, inv_uz);              // rounded on its own (never fused)
             float l = t - kWheelR;
             if (l < kRest) {
                 float x = kRest - fmaxf(l, 0.f);
                 float wrz = A.wx * rby - A.wy * rbx;            // (w x rb).z
-                float xdot = -(A.vz + wrz) / uz;
+                float xdot = __fmul_rn(-(A.vz + wrz), inv_uz);
                 // the damper engages over the first kDampRamp of compression:
                 // the normal force is continuous at touchdown
                 N[i] = fmaxf(0.f, kKSusp * x + kCSusp * xdot * fminf(1.f, x / kDampRamp));
@@ -214,9 +213,18 @@ __device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, f
         Tx += rcy[i] * N[i];
         Ty -= rcx[i] * N[i];
     }
-    float Lx = Iw[0][0] * A.wx + Iw[0][1] * A.wy + Iw[0][2] * A.wz;
-    float Ly = Iw[1][0] * A.wx + Iw[1][1] * A.wy + Iw[1][2] * A.wz;
-    float Lz = Iw[2][0] * A.wx + Iw[2][1] * A.wy + Iw[2][2] * A.wz;
+    // angular momentum L = R I R^T w, through the body frame (each sum in one fixed
+    // rounding order, so that every kernel inlining this step rounds it alike)
+    auto dot3 = [](float a0, float b0, float a1, float b1, float a2, float b2) {
+        return __fmaf_rn(a2, b2, __fmaf_rn(a1, b1, __fmul_rn(a0, b0)));
+    };
+    const float wbx = dot3(R[0][0], A.wx, R[1][0], A.wy, R[2][0], A.wz);
+    const float wby = dot3(R[0][1], A.wx, R[1][1], A.wy, R[2][1], A.wz);
+    const float wbz = dot3(R[0][2], A.wx, R[1][2], A.wy, R[2][2], A.wz);
+    const float lbx = __fmul_rn(kIxx, wbx), lby = __fmul_rn(kIyy, wby), lbz = __fmul_rn(kIzz, wbz);
+    float Lx = dot3(R[0][0], lbx, R[0][1], lby, R[0][2], lbz);
+    float Ly = dot3(R[1][0], lbx, R[1][1], lby, R[1][2], lbz);
+    float Lz = dot3(R[2][0], lbx, R[2][1], lby, R[2][2], lbz);
     float nx_ = Tx - (A.wy * Lz - A.wz * Ly);
     float ny_ = Ty - (A.wz * Lx - A.wx * Lz);
     float nz_ = Tz - (A.wx * Ly - A.wy * Lx);
@@ -242,9 +250,10 @@ __device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, f
         const float c = i < 2 ? cd : 1.f, s = i < 2 ? sd : 0.f;
         float fwx = R[0][0] * c + R[0][1] * s;
         float fwy = R[1][0] * c + R[1][1] * s;
-        float fl = sqrtf(fwx * fwx + fwy * fwy);
-        if (!(fl > 0.f)) continue;
-        float elx = fwx / fl, ely = fwy / fl;
+        const float fl2 = norm2(fwx, fwy);
+        if (!(fl2 > 0.f)) continue;
+        const float rfl = rsqrtf(fl2);
+        float elx = __fmul_rn(fwx, rfl), ely = __fmul_rn(fwy, rfl);
         float etx = -ely, ety = elx;
         float vcx = v1x + (w1y * rcz[i] - w1z * rcy[i]);
         float vcy = v1y + (w1z * rcx[i] - w1x * rcz[i]);
@@ -263,8 +272,8 @@ __device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, f
         float ut = -(vcx * etx + vcy * ety);
         float jl = ul / wl, jt = ut / wt;
         float cap = A.mu * N[i] * h;
-        float jn = sqrtf(jl * jl + jt * jt);
-        float sc = jn <= cap ? 1.f : cap / jn;
+        const float j2 = norm2(jl, jt);
+        float sc = j2 <= __fmul_rn(cap, cap) ? 1.f : __fmul_rn(cap, rsqrtf(j2));   // friction circle
         jl *= sc; jt *= sc;
         float Jx = jl * elx + jt * etx, Jy = jl * ely + jt * ety;
         Px += Jx; Py += Jy;
@@ -295,8 +304,8 @@ __device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, f
     float dqy = w1y * qw + (w1z * qx - w1x * qz);
     float dqz = w1z * qw + (w1x * qy - w1y * qx);
     qw += 0.5f * h * dqw; qx += 0.5f * h * dqx; qy += 0.5f * h * dqy; qz += 0.5f * h * dqz;
-    float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-    A.qw = qw / qn; A.qx = qx / qn; A.qy = qy / qn; A.qz = qz / qn;
+    const float rq = rsqrtf(__fmaf_rn(qz, qz, __fmaf_rn(qy, qy, __fmaf_rn(qx, qx, __fmul_rn(qw, qw)))));
+    A.qw = __fmul_rn(qw, rq); A.qx = __fmul_rn(qx, rq); A.qy = __fmul_rn(qy, rq); A.qz = __fmul_rn(qz, rq);
     A.vx = v1x; A.vy = v1y; A.vz = v1z;
     A.wx = w1x; A.wy = w1y; A.wz = w1z;
 }
@@ -481,13 +490,16 @@ __device__ __forceinline__ void park_agent(Agent& A) {
 // spawn candidate r of agent a (handle index; its draws use its index in the
 // whole CSR, rd.agent_base + a) for episode ep (App. J reading)
 // a world without lane points spawns its slot k at (0, k * spacing), heading +x
+// (cslot: the candidate's index in rd.cands, -1 for the fallback)
 __device__ void spawn_candidate(const DevRoads& rd, int w, int a, int slot, int ep, int r, unsigned long long seed,
-                                float& x, float& y, float& psi, float& gx, float& gy, float& v0) {
+                                float& x, float& y, float& psi, float& gx, float& gy, float& v0, int& cslot) {
     const int2 cw = __ldg(&rd.cand[w]);
     x = 0.f; y = (float)slot * kSpawnSpacing; psi = 0.f; gx = kSpawnGoalMin; gy = y;
+    cslot = -1;
     if (cw.y > 0) {
         uint32_t pick = (uint32_t)(reset_draw(seed, rd.agent_base + a, ep, r, 0) >> 32) % (uint32_t)cw.y;
-        int k = __ldg(&rd.cands[cw.x + (int)pick]);
+        cslot = cw.x + (int)pick;
+        int k = __ldg(&rd.cands[cslot]);
         float4 p = __ldg(&rd.pt[k]);
         x = p.x; y = p.y;
         psi = atan2f(p.w, p.z);
@@ -529,10 +541,12 @@ __device__ __forceinline__ unsigned long long shfl_xor64(unsigned long long v, i
     unsigned lo = __shfl_xor_sync(kFull, (unsigned)v, m), hi = __shfl_xor_sync(kFull, (unsigned)(v >> 32), m);
     return ((unsigned long long)hi << 32) | lo;
 }
+// the warp's smallest 64-bit value: the smallest high word, then the smallest
+// low word among the lanes holding it (two warp reductions)
 __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = umin64(v, shfl_xor64(v, o));
-    return v;
+    const unsigned hi = __reduce_min_sync(kFull, (unsigned)(v >> 32));
+    const unsigned lo = __reduce_min_sync(kFull, (unsigned)(v >> 32) == hi ? (unsigned)v : 0xFFFFFFFFu);
+    return ((unsigned long long)hi << 32) | lo;
 }
 // bitonic sort of one key per lane, ascending with the lane index
 __device__ __forceinline__ unsigned long long warp_sort32(unsigned long long v, int lane) {
@@ -546,16 +560,26 @@ __device__ __forceinline__ unsigned long long warp_sort32(unsigned long long v, 
         }
     return v;
 }
-// merge a sorted running top-32 with 32 new (unsorted) candidates; returns the 32 smallest, sorted
-__device__ __forceinline__ unsigned long long merge32(unsigned long long run, unsigned long long cand, int lane) {
-    cand = warp_sort32(cand, lane);
-    unsigned long long m = umin64(run, shfl64(cand, 31 - lane));   // bitonic, holds the 32 smallest
-#pragma unroll
-    for (int j = 16; j > 0; j >>= 1) {
-        unsigned long long o = shfl_xor64(m, j);
-        m = (lane & j) == 0 ? umin64(m, o) : umax64(m, o);
+// The smallest 32 of the unique keys buf[0, cnt), cnt <= 64, by rank: a key's
+// rank is the number of held keys below it, and the keys of rank < 32 are
+// written back to buf at their rank, so buf[0, min(cnt, 32)) ends ascending.
+// Every lane ranks its (at most two) keys against all of them (broadcast
+// reads, no shuffles).  Returns min(cnt, 32).
+__device__ __forceinline__ int rank_keep32(unsigned long long* buf, int cnt, int lane) {
+    const unsigned long long k0 = lane < cnt ? buf[lane] : kKeyInf;
+    const unsigned long long k1 = lane + 32 < cnt ? buf[lane + 32] : kKeyInf;
+    int r0 = 0, r1 = 0;
+#pragma unroll 4
+    for (int i = 0; i < cnt; ++i) {
+        const unsigned long long k = buf[i];
+        r0 += k < k0 ? 1 : 0;
+        r1 += k < k1 ? 1 : 0;
     }
-    return m;
+    __syncwarp();
+    if (lane < cnt && r0 < 32) buf[r0] = k0;
+    if (lane + 32 < cnt && r1 < 32) buf[r1] = k1;
+    __syncwarp();
+    return cnt < 32 ? cnt : 32;
 }
 
 // One world's road blob as the queries see it: in shared memory when the
@@ -684,18 +708,27 @@ __device__ __forceinline__ unsigned long long warp_min_rec(unsigned long long k,
 }
 
 // tangent, lateral offset and distance of the nearest lane segment from its
-// key and its record r = (a, b)
-__device__ __forceinline__ Lane lane_of(const WRoads& v, unsigned long long best, const float4& r, float qx, float qy,
-                                        float gx, float gy) {
+// key and its record r = (a, b), before the orientation toward the goal
+__device__ __forceinline__ Lane lane_raw_of(const WRoads& v, unsigned long long best, const float4& r, float qx,
+                                            float qy) {
     Lane L;
     if (best == kKeyInf) { L.seg = -1; L.dist = kInf; L.lat = 0.f; L.tx = L.ty = 0.f; return L; }
     L.seg = v.q0 + rkey_local(best);
-    float ex = r.z - r.x, ey = r.w - r.y;
-    float nn = sqrtf(ex * ex + ey * ey);
-    float tx = ex / nn, ty = ey / nn;
-    float lat = cross2(tx, ty, qx - r.x, qy - r.y);
-    if (dot2(tx, gx - qx, ty, gy - qy) < 0.f) { tx = -tx; ty = -ty; lat = -lat; }
-    L.dist = sqrtf(key_d2(best)); L.lat = lat; L.tx = tx; L.ty = ty;
+    const float ex = r.z - r.x, ey = r.w - r.y;
+    const float nn = sqrtf(norm2(ex, ey));
+    L.tx = ex / nn; L.ty = ey / nn;
+    L.lat = cross2(L.tx, L.ty, qx - r.x, qy - r.y);
+    L.dist = sqrtf(key_d2(best));
+    return L;
+}
+// the tangent oriented toward the goal g (App. G), the lateral offset's sign following it
+__device__ __forceinline__ void lane_orient(Lane& L, float qx, float qy, float gx, float gy) {
+    if (L.seg >= 0 && dot2(L.tx, gx - qx, L.ty, gy - qy) < 0.f) { L.tx = -L.tx; L.ty = -L.ty; L.lat = -L.lat; }
+}
+__device__ __forceinline__ Lane lane_of(const WRoads& v, unsigned long long best, const float4& r, float qx, float qy,
+                                        float gx, float gy) {
+    Lane L = lane_raw_of(v, best, r, qx, qy);
+    lane_orient(L, qx, qy, gx, gy);
     return L;
 }
 
@@ -724,8 +757,8 @@ __device__ __forceinline__ bool forb_touch(const float4& sg, float d0, float qx,
 // same scan runs the lane-forbidden test of the footprint's three circles
 // against the road-edge segments (App. G) when `forb` is given: the square
 // then also covers every edge segment that can touch a circle.
-__device__ Lane coop_nearest_lane(const WRoads& v, float qx, float qy, float gx, float gy, float R, int lane,
-                                  bool* forb = nullptr, float hx = 1.f, float hy = 0.f) {
+__device__ Lane coop_nearest_lane_raw(const WRoads& v, float qx, float qy, float R, int lane, bool* forb = nullptr,
+                                      float hx = 1.f, float hy = 0.f) {
     float S = R + kSegReach;
     if (forb) S = fmaxf(S, kCircD + kCircR + kEdgeHalfWidth + kSegReach);
     bool edges = forb != nullptr, f = false;
@@ -752,27 +785,40 @@ __device__ Lane coop_nearest_lane(const WRoads& v, float qx, float qy, float gx,
         if (best != kKeyInf || w.all) break;
         S = Rl * kGrow + kSegReach;
     }
-    return lane_of(v, best, brec, qx, qy, gx, gy);
+    return lane_raw_of(v, best, brec, qx, qy);
+}
+__device__ __forceinline__ Lane coop_nearest_lane(const WRoads& v, float qx, float qy, float gx, float gy, float R,
+                                                  int lane, bool* forb = nullptr, float hx = 1.f, float hy = 0.f) {
+    Lane L = coop_nearest_lane_raw(v, qx, qy, R, lane, forb, hx, hy);
+    lane_orient(L, qx, qy, gx, gy);
+    return L;
 }
 
-// Candidate keys (kKeyInf: none) of a batch into the warp's buffer; every 32
-// collected are merged into the running 32 smallest, whose largest then tightens
-// the admission threshold.
-__device__ __forceinline__ void collect32(unsigned long long key, int lane, unsigned lt, unsigned long long* buf,
-                                          int& cnt, unsigned long long& run, unsigned long long& thr) {
+// Candidate keys (kKeyInf: none) of a batch are appended to the warp's buffer
+// (64 keys); whenever more than 32 are held, the 32 smallest are kept, and the
+// largest of them tightens the admission threshold (a key at or above it can
+// no longer be among the 32 nearest).  `sorted` tells whether buf[0, cnt) is
+// the ascending result of a trim with nothing appended since.
+__device__ __forceinline__ void collect_keys(unsigned long long key, int lane, unsigned lt, unsigned long long* buf,
+                                             int& cnt, unsigned long long& thr, bool& sorted) {
     const unsigned mk = __ballot_sync(kFull, key != kKeyInf);
+    if (!mk) return;
     if (key != kKeyInf) buf[cnt + __popc(mk & lt)] = key;
     cnt += __popc(mk);
+    sorted = false;
     __syncwarp();
-    if (cnt >= 32) {
-        run = merge32(run, buf[lane], lane);
-        const unsigned long long rest = lane < cnt - 32 ? buf[32 + lane] : kKeyInf;
-        __syncwarp();
-        if (lane < cnt - 32) buf[lane] = rest;
-        cnt -= 32;
-        thr = umin64(thr, shfl64(run, 31));
-        __syncwarp();
+    if (cnt > 32) {
+        cnt = rank_keep32(buf, cnt, lane);
+        thr = umin64(thr, buf[31]);
+        sorted = true;
     }
+}
+// lane t's key of the t-th smallest held key (kKeyInf past cnt); buf sorted first if needed
+__device__ __forceinline__ unsigned long long held_key(unsigned long long* buf, int& cnt, bool sorted, int lane) {
+    if (!sorted) cnt = rank_keep32(buf, cnt, lane);
+    const unsigned long long k = lane < cnt ? buf[lane] : kKeyInf;
+    __syncwarp();
+    return k;
 }
 
 // the 32 nearest road points (all types), exact; lane t returns the t-th key.
@@ -781,12 +827,11 @@ __device__ __forceinline__ void collect32(unsigned long long key, int lane, unsi
 __device__ unsigned long long coop_knn32(const WRoads& v, float qx, float qy, float R, int lane,
                                          unsigned long long* buf) {
     const unsigned lt = (1u << lane) - 1u;
-    unsigned long long run = kKeyInf;
     for (;;) {
         const Rows w = rows_covering(v, qx, qy, R);
         unsigned long long thr = w.all ? kKeyInf : key_of(R * R * (1.f - 1e-5f), 0);
-        run = kKeyInf;
         int cnt = 0;
+        bool sorted = true;
         scan_cells(v, w, lane, [&](const float4& P, uint32_t m, int i, bool has) {
             unsigned long long key = kKeyInf;
             if (has) {
@@ -794,17 +839,12 @@ __device__ unsigned long long coop_knn32(const WRoads& v, float qx, float qy, fl
                 key = rkey(norm2(dx, dy), m, i);
                 if (key >= thr) key = kKeyInf;
             }
-            collect32(key, lane, lt, buf, cnt, run, thr);
+            collect_keys(key, lane, lt, buf, cnt, thr, sorted);
         });
-        if (cnt > 0) {
-            const unsigned long long c = lane < cnt ? buf[lane] : kKeyInf;
-            run = merge32(run, c, lane);
-        }
-        __syncwarp();
-        if (shfl64(run, 31) != kKeyInf || w.all) break;
+        const unsigned long long run = held_key(buf, cnt, sorted, lane);
+        if (cnt == 32 || w.all) return run;
         R *= kGrow;
     }
-    return run;
 }
 
 // One pass over the cells around q for the three point queries of an agent
@@ -823,9 +863,9 @@ __device__ Lane coop_point_queries(const WRoads& v, float qx, float qy, float gx
     const float Rle = S - kSegReach;                  // every lane segment within Rle is seen
     const float lim_l = w.all ? kInf : Rle * Rle * (1.f - 1e-5f);
     unsigned long long thr = w.all ? kKeyInf : key_of(R32 * R32 * (1.f - 1e-5f), 0);
-    unsigned long long run = kKeyInf, best = kKeyInf;
+    unsigned long long best = kKeyInf;
     float4 brec = make_float4(0.f, 0.f, 0.f, 0.f);
-    bool f = false;
+    bool f = false, sorted = true;
     int cnt = 0;
     scan_cells(v, w, lane, [&](const float4& sg, uint32_t m, int i, bool has) {
         unsigned long long k = kKeyInf;
@@ -843,17 +883,13 @@ __device__ Lane coop_point_queries(const WRoads& v, float qx, float qy, float gx
                 }
             }
         }
-        collect32(k, lane, lt, buf, cnt, run, thr);
+        collect_keys(k, lane, lt, buf, cnt, thr, sorted);
     });
-    if (cnt > 0) {
-        const unsigned long long c = lane < cnt ? buf[lane] : kKeyInf;
-        run = merge32(run, c, lane);
-    }
-    __syncwarp();
+    const unsigned long long run = held_key(buf, cnt, sorted, lane);
     *forb = __any_sync(kFull, f);
     best = warp_min_rec(best, brec);
     // too few points within R32: the 32 nearest alone, from a larger radius
-    *key = (shfl64(run, 31) != kKeyInf || w.all) ? run : coop_knn32(v, qx, qy, R32 * kGrow, lane, buf);
+    *key = (cnt == 32 || w.all) ? run : coop_knn32(v, qx, qy, R32 * kGrow, lane, buf);
     if (best == kKeyInf && !w.all)                   // no lane within Rle: the nearest lane alone
         return coop_nearest_lane(v, qx, qy, gx, gy, Rle * kGrow, lane);
     return lane_of(v, best, brec, qx, qy, gx, gy);
@@ -878,7 +914,7 @@ __device__ float coop_edge_ray(const WRoads& v, float px, float py, float vx, fl
         const float nt = cross2(apx, apy, exx, eyy), ns = cross2(apx, apy, vx, vy);
         const bool ok = den > 0.f ? (nt >= 0.f && ns >= 0.f && ns <= den && speed * nt <= kEdgeHorizon * den)
                                   : (nt <= 0.f && ns <= 0.f && ns >= den && speed * nt >= kEdgeHorizon * den);
-        if (ok) t_best = fminf(t_best, nt / den);
+        if (ok) t_best = fminf(t_best, __fadd_rn(nt / den, 0.f));   // >= 0 (+0 for a zero time)
     };
     // four segments per lane in flight: the loads are issued before the tests
     constexpr int kU = 4;
@@ -891,7 +927,8 @@ __device__ float coop_edge_ray(const WRoads& v, float px, float py, float vx, fl
         for (int u = 0; u < kU; ++u)
             if (i0 + 32 * u < v.ecnt) hit(e[u]);
     }
-    return warp_min(t_best);
+    // times are >= +0 or +inf, ordered like their bit patterns
+    return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(t_best)));
 }
 
 // road-point features of the observation (App. D analogue) from a k-NN key
@@ -1215,22 +1252,23 @@ __host__ __device__ inline int phys_of(const WorldArgs& a) {
 }
 
 template <int PHYS>
+// act: the lane's raw actions (throttle, steer, brake), loaded by the caller
 __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot& c, int lane, Agent& A, bool& alive,
                                               bool& nonfin, float& prevx, float& prevy, float& hx, float& hy,
-                                              Exch& E) {
+                                              Exch& E, float3 act) {
     const DevState& st = args.st;
     const int a = c.a, base = c.base, n = c.n;
     float thr = 0.f, dstar = 0.f, brk = 0.f;
     if (alive) {
-        const float* act = args.actions + 3 * (size_t)a;
-        thr = clampf(act[0], 0.f, 1.f);
-        dstar = kThetaMax * clampf(act[1], -1.f, 1.f);
-        brk = clampf(act[2], 0.f, 1.f);
+        thr = clampf(act.x, 0.f, 1.f);
+        dstar = kThetaMax * clampf(act.y, -1.f, 1.f);
+        brk = clampf(act.z, 0.f, 1.f);
     }
     prevx = A.px; prevy = A.py;
     bool gated = false;
     if (PHYS == kPhysBicycle) {   // the bicycle backend replaces the substeps (no contact response)
-        if (alive) bicycle_step(A, args.actions + 3 * (size_t)a, args.h * args.substeps);
+        const float av[3] = {act.x, act.y, act.z};
+        if (alive) bicycle_step(A, av, args.h * args.substeps);
         if (alive && !finite_agent(A)) {
             nonfin = true;
             park_agent(A);
@@ -1264,6 +1302,7 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
         if (s == 0) {
             E.bud[lane] = budget;
             __syncwarp();
+#pragma unroll 4
             for (int j = base; j < base + n; ++j) {
                 if (j == lane) continue;
                 const float reach = kPairCullR + budget + E.bud[j] + 0.01f;
@@ -1280,48 +1319,53 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
         const uint32_t wmask = (n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u)) << base;
         const uint32_t above = lane < 31 ? (0xFFFFFFFFu << (lane + 1)) : 0u;
         const uint32_t mine = alive ? (cand & above & wmask) : 0u;
-        const int pc = __popc(mine);
-        int poff = pc;
+        // candidate sets are symmetric: with no lane holding a partner above it there
+        // is no pair, and the forces stay +0 (the body step below is the only one,
+        // so its rounding is the same whichever way a substep goes)
+        if (__any_sync(kFull, mine != 0u)) {
+            const int pc = __popc(mine);
+            int poff = pc;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, poff, o);
-            if (lane >= o) poff += t;
-        }
-        const int npairs = __shfl_sync(kFull, poff, 31);
-        poff -= pc;
-        if (npairs <= kMaxPairs) {
-            E.poff[lane] = poff;
-            E.pmask[lane] = mine;
-            for (uint32_t mm = mine, k = (uint32_t)poff; mm; mm &= mm - 1u, ++k) E.plist[k] = (lane << 8) | (__ffs(mm) - 1);
-            __syncwarp();
-            for (int p = lane; p < npairs; p += 32) {
-                const int lo = E.plist[p] >> 8, hi = E.plist[p] & 0xFF;
-                float fx, fy, tz;
-                pair_force(E.px[lo], E.py[lo], E.dx[lo], E.dy[lo], E.hx[lo], E.hy[lo], E.vx[lo], E.vy[lo],
-                           E.px[hi], E.py[hi], E.dx[hi], E.dy[hi], E.hx[hi], E.hy[hi], E.vx[hi], E.vy[hi],
-                           fx, fy, tz);
-                E.pf[p] = make_float4(fx, fy, tz, 0.f);
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, poff, o);
+                if (lane >= o) poff += t;
             }
-            __syncwarp();
-            if (alive) {
+            const int npairs = __shfl_sync(kFull, poff, 31);
+            poff -= pc;
+            if (npairs <= kMaxPairs) {
+                E.poff[lane] = poff;
+                E.pmask[lane] = mine;
+                for (uint32_t mm = mine, k = (uint32_t)poff; mm; mm &= mm - 1u, ++k) E.plist[k] = (lane << 8) | (__ffs(mm) - 1);
+                __syncwarp();
+                for (int p = lane; p < npairs; p += 32) {
+                    const int lo = E.plist[p] >> 8, hi = E.plist[p] & 0xFF;
+                    float fx, fy, tz;
+                    pair_force(E.px[lo], E.py[lo], E.dx[lo], E.dy[lo], E.hx[lo], E.hy[lo], E.vx[lo], E.vy[lo],
+                               E.px[hi], E.py[hi], E.dx[hi], E.dy[hi], E.hx[hi], E.hy[hi], E.vx[hi], E.vy[hi],
+                               fx, fy, tz);
+                    E.pf[p] = make_float4(fx, fy, tz, 0.f);
+                }
+                __syncwarp();
+                if (alive) {
+                    for (uint32_t pm = cand & wmask & ~(1u << lane); pm; pm &= pm - 1u) {   // ascending j
+                        const int j = __ffs(pm) - 1;
+                        const int lo = min(lane, j), hi = max(lane, j);
+                        const float4 f = E.pf[E.poff[lo] + __popc(E.pmask[lo] & ((1u << hi) - 1u))];
+                        if (lane == lo) { fcx -= f.x; fcy -= f.y; } else { fcx += f.x; fcy += f.y; }
+                        tcz += f.z;
+                    }
+                }
+            } else if (alive) {   // many candidates (all pairs of a crowded world): a loop per lane
                 for (uint32_t pm = cand & wmask & ~(1u << lane); pm; pm &= pm - 1u) {   // ascending j
                     const int j = __ffs(pm) - 1;
                     const int lo = min(lane, j), hi = max(lane, j);
-                    const float4 f = E.pf[E.poff[lo] + __popc(E.pmask[lo] & ((1u << hi) - 1u))];
-                    if (lane == lo) { fcx -= f.x; fcy -= f.y; } else { fcx += f.x; fcy += f.y; }
-                    tcz += f.z;
+                    float fx, fy, tz;
+                    pair_force(E.px[lo], E.py[lo], E.dx[lo], E.dy[lo], E.hx[lo], E.hy[lo], E.vx[lo], E.vy[lo],
+                               E.px[hi], E.py[hi], E.dx[hi], E.dy[hi], E.hx[hi], E.hy[hi], E.vx[hi], E.vy[hi],
+                               fx, fy, tz);
+                    if (lane == lo) { fcx -= fx; fcy -= fy; } else { fcx += fx; fcy += fy; }
+                    tcz += tz;
                 }
-            }
-        } else if (alive) {   // many candidates (all pairs of a crowded world): a loop per lane
-            for (uint32_t pm = cand & wmask & ~(1u << lane); pm; pm &= pm - 1u) {   // ascending j
-                const int j = __ffs(pm) - 1;
-                const int lo = min(lane, j), hi = max(lane, j);
-                float fx, fy, tz;
-                pair_force(E.px[lo], E.py[lo], E.dx[lo], E.dy[lo], E.hx[lo], E.hy[lo], E.vx[lo], E.vy[lo],
-                           E.px[hi], E.py[hi], E.dx[hi], E.dy[hi], E.hx[hi], E.hy[hi], E.vx[hi], E.vy[hi],
-                           fx, fy, tz);
-                if (lane == lo) { fcx -= fx; fcy -= fy; } else { fcx += fx; fcy += fy; }
-                tcz += tz;
             }
         }
         __syncwarp();
@@ -1360,21 +1404,6 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
     publish(E, lane, A, hx, hy);
 }
 
-// road queries of the events for one agent (all lanes of a warp): nearest
-// lane with the lane-forbidden test, the edge ray; the lane hint is updated
-__device__ __forceinline__ AgentQ agent_event_queries(const WRoads& v, float px, float py, float gx, float gy,
-                                                      float hx, float hy, float vx, float vy, float* hnt, int lane) {
-    bool forb = false;
-    const Lane L = coop_nearest_lane(v, px, py, gx, gy, hint_radius(hnt, 1, px, py, kLaneR0), lane, &forb, hx, hy);
-    __syncwarp();
-    if (lane == 0) hnt[1] = L.seg >= 0 ? L.dist : 0.f;
-    const float tedge = coop_edge_ray(v, px, py, vx, vy, lane);
-    AgentQ q;
-    q.seg = L.seg; q.dist = L.dist; q.lat = L.lat; q.tx = L.tx; q.ty = L.ty;
-    q.tedge = tedge; q.forb = forb ? 1 : 0; q.need = 0;
-    return q;
-}
-
 // road-point block of one agent's observation (all lanes of a warp).  With
 // `need` (the agent was respawned, or every agent is observed afresh) the
 // nearest lane is first recomputed from radius rlane into *L; the 32 nearest points start from the hinted
@@ -1410,6 +1439,74 @@ __device__ __forceinline__ void agent_road_block(const WRoads& v, bool alive, bo
 #pragma unroll
     for (int k = 0; k < kObsPt; ++k) orow[kObsPt * lane + k] = f[k];
     if (knn_row) knn_row[lane] = key != kKeyInf ? v.q0 + rkey_local(key) : -1;
+}
+
+// The road queries of one alive agent at its end-of-physics pose (all lanes of
+// a warp), in one pass over the cells around it: the nearest lane with the
+// lane-forbidden test (events) and the 32 nearest road points (the
+// observation's road-point block, written to orow, indices to knn_row), then
+// the edge ray; hv holds the agent's hints, which are updated through hnt.
+// Returns the events' answers (every lane).
+__device__ __forceinline__ AgentQ agent_step_queries(const WRoads& v, float px, float py, float gx, float gy, float hx,
+                                                     float hy, float vx, float vy, const float (&hv)[4], float* hnt,
+                                                     int lane, unsigned long long* kbuf, float* orow,
+                                                     int32_t* knn_row) {
+    bool forb = false;
+    unsigned long long key = kKeyInf;
+    const Lane L = coop_point_queries(v, px, py, gx, gy, hx, hy, hint_radius(hv, 0, px, py, kKnnR0),
+                                      hint_radius(hv, 1, px, py, kLaneR0), lane, kbuf, &forb, &key);
+    // the observation's point records are fetched while the edge ray runs
+    float4 prec = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t pm = 0u;
+    if (key != kKeyInf) { prec = v.seg[rkey_pos(key)]; pm = v.info[rkey_pos(key)]; }
+    const float tedge = coop_edge_ray(v, px, py, vx, vy, lane);
+    const unsigned long long last = shfl64(key, 31);
+    __syncwarp();
+    AgentQ q;
+    q.seg = L.seg; q.dist = L.dist; q.lat = L.lat; q.tx = L.tx; q.ty = L.ty;
+    q.tedge = tedge; q.forb = forb ? 1 : 0; q.need = 0;
+    if (lane == 0) {
+        hnt[0] = last != kKeyInf ? sqrtf(key_d2(last)) : 0.f;
+        hnt[1] = L.seg >= 0 ? L.dist : 0.f;
+        hnt[2] = px;
+        hnt[3] = py;
+    }
+    float f[kObsPt] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (key != kKeyInf) point_features_of(prec, pm, hx, hy, px, py, f);
+#pragma unroll
+    for (int k = 0; k < kObsPt; ++k) orow[kObsPt * lane + k] = f[k];
+    if (knn_row) knn_row[lane] = key != kKeyInf ? v.q0 + rkey_local(key) : -1;
+    return q;
+}
+
+// Road-point block and nearest lane (into *L) of an agent standing exactly on
+// the spawn candidate whose spawn-table entry is e (all lanes of a warp): the
+// table holds the answers of the exact queries at that point, so the result
+// equals agent_road_block's there bit for bit; the hints are updated as it
+// would update them.
+__device__ __forceinline__ void spawn_road_block(const SpawnQ* e, const WRoads& v, float px, float py, float gx,
+                                                 float gy, float hx, float hy, float* hnt, int lane, float* orow,
+                                                 int32_t* knn_row, Lane* L) {
+    const int pos = e->pos[lane];
+    Lane l;
+    l.seg = e->seg; l.dist = e->dist; l.lat = e->lat; l.tx = e->tx; l.ty = e->ty;
+    lane_orient(l, px, py, gx, gy);
+    *L = l;
+    if (lane == 0) {
+        hnt[0] = e->d32;
+        hnt[1] = l.seg >= 0 ? l.dist : 0.f;
+        hnt[2] = px;
+        hnt[3] = py;
+    }
+    float f[kObsPt] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    uint32_t m = 0u;
+    if (pos != 0xFFFF) {
+        m = v.info[pos];
+        point_features_of(v.seg[pos], m, hx, hy, px, py, f);
+    }
+#pragma unroll
+    for (int k = 0; k < kObsPt; ++k) orow[kObsPt * lane + k] = f[k];
+    if (knn_row) knn_row[lane] = pos != 0xFFFF ? v.q0 + (int)(m & 0xFFFFu) : -1;
 }
 
 // Neighbour tables of a block: the 8 nearest agents of every slot and, per
@@ -1516,10 +1613,12 @@ __device__ __forceinline__ void lanes_events_b(const WorldArgs& args, const Slot
     }
 }
 
-// spawn candidates (x, y, psi, goal x, goal y, v0) of every try of every slot
-// of a pack for the slot's next episode, drawn ahead of the respawns by threads
-// t = 0..nt-1 (the draws depend on the slot, its episode and the try only)
+// spawn candidates (x, y, psi, goal x, goal y, v0, candidate slot as int bits)
+// of every try of every slot of a pack for the slot's next episode, drawn ahead
+// of the respawns by threads t = 0..nt-1 (the draws depend on the slot, its
+// episode and the try only)
 constexpr int kSpawnDraws = 32 * kSpawnTries;
+constexpr int kSpawnRows = 7;
 constexpr int kSpawnGroup = 4;   // respawning slots whose tries are drawn together (one lane each)
 __device__ __forceinline__ void draw_spawns(const WorldArgs& args, const int4& pk, const int* s_slot_w,
                                             const int* s_wbase, int t, int nt, float (*sp)[kSpawnDraws]) {
@@ -1527,9 +1626,11 @@ __device__ __forceinline__ void draw_spawns(const WorldArgs& args, const int4& p
         const int j = i / kSpawnTries, r = i % kSpawnTries;
         const int wl = s_slot_w[j], a = pk.z + j;
         float x, y, psi, gx, gy, v0;
+        int cs;
         spawn_candidate(args.rd, pk.x + wl, a, j - s_wbase[wl], args.st.episode[a] + 1, r, args.seed, x, y, psi, gx,
-                        gy, v0);
+                        gy, v0, cs);
         sp[0][i] = x; sp[1][i] = y; sp[2][i] = psi; sp[3][i] = gx; sp[4][i] = gy; sp[5][i] = v0;
+        sp[6][i] = __int_as_float(cs);
     }
 }
 
@@ -1540,12 +1641,19 @@ __device__ __forceinline__ void draw_spawns(const WorldArgs& args, const int4& p
 // to kSpawnGroup slots at once, one lane per (slot, try); the tries are then
 // scored as a sequential loop would: the first one at least the spacing away
 // is taken, else the one with the largest clearance (first on ties).
+// spawn_slot (may be null) receives the respawned lane's spawn candidate slot.
+// The clearances are taken over the positions in E.px / E.py, which this
+// function sets to every lane's current position first (and each placed slot
+// to its new one).
 __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot& c, int lane, Agent& A,
-                                              bool& alive, bool respawn, uint32_t& ev,
-                                              const float (*pre)[kSpawnDraws] = nullptr) {
+                                              bool& alive, bool respawn, uint32_t& ev, Exch& E,
+                                              const float (*pre)[kSpawnDraws] = nullptr, int* spawn_slot = nullptr) {
     static_assert(kSpawnTries * kSpawnGroup == 32, "one lane per (slot, try) of a group");
     const uint32_t rbits = __ballot_sync(kFull, respawn);
     if (!rbits) return;
+    E.px[lane] = A.px;
+    E.py[lane] = A.py;
+    __syncwarp();
     const unsigned long long seed = args.seed;
     const int q = lane / kSpawnTries, r = lane % kSpawnTries;
     for (uint32_t todo = rbits; todo;) {
@@ -1562,52 +1670,58 @@ __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot&
         const int ep_q = __shfl_sync(kFull, A.episode, lq) + 1, w_q = __shfl_sync(kFull, c.w, lq);
         const int a_q = __shfl_sync(kFull, c.a, lq), base_q = __shfl_sync(kFull, c.base, lq);
         float x = 0.f, y = 0.f, psi = 0.f, gx = 0.f, gy = 0.f, v0 = 0.f;
+        int cs = -1;
         if (t) {
             if (pre) {
                 const int i = lq * kSpawnTries + r;
                 x = pre[0][i]; y = pre[1][i]; psi = pre[2][i]; gx = pre[3][i]; gy = pre[4][i]; v0 = pre[5][i];
+                cs = __float_as_int(pre[6][i]);
             } else {
-                spawn_candidate(args.rd, w_q, a_q, lq - base_q, ep_q, r, seed, x, y, psi, gx, gy, v0);
+                spawn_candidate(args.rd, w_q, a_q, lq - base_q, ep_q, r, seed, x, y, psi, gx, gy, v0, cs);
             }
         }
         // the group's slots in order: each takes the first try at least the spacing
-        // away from every eligible agent, else the first of the largest clearance
-        // (the warp minima interleaved over the tries); the eligible agents are the
-        // alive ones of its world, without the slots still waiting to respawn
+        // away from every eligible agent, else the first of the largest clearance;
+        // the eligible agents are the alive ones of its world, without the slots
+        // still waiting to respawn.  Lane s0 + k holds try k of the g-th slot and
+        // takes that try's clearance over the eligible positions; two ballots
+        // (and a maximum) then pick the try as the sequential rule would.
         int g = 0;
         for (uint32_t gg = group; gg; gg &= gg - 1u, ++g) {
             const int l = __ffs(gg) - 1;
-            const int ep = __shfl_sync(kFull, A.episode, l) + 1, wl = __shfl_sync(kFull, c.wl, l);
-            const bool elig = alive && c.wl == wl && lane != l && !(lane > l && ((rbits >> lane) & 1u));
+            const int ep = __shfl_sync(kFull, A.episode, l) + 1;
+            const int lb = __shfl_sync(kFull, c.base, l), ln = __shfl_sync(kFull, c.n, l);
+            const uint32_t wm = (ln >= 32 ? 0xFFFFFFFFu : ((1u << ln) - 1u)) << lb;
+            const uint32_t later = l < 31 ? (rbits & (0xFFFFFFFFu << (l + 1))) : 0u;
+            const uint32_t elig = __ballot_sync(kFull, alive) & wm & ~(1u << l) & ~later;
             const int s0 = g * kSpawnTries;
-            float dmin[kSpawnTries];
-#pragma unroll
-            for (int k = 0; k < kSpawnTries; ++k) {
-                const float xr = __shfl_sync(kFull, x, s0 + k), yr = __shfl_sync(kFull, y, s0 + k);
-                dmin[k] = elig ? norm2(A.px - xr, A.py - yr) : kInf;
+            const bool own = lane >= s0 && lane < s0 + kSpawnTries;
+            float dk = kInf;
+            if (own)
+                for (uint32_t em = elig; em; em &= em - 1u) {
+                    const int j = __ffs(em) - 1;
+                    dk = fminf(dk, norm2(E.px[j] - x, E.py[j] - y));
+                }
+            const unsigned clear = __ballot_sync(kFull, own && dk >= kSpawnSpacing * kSpawnSpacing);
+            int src;
+            if (clear) {
+                src = __ffs(clear) - 1;                  // the first try clear of every agent
+            } else {                                     // the first try of the largest clearance
+                const unsigned best = __reduce_max_sync(kFull, own ? __float_as_uint(dk) : 0u);
+                src = __ffs(__ballot_sync(kFull, own && __float_as_uint(dk) == best)) - 1;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int k = 0; k < kSpawnTries; ++k) dmin[k] = fminf(dmin[k], __shfl_xor_sync(kFull, dmin[k], o));
-            int pick = 0;
-            float bscore = -1.f;
-            bool found = false;
-#pragma unroll
-            for (int k = 0; k < kSpawnTries; ++k) {
-                if (found) continue;
-                if (dmin[k] > bscore) { bscore = dmin[k]; pick = k; }
-                if (dmin[k] >= kSpawnSpacing * kSpawnSpacing) found = true;
-            }
-            const int src = s0 + pick;
             const float bx = __shfl_sync(kFull, x, src), by = __shfl_sync(kFull, y, src);
             const float bpsi = __shfl_sync(kFull, psi, src), bv = __shfl_sync(kFull, v0, src);
             const float bgx = __shfl_sync(kFull, gx, src), bgy = __shfl_sync(kFull, gy, src);
+            const int bcs = __shfl_sync(kFull, cs, src);
             if (lane == l) {
                 place_agent(A, bx, by, bpsi, bv, bgx, bgy);
                 A.episode = ep;
                 alive = true;
                 ev |= kEvRespawned;
+                if (spawn_slot) *spawn_slot = bcs;
+                E.px[l] = A.px;
+                E.py[l] = A.py;
             }
             __syncwarp();
         }
@@ -1727,7 +1841,8 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     __shared__ DevGrid s_grid[32];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ int s_staged;
-    __shared__ float s_sp[6][kSpawnDraws];       // spawn candidates drawn ahead (kDraw)
+    __shared__ float s_sp[kSpawnRows][kSpawnDraws];   // spawn candidates drawn ahead (kDraw)
+    __shared__ int s_spawn[32];                   // spawn candidate slot of each respawned slot, -1: none
     extern __shared__ __align__(128) unsigned char s_blob[];
     // with spare warps, warps 1..NW-1 draw the spawn candidates of every slot
     // while warp 0 runs the physics (a step) or right after the masks (a reset),
@@ -1739,7 +1854,17 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     if (m <= 0) return;                               // CTA-uniform
     bool staged = false;                              // warp 0: this block copies its roads to shared memory
     int stage_total = 0;
+    Agent A;
+    float3 act = make_float3(0.f, 0.f, 0.f);
     if (warp == 0) {
+        // lane l holds slot l = agent a0 + l: its state and actions are loaded
+        // before the pack tables, so that the two memory round trips overlap
+        const int al = a0 + (lane < m ? lane : 0);
+        load_agent(args.st, al, A);
+        if (MODE == kModeStep && lane < m) {
+            const float* ap = args.actions + 3 * (size_t)al;
+            act = make_float3(ap[0], ap[1], ap[2]);
+        }
         pack_tables(args, pk, lane, s_slot_w, s_wbase, s_wn);
         int bytes = 0;
         if (lane < pk.y) {
@@ -1768,7 +1893,6 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
 
     // ---------------- warp 0: agent registers
     const Slot c = slot_of(pk, s_slot_w, s_wbase, s_wn, lane, warp == 0);
-    Agent A;
     bool alive = false, respawn = false, parked_now = false, nonfin = false, done = false;
     bool recompute = false, active = false;       // warp 0: neighbours recomputed / outputs written
     uint32_t ev = 0;
@@ -1778,7 +1902,6 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
 #pragma unroll
     for (int t = 0; t < kK; ++t) { nb[t] = -1; tt[t] = kTtcMax; }
     if (warp == 0) {
-        load_agent(args.st, c.a, A);
         if (!c.has) A.meta = 0;
         alive = c.has && (status_of(A.meta) & kAlive);
         if (MODE == kModeReset) respawn = c.has && args.mask[c.a] != 0;
@@ -1800,7 +1923,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     if (MODE == kModeStep) {
         float prevx = 0.f, prevy = 0.f;
         if (warp == 0) {
-            lanes_physics<PHYS>(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E);
+            lanes_physics<PHYS>(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E, act);
             const unsigned ab = __ballot_sync(kFull, alive);
             if (lane == 0) s_alive = ab;
         }
@@ -1809,14 +1932,21 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
             stg = stage_wait(&s_bar, args.wait_ns ? args.wait_ns : kStageWaitNs);
             if (!stg) atomicOr(args.out.error_word, 2u);
         }
-        // ---------------- road queries of the events (all warps, one agent at a time)
+        // ---------------- road queries at the end-of-physics pose (all warps, one agent at a
+        // time), one pass over the cells: the events' answers and the observation's
+        // road-point block (respawns and parking below replace the blocks they change)
         for (int j = warp; j < m; j += NW) {
             if (!((s_alive >> j) & 1u)) continue;
             const int t = s_slot_w[j];
             const WRoads v = view_of(s_grid[t], (stg && s_woff[t] >= 0) ? s_blob + s_woff[t]
                                                                          : args.rd.blob + s_grid[t].blob);
-            const AgentQ q = agent_event_queries(v, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j], E.vx[j],
-                                                 E.vy[j], args.out.hint + 4 * (size_t)(a0 + j), lane);
+            float* hnt = args.out.hint + 4 * (size_t)(a0 + j);
+            const float4 h4 = *reinterpret_cast<const float4*>(hnt);
+            const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+            const AgentQ q = agent_step_queries(
+                v, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j], E.vx[j], E.vy[j], hv, hnt, lane, kbuf[warp],
+                args.out.obs + (size_t)(a0 + j) * kObsDim + kObsEgo + kK * kObsNbr,
+                (args.flags & kFlagRecord) ? args.out.knn_pts + (size_t)(a0 + j) * kL : nullptr);
             if (lane == 0) Q[j] = q;
         }
         __syncthreads();
@@ -1833,7 +1963,9 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
 
     // ---------------- respawns (warp 0, agents in index order), then the post-reset exchange
     if (warp == 0) {
-        lanes_respawn(args, c, lane, A, alive, respawn, ev, kDraw ? s_sp : nullptr);
+        int spawn_slot = -1;
+        lanes_respawn(args, c, lane, A, alive, respawn, ev, E, kDraw ? s_sp : nullptr, &spawn_slot);
+        s_spawn[lane] = respawn ? spawn_slot : -1;
         // per world (never per pack, so that packing changes no result): a world
         // with a respawn or a parked agent republishes and recomputes its
         // neighbours; a reset leaves the worlds without a masked agent untouched
@@ -1848,12 +1980,10 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         const unsigned ab = __ballot_sync(kFull, alive), act = __ballot_sync(kFull, active);
         if (lane == 0) { s_alive = ab; s_act = act; }
         // road-point blocks to compute: every agent when observing, the respawned
-        // ones otherwise (a reset moves only its masked agents, so the others'
-        // blocks and ego groups, computed at the same pose, stand)
-        if (lane < m) {
-            if (MODE == kModeObserve || respawn) Q[lane].need = 1;
-            else if (MODE == kModeReset) Q[lane].need = 0;
-        }
+        // ones otherwise (the step's queries wrote the others' at the same pose;
+        // a reset moves only its masked agents, so the others' blocks and ego
+        // groups stand)
+        if (lane < m) Q[lane].need = (MODE == kModeObserve || respawn) ? 1 : 0;
     }
     __syncthreads();
 
@@ -1868,13 +1998,18 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         const WRoads v = view_of(s_grid[t], (stg && s_woff[t] >= 0) ? s_blob + s_woff[t]
                                                                      : args.rd.blob + s_grid[t].blob);
         const bool al = (s_alive >> j) & 1u, need = Q[j].need != 0;
-        if (MODE == kModeReset && al && !need) continue;   // unmoved by the reset
+        if (MODE != kModeObserve && al && !need) continue;   // written by the step's queries / unmoved by the reset
+        float* orow = args.out.obs + (size_t)(a0 + j) * kObsDim + kObsEgo + kK * kObsNbr;
+        int32_t* krow = (args.flags & kFlagRecord) ? args.out.knn_pts + (size_t)(a0 + j) * kL : nullptr;
+        float* hnt = args.out.hint + 4 * (size_t)(a0 + j);
+        const int slot = MODE != kModeObserve ? s_spawn[j] : -1;
         Lane L;
-        agent_road_block(v, al, need, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j],
-                         args.out.hint + 4 * (size_t)(a0 + j), lane, kbuf[warp],
-                         args.out.obs + (size_t)(a0 + j) * kObsDim + kObsEgo + kK * kObsNbr,
-                         (args.flags & kFlagRecord) ? args.out.knn_pts + (size_t)(a0 + j) * kL : nullptr, &L,
-                         MODE == kModeObserve ? kLaneR0 : kSpawnLaneR);
+        if (al && need && slot >= 0 && args.rd.spawnq)      // a respawn on a spawn candidate: the table's answers
+            spawn_road_block(args.rd.spawnq + slot, v, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j], hnt,
+                             lane, orow, krow, &L);
+        else
+            agent_road_block(v, al, need, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j], hnt, lane,
+                             kbuf[warp], orow, krow, &L, MODE == kModeObserve ? kLaneR0 : kSpawnLaneR);
         if (al && need && lane == 0) {
             Q[j].seg = L.seg; Q[j].dist = L.dist; Q[j].lat = L.lat; Q[j].tx = L.tx; Q[j].ty = L.ty;
         }
@@ -1916,11 +2051,16 @@ __global__ void __launch_bounds__(32, 16) phys_kernel(const WorldArgs args) {
     const Slot c = slot_of(pk, s_slot_w, s_wbase, s_wn, lane, true);
     Agent A;
     load_agent(args.st, c.a, A);
+    float3 act = make_float3(0.f, 0.f, 0.f);
+    if (c.has) {
+        const float* ap = args.actions + 3 * (size_t)c.a;
+        act = make_float3(ap[0], ap[1], ap[2]);
+    }
     if (!c.has) A.meta = 0;
     bool alive = c.has && (status_of(A.meta) & kAlive), nonfin = false;
     float prevx = 0.f, prevy = 0.f, hx = 1.f, hy = 0.f;
     if (blockIdx.x == 0 && lane == 0) *args.sc.fix_count = 0u;   // the events kernel appends after this kernel
-    lanes_physics<PHYS>(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E);
+    lanes_physics<PHYS>(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E, act);
     if (c.has) {
         store_agent(args.st, c.a, A);
         args.sc.prev[c.a] = make_float2(prevx, prevy);
@@ -1955,32 +2095,9 @@ __global__ void __launch_bounds__(32 * NWQ, 32 / NWQ) query_kernel(const WorldAr
     const DevGrid g = args.rd.grid[wid];
     const WRoads v = view_of(g, args.rd.blob + g.blob);
     const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
-    bool forb = false;
-    unsigned long long key = kKeyInf;
-    const Lane L = coop_point_queries(v, p.x, p.y, goal.x, goal.y, h.x, h.y, hint_radius(hv, 0, p.x, p.y, kKnnR0),
-                                      hint_radius(hv, 1, p.x, p.y, kLaneR0), lane, kbuf[warp], &forb, &key);
-    // the observation's point records are fetched while the edge ray runs
-    float4 prec = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint32_t pm = 0u;
-    if (key != kKeyInf) { prec = v.seg[rkey_pos(key)]; pm = v.info[rkey_pos(key)]; }
-    const float tedge = coop_edge_ray(v, p.x, p.y, vel.x, vel.y, lane);
-    const unsigned long long last = shfl64(key, 31);
-    __syncwarp();
-    if (lane == 0) {
-        AgentQ q;
-        q.seg = L.seg; q.dist = L.dist; q.lat = L.lat; q.tx = L.tx; q.ty = L.ty;
-        q.tedge = tedge; q.forb = forb ? 1 : 0; q.need = 0;
-        args.sc.q[a] = q;
-        hnt[0] = last != kKeyInf ? sqrtf(key_d2(last)) : 0.f;
-        hnt[1] = L.seg >= 0 ? L.dist : 0.f;
-        hnt[2] = p.x;
-        hnt[3] = p.y;
-    }
-    float f[kObsPt] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (key != kKeyInf) point_features_of(prec, pm, h.x, h.y, p.x, p.y, f);
-#pragma unroll
-    for (int k = 0; k < kObsPt; ++k) orow[kObsPt * lane + k] = f[k];
-    if (krow) krow[lane] = key != kKeyInf ? v.q0 + rkey_local(key) : -1;
+    const AgentQ q = agent_step_queries(v, p.x, p.y, goal.x, goal.y, h.x, h.y, vel.x, vel.y, hv, hnt, lane,
+                                        kbuf[warp], orow, krow);
+    if (lane == 0) args.sc.q[a] = q;
 }
 
 // events, rewards, respawns, neighbours, ego group, outputs and state; marks
@@ -2027,7 +2144,7 @@ __global__ void __launch_bounds__(32 * NWE) events_kernel(const WorldArgs args) 
     if (warp == 0) {
         lanes_events_b(args, c, lane, A, alive, nonfin, hx, hy, alive_bits, args.sc.q + c.a, E, nb, tt, r, N, ev,
                        reward, drac, done, respawn, parked_now);
-        lanes_respawn(args, c, lane, A, alive, respawn, ev);
+        lanes_respawn(args, c, lane, A, alive, respawn, ev, E);
         const unsigned chg = __ballot_sync(kFull, respawn || parked_now);
         const uint32_t wmask = c.n >= 32 ? 0xFFFFFFFFu : (((1u << c.n) - 1u) << c.base);
         recompute = (chg & wmask) != 0u;
@@ -2291,6 +2408,38 @@ cudaError_t sf_launch_world(int mode, const WorldArgs& a, int nw, cudaStream_t s
         case kModeReset: return launch_mode<kModeReset>(a, nw, s);
         default: return launch_mode<kModeObserve>(a, nw, s);
     }
+}
+
+// the spawn table: per spawn candidate (one warp each) the exact nearest lane
+// (before the goal orientation) and the 32 nearest road points at the
+// candidate point, by the same queries the step runs
+__global__ void __launch_bounds__(256) spawn_table_kernel(const DevRoads rd, const int32_t* __restrict__ cand_world,
+                                                          int ncand, SpawnQ* __restrict__ out) {
+    __shared__ unsigned long long kbuf[8][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 8 + warp;
+    if (c >= ncand) return;                           // warp-uniform
+    const DevGrid g = rd.grid[cand_world[c]];
+    const WRoads v = view_of(g, rd.blob + g.blob);
+    const float4 p = rd.pt[rd.cands[c]];
+    const unsigned long long key = coop_knn32(v, p.x, p.y, kKnnR0, lane, kbuf[warp]);
+    __syncwarp();
+    const Lane L = coop_nearest_lane_raw(v, p.x, p.y, kSpawnLaneR, lane);
+    const unsigned long long last = shfl64(key, 31);
+    SpawnQ* e = out + c;
+    e->pos[lane] = key != kKeyInf ? (uint16_t)rkey_pos(key) : (uint16_t)0xFFFFu;
+    if (lane == 0) {
+        e->seg = L.seg; e->dist = L.dist; e->lat = L.lat; e->tx = L.tx; e->ty = L.ty;
+        e->d32 = last != kKeyInf ? sqrtf(key_d2(last)) : 0.f;
+        e->pad[0] = e->pad[1] = 0;
+    }
+}
+
+cudaError_t sf_launch_spawn_table(const DevRoads& rd, const int32_t* cand_world, int ncand, SpawnQ* out,
+                                  cudaStream_t s) {
+    if (ncand <= 0) return cudaSuccess;
+    spawn_table_kernel<<<(ncand + 7) / 8, 256, 0, s>>>(rd, cand_world, ncand, out);
+    return cudaGetLastError();
 }
 
 cudaError_t sf_launch_place(const WorldArgs& a, const float* d_place, cudaStream_t s) {

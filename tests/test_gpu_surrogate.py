@@ -159,6 +159,10 @@ def test_ungated_agents_follow_the_physics_exactly():
     resp = ((I1[:, O.I_EVENTS] | I2[:, O.I_EVENTS]) & O.EV["respawned"]) != 0
     same = ~g & ~resp                       # respawn spacing sees every agent's new position
     assert same.sum() > 10
+    bad = np.nonzero(same & (F1[:, :19] != F2[:, :19]).any(1))[0]
+    for a in bad[:4]:
+        cols = np.nonzero(F1[a, :19] != F2[a, :19])[0]
+        print("agent", a, "columns", cols, "max |d|", float(np.abs(F1[a, :19] - F2[a, :19]).max()))
     assert np.array_equal(F1[same][:, :19], F2[same][:, :19])
     sf.sf_surrogate_destroy(s)
 
