@@ -135,10 +135,24 @@ typedef struct {
                               * draws use the agent's index in the whole CSR).  Agent *
                               * indices of the handle's outputs are local to the      *
                               * range                                                 */
-    int32_t reserved[2];     /* must be zero                                          */
+    int32_t weather_model;   /* SF_WEATHER_TABLE (default): mu from the (precip,       *
+                              * surface) table; SF_WEATHER_ALL: the modified ALL     *
+                              * weather-to-friction model of Sec. 3.3 / App. B:      *
+                              * surface 0 AC, 1 SMA, 2 OGFC and a water film h per   *
+                              * agent (sf_roads.film_mm), mu = the model's static    *
+                              * friction at 13.89 m/s (the printed curve points      *
+                              * joined linearly, falling to the 1e-3 floor at the    *
+                              * 0.85 mm aquaplaning threshold), and the ego group's  *
+                              * weather token = Eq. weather_obs (h / 1 mm, one-hot   *
+                              * AC, SMA, OGFC).  The film is resolved to 0.01 mm and *
+                              * held to at most 2.55 mm (beyond 0.85 mm mu is the    *
+                              * floor anyway)                                         */
+    int32_t reserved[1];     /* must be zero                                          */
 } sf_config;
 #define SF_DYN_VEHICLE 0
 #define SF_DYN_BICYCLE 1
+#define SF_WEATHER_TABLE 0
+#define SF_WEATHER_ALL 1
 
 /* Worlds as CSR (host memory, read during sf_load_roads only).
  * World w holds agents [agent_off[w], agent_off[w+1]) (at most 32) and
@@ -158,8 +172,10 @@ typedef struct {
     const uint8_t* poly_type;  /* [num_polylines]                                       */
     const float* px;           /* [num_points]                                          */
     const float* py;           /* [num_points]                                          */
-    const uint8_t* precip;     /* [num_agents] 0..3                                     */
+    const uint8_t* precip;     /* [num_agents] 0..3 (table weather model)               */
     const uint8_t* surface;    /* [num_agents] 0..2                                     */
+    const float* film_mm;      /* [num_agents] water film [mm], finite and >= 0; read   *
+                                * only with SF_WEATHER_ALL (precip is then ignored)    */
 } sf_roads;
 
 /* Device pointers to the library-owned outputs of the last sf_step / sf_reset.

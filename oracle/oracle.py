@@ -29,6 +29,7 @@ ALIVE, PARKED = 1, 2
 EV = dict(goal=1, collision=2, crash=4, lane_forbidden=8, offroad=16, idle=32, timeout=64,
           nonfinite=128, respawned=256)
 FLAG_INVINCIBLE, FLAG_AUTO_RESET, FLAG_BICYCLE = 1, 2, 4
+WEATHER_TABLE, WEATHER_ALL = 0, 1
 K_AGENTS, L_POINTS, OBS = 8, 32, 320
 FULL_EGO, FULL_KR, FULL_PT, FULL_KV, FULL_NB = 11, 350, 5, 24, 7
 FULL_OBS = FULL_EGO + FULL_KR * FULL_PT + FULL_KV * FULL_NB   # 1929 (App. D)
@@ -63,7 +64,10 @@ class Params(C.Structure):
         (n, C.c_double) for n in (
             "spawn_goal_min", "spawn_goal_max", "spawn_v_min", "spawn_v_max", "spawn_spacing",
             "park_x")] + [("spawn_tries", C.c_int), ("mu_table", (C.c_double * 3) * 4)] + [
-        (n, C.c_double) for n in ("bike_theta_max", "bike_a_drive", "bike_a_brake")]
+        (n, C.c_double) for n in ("bike_theta_max", "bike_a_drive", "bike_a_brake")] + [
+        ("weather_model", C.c_int), ("all_mu", (C.c_double * 9) * 3), ("all_h_cut", C.c_double),
+        ("all_floor", C.c_double), ("all_theta", C.c_double * 3), ("all_td", C.c_double * 3),
+        ("h_norm", C.c_double), ("stribeck_b", C.c_double * 4)]
 
 
 class _Scene(C.Structure):
@@ -110,6 +114,10 @@ def lib():
         L.or_ttc_circles.argtypes = [d, d, d, vp, vp]
         L.or_penalty.argtypes = [d, d, d, d]
         L.or_penalty.restype = d
+        L.or_all_mu_static.argtypes = [vp, i, i]
+        L.or_all_mu_static.restype = d
+        L.or_stribeck_vs.argtypes = [vp, d]
+        L.or_stribeck_vs.restype = d
         _lib = L
     return _lib
 
@@ -264,3 +272,16 @@ def ttc_circles(L, W, WB):
 
 def penalty(alpha, tau, tau_floor, pmax):
     return lib().or_penalty(float(alpha), float(tau), float(tau_floor), float(pmax))
+
+
+def all_mu_static(surface, film_cmm, params=None):
+    """Static friction of the modified ALL model (App. B) of surface 0 AC,
+    1 SMA, 2 OGFC at a water film of film_cmm hundredths of a millimetre."""
+    P = params or default_params()
+    return lib().or_all_mu_static(C.byref(P), int(surface), int(film_cmm))
+
+
+def stribeck_vs(h_m, params=None):
+    """Stribeck speed [m/s] at a water film of h_m metres (Eq. app_stribeck_speed)."""
+    P = params or default_params()
+    return lib().or_stribeck_vs(C.byref(P), float(h_m))

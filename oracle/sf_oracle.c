@@ -98,6 +98,21 @@ void or_default_params(or_params* P) {
     P->bike_theta_max = M_PI / 6.0;
     P->bike_a_drive = 2.0 * P->tau_drive / (P->wheel_r * P->mass);
     P->bike_a_brake = 2.0 * (P->tau_brk_f + P->tau_brk_r) / (P->wheel_r * P->mass);
+    /* App. B: mu_static of the modified ALL model at 13.89 m/s, read off the
+     * printed curves of Fig. friction_mu_vs_film (h = 0, 0.1, ..., 0.8 mm);
+     * surface presets theta and T_d; the 1e-3 floor; Eq. weather_obs h_norm */
+    static const double all_mu[3][9] = {
+        {1.1048, 1.0657, 1.0161, 0.9593, 0.9039, 0.8595, 0.8302, 0.8134, 0.8044},   /* AC   */
+        {1.2043, 1.1618, 1.1078, 1.0461, 0.9857, 0.9374, 0.9056, 0.8874, 0.8776},   /* SMA  */
+        {1.3368, 1.2898, 1.2301, 1.1617, 1.0948, 1.0413, 1.0061, 0.9860, 0.9753}};  /* OGFC */
+    memcpy(P->all_mu, all_mu, sizeof(all_mu));
+    P->all_h_cut = 0.85;       /* F5: the figure's aquaplaning threshold */
+    P->all_floor = 1e-3;
+    P->all_theta[0] = 1.00; P->all_theta[1] = 1.09; P->all_theta[2] = 1.21;
+    P->all_td[0] = 0.65;    P->all_td[1] = 0.80;    P->all_td[2] = 1.08;
+    P->h_norm = 1.0;
+    P->stribeck_b[0] = 4.8916; P->stribeck_b[1] = -7.91; P->stribeck_b[2] = 3.01; P->stribeck_b[3] = 3.40;
+    P->weather_model = OR_WEATHER_TABLE;
 }
 
 uint64_t or_splitmix64(uint64_t x) {
@@ -237,6 +252,26 @@ double or_sat(const or_params* P, const double ci[2], const double hi[2], const 
     }
     if (n_out) { n_out[0] = sgn * ax[bk][0]; n_out[1] = sgn * ax[bk][1]; }
     return best;
+}
+
+/* F5: the printed mu_static(h) points joined linearly (0.1 mm apart); from
+ * 0.8 mm linearly down to the floor at the aquaplaning threshold all_h_cut,
+ * the floor beyond it (App. B: full grip loss for h >~ 0.85 mm, mu <= 1e-3 at
+ * h >= 1.0 mm).  The film comes in hundredths of a millimetre, so the
+ * interpolation weight r / 10 of the last step is exact. */
+double or_all_mu_static(const or_params* P, int surface, int film_cmm) {
+    const double* m = P->all_mu[surface];
+    const int cut = (int)lround(P->all_h_cut * 100.0);
+    if (film_cmm >= cut) return P->all_floor;
+    if (film_cmm >= 80) return m[8] + (P->all_floor - m[8]) * (double)(film_cmm - 80) / (double)(cut - 80);
+    const int k = film_cmm / 10, r = film_cmm % 10;
+    return m[k] + (m[k + 1] - m[k]) * (double)r / 10.0;
+}
+
+/* Eq. app_stribeck_speed: v_s(h) = b1 exp(1000 b2 h + b3) + b4, h in metres */
+double or_stribeck_vs(const or_params* P, double h_m) {
+    const double* b = P->stribeck_b;
+    return b[0] * exp(1000.0 * b[1] * h_m + b[2]) + b[3];
 }
 
 void or_ttc_circles(double L, double W, double WB, double* r, double* d) {
@@ -570,7 +605,9 @@ static void observe_agent(const or_params* P, const or_scene* S, int w, const do
         o[4] = gn / P->scene_half;
         o[5] = vbx / 10.0;
         o[6] = vby / 10.0;
-        o[7] = pc / 3.0;
+        /* weather token: (precip / 3, surface one-hot) of the table model, or
+         * Eq. weather_obs (h / h_norm, one-hot AC, SMA, OGFC) of the ALL model */
+        o[7] = P->weather_model == OR_WEATHER_ALL ? pc * 0.01 / P->h_norm : pc / 3.0;
         o[8] = sc == 0; o[9] = sc == 1; o[10] = sc == 2;
         o[11] = f[OR_F_WZ];
         o[12] = f[OR_F_DELTA] / P->theta_max;
@@ -680,7 +717,9 @@ static void observe_full_agent(const or_params* P, const or_scene* S, int w, con
         o[4] = gn / P->scene_half;
         o[5] = vbx / 10.0;
         o[6] = vby / 10.0;
-        o[7] = pc / 3.0;
+        /* weather token: (precip / 3, surface one-hot) of the table model, or
+         * Eq. weather_obs (h / h_norm, one-hot AC, SMA, OGFC) of the ALL model */
+        o[7] = P->weather_model == OR_WEATHER_ALL ? pc * 0.01 / P->h_norm : pc / 3.0;
         o[8] = sc == 0; o[9] = sc == 1; o[10] = sc == 2;
     }
 
@@ -908,7 +947,8 @@ void or_place_agent(const or_params* P, double* F, int32_t* I, int a, double x, 
     f[OR_F_DELTA] = 0; f[OR_F_DDELTA] = 0;
     f[OR_F_GX] = gx; f[OR_F_GY] = gy;
     f[OR_F_SX] = x; f[OR_F_SY] = y;
-    f[OR_F_MU] = P->mu_table[precip][surface];
+    f[OR_F_MU] = P->weather_model == OR_WEATHER_ALL ? or_all_mu_static(P, surface, precip)
+                                                   : P->mu_table[precip][surface];
     f[OR_F_PEAK_DRAC] = 0;
     ii[OR_I_PRECIP] = precip; ii[OR_I_SURFACE] = surface;
     ii[OR_I_STEP] = 0;

@@ -43,8 +43,10 @@ enum {
 };
 /* int state columns */
 enum {
-    OR_I_PRECIP = 0,   /* 0 dry, 1 light rain, 2 heavy rain, 3 snow */
-    OR_I_SURFACE,      /* 0 asphalt, 1 concrete, 2 gravel           */
+    OR_I_PRECIP = 0,   /* table model: 0 dry, 1 light rain, 2 heavy rain, 3 snow;
+                          ALL model: water film thickness in 0.01 mm            */
+    OR_I_SURFACE,      /* table model: 0 asphalt, 1 concrete, 2 gravel;
+                          ALL model: 0 AC, 1 SMA, 2 OGFC                        */
     OR_I_STEP,         /* control steps since spawn                 */
     OR_I_EPISODE,      /* episode counter of this agent slot        */
     OR_I_STATUS,       /* bit0 alive, bit1 parked                   */
@@ -110,7 +112,19 @@ typedef struct {
     double bike_theta_max;        /* steering limit, 30 degrees                                  */
     double bike_a_drive;          /* full-throttle acceleration: both front drive torques / (r m) */
     double bike_a_brake;          /* full-brake deceleration: all four brake torques / (r m)      */
+    /* weather-to-friction model (Sec. 3.3, App. B): OR_WEATHER_TABLE uses mu_table;
+     * OR_WEATHER_ALL the modified ALL model's static friction at 13.89 m/s */
+    int weather_model;
+    double all_mu[3][9];          /* mu_static at h = 0, 0.1, ..., 0.8 mm, [AC, SMA, OGFC] (App. B fig.) */
+    double all_h_cut;             /* film [mm] from which the model predicts full grip loss (F5)        */
+    double all_floor;             /* simulator floor of mu (App. B)                                      */
+    double all_theta[3];          /* texture influence coefficient theta (App. B presets)                */
+    double all_td[3];             /* texture amplitude T_d [mm] (App. B presets)                          */
+    double h_norm;                /* film normaliser of the weather token [mm] (Eq. weather_obs)         */
+    double stribeck_b[4];         /* b1..b4 of Eq. app_stribeck_speed                                    */
 } or_params;
+#define OR_WEATHER_TABLE 0
+#define OR_WEATHER_ALL 1
 
 /* Roads and agents of all worlds, as CSR (world -> polylines -> points). */
 typedef struct {
@@ -224,6 +238,11 @@ double or_drac(const or_params* P, const double pi[2], const double hi[2], const
 double or_lane_keep_q(const or_params* P, double lateral, double cos_dpsi);
 /* circle geometry of the TTC test for a box of length L, width W, wheelbase WB. */
 void or_ttc_circles(double L, double W, double WB, double* r, double* d);
+/* Modified ALL model (App. B): static friction of surface s (0 AC, 1 SMA,
+ * 2 OGFC) at a water film of film_cmm hundredths of a millimetre, and the
+ * Stribeck speed v_s [m/s] at a film of h_m metres (Eq. app_stribeck_speed). */
+double or_all_mu_static(const or_params* P, int surface, int film_cmm);
+double or_stribeck_vs(const or_params* P, double h_m);
 double or_penalty(double alpha, double tau, double tau_floor, double pmax);
 
 #ifdef __cplusplus

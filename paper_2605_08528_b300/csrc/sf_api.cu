@@ -155,7 +155,7 @@ WorldArgs make_args(sf_ctx* h) {
             a.stage_bytes = ps.budget;
         }
     a.sc = h->sc;
-    a.flags = h->cfg.flags;
+    a.flags = h->cfg.flags | (h->cfg.weather_model == SF_WEATHER_ALL ? sfk::kFlagWeatherAll : 0);
     a.seed = h->cfg.seed;
     a.dynamics = h->cfg.dynamics;
     a.substeps = 1;
@@ -273,8 +273,11 @@ sf_status sf_create(const sf_config* cfg, void* cuda_stream, sf_handle* out) {
     *out = nullptr;
     sf_config c{};
     if (cfg) c = *cfg;
-    for (int i = 0; i < 2; ++i)
-        if (c.reserved[i] != 0) { g_create_error = "sf_create: reserved fields must be zero"; return SF_ERR_INVALID_ARG; }
+    if (c.reserved[0] != 0) { g_create_error = "sf_create: reserved fields must be zero"; return SF_ERR_INVALID_ARG; }
+    if (c.weather_model != SF_WEATHER_TABLE && c.weather_model != SF_WEATHER_ALL) {
+        g_create_error = "sf_create: weather_model must be SF_WEATHER_TABLE or SF_WEATHER_ALL";
+        return SF_ERR_INVALID_ARG;
+    }
     if (c.world_begin < 0 || c.world_end < 0 || (c.world_end != 0 && c.world_end <= c.world_begin) ||
         (c.world_end == 0 && c.world_begin != 0)) {
         g_create_error = "sf_create: world range must be 0 <= world_begin < world_end (or both 0)";
@@ -357,6 +360,7 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
         rs.py = r->py ? r->py + q0 : nullptr;
         rs.precip = r->precip ? r->precip + a0 : nullptr;
         rs.surface = r->surface ? r->surface + a0 : nullptr;
+        rs.film_mm = r->film_mm ? r->film_mm + a0 : nullptr;
         agent_base = a0;
         r = &rs;
     }
@@ -380,10 +384,14 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
             return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: point_off not monotone at polyline " + std::to_string(p));
     if (r->point_off[NPl] != NP) return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: point_off[P] != num_points");
     const int A = r->agent_off[W];
-    if (A > 0 && (!r->precip || !r->surface)) return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: NULL weather arrays");
-    for (int a = 0; a < A; ++a)
-        if (r->precip[a] > 3 || r->surface[a] > 2)
+    const bool all_model = h->cfg.weather_model == SF_WEATHER_ALL;
+    if (A > 0 && (!r->surface || (all_model ? !r->film_mm : !r->precip)))
+        return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: NULL weather arrays");
+    for (int a = 0; a < A; ++a) {
+        const bool bad = all_model ? !(std::isfinite(r->film_mm[a]) && r->film_mm[a] >= 0.f) : r->precip[a] > 3;
+        if (bad || r->surface[a] > 2)
             return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: weather code out of range at agent " + std::to_string(a));
+    }
     for (int k = 0; k < NP; ++k)
         if (!std::isfinite(r->px[k]) || !std::isfinite(r->py[k]))
             return fail(h, SF_ERR_INVALID_ARG, "sf_load_roads: non-finite point " + std::to_string(k));
@@ -600,7 +608,13 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
 #undef SF_ALLOC
 
     std::vector<uint32_t> meta_h(Aa);
-    for (size_t a = 0; a < Aa; ++a) meta_h[a] = (uint32_t)r->precip[a] | ((uint32_t)r->surface[a] << 8);
+    // the weather byte: the precipitation class, or (ALL model) the water film in
+    // hundredths of a millimetre, held to 2.55 mm (mu is the floor beyond 0.85 mm)
+    for (size_t a = 0; a < Aa; ++a) {
+        const uint32_t wb = all_model ? (uint32_t)std::min(255.0, std::nearbyint((double)r->film_mm[a] * 100.0))
+                                      : (uint32_t)r->precip[a];
+        meta_h[a] = wb | ((uint32_t)r->surface[a] << 8);
+    }
     cudaError_t e = cudaSuccess;
     auto up = [&](void* d, const void* src, size_t bytes) {
         if (e == cudaSuccess && bytes) e = cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice);
@@ -1011,6 +1025,7 @@ sf_status sf_observe_full(sf_handle h, float* d_obs, int32_t* d_n_road, int32_t*
     f.n_veh = d_n_veh;
     f.road_idx = d_road_idx;
     f.veh_idx = d_veh_idx;
+    f.weather_all = h->cfg.weather_model == SF_WEATHER_ALL ? 1 : 0;
     SF_CUDA(h, sf_launch_full_obs(f, h->stream));
     return SF_OK;
 }

@@ -109,6 +109,7 @@ constexpr uint32_t kAlive = 1u, kParked = 2u;
 constexpr uint32_t kEvGoal = 1u, kEvCollision = 2u, kEvCrash = 4u, kEvLaneForb = 8u, kEvOffroad = 16u,
                    kEvIdle = 32u, kEvTimeout = 64u, kEvNonfinite = 128u, kEvRespawned = 256u;
 constexpr int kFlagInvincible = 1, kFlagAutoReset = 2, kFlagRecord = 4;
+constexpr int kFlagWeatherAll = 1 << 16;   // internal: the ALL weather model (set from sf_config)
 
 }  // namespace sfk
 
@@ -257,6 +258,7 @@ struct FullObsArgs {
     int32_t* n_veh;              // [A] or null
     int32_t* road_idx;           // [A][kFullKR] or null
     int32_t* veh_idx;            // [A][kFullKV] or null
+    int weather_all;             // the weather byte is a water film (ALL model), not a precipitation class
 };
 
 // launch wrappers (sf_world.cu)

@@ -461,7 +461,31 @@ __constant__ float c_mu_table[4][3] = {{0.90f, 0.85f, 0.60f},   // dry       (as
                                        {0.30f, 0.25f, 0.20f}};  // snow
 
 // place agent at (x, y) heading psi with speed v0, static equilibrium, rolling wheels
-__device__ __forceinline__ void place_agent(Agent& A, float x, float y, float psi, float v0, float gx, float gy) {
+// Static friction of the modified ALL weather-to-friction model (App. B) at
+// 13.89 m/s: the printed mu_static(h) curve points of surface s (0 AC, 1 SMA,
+// 2 OGFC) at h = 0, 0.1, ..., 0.8 mm joined linearly, then linearly down to the
+// 1e-3 floor at the 0.85 mm aquaplaning threshold, the floor beyond; the film
+// comes in hundredths of a millimetre.
+__constant__ float c_all_mu[3][9] = {
+    {1.1048f, 1.0657f, 1.0161f, 0.9593f, 0.9039f, 0.8595f, 0.8302f, 0.8134f, 0.8044f},   // AC
+    {1.2043f, 1.1618f, 1.1078f, 1.0461f, 0.9857f, 0.9374f, 0.9056f, 0.8874f, 0.8776f},   // SMA
+    {1.3368f, 1.2898f, 1.2301f, 1.1617f, 1.0948f, 1.0413f, 1.0061f, 0.9860f, 0.9753f}};  // OGFC
+constexpr float kAllFloor = 1e-3f;
+constexpr uint32_t kAllCutCmm = 85;
+__device__ __forceinline__ float all_mu_static(uint32_t s, uint32_t film_cmm) {
+    const float* m = c_all_mu[s > 2 ? 2 : s];
+    if (film_cmm >= kAllCutCmm) return kAllFloor;
+    if (film_cmm >= 80u) return m[8] + (kAllFloor - m[8]) * ((float)(film_cmm - 80u) / (float)(kAllCutCmm - 80u));
+    const uint32_t k = film_cmm / 10u, r = film_cmm % 10u;
+    return m[k] + (m[k + 1] - m[k]) * ((float)r / 10.f);
+}
+// the weather token's first entry: precip / 3 (table model) or h / h_norm, h_norm = 1 mm (Eq. weather_obs)
+__device__ __forceinline__ float weather_level(uint32_t wb, bool all_model) {
+    return all_model ? (float)wb * 0.01f : (float)wb / 3.f;
+}
+
+__device__ __forceinline__ void place_agent(Agent& A, float x, float y, float psi, float v0, float gx, float gy,
+                                            bool all_model) {
     float s, c, sh, ch;
     sincosf(psi, &s, &c);
     sincosf(0.5f * psi, &sh, &ch);
@@ -473,7 +497,7 @@ __device__ __forceinline__ void place_agent(Agent& A, float x, float y, float ps
     A.s0 = A.s1 = A.s2 = A.s3 = om;
     A.gx = gx; A.gy = gy; A.sx = x; A.sy = y;
     uint32_t pc = A.meta & 0xFFu, sc = (A.meta >> 8) & 0xFFu;
-    A.mu = c_mu_table[pc > 3 ? 3 : pc][sc > 2 ? 2 : sc];
+    A.mu = all_model ? all_mu_static(sc, pc) : c_mu_table[pc > 3 ? 3 : pc][sc > 2 ? 2 : sc];
     A.peak = 0.f;
     A.step = 0;
     A.meta = with_status(A.meta, kAlive);
@@ -1715,7 +1739,7 @@ __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot&
             const float bgx = __shfl_sync(kFull, gx, src), bgy = __shfl_sync(kFull, gy, src);
             const int bcs = __shfl_sync(kFull, cs, src);
             if (lane == l) {
-                place_agent(A, bx, by, bpsi, bv, bgx, bgy);
+                place_agent(A, bx, by, bpsi, bv, bgx, bgy, (args.flags & kFlagWeatherAll) != 0);
                 A.episode = ep;
                 alive = true;
                 ev |= kEvRespawned;
@@ -1797,7 +1821,8 @@ __device__ __forceinline__ void lanes_final_b(const WorldArgs& args, const Slot&
         float gn = sqrtf(gbx * gbx + gby * gby);
         uint32_t pc = A.meta & 0xFFu, sc = (A.meta >> 8) & 0xFFu;
         o4[0] = make_float4(gbx / kSceneHalf, gby / kSceneHalf, gn > 0.f ? gby / gn : 0.f, gn > 0.f ? gbx / gn : 1.f);
-        o4[1] = make_float4(gn / kSceneHalf, vbx / 10.f, vby / 10.f, (float)pc / 3.f);
+        o4[1] = make_float4(gn / kSceneHalf, vbx / 10.f, vby / 10.f,
+                            weather_level(pc, (args.flags & kFlagWeatherAll) != 0));
         o4[2] = make_float4(sc == 0 ? 1.f : 0.f, sc == 1 ? 1.f : 0.f, sc == 2 ? 1.f : 0.f, A.wz);
         o4[3] = make_float4(A.dl / kThetaMax, A.mu, q.seg >= 0 ? q.lat / 3.6f : 0.f,
                             q.seg >= 0 ? cross2(q.tx, q.ty, hx, hy) : 0.f);
@@ -2211,7 +2236,7 @@ __global__ void place_kernel(const WorldArgs args, const float* __restrict__ pla
     Agent A;
     load_agent(args.st, a, A);
     const float* p = place + 6 * (size_t)a;
-    place_agent(A, p[0], p[1], p[2], p[3], p[4], p[5]);
+    place_agent(A, p[0], p[1], p[2], p[3], p[4], p[5], (args.flags & kFlagWeatherAll) != 0);
     store_agent(args.st, a, A);
 }
 
@@ -2493,7 +2518,7 @@ __global__ void __launch_bounds__(32 * NW) full_obs_kernel(const FullObsArgs f) 
             case 4: e = gn / kSceneHalf; break;
             case 5: e = vbx / 10.f; break;
             case 6: e = vby / 10.f; break;
-            case 7: e = (float)pc / 3.f; break;
+            case 7: e = weather_level(pc, f.weather_all != 0); break;
             case 8: e = sc == 0 ? 1.f : 0.f; break;
             case 9: e = sc == 1 ? 1.f : 0.f; break;
             case 10: e = sc == 2 ? 1.f : 0.f; break;

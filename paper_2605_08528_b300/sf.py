@@ -27,6 +27,7 @@ FULL_EGO, FULL_KR, FULL_PT, FULL_KV, FULL_NB = 11, 350, 5, 24, 7
 FULL_OBS_DIM = FULL_EGO + FULL_KR * FULL_PT + FULL_KV * FULL_NB   # 1929
 FLAG_INVINCIBLE, FLAG_AUTO_RESET, FLAG_RECORD_INDICES = 1, 2, 4
 DYN_VEHICLE, DYN_BICYCLE = 0, 1
+WEATHER_TABLE, WEATHER_ALL = 0, 1
 ACT_NONE, ACT_ELU, ACT_SILU, ACT_TANH = 0, 1, 2, 3
 
 
@@ -40,14 +41,14 @@ class sf_config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("flags", C.c_int32), ("warps_per_block", C.c_int32),
                 ("pack_agents", C.c_int32), ("stage_bytes", C.c_int32), ("split_step", C.c_int32),
                 ("dynamics", C.c_int32), ("world_begin", C.c_int32), ("world_end", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("weather_model", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class sf_roads(C.Structure):
     _fields_ = [("num_worlds", C.c_int32), ("num_polylines", C.c_int32), ("num_points", C.c_int32),
                 ("agent_off", C.c_void_p), ("poly_off", C.c_void_p), ("point_off", C.c_void_p),
                 ("poly_type", C.c_void_p), ("px", C.c_void_p), ("py", C.c_void_p), ("precip", C.c_void_p),
-                ("surface", C.c_void_p)]
+                ("surface", C.c_void_p), ("film_mm", C.c_void_p)]
 
 
 class sf_outputs(C.Structure):
@@ -139,9 +140,9 @@ def sf_version() -> str:
 
 
 def sf_create(seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0, stage_bytes=0, split_step=0,
-              dynamics=DYN_VEHICLE, world_range=(0, 0)):
+              dynamics=DYN_VEHICLE, world_range=(0, 0), weather_model=WEATHER_TABLE):
     cfg = sf_config(seed, flags, warps_per_block, pack_agents, stage_bytes, split_step, dynamics,
-                    int(world_range[0]), int(world_range[1]))
+                    int(world_range[0]), int(world_range[1]), int(weather_model))
     h = C.c_void_p()
     st = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().sf_create(C.byref(cfg), C.c_void_p(st), C.byref(h)))
@@ -160,9 +161,11 @@ def sf_load_roads(h, scene):
                 px=np.ascontiguousarray(scene.px, np.float32), py=np.ascontiguousarray(scene.py, np.float32),
                 precip=np.ascontiguousarray(scene.precip, np.uint8),
                 surface=np.ascontiguousarray(scene.surface, np.uint8))
+    film = getattr(scene, "film_mm", None)
+    arrs["film_mm"] = None if film is None else np.ascontiguousarray(film, np.float32)
     r = sf_roads(len(arrs["agent_off"]) - 1, len(arrs["poly_type"]), len(arrs["px"]),
                  *[_ptr(arrs[k]) for k in ("agent_off", "poly_off", "point_off", "poly_type", "px", "py", "precip",
-                                           "surface")])
+                                           "surface", "film_mm")])
     _check(lib().sf_load_roads(h, C.byref(r)), h)
 
 
@@ -284,12 +287,12 @@ class World:
     """A handle plus its roads, with torch views of the library-owned outputs."""
 
     def __init__(self, scene, seed=0, flags=0, warps_per_block=0, stream=None, pack_agents=0, stage_bytes=0,
-                 split_step=0, dynamics=DYN_VEHICLE, world_range=(0, 0)):
+                 split_step=0, dynamics=DYN_VEHICLE, world_range=(0, 0), weather_model=WEATHER_TABLE):
         import torch
         self.torch = torch
         self.scene = scene
         self.h = sf_create(seed, flags, warps_per_block, stream, pack_agents, stage_bytes, split_step, dynamics,
-                           world_range)
+                           world_range, weather_model)
         sf_load_roads(self.h, scene)
         self.A = sf_num_agents(self.h)
         self.W = sf_num_worlds(self.h)

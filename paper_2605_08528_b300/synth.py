@@ -31,7 +31,8 @@ class Scene:
     px: np.ndarray          # float32 [NPt]
     py: np.ndarray          # float32 [NPt]
     precip: np.ndarray      # uint8 [A]  0 dry, 1 light rain, 2 heavy rain, 3 snow
-    surface: np.ndarray     # uint8 [A]  0 asphalt, 1 concrete, 2 gravel
+    surface: np.ndarray     # uint8 [A]  0 asphalt, 1 concrete, 2 gravel (ALL model: 0 AC, 1 SMA, 2 OGFC)
+    film_mm: np.ndarray = None   # float32 [A] water film [mm] (the ALL weather model only)
 
     @property
     def num_worlds(self) -> int:
@@ -304,3 +305,21 @@ def subscene(scene: Scene, worlds):
         rows.extend(range(a0, a1))
     rows = np.asarray(rows, int)
     return _assemble(polys, counts, scene.precip[rows], scene.surface[rows]), rows
+
+
+def with_water_films(scene: Scene, seed: int, h_max: float = 1.2) -> Scene:
+    """The scene with the ALL weather model's inputs (Sec. 3.3, App. B): a road
+    surface 0 AC, 1 SMA, 2 OGFC and a water film depth uniform in [0, h_max] mm
+    per agent (h_max 1.2 mm spans dry road to full aquaplaning)."""
+    rng = np.random.default_rng(seed)
+    A = scene.num_agents
+    out = Scene(scene.agent_off, scene.poly_off, scene.point_off, scene.poly_type, scene.px, scene.py,
+                scene.precip, rng.integers(0, 3, A).astype(np.uint8),
+                (rng.random(A) * h_max).astype(np.float32))
+    return out
+
+
+def film_code(film_mm) -> np.ndarray:
+    """The water film in hundredths of a millimetre, held to 2.55 mm, as the
+    library stores it in the agent's weather byte (and the oracle's precip column)."""
+    return np.minimum(255, np.rint(np.asarray(film_mm, np.float64) * 100.0)).astype(np.int32)

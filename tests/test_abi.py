@@ -52,3 +52,9 @@ def test_world_range_is_validated_before_any_device_call():
         with pytest.raises(sf.SFError) as e:
             sf.sf_create(world_range=bad)
         assert e.value.status == sf.SF_ERR_INVALID_ARG, bad
+
+
+def test_weather_model_is_validated_before_any_device_call():
+    with pytest.raises(sf.SFError) as e:
+        sf.sf_create(weather_model=2)
+    assert e.value.status == sf.SF_ERR_INVALID_ARG
