@@ -396,31 +396,6 @@ __device__ __forceinline__ void publish(Exch& E, int lane, const Agent& A, float
     E.gx[lane] = A.gx; E.gy[lane] = A.gy;
 }
 
-// K nearest alive other agents (lexicographic (d^2, index) order); local lane ids
-// over the slots [base, base + n) of the lane's own world
-__device__ __forceinline__ void knn_agents(const Exch& E, int base, int n, int lane, uint32_t alive_bits, float px,
-                                           float py, int nb[kK]) {
-    float key[kK];
-#pragma unroll
-    for (int t = 0; t < kK; ++t) { key[t] = kInf; nb[t] = -1; }
-    for (int j = base; j < base + n; ++j) {
-        if (j == lane || !((alive_bits >> j) & 1u)) continue;
-        const float d2 = norm2(E.px[j] - px, E.py[j] - py);
-        if (!(d2 < key[kK - 1])) continue;
-        float ck = d2;
-        int ci = j;
-        bool ins = false;
-#pragma unroll
-        for (int t = 0; t < kK; ++t) {
-            if (ins || ck < key[t]) {
-                float tk = key[t]; key[t] = ck; ck = tk;
-                int ti = nb[t]; nb[t] = ci; ci = ti;
-                ins = true;
-            }
-        }
-    }
-}
-
 __device__ __forceinline__ void load_agent(const DevState& st, int a, Agent& A) {
     float4 p = st.pos[a], q = st.quat[a], v = st.vel[a], w = st.angv[a], s = st.spin[a], g = st.goal[a];
     A.px = p.x; A.py = p.y; A.pz = p.z; A.dl = p.w;
@@ -1541,11 +1516,111 @@ struct Nbr {
     float hx[32], hy[32];     // heading of each slot for the observation (after respawns)
 };
 
+// The K nearest alive agents of every alive slot in `todo` (lexicographic
+// (d^2, index) order, the order of knn_agents) and, with coll, the footprint
+// overlaps of the collision event (App. G: SAT of the slot's footprint against
+// every alive partner within the cull distance): one (slot, partner) pair per
+// thread.  Phase 1 writes the squared distances into D[slot][partner] (inf for
+// no partner) and sets bit i of *coll on an overlap; phase 2 counts each
+// partner's rank among its slot's partners and writes the partners of rank < K
+// to N.nb (every neighbour of a todo slot is written, -1 past the partners).
+// Positions and headings come from the exchange area.
+__device__ __forceinline__ void pairs_knn(const Exch& E, Nbr& N, float (*D)[32], const int* s_slot_w,
+                                          const int* s_wbase, const int* s_wn, int m, uint32_t alive_bits,
+                                          uint32_t todo, unsigned* coll, int tid, int nthreads) {
+    for (int p = tid; p < m * 32; p += nthreads) {
+        const int i = p >> 5, jj = p & 31;
+        if (!((todo >> i) & 1u)) continue;
+        if (jj < kK) N.nb[i][jj] = -1;
+        const int wl = s_slot_w[i], base = s_wbase[wl], n = s_wn[wl];
+        if (jj >= n) continue;
+        const int j = base + jj;
+        float d2 = kInf;
+        if (j != i && ((alive_bits >> i) & 1u) && ((alive_bits >> j) & 1u)) {
+            d2 = norm2(E.px[j] - E.px[i], E.py[j] - E.py[i]);
+            if (coll && d2 <= kPairCull2) {
+                float nx, ny;
+                if (sat2d(E.px[i], E.py[i], E.hx[i], E.hy[i], E.px[j], E.py[j], E.hx[j], E.hy[j], nx, ny) > 0.f)
+                    atomicOr(coll, 1u << i);
+            }
+        }
+        D[i][jj] = d2;
+    }
+    __syncthreads();
+    for (int p = tid; p < m * 32; p += nthreads) {
+        const int i = p >> 5, jj = p & 31;
+        if (!((todo >> i) & 1u)) continue;
+        const int wl = s_slot_w[i], n = s_wn[wl];
+        if (jj >= n) continue;
+        const float dj = D[i][jj];
+        if (!(dj < kInf)) continue;
+        int rank = 0;
+        for (int kk = 0; kk < n; ++kk) {
+            const float dk = D[i][kk];
+            rank += (dk < dj || (dk == dj && kk < jj)) ? 1 : 0;
+        }
+        if (rank < kK) N.nb[i][rank] = (int8_t)(s_wbase[wl] + jj);
+    }
+}
+
+// K nearest alive other agents (lexicographic (d^2, index) order); local lane ids
+// over the slots [base, base + n) of the lane's own world
+__device__ __forceinline__ void knn_agents(const Exch& E, int base, int n, int lane, uint32_t alive_bits, float px,
+                                           float py, int nb[kK]) {
+    float key[kK];
+#pragma unroll
+    for (int t = 0; t < kK; ++t) { key[t] = kInf; nb[t] = -1; }
+    for (int j = base; j < base + n; ++j) {
+        if (j == lane || !((alive_bits >> j) & 1u)) continue;
+        const float d2 = norm2(E.px[j] - px, E.py[j] - py);
+        if (!(d2 < key[kK - 1])) continue;
+        float ck = d2;
+        int ci = j;
+        bool ins = false;
+#pragma unroll
+        for (int t = 0; t < kK; ++t) {
+            if (ins || ck < key[t]) {
+                float tk = key[t]; key[t] = ck; ck = tk;
+                int ti = nb[t]; nb[t] = ci; ci = ti;
+                ins = true;
+            }
+        }
+    }
+}
+
+
+// The same answers as pairs_knn for a block of one warp, a lane per slot:
+// the lane's K nearest alive agents into N.nb[lane], and whether its footprint
+// overlaps an alive agent's (the same squared distances and SAT tests, so the
+// same results bit for bit)
+__device__ __forceinline__ bool lanes_knn(const Exch& E, int base, int n, int lane, uint32_t alive_bits, bool alive,
+                                          bool coll, Nbr& N) {
+    int nb[kK];
+    bool collided = false;
+    knn_agents(E, base, n, lane, alive_bits, E.px[lane], E.py[lane], nb);
+    if (!alive) {
+#pragma unroll
+        for (int t = 0; t < kK; ++t) nb[t] = -1;
+    }
+    if (coll && alive) {
+        for (int j = base; j < base + n && !collided; ++j) {
+            if (j == lane || !((alive_bits >> j) & 1u)) continue;
+            if (norm2(E.px[j] - E.px[lane], E.py[j] - E.py[lane]) > kPairCull2) continue;
+            float nx, ny;
+            if (sat2d(E.px[lane], E.py[lane], E.hx[lane], E.hy[lane], E.px[j], E.py[j], E.hx[j], E.hy[j], nx, ny) > 0.f)
+                collided = true;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kK; ++t) N.nb[lane][t] = (int8_t)nb[t];
+    return collided;
+}
+
 // events and rewards (App. G), first part, lanes of the agent warp: lane terms,
 // off-road, idle, the 8 nearest agents (into N.nb); returns the partial reward
 __device__ __forceinline__ float lanes_events_a(const Slot& c, int lane, Agent& A, bool alive, float prevx,
-                                                float prevy, float hx, float hy, uint32_t alive_bits, const AgentQ* qp,
-                                                const Exch& E, int (&nb)[kK], uint32_t& ev, Nbr& N) {
+                                                float prevy, float hx, float hy, const AgentQ* qp, int (&nb)[kK],
+                                                uint32_t& ev, const Nbr& N) {
     float r = 0.f;
     if (alive) {
         const AgentQ q = *qp;
@@ -1560,10 +1635,9 @@ __device__ __forceinline__ float lanes_events_a(const Slot& c, int lane, Agent& 
         }
         if (fabsf(q.lat) > kOffroadLat || q.dist > kOffroadDist) { ev |= kEvOffroad; r -= kWOffroad; }
         if (speed < kIdleSpeed) { ev |= kEvIdle; r -= kWIdle; }
-        knn_agents(E, c.base, c.n, lane, alive_bits, A.px, A.py, nb);
-    }
 #pragma unroll
-    for (int t = 0; t < kK; ++t) N.nb[lane][t] = (int8_t)nb[t];
+        for (int t = 0; t < kK; ++t) nb[t] = N.nb[lane][t];   // the 8 nearest agents (pairs_knn)
+    }
     return r;
 }
 
@@ -1582,12 +1656,11 @@ __device__ __forceinline__ void pairs_ttc_drac(const Exch& E, Nbr& N, int m, int
 
 // events and rewards, second part: TTC / DRAC penalties, collision, edge,
 // sparse events; done agents are marked for a respawn (auto-reset) or parked
-__device__ __forceinline__ void lanes_events_b(const WorldArgs& args, const Slot& c, int lane, Agent& A, bool& alive,
-                                               bool nonfin, float hx, float hy, uint32_t alive_bits,
-                                               const AgentQ* qp, const Exch& E, const int (&nb)[kK],
+// (coll_bits: the footprint overlaps found by pairs_knn, bit per slot)
+__device__ __forceinline__ void lanes_events_b(const WorldArgs& args, int lane, Agent& A, bool& alive, bool nonfin,
+                                               uint32_t coll_bits, const AgentQ* qp, const int (&nb)[kK],
                                                float (&tt)[kK], float r, const Nbr& N, uint32_t& ev, float& reward,
                                                float& drac, bool& done, bool& respawn, bool& parked_now) {
-    const int base = c.base, n = c.n;
     if (alive) {
         const AgentQ q = *qp;
         float tmin = kTtcMax, dmax = 0.f;
@@ -1604,14 +1677,7 @@ __device__ __forceinline__ void lanes_events_b(const WorldArgs& args, const Slot
         r -= kWDrac * fmaxf(0.f, dmax - kDracThresh);
         drac = dmax;
         A.peak = fmaxf(A.peak, dmax);
-        bool collided = false;
-        for (int j = base; j < base + n && !collided; ++j) {
-            if (j == lane || !((alive_bits >> j) & 1u)) continue;
-            float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
-            if (norm2(dx, dy) > kPairCull2) continue;
-            float nx, ny;
-            if (sat2d(A.px, A.py, hx, hy, E.px[j], E.py[j], E.hx[j], E.hy[j], nx, ny) > 0.f) collided = true;
-        }
+        const bool collided = (coll_bits >> lane) & 1u;
         if (collided && A.step > kWarmup) ev |= kEvCollision;
         if (q.tedge < kInf) r -= penalty(kTtcAlphaE, q.tedge, kTtcPmaxE);
         if (q.forb) ev |= kEvLaneForb;
@@ -1752,14 +1818,10 @@ __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot&
     }
 }
 
-// neighbours of the final observation (lanes of the agent warp): recomputed
-// after a respawn in the world; the tables get each slot's heading
-__device__ __forceinline__ void lanes_final_a(const Slot& c, int lane, const Agent& A, bool recompute,
-                                              uint32_t alive_bits, const Exch& E, int (&nb)[kK], float hx, float hy,
-                                              Nbr& N) {
-    if (recompute) knn_agents(E, c.base, c.n, lane, alive_bits, A.px, A.py, nb);
-#pragma unroll
-    for (int t = 0; t < kK; ++t) N.nb[lane][t] = (int8_t)nb[t];
+// the final observation's neighbour tables get each slot's heading (lanes of
+// the agent warp); the neighbours of the worlds that changed are recomputed
+// by pairs_knn, and every lane then takes its row back into nb
+__device__ __forceinline__ void lanes_final_a(int lane, float hx, float hy, Nbr& N) {
     N.hx[lane] = hx;
     N.hy[lane] = hy;
 }
@@ -1868,6 +1930,8 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     __shared__ int s_staged;
     __shared__ float s_sp[kSpawnRows][kSpawnDraws];   // spawn candidates drawn ahead (kDraw)
     __shared__ int s_spawn[32];                   // spawn candidate slot of each respawned slot, -1: none
+    __shared__ float s_d2[32][32];                // squared distances of the slot pairs (pairs_knn)
+    __shared__ unsigned s_coll;                   // footprint overlap per slot (the collision event)
     extern __shared__ __align__(128) unsigned char s_blob[];
     // with spare warps, warps 1..NW-1 draw the spawn candidates of every slot
     // while warp 0 runs the physics (a step) or right after the masks (a reset),
@@ -1950,9 +2014,22 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
         if (warp == 0) {
             lanes_physics<PHYS>(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E, act);
             const unsigned ab = __ballot_sync(kFull, alive);
-            if (lane == 0) s_alive = ab;
+            unsigned cb = 0u;
+            if (NW == 1) {                            // a lane per slot: the per-lane forms
+                __syncwarp();
+                cb = __ballot_sync(kFull, lanes_knn(E, c.base, c.n, lane, ab, alive, true, N));
+            }
+            if (lane == 0) { s_alive = ab; s_coll = cb; }
         }
         __syncthreads();
+        // ---------------- neighbours, footprint overlaps, TTC and DRAC at the end-of-physics
+        // poses (all threads, pair-parallel)
+        if (NW > 1) {
+            const uint32_t slots = m >= 32 ? 0xFFFFFFFFu : ((1u << m) - 1u);
+            pairs_knn(E, N, s_d2, s_slot_w, s_wbase, s_wn, m, s_alive, slots, &s_coll, threadIdx.x, 32 * NW);
+            __syncthreads();
+        }
+        pairs_ttc_drac(E, N, m, threadIdx.x, 32 * NW);
         if (s_staged) {
             stg = stage_wait(&s_bar, args.wait_ns ? args.wait_ns : kStageWaitNs);
             if (!stg) atomicOr(args.out.error_word, 2u);
@@ -1975,15 +2052,12 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
             if (lane == 0) Q[j] = q;
         }
         __syncthreads();
-        // ---------------- events and rewards (App. G): lanes, pairs, lanes
-        float r = 0.f;
-        if (warp == 0) r = lanes_events_a(c, lane, A, alive, prevx, prevy, hx, hy, s_alive, &Q[lane], E, nb, ev, N);
-        __syncthreads();
-        pairs_ttc_drac(E, N, m, threadIdx.x, 32 * NW);
-        __syncthreads();
-        if (warp == 0)
-            lanes_events_b(args, c, lane, A, alive, nonfin, hx, hy, s_alive, &Q[lane], E, nb, tt, r, N, ev, reward,
-                           drac, done, respawn, parked_now);
+        // ---------------- events and rewards (App. G), lanes of the agent warp
+        if (warp == 0) {
+            const float r = lanes_events_a(c, lane, A, alive, prevx, prevy, hx, hy, &Q[lane], nb, ev, N);
+            lanes_events_b(args, lane, A, alive, nonfin, s_coll, &Q[lane], nb, tt, r, N, ev, reward, drac, done,
+                           respawn, parked_now);
+        }
     }
 
     // ---------------- respawns (warp 0, agents in index order), then the post-reset exchange
@@ -2041,18 +2115,28 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     }
     __syncthreads();
 
-    // ---------------- neighbours (warp 0), their rows (all warps), ego group, outputs, state (warp 0)
+    // ---------------- neighbours of the worlds that changed (all threads), their rows (all
+    // warps), ego group, outputs, state (warp 0)
     if (warp == 0) {
         // no copy may outlive the block: after a wait that gave up, wait again
         // (bounded by 1 s whatever the caller's limit) for the copy this block issued
         if (lane == 0 && s_staged && !stg && !args.withhold) stage_wait(&s_bar, kStageWaitNs);
-        lanes_final_a(c, lane, A, recompute, s_alive, E, nb, hx, hy, N);
+        lanes_final_a(lane, hx, hy, N);
+        if (NW == 1 && recompute) lanes_knn(E, c.base, c.n, lane, s_alive, alive, false, N);
         const unsigned rb = __ballot_sync(kFull, recompute);
         if (lane == 0) s_rec = rb;
     }
     __syncthreads();
+    if (NW > 1 && s_rec) {                            // CTA-uniform
+        pairs_knn(E, N, s_d2, s_slot_w, s_wbase, s_wn, m, s_alive, s_rec, nullptr, threadIdx.x, 32 * NW);
+        __syncthreads();
+    }
     pairs_nbr_rows(args, E, N, a0, m, s_alive, s_rec, s_act, threadIdx.x, 32 * NW);
     if (warp != 0) return;
+    if (recompute) {
+#pragma unroll
+        for (int t = 0; t < kK; ++t) nb[t] = N.nb[lane][t];
+    }
     lanes_final_b<MODE>(args, c, lane, A, alive, active, &Q[lane], nb, hx, hy, ev, reward, done, drac, respawn);
 }
 
@@ -2133,7 +2217,8 @@ __global__ void __launch_bounds__(32 * NWE) events_kernel(const WorldArgs args) 
     __shared__ Exch E;
     __shared__ Nbr N;
     __shared__ int s_slot_w[32], s_wbase[32], s_wn[32];
-    __shared__ unsigned s_alive, s_rec;
+    __shared__ unsigned s_alive, s_rec, s_coll;
+    __shared__ float s_d2[32][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int4 pk = __ldg(&args.packs[blockIdx.x]);
     const int m = pk.w;
@@ -2160,15 +2245,25 @@ __global__ void __launch_bounds__(32 * NWE) events_kernel(const WorldArgs args) 
         }
         publish(E, lane, A, hx, hy);
         alive_bits = __ballot_sync(kFull, alive);
-        __syncwarp();
-        r = lanes_events_a(c, lane, A, alive, prevx, prevy, hx, hy, alive_bits, args.sc.q + c.a, E, nb, ev, N);
+        unsigned cb = 0u;
+        if (NWE == 1) {                               // a lane per slot: the per-lane forms
+            __syncwarp();
+            cb = __ballot_sync(kFull, lanes_knn(E, c.base, c.n, lane, alive_bits, alive, true, N));
+        }
+        if (lane == 0) { s_alive = alive_bits; s_coll = cb; }
     }
     __syncthreads();
+    if (NWE > 1) {                                    // pair-parallel over the block's warps
+        const uint32_t slots = m >= 32 ? 0xFFFFFFFFu : ((1u << m) - 1u);
+        pairs_knn(E, N, s_d2, s_slot_w, s_wbase, s_wn, m, s_alive, slots, &s_coll, threadIdx.x, 32 * NWE);
+        __syncthreads();
+    }
     pairs_ttc_drac(E, N, m, threadIdx.x, 32 * NWE);
     __syncthreads();
     if (warp == 0) {
-        lanes_events_b(args, c, lane, A, alive, nonfin, hx, hy, alive_bits, args.sc.q + c.a, E, nb, tt, r, N, ev,
-                       reward, drac, done, respawn, parked_now);
+        r = lanes_events_a(c, lane, A, alive, prevx, prevy, hx, hy, args.sc.q + c.a, nb, ev, N);
+        lanes_events_b(args, lane, A, alive, nonfin, s_coll, args.sc.q + c.a, nb, tt, r, N, ev, reward, drac, done,
+                       respawn, parked_now);
         lanes_respawn(args, c, lane, A, alive, respawn, ev, E);
         const unsigned chg = __ballot_sync(kFull, respawn || parked_now);
         const uint32_t wmask = c.n >= 32 ? 0xFFFFFFFFu : (((1u << c.n) - 1u) << c.base);
@@ -2183,13 +2278,22 @@ __global__ void __launch_bounds__(32 * NWE) events_kernel(const WorldArgs args) 
             args.sc.flag[c.a] = (respawn || parked_now) ? 2 : 0;
             if (respawn || parked_now) args.sc.fix_list[atomicAdd(args.sc.fix_count, 1u)] = c.a;
         }
-        lanes_final_a(c, lane, A, recompute, alive_now, E, nb, hx, hy, N);
+        lanes_final_a(lane, hx, hy, N);
+        if (NWE == 1 && recompute) lanes_knn(E, c.base, c.n, lane, alive_now, alive, false, N);
         const unsigned rb = __ballot_sync(kFull, recompute);
         if (lane == 0) { s_alive = alive_now; s_rec = rb; }
     }
     __syncthreads();
+    if (NWE > 1 && s_rec) {                           // CTA-uniform
+        pairs_knn(E, N, s_d2, s_slot_w, s_wbase, s_wn, m, s_alive, s_rec, nullptr, threadIdx.x, 32 * NWE);
+        __syncthreads();
+    }
     pairs_nbr_rows(args, E, N, pk.z, m, s_alive, s_rec, 0xFFFFFFFFu, threadIdx.x, 32 * NWE);
     if (warp != 0) return;
+    if (recompute) {
+#pragma unroll
+        for (int t = 0; t < kK; ++t) nb[t] = N.nb[lane][t];
+    }
     lanes_final_b<kModeStep>(args, c, lane, A, alive, true, args.sc.q + c.a, nb, hx, hy, ev, reward, done, drac,
                              respawn);
 }
