@@ -235,6 +235,24 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, p
                 e2e_obs_wall=e2e_obs_wall, d2h_obs=A * (5 + sf.OBS_DIM * 4))
 
 
+def time_mlp_forward(m, rows, torch, sf, stream, reps=20):
+    """Mean time [ms] of one forward of MLP m over `rows` rows of 30 inputs
+    (CUDA events on the MLP's stream after a warm-up; the surrogate MLP of the
+    step alone, for the phase-level comparison with the physics)."""
+    with torch.cuda.stream(stream):
+        x = torch.randn((rows, sf.SURR_IN), device="cuda")
+        y = torch.empty((rows, sf.SURR_OUT), device="cuda")
+        for _ in range(3):
+            sf.sf_mlp_forward(m, x, rows, y)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            sf.sf_mlp_forward(m, x, rows, y)
+        t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / reps
+
+
 def lf_flops(n_road, n_veh):
     """Algorithmic FLOPs of one late-fusion forward (actor and critic, App. E):
     the set encoders on every filled slot, ego, trunk and heads per agent."""
@@ -478,6 +496,19 @@ def main_ours(args):
                                   "observation_ms": r["obs_ms"], "network_ms": r["lf_ms"]}))
             clocks.stop()
             return
+        if name.endswith("+surrogate"):               # profiling target: the surrogate step graph alone
+            from paper_2605_08528_b300 import surrogate as SU
+            base = name[:-len("+surrogate")]
+            surr, rows, loss = SU.collect_and_train(make_scene("256x16", rank), transitions=args.surr_rows,
+                                                    train_steps=args.surr_steps, seed=31 + rank, stream=stream)
+            r = run_workload(base, args.steps, args.warmup, rank, torch, sf, stream, e2e=False, nw=args.nw,
+                             surrogate=surr, pack=args.pack, stage=args.stage, split=args.split)
+            sf.sf_surrogate_destroy(surr)
+            if rank == 0:
+                print(json.dumps({"profile_run": name, "ms_per_step": float(r["ms"].mean()), "agents": r["A"],
+                                  "gated_fraction": r["surr_frac"], "training_rows": rows}))
+            clocks.stop()
+            return
         if name == "4096x16+policy":                  # profiling target: the policy + step graph alone
             res[name] = run_workload("4096x16", args.steps, args.warmup, rank, torch, sf, stream, e2e=False,
                                      nw=args.nw, policy_seed=4000, pack=args.pack, stage=args.stage,
@@ -511,6 +542,8 @@ def main_ours(args):
             res[name + "+surrogate"] = run_workload(name, args.steps, args.warmup, rank, torch, sf, stream,
                                                     e2e=False, nw=args.nw, surrogate=surr, pack=args.pack,
                                                     stage=args.stage, split=args.split)
+            surr_info["mlp_forward_ms_" + name] = time_mlp_forward(sf.sf_surrogate_mlp(surr),
+                                                                   res[name + "+surrogate"]["A"], torch, sf, stream)
     if not args.only and not args.skip_policy:
         if world > 1:
             dist.barrier()
@@ -757,8 +790,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--only", default=None,
-                    choices=list(WORKLOADS) + ["ragged1024", "4096x16+policy", "paper256x16", "paper4096x16", "ppo"],
-                    help="profiling: run one workload only (paper*: the full-observation + late-fusion loop; "
+                    choices=list(WORKLOADS) + ["ragged1024", "4096x16+policy", "256x16+surrogate", "4096x16+surrogate",
+                                               "paper256x16", "paper4096x16", "ppo"],
+                    help="profiling: run one workload only (*+surrogate: a surrogate trained with --surr-rows / "
+                         "--surr-steps, then its step graph; paper*: the full-observation + late-fusion loop; "
                          "ppo: the on-device PPO leg)")
     ap.add_argument("--profile-update", action="store_true",
                     help="with --only ppo: one iteration, its update bracketed by cudaProfilerStart / Stop")
