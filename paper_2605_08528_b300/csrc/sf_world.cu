@@ -559,6 +559,18 @@ __device__ __forceinline__ unsigned long long warp_sort32(unsigned long long v, 
         }
     return v;
 }
+// merge a sorted running top-32 with 32 new (unsorted) candidates; returns the 32 smallest, sorted
+__device__ __forceinline__ unsigned long long merge32(unsigned long long run, unsigned long long cand, int lane) {
+    cand = warp_sort32(cand, lane);
+    unsigned long long m = umin64(run, shfl64(cand, 31 - lane));   // bitonic, holds the 32 smallest
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        unsigned long long o = shfl_xor64(m, j);
+        m = (lane & j) == 0 ? umin64(m, o) : umax64(m, o);
+    }
+    return m;
+}
+
 // The smallest 32 of the unique keys buf[0, cnt), cnt <= 64, by rank: a key's
 // rank is the number of held keys below it, and the keys of rank < 32 are
 // written back to buf at their rank, so buf[0, min(cnt, 32)) ends ascending.
@@ -820,17 +832,66 @@ __device__ __forceinline__ unsigned long long held_key(unsigned long long* buf, 
     return k;
 }
 
+// The running selection of the 32 smallest candidate keys of one warp, in one
+// of two forms with the same result (the 32 smallest, ascending, lane t
+// holding the t-th): RANK keeps them in the warp's buffer and ranks them
+// (fewer dependent steps: for blocks whose warps wait on one another), else
+// every 32 collected are merged bitonically into a running top-32 in
+// registers (fewer instructions: for grids of independent warps that fill the
+// issue slots).
+template <bool RANK>
+struct Sel32 {
+    unsigned long long* buf;
+    unsigned lt;
+    int lane, cnt;
+    bool sorted;
+    unsigned long long run;
+    __device__ __forceinline__ Sel32(unsigned long long* b, int l)
+        : buf(b), lt((1u << l) - 1u), lane(l), cnt(0), sorted(true), run(kKeyInf) {}
+    __device__ __forceinline__ void add(unsigned long long key, unsigned long long& thr) {
+        if constexpr (RANK) {
+            collect_keys(key, lane, lt, buf, cnt, thr, sorted);
+        } else {
+            const unsigned mk = __ballot_sync(kFull, key != kKeyInf);
+            if (key != kKeyInf) buf[cnt + __popc(mk & lt)] = key;
+            cnt += __popc(mk);
+            __syncwarp();
+            if (cnt >= 32) {
+                run = merge32(run, buf[lane], lane);
+                const unsigned long long rest = lane < cnt - 32 ? buf[32 + lane] : kKeyInf;
+                __syncwarp();
+                if (lane < cnt - 32) buf[lane] = rest;
+                cnt -= 32;
+                thr = umin64(thr, shfl64(run, 31));
+                __syncwarp();
+            }
+        }
+    }
+    // lane t's key of the t-th smallest; full: 32 were found
+    __device__ __forceinline__ unsigned long long result(bool& full) {
+        if constexpr (RANK) {
+            const unsigned long long k = held_key(buf, cnt, sorted, lane);
+            full = cnt == 32;
+            return k;
+        } else {
+            if (cnt > 0) run = merge32(run, lane < cnt ? buf[lane] : kKeyInf, lane);
+            __syncwarp();
+            full = shfl64(run, 31) != kKeyInf;
+            return run;
+        }
+    }
+};
+
 // the 32 nearest road points (all types), exact; lane t returns the t-th key.
 // Only points closer than R compete; if fewer than 32 are, R grows.
 // buf: 64 keys of shared memory owned by the calling warp.
+template <bool RANK>
 __device__ unsigned long long coop_knn32(const WRoads& v, float qx, float qy, float R, int lane,
                                          unsigned long long* buf) {
-    const unsigned lt = (1u << lane) - 1u;
     for (;;) {
         const Rows w = rows_covering(v, qx, qy, R);
         unsigned long long thr = w.all ? kKeyInf : key_of(R * R * (1.f - 1e-5f), 0);
-        int cnt = 0;
-        bool sorted = true;
+        Sel32<RANK> sel(buf, lane);
         scan_cells(v, w, lane, [&](const float4& P, uint32_t m, int i, bool has) {
             unsigned long long key = kKeyInf;
             if (has) {
@@ -838,10 +899,11 @@ __device__ unsigned long long coop_knn32(const WRoads& v, float qx, float qy, fl
                 key = rkey(norm2(dx, dy), m, i);
                 if (key >= thr) key = kKeyInf;
             }
-            collect_keys(key, lane, lt, buf, cnt, thr, sorted);
+            sel.add(key, thr);
         });
-        const unsigned long long run = held_key(buf, cnt, sorted, lane);
-        if (cnt == 32 || w.all) return run;
+        bool full;
+        const unsigned long long run = sel.result(full);
+        if (full || w.all) return run;
         R *= kGrow;
     }
 }
@@ -853,10 +915,10 @@ __device__ unsigned long long coop_knn32(const WRoads& v, float qx, float qy, fl
 // radius held enough candidates, else that query is redone alone with a
 // growing radius (coop_knn32 / coop_nearest_lane).  Returns the lane; lane t
 // of the warp gets the t-th nearest point's key in *key.
+template <bool RANK>
 __device__ Lane coop_point_queries(const WRoads& v, float qx, float qy, float gx, float gy, float hx, float hy,
                                    float R32, float Rl, int lane, unsigned long long* buf, bool* forb,
                                    unsigned long long* key) {
-    const unsigned lt = (1u << lane) - 1u;
     const float S = fmaxf(fmaxf(Rl + kSegReach, kCircD + kCircR + kEdgeHalfWidth + kSegReach), R32);
     const Rows w = rows_covering(v, qx, qy, S);
     const float Rle = S - kSegReach;                  // every lane segment within Rle is seen
@@ -864,8 +926,8 @@ __device__ Lane coop_point_queries(const WRoads& v, float qx, float qy, float gx
     unsigned long long thr = w.all ? kKeyInf : key_of(R32 * R32 * (1.f - 1e-5f), 0);
     unsigned long long best = kKeyInf;
     float4 brec = make_float4(0.f, 0.f, 0.f, 0.f);
-    bool f = false, sorted = true;
-    int cnt = 0;
+    bool f = false;
+    Sel32<RANK> sel(buf, lane);
     scan_cells(v, w, lane, [&](const float4& sg, uint32_t m, int i, bool has) {
         unsigned long long k = kKeyInf;
         if (has) {
@@ -882,13 +944,14 @@ __device__ Lane coop_point_queries(const WRoads& v, float qx, float qy, float gx
                 }
             }
         }
-        collect_keys(k, lane, lt, buf, cnt, thr, sorted);
+        sel.add(k, thr);
     });
-    const unsigned long long run = held_key(buf, cnt, sorted, lane);
+    bool full;
+    const unsigned long long run = sel.result(full);
     *forb = __any_sync(kFull, f);
     best = warp_min_rec(best, brec);
     // too few points within R32: the 32 nearest alone, from a larger radius
-    *key = (cnt == 32 || w.all) ? run : coop_knn32(v, qx, qy, R32 * kGrow, lane, buf);
+    *key = (full || w.all) ? run : coop_knn32<RANK>(v, qx, qy, R32 * kGrow, lane, buf);
     if (best == kKeyInf && !w.all)                   // no lane within Rle: the nearest lane alone
         return coop_nearest_lane(v, qx, qy, gx, gy, Rle * kGrow, lane);
     return lane_of(v, best, brec, qx, qy, gx, gy);
@@ -1412,6 +1475,7 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
 // kSpawnLaneR (the query still grows its radius until the answer is exact).
 constexpr float kSpawnLaneR = 1.0f;
 
+template <bool RANK>
 __device__ __forceinline__ void agent_road_block(const WRoads& v, bool alive, bool need, float px, float py,
                                                  float gx, float gy, float hx, float hy, float* hnt, int lane,
                                                  unsigned long long* kbuf, float* orow, int32_t* knn_row, Lane* L,
@@ -1425,7 +1489,7 @@ __device__ __forceinline__ void agent_road_block(const WRoads& v, bool alive, bo
         }
         const float r32 = need ? kKnnR0 : hint_radius(hnt, 0, px, py, kKnnR0);
         __syncwarp();
-        key = coop_knn32(v, px, py, r32, lane, kbuf);
+        key = coop_knn32<RANK>(v, px, py, r32, lane, kbuf);
         const unsigned long long last = shfl64(key, 31);
         if (lane == 0) {
             hnt[0] = last != kKeyInf ? sqrtf(key_d2(last)) : 0.f;
@@ -1446,13 +1510,14 @@ __device__ __forceinline__ void agent_road_block(const WRoads& v, bool alive, bo
 // observation's road-point block, written to orow, indices to knn_row), then
 // the edge ray; hv holds the agent's hints, which are updated through hnt.
 // Returns the events' answers (every lane).
+template <bool RANK>
 __device__ __forceinline__ AgentQ agent_step_queries(const WRoads& v, float px, float py, float gx, float gy, float hx,
                                                      float hy, float vx, float vy, const float (&hv)[4], float* hnt,
                                                      int lane, unsigned long long* kbuf, float* orow,
                                                      int32_t* knn_row) {
     bool forb = false;
     unsigned long long key = kKeyInf;
-    const Lane L = coop_point_queries(v, px, py, gx, gy, hx, hy, hint_radius(hv, 0, px, py, kKnnR0),
+    const Lane L = coop_point_queries<RANK>(v, px, py, gx, gy, hx, hy, hint_radius(hv, 0, px, py, kKnnR0),
                                       hint_radius(hv, 1, px, py, kLaneR0), lane, kbuf, &forb, &key);
     // the observation's point records are fetched while the edge ray runs
     float4 prec = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -2045,7 +2110,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
             float* hnt = args.out.hint + 4 * (size_t)(a0 + j);
             const float4 h4 = *reinterpret_cast<const float4*>(hnt);
             const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
-            const AgentQ q = agent_step_queries(
+            const AgentQ q = agent_step_queries<true>(
                 v, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j], E.vx[j], E.vy[j], hv, hnt, lane, kbuf[warp],
                 args.out.obs + (size_t)(a0 + j) * kObsDim + kObsEgo + kK * kObsNbr,
                 (args.flags & kFlagRecord) ? args.out.knn_pts + (size_t)(a0 + j) * kL : nullptr);
@@ -2107,7 +2172,7 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
             spawn_road_block(args.rd.spawnq + slot, v, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j], hnt,
                              lane, orow, krow, &L);
         else
-            agent_road_block(v, al, need, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j], hnt, lane,
+            agent_road_block<true>(v, al, need, E.px[j], E.py[j], E.gx[j], E.gy[j], E.hx[j], E.hy[j], hnt, lane,
                              kbuf[warp], orow, krow, &L, MODE == kModeObserve ? kLaneR0 : kSpawnLaneR);
         if (al && need && lane == 0) {
             Q[j].seg = L.seg; Q[j].dist = L.dist; Q[j].lat = L.lat; Q[j].tx = L.tx; Q[j].ty = L.ty;
@@ -2204,7 +2269,7 @@ __global__ void __launch_bounds__(32 * NWQ, 32 / NWQ) query_kernel(const WorldAr
     const DevGrid g = args.rd.grid[wid];
     const WRoads v = view_of(g, args.rd.blob + g.blob);
     const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
-    const AgentQ q = agent_step_queries(v, p.x, p.y, goal.x, goal.y, h.x, h.y, vel.x, vel.y, hv, hnt, lane,
+    const AgentQ q = agent_step_queries<false>(v, p.x, p.y, goal.x, goal.y, h.x, h.y, vel.x, vel.y, hv, hnt, lane,
                                         kbuf[warp], orow, krow);
     if (lane == 0) args.sc.q[a] = q;
 }
@@ -2321,7 +2386,7 @@ __global__ void __launch_bounds__(32 * NWQ) fix_kernel(const WorldArgs args) {
         const float4 p = args.st.pos[a], goal = args.st.goal[a];
         const float2 h = args.sc.head[a];
         Lane L;
-        agent_road_block(v, true, true, p.x, p.y, goal.x, goal.y, h.x, h.y, args.out.hint + 4 * (size_t)a, lane,
+        agent_road_block<false>(v, true, true, p.x, p.y, goal.x, goal.y, h.x, h.y, args.out.hint + 4 * (size_t)a, lane,
                          kbuf[warp], orow, krow, &L, kSpawnLaneR);
         if (lane == 0) {
             float* ego = args.out.obs + (size_t)a * kObsDim;
@@ -2551,7 +2616,7 @@ __global__ void __launch_bounds__(256) spawn_table_kernel(const DevRoads rd, con
     const DevGrid g = rd.grid[cand_world[c]];
     const WRoads v = view_of(g, rd.blob + g.blob);
     const float4 p = rd.pt[rd.cands[c]];
-    const unsigned long long key = coop_knn32(v, p.x, p.y, kKnnR0, lane, kbuf[warp]);
+    const unsigned long long key = coop_knn32<false>(v, p.x, p.y, kKnnR0, lane, kbuf[warp]);
     __syncwarp();
     const Lane L = coop_nearest_lane_raw(v, p.x, p.y, kSpawnLaneR, lane);
     const unsigned long long last = shfl64(key, 31);
