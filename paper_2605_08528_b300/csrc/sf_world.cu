@@ -177,7 +177,9 @@ __device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, f
     const float ux = R[0][2], uy = R[1][2], uz = R[2][2];
     const float inv_uz = uz > kUzMin ? 1.f / uz : 0.f;   // shared by the four rays
 
-    // 3. suspension rays from the hardpoints along -u to the plane z = 0
+    // 3. suspension rays from the hardpoints along -u to the plane z = 0.  The
+    // four wheels are computed without branches and a wheel whose ray misses
+    // selects zeros, so that the wheels' dependency chains interleave
     float N[4], rcx[4], rcy[4], rcz[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -187,21 +189,20 @@ __device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, f
         float rbx = R[0][0] * bx + R[0][1] * by + R[0][2] * bz;
         float rby = R[1][0] * bx + R[1][1] * by + R[1][2] * bz;
         float rbz = R[2][0] * bx + R[2][1] * by + R[2][2] * bz;
-        N[i] = 0.f; rcx[i] = rcy[i] = rcz[i] = 0.f;
-        if (uz > kUzMin) {
-            float az = (A.pz + A.dpz) + rbz;
-            float t = __fmul_rn(az, inv_uz);              // rounded on its own (never fused)
-            float l = t - kWheelR;
-            if (l < kRest) {
-                float x = kRest - fmaxf(l, 0.f);
-                float wrz = A.wx * rby - A.wy * rbx;            // (w x rb).z
-                float xdot = __fmul_rn(-(A.vz + wrz), inv_uz);
-                // the damper engages over the first kDampRamp of compression:
-                // the normal force is continuous at touchdown
-                N[i] = fmaxf(0.f, kKSusp * x + kCSusp * xdot * fminf(1.f, x / kDampRamp));
-                rcx[i] = rbx - t * ux; rcy[i] = rby - t * uy; rcz[i] = rbz - t * uz;
-            }
-        }
+        float az = (A.pz + A.dpz) + rbz;
+        float t = __fmul_rn(az, inv_uz);                  // rounded on its own (never fused)
+        float l = t - kWheelR;
+        const bool hit = uz > kUzMin && l < kRest;
+        float x = kRest - fmaxf(l, 0.f);
+        float wrz = A.wx * rby - A.wy * rbx;                // (w x rb).z
+        float xdot = __fmul_rn(-(A.vz + wrz), inv_uz);
+        // the damper engages over the first kDampRamp of compression:
+        // the normal force is continuous at touchdown
+        const float Ni = fmaxf(0.f, kKSusp * x + kCSusp * xdot * fminf(1.f, x / kDampRamp));
+        N[i] = hit ? Ni : 0.f;
+        rcx[i] = hit ? rbx - t * ux : 0.f;
+        rcy[i] = hit ? rby - t * uy : 0.f;
+        rcz[i] = hit ? rbz - t * uz : 0.f;
     }
 
     // 4. predicted velocities
@@ -245,13 +246,14 @@ __device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, f
     float sp2[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        sp2[i] = sp[i];
-        if (!(N[i] > 0.f)) continue;
+        // an unloaded wheel (or one whose forward direction has no planar part)
+        // selects a zero impulse: the sums below then add +0, which changes no
+        // sum that starts at +0, exactly as if the wheel were skipped
         const float c = i < 2 ? cd : 1.f, s = i < 2 ? sd : 0.f;
         float fwx = R[0][0] * c + R[0][1] * s;
         float fwy = R[1][0] * c + R[1][1] * s;
         const float fl2 = norm2(fwx, fwy);
-        if (!(fl2 > 0.f)) continue;
+        const bool ok = N[i] > 0.f && fl2 > 0.f;
         const float rfl = rsqrtf(fl2);
         float elx = __fmul_rn(fwx, rfl), ely = __fmul_rn(fwy, rfl);
         float etx = -ely, ety = elx;
@@ -275,12 +277,12 @@ __device__ __forceinline__ void body_substep(Agent& A, float thr, float dstar, f
         const float j2 = norm2(jl, jt);
         float sc = j2 <= __fmul_rn(cap, cap) ? 1.f : __fmul_rn(cap, rsqrtf(j2));   // friction circle
         jl *= sc; jt *= sc;
-        float Jx = jl * elx + jt * etx, Jy = jl * ely + jt * ety;
+        float Jx = ok ? jl * elx + jt * etx : 0.f, Jy = ok ? jl * ely + jt * ety : 0.f;
         Px += Jx; Py += Jy;
         Lmx += -rcz[i] * Jy;
         Lmy += rcz[i] * Jx;
         Lmz += rcx[i] * Jy - rcy[i] * Jx;
-        sp2[i] = sp[i] - jl * kWheelR * kInvWheelI;
+        sp2[i] = ok ? sp[i] - jl * kWheelR * kInvWheelI : sp[i];
     }
     const float bf = h * brk * kTauBrkF * kInvWheelI, br = h * brk * kTauBrkR * kInvWheelI;
 #pragma unroll
