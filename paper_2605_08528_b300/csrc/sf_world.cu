@@ -385,7 +385,6 @@ struct Exch {
     // partners above it; the pair list and each pair's force (fx, fy, tz)
     int poff[32];
     uint32_t pmask[32];
-    float bud[32];            // each agent's displacement budget for the control step
     int plist[kMaxPairs];
     float4 pf[kMaxPairs];
 };
@@ -1315,11 +1314,43 @@ __host__ __device__ inline int phys_of(const WorldArgs& a) {
     return a.dynamics == 1 ? kPhysBicycle : (a.surr_mode != 0 ? kPhysSurrogate : kPhysVehicle);
 }
 
+// contact culling (lanes_physics): the distance an agent may move in a control
+// step, and whether slot j is a contact candidate of slot i (i's view: the
+// sums in this order, so that every kernel evaluating it rounds alike)
+__device__ __forceinline__ float cull_budget(float vx, float vy, float T) {
+    return __fmaf_rn(sqrtf(norm2(vx, vy)), T, 1.f);
+}
+__device__ __forceinline__ bool cull_near(float pxi, float pyi, float bi, float pxj, float pyj, float bj) {
+    const float reach = kPairCullR + bi + bj + 0.01f;
+    return norm2(pxj - pxi, pyj - pyi) <= __fmul_rn(reach, reach);
+}
+
+// every slot's contact candidates (the s = 0 set of lanes_physics), one slot
+// per warp at a time over warps w0, w0 + nwarps, ...; lane l holds slot l's
+// start-of-step position and budget
+__device__ __forceinline__ void pairs_near(const int4& pk, const int* s_slot_w, const int* s_wbase, const int* s_wn,
+                                           int w0, int nwarps, int lane, float px, float py, float budget,
+                                           unsigned* s_near) {
+    for (int i = w0; i < pk.w; i += nwarps) {
+        const float bi = __shfl_sync(kFull, budget, i);
+        const float pxi = __shfl_sync(kFull, px, i), pyi = __shfl_sync(kFull, py, i);
+        const int wl = s_slot_w[i];
+        const int base = s_wbase[wl], n = s_wn[wl];
+        const bool hit = lane >= base && lane < base + n && lane != i && cull_near(pxi, pyi, bi, px, py, budget);
+        const unsigned mask = __ballot_sync(kFull, hit);
+        if (lane == 0) s_near[i] = mask;
+    }
+}
+
 template <int PHYS>
 // act: the lane's raw actions (throttle, steer, brake), loaded by the caller
+// pre_near: every slot's contact candidates, written by other warps of the
+// block, which arrive on named barrier 2 (bar_threads threads with this warp)
+// when they are; nullptr: this warp computes them
 __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot& c, int lane, Agent& A, bool& alive,
                                               bool& nonfin, float& prevx, float& prevy, float& hx, float& hy,
-                                              Exch& E, float3 act) {
+                                              Exch& E, float3 act, const unsigned* pre_near = nullptr,
+                                              int bar_threads = 0) {
     const DevState& st = args.st;
     const int a = c.a, base = c.base, n = c.n;
     float thr = 0.f, dstar = 0.f, brk = 0.f;
@@ -1352,8 +1383,12 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
     // at +0 is never -0).  A lane that exceeds its budget rebuilds the set as
     // all pairs of its world for the remaining substeps.
     const float T = args.h * args.substeps;
-    const float budget = sqrtf(A.vx * A.vx + A.vy * A.vy) * T + 1.f;
+    const float budget = cull_budget(A.vx, A.vy, T);
     uint32_t near = 0u;
+    if (pre_near) {
+        named_bar_sync(2, bar_threads);
+        near = c.has ? pre_near[lane] : 0u;
+    }
     bool wide = false;
     for (int s = 0; s < args.substeps; ++s) {
         float sx_, sy_;
@@ -1363,15 +1398,16 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
         __syncwarp();
         if (PHYS == kPhysSurrogate && s == 0 && args.surr_mode != 0)
             gated = surr_gate(E, base, n, lane, alive_bits, A, args.h * args.substeps);
-        if (s == 0) {
-            E.bud[lane] = budget;
-            __syncwarp();
+        if (s == 0 && !pre_near) {
+            // every slot of the pack in turn (a warp-uniform count), its position and
+            // budget by shuffles
+            const int jend = __reduce_max_sync(kFull, (uint32_t)(base + n));
 #pragma unroll 4
-            for (int j = base; j < base + n; ++j) {
-                if (j == lane) continue;
-                const float reach = kPairCullR + budget + E.bud[j] + 0.01f;
-                const float dx = E.px[j] - A.px, dy = E.py[j] - A.py;
-                if (norm2(dx, dy) <= reach * reach) near |= 1u << j;
+            for (int j = 0; j < jend; ++j) {
+                const float bj = __shfl_sync(kFull, budget, j);
+                const float pxj = __shfl_sync(kFull, A.px, j), pyj = __shfl_sync(kFull, A.py, j);
+                if (j >= base && j < base + n && j != lane && cull_near(A.px, A.py, budget, pxj, pyj, bj))
+                    near |= 1u << j;
             }
         }
         if (!wide && __any_sync(kFull, alive && A.dpx * A.dpx + A.dpy * A.dpy > budget * budget)) wide = true;
@@ -1387,15 +1423,17 @@ __device__ __forceinline__ void lanes_physics(const WorldArgs& args, const Slot&
         // is no pair, and the forces stay +0 (the body step below is the only one,
         // so its rounding is the same whichever way a substep goes)
         if (__any_sync(kFull, mine != 0u)) {
+            // exclusive prefix sum of the pair counts (at most 31, five bits) over the
+            // lanes: one ballot per bit, all independent
             const int pc = __popc(mine);
-            int poff = pc;
+            const uint32_t lt = (1u << lane) - 1u;
+            int poff = 0, npairs = 0;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(kFull, poff, o);
-                if (lane >= o) poff += t;
+            for (int b = 0; b < 5; ++b) {
+                const uint32_t bb = __ballot_sync(kFull, (pc >> b) & 1);
+                poff += __popc(bb & lt) << b;
+                npairs += __popc(bb) << b;
             }
-            const int npairs = __shfl_sync(kFull, poff, 31);
-            poff -= pc;
             if (npairs <= kMaxPairs) {
                 E.poff[lane] = poff;
                 E.pmask[lane] = mine;
@@ -1999,11 +2037,14 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     __shared__ int s_spawn[32];                   // spawn candidate slot of each respawned slot, -1: none
     __shared__ float s_d2[32][32];                // squared distances of the slot pairs (pairs_knn)
     __shared__ unsigned s_coll;                   // footprint overlap per slot (the collision event)
+    __shared__ unsigned s_near[32];               // contact candidates of each slot (kDraw, step)
     extern __shared__ __align__(128) unsigned char s_blob[];
     // with spare warps, warps 1..NW-1 draw the spawn candidates of every slot
     // while warp 0 runs the physics (a step) or right after the masks (a reset),
     // so that the in-order respawns only pick among them
     constexpr bool kDraw = NW >= 4 && MODE != kModeObserve;
+    // and, before the draws of a step, every slot's contact candidates (vehicle physics)
+    constexpr bool kNear = kDraw && MODE == kModeStep && PHYS != kPhysBicycle;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int4 pk = __ldg(&args.packs[blockIdx.x]);   // (first world, worlds, first agent, agents)
     const int a0 = pk.z, m = pk.w;
@@ -2043,7 +2084,15 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
             stage_issue(args.rd.blob, s_grid, s_woff, pk.y, stage_total, s_blob, &s_bar, lane, args.withhold != 0);
         if (kDraw && MODE == kModeStep) named_bar_arrive(1, 32 * NW);   // the pack tables are written
     } else if (kDraw && MODE == kModeStep) {
+        // the contact candidates for warp 0's physics, then the spawn draws
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
+        if (kNear) { p = args.st.pos[a0 + (lane < m ? lane : 0)]; v = args.st.vel[a0 + (lane < m ? lane : 0)]; }
         named_bar_sync(1, 32 * NW);
+        if (kNear) {
+            pairs_near(pk, s_slot_w, s_wbase, s_wn, warp - 1, NW - 1, lane, p.x, p.y,
+                       cull_budget(v.x, v.y, args.h * args.substeps), s_near);
+            named_bar_arrive(2, 32 * NW);
+        }
         draw_spawns(args, pk, s_slot_w, s_wbase, threadIdx.x - 32, 32 * (NW - 1), s_sp);
     }
 
@@ -2079,7 +2128,8 @@ __global__ void __launch_bounds__(32 * NW, (16 / NW > 0 ? 16 / NW : 1)) world_ke
     if (MODE == kModeStep) {
         float prevx = 0.f, prevy = 0.f;
         if (warp == 0) {
-            lanes_physics<PHYS>(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E, act);
+            lanes_physics<PHYS>(args, c, lane, A, alive, nonfin, prevx, prevy, hx, hy, E, act,
+                                kNear ? s_near : nullptr, 32 * NW);
             const unsigned ab = __ballot_sync(kFull, alive);
             unsigned cb = 0u;
             if (NW == 1) {                            // a lane per slot: the per-lane forms
