@@ -1878,9 +1878,10 @@ __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot&
         // the group's slots in order: each takes the first try at least the spacing
         // away from every eligible agent, else the first of the largest clearance;
         // the eligible agents are the alive ones of its world, without the slots
-        // still waiting to respawn.  Lane s0 + k holds try k of the g-th slot and
-        // takes that try's clearance over the eligible positions; two ballots
-        // (and a maximum) then pick the try as the sequential rule would.
+        // still waiting to respawn.  Lane s0 + k holds try k of the g-th slot; the
+        // tries are broadcast, lane j takes eligible agent j's squared distance to
+        // each, and one warp minimum per try gives its clearance (a minimum of
+        // squared distances >= +0: exact in any order, ordered like its bits).
         int g = 0;
         for (uint32_t gg = group; gg; gg &= gg - 1u, ++g) {
             const int l = __ffs(gg) - 1;
@@ -1890,21 +1891,24 @@ __device__ __forceinline__ void lanes_respawn(const WorldArgs& args, const Slot&
             const uint32_t later = l < 31 ? (rbits & (0xFFFFFFFFu << (l + 1))) : 0u;
             const uint32_t elig = __ballot_sync(kFull, alive) & wm & ~(1u << l) & ~later;
             const int s0 = g * kSpawnTries;
-            const bool own = lane >= s0 && lane < s0 + kSpawnTries;
-            float dk = kInf;
-            if (own)
-                for (uint32_t em = elig; em; em &= em - 1u) {
-                    const int j = __ffs(em) - 1;
-                    dk = fminf(dk, norm2(E.px[j] - x, E.py[j] - y));
-                }
-            const unsigned clear = __ballot_sync(kFull, own && dk >= kSpawnSpacing * kSpawnSpacing);
-            int src;
-            if (clear) {
-                src = __ffs(clear) - 1;                  // the first try clear of every agent
-            } else {                                     // the first try of the largest clearance
-                const unsigned best = __reduce_max_sync(kFull, own ? __float_as_uint(dk) : 0u);
-                src = __ffs(__ballot_sync(kFull, own && __float_as_uint(dk) == best)) - 1;
+            const bool me = (elig >> lane) & 1u;
+            const float ex = E.px[lane], ey = E.py[lane];
+            unsigned dk[kSpawnTries];
+#pragma unroll
+            for (int k = 0; k < kSpawnTries; ++k) {
+                const float tx = __shfl_sync(kFull, x, s0 + k), ty = __shfl_sync(kFull, y, s0 + k);
+                dk[k] = __reduce_min_sync(kFull, me ? __float_as_uint(norm2(ex - tx, ey - ty)) : __float_as_uint(kInf));
             }
+            const unsigned kClear = __float_as_uint(kSpawnSpacing * kSpawnSpacing);
+            int pick = -1;
+            unsigned best = 0u;
+            int bk = 0;
+#pragma unroll
+            for (int k = 0; k < kSpawnTries; ++k) {
+                if (pick < 0 && dk[k] >= kClear) pick = k;   // the first try clear of every agent
+                if (dk[k] > best) { best = dk[k]; bk = k; }  // else the first of the largest clearance
+            }
+            const int src = s0 + (pick >= 0 ? pick : bk);
             const float bx = __shfl_sync(kFull, x, src), by = __shfl_sync(kFull, y, src);
             const float bpsi = __shfl_sync(kFull, psi, src), bv = __shfl_sync(kFull, v0, src);
             const float bgx = __shfl_sync(kFull, gx, src), bgy = __shfl_sync(kFull, gy, src);
