@@ -197,6 +197,17 @@ std::vector<int4> make_packs(const std::vector<int4>& world, const std::vector<D
         else { cur.y += 1; cur.w += n; bytes += b; }
     }
     if (open) packs.push_back(cur);
+    // blocks longest first: the block scheduler starts them in index order as
+    // earlier ones finish, so the costliest packs do not start last (a block's
+    // results do not depend on when it runs).  Estimated cycles: the physics,
+    // then the road queries of its agents over its warps, each growing with
+    // its world's edge segments (the edge ray tests all of them)
+    auto cost = [&](const int4& p) {
+        double c = 12000.0;
+        for (int w = p.x; w < p.x + p.y; ++w) c += world[w].y * (7000.0 + 10.0 * grid[w].ecnt) / 8.0;
+        return c;
+    };
+    std::stable_sort(packs.begin(), packs.end(), [&](const int4& a, const int4& b) { return cost(a) > cost(b); });
     return packs;
 }
 
