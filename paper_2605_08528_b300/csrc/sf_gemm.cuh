@@ -33,6 +33,18 @@ struct GemmArgs {
     // out on a barrier nothing completes (a test of the timeout path)
     unsigned long long wait_ns;
     int withhold;
+    // fused narrow head (optional; no split K): with head_w set, every row's
+    // activated values, rounded to bf16, are also multiplied by the bf16 head
+    // weights head_w [H][ldhw] (columns 0..N-1 used) and summed over all N
+    // columns; the CTA that owns a row block computes all of its column tiles,
+    // so each row's sum is formed in one fixed order (column tiles in order,
+    // each thread's columns in order, then the two column halves of a tile) and
+    //   head_out[r * ldh + j] = head_act(sum_j + head_b[j]),  j < H <= 4.
+    // The layer's own outputs (out_f32, out_bf16, ...) may be null.
+    const __nv_bfloat16* head_w;
+    const float* head_b;
+    float* head_out;
+    int H, ldhw, ldh, head_act;
 };
 
 cudaError_t sf_gemm_launch(const GemmArgs& g, cudaStream_t s);

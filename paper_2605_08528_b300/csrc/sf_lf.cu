@@ -515,6 +515,21 @@ cudaError_t gemm(sf_lf* m, cudaStream_t st, const __nv_bfloat16* A, const __nv_b
     return sf_gemm_launch(g, st);
 }
 
+// layer C = ELU(A . B^T + bias) [M, N] followed by a linear head of H <= 4 outputs,
+// out[r * H + j] = bias_h[j] + sum_c bf16(C[r, c]) wh[j, c], in the GEMM's epilogue
+cudaError_t gemm_head(sf_lf* m, cudaStream_t st, const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias,
+                      int M, int N, int K, const __nv_bfloat16* wh, const float* bias_h, int H, float* out) {
+    GemmArgs g{};
+    g.A = A; g.B = B; g.bias = bias;
+    g.M = M; g.N = N; g.Nb = N; g.K = K;
+    g.ldc = N; g.ldt = 0;
+    g.act = SF_ACT_ELU;
+    g.bn = N > 64 ? 128 : 64;
+    g.err = m->d_err;
+    g.head_w = wh; g.ldhw = N; g.head_b = bias_h; g.head_out = out; g.H = H; g.ldh = H; g.head_act = SF_ACT_NONE;
+    return sf_gemm_launch(g, st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -629,12 +644,12 @@ sf_status sf_lf_forward_on(sf_lf_handle m, cudaStream_t st, const float* d_obs, 
         e = cudaGetLastError();
     }
     for (int n = 0; n < 2 && e == cudaSuccess; ++n) {
+        if (n == 1 && !d_value) break;   // no value wanted: the critic's trunk is not run
         e = gemm(m, st, m->x[n], m->w[n][2], m->b[n][2], A, 128, 256, SF_ACT_ELU, nullptr, m->t1, 128);
-        if (e == cudaSuccess) e = gemm(m, st, m->t1, m->w[n][3], m->b[n][3], A, 64, 128, SF_ACT_ELU, nullptr, m->t2, 64);
-        if (e == cudaSuccess) {
-            if (n == 0) e = gemm(m, st, m->t2, m->w[0][4], m->b[0][4], A, 3, 64, SF_ACT_NONE, d_mean, nullptr, 3);
-            else if (d_value) e = gemm(m, st, m->t2, m->w[1][4], m->b[1][4], A, 1, 64, SF_ACT_NONE, d_value, nullptr, 1);
-        }
+        // trunk layer 2 with the linear head (3 action means, or the value) in its epilogue
+        if (e == cudaSuccess)
+            e = gemm_head(m, st, m->t1, m->w[n][3], m->b[n][3], A, 64, 128, m->w[n][4], m->b[n][4], n == 0 ? 3 : 1,
+                          n == 0 ? d_mean : d_value);
     }
     if (e == cudaSuccess && d_embed) {
         lf_embed_kernel<<<(A * 512 + 255) / 256, 256, 0, st>>>(m->x[0], m->x[1], A, d_embed);

@@ -313,6 +313,23 @@ cudaError_t gemm(sf_mlp* m, const __nv_bfloat16* A, const __nv_bfloat16* B, cons
     return sf_gemm_launch(g, use_st ? st : m->stream);
 }
 
+// inference with a narrow last layer (at most 4 outputs): that layer runs in the
+// epilogue of the layer before it (the GEMM's fused head), which then stores no
+// activations: C_head = out_act(bf16(act(X W^T + b)) . W_last^T + b_last)
+bool head_fusable(const sf_mlp* m) { return m->L >= 2 && m->dim[m->L] <= 4; }
+
+// layer L - 2 with layer L - 1 as its fused head, into y [B][ldy]
+cudaError_t gemm_head(sf_mlp* m, const __nv_bfloat16* A, int B, float* y, int ldy, cudaStream_t st) {
+    const int l = m->L - 2;
+    GemmArgs g{};
+    g.A = A; g.B = m->wb[l]; g.bias = m->b[l];
+    g.M = B; g.N = m->dim[l + 1]; g.Nb = m->dim[l + 1]; g.K = m->ld[l]; g.ldc = m->ld[l + 1]; g.act = m->hidden_act;
+    g.bn = tile_for(g.N); g.err = m->errw; g.wait_ns = m->wait_ns; g.withhold = m->withhold;
+    g.head_w = m->wb[l + 1]; g.ldhw = m->ld[l + 1]; g.head_b = m->b[l + 1]; g.head_out = y; g.ldh = ldy;
+    g.H = m->dim[m->L]; g.head_act = m->out_act;
+    return sf_gemm_launch(g, st);
+}
+
 cudaError_t ensure_batch(sf_mlp* m, int B) {
     if (B <= m->cap) return cudaSuccess;
     // buffers of a smaller batch stay allocated until destroy; the new set replaces them
@@ -341,8 +358,13 @@ const __nv_bfloat16* xt_in(const sf_mlp* m, int l) { return l == 0 && m->share ?
 cudaError_t forward_core(sf_mlp* m, int B, bool train, float* y_out = nullptr, int ldy = 0,
                          cudaStream_t st = nullptr, bool use_st = false) {
     cudaError_t e = cudaSuccess;
+    const bool fuse = !train && head_fusable(m);
     for (int l = 0; l < m->L && e == cudaSuccess; ++l) {
         const bool last = l == m->L - 1;
+        if (fuse && l == m->L - 2) {
+            e = gemm_head(m, x_in(m, l), B, y_out ? y_out : m->y, y_out ? ldy : m->ld[m->L], use_st ? st : m->stream);
+            break;
+        }
         e = gemm(m, x_in(m, l), m->wb[l], m->b[l], B, m->dim[l + 1], m->dim[l + 1], m->ld[l], act_of(m, l),
                  train ? m->z[l] : nullptr, last ? (y_out ? y_out : m->y) : nullptr, last ? nullptr : m->x[l + 1],
                  (train && !last) ? m->xt[l + 1] : nullptr, (last && y_out) ? ldy : m->ld[l + 1], B, st, use_st);
@@ -570,6 +592,10 @@ sf_status sf_mlp_forward_static(sf_mlp_handle m, const float* d_x, int ldx, int 
     }
     for (int l = 0; l < m->L && e == cudaSuccess; ++l) {
         const bool last = l == m->L - 1;
+        if (head_fusable(m) && l == m->L - 2) {   // the same layer sequence as sf_mlp_forward
+            e = gemm_head(m, xs[l], batch, y, m->ld[m->L], m->stream);
+            break;
+        }
         e = gemm(m, xs[l], m->wb[l], m->b[l], batch, m->dim[l + 1], m->dim[l + 1], m->ld[l], act_of(m, l), nullptr,
                  last ? y : nullptr, last ? nullptr : xs[l + 1], nullptr, m->ld[l + 1], batch);
     }

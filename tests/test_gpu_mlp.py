@@ -28,8 +28,10 @@ def bf16(shape, rng, scale=1.0):
     return t.cuda().contiguous(), t.float().numpy().astype(np.float64)
 
 
+# the last two shapes give every persistent CTA several tiles (both TMEM accumulators reused)
 @pytest.mark.parametrize("M,N,K,tile", [(128, 64, 64, 64), (300, 200, 136, 128), (1000, 512, 320, 256),
-                                        (77, 3, 512, 64), (4096, 256, 64, 256), (129, 130, 8, 128)])
+                                        (77, 3, 512, 64), (4096, 256, 64, 256), (129, 130, 8, 128),
+                                        (20000, 512, 320, 256), (40001, 96, 136, 64)])
 @pytest.mark.parametrize("act", [sf.ACT_NONE, sf.ACT_ELU, sf.ACT_SILU, sf.ACT_TANH])
 def test_gemm_against_fp64(M, N, K, tile, act):
     rng = np.random.default_rng(M * 7 + N + K + act)
@@ -68,7 +70,11 @@ def make_mlp(dims, hidden, out, rng):
     return m, params
 
 
+# outputs of at most 4 run as the fused head of the layer before; at 20,000 rows every
+# persistent CTA computes two or more row blocks (both head-partial buffers reused)
 @pytest.mark.parametrize("dims,hidden,out,batch", [([320, 512, 512, 3], sf.ACT_ELU, sf.ACT_TANH, 1000),
+                                                   ([320, 512, 512, 3], sf.ACT_ELU, sf.ACT_TANH, 20000),
+                                                   ([320, 512, 512, 1], sf.ACT_ELU, sf.ACT_NONE, 777),
                                                    ([30, 256, 256, 256, 16], sf.ACT_SILU, sf.ACT_NONE, 4096)])
 def test_mlp_forward_against_fp64(dims, hidden, out, batch):
     rng = np.random.default_rng(len(dims) + batch)
