@@ -42,6 +42,7 @@ FLUSH_BYTES = 256 << 20
 
 
 RAGGED = (1024, 2000, 0.2)   # worlds, road seed base, per-step reset fraction
+PROFILE_STEPS = False        # --profile-steps: the timed steps bracketed by cudaProfilerStart / Stop
 
 
 def make_scene(name: str, rank: int = 0):
@@ -179,6 +180,8 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, p
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         torch.cuda.synchronize()
+        if PROFILE_STEPS:                                 # an external profiler captures the timed steps only
+            torch.cuda.profiler.start()
         t0 = time.perf_counter()
         for t in range(steps):
             act_cur.copy_(acts[(warmup + t) % ring])      # stage this step's actions (untimed)
@@ -190,6 +193,8 @@ def run_workload(name, steps, warmup, rank, torch, sf, stream, e2e=True, nw=0, p
             ends[t].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        if PROFILE_STEPS:
+            torch.cuda.profiler.stop()
     st = sf.sf_sync(W.h, allow=(sf.SF_ERR_NONFINITE,))
     ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
     surr_used = sf.sf_surrogate_audit(W.h)[1] if surrogate is not None else 0
@@ -797,6 +802,9 @@ def main():
                          "ppo: the on-device PPO leg)")
     ap.add_argument("--profile-update", action="store_true",
                     help="with --only ppo: one iteration, its update bracketed by cudaProfilerStart / Stop")
+    ap.add_argument("--profile-steps", action="store_true",
+                    help="profiling: the timed steps of each leg bracketed by cudaProfilerStart / Stop "
+                         "(for ncu --profile-from-start off)")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling: no end-to-end leg")
     ap.add_argument("--skip-cpu", action="store_true", help="no oracle CPU baseline")
     ap.add_argument("--nw", type=int, default=0, help="warps per block (1, 2, 4, 8; 0 = autotuned)")
@@ -811,6 +819,8 @@ def main():
     ap.add_argument("--surr-rows", type=int, default=10_000_000, help="surrogate training transitions")
     ap.add_argument("--surr-steps", type=int, default=60000, help="surrogate Adam steps")
     args = ap.parse_args()
+    global PROFILE_STEPS
+    PROFILE_STEPS = args.profile_steps
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
