@@ -134,3 +134,80 @@ def forward_loops(params, obs_row, n_road, n_veh):
         z = layer(p["trunk1"], layer(p["trunk0"], z))
         res.append(layer(p["head"], z, act=False))
     return np.array(res[0]), res[1][0]
+
+
+def _elu_grad(z):
+    return np.where(z > 0, 1.0, np.exp(np.minimum(z, 0.0)))
+
+
+def _dense_back(x, W, dz):
+    """Gradients of z = x W^T + b (rows of x summed over): dW, db, dx."""
+    return dz.T @ x, dz.sum(axis=0), dz @ W
+
+
+def gradients(params, obs, n_road, n_veh, dmean, dvalue):
+    """Gradient of L = sum(dmean * mean) + sum(dvalue * value) with respect to
+    every parameter, as a flat vector in the parameter layout (the log_std
+    entries are zero: the forward does not use them).
+
+    Back-propagation through the layers of `forward` in reverse order; the
+    masked max-pool passes each feature's gradient to the valid slot holding
+    the maximum, the first one (lowest slot) when several do (a subgradient:
+    the maximum is not differentiable where slots tie).  A group without a
+    valid slot outputs constant zeros and receives no gradient."""
+    P = unpack(params) if not isinstance(params, dict) else params
+    obs = np.asarray(obs, np.float64)
+    A = obs.shape[0]
+    grads = []
+    for net, g_out in (("actor", np.asarray(dmean, np.float64).reshape(A, -1)),
+                       ("critic", np.asarray(dvalue, np.float64).reshape(A, 1))):
+        p = P[net]
+        G = {}
+        # forward, keeping the pre-activations
+        xe = obs[:, :EGO]
+        a0 = _dense(xe, p["ego0"]); h0 = MO.act(a0, MO.ELU)
+        a1 = _dense(h0, p["ego1"]); ego = MO.act(a1, MO.ELU)
+        sets = []
+        for (l0, l1, lo, hi, F, cnt) in (("road0", "road1", ROAD0, VEH0, PT, n_road),
+                                         ("veh0", "veh1", VEH0, OBS, NB, n_veh)):
+            slots = obs[:, lo:hi].reshape(A, -1, F)
+            K = slots.shape[1]
+            z1 = _dense(slots, p[l0]); h1 = MO.act(z1, MO.ELU)
+            z2 = _dense(h1, p[l1]); h2 = MO.act(z2, MO.ELU)
+            cnt = np.asarray(cnt)
+            valid = np.arange(K)[None, :] < cnt[:, None]
+            masked = np.where(valid[:, :, None], h2, -np.inf)
+            arg = masked.argmax(axis=1)                          # first maximum along the slots
+            pooled = np.where(cnt[:, None] > 0, np.take_along_axis(h2, arg[:, None, :], axis=1)[:, 0, :], 0.0)
+            sets.append((l0, l1, slots, z1, h1, z2, arg, cnt, pooled))
+        x = np.concatenate([ego, sets[0][8], sets[1][8]], axis=1)
+        t0 = _dense(x, p["trunk0"]); u0 = MO.act(t0, MO.ELU)
+        t1 = _dense(u0, p["trunk1"]); u1 = MO.act(t1, MO.ELU)
+        # backward
+        G["head"] = _dense_back(u1, p["head"][0], g_out)
+        dt1 = G["head"][2] * _elu_grad(t1)
+        G["trunk1"] = _dense_back(u0, p["trunk1"][0], dt1)
+        dt0 = G["trunk1"][2] * _elu_grad(t0)
+        G["trunk0"] = _dense_back(x, p["trunk0"][0], dt0)
+        dx = G["trunk0"][2]
+        da1 = dx[:, :64] * _elu_grad(a1)
+        G["ego1"] = _dense_back(h0, p["ego1"][0], da1)
+        da0 = G["ego1"][2] * _elu_grad(a0)
+        G["ego0"] = _dense_back(xe, p["ego0"][0], da0)
+        for (l0, l1, slots, z1, h1, z2, arg, cnt, _), c0 in zip(sets, (64, 160)):
+            K = slots.shape[1]
+            dpool = np.where(cnt[:, None] > 0, dx[:, c0:c0 + 96], 0.0)
+            dh2 = np.zeros((A, K, 96))
+            np.put_along_axis(dh2, arg[:, None, :], dpool[:, None, :], axis=1)
+            dz2 = (dh2 * _elu_grad(z2)).reshape(A * K, 96)
+            W2, W1 = p[l1][0], p[l0][0]
+            dW2, db2, dh1 = _dense_back(h1.reshape(A * K, 96), W2, dz2)
+            dz1 = dh1 * _elu_grad(z1.reshape(A * K, 96))
+            dW1, db1, _ = _dense_back(slots.reshape(A * K, -1), W1, dz1)
+            G[l1] = (dW2, db2)
+            G[l0] = (dW1, db1)
+        for n, o, i in net_layers(net):
+            grads.append(G[n][0].reshape(-1))
+            grads.append(G[n][1].reshape(-1))
+    grads.append(np.zeros(3))
+    return np.concatenate(grads)

@@ -101,3 +101,57 @@ def test_actor_and_critic_are_independent():
     np.testing.assert_array_equal(va, value)
     np.testing.assert_array_equal(mc, mean)
     assert np.abs(ma - mean).max() > 1e-3 and np.abs(vc - value).max() > 1e-3
+
+
+def test_gradients_match_central_differences():
+    """The analytic gradient of L = sum(dmean * mean) + sum(dvalue * value)
+    against central differences of the forward pass, on 20 parameters drawn
+    from every layer of both networks (3 agents: full groups, a partly filled
+    road group, an empty vehicle group)."""
+    n_road, n_veh = [4, 2, 3], [3, 0, 1]
+    P = params(11)
+    obs = observations(12, 3, n_road, n_veh)
+    rng = np.random.default_rng(13)
+    dmean, dvalue = rng.normal(0, 1, (3, 3)), rng.normal(0, 1, 3)
+    G = LF.gradients(P, obs, n_road, n_veh, dmean, dvalue)
+    assert G.shape == P.shape
+
+    def L(q):
+        m, v = LF.forward(q, obs, n_road, n_veh)
+        return float((m * dmean).sum() + (v * dvalue).sum())
+
+    k, checked, expected = 0, 0, 0
+    for net in ("actor", "critic"):
+        for _, o, i in LF.net_layers(net):
+            nw, nb = min(15, o * i), min(5, o)
+            picks = [k + int(t) for t in rng.choice(o * i, nw, replace=False)]
+            picks += [k + o * i + int(t) for t in rng.choice(o, nb, replace=False)]
+            for j in picks:
+                e = 1e-6
+                qp, qm = P.copy(), P.copy()
+                qp[j] += e
+                qm[j] -= e
+                fd = (L(qp) - L(qm)) / (2 * e)
+                assert abs(fd - G[j]) <= 1e-6 + 1e-5 * abs(fd), (net, j, fd, G[j])
+                checked += 1
+            expected += nw + nb
+            k += o * i + o
+    assert checked == expected
+    assert np.all(G[-3:] == 0)
+
+
+def test_gradient_of_a_pool_reaches_only_its_argmax_slot():
+    """A feature's pooled gradient reaches the encoder through one slot: the
+    layer-1 weight gradient of a road encoder vanishes when every valid slot
+    but the maximising ones is changed (their inputs matter to the gradient
+    only through the max)."""
+    n_road, n_veh = [3], [0]
+    P = params(21)
+    obs = observations(22, 1, n_road, n_veh)
+    dmean = np.array([[1.0, -0.5, 0.25]])
+    G = LF.gradients(P, obs, n_road, n_veh, dmean, np.zeros(1))
+    # a copy of the first road slot appended as a fourth (tied) slot changes nothing
+    obs2 = obs.copy()
+    obs2[0, LF.ROAD0 + 3 * LF.PT:LF.ROAD0 + 4 * LF.PT] = obs[0, LF.ROAD0:LF.ROAD0 + LF.PT]
+    G2 = LF.gradients(P, obs2, [4], n_veh, dmean, np.zeros(1))
+    assert np.allclose(G, G2, rtol=0, atol=1e-12)
