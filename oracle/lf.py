@@ -145,7 +145,17 @@ def _dense_back(x, W, dz):
     return dz.T @ x, dz.sum(axis=0), dz @ W
 
 
-def gradients(params, obs, n_road, n_veh, dmean, dvalue):
+def slot_outputs(p, obs, group):
+    """Every slot's encoder output h2 [A, K, 96] of one network's group
+    ("road" or "vehicles"), padded slots included."""
+    obs = np.asarray(obs, np.float64)
+    A = obs.shape[0]
+    l0, l1, lo, hi, F = (("road0", "road1", ROAD0, VEH0, PT) if group == "road" else ("veh0", "veh1", VEH0, OBS, NB))
+    slots = obs[:, lo:hi].reshape(A, -1, F)
+    return MO.act(_dense(MO.act(_dense(slots, p[l0]), MO.ELU), p[l1]), MO.ELU)
+
+
+def gradients(params, obs, n_road, n_veh, dmean, dvalue, arg=None):
     """Gradient of L = sum(dmean * mean) + sum(dvalue * value) with respect to
     every parameter, as a flat vector in the parameter layout (the log_std
     entries are zero: the forward does not use them).
@@ -154,13 +164,16 @@ def gradients(params, obs, n_road, n_veh, dmean, dvalue):
     masked max-pool passes each feature's gradient to the valid slot holding
     the maximum, the first one (lowest slot) when several do (a subgradient:
     the maximum is not differentiable where slots tie).  A group without a
-    valid slot outputs constant zeros and receives no gradient."""
+    valid slot outputs constant zeros and receives no gradient.  arg, when
+    given, fixes that choice: arg[net][group] ([A, 96] slot indices, net 0
+    actor / 1 critic, group 0 road / 1 vehicles) replaces the first maximum
+    (any maximising slot gives a valid subgradient)."""
     P = unpack(params) if not isinstance(params, dict) else params
     obs = np.asarray(obs, np.float64)
     A = obs.shape[0]
     grads = []
-    for net, g_out in (("actor", np.asarray(dmean, np.float64).reshape(A, -1)),
-                       ("critic", np.asarray(dvalue, np.float64).reshape(A, 1))):
+    for ni, (net, g_out) in enumerate((("actor", np.asarray(dmean, np.float64).reshape(A, -1)),
+                                       ("critic", np.asarray(dvalue, np.float64).reshape(A, 1)))):
         p = P[net]
         G = {}
         # forward, keeping the pre-activations
@@ -168,8 +181,8 @@ def gradients(params, obs, n_road, n_veh, dmean, dvalue):
         a0 = _dense(xe, p["ego0"]); h0 = MO.act(a0, MO.ELU)
         a1 = _dense(h0, p["ego1"]); ego = MO.act(a1, MO.ELU)
         sets = []
-        for (l0, l1, lo, hi, F, cnt) in (("road0", "road1", ROAD0, VEH0, PT, n_road),
-                                         ("veh0", "veh1", VEH0, OBS, NB, n_veh)):
+        for gi, (l0, l1, lo, hi, F, cnt) in enumerate((("road0", "road1", ROAD0, VEH0, PT, n_road),
+                                                       ("veh0", "veh1", VEH0, OBS, NB, n_veh))):
             slots = obs[:, lo:hi].reshape(A, -1, F)
             K = slots.shape[1]
             z1 = _dense(slots, p[l0]); h1 = MO.act(z1, MO.ELU)
@@ -177,9 +190,11 @@ def gradients(params, obs, n_road, n_veh, dmean, dvalue):
             cnt = np.asarray(cnt)
             valid = np.arange(K)[None, :] < cnt[:, None]
             masked = np.where(valid[:, :, None], h2, -np.inf)
-            arg = masked.argmax(axis=1)                          # first maximum along the slots
-            pooled = np.where(cnt[:, None] > 0, np.take_along_axis(h2, arg[:, None, :], axis=1)[:, 0, :], 0.0)
-            sets.append((l0, l1, slots, z1, h1, z2, arg, cnt, pooled))
+            am = masked.argmax(axis=1)                           # first maximum along the slots
+            if arg is not None:
+                am = np.where(cnt[:, None] > 0, np.asarray(arg[ni][gi], np.int64), am)
+            pooled = np.where(cnt[:, None] > 0, np.take_along_axis(h2, am[:, None, :], axis=1)[:, 0, :], 0.0)
+            sets.append((l0, l1, slots, z1, h1, z2, am, cnt, pooled))
         x = np.concatenate([ego, sets[0][8], sets[1][8]], axis=1)
         t0 = _dense(x, p["trunk0"]); u0 = MO.act(t0, MO.ELU)
         t1 = _dense(u0, p["trunk1"]); u1 = MO.act(t1, MO.ELU)
@@ -194,11 +209,11 @@ def gradients(params, obs, n_road, n_veh, dmean, dvalue):
         G["ego1"] = _dense_back(h0, p["ego1"][0], da1)
         da0 = G["ego1"][2] * _elu_grad(a0)
         G["ego0"] = _dense_back(xe, p["ego0"][0], da0)
-        for (l0, l1, slots, z1, h1, z2, arg, cnt, _), c0 in zip(sets, (64, 160)):
+        for (l0, l1, slots, z1, h1, z2, am, cnt, _), c0 in zip(sets, (64, 160)):
             K = slots.shape[1]
             dpool = np.where(cnt[:, None] > 0, dx[:, c0:c0 + 96], 0.0)
             dh2 = np.zeros((A, K, 96))
-            np.put_along_axis(dh2, arg[:, None, :], dpool[:, None, :], axis=1)
+            np.put_along_axis(dh2, am[:, None, :], dpool[:, None, :], axis=1)
             dz2 = (dh2 * _elu_grad(z2)).reshape(A * K, 96)
             W2, W1 = p[l1][0], p[l0][0]
             dW2, db2, dh1 = _dense_back(h1.reshape(A * K, 96), W2, dz2)

@@ -155,3 +155,32 @@ def test_gradient_of_a_pool_reaches_only_its_argmax_slot():
     obs2[0, LF.ROAD0 + 3 * LF.PT:LF.ROAD0 + 4 * LF.PT] = obs[0, LF.ROAD0:LF.ROAD0 + LF.PT]
     G2 = LF.gradients(P, obs2, [4], n_veh, dmean, np.zeros(1))
     assert np.allclose(G, G2, rtol=0, atol=1e-12)
+
+
+def test_gradient_with_a_given_maximising_slot():
+    """The slot choice of the max-pool's gradient can be given: the natural
+    choice reproduces the default, and a tied duplicate slot gives the same
+    gradient as the slot it copies."""
+    n_road, n_veh = [3, 2], [2, 1]
+    P = params(31)
+    obs = observations(32, 2, n_road, n_veh)
+    rng = np.random.default_rng(33)
+    dmean, dvalue = rng.normal(0, 1, (2, 3)), rng.normal(0, 1, 2)
+    G = LF.gradients(P, obs, n_road, n_veh, dmean, dvalue)
+    U = LF.unpack(P)
+
+    def first_max(h2, cnts):   # [A, 96] first maximising valid slot per feature
+        K = h2.shape[1]
+        return np.where(np.arange(K)[None, :, None] < np.asarray(cnts)[:, None, None], h2, -np.inf).argmax(axis=1)
+
+    arg = [[first_max(LF.slot_outputs(U[net], obs, grp), cnts)
+            for grp, cnts in (("road", n_road), ("vehicles", n_veh))] for net in ("actor", "critic")]
+    assert np.array_equal(LF.gradients(P, obs, n_road, n_veh, dmean, dvalue, arg=arg), G)
+    # agent 0's road slot 0 duplicated as slot 3: pointing every feature held by slot 0 at slot 3 changes nothing
+    obs2 = obs.copy()
+    obs2[0, LF.ROAD0 + 3 * LF.PT:LF.ROAD0 + 4 * LF.PT] = obs[0, LF.ROAD0:LF.ROAD0 + LF.PT]
+    arg2 = [[a.copy() for a in row] for row in arg]
+    for ni in range(2):
+        arg2[ni][0][0] = np.where(arg[ni][0][0] == 0, 3, arg[ni][0][0])
+    G2 = LF.gradients(P, obs2, [4, 2], n_veh, dmean, dvalue, arg=arg2)
+    assert np.allclose(G2, G, rtol=0, atol=1e-12)
