@@ -735,6 +735,47 @@ sf_status sf_ppo_rollout_ptrs(sf_ppo_handle p, sf_ppo_rollout* out);
 sf_status sf_ppo_loss_grads(sf_ppo_handle p, const float* d_obs, const float* d_small, int rows, float* d_mean,
                             float* d_value, float* d_dmean, float* d_dvalue, float* h_out);
 
+/* PPO on the paper's own network (SceneFactory Alg. 1 with App. E and App. L):
+ * the late-fusion actor-critic `lf` (sf_lf_create) on the full observation
+ * (sf_observe_full), trained in place.  The engine takes lf's current
+ * parameters (their last three, the log standard deviations, start the
+ * policy's), keeps its own fp32 masters with Adam moments and, after every
+ * update, writes the trained weights back into lf's device copies, so that
+ * sf_lf_forward and the next rollout use them (sf_lf_get_params keeps
+ * returning the parameters last set from the host; sf_ppo_lf_params returns
+ * the trained ones).  Per rollout step the engine observes the full
+ * observation and its group counts, runs lf, samples and steps; the rollout
+ * buffers' obs are then [T][A][SF_FULL_OBS_DIM].  Every other part of the
+ * update is the MLP engine's (GAE, the clipped loss, adaptive KL learning
+ * rate, norm clipping, Adam).  The backward of each masked max-pool passes a
+ * feature's gradient to the slot that held the maximum (the lowest slot on
+ * ties) and recomputes that slot's first layer; the weight gradients are
+ * sums in a fixed order, so two runs give bit-identical weights.
+ * Errors: SF_ERR_INVALID_ARG (configuration), SF_ERR_STATE (no roads),
+ * SF_ERR_OOM.  lf must not be used on another stream while the engine runs. */
+sf_status sf_ppo_create_lf(sf_handle h, sf_lf_handle lf, const sf_ppo_config* cfg, sf_ppo_handle* out);
+
+/* Gradient of L = sum(d_dmean * mean) + sum(d_dvalue * value) with respect to
+ * every parameter of the engine's late-fusion network at its current
+ * parameters, for `rows` observation rows (rows % 8 == 0): d_obs
+ * [rows][SF_FULL_OBS_DIM], d_n_road / d_n_veh [rows] int32, d_dmean [rows][3],
+ * d_dvalue [rows]; d_mean [rows][3] / d_value [rows] receive the training
+ * forward's outputs (may be NULL when rows <= the minibatch rows); d_argmax
+ * (may be NULL) [2 groups: road, vehicles][2 networks: actor, critic][rows][96]
+ * uint16 receives the slot each pooled feature's gradient went to (the first
+ * maximising slot as the forward computed it; 0xFFFF for an empty group).  h_grads
+ * [n == sf_lf_num_params()] receives the gradient in sf_lf_set_params' layout
+ * (the three log-std entries zero).  Updates nothing.  Synchronous.
+ * Errors: SF_ERR_INVALID_ARG (an MLP-mode engine, NULL buffers, sizes). */
+sf_status sf_ppo_lf_grads(sf_ppo_handle p, const float* d_obs, const int32_t* d_n_road, const int32_t* d_n_veh,
+                          int rows, const float* d_dmean, const float* d_dvalue, float* d_mean, float* d_value,
+                          uint16_t* d_argmax, float* h_grads, size_t n);
+
+/* The late-fusion engine's trained parameters in sf_lf_set_params' layout,
+ * log standard deviations included (h_params [n == sf_lf_num_params()]).
+ * Synchronous. */
+sf_status sf_ppo_lf_params(sf_ppo_handle p, float* h_params, size_t n);
+
 /* Number of agents and worlds of the loaded roads (0 before sf_load_roads). */
 int32_t sf_num_agents(sf_handle h);
 int32_t sf_num_worlds(sf_handle h);

@@ -311,8 +311,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const bool live = r < args.M;
                 const int rows_valid = min(32, args.M - r0);
                 // staged (coalesced) stores when rows are 16-byte aligned; else one element at a time
-                const bool vf = args.ldc % 4 == 0 && ((reinterpret_cast<uintptr_t>(out_f32) |
-                                                      reinterpret_cast<uintptr_t>(args.pre)) & 15) == 0;
+                const int ldp = args.ldp ? args.ldp : args.ldc;
+                const bool vf = args.ldc % 4 == 0 && (reinterpret_cast<uintptr_t>(out_f32) & 15) == 0;
+                const bool vp = ldp % 4 == 0 && (reinterpret_cast<uintptr_t>(args.pre) & 15) == 0;
                 const bool vb = args.ldc % 8 == 0 && (reinterpret_cast<uintptr_t>(args.out_bf16) & 15) == 0;
 #pragma unroll 1
                 for (int c = part; c < BN / 32; c += kParts) {
@@ -344,12 +345,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     const size_t row = (size_t)r * args.ldc + nb;
                     if (args.pre) {
-                        if (full && vf) {
-                            stage_store_f32(stg, v, args.pre + (size_t)r0 * args.ldc + nb, args.ldc, rows_valid, lane);
+                        if (full && vp) {
+                            stage_store_f32(stg, v, args.pre + (size_t)r0 * ldp + nb, ldp, rows_valid, lane);
                         } else if (live) {
+                            const size_t prow = (size_t)r * ldp + nb;
 #pragma unroll
                             for (int k = 0; k < 32; ++k)
-                                if (nb + k < args.N) args.pre[row + k] = v[k];
+                                if (nb + k < args.N) args.pre[prow + k] = v[k];
                         }
                     }
                     activate32(v, args.act);

@@ -20,6 +20,7 @@ struct GemmArgs {
     __nv_bfloat16* out_bf16_t;// [N, ldt] transposed or null
     int M, N, Nb, K;
     int ldc, ldt;
+    int ldp;                  // row stride of pre (0: ldc)
     int act;
     int bn;                   // tile width 64, 128 or 256
     unsigned* err;            // device error word (SF_GEMM_TIMEOUT)

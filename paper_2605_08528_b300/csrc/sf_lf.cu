@@ -68,6 +68,9 @@ constexpr int kOffMeta = kOffPool + kG * kHid * 4;  // 106496: u32 [kMaxGroups] 
 constexpr int kOffMisc = kOffMeta + kMaxGroups * 4; // 112128
 constexpr int kMiscBytes = 1024;
 constexpr int kSmemBytes = kOffMisc + kMiscBytes + 1024;   // 114176: two CTAs per SM
+// the training variant pools 64-bit keys (value, then the lowest slot) after the misc area
+constexpr int kOffPool64 = kOffMisc + kMiscBytes;            // u64 [kG][96]
+constexpr int kSmemBytesTrain = kOffPool64 + kG * kHid * 8 + 1024;   // one CTA per SM
 constexpr uint32_t kTmemCols = 256;                 // D1 at column 0 (96), D2 at column 128 (128)
 
 struct SetArgs {
@@ -77,10 +80,18 @@ struct SetArgs {
     int num_agents;
     const uint4* wimg;         // 2 x kImgBytes: actor then critic weight images (bf16, swizzled)
     const float* b2;           // [2][96] layer-2 biases (layer-1 biases are in the images)
-    __nv_bfloat16* xa;         // [A][ldx] actor trunk input
+    __nv_bfloat16* xa;         // [A][ldx] actor trunk input (may be null in the training variant)
     __nv_bfloat16* xc;         // [A][ldx] critic trunk input
     int ldx, xoff;             // columns [xoff, xoff + 96) receive the pooled embedding
     unsigned* err;
+    // training variant only: per network n (actor 0, critic 1), the fp32 pooled
+    // embedding xf + n * xf_net [A][ldxf] (columns xoff..), the pooled
+    // pre-activation maximum pmax + n * A * 96 and its slot amax (0xFFFF: empty group)
+    float* xf;
+    size_t xf_net;
+    int ldxf;
+    float* pmax;
+    uint16_t* amax;
 };
 
 __device__ __forceinline__ uint32_t fkey(float f) {   // order-preserving float -> u32 (0 is below every key)
@@ -160,13 +171,17 @@ __device__ __forceinline__ bool gather_row(const SetArgs& a, const uint32_t* met
     return true;
 }
 
-// Two CTAs per SM; even CTAs run the actor's encoder, odd ones the critic's.
-__global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
+// Two CTAs per SM (one in the training variant); even CTAs run the actor's
+// encoder, odd ones the critic's.  The training variant also keeps, for every
+// pooled feature, the slot that holds the maximum (the lowest one on ties).
+template <bool TRAIN>
+__global__ void __launch_bounds__(kThreads, TRAIN ? 1 : 2) lf_set_kernel(const SetArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(sm);
     uint32_t* pool = reinterpret_cast<uint32_t*>(sm + kOffPool);
+    unsigned long long* pool64 = reinterpret_cast<unsigned long long*>(sm + kOffPool64);   // TRAIN only
     uint32_t* meta = reinterpret_cast<uint32_t*>(sm + kOffMeta);
     int* rs = reinterpret_cast<int*>(sm + kOffMisc);                       // [kG + 1] item row starts (x8)
     int* cnt = reinterpret_cast<int*>(sm + kOffMisc + 640);               // [kG] filled slots per agent
@@ -181,7 +196,10 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
     const uint4* img = a.wimg + (size_t)net * (kImgBytes / 16);
     for (int i = tid; i < kImgBytes / 16; i += kThreads) reinterpret_cast<uint4*>(sm)[i] = __ldg(img + i);
     for (int i = tid; i < kHid; i += kThreads) sb2[i] = __ldg(a.b2 + net * kHid + i);
-    for (int i = tid; i < kG * kHid; i += kThreads) pool[i] = 0u;
+    for (int i = tid; i < kG * kHid; i += kThreads) {
+        if (TRAIN) pool64[i] = 0ull;
+        else pool[i] = 0u;
+    }
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -311,11 +329,18 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
                 const int f = 32 * q + lane;
                 int cur = -1;                            // agent of the running max
                 float m = -INFINITY;
+                int msl = 0;                             // TRAIN: the slot of the running max
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int s = (int)((md[i] >> 8) & 0xFFu), valid = (int)(md[i] & 0xFFu);
                     if (s != cur) {                      // warp-uniform: the group starts the next agent
-                        if (cur >= 0 && cur < kG) atomicMax(&pool[cur * kHid + f], fkey(m));
+                        if (cur >= 0 && cur < kG) {
+                            if (TRAIN)
+                                atomicMax(&pool64[cur * kHid + f],
+                                          ((unsigned long long)fkey(m) << 32) | (unsigned long long)(0xFFFF - msl));
+                            else
+                                atomicMax(&pool[cur * kHid + f], fkey(m));
+                        }
                         cur = s;
                         m = -INFINITY;
                     }
@@ -324,13 +349,26 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
                     float x[8];
 #pragma unroll
                     for (int k = 0; k < 8; ++k) x[k] = __uint_as_float(v[k]);
-                    if (valid < 8) {                     // warp-uniform: the agent's last, partly filled group
+                    if (TRAIN) {                         // slots in increasing order: strict > keeps the first maximum
+                        const int slot0 = (int)(md[i] >> 16);
 #pragma unroll
-                        for (int k = 1; k < 8; ++k) x[k] = k < valid ? x[k] : x[0];
+                        for (int k = 0; k < 8; ++k)
+                            if (k < valid && x[k] > m) { m = x[k]; msl = slot0 + k; }
+                    } else {
+                        if (valid < 8) {                 // warp-uniform: the agent's last, partly filled group
+#pragma unroll
+                            for (int k = 1; k < 8; ++k) x[k] = k < valid ? x[k] : x[0];
+                        }
+                        m = max3f(max3f(m, x[0], x[1]), max3f(x[2], x[3], x[4]), max3f(x[5], x[6], x[7]));
                     }
-                    m = max3f(max3f(m, x[0], x[1]), max3f(x[2], x[3], x[4]), max3f(x[5], x[6], x[7]));
                 }
-                if (cur >= 0 && cur < kG) atomicMax(&pool[cur * kHid + f], fkey(m));   // continues past these rows
+                if (cur >= 0 && cur < kG) {              // continues past these rows
+                    if (TRAIN)
+                        atomicMax(&pool64[cur * kHid + f],
+                                  ((unsigned long long)fkey(m) << 32) | (unsigned long long)(0xFFFF - msl));
+                    else
+                        atomicMax(&pool[cur * kHid + f], fkey(m));
+                }
             }
             tc_before();   // this tile's TMEM reads before the next tile's barrier and MMAs
         }
@@ -340,10 +378,23 @@ __global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
         // ---- the item's pooled embeddings: + bias, ELU, bf16 into the trunk inputs
         for (int i = tid; i < na * kHid; i += kThreads) {
             const int al = i / kHid, col = i - al * kHid;
-            const uint32_t k = pool[i];
-            pool[i] = 0u;
-            const float y = k ? elu(funkey(k) + sb2[col]) : 0.f;
-            X[(size_t)(a0 + al) * a.ldx + a.xoff + col] = __float2bfloat16_rn(y);
+            if (TRAIN) {
+                const unsigned long long k = pool64[i];
+                pool64[i] = 0ull;
+                const float pm = k ? funkey((uint32_t)(k >> 32)) : 0.f;
+                const float y = k ? elu(pm + sb2[col]) : 0.f;
+                const size_t row = (size_t)(a0 + al);
+                if (X) X[row * a.ldx + a.xoff + col] = __float2bfloat16_rn(y);
+                a.xf[net * a.xf_net + row * a.ldxf + a.xoff + col] = y;
+                a.pmax[((size_t)net * a.num_agents + row) * kHid + col] = pm;
+                a.amax[((size_t)net * a.num_agents + row) * kHid + col] =
+                    k ? (uint16_t)(0xFFFF - (uint32_t)(k & 0xFFFFull)) : (uint16_t)0xFFFF;
+            } else {
+                const uint32_t k = pool[i];
+                pool[i] = 0u;
+                const float y = k ? elu(funkey(k) + sb2[col]) : 0.f;
+                X[(size_t)(a0 + al) * a.ldx + a.xoff + col] = __float2bfloat16_rn(y);
+            }
         }
         __syncthreads();
     }
@@ -370,6 +421,256 @@ __global__ void lf_embed_kernel(const __nv_bfloat16* __restrict__ xa, const __nv
     if (i >= A * 512) return;
     const int a = i >> 9, j = i & 511;
     out[i] = __bfloat162float(j < 256 ? xa[(size_t)a * 256 + j] : xc[(size_t)a * 256 + j - 256]);
+}
+
+// ------------------------------------------------------------------ set-encoder backward (training)
+// Gradient of one group's encoder (W1 [96][F], b1, W2 [96][96], b2) for each
+// network from the gradient of its pooled embedding.  The pooled feature f of
+// a sample is y_f = ELU(z2max_f + b2_f), z2max_f the layer-2 pre-activation of
+// the slot s_f holding the maximum (recorded by the training forward), so
+//   dp_f = dy_f ELU'(z2max_f + b2_f),  db2_f += dp_f,  dW2[f][.] += dp_f h1(s_f),
+//   dh1(s)[.] = sum over f with s_f = s of dp_f W2[f][.],
+//   dz1(s) = dh1(s) ELU'(z1(s)),  dW1 += dz1(s) x(s)^T,  db1 += dz1(s),
+// with h1 and z1 of the maximising slots recomputed as the forward computed
+// them (bf16 inputs, weights and layer-1 bias, fp32 sums, the bf16 ELU).
+// One block per (range of samples, network): thread-owned gradient entries
+// accumulate over the block's samples in order, and each block writes its
+// partial sums; a second kernel adds the blocks' partials in block order, so
+// the result repeats bit for bit.
+constexpr int kBackThreads = 256;
+constexpr int kBackW2 = kHid * kHid / kBackThreads;   // 36 dW2 entries per thread
+
+struct SetBackArgs {
+    const float* obs;          // [B][ld] the minibatch's observations
+    int ld, off, F, K;         // row stride, group offset, features per slot, slots
+    const int32_t* count;      // [B]
+    int B;
+    const float* theta;        // per network: the group's masters [W1 (96 x F) | b1 | W2 (96 x 96) | b2]
+    size_t theta_net;          // distance between the two networks' masters
+    const float* pmax;         // [2][B][96] pooled pre-activation maxima
+    const uint16_t* amax;      // [2][B][96] their slots (0xFFFF: empty group)
+    const float* dx;           // [2][B][lddx] gradient of the trunk input (columns xoff..)
+    size_t dx_net;
+    int lddx, xoff;
+    float* part;               // [2][blocks][P] partial gradients
+    int P;
+};
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__global__ void __launch_bounds__(kBackThreads, 1) lf_set_back_kernel(const SetBackArgs a) {
+    extern __shared__ __align__(16) unsigned char sraw[];
+    float* W2 = reinterpret_cast<float*>(sraw);          // [96][96] bf16-rounded
+    float* H1 = W2 + kHid * kHid;                         // [96 slots][96]
+    float* Z1 = H1 + kHid * kHid;                         // [96][96]
+    float* DH = Z1 + kHid * kHid;                         // [96][96] dh1, then dz1
+    float* W1 = DH + kHid * kHid;                         // [96][8] bf16-rounded; column 7: b1 (bf16)
+    float* XS = W1 + kHid * 8;                            // [96 slots][8] inputs (bf16), column 7: 1
+    float* dp = XS + kHid * 8;                            // [96]
+    float* b2 = dp + kHid;                                // [96]
+    int* sl = reinterpret_cast<int*>(b2 + kHid);          // [96] slot of feature f
+    int* jf = sl + kHid;                                  // [96] its index among the distinct slots
+    int* dl = jf + kHid;                                  // [96] distinct slots, ascending
+    unsigned* bits = reinterpret_cast<unsigned*>(dl + kHid);   // [12] slot bitmap (K <= 384)
+    int* nd = reinterpret_cast<int*>(bits + 12);          // distinct slots of the sample
+
+    const int tid = threadIdx.x, net = blockIdx.y, F = a.F;
+    const float* th = a.theta + (size_t)net * a.theta_net;
+    const float* tW1 = th;
+    const float* tb1 = th + kHid * F;
+    const float* tW2 = tb1 + kHid;
+    const float* tb2 = tW2 + kHid * kHid;
+    for (int i = tid; i < kHid * kHid; i += kBackThreads) W2[i] = bf16r(tW2[i]);
+    for (int i = tid; i < kHid * 8; i += kBackThreads) {
+        const int h = i >> 3, k = i & 7;
+        W1[i] = k < F ? bf16r(tW1[h * F + k]) : (k == 7 ? bf16r(tb1[h]) : 0.f);
+    }
+    for (int i = tid; i < kHid; i += kBackThreads) b2[i] = tb2[i];
+    if (tid < 12) bits[tid] = 0u;
+    float gW2[kBackW2], gW1[3], gb2 = 0.f;
+#pragma unroll
+    for (int r = 0; r < kBackW2; ++r) gW2[r] = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) gW1[r] = 0.f;
+    __syncthreads();
+
+    const int b0 = (int)(((long long)a.B * blockIdx.x) / gridDim.x);
+    const int b1e = (int)(((long long)a.B * (blockIdx.x + 1)) / gridDim.x);
+    const float* pm = a.pmax + (size_t)net * a.B * kHid;
+    const uint16_t* am = a.amax + (size_t)net * a.B * kHid;
+    const float* dxn = a.dx + (size_t)net * a.dx_net;
+    for (int b = b0; b < b1e; ++b) {
+        const int n = min(max(a.count[b], 0), a.K);
+        if (n == 0) continue;                             // block-uniform: an empty group has no gradient
+        // (1) dp and the maximising slots
+        if (tid < kHid) {
+            const int s = am[(size_t)b * kHid + tid];
+            const float u = pm[(size_t)b * kHid + tid] + b2[tid];
+            const float g = dxn[(size_t)b * a.lddx + a.xoff + tid];
+            const bool ok = s < n;
+            dp[tid] = ok ? g * (u > 0.f ? 1.f : expf(u)) : 0.f;
+            sl[tid] = ok ? s : 0;
+            atomicOr(&bits[sl[tid] >> 5], 1u << (sl[tid] & 31));
+        }
+        __syncthreads();
+        // (2) rank of each feature's slot among the distinct ones
+        if (tid < kHid) {
+            const int s = sl[tid];
+            int r = __popc(bits[s >> 5] & ((1u << (s & 31)) - 1u));
+            for (int w = 0; w < (s >> 5); ++w) r += __popc(bits[w]);
+            jf[tid] = r;
+            dl[r] = s;                                    // the same value from every feature of slot s
+        }
+        if (tid == kHid) {
+            int t = 0;
+            for (int w = 0; w < 12; ++w) t += __popc(bits[w]);
+            *nd = t;
+        }
+        __syncthreads();
+        const int D = *nd;
+        if (tid < 12) bits[tid] = 0u;                     // read by no one until the next sample's (1)
+        for (int i = tid; i < D * 8; i += kBackThreads) {
+            const int j = i >> 3, k = i & 7;
+            XS[i] = k < F ? bf16r(a.obs[(size_t)b * a.ld + a.off + (size_t)dl[j] * F + k]) : (k == 7 ? 1.f : 0.f);
+        }
+        __syncthreads();
+        // (3) layer 1 of the distinct slots: z1 (fp32) and the bf16 ELU, two units per work item
+        for (int i = tid; i < D * (kHid / 2); i += kBackThreads) {
+            const int j = i / (kHid / 2), h = 2 * (i - j * (kHid / 2));
+            const float* x = XS + j * 8;
+            float z[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float* w = W1 + (h + u) * 8;
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc = fmaf(x[k], w[k], acc);
+                z[u] = acc;
+            }
+            const uint32_t e = elu_bf16x2(__float_as_uint(z[0]), __float_as_uint(z[1]));
+            Z1[j * kHid + h] = z[0];
+            Z1[j * kHid + h + 1] = z[1];
+            H1[j * kHid + h] = __uint_as_float(e << 16);
+            H1[j * kHid + h + 1] = __uint_as_float(e & 0xFFFF0000u);
+            DH[j * kHid + h] = 0.f;
+            DH[j * kHid + h + 1] = 0.f;
+        }
+        __syncthreads();
+        // (4) dW2 and db2 (thread-owned entries), then dh1 by unit (features in order)
+#pragma unroll
+        for (int r = 0; r < kBackW2; ++r) {
+            const int e = tid + kBackThreads * r, f = e / kHid, h = e - f * kHid;
+            gW2[r] = fmaf(dp[f], H1[jf[f] * kHid + h], gW2[r]);
+        }
+        if (tid < kHid) {
+            gb2 += dp[tid];
+            for (int f = 0; f < kHid; ++f) DH[jf[f] * kHid + tid] = fmaf(dp[f], W2[f * kHid + tid], DH[jf[f] * kHid + tid]);
+        }
+        __syncthreads();
+        // (5) dz1 = dh1 ELU'(z1)
+        for (int i = tid; i < D * kHid; i += kBackThreads) {
+            const float z = Z1[i];
+            DH[i] *= z > 0.f ? 1.f : expf(z);
+        }
+        __syncthreads();
+        // (6) dW1 and db1 (thread-owned (unit, input) entries; input 7 is the bias), slots in order
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int e = tid + kBackThreads * r, h = e >> 3, k = e & 7;
+            float acc = gW1[r];
+            for (int j = 0; j < D; ++j) acc = fmaf(DH[j * kHid + h], XS[j * 8 + k], acc);
+            gW1[r] = acc;
+        }
+        __syncthreads();
+    }
+    // partial sums in the masters' layout [W1 (96 x F) | b1 | W2 | b2]
+    float* out = a.part + ((size_t)net * gridDim.x + blockIdx.x) * a.P;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int e = tid + kBackThreads * r, h = e >> 3, k = e & 7;
+        if (k < F) out[h * F + k] = gW1[r];
+        else if (k == 7) out[kHid * F + h] = gW1[r];
+    }
+#pragma unroll
+    for (int r = 0; r < kBackW2; ++r) out[kHid * F + kHid + tid + kBackThreads * r] = gW2[r];
+    if (tid < kHid) out[kHid * F + kHid + kHid * kHid + tid] = gb2;
+}
+constexpr size_t kBackSmem = (4 * kHid * kHid + 2 * kHid * 8 + 2 * kHid) * 4 + 3 * kHid * 4 + 12 * 4 + 16;
+
+// grad[net][e] = the blocks' partials added in block order
+__global__ void lf_part_sum_kernel(const float* __restrict__ part, int blocks, int P, float* __restrict__ grad,
+                                   size_t grad_net) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x, net = blockIdx.y;
+    if (e >= P) return;
+    const float* p = part + (size_t)net * blocks * P + e;
+    float acc = 0.f;
+    for (int k = 0; k < blocks; ++k) acc += p[(size_t)k * P];
+    grad[(size_t)net * grad_net + e] = acc;
+}
+
+// The inference images of both networks' set encoders from the masters:
+// layer 1 as bf16 [96 rows][K 16] with the bias at K 15, layer 2 as [128 rows][K 96]
+// (K-major 128-byte swizzled atoms of 64 columns), and the layer-2 biases
+__global__ void lf_image_kernel(const float* __restrict__ theta, size_t theta_net, int F, unsigned char* __restrict__ img,
+                                float* __restrict__ sb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;   // (net, row, column) of the two layers
+    const int per = kHid * 16 + kHid * kHid + kHid;
+    if (i >= 2 * per) return;
+    const int net = i / per, e = i - net * per;
+    const float* th = theta + (size_t)net * theta_net;
+    unsigned char* base = img + (size_t)net * kImgBytes;
+    auto put = [&](int off, int rows_total, int r, int k, float v) {
+        const int atom = k / 64, kk = k % 64;
+        const size_t o = (size_t)off + (size_t)atom * rows_total * 128 + (size_t)r * 128 +
+                         (size_t)((((kk / 8) ^ (r & 7)) * 16) + (kk % 8) * 2);
+        *reinterpret_cast<__nv_bfloat16*>(base + o) = __float2bfloat16_rn(v);
+    };
+    if (e < kHid * 16) {                                   // layer 1: inputs 0..F-1, zeros, the bias at K 15
+        const int r = e / 16, k = e % 16;
+        const float v = k < F ? th[r * F + k] : (k == 15 ? th[kHid * F + r] : 0.f);
+        put(kOffW1, 96, r, k, v);
+    } else if (e < kHid * 16 + kHid * kHid) {
+        const int t = e - kHid * 16, r = t / kHid, k = t % kHid;
+        put(kOffW2, 128, r, k, th[kHid * F + kHid + t]);
+    } else {
+        const int j = e - kHid * 16 - kHid * kHid;
+        sb[net * kHid + j] = th[kHid * F + kHid + kHid * kHid + j];
+    }
+}
+
+// Adam (0.9, 0.999, 1e-8) over the set encoders' masters, gradients scaled by *scale
+__global__ void lf_adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                               float* __restrict__ v, size_t n, const float* __restrict__ lr,
+                               const float* __restrict__ scale, float c1, float c2) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i] * *scale;
+    const float mi = 0.9f * m[i] + 0.1f * gi, vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= *lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+// sum of squares of g[0, n): per-block partials (fixed order), then one thread adds them in order to *acc
+constexpr int kSqBlocks = 128;
+__global__ void lf_sumsq_part_kernel(const float* __restrict__ g, size_t n, float* __restrict__ part) {
+    __shared__ float red[256];
+    float s = 0.f;
+    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (size_t)gridDim.x * 256) s += g[i] * g[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void lf_sumsq_final_kernel(const float* __restrict__ part, int k, float* __restrict__ acc) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        float s = 0.f;
+        for (int i = 0; i < k; ++i) s += part[i];
+        *acc += s;
+    }
 }
 
 // ------------------------------------------------------------------ host side
@@ -556,8 +857,10 @@ sf_status sf_lf_create(void* cuda_stream, sf_lf_handle* out) {
     okk = okk && lalloc(m, &m->d_err, 1);
     static bool attr = false;
     if (okk && !attr) {
-        okk = cudaFuncSetAttribute(lf_set_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) ==
-              cudaSuccess;
+        okk = cudaFuncSetAttribute(lf_set_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) ==
+                  cudaSuccess &&
+              cudaFuncSetAttribute(lf_set_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kSmemBytesTrain) == cudaSuccess;
         attr = okk;
     }
     if (!okk || cudaMemset(m->d_err, 0, 4) != cudaSuccess || upload(m) != SF_OK) {
@@ -640,7 +943,7 @@ sf_status sf_lf_forward_on(sf_lf_handle m, cudaStream_t st, const float* d_obs, 
         sa.xoff = g == 0 ? 64 : 160;
         sa.err = m->d_err;
         const int items = (A + kG - 1) / kG;
-        lf_set_kernel<<<2 * (items < sms ? items : sms), kThreads, kSmemBytes, st>>>(sa);
+        lf_set_kernel<false><<<2 * (items < sms ? items : sms), kThreads, kSmemBytes, st>>>(sa);
         e = cudaGetLastError();
     }
     for (int n = 0; n < 2 && e == cudaSuccess; ++n) {
@@ -681,3 +984,324 @@ sf_status sf_lf_sync(sf_lf_handle m) {
 }
 
 }  // extern "C"
+
+// ====================================================================== training
+// LfTrainer: the two networks as trainable parts.  Ego encoder: an MLP
+// 11 -> 64 -> 64 (ELU, ELU); trunk with its head: an MLP 256 -> 128 -> 64 -> H
+// (ELU, ELU, linear); set encoders: fp32 masters updated by Adam, whose bf16
+// inference images (the ones the tensor-core set kernel reads) are rebuilt
+// after every update, so the training forward and the rollout's forward use
+// the same weights.  The trunk input of the training forward is kept in fp32
+// (the trunk MLP rounds it to bf16 as the inference path does).
+constexpr int kBackBlocks = 148;
+
+struct LfTrainer {
+    sf_lf* lf = nullptr;
+    cudaStream_t st = nullptr;
+    std::string err;
+    std::vector<void*> allocs;
+    sf_mlp_handle ego[2] = {nullptr, nullptr}, trunk[2] = {nullptr, nullptr};
+    // set encoders: group g's block at goff[g] holds both networks' masters, P[g] floats each
+    float *theta = nullptr, *grad = nullptr, *mom = nullptr, *var = nullptr;
+    size_t n_set = 0, goff[2] = {0, 0};
+    int P[2] = {0, 0};
+    float* part = nullptr;    // [2][kBackBlocks][max P]
+    float* sq = nullptr;      // [kSqBlocks]
+    int adam_t = 0;
+    // batch buffers of the last forward
+    int cap = 0, rows = 0;
+    float* xf = nullptr;      // [2][cap][256] trunk inputs
+    float* dx = nullptr;      // [2][cap][256] their gradients
+    float* pmax[2] = {nullptr, nullptr};      // per group [2][cap][96]
+    uint16_t* amax[2] = {nullptr, nullptr};
+    const float* obs = nullptr;
+    const int32_t* cnt[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+sf_status tfail(LfTrainer* t, sf_status s, const std::string& msg) {
+    if (t) t->err = msg;
+    return s;
+}
+
+template <class T>
+bool talloc(LfTrainer* t, T** p, size_t count) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess) return false;
+    t->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaMemset(q, 0, count * sizeof(T) + 16) == cudaSuccess;
+}
+
+// offsets of every layer's weight and bias in the sf_lf flat layout
+struct FlatLayout {
+    size_t w[2][9], b[2][9];
+};
+FlatLayout flat_layout() {
+    FlatLayout L{};
+    size_t k = 0;
+    for (int n = 0; n < 2; ++n)
+        for (int l = 0; l < 9; ++l) {
+            const int o = l == L_HEAD ? (n == 0 ? 3 : 1) : kLayers[l].out, i = kLayers[l].in;
+            L.w[n][l] = k; k += (size_t)o * i;
+            L.b[n][l] = k; k += o;
+        }
+    return L;
+}
+int layer_out(int n, int l) { return l == L_HEAD ? (n == 0 ? 3 : 1) : kLayers[l].out; }
+
+// (MLP, its layer) of dense layer l of network n
+void mlp_of(LfTrainer* t, int n, int l, sf_mlp_handle* m, int* ml) {
+    if (l == L_EGO0 || l == L_EGO1) { *m = t->ego[n]; *ml = l - L_EGO0; }
+    else { *m = t->trunk[n]; *ml = l - L_TRUNK0; }
+}
+
+}  // namespace
+
+sf_status lft_create(sf_lf_handle lf, cudaStream_t st, LfTrainer** out) {
+    if (!lf || !out) return SF_ERR_INVALID_ARG;
+    *out = nullptr;
+    LfTrainer* t = new LfTrainer();
+    t->lf = lf;
+    t->st = st;
+    const FlatLayout FL = flat_layout();
+    const float* P = lf->params.data();
+    bool ok = true;
+    for (int n = 0; n < 2 && ok; ++n) {
+        const int de[3] = {kLayers[L_EGO0].in, kLayers[L_EGO0].out, kLayers[L_EGO1].out};
+        const int dt[4] = {kLayers[L_TRUNK0].in, kLayers[L_TRUNK0].out, kLayers[L_TRUNK1].out, n == 0 ? 3 : 1};
+        ok = sf_mlp_create(2, de, SF_ACT_ELU, SF_ACT_ELU, st, &t->ego[n]) == SF_OK &&
+             sf_mlp_create(3, dt, SF_ACT_ELU, SF_ACT_NONE, st, &t->trunk[n]) == SF_OK;
+        for (int l : {L_EGO0, L_EGO1, L_TRUNK0, L_TRUNK1, L_HEAD}) {
+            if (!ok) break;
+            sf_mlp_handle m;
+            int ml;
+            mlp_of(t, n, l, &m, &ml);
+            ok = sf_mlp_set_layer(m, ml, P + FL.w[n][l], P + FL.b[n][l]) == SF_OK;
+        }
+    }
+    for (int g = 0; g < 2; ++g) {
+        const int F = g == 0 ? kPT : kNB;
+        t->P[g] = kHid * F + kHid + kHid * kHid + kHid;
+    }
+    t->goff[1] = 2 * (size_t)t->P[0];
+    t->n_set = 2 * (size_t)(t->P[0] + t->P[1]);
+    const int pmaxP = std::max(t->P[0], t->P[1]);
+    ok = ok && talloc(t, &t->theta, t->n_set) && talloc(t, &t->grad, t->n_set) && talloc(t, &t->mom, t->n_set) &&
+         talloc(t, &t->var, t->n_set) && talloc(t, &t->part, (size_t)2 * kBackBlocks * pmaxP) &&
+         talloc(t, &t->sq, kSqBlocks);
+    if (ok) {   // the masters from the network's parameters: group blocks are contiguous in the flat layout
+        std::vector<float> h(t->n_set);
+        for (int g = 0; g < 2; ++g)
+            for (int n = 0; n < 2; ++n) {
+                const int l0 = g == 0 ? L_ROAD0 : L_VEH0;
+                std::memcpy(h.data() + t->goff[g] + (size_t)n * t->P[g], P + FL.w[n][l0], (size_t)t->P[g] * 4);
+            }
+        ok = cudaMemcpy(t->theta, h.data(), t->n_set * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaFuncSetAttribute(lf_set_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBackSmem) ==
+                 cudaSuccess;
+    }
+    if (!ok) {
+        lft_destroy(t);
+        return SF_ERR_OOM;
+    }
+    *out = t;
+    return SF_OK;
+}
+
+void lft_destroy(LfTrainer* t) {
+    if (!t) return;
+    cudaStreamSynchronize(t->st);
+    for (int n = 0; n < 2; ++n) {
+        sf_mlp_destroy(t->ego[n]);
+        sf_mlp_destroy(t->trunk[n]);
+    }
+    for (void* p : t->allocs) cudaFree(p);
+    delete t;
+}
+
+const char* lft_error(LfTrainer* t) { return t ? t->err.c_str() : "NULL trainer"; }
+
+namespace {
+sf_status lft_reserve(LfTrainer* t, int rows) {
+    if (rows <= t->cap) return SF_OK;
+    cudaStreamSynchronize(t->st);
+    bool ok = talloc(t, &t->xf, (size_t)2 * rows * 256) && talloc(t, &t->dx, (size_t)2 * rows * 256);
+    for (int g = 0; g < 2 && ok; ++g)
+        ok = talloc(t, &t->pmax[g], (size_t)2 * rows * kHid) && talloc(t, &t->amax[g], (size_t)2 * rows * kHid);
+    for (int n = 0; n < 2 && ok; ++n)
+        ok = sf_mlp_reserve(t->ego[n], rows) == SF_OK && sf_mlp_reserve(t->trunk[n], rows) == SF_OK;
+    if (!ok) return tfail(t, SF_ERR_OOM, "late-fusion training buffers");
+    t->cap = rows;   // buffers of a smaller batch stay allocated until destroy
+    return SF_OK;
+}
+}  // namespace
+
+sf_status lft_forward(LfTrainer* t, const float* d_obs, const int32_t* d_n_road, const int32_t* d_n_veh, int rows,
+                      float* d_mean, float* d_value) {
+    if (!t || !d_obs || !d_n_road || !d_n_veh || !d_mean || !d_value || rows < 8 || rows % 8)
+        return SF_ERR_INVALID_ARG;
+    sf_status s = lft_reserve(t, rows);
+    if (s != SF_OK) return s;
+    const size_t xnet = (size_t)rows * 256;
+    t->rows = rows;
+    t->obs = d_obs;
+    t->cnt[0] = d_n_road;
+    t->cnt[1] = d_n_veh;
+    for (int n = 0; n < 2 && s == SF_OK; ++n)   // ego encoders into trunk-input columns 0..63
+        s = sf_mlp_forward_train_on(t->ego[n], t->st, d_obs, kObs, rows, t->xf + n * xnet, 256);
+    if (s != SF_OK) return tfail(t, s, "late-fusion training forward: ego encoder");
+    int sms = 148, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaSuccess;
+    for (int g = 0; g < 2 && e == cudaSuccess; ++g) {
+        SetArgs sa{};
+        sa.obs = d_obs; sa.ld = kObs;
+        sa.off = g == 0 ? kRoad0 : kVeh0;
+        sa.F = g == 0 ? kPT : kNB;
+        sa.K = g == 0 ? kKR : kKV;
+        sa.count = t->cnt[g];
+        sa.num_agents = rows;
+        sa.wimg = t->lf->img[g];
+        sa.b2 = t->lf->sb[g];
+        sa.xa = nullptr; sa.xc = nullptr; sa.ldx = 256;
+        sa.xoff = g == 0 ? 64 : 160;
+        sa.err = t->lf->d_err;
+        sa.xf = t->xf; sa.xf_net = xnet; sa.ldxf = 256;
+        sa.pmax = t->pmax[g]; sa.amax = t->amax[g];
+        const int items = (rows + kG - 1) / kG;
+        lf_set_kernel<true><<<2 * (items < sms ? items : sms), kThreads, kSmemBytesTrain, t->st>>>(sa);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return tfail(t, SF_ERR_CUDA, std::string("late-fusion training forward: ") + cudaGetErrorString(e));
+    s = sf_mlp_forward_train_on(t->trunk[0], t->st, t->xf, 256, rows, d_mean, 3);
+    if (s == SF_OK) s = sf_mlp_forward_train_on(t->trunk[1], t->st, t->xf + xnet, 256, rows, d_value, 1);
+    return s == SF_OK ? SF_OK : tfail(t, s, "late-fusion training forward: trunk");
+}
+
+sf_status lft_backward(LfTrainer* t, const float* d_dmean, const float* d_dvalue, int rows) {
+    if (!t || !d_dmean || !d_dvalue || rows != t->rows) return SF_ERR_INVALID_ARG;
+    const size_t xnet = (size_t)rows * 256;
+    sf_status s = sf_mlp_backward_dx_on(t->trunk[0], t->st, d_dmean, 3, rows, t->dx, 256);
+    if (s == SF_OK) s = sf_mlp_backward_dx_on(t->trunk[1], t->st, d_dvalue, 1, rows, t->dx + xnet, 256);
+    for (int n = 0; n < 2 && s == SF_OK; ++n) s = sf_mlp_backward_on(t->ego[n], t->st, t->dx + n * xnet, 256, rows);
+    if (s != SF_OK) return tfail(t, s, "late-fusion backward: dense layers");
+    cudaError_t e = cudaSuccess;
+    for (int g = 0; g < 2 && e == cudaSuccess; ++g) {
+        SetBackArgs b{};
+        b.obs = t->obs; b.ld = kObs;
+        b.off = g == 0 ? kRoad0 : kVeh0;
+        b.F = g == 0 ? kPT : kNB;
+        b.K = g == 0 ? kKR : kKV;
+        b.count = t->cnt[g];
+        b.B = rows;
+        b.theta = t->theta + t->goff[g];
+        b.theta_net = t->P[g];
+        b.pmax = t->pmax[g];
+        b.amax = t->amax[g];
+        b.dx = t->dx; b.dx_net = xnet; b.lddx = 256;
+        b.xoff = g == 0 ? 64 : 160;
+        b.part = t->part;
+        b.P = t->P[g];
+        lf_set_back_kernel<<<dim3(kBackBlocks, 2), kBackThreads, kBackSmem, t->st>>>(b);
+        lf_part_sum_kernel<<<dim3((unsigned)((t->P[g] + 255) / 256), 2), 256, 0, t->st>>>(
+            t->part, kBackBlocks, t->P[g], t->grad + t->goff[g], t->P[g]);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? SF_OK
+                            : tfail(t, SF_ERR_CUDA, std::string("late-fusion backward: ") + cudaGetErrorString(e));
+}
+
+sf_status lft_grad_sumsq(LfTrainer* t, float* d_acc) {
+    if (!t || !d_acc) return SF_ERR_INVALID_ARG;
+    sf_status s = SF_OK;
+    for (int n = 0; n < 2 && s == SF_OK; ++n) {
+        s = sf_mlp_grad_sumsq_on(t->ego[n], t->st, d_acc);
+        if (s == SF_OK) s = sf_mlp_grad_sumsq_on(t->trunk[n], t->st, d_acc);
+    }
+    if (s != SF_OK) return tfail(t, s, "late-fusion gradient norm");
+    lf_sumsq_part_kernel<<<kSqBlocks, 256, 0, t->st>>>(t->grad, t->n_set, t->sq);
+    lf_sumsq_final_kernel<<<1, 32, 0, t->st>>>(t->sq, kSqBlocks, d_acc);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SF_OK : tfail(t, SF_ERR_CUDA, cudaGetErrorString(e));
+}
+
+sf_status lft_adam(LfTrainer* t, const float* d_lr, const float* d_scale) {
+    if (!t || !d_lr || !d_scale) return SF_ERR_INVALID_ARG;
+    sf_status s = SF_OK;
+    for (int n = 0; n < 2 && s == SF_OK; ++n) {
+        s = sf_mlp_adam_on(t->ego[n], t->st, d_lr, d_scale);
+        if (s == SF_OK) s = sf_mlp_adam_on(t->trunk[n], t->st, d_lr, d_scale);
+    }
+    if (s != SF_OK) return tfail(t, s, "late-fusion Adam");
+    ++t->adam_t;
+    const float c1 = 1.f - std::pow(0.9f, (float)t->adam_t), c2 = 1.f - std::pow(0.999f, (float)t->adam_t);
+    lf_adam_kernel<<<(unsigned)((t->n_set + 255) / 256), 256, 0, t->st>>>(t->theta, t->grad, t->mom, t->var, t->n_set,
+                                                                          d_lr, d_scale, c1, c2);
+    for (int g = 0; g < 2; ++g) {   // the tensor-core set kernel's images follow the masters
+        const int per = kHid * 16 + kHid * kHid + kHid;
+        lf_image_kernel<<<(unsigned)((2 * per + 255) / 256), 256, 0, t->st>>>(
+            t->theta + t->goff[g], t->P[g], g == 0 ? kPT : kNB, reinterpret_cast<unsigned char*>(t->lf->img[g]),
+            t->lf->sb[g]);
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SF_OK : tfail(t, SF_ERR_CUDA, cudaGetErrorString(e));
+}
+
+sf_status lft_publish(LfTrainer* t) {
+    if (!t) return SF_ERR_INVALID_ARG;
+    const int dl[5] = {L_EGO0, L_EGO1, L_TRUNK0, L_TRUNK1, L_HEAD};
+    cudaError_t e = cudaSuccess;
+    for (int n = 0; n < 2 && e == cudaSuccess; ++n)
+        for (int k = 0; k < 5 && e == cudaSuccess; ++k) {
+            sf_mlp_handle m;
+            int ml, ld = 0;
+            mlp_of(t, n, dl[k], &m, &ml);
+            const void* wb = nullptr;
+            const float* b = nullptr;
+            if (sf_mlp_device_layer(m, ml, &wb, &ld, &b) != SF_OK) return tfail(t, SF_ERR_STATE, "layer pointers");
+            const int o = layer_out(n, dl[k]);
+            // the same [out][in padded] bf16 layout as the inference network's (ego input padded to 16)
+            e = cudaMemcpyAsync(t->lf->w[n][k], wb, (size_t)o * ld * 2, cudaMemcpyDeviceToDevice, t->st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(t->lf->b[n][k], b, (size_t)o * 4, cudaMemcpyDeviceToDevice, t->st);
+        }
+    return e == cudaSuccess ? SF_OK : tfail(t, SF_ERR_CUDA, std::string("publish: ") + cudaGetErrorString(e));
+}
+
+sf_status lft_argmax(LfTrainer* t, uint16_t* d_out) {
+    if (!t || !d_out || t->rows <= 0) return SF_ERR_INVALID_ARG;
+    const size_t n = (size_t)2 * t->rows * kHid;
+    cudaError_t e = cudaMemcpyAsync(d_out, t->amax[0], n * 2, cudaMemcpyDeviceToDevice, t->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_out + n, t->amax[1], n * 2, cudaMemcpyDeviceToDevice, t->st);
+    return e == cudaSuccess ? SF_OK : tfail(t, SF_ERR_CUDA, cudaGetErrorString(e));
+}
+
+sf_status lft_get(LfTrainer* t, float* h_params, float* h_grads) {
+    if (!t || (!h_params && !h_grads)) return SF_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(t->st) != cudaSuccess) return tfail(t, SF_ERR_CUDA, "synchronize");
+    const FlatLayout FL = flat_layout();
+    for (int n = 0; n < 2; ++n)
+        for (int l : {L_EGO0, L_EGO1, L_TRUNK0, L_TRUNK1, L_HEAD}) {
+            sf_mlp_handle m;
+            int ml;
+            mlp_of(t, n, l, &m, &ml);
+            const sf_status s = sf_mlp_get_layer(m, ml, h_params ? h_params + FL.w[n][l] : nullptr,
+                                                 h_params ? h_params + FL.b[n][l] : nullptr,
+                                                 h_grads ? h_grads + FL.w[n][l] : nullptr,
+                                                 h_grads ? h_grads + FL.b[n][l] : nullptr);
+            if (s != SF_OK) return tfail(t, s, "dense layer read-back");
+        }
+    std::vector<float> hp(t->n_set), hg(t->n_set);
+    if (cudaMemcpy(hp.data(), t->theta, t->n_set * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(hg.data(), t->grad, t->n_set * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return tfail(t, SF_ERR_CUDA, "set encoder read-back");
+    for (int g = 0; g < 2; ++g)
+        for (int n = 0; n < 2; ++n) {
+            const int l0 = g == 0 ? L_ROAD0 : L_VEH0;
+            const size_t src = t->goff[g] + (size_t)n * t->P[g];
+            if (h_params) std::memcpy(h_params + FL.w[n][l0], hp.data() + src, (size_t)t->P[g] * 4);
+            if (h_grads) std::memcpy(h_grads + FL.w[n][l0], hg.data() + src, (size_t)t->P[g] * 4);
+        }
+    return SF_OK;
+}

@@ -305,8 +305,9 @@ int tile_for(int n) { return n >= 256 ? 256 : (n > 64 ? 128 : 64); }
 
 cudaError_t gemm(sf_mlp* m, const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, int M, int N, int Nb,
                  int K, int act, float* pre, float* out_f32, __nv_bfloat16* out_bf16, __nv_bfloat16* out_t, int ldc,
-                 int ldt, cudaStream_t st = nullptr, bool use_st = false) {
+                 int ldt, cudaStream_t st = nullptr, bool use_st = false, int ldp = 0) {
     GemmArgs g{};
+    g.ldp = ldp;
     g.A = A; g.B = B; g.bias = bias; g.pre = pre; g.out_f32 = out_f32; g.out_bf16 = out_bf16; g.out_bf16_t = out_t;
     g.M = M; g.N = N; g.Nb = Nb; g.K = K; g.ldc = ldc; g.ldt = ldt; g.act = act; g.bn = tile_for(N); g.err = m->errw;
     g.wait_ns = m->wait_ns; g.withhold = m->withhold;
@@ -365,9 +366,11 @@ cudaError_t forward_core(sf_mlp* m, int B, bool train, float* y_out = nullptr, i
             e = gemm_head(m, x_in(m, l), B, y_out ? y_out : m->y, y_out ? ldy : m->ld[m->L], use_st ? st : m->stream);
             break;
         }
+        // the pre-activations keep the layer's own row stride whatever the output's (the backward reads them so)
         e = gemm(m, x_in(m, l), m->wb[l], m->b[l], B, m->dim[l + 1], m->dim[l + 1], m->ld[l], act_of(m, l),
                  train ? m->z[l] : nullptr, last ? (y_out ? y_out : m->y) : nullptr, last ? nullptr : m->x[l + 1],
-                 (train && !last) ? m->xt[l + 1] : nullptr, (last && y_out) ? ldy : m->ld[l + 1], B, st, use_st);
+                 (train && !last) ? m->xt[l + 1] : nullptr, (last && y_out) ? ldy : m->ld[l + 1], B, st, use_st,
+                 m->ld[l + 1]);
     }
     return e;
 }
@@ -400,8 +403,10 @@ cudaError_t weight_grad(sf_mlp* m, int l, int B, const __nv_bfloat16* dzt, cudaS
     return cudaGetLastError();
 }
 
-// backward of the activations kept by the last training forward, from dA (holding dL/dy)
-cudaError_t backward_core(sf_mlp* m, int B, cudaStream_t st) {
+// backward of the activations kept by the last training forward, from dA (holding dL/dy);
+// with dx0 set, also the gradient with respect to the input, dX_0 = dZ_0 W_0, as
+// fp32 [B][lddx] (ld[0] columns, the padding ones zero)
+cudaError_t backward_core(sf_mlp* m, int B, cudaStream_t st, float* dx0 = nullptr, int lddx = 0) {
     cudaError_t e = cudaSuccess;
     for (int l = m->L - 1; l >= 0 && e == cudaSuccess; --l) {
         const int o = m->dim[l + 1], lo = m->ld[l + 1], li = m->ld[l];
@@ -417,6 +422,9 @@ cudaError_t backward_core(sf_mlp* m, int B, cudaStream_t st) {
         }
         if (e == cudaSuccess && l > 0)
             e = gemm(m, m->dz, m->wbt[l], nullptr, B, li, li, lo, SF_ACT_NONE, nullptr, m->dA, nullptr, nullptr, li,
+                     0, st, true);
+        else if (e == cudaSuccess && dx0)
+            e = gemm(m, m->dz, m->wbt[0], nullptr, B, li, li, lo, SF_ACT_NONE, nullptr, dx0, nullptr, nullptr, lddx,
                      0, st, true);
     }
     return e;
@@ -806,6 +814,17 @@ sf_status sf_mlp_backward_on(sf_mlp_handle m, cudaStream_t st, const float* d_dy
     return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("backward: ") + cudaGetErrorString(e));
 }
 
+sf_status sf_mlp_backward_dx_on(sf_mlp_handle m, cudaStream_t st, const float* d_dy, int ldy, int batch, float* d_dx,
+                                int lddx) {
+    if (!m || !d_dy || !d_dx || batch < 8 || batch > m->cap || ldy < m->dim[m->L] || lddx < m->ld[0])
+        return SF_ERR_INVALID_ARG;
+    const int L = m->L;
+    dy_in_kernel<<<grid1((size_t)batch * m->ld[L]), 256, 0, st>>>(d_dy, batch, m->dim[L], ldy, m->ld[L], m->dA);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = backward_core(m, batch, st, d_dx, lddx);
+    return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("backward: ") + cudaGetErrorString(e));
+}
+
 sf_status sf_mlp_grad_sumsq_on(sf_mlp_handle m, cudaStream_t st, float* d_acc) {
     if (!m || !d_acc) return SF_ERR_INVALID_ARG;
     sumsq_part_kernel<<<kSumsqBlocks, 256, 0, st>>>(segs_of(m), m->red);
@@ -823,6 +842,14 @@ sf_status sf_mlp_adam_on(sf_mlp_handle m, cudaStream_t st, const float* d_lr, co
     adam_all_kernel<<<grid1((size_t)S.off[S.nseg]), 256, 0, st>>>(S, d_lr, d_scale, b1, b2, eps, c1, c2);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, cudaGetErrorString(e));
+}
+
+sf_status sf_mlp_device_layer(sf_mlp_handle m, int layer, const void** d_wb, int* ld_in, const float** d_b) {
+    if (!m || layer < 0 || layer >= m->L || !d_wb || !ld_in || !d_b) return SF_ERR_INVALID_ARG;
+    *d_wb = m->wb[layer];
+    *ld_in = m->ld[layer];
+    *d_b = m->b[layer];
+    return SF_OK;
 }
 
 int sf_mlp_out_dim(sf_mlp_handle m) { return m ? m->dim[m->L] : 0; }

@@ -186,17 +186,26 @@ struct Perm {
 };
 __device__ __forceinline__ size_t perm_row(const Perm& p, size_t i) { return (size_t)((p.mul * i + p.add) % p.n); }
 
-__global__ void gather_kernel(Perm p, size_t i0, int B, const float* __restrict__ obs, const float* __restrict__ act,
-                              const float* __restrict__ mu, const float* __restrict__ logp,
-                              const float* __restrict__ adv, const float* __restrict__ ret,
-                              float* __restrict__ g_obs, float* __restrict__ g_small) {
-    // one warp per row: the 320-float observation with coalesced float4 copies, then the small fields
+__global__ void gather_kernel(Perm p, size_t i0, int B, int W, const float* __restrict__ obs,
+                              const float* __restrict__ act, const float* __restrict__ mu,
+                              const float* __restrict__ logp, const float* __restrict__ adv,
+                              const float* __restrict__ ret, float* __restrict__ g_obs, float* __restrict__ g_small,
+                              const int32_t* __restrict__ nr, const int32_t* __restrict__ nv, int32_t* __restrict__ g_nr,
+                              int32_t* __restrict__ g_nv) {
+    // one warp per row: the W-float observation (coalesced float4 copies when W % 4 == 0),
+    // the group counts of a full observation, then the small fields
     const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (row >= B) return;
     const size_t r = perm_row(p, i0 + row);
-    const float4* src = reinterpret_cast<const float4*>(obs + r * kObsW);
-    float4* dst = reinterpret_cast<float4*>(g_obs + (size_t)row * kObsW);
-    for (int k = lane; k < kObsW / 4; k += 32) dst[k] = src[k];
+    if (W % 4 == 0) {
+        const float4* src = reinterpret_cast<const float4*>(obs + r * W);
+        float4* dst = reinterpret_cast<float4*>(g_obs + (size_t)row * W);
+        for (int k = lane; k < W / 4; k += 32) dst[k] = src[k];
+    } else {
+        for (int k = lane; k < W; k += 32) g_obs[(size_t)row * W + k] = obs[r * W + k];
+    }
+    if (nr && lane == 6) g_nr[row] = nr[r];
+    if (nv && lane == 7) g_nv[row] = nv[r];
     if (lane < 3) {
         g_small[(size_t)row * 12 + lane] = act[3 * r + lane];
         g_small[(size_t)row * 12 + 3 + lane] = mu[3 * r + lane];
@@ -302,6 +311,13 @@ unsigned grid_for(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 struct sf_ppo {
     sf_handle h = nullptr;
     sf_mlp_handle actor = nullptr, critic = nullptr;
+    // the late-fusion mode: the paper's network on the full observation (W = 1929, group counts)
+    sf_lf_handle lf = nullptr;
+    LfTrainer* lft = nullptr;
+    int W = kObsW;
+    int32_t *nr = nullptr, *nv = nullptr, *g_nr = nullptr, *g_nv = nullptr;
+    float *obs_boot = nullptr, *mu_boot = nullptr;      // the bootstrap state's observation, a scratch mean
+    int32_t *nr_boot = nullptr, *nv_boot = nullptr;
     sf_ppo_config cfg{};
     cudaStream_t st = nullptr;
     std::string err;
@@ -330,6 +346,42 @@ namespace {
 
 sf_status pfail(sf_ppo* p, sf_status s, const std::string& e) {
     if (p) p->err = e;
+    return s;
+}
+
+// the two networks of either mode: rollout inference of A rows (val may be null
+// with the MLPs; mu is required), the training forward, backward, gradient norm
+// and Adam of the minibatch
+sf_status nets_infer(sf_ppo* p, const float* obs, const int32_t* nr, const int32_t* nv, float* mu, float* val) {
+    if (p->lft) return sf_lf_forward_on(p->lf, p->st, obs, nr, nv, p->A, mu, val, nullptr);
+    sf_status s = mu ? sf_mlp_forward_on(p->actor, p->st, obs, kObsW, p->A, mu, 3) : SF_OK;
+    if (s == SF_OK && val) s = sf_mlp_forward_on(p->critic, p->st, obs, kObsW, p->A, val, 1);
+    return s;
+}
+sf_status nets_train_forward(sf_ppo* p, int B) {
+    if (p->lft) return lft_forward(p->lft, p->g_obs, p->g_nr, p->g_nv, B, p->mu_new, p->v_new);
+    // the critic reads the actor's bf16 copy of the minibatch (converted once)
+    sf_status s = sf_mlp_forward_train_on(p->actor, p->st, p->g_obs, kObsW, B, p->mu_new, 3);
+    if (s == SF_OK) s = sf_mlp_forward_train_shared_on(p->critic, p->actor, p->st, B, p->v_new, 1);
+    return s;
+}
+sf_status nets_backward(sf_ppo* p, int B) {
+    sf_status s;
+    if (p->lft) {
+        s = lft_backward(p->lft, p->d_mu, p->d_v, B);
+        if (s == SF_OK) s = lft_grad_sumsq(p->lft, p->scal + S_SUMSQ);
+        return s;
+    }
+    s = sf_mlp_backward_on(p->actor, p->st, p->d_mu, 3, B);
+    if (s == SF_OK) s = sf_mlp_backward_on(p->critic, p->st, p->d_v, 1, B);
+    if (s == SF_OK) s = sf_mlp_grad_sumsq_on(p->actor, p->st, p->scal + S_SUMSQ);
+    if (s == SF_OK) s = sf_mlp_grad_sumsq_on(p->critic, p->st, p->scal + S_SUMSQ);
+    return s;
+}
+sf_status nets_adam(sf_ppo* p) {
+    if (p->lft) return lft_adam(p->lft, p->scal + S_LR, p->scal + S_SCALE);
+    sf_status s = sf_mlp_adam_on(p->actor, p->st, p->scal + S_LR, p->scal + S_SCALE);
+    if (s == SF_OK) s = sf_mlp_adam_on(p->critic, p->st, p->scal + S_LR, p->scal + S_SCALE);
     return s;
 }
 
@@ -421,9 +473,91 @@ sf_status sf_ppo_create(sf_handle h, sf_mlp_handle actor, sf_mlp_handle critic, 
     return SF_OK;
 }
 
+sf_status sf_ppo_create_lf(sf_handle h, sf_lf_handle lf, const sf_ppo_config* cfg, sf_ppo_handle* out) {
+    if (!h || !lf || !cfg || !out) return SF_ERR_INVALID_ARG;
+    *out = nullptr;
+    const int A = sf_num_agents(h);
+    if (A <= 0) return SF_ERR_STATE;
+    const sf_ppo_config& c = *cfg;
+    if (c.horizon < 1 || c.minibatches < 1 || c.epochs < 1 || !(c.lr > 0.f) || !(c.kl_target > 0.f) ||
+        c.substeps < 1 || !(c.dt > 0.f))
+        return SF_ERR_INVALID_ARG;
+    const size_t N = (size_t)A * c.horizon;
+    const int B = (int)((N / c.minibatches) / 8 * 8);
+    if (B < 8) return SF_ERR_INVALID_ARG;
+    sf_ppo* p = new sf_ppo();
+    p->h = h; p->lf = lf; p->cfg = c;
+    p->st = sf_handle_stream(h);
+    p->A = A; p->T = c.horizon; p->B = B;
+    p->W = SF_FULL_OBS_DIM;
+    const size_t T = (size_t)c.horizon, W = (size_t)p->W;
+    bool ok = palloc(p, &p->obs, T * A * W) && palloc(p, &p->nr, T * A) && palloc(p, &p->nv, T * A) &&
+              palloc(p, &p->act, T * A * 3) && palloc(p, &p->mu, T * A * 3) && palloc(p, &p->logp, T * A) &&
+              palloc(p, &p->val, (T + 1) * A) && palloc(p, &p->rew, T * A) && palloc(p, &p->done, T * A) &&
+              palloc(p, &p->adv, T * A) && palloc(p, &p->ret, T * A) && palloc(p, &p->log_std, 3) &&
+              palloc(p, &p->log_std_old, 3) && palloc(p, &p->g_std, 3) && palloc(p, &p->m_std, 3) &&
+              palloc(p, &p->v_std, 3) && palloc(p, &p->scal, S_COUNT) && palloc(p, &p->moments, 2) &&
+              palloc(p, &p->g_obs, (size_t)B * W) && palloc(p, &p->g_nr, (size_t)B) && palloc(p, &p->g_nv, (size_t)B) &&
+              palloc(p, &p->obs_boot, (size_t)A * W) && palloc(p, &p->nr_boot, (size_t)A) &&
+              palloc(p, &p->nv_boot, (size_t)A) && palloc(p, &p->mu_boot, (size_t)A * 3) &&
+              palloc(p, &p->lpart, (size_t)grid_for(B) * 8) && palloc(p, &p->mpart, (size_t)grid_for(A) * 2) &&
+              palloc(p, &p->rpart, (size_t)kSumBlocks) && palloc(p, &p->g_small, (size_t)B * 12) &&
+              palloc(p, &p->mu_new, (size_t)B * 3) && palloc(p, &p->v_new, (size_t)B) &&
+              palloc(p, &p->d_mu, (size_t)B * 3) && palloc(p, &p->d_v, (size_t)B);
+    if (ok) ok = sf_lf_reserve(lf, A) == SF_OK && lft_create(lf, p->st, &p->lft) == SF_OK;
+    if (!ok) {
+        lft_destroy(p->lft);
+        for (void* q : p->allocs) cudaFree(q);
+        delete p;
+        return SF_ERR_OOM;
+    }
+    // the policy's log standard deviations start from the network's own (its last 3 parameters)
+    std::vector<float> prm(sf_lf_num_params());
+    float s0[3] = {c.init_log_std, c.init_log_std, c.init_log_std};
+    if (sf_lf_get_params(lf, prm.data(), prm.size()) == SF_OK)
+        for (int i = 0; i < 3; ++i) s0[i] = prm[prm.size() - 3 + i];
+    float sc[S_COUNT] = {0};
+    sc[S_LR] = c.lr;
+    sc[S_SCALE] = 1.f;
+    cudaMemcpy(p->log_std, s0, 12, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->scal, sc, sizeof(sc), cudaMemcpyHostToDevice);
+    *out = p;
+    return SF_OK;
+}
+
+sf_status sf_ppo_lf_grads(sf_ppo_handle p, const float* d_obs, const int32_t* d_n_road, const int32_t* d_n_veh,
+                          int rows, const float* d_dmean, const float* d_dvalue, float* d_mean, float* d_value,
+                          uint16_t* d_argmax, float* h_grads, size_t n) {
+    if (!p || !p->lft || !d_obs || !d_n_road || !d_n_veh || !d_dmean || !d_dvalue || !h_grads ||
+        n != sf_lf_num_params() || rows < 8 || rows % 8)
+        return SF_ERR_INVALID_ARG;
+    float* mu = d_mean;
+    float* v = d_value;
+    if (!mu || !v) {   // the rollout-sized scratch would not hold more than A rows: use the minibatch buffers
+        if (rows > p->B) return pfail(p, SF_ERR_INVALID_ARG, "sf_ppo_lf_grads: rows above the minibatch size need outputs");
+        if (!mu) mu = p->mu_new;
+        if (!v) v = p->v_new;
+    }
+    sf_status s = lft_forward(p->lft, d_obs, d_n_road, d_n_veh, rows, mu, v);
+    if (s == SF_OK) s = lft_backward(p->lft, d_dmean, d_dvalue, rows);
+    if (s == SF_OK && d_argmax) s = lft_argmax(p->lft, d_argmax);
+    if (s == SF_OK) s = lft_get(p->lft, nullptr, h_grads);
+    if (s != SF_OK) return pfail(p, s, std::string("sf_ppo_lf_grads: ") + lft_error(p->lft));
+    h_grads[n - 3] = h_grads[n - 2] = h_grads[n - 1] = 0.f;
+    return SF_OK;
+}
+
+sf_status sf_ppo_lf_params(sf_ppo_handle p, float* h_params, size_t n) {
+    if (!p || !p->lft || !h_params || n != sf_lf_num_params()) return SF_ERR_INVALID_ARG;
+    sf_status s = lft_get(p->lft, h_params, nullptr);
+    if (s != SF_OK) return pfail(p, s, std::string("sf_ppo_lf_params: ") + lft_error(p->lft));
+    return cudaMemcpy(h_params + n - 3, p->log_std, 12, cudaMemcpyDeviceToHost) == cudaSuccess ? SF_OK : SF_ERR_CUDA;
+}
+
 sf_status sf_ppo_destroy(sf_ppo_handle p) {
     if (!p) return SF_OK;
     cudaStreamSynchronize(p->st);
+    lft_destroy(p->lft);
     for (void* q : p->allocs) cudaFree(q);
     delete p;
     return SF_OK;
@@ -437,11 +571,18 @@ sf_status sf_ppo_collect(sf_ppo_handle p) {
     const int A = p->A;
     cudaError_t e = cudaMemcpyAsync(p->log_std_old, p->log_std, 12, cudaMemcpyDeviceToDevice, p->st);
     for (int t = 0; t < p->T && e == cudaSuccess; ++t) {
-        float* obs_t = p->obs + (size_t)t * A * kObsW;
-        e = cudaMemcpyAsync(obs_t, o.obs, (size_t)A * kObsW * 4, cudaMemcpyDeviceToDevice, p->st);
-        if (e != cudaSuccess) break;
-        s = sf_mlp_forward_on(p->actor, p->st, obs_t, kObsW, A, p->mu + (size_t)t * A * 3, 3);
-        if (s == SF_OK) s = sf_mlp_forward_on(p->critic, p->st, obs_t, kObsW, A, p->val + (size_t)t * A, 1);
+        float* obs_t = p->obs + (size_t)t * A * p->W;
+        int32_t *nr_t = nullptr, *nv_t = nullptr;
+        if (p->lft) {   // the full observation (App. D) of the current state and its group counts
+            nr_t = p->nr + (size_t)t * A;
+            nv_t = p->nv + (size_t)t * A;
+            s = sf_observe_full(p->h, obs_t, nr_t, nv_t, nullptr, nullptr);
+            if (s != SF_OK) return pfail(p, s, std::string("sf_ppo_collect: observation: ") + sf_last_error(p->h));
+        } else {
+            e = cudaMemcpyAsync(obs_t, o.obs, (size_t)A * kObsW * 4, cudaMemcpyDeviceToDevice, p->st);
+            if (e != cudaSuccess) break;
+        }
+        s = nets_infer(p, obs_t, nr_t, nv_t, p->mu + (size_t)t * A * 3, p->val + (size_t)t * A);
         if (s != SF_OK) return pfail(p, s, "sf_ppo_collect: policy / value forward");
         sample_kernel<<<grid_for(A), 256, 0, p->st>>>(p->mu + (size_t)t * A * 3, p->log_std, A, p->cfg.seed,
                                                        p->steps, p->act + (size_t)t * A * 3, p->logp + (size_t)t * A);
@@ -455,7 +596,13 @@ sf_status sf_ppo_collect(sf_ppo_handle p) {
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {   // the value of the state after the last step bootstraps GAE
-        s = sf_mlp_forward_on(p->critic, p->st, o.obs, kObsW, A, p->val + (size_t)p->T * A, 1);
+        if (p->lft) {
+            s = sf_observe_full(p->h, p->obs_boot, p->nr_boot, p->nv_boot, nullptr, nullptr);
+            if (s == SF_OK)
+                s = nets_infer(p, p->obs_boot, p->nr_boot, p->nv_boot, p->mu_boot, p->val + (size_t)p->T * A);
+        } else {
+            s = nets_infer(p, o.obs, nullptr, nullptr, nullptr, p->val + (size_t)p->T * A);
+        }
         if (s != SF_OK) return pfail(p, s, "sf_ppo_collect: bootstrap value");
     }
     if (e != cudaSuccess) return pfail(p, SF_ERR_CUDA, std::string("sf_ppo_collect: ") + cudaGetErrorString(e));
@@ -499,14 +646,12 @@ sf_status sf_ppo_update(sf_ppo_handle p, float* h_stats) {
         while (pm.mul == 0 || gcd_ull(pm.mul, N) != 1) pm.mul = (pm.mul + 1) % N;
         pm.add = mix(h0 + 1) % N;
         for (int mb = 0; mb < c.minibatches && e == cudaSuccess; ++mb) {
-            gather_kernel<<<grid_for((size_t)B * 32), 256, 0, p->st>>>(pm, (size_t)mb * B, B, p->obs, p->act, p->mu,
-                                                                        p->logp, p->adv, p->ret, p->g_obs,
-                                                                        p->g_small);
+            gather_kernel<<<grid_for((size_t)B * 32), 256, 0, p->st>>>(pm, (size_t)mb * B, B, p->W, p->obs, p->act,
+                                                                        p->mu, p->logp, p->adv, p->ret, p->g_obs,
+                                                                        p->g_small, p->nr, p->nv, p->g_nr, p->g_nv);
             e = cudaGetLastError();
             if (e != cudaSuccess) break;
-            // the critic reads the actor's bf16 copy of the minibatch (converted once)
-            sf_status s = sf_mlp_forward_train_on(p->actor, p->st, p->g_obs, kObsW, B, p->mu_new, 3);
-            if (s == SF_OK) s = sf_mlp_forward_train_shared_on(p->critic, p->actor, p->st, B, p->v_new, 1);
+            sf_status s = nets_train_forward(p, B);
             if (s != SF_OK) return pfail(p, s, "sf_ppo_update: forward");
             loss_grad_kernel<<<grid_for(B), 256, 0, p->st>>>(B, p->g_small, p->mu_new, p->v_new, p->log_std,
                                                               p->log_std_old, c.clip, c.vf_coef, p->d_mu, p->d_v,
@@ -514,14 +659,10 @@ sf_status sf_ppo_update(sf_ppo_handle p, float* h_stats) {
             loss_sums_kernel<<<1, 32, 0, p->st>>>(p->lpart, (int)grid_for(B), p->g_std, p->scal);
             e = cudaGetLastError();
             if (e != cudaSuccess) break;
-            s = sf_mlp_backward_on(p->actor, p->st, p->d_mu, 3, B);
-            if (s == SF_OK) s = sf_mlp_backward_on(p->critic, p->st, p->d_v, 1, B);
-            if (s == SF_OK) s = sf_mlp_grad_sumsq_on(p->actor, p->st, p->scal + S_SUMSQ);
-            if (s == SF_OK) s = sf_mlp_grad_sumsq_on(p->critic, p->st, p->scal + S_SUMSQ);
+            s = nets_backward(p, B);
             if (s != SF_OK) return pfail(p, s, "sf_ppo_update: backward");
             finalize_kernel<<<1, 32, 0, p->st>>>(B, c.ent_coef, c.kl_target, c.max_grad_norm, p->g_std, p->scal);
-            s = sf_mlp_adam_on(p->actor, p->st, p->scal + S_LR, p->scal + S_SCALE);
-            if (s == SF_OK) s = sf_mlp_adam_on(p->critic, p->st, p->scal + S_LR, p->scal + S_SCALE);
+            s = nets_adam(p);
             if (s != SF_OK) return pfail(p, s, "sf_ppo_update: Adam");
             ++p->std_t;
             const float c1 = 1.f - std::pow(0.9f, (float)p->std_t), c2 = 1.f - std::pow(0.999f, (float)p->std_t);
@@ -531,6 +672,10 @@ sf_status sf_ppo_update(sf_ppo_handle p, float* h_stats) {
         }
     }
     ++p->updates;
+    if (e == cudaSuccess && p->lft) {   // the rollout's network takes the trained dense layers
+        const sf_status s = lft_publish(p->lft);
+        if (s != SF_OK) return pfail(p, s, std::string("sf_ppo_update: ") + lft_error(p->lft));
+    }
     if (e != cudaSuccess) return pfail(p, SF_ERR_CUDA, std::string("sf_ppo_update: ") + cudaGetErrorString(e));
     if (h_stats) {
         float sc[S_COUNT];
@@ -564,6 +709,7 @@ sf_status sf_ppo_rollout_ptrs(sf_ppo_handle p, sf_ppo_rollout* r) {
 sf_status sf_ppo_loss_grads(sf_ppo_handle p, const float* d_obs, const float* d_small, int rows, float* d_mean,
                             float* d_value, float* d_dmean, float* d_dvalue, float* h_out) {
     if (!p || !d_obs || !d_small || rows < 8 || rows % 8 || rows > p->B || !h_out) return SF_ERR_INVALID_ARG;
+    if (p->lft) return pfail(p, SF_ERR_STATE, "sf_ppo_loss_grads: an MLP-mode call (this engine trains the late-fusion network)");
     const sf_ppo_config& c = p->cfg;
     float* mu = d_mean ? d_mean : p->mu_new;
     float* v = d_value ? d_value : p->v_new;

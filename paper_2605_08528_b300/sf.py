@@ -110,6 +110,9 @@ def lib():
             "sf_ppo_update": ([vp, vp], i32), "sf_ppo_log_std": ([vp, vp], i32),
             "sf_ppo_rollout_ptrs": ([vp, vp], i32),
             "sf_ppo_loss_grads": ([vp, vp, vp, C.c_int, vp, vp, vp, vp, vp], i32),
+            "sf_ppo_create_lf": ([vp, vp, vp, vp], i32),
+            "sf_ppo_lf_grads": ([vp, vp, vp, vp, C.c_int, vp, vp, vp, vp, vp, vp, C.c_size_t], i32),
+            "sf_ppo_lf_params": ([vp, vp, C.c_size_t], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -646,6 +649,30 @@ def sf_ppo_create(h, actor, critic, cfg=None):
     p = C.c_void_p()
     _check(lib().sf_ppo_create(h, actor, critic, C.byref(cfg), C.byref(p)), h)
     return p
+
+
+def sf_ppo_create_lf(h, lf, cfg=None):
+    """PPO on the late-fusion network lf (the full observation); lf is trained in place."""
+    cfg = cfg if cfg is not None else sf_ppo_default_config()
+    p = C.c_void_p()
+    _check(lib().sf_ppo_create_lf(h, lf, C.byref(cfg), C.byref(p)), h)
+    return p
+
+
+def sf_ppo_lf_grads(p, d_obs, d_n_road, d_n_veh, rows, d_dmean, d_dvalue, d_mean=None, d_value=None,
+                    d_argmax=None):
+    """Flat gradient (sf_lf_set_params layout) of sum(dmean * mean) + sum(dvalue * value)."""
+    g = np.zeros(sf_lf_num_params(), np.float32)
+    _pcheck(lib().sf_ppo_lf_grads(p, _ptr(d_obs), _ptr(d_n_road), _ptr(d_n_veh), int(rows), _ptr(d_dmean),
+                                  _ptr(d_dvalue), _ptr(d_mean), _ptr(d_value), _ptr(d_argmax), g.ctypes.data,
+                                  C.c_size_t(g.size)), p)
+    return g
+
+
+def sf_ppo_lf_params(p):
+    q = np.zeros(sf_lf_num_params(), np.float32)
+    _pcheck(lib().sf_ppo_lf_params(p, q.ctypes.data, C.c_size_t(q.size)), p)
+    return q
 
 
 def sf_ppo_destroy(p):
