@@ -329,22 +329,31 @@ def run_paper_loop(name, steps, warmup, rank, torch, sf, stream, nw=0, pack=0, s
                 mean_road=float(n_road.mean()), mean_veh=float(n_veh.mean()))
 
 
-def run_ppo(name, iters, rank, torch, sf, stream, profile_update=False):
+def run_ppo(name, iters, rank, torch, sf, stream, profile_update=False, net="mlp", stat_iters=3):
     """On-device PPO with the paper's hyperparameters (App. L: horizon 128, 16
     minibatches, 5 epochs): per iteration one rollout (policy and value forward,
     Gaussian sampling, the step) and one update (GAE and 80 minibatch steps),
     timed with CUDA events; the training CASPS counts the rollout's agent-steps
-    over the whole iteration, as the paper's CASPS includes the PPO update."""
+    over the whole iteration, as the paper's CASPS includes the PPO update.
+    net "mlp": actor / critic MLPs on the 320-value observation; "lf": the
+    paper's late-fusion actor-critic (App. E) on the full observation."""
     scene = make_scene(name, rank)
     W = sf.World(scene, seed=4242 + rank, flags=sf.FLAG_AUTO_RESET, stream=stream)
     A = W.A
     with torch.cuda.stream(stream):
         sf.sf_reset(W.h, torch.ones(A, dtype=torch.uint8, device="cuda"))
         sf.sf_autotune(W.h, torch.zeros((A, 3), device="cuda"), iters=10)
-    actor = sf.init_policy(seed=5000 + rank, stream=stream, out_scale=0.1)
-    critic = sf.init_value(seed=6000 + rank, stream=stream)
-    cfg = sf.sf_ppo_default_config(init_log_std=-0.5, seed=77 + rank)
-    ppo = sf.sf_ppo_create(W.h, actor, critic, cfg)
+    actor = critic = lf = None
+    if net == "lf":
+        lf = sf.sf_lf_create(stream)
+        sf.sf_lf_set_params(lf, sf.init_lf(seed=5000 + rank, log_std=-0.5))
+        cfg = sf.sf_ppo_default_config(seed=77 + rank)
+        ppo = sf.sf_ppo_create_lf(W.h, lf, cfg)
+    else:
+        actor = sf.init_policy(seed=5000 + rank, stream=stream, out_scale=0.1)
+        critic = sf.init_value(seed=6000 + rank, stream=stream)
+        cfg = sf.sf_ppo_default_config(init_log_std=-0.5, seed=77 + rank)
+        ppo = sf.sf_ppo_create(W.h, actor, critic, cfg)
     sf.sf_ppo_collect(ppo)                        # warm-up iteration (buffers, kernel attributes)
     sf.sf_ppo_update(ppo)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(iters)]
@@ -365,13 +374,16 @@ def run_ppo(name, iters, rank, torch, sf, stream, profile_update=False):
     torch.cuda.synchronize()
     collect_ms = np.array([e[0].elapsed_time(e[1]) for e in ev])
     update_ms = np.array([e[1].elapsed_time(e[2]) for e in ev])
-    for i in range(3):                            # learning statistics (untimed iterations)
+    for i in range(stat_iters):                   # learning statistics (untimed iterations)
         sf.sf_ppo_collect(ppo)
         stats.append(sf.sf_ppo_update(ppo).tolist())
     log_std = sf.sf_ppo_log_std(ppo).tolist()
     sf.sf_ppo_destroy(ppo)
-    sf.sf_mlp_destroy(actor)
-    sf.sf_mlp_destroy(critic)
+    if lf is not None:
+        sf.sf_lf_destroy(lf)
+    else:
+        sf.sf_mlp_destroy(actor)
+        sf.sf_mlp_destroy(critic)
     W.close()
     steps = A * cfg.horizon
     return dict(A=A, horizon=cfg.horizon, collect_ms=float(collect_ms.mean()), update_ms=float(update_ms.mean()),
@@ -486,9 +498,10 @@ def main_ours(args):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        if name == "ppo":                             # profiling target: the PPO leg alone
-            r = run_ppo("256x16", 1 if args.profile_update else 3, rank, torch, sf, stream,
-                        profile_update=args.profile_update)
+        if name in ("ppo", "ppo_lf"):                 # profiling target: a PPO leg alone
+            r = run_ppo("256x16", 1 if args.profile_update else (3 if name == "ppo" else 2), rank, torch, sf, stream,
+                        profile_update=args.profile_update, net="lf" if name == "ppo_lf" else "mlp",
+                        stat_iters=3 if name == "ppo" else 1)
             if rank == 0:
                 print(json.dumps({"profile_run": name, "rollout_ms": r["collect_ms"], "update_ms": r["update_ms"]}))
             clocks.stop()
@@ -565,11 +578,14 @@ def main_ours(args):
             bikes[name] = run_workload(name, max(args.steps // 4, 50), args.warmup, rank, torch, sf, stream,
                                        e2e=False, nw=args.nw, pack=args.pack, stage=args.stage, split=args.split,
                                        dynamics=sf.DYN_BICYCLE)
-    ppo = None
+    ppo = ppo_lf = None
     if not args.only and not args.skip_ppo:
         if world > 1:
             dist.barrier()
         ppo = run_ppo("256x16", 3, rank, torch, sf, stream)
+        if world > 1:
+            dist.barrier()
+        ppo_lf = run_ppo("256x16", 2, rank, torch, sf, stream, net="lf", stat_iters=2)
     loops = {}
     if not args.only and not args.skip_paper_loop:
         for name in ("256x16", "4096x16"):
@@ -684,6 +700,15 @@ def main_ours(args):
                 "stats_columns": ["mean reward", "policy loss", "value loss", "kl", "lr", "grad norm"],
                 "stats_last_iterations": ppo["stats"], "log_std": ppo["log_std"],
                 "paper_context": "19,250 CASPS during PPO training at 256 x 16 (RTX PRO 6000, Isaac Sim/PhysX)"},
+            "ppo_lf": None if ppo_lf is None else {
+                "value": ppo_lf["casps_train"] * world, "unit": "CASPS (training: rollout + PPO update)",
+                "workload": "256 worlds x 16 agents, App. L hyperparameters, the paper's late-fusion actor-critic "
+                            "(App. E) on the full 1929-value observation (App. D): tensor-core set encoders with "
+                            "masked max-pool, trunk and heads; backward through the max-pool on the CUDA cores",
+                "rollout_ms": ppo_lf["collect_ms"], "update_ms": ppo_lf["update_ms"],
+                "rollout_casps": ppo_lf["casps_collect"] * world,
+                "stats_columns": ["mean reward", "policy loss", "value loss", "kl", "lr", "grad norm"],
+                "stats_last_iterations": ppo_lf["stats"], "log_std": ppo_lf["log_std"]},
             "paper_loop": {k: {
                 "value": v["A"] * world * len(v["ms"]) / (float(v["ms"].sum()) / 1e3), "unit": "CASPS",
                 "ms_per_step": float(v["ms"].mean()), "p50_ms": float(np.percentile(v["ms"], 50)),
@@ -796,7 +821,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--only", default=None,
                     choices=list(WORKLOADS) + ["ragged1024", "4096x16+policy", "256x16+surrogate", "4096x16+surrogate",
-                                               "paper256x16", "paper4096x16", "ppo"],
+                                               "paper256x16", "paper4096x16", "ppo", "ppo_lf"],
                     help="profiling: run one workload only (*+surrogate: a surrogate trained with --surr-rows / "
                          "--surr-steps, then its step graph; paper*: the full-observation + late-fusion loop; "
                          "ppo: the on-device PPO leg)")

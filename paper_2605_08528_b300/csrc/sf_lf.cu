@@ -433,7 +433,7 @@ __global__ void lf_embed_kernel(const __nv_bfloat16* __restrict__ xa, const __nv
 //   dz1(s) = dh1(s) ELU'(z1(s)),  dW1 += dz1(s) x(s)^T,  db1 += dz1(s),
 // with h1 and z1 of the maximising slots recomputed as the forward computed
 // them (bf16 inputs, weights and layer-1 bias, fp32 sums, the bf16 ELU).
-// One block per (range of samples, network): thread-owned gradient entries
+// One block per (range of samples, network), two per SM: thread-owned gradient entries
 // accumulate over the block's samples in order, and each block writes its
 // partial sums; a second kernel adds the blocks' partials in block order, so
 // the result repeats bit for bit.
@@ -458,21 +458,22 @@ struct SetBackArgs {
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-__global__ void __launch_bounds__(kBackThreads, 1) lf_set_back_kernel(const SetBackArgs a) {
+__global__ void __launch_bounds__(kBackThreads, 2) lf_set_back_kernel(const SetBackArgs a) {
     extern __shared__ __align__(16) unsigned char sraw[];
-    float* W2 = reinterpret_cast<float*>(sraw);          // [96][96] bf16-rounded
-    float* H1 = W2 + kHid * kHid;                         // [96 slots][96]
-    float* Z1 = H1 + kHid * kHid;                         // [96][96]
-    float* DH = Z1 + kHid * kHid;                         // [96][96] dh1, then dz1
-    float* W1 = DH + kHid * kHid;                         // [96][8] bf16-rounded; column 7: b1 (bf16)
-    float* XS = W1 + kHid * 8;                            // [96 slots][8] inputs (bf16), column 7: 1
-    float* dp = XS + kHid * 8;                            // [96]
-    float* b2 = dp + kHid;                                // [96]
-    int* sl = reinterpret_cast<int*>(b2 + kHid);          // [96] slot of feature f
-    int* jf = sl + kHid;                                  // [96] its index among the distinct slots
-    int* dl = jf + kHid;                                  // [96] distinct slots, ascending
-    unsigned* bits = reinterpret_cast<unsigned*>(dl + kHid);   // [12] slot bitmap (K <= 384)
-    int* nd = reinterpret_cast<int*>(bits + 12);          // distinct slots of the sample
+    float* W2 = reinterpret_cast<float*>(sraw);                       // [96][96] bf16-rounded
+    float* DZ = W2 + kHid * kHid;                                      // [96 slots][96] dz1
+    float* W1 = DZ + kHid * kHid;                                      // [96][8] bf16-rounded; column 7: b1
+    float* XS = W1 + kHid * 8;                                         // [96 slots][8] inputs (bf16), column 7: 1
+    float* dp = XS + kHid * 8;                                         // [96]
+    float* b2 = dp + kHid;                                             // [96]
+    __nv_bfloat16* H1 = reinterpret_cast<__nv_bfloat16*>(b2 + kHid);  // [96 slots][96] (bf16 values)
+    int* sl = reinterpret_cast<int*>(H1 + kHid * kHid);               // [96] slot of feature f
+    int* jf = sl + kHid;                                               // [96] its index among the distinct slots
+    int* dl = jf + kHid;                                               // [96] distinct slots, ascending
+    int* fl = dl + kHid;                                               // [96] features grouped by slot, ascending
+    int* fs = fl + kHid;                                               // [97] start of each slot's features in fl
+    unsigned* bits = reinterpret_cast<unsigned*>(fs + kHid + 1);       // [12] slot bitmap (K <= 384)
+    int* nd = reinterpret_cast<int*>(bits + 12);                       // distinct slots of the sample
 
     const int tid = threadIdx.x, net = blockIdx.y, F = a.F;
     const float* th = a.theta + (size_t)net * a.theta_net;
@@ -499,21 +500,45 @@ __global__ void __launch_bounds__(kBackThreads, 1) lf_set_back_kernel(const SetB
     const float* pm = a.pmax + (size_t)net * a.B * kHid;
     const uint16_t* am = a.amax + (size_t)net * a.B * kHid;
     const float* dxn = a.dx + (size_t)net * a.dx_net;
+    // z1 of unit h for the inputs x: the same sum, in the same order, wherever it is formed
+    auto z1_of = [&](const float* x, int h) {
+        const float* w = W1 + h * 8;
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc = fmaf(x[k], w[k], acc);
+        return acc;
+    };
+    // the per-feature inputs of sample b (slot, pooled maximum, upstream gradient) and its count,
+    // loaded one sample ahead so that their round trip overlaps the previous sample's work
+    int nx_s = 0, nx_n = 0;
+    float nx_pm = 0.f, nx_g = 0.f;
+    auto fetch = [&](int b) {
+        if (b >= b1e) return;
+        nx_n = min(max(a.count[b], 0), a.K);
+        if (tid < kHid) {
+            nx_s = am[(size_t)b * kHid + tid];
+            nx_pm = pm[(size_t)b * kHid + tid];
+            nx_g = dxn[(size_t)b * a.lddx + a.xoff + tid];
+        }
+    };
+    fetch(b0);
     for (int b = b0; b < b1e; ++b) {
-        const int n = min(max(a.count[b], 0), a.K);
+        const int n = nx_n, s_b = nx_s;
+        const float pm_b = nx_pm, g_b = nx_g;
+        fetch(b + 1);
         if (n == 0) continue;                             // block-uniform: an empty group has no gradient
         // (1) dp and the maximising slots
         if (tid < kHid) {
-            const int s = am[(size_t)b * kHid + tid];
-            const float u = pm[(size_t)b * kHid + tid] + b2[tid];
-            const float g = dxn[(size_t)b * a.lddx + a.xoff + tid];
+            const int s = s_b;
+            const float u = pm_b + b2[tid];
+            const float g = g_b;
             const bool ok = s < n;
             dp[tid] = ok ? g * (u > 0.f ? 1.f : expf(u)) : 0.f;
             sl[tid] = ok ? s : 0;
             atomicOr(&bits[sl[tid] >> 5], 1u << (sl[tid] & 31));
         }
         __syncthreads();
-        // (2) rank of each feature's slot among the distinct ones
+        // (2) each feature's slot rank, and the features grouped by slot (ascending within a slot)
         if (tid < kHid) {
             const int s = sl[tid];
             int r = __popc(bits[s >> 5] & ((1u << (s & 31)) - 1u));
@@ -528,57 +553,56 @@ __global__ void __launch_bounds__(kBackThreads, 1) lf_set_back_kernel(const SetB
         }
         __syncthreads();
         const int D = *nd;
+        if (tid < kHid) {
+            const int j = jf[tid];
+            int before = 0, earlier = 0;                  // features of lower slots; of this slot with lower index
+            for (int f = 0; f < kHid; ++f) {
+                const int jj = jf[f];
+                before += jj < j;
+                earlier += (jj == j) & (f < tid);
+            }
+            fl[before + earlier] = tid;
+            if (earlier == 0) fs[j] = before;
+        }
+        if (tid == kHid) fs[D] = kHid;
         if (tid < 12) bits[tid] = 0u;                     // read by no one until the next sample's (1)
         for (int i = tid; i < D * 8; i += kBackThreads) {
             const int j = i >> 3, k = i & 7;
             XS[i] = k < F ? bf16r(a.obs[(size_t)b * a.ld + a.off + (size_t)dl[j] * F + k]) : (k == 7 ? 1.f : 0.f);
         }
         __syncthreads();
-        // (3) layer 1 of the distinct slots: z1 (fp32) and the bf16 ELU, two units per work item
+        // (3) h1 of the distinct slots: the bf16 ELU of z1, two units per work item
         for (int i = tid; i < D * (kHid / 2); i += kBackThreads) {
             const int j = i / (kHid / 2), h = 2 * (i - j * (kHid / 2));
-            const float* x = XS + j * 8;
-            float z[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const float* w = W1 + (h + u) * 8;
-                float acc = 0.f;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) acc = fmaf(x[k], w[k], acc);
-                z[u] = acc;
-            }
-            const uint32_t e = elu_bf16x2(__float_as_uint(z[0]), __float_as_uint(z[1]));
-            Z1[j * kHid + h] = z[0];
-            Z1[j * kHid + h + 1] = z[1];
-            H1[j * kHid + h] = __uint_as_float(e << 16);
-            H1[j * kHid + h + 1] = __uint_as_float(e & 0xFFFF0000u);
-            DH[j * kHid + h] = 0.f;
-            DH[j * kHid + h + 1] = 0.f;
+            const float z0 = z1_of(XS + j * 8, h), z1v = z1_of(XS + j * 8, h + 1);
+            const uint32_t e = elu_bf16x2(__float_as_uint(z0), __float_as_uint(z1v));
+            *reinterpret_cast<uint32_t*>(H1 + j * kHid + h) = e;   // low half: unit h, high: h + 1
         }
         __syncthreads();
-        // (4) dW2 and db2 (thread-owned entries), then dh1 by unit (features in order)
+        // (4) dW2, db2 (thread-owned entries) and dz1 = (sum over the slot's features of dp W2) ELU'(z1)
 #pragma unroll
         for (int r = 0; r < kBackW2; ++r) {
             const int e = tid + kBackThreads * r, f = e / kHid, h = e - f * kHid;
-            gW2[r] = fmaf(dp[f], H1[jf[f] * kHid + h], gW2[r]);
+            gW2[r] = fmaf(dp[f], __bfloat162float(H1[jf[f] * kHid + h]), gW2[r]);
         }
-        if (tid < kHid) {
-            gb2 += dp[tid];
-            for (int f = 0; f < kHid; ++f) DH[jf[f] * kHid + tid] = fmaf(dp[f], W2[f * kHid + tid], DH[jf[f] * kHid + tid]);
-        }
-        __syncthreads();
-        // (5) dz1 = dh1 ELU'(z1)
+        if (tid < kHid) gb2 += dp[tid];
         for (int i = tid; i < D * kHid; i += kBackThreads) {
-            const float z = Z1[i];
-            DH[i] *= z > 0.f ? 1.f : expf(z);
+            const int j = i / kHid, h = i - j * kHid;
+            float acc = 0.f;
+            for (int q = fs[j]; q < fs[j + 1]; ++q) {
+                const int f = fl[q];
+                acc = fmaf(dp[f], W2[f * kHid + h], acc);
+            }
+            const float z = z1_of(XS + j * 8, h);
+            DZ[i] = acc * (z > 0.f ? 1.f : expf(z));
         }
         __syncthreads();
-        // (6) dW1 and db1 (thread-owned (unit, input) entries; input 7 is the bias), slots in order
+        // (5) dW1 and db1 (thread-owned (unit, input) entries; input 7 is the bias), slots in order
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             const int e = tid + kBackThreads * r, h = e >> 3, k = e & 7;
             float acc = gW1[r];
-            for (int j = 0; j < D; ++j) acc = fmaf(DH[j * kHid + h], XS[j * 8 + k], acc);
+            for (int j = 0; j < D; ++j) acc = fmaf(DZ[j * kHid + h], XS[j * 8 + k], acc);
             gW1[r] = acc;
         }
         __syncthreads();
@@ -595,7 +619,8 @@ __global__ void __launch_bounds__(kBackThreads, 1) lf_set_back_kernel(const SetB
     for (int r = 0; r < kBackW2; ++r) out[kHid * F + kHid + tid + kBackThreads * r] = gW2[r];
     if (tid < kHid) out[kHid * F + kHid + kHid * kHid + tid] = gb2;
 }
-constexpr size_t kBackSmem = (4 * kHid * kHid + 2 * kHid * 8 + 2 * kHid) * 4 + 3 * kHid * 4 + 12 * 4 + 16;
+constexpr size_t kBackSmem = (2 * kHid * kHid + 2 * kHid * 8 + 2 * kHid) * 4 + kHid * kHid * 2 + (4 * kHid + kHid + 1) * 4 +
+                             12 * 4 + 4 + 16;   // two blocks per SM
 
 // grad[net][e] = the blocks' partials added in block order
 __global__ void lf_part_sum_kernel(const float* __restrict__ part, int blocks, int P, float* __restrict__ grad,
