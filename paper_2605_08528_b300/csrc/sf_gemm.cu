@@ -315,6 +315,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const bool vf = args.ldc % 4 == 0 && (reinterpret_cast<uintptr_t>(out_f32) & 15) == 0;
                 const bool vp = ldp % 4 == 0 && (reinterpret_cast<uintptr_t>(args.pre) & 15) == 0;
                 const bool vb = args.ldc % 8 == 0 && (reinterpret_cast<uintptr_t>(args.out_bf16) & 15) == 0;
+                // the layer's ELU values leave it only as bf16 (inference hidden layers, a head's input)
+                const bool packed_elu = args.act == SF_ACT_ELU && !args.pre && !out_f32 && !args.out_bf16_t &&
+                                        (args.out_bf16 || headed);
 #pragma unroll 1
                 for (int c = part; c < BN / 32; c += kParts) {
                     float v[32];
@@ -344,6 +347,39 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     const size_t row = (size_t)r * args.ldc + nb;
+                    if (packed_elu) {   // ELU in packed bf16 when only bf16 values leave this layer
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) pk[e] = elu_bf16x2(__float_as_uint(v[2 * e]), __float_as_uint(v[2 * e + 1]));
+                        if (args.out_bf16) {
+                            if (full && vb) {
+                                uint4 w[4];
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) w[k] = make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+                                stage_store(stg, w, reinterpret_cast<unsigned char*>(args.out_bf16 + (size_t)r0 * args.ldc + nb),
+                                            (size_t)args.ldc * 2, rows_valid, lane);
+                            } else if (live) {
+#pragma unroll
+                                for (int k = 0; k < 32; ++k)
+                                    if (nb + k < args.N)
+                                        args.out_bf16[row + k] = __ushort_as_bfloat16((unsigned short)(pk[k >> 1] >> (16 * (k & 1))));
+                            }
+                        }
+                        if (headed) {   // the same bf16 activations times the head weights, columns in order
+                            const float* hw = &S.hw[0][nb];    // weights beyond N are zero
+#pragma unroll
+                            for (int k = 0; k < 32; k += 2) {
+                                const float x0 = __uint_as_float(pk[k >> 1] << 16), x1 = __uint_as_float(pk[k >> 1] & 0xFFFF0000u);
+#pragma unroll
+                                for (int j = 0; j < kMaxHead; ++j)
+                                    if (j < args.H) {
+                                        const float2 w2 = *reinterpret_cast<const float2*>(hw + j * kHeadMaxN + k);
+                                        hs[j] = fmaf(x1, w2.y, fmaf(x0, w2.x, hs[j]));
+                                    }
+                            }
+                        }
+                        continue;
+                    }
                     if (args.pre) {
                         if (full && vp) {
                             stage_store_f32(stg, v, args.pre + (size_t)r0 * ldp + nb, ldp, rows_valid, lane);

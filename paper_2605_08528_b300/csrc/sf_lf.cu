@@ -118,21 +118,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// ELU of two fp32 accumulators, in packed bf16: the positive part is the
-// rounded input, the negative part 2^(x log2 e) - 1 from the two-lane bf16
-// exp2; one of the two parts is zero, so their sum is exact
-__device__ __forceinline__ uint32_t elu_bf16x2(uint32_t a, uint32_t b) {
-    uint32_t x, pos, neg, e, t, y;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(x) : "f"(__uint_as_float(b)), "f"(__uint_as_float(a)));
-    asm("max.bf16x2 %0, %1, %2;" : "=r"(pos) : "r"(x), "r"(0u));
-    asm("min.bf16x2 %0, %1, %2;" : "=r"(neg) : "r"(x), "r"(0u));
-    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(neg) : "r"(neg), "r"(0x3FB93FB9u));   // log2(e) in bf16
-    asm("ex2.approx.ftz.bf16x2 %0, %1;" : "=r"(e) : "r"(neg));
-    asm("sub.rn.bf16x2 %0, %1, %2;" : "=r"(t) : "r"(e), "r"(0x3F803F80u));       // e - 1 (exact for e >= 1/2)
-    asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(y) : "r"(pos), "r"(t));
-    return y;
-}
-
 // the agent (item-local) whose rows contain item row r: last s with rs[s] <= r
 __device__ __forceinline__ int agent_of_row(const int* rs, int r) {
     int lo = 0, hi = kG - 1;

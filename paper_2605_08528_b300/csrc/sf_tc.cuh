@@ -165,4 +165,19 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, 
 // row at ((c ^ (r & 7)) * 16); atoms 1024-byte aligned
 __device__ __forceinline__ uint32_t swz128(int r, int chunk) { return (uint32_t)(r * 128 + ((chunk ^ (r & 7)) << 4)); }
 
+// ELU of two fp32 accumulators, in packed bf16: the positive part is the
+// rounded input, the negative part 2^(x log2 e) - 1 from the two-lane bf16
+// exp2; one of the two parts is zero, so their sum is exact
+__device__ __forceinline__ uint32_t elu_bf16x2(uint32_t a, uint32_t b) {
+    uint32_t x, pos, neg, e, t, y;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(x) : "f"(__uint_as_float(b)), "f"(__uint_as_float(a)));
+    asm("max.bf16x2 %0, %1, %2;" : "=r"(pos) : "r"(x), "r"(0u));
+    asm("min.bf16x2 %0, %1, %2;" : "=r"(neg) : "r"(x), "r"(0u));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(neg) : "r"(neg), "r"(0x3FB93FB9u));   // log2(e) in bf16
+    asm("ex2.approx.ftz.bf16x2 %0, %1;" : "=r"(e) : "r"(neg));
+    asm("sub.rn.bf16x2 %0, %1, %2;" : "=r"(t) : "r"(e), "r"(0x3F803F80u));       // e - 1 (exact for e >= 1/2)
+    asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(y) : "r"(pos), "r"(t));
+    return y;
+}
+
 }  // namespace sftc
