@@ -454,10 +454,8 @@ __global__ void __launch_bounds__(kBackThreads, 2) lf_set_back_kernel(const SetB
     __nv_bfloat16* H1 = reinterpret_cast<__nv_bfloat16*>(b2 + kHid);  // [96 slots][96] (bf16 values)
     int* sl = reinterpret_cast<int*>(H1 + kHid * kHid);               // [96] slot of feature f
     int* jf = sl + kHid;                                               // [96] its index among the distinct slots
-    int* dl = jf + kHid;                                               // [96] distinct slots, ascending
-    int* fl = dl + kHid;                                               // [96] features grouped by slot, ascending
-    int* fs = fl + kHid;                                               // [97] start of each slot's features in fl
-    unsigned* bits = reinterpret_cast<unsigned*>(fs + kHid + 1);       // [12] slot bitmap (K <= 384)
+    unsigned* fm = reinterpret_cast<unsigned*>(jf + kHid);            // [96 slots][3] the features of each slot
+    unsigned* bits = fm + kHid * 3;                                    // [12] slot bitmap (K <= 384)
     int* nd = reinterpret_cast<int*>(bits + 12);                       // distinct slots of the sample
 
     const int tid = threadIdx.x, net = blockIdx.y, F = a.F;
@@ -472,6 +470,8 @@ __global__ void __launch_bounds__(kBackThreads, 2) lf_set_back_kernel(const SetB
         W1[i] = k < F ? bf16r(tW1[h * F + k]) : (k == 7 ? bf16r(tb1[h]) : 0.f);
     }
     for (int i = tid; i < kHid; i += kBackThreads) b2[i] = tb2[i];
+    for (int i = tid; i < kHid * 3; i += kBackThreads) fm[i] = 0u;
+    for (int i = tid; i < kHid * 8; i += kBackThreads) XS[i] = 0.f;
     if (tid < 12) bits[tid] = 0u;
     float gW2[kBackW2], gW1[3], gb2 = 0.f;
 #pragma unroll
@@ -493,10 +493,11 @@ __global__ void __launch_bounds__(kBackThreads, 2) lf_set_back_kernel(const SetB
         for (int k = 0; k < 8; ++k) acc = fmaf(x[k], w[k], acc);
         return acc;
     };
-    // the per-feature inputs of sample b (slot, pooled maximum, upstream gradient) and its count,
-    // loaded one sample ahead so that their round trip overlaps the previous sample's work
+    // the per-feature inputs of sample b (slot, pooled maximum, upstream gradient), its count
+    // and the inputs of each feature's slot, loaded one sample ahead so that their round
+    // trips overlap the previous sample's work
     int nx_s = 0, nx_n = 0;
-    float nx_pm = 0.f, nx_g = 0.f;
+    float nx_pm = 0.f, nx_g = 0.f, nx_x[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     auto fetch = [&](int b) {
         if (b >= b1e) return;
         nx_n = min(max(a.count[b], 0), a.K);
@@ -506,30 +507,49 @@ __global__ void __launch_bounds__(kBackThreads, 2) lf_set_back_kernel(const SetB
             nx_g = dxn[(size_t)b * a.lddx + a.xoff + tid];
         }
     };
+    auto fetch_x = [&](int b) {   // after fetch(b) has landed: the inputs of this feature's slot
+        if (b >= b1e || tid >= kHid || nx_s >= nx_n) return;
+        const float* src = a.obs + (size_t)b * a.ld + a.off + (size_t)nx_s * F;
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+            if (k < F) nx_x[k] = src[k];
+    };
     fetch(b0);
+    fetch_x(b0);
     for (int b = b0; b < b1e; ++b) {
         const int n = nx_n, s_b = nx_s;
         const float pm_b = nx_pm, g_b = nx_g;
+        float x_b[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) x_b[k] = nx_x[k];
         fetch(b + 1);
-        if (n == 0) continue;                             // block-uniform: an empty group has no gradient
+        if (n == 0) {                                     // block-uniform: an empty group has no gradient
+            fetch_x(b + 1);
+            continue;
+        }
         // (1) dp and the maximising slots
         if (tid < kHid) {
-            const int s = s_b;
+            const bool ok = s_b < n;
             const float u = pm_b + b2[tid];
-            const float g = g_b;
-            const bool ok = s < n;
-            dp[tid] = ok ? g * (u > 0.f ? 1.f : expf(u)) : 0.f;
-            sl[tid] = ok ? s : 0;
+            dp[tid] = ok ? g_b * (u > 0.f ? 1.f : expf(u)) : 0.f;
+            sl[tid] = ok ? s_b : 0;
             atomicOr(&bits[sl[tid] >> 5], 1u << (sl[tid] & 31));
         }
         __syncthreads();
-        // (2) each feature's slot rank, and the features grouped by slot (ascending within a slot)
+        // (2) each feature's slot rank; the features of each slot (a 96-bit mask); the slots' inputs
+        // (every feature of a slot writes the same values)
         if (tid < kHid) {
             const int s = sl[tid];
             int r = __popc(bits[s >> 5] & ((1u << (s & 31)) - 1u));
             for (int w = 0; w < (s >> 5); ++w) r += __popc(bits[w]);
             jf[tid] = r;
-            dl[r] = s;                                    // the same value from every feature of slot s
+            atomicOr(&fm[r * 3 + (tid >> 5)], 1u << (tid & 31));
+            if (s_b < n) {   // (a feature without a valid slot has dp = 0 and leaves its row alone)
+                float* xs = XS + r * 8;
+#pragma unroll
+                for (int k = 0; k < 7; ++k) xs[k] = k < F ? bf16r(x_b[k]) : 0.f;
+                xs[7] = 1.f;
+            }
         }
         if (tid == kHid) {
             int t = 0;
@@ -538,24 +558,7 @@ __global__ void __launch_bounds__(kBackThreads, 2) lf_set_back_kernel(const SetB
         }
         __syncthreads();
         const int D = *nd;
-        if (tid < kHid) {
-            const int j = jf[tid];
-            int before = 0, earlier = 0;                  // features of lower slots; of this slot with lower index
-            for (int f = 0; f < kHid; ++f) {
-                const int jj = jf[f];
-                before += jj < j;
-                earlier += (jj == j) & (f < tid);
-            }
-            fl[before + earlier] = tid;
-            if (earlier == 0) fs[j] = before;
-        }
-        if (tid == kHid) fs[D] = kHid;
         if (tid < 12) bits[tid] = 0u;                     // read by no one until the next sample's (1)
-        for (int i = tid; i < D * 8; i += kBackThreads) {
-            const int j = i >> 3, k = i & 7;
-            XS[i] = k < F ? bf16r(a.obs[(size_t)b * a.ld + a.off + (size_t)dl[j] * F + k]) : (k == 7 ? 1.f : 0.f);
-        }
-        __syncthreads();
         // (3) h1 of the distinct slots: the bf16 ELU of z1, two units per work item
         for (int i = tid; i < D * (kHid / 2); i += kBackThreads) {
             const int j = i / (kHid / 2), h = 2 * (i - j * (kHid / 2));
@@ -564,7 +567,9 @@ __global__ void __launch_bounds__(kBackThreads, 2) lf_set_back_kernel(const SetB
             *reinterpret_cast<uint32_t*>(H1 + j * kHid + h) = e;   // low half: unit h, high: h + 1
         }
         __syncthreads();
-        // (4) dW2, db2 (thread-owned entries) and dz1 = (sum over the slot's features of dp W2) ELU'(z1)
+        // (4) dW2, db2 (thread-owned entries) and dz1 = (sum over the slot's features, ascending,
+        // of dp W2) ELU'(z1); meanwhile the next sample's slot inputs are fetched
+        fetch_x(b + 1);
 #pragma unroll
         for (int r = 0; r < kBackW2; ++r) {
             const int e = tid + kBackThreads * r, f = e / kHid, h = e - f * kHid;
@@ -574,15 +579,18 @@ __global__ void __launch_bounds__(kBackThreads, 2) lf_set_back_kernel(const SetB
         for (int i = tid; i < D * kHid; i += kBackThreads) {
             const int j = i / kHid, h = i - j * kHid;
             float acc = 0.f;
-            for (int q = fs[j]; q < fs[j + 1]; ++q) {
-                const int f = fl[q];
-                acc = fmaf(dp[f], W2[f * kHid + h], acc);
-            }
+#pragma unroll
+            for (int w = 0; w < 3; ++w)
+                for (unsigned m = fm[j * 3 + w]; m; m &= m - 1u) {
+                    const int f = 32 * w + __ffs(m) - 1;
+                    acc = fmaf(dp[f], W2[f * kHid + h], acc);
+                }
             const float z = z1_of(XS + j * 8, h);
             DZ[i] = acc * (z > 0.f ? 1.f : expf(z));
         }
         __syncthreads();
-        // (5) dW1 and db1 (thread-owned (unit, input) entries; input 7 is the bias), slots in order
+        // (5) dW1 and db1 (thread-owned (unit, input) entries; input 7 is the bias), slots in order;
+        // the slots' feature masks are cleared for the next sample
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             const int e = tid + kBackThreads * r, h = e >> 3, k = e & 7;
@@ -590,6 +598,7 @@ __global__ void __launch_bounds__(kBackThreads, 2) lf_set_back_kernel(const SetB
             for (int j = 0; j < D; ++j) acc = fmaf(DZ[j * kHid + h], XS[j * 8 + k], acc);
             gW1[r] = acc;
         }
+        for (int i = tid; i < D * 3; i += kBackThreads) fm[i] = 0u;
         __syncthreads();
     }
     // partial sums in the masters' layout [W1 (96 x F) | b1 | W2 | b2]
@@ -604,7 +613,7 @@ __global__ void __launch_bounds__(kBackThreads, 2) lf_set_back_kernel(const SetB
     for (int r = 0; r < kBackW2; ++r) out[kHid * F + kHid + tid + kBackThreads * r] = gW2[r];
     if (tid < kHid) out[kHid * F + kHid + kHid * kHid + tid] = gb2;
 }
-constexpr size_t kBackSmem = (2 * kHid * kHid + 2 * kHid * 8 + 2 * kHid) * 4 + kHid * kHid * 2 + (4 * kHid + kHid + 1) * 4 +
+constexpr size_t kBackSmem = (2 * kHid * kHid + 2 * kHid * 8 + 2 * kHid) * 4 + kHid * kHid * 2 + (2 * kHid + 3 * kHid) * 4 +
                              12 * 4 + 4 + 16;   // two blocks per SM
 
 // grad[net][e] = the blocks' partials added in block order
