@@ -504,9 +504,28 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
                 edges.push_back(make_float4(r->px[k], r->py[k], r->px[k + 1], r->py[k + 1]));
         }
         for (int i = 0; i < ncell; ++i) cnt[i + 1] += cnt[i];
+        // the edges sorted (stable) by the cell of their start point in the coarse edge grid
+        const double ce = std::max(sfk::kEdgeCellMin, std::max(xmax - xmin, ymax - ymin) / (sfk::kEdgeGridMax - 1));
+        const int ex = std::min(sfk::kEdgeGridMax, (int)std::floor((xmax - xmin) / ce) + 1);
+        const int ey = std::min(sfk::kEdgeGridMax, (int)std::floor((ymax - ymin) / ce) + 1);
+        auto ecell = [&](const float4& e) {
+            const int cx = std::min(ex - 1, std::max(0, (int)std::floor((e.x - xmin) / ce)));
+            const int cy = std::min(ey - 1, std::max(0, (int)std::floor((e.y - ymin) / ce)));
+            return cy * ex + cx;
+        };
+        std::vector<int> ecnt_c(ex * ey + 1, 0);
+        for (const float4& e : edges) ecnt_c[ecell(e) + 1]++;
+        for (int i = 0; i < ex * ey; ++i) ecnt_c[i + 1] += ecnt_c[i];
+        {
+            std::vector<float4> sorted(edges.size());
+            std::vector<int> pos(ecnt_c.begin(), ecnt_c.end() - 1);
+            for (const float4& e : edges) sorted[pos[ecell(e)]++] = e;
+            edges.swap(sorted);
+        }
         auto a16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
         const size_t o_seg = a16(2 * (size_t)(ncell + 1)), o_info = o_seg + 16 * (size_t)np,
-                     o_edge = o_info + a16(4 * (size_t)np), bytes = o_edge + 16 * edges.size();
+                     o_edge = o_info + a16(4 * (size_t)np), o_eoff = o_edge + 16 * edges.size(),
+                     bytes = a16(o_eoff + 2 * (size_t)(ex * ey + 1));
         const size_t at = blob.size();
         blob.resize(at + bytes, 0);
         unsigned char* B = blob.data() + at;
@@ -528,7 +547,12 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
             std::memcpy(B + o_info + 4 * (size_t)slot, &info, 4);
         }
         if (!edges.empty()) std::memcpy(B + o_edge, edges.data(), 16 * edges.size());
+        for (int i = 0; i <= ex * ey; ++i) {
+            const uint16_t v = (uint16_t)ecnt_c[i];
+            std::memcpy(B + o_eoff + 2 * i, &v, 2);
+        }
         DevGrid g{};
+        g.inv_ce = (float)(1.0 / ce); g.ex = ex; g.ey = ey; g.o_eoff = (int)o_eoff;
         g.x0 = (float)xmin; g.y0 = (float)ymin; g.c = (float)c; g.inv_c = (float)(1.0 / c);
         g.nx = nx; g.ny = ny; g.np = np; g.ecnt = (int)edges.size();
         g.bytes = (int)bytes; g.o_seg = (int)o_seg; g.o_info = (int)o_info; g.o_edge = (int)o_edge;

@@ -75,6 +75,8 @@ constexpr int kSpawnTries = 8;
 // ---------------------------------------------------------------- road grid
 constexpr double kCellMin = 4.0;   // grid cell edge [m]; larger when a world spans > 128 cells
 constexpr int kGridMax = 128;
+constexpr double kEdgeCellMin = 16.0;   // edge-grid cell edge [m]
+constexpr int kEdgeGridMax = 16;
 constexpr float kSegReach = 3.0f;  // no segment is longer (App. C gap rule)
 constexpr float kKnnR0 = 10.0f, kLaneR0 = 6.0f, kGrow = 1.6f;
 constexpr float kHintJump = 20.0f;   // a hint farther than this from the agent is not used
@@ -135,16 +137,21 @@ struct DevState {
 //                           the polyline, the previous one at its end, the
 //                           point itself for a one-point polyline
 //   u32    info[np]         input index within the world | type << 16 | kInfo*
-//   float4 edge[ecnt]       the world's road-edge segments (a, b)
+//   float4 edge[ecnt]       the world's road-edge segments (a, b), sorted by the
+//                           cell of a in a coarser edge grid (row-major, stable)
+//   u16    eoff[ex*ey + 1]  edge-grid cell offsets into edge
 // Cell (cx, cy) = floor((x - x0) / c), clamped; the cells of one grid row form
 // one contiguous range [coff[cy*nx + cx0], coff[cy*nx + cx1 + 1]).  Segments
-// are found through their start points.
+// are found through their start points.  The edge grid has the same origin
+// and cells of ce >= kEdgeCellMin (at most kEdgeGridMax per side).
 struct DevGrid {
     float x0, y0, c, inv_c;
     int nx, ny, np, ecnt;
     int bytes, o_seg, o_info, o_edge;   // blob size and section offsets [bytes]
     int q0, pad;                        // the world's first point (input order)
     unsigned long long blob;            // byte offset of the blob in the road store
+    float inv_ce;                       // the edge grid: 1 / cell size, cells per side, offsets [bytes]
+    int ex, ey, o_eoff;
 };
 
 // Road store of all worlds.

@@ -600,9 +600,10 @@ struct WRoads {
     const uint16_t* coff;   // [nx*ny + 1] cell offsets into the sorted records
     const float4* seg;      // sorted segment records (x, y, x', y')
     const uint32_t* info;   // local input index | type << 16 | kInfo* bits
-    const float4* edge;     // edge segments (a, b)
-    float x0, y0, inv_c;
-    int nx, ny, ecnt, q0;
+    const float4* edge;     // edge segments (a, b), sorted by edge-grid cell
+    const uint16_t* eoff;   // [ex*ey + 1] edge-grid cell offsets into edge
+    float x0, y0, inv_c, inv_ce;
+    int nx, ny, ecnt, q0, ex, ey;
 };
 
 __device__ __forceinline__ WRoads view_of(const DevGrid& g, const unsigned char* base) {
@@ -611,8 +612,9 @@ __device__ __forceinline__ WRoads view_of(const DevGrid& g, const unsigned char*
     v.seg = reinterpret_cast<const float4*>(base + g.o_seg);
     v.info = reinterpret_cast<const uint32_t*>(base + g.o_info);
     v.edge = reinterpret_cast<const float4*>(base + g.o_edge);
-    v.x0 = g.x0; v.y0 = g.y0; v.inv_c = g.inv_c;
-    v.nx = g.nx; v.ny = g.ny; v.ecnt = g.ecnt; v.q0 = g.q0;
+    v.eoff = reinterpret_cast<const uint16_t*>(base + g.o_eoff);
+    v.x0 = g.x0; v.y0 = g.y0; v.inv_c = g.inv_c; v.inv_ce = g.inv_ce;
+    v.nx = g.nx; v.ny = g.ny; v.ecnt = g.ecnt; v.q0 = g.q0; v.ex = g.ex; v.ey = g.ey;
     return v;
 }
 
@@ -959,13 +961,19 @@ __device__ Lane coop_point_queries(const WRoads& v, float qx, float qy, float gx
 }
 
 // time for the constant-velocity ray from an agent to reach the nearest road
-// edge segment within 40 m (App. G)
+// edge segment within 40 m (App. G).  GRID: scan only the edge-grid cells the
+// ray can reach; else every edge of the world, four loads per lane in flight
+// (fewer registers and round trips: the split step's query kernel).  Both give
+// the same answer: the earliest accepted hit, and the edges GRID skips cannot
+// be hit.
+template <bool GRID>
 __device__ float coop_edge_ray(const WRoads& v, float px, float py, float vx, float vy, int lane) {
-    // ray p + v t against every edge segment; the acceptance tests t >= 0,
+    // ray p + v t against the edge segments; the acceptance tests t >= 0,
     // 0 <= s <= 1 and |v| t <= 40 m are evaluated multiplied through by the
     // denominator (sign-aware), and only accepted hits divide.  A segment whose
     // start is farther than 40 m + 3 m cannot be hit within the horizon.
     const float speed = sqrtf(vx * vx + vy * vy);
+    if (!(speed > 0.f)) return kInf;   // a ray that does not move hits nothing (every denominator is 0)
     const float reach2 = (kEdgeHorizon + kSegReach) * (kEdgeHorizon + kSegReach);
     float t_best = kInf;
     auto hit = [&](const float4& sg4) {
@@ -979,17 +987,43 @@ __device__ float coop_edge_ray(const WRoads& v, float px, float py, float vx, fl
                                   : (nt <= 0.f && ns <= 0.f && ns >= den && speed * nt >= kEdgeHorizon * den);
         if (ok) t_best = fminf(t_best, __fadd_rn(nt / den, 0.f));   // >= 0 (+0 for a zero time)
     };
-    // four segments per lane in flight: the loads are issued before the tests
-    constexpr int kU = 4;
-    for (int i0 = lane; i0 < v.ecnt; i0 += 32 * kU) {
-        float4 e[kU];
+    if (!GRID) {
+        constexpr int kU = 4;
+        for (int i0 = lane; i0 < v.ecnt; i0 += 32 * kU) {
+            float4 e[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
-            if (i0 + 32 * u < v.ecnt) e[u] = v.edge[i0 + 32 * u];
+            for (int u = 0; u < kU; ++u)
+                if (i0 + 32 * u < v.ecnt) e[u] = v.edge[i0 + 32 * u];
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
-            if (i0 + 32 * u < v.ecnt) hit(e[u]);
+            for (int u = 0; u < kU; ++u)
+                if (i0 + 32 * u < v.ecnt) hit(e[u]);
+        }
+        return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(t_best)));
     }
+    // an accepted hit lies on the ray within 40 m and on a segment no longer than
+    // 3 m, so the segment's start lies in the ray segment's bounding box grown by
+    // 3 m; 1 m more covers rounding.  Only the edge-grid cells of that box are scanned.
+    const float ux = vx / speed * kEdgeHorizon, uy = vy / speed * kEdgeHorizon, pad = kSegReach + 1.f;
+    const float bx0 = fminf(px, px + ux) - pad, bx1 = fmaxf(px, px + ux) + pad;
+    const float by0 = fminf(py, py + uy) - pad, by1 = fmaxf(py, py + uy) + pad;
+    const int cx0 = max((int)floorf(fminf(fmaxf((bx0 - v.x0) * v.inv_ce, -1.f), (float)v.ex)), 0);
+    const int cx1 = min((int)floorf(fminf(fmaxf((bx1 - v.x0) * v.inv_ce, -1.f), (float)v.ex)), v.ex - 1);
+    const int cy0 = max((int)floorf(fminf(fmaxf((by0 - v.y0) * v.inv_ce, -1.f), (float)v.ey)), 0);
+    const int cy1 = min((int)floorf(fminf(fmaxf((by1 - v.y0) * v.inv_ce, -1.f), (float)v.ey)), v.ey - 1);
+    if (cx0 <= cx1)
+        for (int cy = cy0; cy <= cy1; ++cy) {   // a row's cells are one contiguous range of edges
+            const int e0 = v.eoff[cy * v.ex + cx0], e1 = v.eoff[cy * v.ex + cx1 + 1];
+            constexpr int kU = 2;               // two segments per lane in flight
+            for (int i0 = e0 + lane; i0 < e1; i0 += 32 * kU) {
+                float4 e[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (i0 + 32 * u < e1) e[u] = v.edge[i0 + 32 * u];
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (i0 + 32 * u < e1) hit(e[u]);
+            }
+        }
     // times are >= +0 or +inf, ordered like their bit patterns
     return __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(t_best)));
 }
@@ -1563,7 +1597,8 @@ __device__ __forceinline__ AgentQ agent_step_queries(const WRoads& v, float px, 
     float4 prec = make_float4(0.f, 0.f, 0.f, 0.f);
     uint32_t pm = 0u;
     if (key != kKeyInf) { prec = v.seg[rkey_pos(key)]; pm = v.info[rkey_pos(key)]; }
-    const float tedge = coop_edge_ray(v, px, py, vx, vy, lane);
+    // the fused kernel (RANK) takes the edge grid; the split query kernel the linear scan
+    const float tedge = coop_edge_ray<RANK>(v, px, py, vx, vy, lane);
     const unsigned long long last = shfl64(key, 31);
     __syncwarp();
     AgentQ q;
