@@ -69,6 +69,12 @@ struct sf_ctx {
         cudaGraphNode_t n_act = nullptr, n_rew = nullptr, n_done = nullptr;   // copy nodes (not mapped)
         cudaGraphNode_t n_obs = nullptr;                                        // observation copy node
         cudaGraphNode_t n_in = nullptr, n_out = nullptr;                      // kernel nodes (mapped)
+        // mapped buffers and the fused step: the world kernel itself reads the
+        // actions and writes rewards and done flags through the host mapping
+        // (one kernel node, whose arguments `wa` are rewritten to retarget it)
+        bool fused = false;
+        WorldArgs wa{};
+        cudaGraphNode_t n_step = nullptr;
     } hs;
 };
 
@@ -757,6 +763,7 @@ void find_copy_nodes(sf_ctx* h) {
             if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
             if (kp.func == reinterpret_cast<void*>(host_in_kernel)) h->hs.n_in = nd;
             else if (kp.func == reinterpret_cast<void*>(host_out_kernel)) h->hs.n_out = nd;
+            else if (h->hs.fused) h->hs.n_step = nd;   // the graph's one other kernel: the world kernel
             continue;
         }
         if (t != cudaGraphNodeTypeMemcpy) continue;
@@ -814,12 +821,23 @@ sf_status step_host(sf_handle h, const float* h_actions, float* h_obs, float* h_
     float* dr = static_cast<float*>(device_view(h_reward));
     uint8_t* dd = static_cast<uint8_t*>(device_view(h_done));
     const bool mapped = da && dr && dd;
+    const bool fused = mapped && !h->cfg.split_step;
     const int n3 = (int)(3 * A), nA = (int)A;
-    if (same && c.mapped == mapped && (!h_obs || c.n_obs)) {   // other buffers: retarget the graph's transfers
+    if (same && c.mapped == mapped && c.fused == fused && (!h_obs || c.n_obs)) {   // other buffers: retarget
         if (h_obs)
             SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_obs, h_obs, h->out.obs, obs_bytes,
                                                           cudaMemcpyDeviceToHost));
-        if (mapped && c.n_in && c.n_out) {
+        if (fused && c.n_step) {
+            cudaKernelNodeParams kp{};
+            SF_CUDA(h, cudaGraphKernelNodeGetParams(c.n_step, &kp));
+            c.wa.actions = da;
+            c.wa.host_reward = dr;
+            c.wa.host_done = dd;
+            void* step_args[] = {&c.wa};
+            kp.kernelParams = step_args;
+            kp.extra = nullptr;
+            SF_CUDA(h, cudaGraphExecKernelNodeSetParams(c.exec, c.n_step, &kp));
+        } else if (mapped && !fused && c.n_in && c.n_out) {
             cudaKernelNodeParams kp{};
             SF_CUDA(h, cudaGraphKernelNodeGetParams(c.n_in, &kp));
             float* dst = c.d_act;
@@ -854,14 +872,27 @@ capture:
     SF_CUDA(h, cudaStreamSynchronize(h->stream));
     SF_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    if (mapped) {
-        host_in_kernel<<<(n3 + 255) / 256, 256, 0, h->stream>>>(da, c.d_act, n3);
-        e = cudaGetLastError();
+    sf_status st = SF_OK;
+    c.fused = fused;
+    if (fused) {   // one node: the world kernel on the host buffers
+        c.wa = make_args(h);
+        c.wa.actions = da;
+        c.wa.h = dt / (float)substeps;
+        c.wa.substeps = substeps;
+        c.wa.host_reward = dr;
+        c.wa.host_done = dd;
+        e = launch_step(h, c.wa);
+        if (e != cudaSuccess) st = SF_ERR_CUDA;
     } else {
-        e = cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream);
+        if (mapped) {
+            host_in_kernel<<<(n3 + 255) / 256, 256, 0, h->stream>>>(da, c.d_act, n3);
+            e = cudaGetLastError();
+        } else {
+            e = cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream);
+        }
+        st = e == cudaSuccess ? sf_step(h, c.d_act, dt, substeps) : SF_ERR_CUDA;
     }
-    sf_status st = e == cudaSuccess ? sf_step(h, c.d_act, dt, substeps) : SF_ERR_CUDA;
-    if (e == cudaSuccess && st == SF_OK) {
+    if (e == cudaSuccess && st == SF_OK && !fused) {
         if (mapped) {
             host_out_kernel<<<(nA + 255) / 256, 256, 0, h->stream>>>(h->out.reward, h->out.done, dr, dd, nA);
             e = cudaGetLastError();
@@ -869,10 +900,10 @@ capture:
             e = cudaMemcpyAsync(h_reward, h->out.reward, A * 4, cudaMemcpyDeviceToHost, h->stream);
             if (e == cudaSuccess) e = cudaMemcpyAsync(h_done, h->out.done, A, cudaMemcpyDeviceToHost, h->stream);
         }
-        // the observation block goes by the copy engine (1,280 B per agent)
-        if (e == cudaSuccess && h_obs)
-            e = cudaMemcpyAsync(h_obs, h->out.obs, obs_bytes, cudaMemcpyDeviceToHost, h->stream);
     }
+    // the observation block goes by the copy engine (1,280 B per agent)
+    if (e == cudaSuccess && st == SF_OK && h_obs)
+        e = cudaMemcpyAsync(h_obs, h->out.obs, obs_bytes, cudaMemcpyDeviceToHost, h->stream);
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess || st != SF_OK) {

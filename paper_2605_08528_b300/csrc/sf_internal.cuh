@@ -249,6 +249,10 @@ struct WorldArgs {
     // the barrier up but issues no copy (a test of the timeout path)
     unsigned long long wait_ns;
     int withhold;
+    // optional: device views of page-locked host buffers [A] that also receive
+    // the step's rewards and done flags (the host-buffer step, sf_step_host)
+    float* host_reward;
+    uint8_t* host_done;
 };
 
 // surrogate feature / target layout (dynamics surrogate of the step)

@@ -2044,6 +2044,10 @@ __device__ __forceinline__ void lanes_final_b(const WorldArgs& args, const Slot&
     if (MODE == kModeStep) {
         args.out.reward[a] = reward;
         args.out.done[a] = done ? 1 : 0;
+        if (args.host_reward) {   // straight to the host buffers over the host link (posted stores)
+            args.host_reward[a] = reward;
+            args.host_done[a] = done ? 1 : 0;
+        }
         args.out.events[a] = ev;
         args.out.drac[a] = drac;
     } else if (MODE == kModeReset && respawn) {

@@ -11,8 +11,8 @@ from paper_2605_08528_b300 import sf, synth
 pytestmark = pytest.mark.gpu
 
 
-def world(sc, stream, seed=5):
-    W = sf.World(sc, seed=seed, flags=sf.FLAG_AUTO_RESET, stream=stream)
+def world(sc, stream, seed=5, **shape):
+    W = sf.World(sc, seed=seed, flags=sf.FLAG_AUTO_RESET, stream=stream, **shape)
     with torch.cuda.stream(stream):
         sf.sf_reset(W.h, torch.ones(W.A, dtype=torch.uint8, device="cuda"))
     return W
@@ -100,15 +100,18 @@ def test_graph_with_surrogate_matches_individual_calls():
     sf.sf_surrogate_destroy(sur)
 
 
-def test_step_from_host_buffers_equals_device_step():
+@pytest.mark.parametrize("shape", [dict(), dict(warps_per_block=8, stage_bytes=49152), dict(split_step=1)],
+                         ids=["fused", "fused-staged", "split"])
+def test_step_from_host_buffers_equals_device_step(shape):
     """sf_step_host (copy in, step, copies out, one captured graph for
     page-locked buffers) gives the device step's rewards, done flags and state
     bit for bit: replays, a ring of page-locked action buffers (the graph's
-    copies are retargeted), pageable numpy buffers (no graph) and a re-capture
-    after sf_autotune."""
+    transfers are retargeted: with the fused step the world kernel's own
+    arguments), pageable numpy buffers (no graph) and a re-capture after
+    sf_autotune; in each launch shape."""
     sc = synth.procedural_scene(6, 16, seed_base=720)
     s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
-    W1, W2 = world(sc, s1), world(sc, s2)
+    W1, W2 = world(sc, s1, **shape), world(sc, s2, **shape)
     A = W1.A
     acts = synth.ou_actions(A, 24, seed=6)
     ring = [torch.as_tensor(acts[t]).pin_memory() for t in range(3)]
