@@ -232,8 +232,9 @@ sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps);
  * (cudaHostAlloc / cudaHostRegister) the transfers and the step are captured
  * into one CUDA graph that later calls with the same dt and substeps replay
  * (other page-locked buffers retarget its transfers); buffers with a device
- * mapping are read and written in place by two small kernels of the graph,
- * others by copy nodes.  The graph is re-captured after sf_load_roads or
+ * mapping are read and written in place by the step's own kernels (the actions
+ * loaded, rewards and done flags stored over the host link, also into the
+ * device outputs), others by copy nodes.  The graph is re-captured after sf_load_roads or
  * sf_autotune.  Pageable buffers or the legacy stream run copies and the step
  * without a graph.  The buffers are caller-owned and must stay valid during the
  * call.

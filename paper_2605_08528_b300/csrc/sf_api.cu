@@ -65,16 +65,16 @@ struct sf_ctx {
         float* d_act = nullptr;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
-        bool mapped = false;    // the kernels read / write the host buffers through their device mapping
+        // mapped: the step's own kernels read the actions and write rewards and
+        // done flags through the buffers' device mapping (their arguments `wa`
+        // are rewritten to retarget the graph); else copy nodes move them
+        bool mapped = false;
+        WorldArgs wa{};
+        static constexpr int kMaxStepNodes = 8;
+        cudaGraphNode_t n_step[kMaxStepNodes] = {};                            // kernel nodes (mapped)
+        int n_steps = 0;
         cudaGraphNode_t n_act = nullptr, n_rew = nullptr, n_done = nullptr;   // copy nodes (not mapped)
         cudaGraphNode_t n_obs = nullptr;                                        // observation copy node
-        cudaGraphNode_t n_in = nullptr, n_out = nullptr;                      // kernel nodes (mapped)
-        // mapped buffers and the fused step: the world kernel itself reads the
-        // actions and writes rewards and done flags through the host mapping
-        // (one kernel node, whose arguments `wa` are rewritten to retarget it)
-        bool fused = false;
-        WorldArgs wa{};
-        cudaGraphNode_t n_step = nullptr;
     } hs;
 };
 
@@ -717,19 +717,6 @@ sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps) {
 
 namespace {
 
-// the actions of a step from (device-mapped) host memory, and its rewards and
-// done flags back to it: plain loads and stores over the host link, one
-// element per thread, instead of copy operations
-__global__ void host_in_kernel(const float* __restrict__ src, float* __restrict__ dst, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[i];
-}
-__global__ void host_out_kernel(const float* __restrict__ rew, const uint8_t* __restrict__ done,
-                                float* __restrict__ hrew, uint8_t* __restrict__ hdone, int A) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < A) { hrew[i] = rew[i]; hdone[i] = done[i]; }
-}
-
 // the device address of a page-locked host buffer, or null when it has none
 void* device_view(const void* p) {
     void* d = nullptr;
@@ -749,7 +736,9 @@ bool page_locked(const void* p) {
     return at.type == cudaMemoryTypeHost;
 }
 
-// the copy nodes of a captured host step, told apart by their host pointers
+// the transfer nodes of a captured host step: the step's kernel nodes (mapped
+// buffers; every kernel of the step takes the one WorldArgs) or the copy nodes,
+// told apart by their host pointers
 void find_copy_nodes(sf_ctx* h) {
     size_t n = 0;
     cudaGraphGetNodes(h->hs.graph, nullptr, &n);
@@ -759,11 +748,8 @@ void find_copy_nodes(sf_ctx* h) {
         cudaGraphNodeType t;
         if (cudaGraphNodeGetType(nd, &t) != cudaSuccess) continue;
         if (t == cudaGraphNodeTypeKernel) {
-            cudaKernelNodeParams kp{};
-            if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
-            if (kp.func == reinterpret_cast<void*>(host_in_kernel)) h->hs.n_in = nd;
-            else if (kp.func == reinterpret_cast<void*>(host_out_kernel)) h->hs.n_out = nd;
-            else if (h->hs.fused) h->hs.n_step = nd;   // the graph's one other kernel: the world kernel
+            if (h->hs.n_steps < sf_ctx::HostStep::kMaxStepNodes) h->hs.n_step[h->hs.n_steps] = nd;
+            ++h->hs.n_steps;   // more than kMaxStepNodes: not retargeted (re-captured)
             continue;
         }
         if (t != cudaGraphNodeTypeMemcpy) continue;
@@ -815,43 +801,29 @@ sf_status step_host(sf_handle h, const float* h_actions, float* h_obs, float* h_
         SF_CUDA(h, cudaStreamSynchronize(h->stream));
         return SF_OK;
     }
-    // page-locked buffers with device addresses are read and written by two small
-    // kernels inside the graph; others get copy nodes
+    // page-locked buffers with device addresses are read and written by the
+    // step's kernels themselves (loads and posted stores over the host link);
+    // others get copy nodes
     const float* da = static_cast<const float*>(device_view(h_actions));
     float* dr = static_cast<float*>(device_view(h_reward));
     uint8_t* dd = static_cast<uint8_t*>(device_view(h_done));
     const bool mapped = da && dr && dd;
-    const bool fused = mapped && !h->cfg.split_step;
-    const int n3 = (int)(3 * A), nA = (int)A;
-    if (same && c.mapped == mapped && c.fused == fused && (!h_obs || c.n_obs)) {   // other buffers: retarget
+    if (same && c.mapped == mapped && (!h_obs || c.n_obs)) {   // other buffers: retarget the graph's transfers
         if (h_obs)
             SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_obs, h_obs, h->out.obs, obs_bytes,
                                                           cudaMemcpyDeviceToHost));
-        if (fused && c.n_step) {
-            cudaKernelNodeParams kp{};
-            SF_CUDA(h, cudaGraphKernelNodeGetParams(c.n_step, &kp));
+        if (mapped && c.n_steps > 0 && c.n_steps <= sf_ctx::HostStep::kMaxStepNodes) {
             c.wa.actions = da;
             c.wa.host_reward = dr;
             c.wa.host_done = dd;
-            void* step_args[] = {&c.wa};
-            kp.kernelParams = step_args;
-            kp.extra = nullptr;
-            SF_CUDA(h, cudaGraphExecKernelNodeSetParams(c.exec, c.n_step, &kp));
-        } else if (mapped && !fused && c.n_in && c.n_out) {
-            cudaKernelNodeParams kp{};
-            SF_CUDA(h, cudaGraphKernelNodeGetParams(c.n_in, &kp));
-            float* dst = c.d_act;
-            void* in_args[] = {&da, &dst, const_cast<int*>(&n3)};
-            kp.kernelParams = in_args;
-            kp.extra = nullptr;
-            SF_CUDA(h, cudaGraphExecKernelNodeSetParams(c.exec, c.n_in, &kp));
-            SF_CUDA(h, cudaGraphKernelNodeGetParams(c.n_out, &kp));
-            const float* rew = h->out.reward;
-            const uint8_t* dn = h->out.done;
-            void* out_args[] = {&rew, &dn, &dr, &dd, const_cast<int*>(&nA)};
-            kp.kernelParams = out_args;
-            kp.extra = nullptr;
-            SF_CUDA(h, cudaGraphExecKernelNodeSetParams(c.exec, c.n_out, &kp));
+            for (int i = 0; i < c.n_steps; ++i) {
+                cudaKernelNodeParams kp{};
+                SF_CUDA(h, cudaGraphKernelNodeGetParams(c.n_step[i], &kp));
+                void* step_args[] = {&c.wa};
+                kp.kernelParams = step_args;
+                kp.extra = nullptr;
+                SF_CUDA(h, cudaGraphExecKernelNodeSetParams(c.exec, c.n_step[i], &kp));
+            }
         } else if (!mapped && c.n_act && c.n_rew && c.n_done) {
             SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_act, c.d_act, h_actions, A * 12,
                                                           cudaMemcpyHostToDevice));
@@ -873,8 +845,7 @@ capture:
     SF_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     sf_status st = SF_OK;
-    c.fused = fused;
-    if (fused) {   // one node: the world kernel on the host buffers
+    if (mapped) {   // the step's kernels on the host buffers (fused: one node; split: four)
         c.wa = make_args(h);
         c.wa.actions = da;
         c.wa.h = dt / (float)substeps;
@@ -884,19 +855,9 @@ capture:
         e = launch_step(h, c.wa);
         if (e != cudaSuccess) st = SF_ERR_CUDA;
     } else {
-        if (mapped) {
-            host_in_kernel<<<(n3 + 255) / 256, 256, 0, h->stream>>>(da, c.d_act, n3);
-            e = cudaGetLastError();
-        } else {
-            e = cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream);
-        }
+        e = cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream);
         st = e == cudaSuccess ? sf_step(h, c.d_act, dt, substeps) : SF_ERR_CUDA;
-    }
-    if (e == cudaSuccess && st == SF_OK && !fused) {
-        if (mapped) {
-            host_out_kernel<<<(nA + 255) / 256, 256, 0, h->stream>>>(h->out.reward, h->out.done, dr, dd, nA);
-            e = cudaGetLastError();
-        } else {
+        if (e == cudaSuccess && st == SF_OK) {
             e = cudaMemcpyAsync(h_reward, h->out.reward, A * 4, cudaMemcpyDeviceToHost, h->stream);
             if (e == cudaSuccess) e = cudaMemcpyAsync(h_done, h->out.done, A, cudaMemcpyDeviceToHost, h->stream);
         }
