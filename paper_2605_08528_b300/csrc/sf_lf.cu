@@ -415,17 +415,22 @@ __global__ void lf_embed_kernel(const __nv_bfloat16* __restrict__ xa, const __nv
 // the slot s_f holding the maximum (recorded by the training forward), so
 //   dp_f = dy_f ELU'(z2max_f + b2_f),  db2_f += dp_f,  dW2[f][.] += dp_f h1(s_f),
 //   dh1(s)[.] = sum over f with s_f = s of dp_f W2[f][.],
-//   dz1(s) = dh1(s) ELU'(z1(s)),  dW1 += dz1(s) x(s)^T,  db1 += dz1(s),
-// with h1 and z1 of the maximising slots recomputed as the forward computed
-// them (bf16 inputs, weights and layer-1 bias, fp32 sums, the bf16 ELU).
-// One block per (range of samples, network), two per SM: thread-owned gradient entries
-// accumulate over the block's samples in order, and each block writes its
-// partial sums; a second kernel adds the blocks' partials in block order, so
-// the result repeats bit for bit.
-constexpr int kBackThreads = 256;
-constexpr int kBackW2 = kHid * kHid / kBackThreads;   // 36 dW2 entries per thread
+//   dz1(s) = dh1(s) ELU'(z1(s)),  dW1 += dz1(s) x(s)^T,  db1 += dz1(s).
+// Only the distinct maximising slots of a sample carry a gradient, and they
+// become the rows of dense products on the tensor cores: row (b, j) is sample
+// b's j-th distinct maximising slot (ascending), X its bf16 inputs with 1 at
+// column 15, dZ2 its row of dp_f over the features f whose maximum it holds
+// (zeros elsewhere).  Over the R rows of a minibatch:
+//   H1 = ELU(X W1b^T)        W1b: bf16 W1 with the bf16 b1 at column 15 (the forward's image)
+//   dH1 = dZ2 W2,  dZ1 = dH1 * ELU'(z1), z1 recomputed in fp32 from X and W1b
+//   [dW2 | db2] = dZ2^T [H1 | 1],   [dW1 | . | db1] = dZ1^T X
+// The two weight-gradient products reduce over the rows with split K, their
+// partials added in split order, so the result repeats bit for bit.
+constexpr int kSlotWords = (kKR + 31) / 32;   // bitmap words of a sample's slots
+constexpr int kLdW2 = 104;                    // row stride of the [dW2 | db2] partials (97 used)
+constexpr int kBackSplit = 148;               // split-K partials of the weight gradients at most
 
-struct SetBackArgs {
+struct BackRows {
     const float* obs;          // [B][ld] the minibatch's observations
     int ld, off, F, K;         // row stride, group offset, features per slot, slots
     const int32_t* count;      // [B]
@@ -437,194 +442,248 @@ struct SetBackArgs {
     const float* dx;           // [2][B][lddx] gradient of the trunk input (columns xoff..)
     size_t dx_net;
     int lddx, xoff;
-    float* part;               // [2][blocks][P] partial gradients
-    int P;
+    int* nd;                   // [2][B] distinct maximising slots of each sample
+    int* offs;                 // [2][B + 1] their first row (exclusive prefix sum); [B]: R
 };
 
-__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-__global__ void __launch_bounds__(kBackThreads, 2) lf_set_back_kernel(const SetBackArgs a) {
-    extern __shared__ __align__(16) unsigned char sraw[];
-    float* W2 = reinterpret_cast<float*>(sraw);                       // [96][96] bf16-rounded
-    float* DZ = W2 + kHid * kHid;                                      // [96 slots][96] dz1
-    float* W1 = DZ + kHid * kHid;                                      // [96][8] bf16-rounded; column 7: b1
-    float* XS = W1 + kHid * 8;                                         // [96 slots][8] inputs (bf16), column 7: 1
-    float* dp = XS + kHid * 8;                                         // [96]
-    float* b2 = dp + kHid;                                             // [96]
-    __nv_bfloat16* H1 = reinterpret_cast<__nv_bfloat16*>(b2 + kHid);  // [96 slots][96] (bf16 values)
-    int* sl = reinterpret_cast<int*>(H1 + kHid * kHid);               // [96] slot of feature f
-    int* jf = sl + kHid;                                               // [96] its index among the distinct slots
-    unsigned* fm = reinterpret_cast<unsigned*>(jf + kHid);            // [96 slots][3] the features of each slot
-    unsigned* bits = fm + kHid * 3;                                    // [12] slot bitmap (K <= 384)
-    int* nd = reinterpret_cast<int*>(bits + 12);                       // distinct slots of the sample
-
-    const int tid = threadIdx.x, net = blockIdx.y, F = a.F;
-    const float* th = a.theta + (size_t)net * a.theta_net;
-    const float* tW1 = th;
-    const float* tb1 = th + kHid * F;
-    const float* tW2 = tb1 + kHid;
-    const float* tb2 = tW2 + kHid * kHid;
-    for (int i = tid; i < kHid * kHid; i += kBackThreads) W2[i] = bf16r(tW2[i]);
-    for (int i = tid; i < kHid * 8; i += kBackThreads) {
-        const int h = i >> 3, k = i & 7;
-        W1[i] = k < F ? bf16r(tW1[h * F + k]) : (k == 7 ? bf16r(tb1[h]) : 0.f);
+// the bitmap of sample b's valid maximising slots (network net) in words[0..kSlotWords), one warp
+__device__ __forceinline__ void slot_bitmap(const BackRows& a, int net, int b, int n, int lane, unsigned* words) {
+    if (lane < kSlotWords) words[lane] = 0u;
+    __syncwarp();
+    const uint16_t* am = a.amax + ((size_t)net * a.B + b) * kHid;
+    for (int f = lane; f < kHid; f += 32) {
+        const int s = am[f];
+        if (s < n) atomicOr(&words[s >> 5], 1u << (s & 31));
     }
-    for (int i = tid; i < kHid; i += kBackThreads) b2[i] = tb2[i];
-    for (int i = tid; i < kHid * 3; i += kBackThreads) fm[i] = 0u;
-    for (int i = tid; i < kHid * 8; i += kBackThreads) XS[i] = 0.f;
-    if (tid < 12) bits[tid] = 0u;
-    float gW2[kBackW2], gW1[3], gb2 = 0.f;
-#pragma unroll
-    for (int r = 0; r < kBackW2; ++r) gW2[r] = 0.f;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) gW1[r] = 0.f;
-    __syncthreads();
+    __syncwarp();
+}
 
-    const int b0 = (int)(((long long)a.B * blockIdx.x) / gridDim.x);
-    const int b1e = (int)(((long long)a.B * (blockIdx.x + 1)) / gridDim.x);
-    const float* pm = a.pmax + (size_t)net * a.B * kHid;
-    const uint16_t* am = a.amax + (size_t)net * a.B * kHid;
-    const float* dxn = a.dx + (size_t)net * a.dx_net;
-    // z1 of unit h for the inputs x: the same sum, in the same order, wherever it is formed
-    auto z1_of = [&](const float* x, int h) {
-        const float* w = W1 + h * 8;
-        float acc = 0.f;
+// distinct maximising slots per (sample, network): one warp per sample, networks on grid y
+__global__ void __launch_bounds__(256) lfb_count_kernel(const BackRows a) {
+    __shared__ unsigned words[8][kSlotWords + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, net = blockIdx.y;
+    const int b = blockIdx.x * 8 + warp;
+    if (b >= a.B) return;   // warp-uniform
+    const int n = min(max(a.count[b], 0), a.K);
+    slot_bitmap(a, net, b, n, lane, words[warp]);
+    const int d = __reduce_add_sync(0xFFFFFFFFu, lane < kSlotWords ? __popc(words[warp][lane]) : 0);
+    if (lane == 0) a.nd[(size_t)net * a.B + b] = d;
+}
+
+// first row of every sample (exclusive prefix sum of the counts, samples in order)
+// and the total R, per network (one block each)
+__global__ void __launch_bounds__(1024) lfb_scan_kernel(const int* __restrict__ nd, int B, int* __restrict__ offs) {
+    __shared__ int wsum[32];
+    const int net = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int per = (B + 1023) / 1024, i0 = min(B, t * per), i1 = min(B, i0 + per);
+    const int* d = nd + (size_t)net * B;
+    int* o = offs + (size_t)net * (B + 1);
+    int s = 0;
+    for (int i = i0; i < i1; ++i) s += d[i];
+    int incl = s;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc = fmaf(x[k], w[k], acc);
-        return acc;
-    };
-    // the per-feature inputs of sample b (slot, pooled maximum, upstream gradient), its count
-    // and the inputs of each feature's slot, loaded one sample ahead so that their round
-    // trips overlap the previous sample's work
-    int nx_s = 0, nx_n = 0;
-    float nx_pm = 0.f, nx_g = 0.f, nx_x[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    auto fetch = [&](int b) {
-        if (b >= b1e) return;
-        nx_n = min(max(a.count[b], 0), a.K);
-        if (tid < kHid) {
-            nx_s = am[(size_t)b * kHid + tid];
-            nx_pm = pm[(size_t)b * kHid + tid];
-            nx_g = dxn[(size_t)b * a.lddx + a.xoff + tid];
+    for (int k = 1; k < 32; k <<= 1) {
+        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, k);
+        if (lane >= k) incl += v;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int v = wsum[lane];
+        int iv = v;
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {
+            const int u = __shfl_up_sync(0xFFFFFFFFu, iv, k);
+            if (lane >= k) iv += u;
         }
-    };
-    auto fetch_x = [&](int b) {   // after fetch(b) has landed: the inputs of this feature's slot
-        if (b >= b1e || tid >= kHid || nx_s >= nx_n) return;
-        const float* src = a.obs + (size_t)b * a.ld + a.off + (size_t)nx_s * F;
+        wsum[lane] = iv - v;
+    }
+    __syncthreads();
+    int run = wsum[w] + incl - s;
+    for (int i = i0; i < i1; ++i) {
+        o[i] = run;
+        run += d[i];
+    }
+    if (t == 1023) o[B] = run;
+}
+
+// the row buffers of one network's products (ldR: row stride of the transposed ones)
+struct BackBufs {
+    __nv_bfloat16* x;      // [R][16]   inputs, 1 at column 15
+    __nv_bfloat16* xt;     // [16][ldR]
+    __nv_bfloat16* dz2;    // [R][96]
+    __nv_bfloat16* dz2t;   // [96][ldR]
+    __nv_bfloat16* h1t;    // [97][ldR] H1^T (the tensor cores write rows 0..95), row 96: ones
+    __nv_bfloat16* dh1t;   // [96][ldR]
+    __nv_bfloat16* dz1t;   // [96][ldR]
+    __nv_bfloat16* w1b;    // [96][16]
+    __nv_bfloat16* w2t;    // [96 hidden][96 features]: W2 transposed
+    int ldR;
+};
+
+// the rows of network net's products, one warp per sample: the slots' inputs (X, X^T),
+// dZ2 and dZ2^T, and the ones row of H1^T
+__global__ void __launch_bounds__(256) lfb_rows_kernel(const BackRows a, const BackBufs o, int net) {
+    __shared__ unsigned words[8][kSlotWords + 1];
+    __shared__ int wpre[8][kSlotWords + 1];   // set bits before each word
+    __shared__ int rank[8][kHid];             // feature -> row of its slot within the sample (-1: none)
+    __shared__ float dpv[8][kHid];            // feature -> dp
+    __shared__ int slot[8][kHid];             // row within the sample -> slot
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 8 + warp;
+    if (b >= a.B) return;   // warp-uniform
+    const int n = min(max(a.count[b], 0), a.K);
+    if (n == 0) return;     // warp-uniform: an empty group has no rows
+    slot_bitmap(a, net, b, n, lane, words[warp]);
+    if (lane == 0) {
+        int c = 0;
+        for (int w = 0; w < kSlotWords; ++w) {
+            wpre[warp][w] = c;
+            c += __popc(words[warp][w]);
+        }
+        wpre[warp][kSlotWords] = c;
+    }
+    __syncwarp();
+    const int D = wpre[warp][kSlotWords];
+    const size_t bi = ((size_t)net * a.B + b) * kHid;
+    const float* b2 = a.theta + (size_t)net * a.theta_net + kHid * a.F + kHid + kHid * kHid;
+    const float* dy = a.dx + (size_t)net * a.dx_net + (size_t)b * a.lddx + a.xoff;
+    for (int f = lane; f < kHid; f += 32) {
+        const int s = a.amax[bi + f];
+        int r = -1;
+        float d = 0.f;
+        if (s < n) {
+            const float u = a.pmax[bi + f] + b2[f];
+            d = dy[f] * (u > 0.f ? 1.f : expf(u));
+            r = wpre[warp][s >> 5] + __popc(words[warp][s >> 5] & ((1u << (s & 31)) - 1u));
+            slot[warp][r] = s;   // every feature of the slot writes the same value
+        }
+        rank[warp][f] = r;
+        dpv[warp][f] = d;
+    }
+    __syncwarp();
+    const int r0 = a.offs[(size_t)net * (a.B + 1) + b];
+    const int ldR = o.ldR;
+    for (int j = lane; j < D; j += 32) {   // lanes: rows
+        const size_t row = (size_t)r0 + j;
+        const float* src = a.obs + (size_t)b * a.ld + a.off + (size_t)slot[warp][j] * a.F;
+        float x[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[k] = 0.f;
 #pragma unroll
         for (int k = 0; k < 7; ++k)
-            if (k < F) nx_x[k] = src[k];
-    };
-    fetch(b0);
-    fetch_x(b0);
-    for (int b = b0; b < b1e; ++b) {
-        const int n = nx_n, s_b = nx_s;
-        const float pm_b = nx_pm, g_b = nx_g;
-        float x_b[7];
+            if (k < a.F) x[k] = src[k];
+        x[15] = 1.f;
+        uint4* xr = reinterpret_cast<uint4*>(o.x + row * 16);
+        xr[0] = make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
+        xr[1] = make_uint4(pack_bf16(x[8], x[9]), pack_bf16(x[10], x[11]), pack_bf16(x[12], x[13]),
+                           pack_bf16(x[14], x[15]));
 #pragma unroll
-        for (int k = 0; k < 7; ++k) x_b[k] = nx_x[k];
-        fetch(b + 1);
-        if (n == 0) {                                     // block-uniform: an empty group has no gradient
-            fetch_x(b + 1);
-            continue;
-        }
-        // (1) dp and the maximising slots
-        if (tid < kHid) {
-            const bool ok = s_b < n;
-            const float u = pm_b + b2[tid];
-            dp[tid] = ok ? g_b * (u > 0.f ? 1.f : expf(u)) : 0.f;
-            sl[tid] = ok ? s_b : 0;
-            atomicOr(&bits[sl[tid] >> 5], 1u << (sl[tid] & 31));
-        }
-        __syncthreads();
-        // (2) each feature's slot rank; the features of each slot (a 96-bit mask); the slots' inputs
-        // (every feature of a slot writes the same values)
-        if (tid < kHid) {
-            const int s = sl[tid];
-            int r = __popc(bits[s >> 5] & ((1u << (s & 31)) - 1u));
-            for (int w = 0; w < (s >> 5); ++w) r += __popc(bits[w]);
-            jf[tid] = r;
-            atomicOr(&fm[r * 3 + (tid >> 5)], 1u << (tid & 31));
-            if (s_b < n) {   // (a feature without a valid slot has dp = 0 and leaves its row alone)
-                float* xs = XS + r * 8;
+        for (int k = 0; k < 16; ++k) o.xt[(size_t)k * ldR + row] = __float2bfloat16_rn(x[k]);
+        o.h1t[(size_t)kHid * ldR + row] = __float2bfloat16_rn(1.f);
+        uint4* dr = reinterpret_cast<uint4*>(o.dz2 + row * kHid);
+#pragma unroll 1
+        for (int c = 0; c < kHid / 8; ++c) {
+            uint32_t p[4];
 #pragma unroll
-                for (int k = 0; k < 7; ++k) xs[k] = k < F ? bf16r(x_b[k]) : 0.f;
-                xs[7] = 1.f;
+            for (int e = 0; e < 4; ++e) {
+                const int f = 8 * c + 2 * e;
+                p[e] = pack_bf16(rank[warp][f] == j ? dpv[warp][f] : 0.f, rank[warp][f + 1] == j ? dpv[warp][f + 1] : 0.f);
             }
+            dr[c] = make_uint4(p[0], p[1], p[2], p[3]);
         }
-        if (tid == kHid) {
-            int t = 0;
-            for (int w = 0; w < 12; ++w) t += __popc(bits[w]);
-            *nd = t;
-        }
-        __syncthreads();
-        const int D = *nd;
-        if (tid < 12) bits[tid] = 0u;                     // read by no one until the next sample's (1)
-        // (3) h1 of the distinct slots: the bf16 ELU of z1, two units per work item
-        for (int i = tid; i < D * (kHid / 2); i += kBackThreads) {
-            const int j = i / (kHid / 2), h = 2 * (i - j * (kHid / 2));
-            const float z0 = z1_of(XS + j * 8, h), z1v = z1_of(XS + j * 8, h + 1);
-            const uint32_t e = elu_bf16x2(__float_as_uint(z0), __float_as_uint(z1v));
-            *reinterpret_cast<uint32_t*>(H1 + j * kHid + h) = e;   // low half: unit h, high: h + 1
-        }
-        __syncthreads();
-        // (4) dW2, db2 (thread-owned entries) and dz1 = (sum over the slot's features, ascending,
-        // of dp W2) ELU'(z1); meanwhile the next sample's slot inputs are fetched
-        fetch_x(b + 1);
-#pragma unroll
-        for (int r = 0; r < kBackW2; ++r) {
-            const int e = tid + kBackThreads * r, f = e / kHid, h = e - f * kHid;
-            gW2[r] = fmaf(dp[f], __bfloat162float(H1[jf[f] * kHid + h]), gW2[r]);
-        }
-        if (tid < kHid) gb2 += dp[tid];
-        for (int i = tid; i < D * kHid; i += kBackThreads) {
-            const int j = i / kHid, h = i - j * kHid;
-            float acc = 0.f;
-#pragma unroll
-            for (int w = 0; w < 3; ++w)
-                for (unsigned m = fm[j * 3 + w]; m; m &= m - 1u) {
-                    const int f = 32 * w + __ffs(m) - 1;
-                    acc = fmaf(dp[f], W2[f * kHid + h], acc);
-                }
-            const float z = z1_of(XS + j * 8, h);
-            DZ[i] = acc * (z > 0.f ? 1.f : expf(z));
-        }
-        __syncthreads();
-        // (5) dW1 and db1 (thread-owned (unit, input) entries; input 7 is the bias), slots in order;
-        // the slots' feature masks are cleared for the next sample
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const int e = tid + kBackThreads * r, h = e >> 3, k = e & 7;
-            float acc = gW1[r];
-            for (int j = 0; j < D; ++j) acc = fmaf(DZ[j * kHid + h], XS[j * 8 + k], acc);
-            gW1[r] = acc;
-        }
-        for (int i = tid; i < D * 3; i += kBackThreads) fm[i] = 0u;
-        __syncthreads();
     }
-    // partial sums in the masters' layout [W1 (96 x F) | b1 | W2 | b2]
-    float* out = a.part + ((size_t)net * gridDim.x + blockIdx.x) * a.P;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        const int e = tid + kBackThreads * r, h = e >> 3, k = e & 7;
-        if (k < F) out[h * F + k] = gW1[r];
-        else if (k == 7) out[kHid * F + h] = gW1[r];
+    for (int f = 0; f < kHid; ++f) {       // dZ2^T: the sample's D columns of each feature (lanes: columns)
+        const int rf = rank[warp][f];
+        const float v = dpv[warp][f];
+        for (int j = lane; j < D; j += 32)
+            o.dz2t[(size_t)f * ldR + r0 + j] = __float2bfloat16_rn(j == rf ? v : 0.f);
     }
-#pragma unroll
-    for (int r = 0; r < kBackW2; ++r) out[kHid * F + kHid + tid + kBackThreads * r] = gW2[r];
-    if (tid < kHid) out[kHid * F + kHid + kHid * kHid + tid] = gb2;
 }
-constexpr size_t kBackSmem = (2 * kHid * kHid + 2 * kHid * 8 + 2 * kHid) * 4 + kHid * kHid * 2 + (2 * kHid + 3 * kHid) * 4 +
-                             12 * 4 + 4 + 16;   // two blocks per SM
 
-// grad[net][e] = the blocks' partials added in block order
-__global__ void lf_part_sum_kernel(const float* __restrict__ part, int blocks, int P, float* __restrict__ grad,
-                                   size_t grad_net) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x, net = blockIdx.y;
-    if (e >= P) return;
-    const float* p = part + (size_t)net * blocks * P + e;
+// zeros in the padding columns [R, ldR) of the transposed operands the weight-gradient
+// products read (X^T 16 rows, dZ2^T 96, H1^T 97), one block per row
+__global__ void lfb_pad_kernel(BackBufs o, int R) {
+    const int row = blockIdx.x, c = R + threadIdx.x;
+    if (c >= o.ldR) return;
+    __nv_bfloat16* p = row < 16 ? o.xt + (size_t)row * o.ldR
+                     : row < 16 + kHid ? o.dz2t + (size_t)(row - 16) * o.ldR
+                                       : o.h1t + (size_t)(row - 16 - kHid) * o.ldR;
+    p[c] = __float2bfloat16_rn(0.f);
+}
+
+// the bf16 operands of one network's weights: W1b [96][16] (W1, zeros, the layer-1 bias
+// at column 15, the forward's image) and W2 transposed
+__global__ void lfb_weights_kernel(const float* __restrict__ th, int F, __nv_bfloat16* __restrict__ w1b,
+                                   __nv_bfloat16* __restrict__ w2t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kHid * 16) {
+        const int h = i >> 4, k = i & 15;
+        const float v = k < F ? th[h * F + k] : (k == 15 ? th[kHid * F + h] : 0.f);
+        w1b[i] = __float2bfloat16_rn(v);
+    } else if (i < kHid * 16 + kHid * kHid) {
+        const int e = i - kHid * 16, h = e / kHid, f = e - h * kHid;
+        w2t[e] = __float2bfloat16_rn(th[kHid * F + kHid + f * kHid + h]);
+    }
+}
+
+// dZ1^T = (dH1 * ELU'(z1))^T, one thread per row (z1 recomputed in fp32 from the bf16
+// inputs and weights); padding columns [R, ldR) get zeros
+__global__ void __launch_bounds__(256) lfb_dz1_kernel(BackBufs o, int R) {
+    __shared__ float w[kHid][16];
+    for (int i = threadIdx.x; i < kHid * 16; i += blockDim.x) w[i >> 4][i & 15] = __bfloat162float(o.w1b[i]);
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= o.ldR) return;
+    const size_t ld = (size_t)o.ldR;
+    if (r >= R) {
+        for (int h = 0; h < kHid; ++h) o.dz1t[h * ld + r] = __float2bfloat16_rn(0.f);
+        return;
+    }
+    float x[16];
+    const uint4* xr = reinterpret_cast<const uint4*>(o.x + (size_t)r * 16);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const uint4 u = xr[q];
+        const uint32_t p[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            x[8 * q + 2 * e] = __uint_as_float(p[e] << 16);
+            x[8 * q + 2 * e + 1] = __uint_as_float(p[e] & 0xFFFF0000u);
+        }
+    }
+#pragma unroll 4
+    for (int h = 0; h < kHid; ++h) {
+        float z = 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) z = fmaf(x[k], w[h][k], z);
+        const float g = __bfloat162float(o.dh1t[h * ld + r]);
+        o.dz1t[h * ld + r] = __float2bfloat16_rn(g * (z > 0.f ? 1.f : expf(z)));
+    }
+}
+
+// the weight-gradient partials added in split order, into the masters' layout
+// [W1 (96 x F) | b1 | W2 (96 x 96) | b2]: ws1 [S1][96][16] ([dW1 | . | db1]),
+// ws2 [S2][96][kLdW2] ([dW2 | db2])
+__global__ void lfb_reduce_kernel(const float* __restrict__ ws1, int S1, const float* __restrict__ ws2, int S2, int F,
+                                  float* __restrict__ g) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nW1 = kHid * F, nW2 = kHid * kHid;
+    if (e >= nW1 + kHid + nW2 + kHid) return;
+    const float* p;
+    int S;
+    size_t stride;
+    if (e < nW1 + kHid) {
+        const int h = e < nW1 ? e / F : e - nW1, k = e < nW1 ? e - h * F : 15;
+        p = ws1 + h * 16 + k; S = S1; stride = (size_t)kHid * 16;
+    } else {
+        const int q = e - nW1 - kHid;
+        const int f = q < nW2 ? q / kHid : q - nW2, h = q < nW2 ? q - f * kHid : kHid;
+        p = ws2 + f * kLdW2 + h; S = S2; stride = (size_t)kHid * kLdW2;
+    }
     float acc = 0.f;
-    for (int k = 0; k < blocks; ++k) acc += p[(size_t)k * P];
-    grad[(size_t)net * grad_net + e] = acc;
+    for (int s = 0; s < S; ++s) acc += p[s * stride];
+    g[e] = acc;
 }
 
 // The inference images of both networks' set encoders from the masters:
@@ -1012,7 +1071,6 @@ sf_status sf_lf_sync(sf_lf_handle m) {
 // after every update, so the training forward and the rollout's forward use
 // the same weights.  The trunk input of the training forward is kept in fp32
 // (the trunk MLP rounds it to bf16 as the inference path does).
-constexpr int kBackBlocks = 148;
 
 struct LfTrainer {
     sf_lf* lf = nullptr;
@@ -1024,7 +1082,13 @@ struct LfTrainer {
     float *theta = nullptr, *grad = nullptr, *mom = nullptr, *var = nullptr;
     size_t n_set = 0, goff[2] = {0, 0};
     int P[2] = {0, 0};
-    float* part = nullptr;    // [2][kBackBlocks][max P]
+    // set-encoder backward: per group the distinct-slot counts and first rows of both
+    // networks' samples, the row buffers of one (group, network) pass (sized for 96 rows
+    // a sample, the most a sample can have) and the split-K partials
+    int* nd[2] = {nullptr, nullptr};      // per group [2][cap]
+    int* offs[2] = {nullptr, nullptr};    // per group [2][cap + 1]
+    BackBufs bb{};
+    float *ws1 = nullptr, *ws2 = nullptr;
     float* sq = nullptr;      // [kSqBlocks]
     int adam_t = 0;
     // batch buffers of the last forward
@@ -1106,10 +1170,10 @@ sf_status lft_create(sf_lf_handle lf, cudaStream_t st, LfTrainer** out) {
     }
     t->goff[1] = 2 * (size_t)t->P[0];
     t->n_set = 2 * (size_t)(t->P[0] + t->P[1]);
-    const int pmaxP = std::max(t->P[0], t->P[1]);
     ok = ok && talloc(t, &t->theta, t->n_set) && talloc(t, &t->grad, t->n_set) && talloc(t, &t->mom, t->n_set) &&
-         talloc(t, &t->var, t->n_set) && talloc(t, &t->part, (size_t)2 * kBackBlocks * pmaxP) &&
-         talloc(t, &t->sq, kSqBlocks);
+         talloc(t, &t->var, t->n_set) && talloc(t, &t->sq, kSqBlocks) &&
+         talloc(t, &t->ws1, (size_t)kBackSplit * kHid * 16) && talloc(t, &t->ws2, (size_t)kBackSplit * kHid * kLdW2) &&
+         talloc(t, &t->bb.w1b, (size_t)kHid * 16) && talloc(t, &t->bb.w2t, (size_t)kHid * kHid);
     if (ok) {   // the masters from the network's parameters: group blocks are contiguous in the flat layout
         std::vector<float> h(t->n_set);
         for (int g = 0; g < 2; ++g)
@@ -1117,9 +1181,7 @@ sf_status lft_create(sf_lf_handle lf, cudaStream_t st, LfTrainer** out) {
                 const int l0 = g == 0 ? L_ROAD0 : L_VEH0;
                 std::memcpy(h.data() + t->goff[g] + (size_t)n * t->P[g], P + FL.w[n][l0], (size_t)t->P[g] * 4);
             }
-        ok = cudaMemcpy(t->theta, h.data(), t->n_set * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaFuncSetAttribute(lf_set_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBackSmem) ==
-                 cudaSuccess;
+        ok = cudaMemcpy(t->theta, h.data(), t->n_set * 4, cudaMemcpyHostToDevice) == cudaSuccess;
     }
     if (!ok) {
         lft_destroy(t);
@@ -1148,7 +1210,14 @@ sf_status lft_reserve(LfTrainer* t, int rows) {
     cudaStreamSynchronize(t->st);
     bool ok = talloc(t, &t->xf, (size_t)2 * rows * 256) && talloc(t, &t->dx, (size_t)2 * rows * 256);
     for (int g = 0; g < 2 && ok; ++g)
-        ok = talloc(t, &t->pmax[g], (size_t)2 * rows * kHid) && talloc(t, &t->amax[g], (size_t)2 * rows * kHid);
+        ok = talloc(t, &t->pmax[g], (size_t)2 * rows * kHid) && talloc(t, &t->amax[g], (size_t)2 * rows * kHid) &&
+             talloc(t, &t->nd[g], (size_t)2 * rows) && talloc(t, &t->offs[g], (size_t)2 * (rows + 1));
+    // the backward's rows: at most 96 a sample (one per pooled feature)
+    const size_t ldcap = std::max<size_t>(128, ((size_t)kHid * rows + 63) / 64 * 64);
+    BackBufs& o = t->bb;
+    ok = ok && talloc(t, &o.x, ldcap * 16) && talloc(t, &o.xt, 16 * ldcap) && talloc(t, &o.dz2, ldcap * kHid) &&
+         talloc(t, &o.dz2t, kHid * ldcap) && talloc(t, &o.h1t, (kHid + 1) * ldcap) && talloc(t, &o.dh1t, kHid * ldcap) &&
+         talloc(t, &o.dz1t, kHid * ldcap);
     for (int n = 0; n < 2 && ok; ++n)
         ok = sf_mlp_reserve(t->ego[n], rows) == SF_OK && sf_mlp_reserve(t->trunk[n], rows) == SF_OK;
     if (!ok) return tfail(t, SF_ERR_OOM, "late-fusion training buffers");
@@ -1199,6 +1268,21 @@ sf_status lft_forward(LfTrainer* t, const float* d_obs, const int32_t* d_n_road,
     return s == SF_OK ? SF_OK : tfail(t, s, "late-fusion training forward: trunk");
 }
 
+namespace {
+// one product of the set-encoder backward on the tensor cores: C = A B^T (A [M][K], B [N][K]
+// bf16), written transposed (out_t [N][ldt]) or as split-K partials (ws [splits][M][ldc])
+cudaError_t back_gemm(LfTrainer* t, const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K, int act,
+                      __nv_bfloat16* out_t, int ldt, float* ws, int splits, int ldc, int bn) {
+    GemmArgs g{};
+    g.A = A; g.B = B; g.M = M; g.N = N; g.Nb = N; g.K = K; g.act = act;
+    g.out_bf16_t = out_t; g.ldt = ldt;
+    g.ws = ws; g.splits = splits; g.ldc = ldc;
+    g.bn = bn;
+    g.err = t->lf->d_err;
+    return sf_gemm_launch(g, t->st);
+}
+}  // namespace
+
 sf_status lft_backward(LfTrainer* t, const float* d_dmean, const float* d_dvalue, int rows) {
     if (!t || !d_dmean || !d_dvalue || rows != t->rows) return SF_ERR_INVALID_ARG;
     const size_t xnet = (size_t)rows * 256;
@@ -1206,9 +1290,14 @@ sf_status lft_backward(LfTrainer* t, const float* d_dmean, const float* d_dvalue
     if (s == SF_OK) s = sf_mlp_backward_dx_on(t->trunk[1], t->st, d_dvalue, 1, rows, t->dx + xnet, 256);
     for (int n = 0; n < 2 && s == SF_OK; ++n) s = sf_mlp_backward_on(t->ego[n], t->st, t->dx + n * xnet, 256, rows);
     if (s != SF_OK) return tfail(t, s, "late-fusion backward: dense layers");
+    // set encoders: the rows of every (group, network) pass, counted first (one wait for
+    // the four row totals, which size the products), then the products pass by pass
     cudaError_t e = cudaSuccess;
+    BackRows br[2];
+    int tot[2][2] = {{0, 0}, {0, 0}};
     for (int g = 0; g < 2 && e == cudaSuccess; ++g) {
-        SetBackArgs b{};
+        BackRows& b = br[g];
+        b = BackRows{};
         b.obs = t->obs; b.ld = kObs;
         b.off = g == 0 ? kRoad0 : kVeh0;
         b.F = g == 0 ? kPT : kNB;
@@ -1221,13 +1310,50 @@ sf_status lft_backward(LfTrainer* t, const float* d_dmean, const float* d_dvalue
         b.amax = t->amax[g];
         b.dx = t->dx; b.dx_net = xnet; b.lddx = 256;
         b.xoff = g == 0 ? 64 : 160;
-        b.part = t->part;
-        b.P = t->P[g];
-        lf_set_back_kernel<<<dim3(kBackBlocks, 2), kBackThreads, kBackSmem, t->st>>>(b);
-        lf_part_sum_kernel<<<dim3((unsigned)((t->P[g] + 255) / 256), 2), 256, 0, t->st>>>(
-            t->part, kBackBlocks, t->P[g], t->grad + t->goff[g], t->P[g]);
+        b.nd = t->nd[g];
+        b.offs = t->offs[g];
+        lfb_count_kernel<<<dim3((unsigned)((rows + 7) / 8), 2), 256, 0, t->st>>>(b);
+        lfb_scan_kernel<<<2, 1024, 0, t->st>>>(b.nd, rows, b.offs);
         e = cudaGetLastError();
+        for (int n = 0; n < 2 && e == cudaSuccess; ++n)
+            e = cudaMemcpyAsync(&tot[g][n], b.offs + (size_t)n * (rows + 1) + rows, sizeof(int), cudaMemcpyDeviceToHost,
+                                t->st);
     }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(t->st);
+    for (int g = 0; g < 2 && e == cudaSuccess; ++g)
+        for (int n = 0; n < 2 && e == cudaSuccess; ++n) {
+            const int R = tot[g][n], F = br[g].F, P = t->P[g];
+            float* gout = t->grad + t->goff[g] + (size_t)n * P;
+            if (R <= 0) {   // no sample of this group has a filled slot: no gradient
+                e = cudaMemsetAsync(gout, 0, (size_t)P * 4, t->st);
+                continue;
+            }
+            BackBufs o = t->bb;
+            o.ldR = std::max(128, (R + 63) / 64 * 64);
+            const int S = std::min(kBackSplit, o.ldR / 64);   // the GEMM's split of ldR / 64 K tiles
+            lfb_weights_kernel<<<(kHid * 16 + kHid * kHid + 255) / 256, 256, 0, t->st>>>(
+                br[g].theta + (size_t)n * P, F, o.w1b, o.w2t);
+            lfb_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, t->st>>>(br[g], o, n);
+            lfb_pad_kernel<<<16 + kHid + kHid + 1, 128, 0, t->st>>>(o, R);
+            e = cudaGetLastError();
+            // H1^T = ELU(X W1b^T)^T; dH1^T = (dZ2 W2)^T
+            if (e == cudaSuccess) e = back_gemm(t, o.x, o.w1b, R, kHid, 16, SF_ACT_ELU, o.h1t, o.ldR, nullptr, 1, kHid, 128);
+            if (e == cudaSuccess)
+                e = back_gemm(t, o.dz2, o.w2t, R, kHid, kHid, SF_ACT_NONE, o.dh1t, o.ldR, nullptr, 1, kHid, 128);
+            if (e == cudaSuccess) {
+                lfb_dz1_kernel<<<(unsigned)((o.ldR + 255) / 256), 256, 0, t->st>>>(o, R);
+                e = cudaGetLastError();
+            }
+            // [dW2 | db2] = dZ2^T [H1 | 1]; [dW1 | . | db1] = dZ1^T X (K: the rows, split)
+            if (e == cudaSuccess)
+                e = back_gemm(t, o.dz2t, o.h1t, kHid, kHid + 1, o.ldR, SF_ACT_NONE, nullptr, 0, t->ws2, S, kLdW2, 128);
+            if (e == cudaSuccess)
+                e = back_gemm(t, o.dz1t, o.xt, kHid, 16, o.ldR, SF_ACT_NONE, nullptr, 0, t->ws1, S, 16, 64);
+            if (e == cudaSuccess) {
+                lfb_reduce_kernel<<<(unsigned)((P + 255) / 256), 256, 0, t->st>>>(t->ws1, S, t->ws2, S, F, gout);
+                e = cudaGetLastError();
+            }
+        }
     return e == cudaSuccess ? SF_OK
                             : tfail(t, SF_ERR_CUDA, std::string("late-fusion backward: ") + cudaGetErrorString(e));
 }
