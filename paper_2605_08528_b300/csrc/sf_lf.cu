@@ -422,7 +422,7 @@ __global__ void lf_embed_kernel(const __nv_bfloat16* __restrict__ xa, const __nv
 // column 15, dZ2 its row of dp_f over the features f whose maximum it holds
 // (zeros elsewhere).  Over the R rows of a minibatch:
 //   H1 = ELU(X W1b^T)        W1b: bf16 W1 with the bf16 b1 at column 15 (the forward's image)
-//   dH1 = dZ2 W2,  dZ1 = dH1 * ELU'(z1), z1 recomputed in fp32 from X and W1b
+//   dH1 = dZ2 W2,  dZ1 = dH1 * ELU'(z1), with ELU'(z1) = h1 + 1 where h1 <= 0
 //   [dW2 | db2] = dZ2^T [H1 | 1],   [dW1 | . | db1] = dZ1^T X
 // The two weight-gradient products reduce over the rows with split K, their
 // partials added in split order, so the result repeats bit for bit.
@@ -471,40 +471,42 @@ __global__ void __launch_bounds__(256) lfb_count_kernel(const BackRows a) {
 }
 
 // first row of every sample (exclusive prefix sum of the counts, samples in order)
-// and the total R, per network (one block each)
+// and the total R, per network (one block each, 1024 samples a pass, loads coalesced)
 __global__ void __launch_bounds__(1024) lfb_scan_kernel(const int* __restrict__ nd, int B, int* __restrict__ offs) {
     __shared__ int wsum[32];
+    __shared__ int tile_total;
     const int net = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int per = (B + 1023) / 1024, i0 = min(B, t * per), i1 = min(B, i0 + per);
     const int* d = nd + (size_t)net * B;
     int* o = offs + (size_t)net * (B + 1);
-    int s = 0;
-    for (int i = i0; i < i1; ++i) s += d[i];
-    int incl = s;
-#pragma unroll
-    for (int k = 1; k < 32; k <<= 1) {
-        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, k);
-        if (lane >= k) incl += v;
-    }
-    if (lane == 31) wsum[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        const int v = wsum[lane];
-        int iv = v;
+    int carry = 0;
+    for (int base = 0; base < B; base += 1024) {
+        const int i = base + t;
+        const int v = i < B ? d[i] : 0;
+        int incl = v;
 #pragma unroll
         for (int k = 1; k < 32; k <<= 1) {
-            const int u = __shfl_up_sync(0xFFFFFFFFu, iv, k);
-            if (lane >= k) iv += u;
+            const int u = __shfl_up_sync(0xFFFFFFFFu, incl, k);
+            if (lane >= k) incl += u;
         }
-        wsum[lane] = iv - v;
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const int x = wsum[lane];
+            int ix = x;
+#pragma unroll
+            for (int k = 1; k < 32; k <<= 1) {
+                const int u = __shfl_up_sync(0xFFFFFFFFu, ix, k);
+                if (lane >= k) ix += u;
+            }
+            wsum[lane] = ix - x;
+            if (lane == 31) tile_total = ix;
+        }
+        __syncthreads();
+        if (i < B) o[i] = carry + wsum[w] + incl - v;
+        carry += tile_total;
+        __syncthreads();   // wsum and tile_total are rewritten by the next pass
     }
-    __syncthreads();
-    int run = wsum[w] + incl - s;
-    for (int i = i0; i < i1; ++i) {
-        o[i] = run;
-        run += d[i];
-    }
-    if (t == 1023) o[B] = run;
+    if (t == 0) o[B] = carry;
 }
 
 // the row buffers of one network's products (ldR: row stride of the transposed ones)
@@ -522,7 +524,7 @@ struct BackBufs {
 };
 
 // the rows of network net's products, one warp per sample: the slots' inputs (X, X^T),
-// dZ2 and dZ2^T, and the ones row of H1^T
+// dp into dZ2 and dZ2^T (zeroed before: one nonzero per feature), and the ones row of H1^T
 __global__ void __launch_bounds__(256) lfb_rows_kernel(const BackRows a, const BackBufs o, int net) {
     __shared__ unsigned words[8][kSlotWords + 1];
     __shared__ int wpre[8][kSlotWords + 1];   // set bits before each word
@@ -581,34 +583,22 @@ __global__ void __launch_bounds__(256) lfb_rows_kernel(const BackRows a, const B
 #pragma unroll
         for (int k = 0; k < 16; ++k) o.xt[(size_t)k * ldR + row] = __float2bfloat16_rn(x[k]);
         o.h1t[(size_t)kHid * ldR + row] = __float2bfloat16_rn(1.f);
-        uint4* dr = reinterpret_cast<uint4*>(o.dz2 + row * kHid);
-#pragma unroll 1
-        for (int c = 0; c < kHid / 8; ++c) {
-            uint32_t p[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int f = 8 * c + 2 * e;
-                p[e] = pack_bf16(rank[warp][f] == j ? dpv[warp][f] : 0.f, rank[warp][f + 1] == j ? dpv[warp][f + 1] : 0.f);
-            }
-            dr[c] = make_uint4(p[0], p[1], p[2], p[3]);
-        }
     }
-    for (int f = 0; f < kHid; ++f) {       // dZ2^T: the sample's D columns of each feature (lanes: columns)
-        const int rf = rank[warp][f];
-        const float v = dpv[warp][f];
-        for (int j = lane; j < D; j += 32)
-            o.dz2t[(size_t)f * ldR + r0 + j] = __float2bfloat16_rn(j == rf ? v : 0.f);
+    for (int f = lane; f < kHid; f += 32) {   // the feature's dp in its slot's row
+        const int r = rank[warp][f];
+        if (r < 0) continue;
+        const __nv_bfloat16 v = __float2bfloat16_rn(dpv[warp][f]);
+        o.dz2[((size_t)r0 + r) * kHid + f] = v;
+        o.dz2t[(size_t)f * ldR + r0 + r] = v;
     }
 }
 
 // zeros in the padding columns [R, ldR) of the transposed operands the weight-gradient
-// products read (X^T 16 rows, dZ2^T 96, H1^T 97), one block per row
+// products read (X^T 16 rows, H1^T 97; dZ2^T is zeroed whole), one block per row
 __global__ void lfb_pad_kernel(BackBufs o, int R) {
     const int row = blockIdx.x, c = R + threadIdx.x;
     if (c >= o.ldR) return;
-    __nv_bfloat16* p = row < 16 ? o.xt + (size_t)row * o.ldR
-                     : row < 16 + kHid ? o.dz2t + (size_t)(row - 16) * o.ldR
-                                       : o.h1t + (size_t)(row - 16 - kHid) * o.ldR;
+    __nv_bfloat16* p = row < 16 ? o.xt + (size_t)row * o.ldR : o.h1t + (size_t)(row - 16) * o.ldR;
     p[c] = __float2bfloat16_rn(0.f);
 }
 
@@ -627,39 +617,29 @@ __global__ void lfb_weights_kernel(const float* __restrict__ th, int F, __nv_bfl
     }
 }
 
-// dZ1^T = (dH1 * ELU'(z1))^T, one thread per row (z1 recomputed in fp32 from the bf16
-// inputs and weights); padding columns [R, ldR) get zeros
+// dZ1^T = (dH1 * ELU'(z1))^T elementwise on the transposed layout, ELU'(z1) from the
+// recomputed bf16 H1 (1 where h1 > 0, else h1 + 1 = exp(z1)); padding columns get zeros.
+// Eight columns a thread (16-byte accesses; ldR is a multiple of 64)
 __global__ void __launch_bounds__(256) lfb_dz1_kernel(BackBufs o, int R) {
-    __shared__ float w[kHid][16];
-    for (int i = threadIdx.x; i < kHid * 16; i += blockDim.x) w[i >> 4][i & 15] = __bfloat162float(o.w1b[i]);
-    __syncthreads();
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = 8 * (blockIdx.x * blockDim.x + threadIdx.x), h = blockIdx.y;
     if (r >= o.ldR) return;
-    const size_t ld = (size_t)o.ldR;
-    if (r >= R) {
-        for (int h = 0; h < kHid; ++h) o.dz1t[h * ld + r] = __float2bfloat16_rn(0.f);
-        return;
-    }
-    float x[16];
-    const uint4* xr = reinterpret_cast<const uint4*>(o.x + (size_t)r * 16);
+    const size_t i = (size_t)h * o.ldR + r;
+    const uint4 hv = *reinterpret_cast<const uint4*>(o.h1t + i);
+    const uint4 gv = *reinterpret_cast<const uint4*>(o.dh1t + i);
+    const uint32_t hp[4] = {hv.x, hv.y, hv.z, hv.w}, gp[4] = {gv.x, gv.y, gv.z, gv.w};
+    uint32_t out[4];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const uint4 u = xr[q];
-        const uint32_t p[4] = {u.x, u.y, u.z, u.w};
+    for (int e = 0; e < 4; ++e) {
+        float v[2];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            x[8 * q + 2 * e] = __uint_as_float(p[e] << 16);
-            x[8 * q + 2 * e + 1] = __uint_as_float(p[e] & 0xFFFF0000u);
+        for (int q = 0; q < 2; ++q) {
+            const float h1 = __uint_as_float(q ? (hp[e] & 0xFFFF0000u) : (hp[e] << 16));
+            const float g = __uint_as_float(q ? (gp[e] & 0xFFFF0000u) : (gp[e] << 16));
+            v[q] = r + 2 * e + q < R ? g * (h1 > 0.f ? 1.f : h1 + 1.f) : 0.f;
         }
+        out[e] = pack_bf16(v[0], v[1]);
     }
-#pragma unroll 4
-    for (int h = 0; h < kHid; ++h) {
-        float z = 0.f;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) z = fmaf(x[k], w[h][k], z);
-        const float g = __bfloat162float(o.dh1t[h * ld + r]);
-        o.dz1t[h * ld + r] = __float2bfloat16_rn(g * (z > 0.f ? 1.f : expf(z)));
-    }
+    *reinterpret_cast<uint4*>(o.dz1t + i) = make_uint4(out[0], out[1], out[2], out[3]);
 }
 
 // the weight-gradient partials added in split order, into the masters' layout
@@ -1333,15 +1313,17 @@ sf_status lft_backward(LfTrainer* t, const float* d_dmean, const float* d_dvalue
             const int S = std::min(kBackSplit, o.ldR / 64);   // the GEMM's split of ldR / 64 K tiles
             lfb_weights_kernel<<<(kHid * 16 + kHid * kHid + 255) / 256, 256, 0, t->st>>>(
                 br[g].theta + (size_t)n * P, F, o.w1b, o.w2t);
+            e = cudaMemsetAsync(o.dz2, 0, (size_t)R * kHid * 2, t->st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(o.dz2t, 0, (size_t)kHid * o.ldR * 2, t->st);
             lfb_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, t->st>>>(br[g], o, n);
-            lfb_pad_kernel<<<16 + kHid + kHid + 1, 128, 0, t->st>>>(o, R);
-            e = cudaGetLastError();
+            lfb_pad_kernel<<<16 + kHid + 1, 128, 0, t->st>>>(o, R);
+            if (e == cudaSuccess) e = cudaGetLastError();
             // H1^T = ELU(X W1b^T)^T; dH1^T = (dZ2 W2)^T
             if (e == cudaSuccess) e = back_gemm(t, o.x, o.w1b, R, kHid, 16, SF_ACT_ELU, o.h1t, o.ldR, nullptr, 1, kHid, 128);
             if (e == cudaSuccess)
                 e = back_gemm(t, o.dz2, o.w2t, R, kHid, kHid, SF_ACT_NONE, o.dh1t, o.ldR, nullptr, 1, kHid, 128);
             if (e == cudaSuccess) {
-                lfb_dz1_kernel<<<(unsigned)((o.ldR + 255) / 256), 256, 0, t->st>>>(o, R);
+                lfb_dz1_kernel<<<dim3((unsigned)((o.ldR / 8 + 255) / 256), kHid), 256, 0, t->st>>>(o, R);
                 e = cudaGetLastError();
             }
             // [dW2 | db2] = dZ2^T [H1 | 1]; [dW1 | . | db1] = dZ1^T X (K: the rows, split)
