@@ -421,8 +421,9 @@ __global__ void lf_embed_kernel(const __nv_bfloat16* __restrict__ xa, const __nv
 // b's j-th distinct maximising slot (ascending), X its bf16 inputs with 1 at
 // column 15, dZ2 its row of dp_f over the features f whose maximum it holds
 // (zeros elsewhere).  Over the R rows of a minibatch:
-//   H1 = ELU(X W1b^T)        W1b: bf16 W1 with the bf16 b1 at column 15 (the forward's image)
-//   dH1 = dZ2 W2,  dZ1 = dH1 * ELU'(z1), with ELU'(z1) = h1 + 1 where h1 <= 0
+//   z1 = X W1b^T, H1 = ELU(z1)   W1b: bf16 W1 with the bf16 b1 at column 15 (the forward's
+//                                 image); K = 16, so on the CUDA cores, fp32 sums
+//   dH1 = dZ2 W2,  dZ1 = dH1 * ELU'(z1)
 //   [dW2 | db2] = dZ2^T [H1 | 1],   [dW1 | . | db1] = dZ1^T X
 // The two weight-gradient products reduce over the rows with split K, their
 // partials added in split order, so the result repeats bit for bit.
@@ -593,12 +594,12 @@ __global__ void __launch_bounds__(256) lfb_rows_kernel(const BackRows a, const B
     }
 }
 
-// zeros in the padding columns [R, ldR) of the transposed operands the weight-gradient
-// products read (X^T 16 rows, H1^T 97; dZ2^T is zeroed whole), one block per row
+// zeros in the padding columns [R, ldR) of X^T (16 rows) and of the ones row of H1^T
+// (dZ2^T is zeroed whole, the other rows of H1^T with dZ1^T), one block per row
 __global__ void lfb_pad_kernel(BackBufs o, int R) {
     const int row = blockIdx.x, c = R + threadIdx.x;
     if (c >= o.ldR) return;
-    __nv_bfloat16* p = row < 16 ? o.xt + (size_t)row * o.ldR : o.h1t + (size_t)(row - 16) * o.ldR;
+    __nv_bfloat16* p = row < 16 ? o.xt + (size_t)row * o.ldR : o.h1t + (size_t)kHid * o.ldR;
     p[c] = __float2bfloat16_rn(0.f);
 }
 
@@ -617,29 +618,54 @@ __global__ void lfb_weights_kernel(const float* __restrict__ th, int F, __nv_bfl
     }
 }
 
-// dZ1^T = (dH1 * ELU'(z1))^T elementwise on the transposed layout, ELU'(z1) from the
-// recomputed bf16 H1 (1 where h1 > 0, else h1 + 1 = exp(z1)); padding columns get zeros.
-// Eight columns a thread (16-byte accesses; ldR is a multiple of 64)
-__global__ void __launch_bounds__(256) lfb_dz1_kernel(BackBufs o, int R) {
-    const int r = 8 * (blockIdx.x * blockDim.x + threadIdx.x), h = blockIdx.y;
+// H1^T = bf16(ELU(z1)) and dZ1^T = bf16(dH1 * ELU'(z1)) with z1 = X W1b^T recomputed in
+// fp32 from the bf16 inputs and weights (K = 16: a CUDA-core job), two rows a thread
+// (4-byte accesses; lanes hold consecutive rows, so every store is contiguous across the
+// warp); columns [R, ldR) get zeros
+__global__ void __launch_bounds__(256) lfb_h1dz1_kernel(BackBufs o, int R) {
+    __shared__ float w[kHid][16];
+    for (int i = threadIdx.x; i < kHid * 16; i += blockDim.x) w[i >> 4][i & 15] = __bfloat162float(o.w1b[i]);
+    __syncthreads();
+    const int r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (r >= o.ldR) return;
-    const size_t i = (size_t)h * o.ldR + r;
-    const uint4 hv = *reinterpret_cast<const uint4*>(o.h1t + i);
-    const uint4 gv = *reinterpret_cast<const uint4*>(o.dh1t + i);
-    const uint32_t hp[4] = {hv.x, hv.y, hv.z, hv.w}, gp[4] = {gv.x, gv.y, gv.z, gv.w};
-    uint32_t out[4];
+    const size_t ld = (size_t)o.ldR;
+    float x[2][16];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        float v[2];
+    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[q][k] = 0.f;
+        if (r + q < R) {
+            const uint4* xr = reinterpret_cast<const uint4*>(o.x + (size_t)(r + q) * 16);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const uint4 u = xr[c];
+                const uint32_t p[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    x[q][8 * c + 2 * e] = __uint_as_float(p[e] << 16);
+                    x[q][8 * c + 2 * e + 1] = __uint_as_float(p[e] & 0xFFFF0000u);
+                }
+            }
+        }
+    }
+#pragma unroll 2
+    for (int h = 0; h < kHid; ++h) {
+        const uint32_t gp = *reinterpret_cast<const uint32_t*>(o.dh1t + h * ld + r);
+        float hv[2], dv[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const float h1 = __uint_as_float(q ? (hp[e] & 0xFFFF0000u) : (hp[e] << 16));
-            const float g = __uint_as_float(q ? (gp[e] & 0xFFFF0000u) : (gp[e] << 16));
-            v[q] = r + 2 * e + q < R ? g * (h1 > 0.f ? 1.f : h1 + 1.f) : 0.f;
+            float z = 0.f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) z = fmaf(x[q][k], w[h][k], z);
+            const float e = z > 0.f ? 1.f : expf(z);
+            const float g = __uint_as_float(q ? (gp & 0xFFFF0000u) : (gp << 16));
+            const bool in = r + q < R;
+            hv[q] = in ? (z > 0.f ? z : e - 1.f) : 0.f;
+            dv[q] = in ? g * e : 0.f;
         }
-        out[e] = pack_bf16(v[0], v[1]);
+        *reinterpret_cast<uint32_t*>(o.h1t + h * ld + r) = pack_bf16(hv[0], hv[1]);
+        *reinterpret_cast<uint32_t*>(o.dz1t + h * ld + r) = pack_bf16(dv[0], dv[1]);
     }
-    *reinterpret_cast<uint4*>(o.dz1t + i) = make_uint4(out[0], out[1], out[2], out[3]);
 }
 
 // the weight-gradient partials added in split order, into the masters' layout
@@ -1316,14 +1342,13 @@ sf_status lft_backward(LfTrainer* t, const float* d_dmean, const float* d_dvalue
             e = cudaMemsetAsync(o.dz2, 0, (size_t)R * kHid * 2, t->st);
             if (e == cudaSuccess) e = cudaMemsetAsync(o.dz2t, 0, (size_t)kHid * o.ldR * 2, t->st);
             lfb_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, t->st>>>(br[g], o, n);
-            lfb_pad_kernel<<<16 + kHid + 1, 128, 0, t->st>>>(o, R);
+            lfb_pad_kernel<<<16 + 1, 128, 0, t->st>>>(o, R);
             if (e == cudaSuccess) e = cudaGetLastError();
-            // H1^T = ELU(X W1b^T)^T; dH1^T = (dZ2 W2)^T
-            if (e == cudaSuccess) e = back_gemm(t, o.x, o.w1b, R, kHid, 16, SF_ACT_ELU, o.h1t, o.ldR, nullptr, 1, kHid, 128);
+            // dH1^T = (dZ2 W2)^T on the tensor cores; H1^T and dZ1^T
             if (e == cudaSuccess)
                 e = back_gemm(t, o.dz2, o.w2t, R, kHid, kHid, SF_ACT_NONE, o.dh1t, o.ldR, nullptr, 1, kHid, 128);
             if (e == cudaSuccess) {
-                lfb_dz1_kernel<<<dim3((unsigned)((o.ldR / 8 + 255) / 256), kHid), 256, 0, t->st>>>(o, R);
+                lfb_h1dz1_kernel<<<(unsigned)((o.ldR / 2 + 255) / 256), 256, 0, t->st>>>(o, R);
                 e = cudaGetLastError();
             }
             // [dW2 | db2] = dZ2^T [H1 | 1]; [dW1 | . | db1] = dZ1^T X (K: the rows, split)
