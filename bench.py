@@ -704,7 +704,8 @@ def main_ours(args):
                 "value": ppo_lf["casps_train"] * world, "unit": "CASPS (training: rollout + PPO update)",
                 "workload": "256 worlds x 16 agents, App. L hyperparameters, the paper's late-fusion actor-critic "
                             "(App. E) on the full 1929-value observation (App. D): tensor-core set encoders with "
-                            "masked max-pool, trunk and heads; backward through the max-pool on the CUDA cores",
+                            "masked max-pool, trunk and heads; backward through the max-pool as tensor-core products over "
+                            "each sample's distinct maximising slots",
                 "rollout_ms": ppo_lf["collect_ms"], "update_ms": ppo_lf["update_ms"],
                 "rollout_casps": ppo_lf["casps_collect"] * world,
                 "stats_columns": ["mean reward", "policy loss", "value loss", "kl", "lr", "grad norm"],
