@@ -70,8 +70,11 @@ def full_obs(W, stream):
     return obs, nr, nv
 
 
-def test_lf_gradients_against_fp64():
-    W, lf, ppo, p0, stream = lf_setup()
+@pytest.mark.parametrize("worlds", [4, 24])
+def test_lf_gradients_against_fp64(worlds):
+    """24 worlds: about 7,000 rows in the set encoders' backward products (many split-K
+    partials and tiles)."""
+    W, lf, ppo, p0, stream = lf_setup(worlds=worlds)
     obs, nr, nv = full_obs(W, stream)
     A = W.A
     rng = np.random.default_rng(7)
