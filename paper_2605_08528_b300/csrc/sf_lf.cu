@@ -68,9 +68,10 @@ constexpr int kOffMeta = kOffPool + kG * kHid * 4;  // 106496: u32 [kMaxGroups] 
 constexpr int kOffMisc = kOffMeta + kMaxGroups * 4; // 112128
 constexpr int kMiscBytes = 1024;
 constexpr int kSmemBytes = kOffMisc + kMiscBytes + 1024;   // 114176: two CTAs per SM
-// the training variant pools 64-bit keys (value, then the lowest slot) after the misc area
-constexpr int kOffPool64 = kOffMisc + kMiscBytes;            // u64 [kG][96]
-constexpr int kSmemBytesTrain = kOffPool64 + kG * kHid * 8 + 1024;   // one CTA per SM
+// the training variant pools 64-bit keys (value, then the lowest slot) for items of
+// kGTrain agents, in the 32-bit pool's space: two CTAs per SM as in inference
+constexpr int kGTrain = 16;
+static_assert(kGTrain * kHid * 8 <= kG * kHid * 4, "the training pool must fit the inference pool's space");
 constexpr uint32_t kTmemCols = 256;                 // D1 at column 0 (96), D2 at column 128 (128)
 
 struct SetArgs {
@@ -156,17 +157,18 @@ __device__ __forceinline__ bool gather_row(const SetArgs& a, const uint32_t* met
     return true;
 }
 
-// Two CTAs per SM (one in the training variant); even CTAs run the actor's
-// encoder, odd ones the critic's.  The training variant also keeps, for every
-// pooled feature, the slot that holds the maximum (the lowest one on ties).
+// Two CTAs per SM; even CTAs run the actor's encoder, odd ones the critic's.
+// The training variant also keeps, for every pooled feature, the slot that
+// holds the maximum (the lowest one on ties), on items of kGTrain agents.
 template <bool TRAIN>
-__global__ void __launch_bounds__(kThreads, TRAIN ? 1 : 2) lf_set_kernel(const SetArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) lf_set_kernel(const SetArgs a) {
+    constexpr int G = TRAIN ? kGTrain : kG;   // agents per item
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(sm);
     uint32_t* pool = reinterpret_cast<uint32_t*>(sm + kOffPool);
-    unsigned long long* pool64 = reinterpret_cast<unsigned long long*>(sm + kOffPool64);   // TRAIN only
+    unsigned long long* pool64 = reinterpret_cast<unsigned long long*>(sm + kOffPool);   // TRAIN only
     uint32_t* meta = reinterpret_cast<uint32_t*>(sm + kOffMeta);
     int* rs = reinterpret_cast<int*>(sm + kOffMisc);                       // [kG + 1] item row starts (x8)
     int* cnt = reinterpret_cast<int*>(sm + kOffMisc + 640);               // [kG] filled slots per agent
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, TRAIN ? 1 : 2) lf_set_kernel(const S
     const uint4* img = a.wimg + (size_t)net * (kImgBytes / 16);
     for (int i = tid; i < kImgBytes / 16; i += kThreads) reinterpret_cast<uint4*>(sm)[i] = __ldg(img + i);
     for (int i = tid; i < kHid; i += kThreads) sb2[i] = __ldg(a.b2 + net * kHid + i);
-    for (int i = tid; i < kG * kHid; i += kThreads) {
+    for (int i = tid; i < G * kHid; i += kThreads) {
         if (TRAIN) pool64[i] = 0ull;
         else pool[i] = 0u;
     }
@@ -208,11 +210,11 @@ __global__ void __launch_bounds__(kThreads, TRAIN ? 1 : 2) lf_set_kernel(const S
     const int q = warp & 3, hh = warp >> 2;                 // TMEM lane quarter, column half of this warp
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
     __nv_bfloat16* X = net ? a.xc : a.xa;
-    const int num_items = (a.num_agents + kG - 1) / kG;
+    const int num_items = (a.num_agents + G - 1) / G;
 
     for (int item = cta; item < num_items && ok; item += ncta) {
-        const int a0 = item * kG;
-        const int na = min(kG, a.num_agents - a0);
+        const int a0 = item * G;
+        const int na = min(G, a.num_agents - a0);
         if (warp == 0) {   // each agent's slots take a multiple of 8 rows: an 8-row group is one agent's
             const int n = lane < na ? min(max(__ldg(a.count + a0 + lane), 0), a.K) : 0;
             int n8 = (n + 7) & ~7;
@@ -943,8 +945,8 @@ sf_status sf_lf_create(void* cuda_stream, sf_lf_handle* out) {
     if (okk && !attr) {
         okk = cudaFuncSetAttribute(lf_set_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) ==
                   cudaSuccess &&
-              cudaFuncSetAttribute(lf_set_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kSmemBytesTrain) == cudaSuccess;
+              cudaFuncSetAttribute(lf_set_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) ==
+                  cudaSuccess;
         attr = okk;
     }
     if (!okk || cudaMemset(m->d_err, 0, 4) != cudaSuccess || upload(m) != SF_OK) {
@@ -1264,8 +1266,8 @@ sf_status lft_forward(LfTrainer* t, const float* d_obs, const int32_t* d_n_road,
         sa.err = t->lf->d_err;
         sa.xf = t->xf; sa.xf_net = xnet; sa.ldxf = 256;
         sa.pmax = t->pmax[g]; sa.amax = t->amax[g];
-        const int items = (rows + kG - 1) / kG;
-        lf_set_kernel<true><<<2 * (items < sms ? items : sms), kThreads, kSmemBytesTrain, t->st>>>(sa);
+        const int items = (rows + kGTrain - 1) / kGTrain;
+        lf_set_kernel<true><<<2 * (items < sms ? items : sms), kThreads, kSmemBytes, t->st>>>(sa);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return tfail(t, SF_ERR_CUDA, std::string("late-fusion training forward: ") + cudaGetErrorString(e));
