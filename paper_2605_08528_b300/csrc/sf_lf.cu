@@ -526,82 +526,113 @@ struct BackBufs {
     int ldR;
 };
 
-// the rows of network net's products, one warp per sample: the slots' inputs (X, X^T),
-// dp into dZ2 and dZ2^T (zeroed before: one nonzero per feature), and the ones row of H1^T
+// the rows of network net's products: one warp per sample writes its slots' inputs (X,
+// X^T) and the ones row of H1^T; the block's 8 samples own a contiguous range of rows,
+// whose dZ2 and dZ2^T (dp_f in the row of f's slot, zeros elsewhere) are staged in
+// shared memory kRowChunk rows at a time and written out with consecutive threads on
+// consecutive elements
+constexpr int kRowChunk = 192;
+constexpr int kTileLd = kRowChunk + 2;   // bf16 stride of the staged dZ2^T rows (97 words: no bank conflicts)
 __global__ void __launch_bounds__(256) lfb_rows_kernel(const BackRows a, const BackBufs o, int net) {
     __shared__ unsigned words[8][kSlotWords + 1];
     __shared__ int wpre[8][kSlotWords + 1];   // set bits before each word
     __shared__ int rank[8][kHid];             // feature -> row of its slot within the sample (-1: none)
     __shared__ float dpv[8][kHid];            // feature -> dp
     __shared__ int slot[8][kHid];             // row within the sample -> slot
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ int s_r0[8], s_d[8];
+    __shared__ __nv_bfloat16 tile[kHid][kTileLd];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
     const int b = blockIdx.x * 8 + warp;
-    if (b >= a.B) return;   // warp-uniform
-    const int n = min(max(a.count[b], 0), a.K);
-    if (n == 0) return;     // warp-uniform: an empty group has no rows
-    slot_bitmap(a, net, b, n, lane, words[warp]);
-    if (lane == 0) {
-        int c = 0;
-        for (int w = 0; w < kSlotWords; ++w) {
-            wpre[warp][w] = c;
-            c += __popc(words[warp][w]);
-        }
-        wpre[warp][kSlotWords] = c;
-    }
-    __syncwarp();
-    const int D = wpre[warp][kSlotWords];
-    const size_t bi = ((size_t)net * a.B + b) * kHid;
-    const float* b2 = a.theta + (size_t)net * a.theta_net + kHid * a.F + kHid + kHid * kHid;
-    const float* dy = a.dx + (size_t)net * a.dx_net + (size_t)b * a.lddx + a.xoff;
-    for (int f = lane; f < kHid; f += 32) {
-        const int s = a.amax[bi + f];
-        int r = -1;
-        float d = 0.f;
-        if (s < n) {
-            const float u = a.pmax[bi + f] + b2[f];
-            d = dy[f] * (u > 0.f ? 1.f : expf(u));
-            r = wpre[warp][s >> 5] + __popc(words[warp][s >> 5] & ((1u << (s & 31)) - 1u));
-            slot[warp][r] = s;   // every feature of the slot writes the same value
-        }
-        rank[warp][f] = r;
-        dpv[warp][f] = d;
-    }
-    __syncwarp();
-    const int r0 = a.offs[(size_t)net * (a.B + 1) + b];
+    const int n = b < a.B ? min(max(a.count[b], 0), a.K) : 0;
     const int ldR = o.ldR;
-    for (int j = lane; j < D; j += 32) {   // lanes: rows
-        const size_t row = (size_t)r0 + j;
-        const float* src = a.obs + (size_t)b * a.ld + a.off + (size_t)slot[warp][j] * a.F;
-        float x[16];
+    int D = 0;
+    if (n > 0) {   // warp-uniform
+        slot_bitmap(a, net, b, n, lane, words[warp]);
+        if (lane == 0) {
+            int c = 0;
+            for (int w = 0; w < kSlotWords; ++w) {
+                wpre[warp][w] = c;
+                c += __popc(words[warp][w]);
+            }
+            wpre[warp][kSlotWords] = c;
+        }
+        __syncwarp();
+        D = wpre[warp][kSlotWords];
+        const size_t bi = ((size_t)net * a.B + b) * kHid;
+        const float* b2 = a.theta + (size_t)net * a.theta_net + kHid * a.F + kHid + kHid * kHid;
+        const float* dy = a.dx + (size_t)net * a.dx_net + (size_t)b * a.lddx + a.xoff;
+        for (int f = lane; f < kHid; f += 32) {
+            const int s = a.amax[bi + f];
+            int r = -1;
+            float d = 0.f;
+            if (s < n) {
+                const float u = a.pmax[bi + f] + b2[f];
+                d = dy[f] * (u > 0.f ? 1.f : expf(u));
+                r = wpre[warp][s >> 5] + __popc(words[warp][s >> 5] & ((1u << (s & 31)) - 1u));
+                slot[warp][r] = s;   // every feature of the slot writes the same value
+            }
+            rank[warp][f] = r;
+            dpv[warp][f] = d;
+        }
+        __syncwarp();
+        const int r0 = a.offs[(size_t)net * (a.B + 1) + b];
+        if (lane == 0) s_r0[warp] = r0;
+        for (int j = lane; j < D; j += 32) {   // lanes: rows
+            const size_t row = (size_t)r0 + j;
+            const float* src = a.obs + (size_t)b * a.ld + a.off + (size_t)slot[warp][j] * a.F;
+            float x[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) x[k] = 0.f;
+            for (int k = 0; k < 16; ++k) x[k] = 0.f;
 #pragma unroll
-        for (int k = 0; k < 7; ++k)
-            if (k < a.F) x[k] = src[k];
-        x[15] = 1.f;
-        uint4* xr = reinterpret_cast<uint4*>(o.x + row * 16);
-        xr[0] = make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
-        xr[1] = make_uint4(pack_bf16(x[8], x[9]), pack_bf16(x[10], x[11]), pack_bf16(x[12], x[13]),
-                           pack_bf16(x[14], x[15]));
+            for (int k = 0; k < 7; ++k)
+                if (k < a.F) x[k] = src[k];
+            x[15] = 1.f;
+            uint4* xr = reinterpret_cast<uint4*>(o.x + row * 16);
+            xr[0] = make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
+            xr[1] = make_uint4(pack_bf16(x[8], x[9]), pack_bf16(x[10], x[11]), pack_bf16(x[12], x[13]),
+                               pack_bf16(x[14], x[15]));
 #pragma unroll
-        for (int k = 0; k < 16; ++k) o.xt[(size_t)k * ldR + row] = __float2bfloat16_rn(x[k]);
-        o.h1t[(size_t)kHid * ldR + row] = __float2bfloat16_rn(1.f);
+            for (int k = 0; k < 16; ++k) o.xt[(size_t)k * ldR + row] = __float2bfloat16_rn(x[k]);
+            o.h1t[(size_t)kHid * ldR + row] = __float2bfloat16_rn(1.f);
+        }
     }
-    for (int f = lane; f < kHid; f += 32) {   // the feature's dp in its slot's row
-        const int r = rank[warp][f];
-        if (r < 0) continue;
-        const __nv_bfloat16 v = __float2bfloat16_rn(dpv[warp][f]);
-        o.dz2[((size_t)r0 + r) * kHid + f] = v;
-        o.dz2t[(size_t)f * ldR + r0 + r] = v;
+    if (lane == 0) s_d[warp] = D;
+    // the block's rows [rb0, rb1): its samples' first rows in order
+    const int bb0 = min(blockIdx.x * 8, a.B), bb1 = min(blockIdx.x * 8 + 8, a.B);
+    const int rb0 = a.offs[(size_t)net * (a.B + 1) + bb0], rb1 = a.offs[(size_t)net * (a.B + 1) + bb1];
+    __syncthreads();
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    for (int c0 = rb0; c0 < rb1; c0 += kRowChunk) {
+        const int cw = min(kRowChunk, rb1 - c0);
+        for (int f = warp; f < kHid; f += 8)
+            for (int c = lane; c < cw; c += 32) tile[f][c] = zero;
+        __syncthreads();
+        for (int w = 0; w < 8; ++w) {                 // every (sample, feature): dp into its row
+            if (s_d[w] == 0) continue;                 // block-uniform
+            const int f = tid;
+            if (f >= kHid) continue;
+            const int r = rank[w][f];
+            if (r < 0) continue;
+            const int c = s_r0[w] + r - c0;
+            if (c >= 0 && c < cw) tile[f][c] = __float2bfloat16_rn(dpv[w][f]);
+        }
+        __syncthreads();
+        for (int f = warp; f < kHid; f += 8)           // dZ2^T: lanes on consecutive columns
+            for (int c = lane; c < cw; c += 32) o.dz2t[(size_t)f * ldR + c0 + c] = tile[f][c];
+        for (int c = warp; c < cw; c += 8)             // dZ2: lanes on consecutive features of a row
+            for (int f = lane; f < kHid; f += 32) o.dz2[((size_t)c0 + c) * kHid + f] = tile[f][c];
+        __syncthreads();
     }
 }
 
-// zeros in the padding columns [R, ldR) of X^T (16 rows) and of the ones row of H1^T
-// (dZ2^T is zeroed whole, the other rows of H1^T with dZ1^T), one block per row
+// zeros in the padding columns [R, ldR) of X^T (16 rows), dZ2^T (96) and the ones row of
+// H1^T (its other rows are written with dZ1^T), one block per row
 __global__ void lfb_pad_kernel(BackBufs o, int R) {
     const int row = blockIdx.x, c = R + threadIdx.x;
     if (c >= o.ldR) return;
-    __nv_bfloat16* p = row < 16 ? o.xt + (size_t)row * o.ldR : o.h1t + (size_t)kHid * o.ldR;
+    __nv_bfloat16* p = row < 16 ? o.xt + (size_t)row * o.ldR
+                     : row < 16 + kHid ? o.dz2t + (size_t)(row - 16) * o.ldR
+                                       : o.h1t + (size_t)kHid * o.ldR;
     p[c] = __float2bfloat16_rn(0.f);
 }
 
@@ -1341,11 +1372,9 @@ sf_status lft_backward(LfTrainer* t, const float* d_dmean, const float* d_dvalue
             const int S = std::min(kBackSplit, o.ldR / 64);   // the GEMM's split of ldR / 64 K tiles
             lfb_weights_kernel<<<(kHid * 16 + kHid * kHid + 255) / 256, 256, 0, t->st>>>(
                 br[g].theta + (size_t)n * P, F, o.w1b, o.w2t);
-            e = cudaMemsetAsync(o.dz2, 0, (size_t)R * kHid * 2, t->st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(o.dz2t, 0, (size_t)kHid * o.ldR * 2, t->st);
             lfb_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, t->st>>>(br[g], o, n);
-            lfb_pad_kernel<<<16 + 1, 128, 0, t->st>>>(o, R);
-            if (e == cudaSuccess) e = cudaGetLastError();
+            lfb_pad_kernel<<<16 + kHid + 1, 128, 0, t->st>>>(o, R);
+            e = cudaGetLastError();
             // dH1^T = (dZ2 W2)^T on the tensor cores; H1^T and dZ1^T
             if (e == cudaSuccess)
                 e = back_gemm(t, o.dz2, o.w2t, R, kHid, kHid, SF_ACT_NONE, o.dh1t, o.ldR, nullptr, 1, kHid, 128);
