@@ -751,7 +751,10 @@ sf_status sf_ppo_loss_grads(sf_ppo_handle p, const float* d_obs, const float* d_
  * rate, norm clipping, Adam).  The backward of each masked max-pool passes a
  * feature's gradient to the slot that held the maximum (the lowest slot on
  * ties) and recomputes that slot's first layer; the weight gradients are
- * sums in a fixed order, so two runs give bit-identical weights.
+ * sums in a fixed order, so two runs give bit-identical weights.  Each
+ * minibatch step of sf_ppo_update waits once on its stream for the number of
+ * distinct maximising slots (the row count of the set encoders' backward
+ * products), so the update cannot be captured into a CUDA graph.
  * Errors: SF_ERR_INVALID_ARG (configuration), SF_ERR_STATE (no roads),
  * SF_ERR_OOM.  lf must not be used on another stream while the engine runs. */
 sf_status sf_ppo_create_lf(sf_handle h, sf_lf_handle lf, const sf_ppo_config* cfg, sf_ppo_handle* out);
