@@ -72,6 +72,7 @@ struct sf_ctx {
         WorldArgs wa{};
         static constexpr int kMaxStepNodes = 8;
         cudaGraphNode_t n_step[kMaxStepNodes] = {};                            // kernel nodes (mapped)
+        cudaKernelNodeParams kp_step[kMaxStepNodes] = {};                     // their launch parameters
         int n_steps = 0;
         cudaGraphNode_t n_act = nullptr, n_rew = nullptr, n_done = nullptr;   // copy nodes (not mapped)
         cudaGraphNode_t n_obs = nullptr;                                        // observation copy node
@@ -748,8 +749,15 @@ void find_copy_nodes(sf_ctx* h) {
         cudaGraphNodeType t;
         if (cudaGraphNodeGetType(nd, &t) != cudaSuccess) continue;
         if (t == cudaGraphNodeTypeKernel) {
-            if (h->hs.n_steps < sf_ctx::HostStep::kMaxStepNodes) h->hs.n_step[h->hs.n_steps] = nd;
-            ++h->hs.n_steps;   // more than kMaxStepNodes: not retargeted (re-captured)
+            const int i = h->hs.n_steps++;   // more than kMaxStepNodes: not retargeted (re-captured)
+            if (i < sf_ctx::HostStep::kMaxStepNodes) {
+                h->hs.n_step[i] = nd;
+                cudaKernelNodeParams kp{};
+                if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) h->hs.n_steps = sf_ctx::HostStep::kMaxStepNodes + 1;
+                kp.kernelParams = nullptr;
+                kp.extra = nullptr;
+                h->hs.kp_step[i] = kp;
+            }
             continue;
         }
         if (t != cudaGraphNodeTypeMemcpy) continue;
@@ -787,7 +795,13 @@ sf_status step_host(sf_handle h, const float* h_actions, float* h_obs, float* h_
         SF_CUDA(h, cudaStreamSynchronize(h->stream));
         return SF_OK;
     }
-    const bool pinned = page_locked(h_actions) && page_locked(h_reward) && page_locked(h_done) &&
+    // buffers with a device address are page-locked (and mapped): only the others
+    // need the pointer query
+    const float* da = A > 0 ? static_cast<const float*>(device_view(h_actions)) : nullptr;
+    float* dr = A > 0 ? static_cast<float*>(device_view(h_reward)) : nullptr;
+    uint8_t* dd = A > 0 ? static_cast<uint8_t*>(device_view(h_done)) : nullptr;
+    const bool mapped = da && dr && dd;
+    const bool pinned = (mapped || (page_locked(h_actions) && page_locked(h_reward) && page_locked(h_done))) &&
                         (!h_obs || page_locked(h_obs));
     if (!h->stream || !pinned || A == 0) {   // no graph: plain copies around the step
         if (A > 0) SF_CUDA(h, cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream));
@@ -804,10 +818,6 @@ sf_status step_host(sf_handle h, const float* h_actions, float* h_obs, float* h_
     // page-locked buffers with device addresses are read and written by the
     // step's kernels themselves (loads and posted stores over the host link);
     // others get copy nodes
-    const float* da = static_cast<const float*>(device_view(h_actions));
-    float* dr = static_cast<float*>(device_view(h_reward));
-    uint8_t* dd = static_cast<uint8_t*>(device_view(h_done));
-    const bool mapped = da && dr && dd;
     if (same && c.mapped == mapped && (!h_obs || c.n_obs)) {   // other buffers: retarget the graph's transfers
         if (h_obs)
             SF_CUDA(h, cudaGraphExecMemcpyNodeSetParams1D(c.exec, c.n_obs, h_obs, h->out.obs, obs_bytes,
@@ -817,8 +827,7 @@ sf_status step_host(sf_handle h, const float* h_actions, float* h_obs, float* h_
             c.wa.host_reward = dr;
             c.wa.host_done = dd;
             for (int i = 0; i < c.n_steps; ++i) {
-                cudaKernelNodeParams kp{};
-                SF_CUDA(h, cudaGraphKernelNodeGetParams(c.n_step[i], &kp));
+                cudaKernelNodeParams kp = c.kp_step[i];   // as captured (function, grid, block, shared memory)
                 void* step_args[] = {&c.wa};
                 kp.kernelParams = step_args;
                 kp.extra = nullptr;
