@@ -97,6 +97,7 @@ enum {
 #define SF_FLAG_INVINCIBLE 1     /* events are logged but never terminate (Sec. 4.1)    */
 #define SF_FLAG_AUTO_RESET 2     /* done agents respawn inside sf_step; else they park   */
 #define SF_FLAG_RECORD_INDICES 4 /* keep nearest-lane and k-NN indices for inspection    */
+#define SF_FLAG_METRICS 8        /* count ended episodes on the device (sf_get_metrics)  */
 
 typedef struct {
     uint64_t seed;           /* seed of the counter-based reset draws                 */
@@ -288,6 +289,46 @@ sf_status sf_get_obs(sf_handle h, float* d_obs, float* d_reward, uint8_t* d_done
  * may be NULL.  Asynchronous device-to-device copies. */
 sf_status sf_get_indices(sf_handle h, int32_t* d_lane_seg, int32_t* d_knn_points, int32_t* d_knn_agents,
                          float* d_drac);
+
+/* Episode metrics of Sec. 4 (the paragraph that defines SR, CR and DRAC),
+ * over the episodes that ended since the handle was loaded or the counters
+ * were last cleared.  With SF_FLAG_METRICS every step (sf_step, the captured
+ * graphs, sf_step_host, the surrogate step) is followed by a small kernel that
+ * keeps, per agent, the running episode's maximum step DRAC (the value of
+ * sf_get_indices) and the union of its event bits, and adds each episode that
+ * ends (done) to the counters: the success rate is the share of ended
+ * episodes that reached their goal, the collision rate the share with an
+ * inter-vehicle contact (the collision event, App. G; depth > 0 stands for
+ * the paper's 25 N contact threshold), and the DRAC figure the mean over
+ * ended episodes of their maximum DRAC, with the share above the paper's
+ * 3.4 m/s^2 highway threshold.  A masked reset (sf_reset) starts new episodes
+ * of the masked agents without counting the interrupted ones.  Counters are
+ * integers (the DRAC sum in units of 1e-6 m/s^2, each episode's maximum held
+ * to 1e6), so they do not depend on the order of the agents. */
+typedef struct {
+    uint64_t episodes;        /* ended episodes; the others count those in which the */
+    uint64_t goals;           /* event (SF_EV_*) occurred at some step: goal reached */
+    uint64_t collisions;      /* inter-vehicle contact                               */
+    uint64_t crashes;         /* below the ground, drifted or tipped over            */
+    uint64_t offroad;         /* off the road                                        */
+    uint64_t lane_forbidden;  /* in a forbidden lane                                 */
+    uint64_t idle;            /* idle                                                */
+    uint64_t timeouts;        /* the time-out                                        */
+    uint64_t nonfinite;       /* a non-finite state                                  */
+    uint64_t drac_over;       /* ended episodes whose maximum DRAC exceeded 3.4 m/s^2 */
+    double success_rate;      /* goals / episodes (SR), 0 without an ended episode   */
+    double collision_rate;    /* collisions / episodes (CR)                          */
+    double mean_episode_max_drac;  /* m/s^2                                          */
+    double drac_over_rate;    /* drac_over / episodes                                */
+} sf_metrics;
+
+/* The counters into *out (synchronises the handle's stream).
+ * Errors: SF_ERR_INVALID_ARG (NULL), SF_ERR_STATE (no roads, or the handle was
+ * created without SF_FLAG_METRICS), SF_ERR_CUDA. */
+sf_status sf_get_metrics(sf_handle h, sf_metrics* out);
+/* Clears the counters (asynchronous on the handle's stream); episodes under
+ * way count when they end.  Errors: as sf_get_metrics. */
+sf_status sf_reset_metrics(sf_handle h);
 
 /* The paper's full observation (SceneFactory App. D), 1,929 values per agent,
  * computed from the current state (after any sf_step / sf_reset / placement):

@@ -1,9 +1,10 @@
 // sf_api.cu -- the C-ABI of the vehicle step (include/sf.h).
 //
-// Host side only: argument validation, the derived road store built once at
-// load time, device allocations, the exchange layout of the agent state,
-// checkpoints and the device error word.  Every step computation runs in the
-// kernels of sf_world.cu.
+// Host side: argument validation, the derived road store built once at load
+// time, device allocations, the exchange layout of the agent state,
+// checkpoints and the device error word; and the episode-metrics pass (a
+// small kernel after each step).  Every step computation runs in the kernels
+// of sf_world.cu.
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
@@ -19,6 +20,12 @@
 namespace {
 
 thread_local std::string g_create_error;
+
+// counters of the episode metrics, in the order of sf_metrics
+enum : int {
+    kMetricEpisodes = 0, kMetricGoals, kMetricCollisions, kMetricCrashes, kMetricOffroad, kMetricLaneForb,
+    kMetricIdle, kMetricTimeouts, kMetricNonfinite, kMetricDracOver, kMetricDracMicro, kMetricCount
+};
 
 struct DevBuf {
     void* p = nullptr;
@@ -40,6 +47,11 @@ struct sf_ctx {
     float* place_buf = nullptr;
     uint8_t* all_mask = nullptr;
     float* act_buf = nullptr;   // [A][3] actions written by an attached policy
+    // episode metrics (SF_FLAG_METRICS): per agent the running episode's maximum DRAC
+    // and event bits; the counters of the ended episodes (kMetric*)
+    float* m_epmax = nullptr;
+    uint32_t* m_epev = nullptr;
+    unsigned long long* m_cnt = nullptr;
     void* surr = nullptr;       // surrogate step buffers (allocated on first use)
     void* lfb = nullptr;        // full observation and critic values of the late-fusion policy step
     struct PackSet {                // blocks of the world kernel for one (packing, staging) choice
@@ -138,12 +150,85 @@ void free_all(sf_ctx* h) {
     h->place_buf = nullptr;
     h->all_mask = nullptr;
     h->act_buf = nullptr;
+    h->m_epmax = nullptr;
+    h->m_epev = nullptr;
+    h->m_cnt = nullptr;
     h->surr = nullptr;
     h->lfb = nullptr;
     h->packsets.clear();
     h->sc = StepScratch{};
     h->loaded = false;
     h->W = h->A = h->NP = 0;
+}
+
+// ---- episode metrics (Sec. 4): success rate (episodes that reach their goal),
+// collision rate (episodes with inter-vehicle contact, the collision event),
+// mean episode-maximum DRAC and the share of episodes above 3.4 m/s^2, over the
+// episodes ended since the counters were last cleared.  One thread per agent
+// after each step: the running maximum of the step DRAC and the union of the
+// step's event bits; a done agent's episode goes into the counters (integer
+// atomics, block sums first, so the totals do not depend on the order), the
+// DRAC sum in fixed point of 1e-6 m/s^2.
+__global__ void __launch_bounds__(256) metrics_kernel(const uint32_t* __restrict__ events,
+                                                      const uint8_t* __restrict__ done,
+                                                      const float* __restrict__ drac, int A, float* __restrict__ epmax,
+                                                      uint32_t* __restrict__ epev, unsigned long long* __restrict__ cnt) {
+    __shared__ unsigned long long part[8][kMetricCount];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long v[kMetricCount];
+#pragma unroll
+    for (int i = 0; i < kMetricCount; ++i) v[i] = 0ull;
+    if (a < A) {
+        const float d = drac[a];
+        float m = epmax[a];
+        if (d > m) m = d;                               // NaN never raises the maximum
+        uint32_t e = epev[a] | events[a];
+        if (done[a]) {
+            v[kMetricEpisodes] = 1ull;
+            v[kMetricGoals] = (e & sfk::kEvGoal) ? 1ull : 0ull;
+            v[kMetricCollisions] = (e & sfk::kEvCollision) ? 1ull : 0ull;
+            v[kMetricCrashes] = (e & sfk::kEvCrash) ? 1ull : 0ull;
+            v[kMetricOffroad] = (e & sfk::kEvOffroad) ? 1ull : 0ull;
+            v[kMetricLaneForb] = (e & sfk::kEvLaneForb) ? 1ull : 0ull;
+            v[kMetricIdle] = (e & sfk::kEvIdle) ? 1ull : 0ull;
+            v[kMetricTimeouts] = (e & sfk::kEvTimeout) ? 1ull : 0ull;
+            v[kMetricNonfinite] = (e & sfk::kEvNonfinite) ? 1ull : 0ull;
+            v[kMetricDracOver] = m > 3.4f ? 1ull : 0ull;
+            v[kMetricDracMicro] = (unsigned long long)llrint((double)fminf(m, 1e6f) * 1e6);
+            m = 0.f;
+            e = 0u;
+        }
+        epmax[a] = m;
+        epev[a] = e;
+    }
+#pragma unroll
+    for (int i = 0; i < kMetricCount; ++i) {
+        unsigned long long x = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0) part[warp][i] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kMetricCount) {
+        unsigned long long x = 0ull;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += part[w][threadIdx.x];
+        if (x) atomicAdd(cnt + threadIdx.x, x);
+    }
+}
+
+// a masked reset starts new episodes: their running maxima and event bits are dropped
+__global__ void metrics_reset_kernel(const uint8_t* __restrict__ mask, int A, float* __restrict__ epmax,
+                                     uint32_t* __restrict__ epev) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < A && mask[a]) { epmax[a] = 0.f; epev[a] = 0u; }
+}
+
+// the metrics pass after a step (nothing without SF_FLAG_METRICS)
+cudaError_t launch_metrics(const sf_ctx* h) {
+    if (!h->m_cnt || h->A <= 0) return cudaSuccess;
+    metrics_kernel<<<(h->A + 255) / 256, 256, 0, h->stream>>>(h->out.events, h->out.done, h->out.drac, h->A,
+                                                             h->m_epmax, h->m_epev, h->m_cnt);
+    return cudaGetLastError();
 }
 
 WorldArgs make_args(sf_ctx* h) {
@@ -647,6 +732,11 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
             SF_ALLOC(ps.d, int4, pack_host.back().size());
             h->packsets.push_back(ps);
         }
+    if (h->cfg.flags & SF_FLAG_METRICS) {
+        SF_ALLOC(h->m_epmax, float, Aa);
+        SF_ALLOC(h->m_epev, uint32_t, Aa);
+        SF_ALLOC(h->m_cnt, unsigned long long, kMetricCount);
+    }
 #undef SF_ALLOC
 
     std::vector<uint32_t> meta_h(Aa);
@@ -682,6 +772,7 @@ sf_status sf_load_roads(sf_handle h, const sf_roads* r) {
     zero(sccount, 4);
     zero(obs, Aa * SF_OBS_DIM * 4); zero(reward, Aa * 4); zero(done, Aa); zero(events, Aa * 4);
     zero(drac, Aa * 4); zero(err_word, 4); zero(hint, Aa * 16);
+    if (h->m_cnt) { zero(h->m_epmax, Aa * 4); zero(h->m_epev, Aa * 4); zero(h->m_cnt, kMetricCount * 8); }
     if (e == cudaSuccess && Aa) e = cudaMemset(lane_seg, 0xFF, Aa * 4);
     if (e == cudaSuccess && Aa) e = cudaMemset(knn_pts, 0xFF, Aa * SF_L_POINTS * 4);
     if (e == cudaSuccess && Aa) e = cudaMemset(knn_agents, 0xFF, Aa * SF_K_AGENTS * 4);
@@ -712,6 +803,7 @@ sf_status sf_step(sf_handle h, const float* d_actions, float dt, int substeps) {
     a.h = dt / (float)substeps;
     a.substeps = substeps;
     cudaError_t e = launch_step(h, a);
+    if (e == cudaSuccess) e = launch_metrics(h);
     if (e != cudaSuccess) return cuda_fail(h, e, "sf_step launch");
     return SF_OK;
 }
@@ -749,6 +841,10 @@ void find_copy_nodes(sf_ctx* h) {
         cudaGraphNodeType t;
         if (cudaGraphNodeGetType(nd, &t) != cudaSuccess) continue;
         if (t == cudaGraphNodeTypeKernel) {
+            cudaKernelNodeParams mk{};
+            if (cudaGraphKernelNodeGetParams(nd, &mk) == cudaSuccess &&
+                mk.func == reinterpret_cast<void*>(metrics_kernel))
+                continue;   // the metrics pass reads only device outputs
             const int i = h->hs.n_steps++;   // more than kMaxStepNodes: not retargeted (re-captured)
             if (i < sf_ctx::HostStep::kMaxStepNodes) {
                 h->hs.n_step[i] = nd;
@@ -862,6 +958,7 @@ capture:
         c.wa.host_reward = dr;
         c.wa.host_done = dd;
         e = launch_step(h, c.wa);
+        if (e == cudaSuccess) e = launch_metrics(h);
         if (e != cudaSuccess) st = SF_ERR_CUDA;
     } else {
         e = cudaMemcpyAsync(c.d_act, h_actions, A * 12, cudaMemcpyHostToDevice, h->stream);
@@ -1014,7 +1111,46 @@ sf_status sf_reset(sf_handle h, const uint8_t* d_mask) {
     WorldArgs a = make_args(h);
     a.mask = d_mask;
     cudaError_t e = sf_launch_world(kModeReset, a, wpb_of(h), h->stream);
+    if (e == cudaSuccess && h->m_cnt && h->A > 0) {
+        metrics_reset_kernel<<<(h->A + 255) / 256, 256, 0, h->stream>>>(d_mask, h->A, h->m_epmax, h->m_epev);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "sf_reset launch");
+    return SF_OK;
+}
+
+sf_status sf_get_metrics(sf_handle h, sf_metrics* out) {
+    if (!h || !out) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_get_metrics: no roads loaded");
+    if (!h->m_cnt) return fail(h, SF_ERR_STATE, "sf_get_metrics: the handle was created without SF_FLAG_METRICS");
+    unsigned long long c[kMetricCount];
+    SF_CUDA(h, cudaMemcpyAsync(c, h->m_cnt, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    SF_CUDA(h, cudaStreamSynchronize(h->stream));
+    sf_metrics m{};
+    m.episodes = c[kMetricEpisodes];
+    m.goals = c[kMetricGoals];
+    m.collisions = c[kMetricCollisions];
+    m.crashes = c[kMetricCrashes];
+    m.offroad = c[kMetricOffroad];
+    m.lane_forbidden = c[kMetricLaneForb];
+    m.idle = c[kMetricIdle];
+    m.timeouts = c[kMetricTimeouts];
+    m.nonfinite = c[kMetricNonfinite];
+    m.drac_over = c[kMetricDracOver];
+    const double n = (double)m.episodes;
+    m.success_rate = n > 0 ? (double)m.goals / n : 0.0;
+    m.collision_rate = n > 0 ? (double)m.collisions / n : 0.0;
+    m.mean_episode_max_drac = n > 0 ? (double)c[kMetricDracMicro] * 1e-6 / n : 0.0;
+    m.drac_over_rate = n > 0 ? (double)m.drac_over / n : 0.0;
+    *out = m;
+    return SF_OK;
+}
+
+sf_status sf_reset_metrics(sf_handle h) {
+    if (!h) return SF_ERR_INVALID_ARG;
+    if (!h->loaded) return fail(h, SF_ERR_STATE, "sf_reset_metrics: no roads loaded");
+    if (!h->m_cnt) return fail(h, SF_ERR_STATE, "sf_reset_metrics: the handle was created without SF_FLAG_METRICS");
+    SF_CUDA(h, cudaMemsetAsync(h->m_cnt, 0, kMetricCount * sizeof(unsigned long long), h->stream));
     return SF_OK;
 }
 
@@ -1524,6 +1660,7 @@ sf_status sf_step_surrogate(sf_handle h, sf_surrogate_handle s, const float* d_a
     a.audit_err = b->words;
     a.surr_count = b->words + 1;
     e = launch_step(h, a);
+    if (e == cudaSuccess) e = launch_metrics(h);
     return e == cudaSuccess ? SF_OK : cuda_fail(h, e, "sf_step_surrogate");
 }
 

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "SF_OK", 1: "SF_ERR_INVALID_ARG", 2: "SF_ERR_CUDA", 3: "SF_ER
 NF, NI, OBS_DIM, K_AGENTS, L_POINTS = 25, 6, 320, 8, 32
 FULL_EGO, FULL_KR, FULL_PT, FULL_KV, FULL_NB = 11, 350, 5, 24, 7
 FULL_OBS_DIM = FULL_EGO + FULL_KR * FULL_PT + FULL_KV * FULL_NB   # 1929
-FLAG_INVINCIBLE, FLAG_AUTO_RESET, FLAG_RECORD_INDICES = 1, 2, 4
+FLAG_INVINCIBLE, FLAG_AUTO_RESET, FLAG_RECORD_INDICES, FLAG_METRICS = 1, 2, 4, 8
 DYN_VEHICLE, DYN_BICYCLE = 0, 1
 WEATHER_TABLE, WEATHER_ALL = 0, 1
 ACT_NONE, ACT_ELU, ACT_SILU, ACT_TANH = 0, 1, 2, 3
@@ -35,6 +35,12 @@ class SFError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
         self.status = status
+
+
+class sf_metrics(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("episodes", "goals", "collisions", "crashes", "offroad", "lane_forbidden",
+                                          "idle", "timeouts", "nonfinite", "drac_over")] + \
+               [(n, C.c_double) for n in ("success_rate", "collision_rate", "mean_episode_max_drac", "drac_over_rate")]
 
 
 class sf_config(C.Structure):
@@ -74,7 +80,8 @@ def lib():
             "sf_step_host": ([vp, vp, vp, vp, f32, C.c_int], i32),
             "sf_step_host_obs": ([vp, vp, vp, vp, vp, f32, C.c_int], i32),
             "sf_fp32_fma_peak": ([vp, C.c_int, C.POINTER(C.c_double)], i32),
-            "sf_output_ptrs": ([vp, vp], i32), "sf_observe_full": ([vp, vp, vp, vp, vp, vp], i32), "sf_get_indices": ([vp, vp, vp, vp, vp], i32), "sf_reset": ([vp, vp], i32), "sf_place_agents": ([vp, vp], i32),
+            "sf_output_ptrs": ([vp, vp], i32), "sf_observe_full": ([vp, vp, vp, vp, vp, vp], i32), "sf_get_indices": ([vp, vp, vp, vp, vp], i32),
+            "sf_get_metrics": ([vp, vp], i32), "sf_reset_metrics": ([vp], i32), "sf_reset": ([vp, vp], i32), "sf_place_agents": ([vp, vp], i32),
             "sf_get_state": ([vp, vp, vp], i32), "sf_set_state": ([vp, vp, vp], i32),
             "sf_save_state": ([vp, C.c_char_p], i32), "sf_load_state": ([vp, C.c_char_p], i32),
             "sf_sync": ([vp], i32), "sf_set_wait_limit": ([vp, C.c_ulonglong, C.c_int], i32),
@@ -201,6 +208,17 @@ def sf_fp32_fma_peak(stream=None, iters=20000):
 
 def sf_get_obs(h, d_obs=None, d_reward=None, d_done=None, d_events=None):
     _check(lib().sf_get_obs(h, _ptr(d_obs), _ptr(d_reward), _ptr(d_done), _ptr(d_events)), h)
+
+
+def sf_get_metrics(h):
+    """The episode metrics of a handle created with FLAG_METRICS, as a dict."""
+    m = sf_metrics()
+    _check(lib().sf_get_metrics(h, C.byref(m)), h)
+    return {n: getattr(m, n) for n, _ in sf_metrics._fields_}
+
+
+def sf_reset_metrics(h):
+    _check(lib().sf_reset_metrics(h), h)
 
 
 def sf_get_indices(h, d_lane_seg=None, d_knn_points=None, d_knn_agents=None, d_drac=None):
