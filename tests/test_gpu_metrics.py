@@ -67,10 +67,11 @@ def outputs(W, stream):
     return ev.cpu().numpy().view(np.uint32), dn.cpu().numpy(), dr.cpu().numpy()
 
 
-def test_metrics_match_host_counts():
+@pytest.mark.parametrize("split", [0, 1], ids=["fused", "split"])
+def test_metrics_match_host_counts(split):
     sc = synth.procedural_scene(8, 16, seed_base=940)
     stream = torch.cuda.Stream()
-    W = sf.World(sc, seed=3, flags=sf.FLAG_AUTO_RESET | sf.FLAG_METRICS, stream=stream)
+    W = sf.World(sc, seed=3, flags=sf.FLAG_AUTO_RESET | sf.FLAG_METRICS, stream=stream, split_step=split)
     A = W.A
     with torch.cuda.stream(stream):
         sf.sf_reset(W.h, torch.ones(A, dtype=torch.uint8, device="cuda"))
