@@ -84,28 +84,50 @@ __global__ void to_bf16_kernel(const float* __restrict__ x, int B, int n, int ld
         if (b < B && c < ld) yt[(size_t)c * B + b] = tile[tx][ty + 8 * j];
     }
 }
-// dZ = dA * act'(Z) as bf16 [B, ld] and its transpose [ld, B] (tiled like to_bf16_kernel)
+// dZ = dA * act'(Z) as bf16 [B, ld] and its transpose dZ^T [ld, B] (32 x 32 tiles
+// through shared memory), and the partial column sums of the bf16 dZ for the bias
+// gradient: block (x, s) covers columns [32 x, 32 x + 32) of rows [kBackRows s,
+// kBackRows (s + 1)); thread (ty, tx) adds its rows of column tx in order, then the
+// 8 row threads are added in order: part[s][c] (c < n)
+constexpr int kBackRows = 256;
 __global__ void act_back_kernel(const float* __restrict__ dA, const float* __restrict__ Z, int B, int n, int ld,
-                                int act, __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt) {
+                                int act, __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt,
+                                float* __restrict__ part) {
     __shared__ __nv_bfloat16 tile[32][34];
-    const int c0 = blockIdx.x * 32, b0 = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+    __shared__ float red[8][33];
+    const int c0 = blockIdx.x * 32, tx = threadIdx.x, ty = threadIdx.y;
+    const int rb = blockIdx.y * kBackRows;
+    float acc = 0.f;
+    for (int b0 = rb; b0 < rb + kBackRows && b0 < B; b0 += 32) {   // block-uniform
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int b = b0 + ty + 8 * j, c = c0 + tx;
-        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-        if (b < B && c < ld) {
-            float g = 0.f;
-            if (c < n) g = dA[(size_t)b * ld + c] * act_grad(Z[(size_t)b * ld + c], act);
-            v = __float2bfloat16_rn(g);
-            dz[(size_t)b * ld + c] = v;
+        for (int j = 0; j < 4; ++j) {
+            const int b = b0 + ty + 8 * j, c = c0 + tx;
+            __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+            if (b < B && c < ld) {
+                float g = 0.f;
+                if (c < n) g = dA[(size_t)b * ld + c] * act_grad(Z[(size_t)b * ld + c], act);
+                v = __float2bfloat16_rn(g);
+                dz[(size_t)b * ld + c] = v;
+            }
+            acc += __bfloat162float(v);
+            tile[ty + 8 * j][tx] = v;
         }
-        tile[ty + 8 * j][tx] = v;
-    }
-    __syncthreads();
+        __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int c = c0 + ty + 8 * j, b = b0 + tx;
-        if (b < B && c < ld) dzt[(size_t)c * B + b] = tile[tx][ty + 8 * j];
+        for (int j = 0; j < 4; ++j) {
+            const int c = c0 + ty + 8 * j, b = b0 + tx;
+            if (b < B && c < ld) dzt[(size_t)c * B + b] = tile[tx][ty + 8 * j];
+        }
+        __syncthreads();   // the tile is rewritten by the next 32 rows
+    }
+    red[ty][tx] = acc;
+    __syncthreads();
+    if (ty == 0) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += red[k][tx];
+        const int c = c0 + tx;
+        if (c < n) part[(size_t)blockIdx.y * n + c] = t;
     }
 }
 
@@ -141,48 +163,7 @@ __global__ void mse_loss_kernel(const float* __restrict__ y, const float* __rest
     if (threadIdx.x == 0) *loss = red[0] / ((float)B * (float)n);
 }
 
-// column sums of dZ [B, ld] (bf16, row-major): db[c] = sum_b dZ[b, c], in two
-// deterministic passes.  Pass 1: block (x, s) sums columns [64 x, 64 x + 64)
-// over rows split s (a lane holds a column pair, so a warp reads whole 128-byte
-// rows; warp w takes rows w, w + 8, ...; the 8 warps are added in order).
-// Pass 2: each column adds its S split sums in order.
-constexpr int kBiasSplitMax = 32;
-__global__ void bias_part_kernel(const __nv_bfloat16* __restrict__ dz, int B, int ld, int n, int S,
-                                 float* __restrict__ part) {
-    __shared__ float2 red[8][32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * 64 + 2 * lane, s = blockIdx.y;
-    const int R = (B + S - 1) / S, r0 = s * R, r1 = min(B, r0 + R);
-    float2 acc = make_float2(0.f, 0.f);
-    if (c < ld) {
-        const __nv_bfloat162* col = reinterpret_cast<const __nv_bfloat162*>(dz + c);
-        int b = r0 + warp;
-        for (; b + 24 < r1; b += 32) {     // four rows in flight
-            const float2 v0 = __bfloat1622float2(col[(size_t)b * (ld / 2)]);
-            const float2 v1 = __bfloat1622float2(col[(size_t)(b + 8) * (ld / 2)]);
-            const float2 v2 = __bfloat1622float2(col[(size_t)(b + 16) * (ld / 2)]);
-            const float2 v3 = __bfloat1622float2(col[(size_t)(b + 24) * (ld / 2)]);
-            acc.x += v0.x; acc.y += v0.y;
-            acc.x += v1.x; acc.y += v1.y;
-            acc.x += v2.x; acc.y += v2.y;
-            acc.x += v3.x; acc.y += v3.y;
-        }
-        for (; b < r1; b += 8) {
-            const float2 v = __bfloat1622float2(col[(size_t)b * (ld / 2)]);
-            acc.x += v.x; acc.y += v.y;
-        }
-    }
-    red[warp][lane] = acc;
-    __syncthreads();
-    if (threadIdx.x < 64) {
-        const int l = threadIdx.x >> 1, k = threadIdx.x & 1;
-        float t = 0.f;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) t += k ? red[w][l].y : red[w][l].x;
-        const int cc = blockIdx.x * 64 + threadIdx.x;
-        if (cc < n) part[(size_t)s * n + cc] = t;
-    }
-}
+// the bias gradient: db[c] = the S partial column sums of act_back_kernel added in order
 __global__ void bias_sum_kernel(const float* __restrict__ part, int n, int S, float* __restrict__ db) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
@@ -274,6 +255,7 @@ struct sf_mlp {
     __nv_bfloat16 *dz = nullptr, *dzt = nullptr;
     float* gwfull = nullptr;                 // [max out, max ld] f32 (padded gradient)
     float* ws = nullptr;                     // [kSplitMax][max out][max ld] f32 split-K partials of dW
+    float* bpart = nullptr;                  // [cap / kBackRows][max ld] f32 partial bias gradients
     float* loss = nullptr;
     float* red = nullptr;                    // [kSumsqBlocks] partial sums of the gradient norm
     const sf_mlp* share = nullptr;           // while set: layer 0 reads its bf16 input (and its transpose) from it
@@ -346,6 +328,7 @@ cudaError_t ensure_batch(sf_mlp* m, int B) {
     if (e == cudaSuccess) e = malloc_zero(m, &m->dA, (size_t)B * maxld);
     if (e == cudaSuccess) e = malloc_zero(m, &m->dz, (size_t)B * maxld);
     if (e == cudaSuccess) e = malloc_zero(m, &m->dzt, (size_t)B * maxld);
+    if (e == cudaSuccess) e = malloc_zero(m, &m->bpart, (size_t)((B + kBackRows - 1) / kBackRows) * maxld);
     if (e == cudaSuccess) m->cap = B;
     return e;
 }
@@ -410,16 +393,12 @@ cudaError_t backward_core(sf_mlp* m, int B, cudaStream_t st, float* dx0 = nullpt
     cudaError_t e = cudaSuccess;
     for (int l = m->L - 1; l >= 0 && e == cudaSuccess; --l) {
         const int o = m->dim[l + 1], lo = m->ld[l + 1], li = m->ld[l];
-        act_back_kernel<<<tgrid(B, lo), kTBlock, 0, st>>>(m->dA, m->z[l], B, o, lo, act_of(m, l), m->dz, m->dzt);
+        const int S = (B + kBackRows - 1) / kBackRows;   // partial bias sums, one per kBackRows rows
+        act_back_kernel<<<dim3((unsigned)((lo + 31) / 32), (unsigned)S), kTBlock, 0, st>>>(
+            m->dA, m->z[l], B, o, lo, act_of(m, l), m->dz, m->dzt, m->bpart);
+        bias_sum_kernel<<<(unsigned)((o + 255) / 256), 256, 0, st>>>(m->bpart, o, S, m->gb[l]);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = weight_grad(m, l, B, m->dzt, st);
-        if (e == cudaSuccess) {
-            // the split-K partials of dW are consumed: their workspace holds the bias partials
-            const int S = std::max(1, std::min(kBiasSplitMax, B / 256));
-            bias_part_kernel<<<dim3((unsigned)((o + 63) / 64), (unsigned)S), 256, 0, st>>>(m->dz, B, lo, o, S, m->ws);
-            bias_sum_kernel<<<(unsigned)((o + 255) / 256), 256, 0, st>>>(m->ws, o, S, m->gb[l]);
-            e = cudaGetLastError();
-        }
         if (e == cudaSuccess && l > 0)
             e = gemm(m, m->dz, m->wbt[l], nullptr, B, li, li, lo, SF_ACT_NONE, nullptr, m->dA, nullptr, nullptr, li,
                      0, st, true);
