@@ -89,7 +89,7 @@ __global__ void to_bf16_kernel(const float* __restrict__ x, int B, int n, int ld
 // gradient: block (x, s) covers columns [32 x, 32 x + 32) of rows [kBackRows s,
 // kBackRows (s + 1)); thread (ty, tx) adds its rows of column tx in order, then the
 // 8 row threads are added in order: part[s][c] (c < n)
-constexpr int kBackRows = 256;
+constexpr int kBackRows = 128;
 __global__ void act_back_kernel(const float* __restrict__ dA, const float* __restrict__ Z, int B, int n, int ld,
                                 int act, __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt,
                                 float* __restrict__ part) {
@@ -163,13 +163,17 @@ __global__ void mse_loss_kernel(const float* __restrict__ y, const float* __rest
     if (threadIdx.x == 0) *loss = red[0] / ((float)B * (float)n);
 }
 
-// the bias gradient: db[c] = the S partial column sums of act_back_kernel added in order
+// the bias gradient: db[c] = the S partial column sums of act_back_kernel, one warp per
+// column: lane l adds partials l, l + 32, ... in order, then the lanes meet in a fixed
+// butterfly, so the sum is the same on every run
 __global__ void bias_sum_kernel(const float* __restrict__ part, int n, int S, float* __restrict__ db) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (c >= n) return;   // warp-uniform
     float t = 0.f;
-    for (int s = 0; s < S; ++s) t += part[(size_t)s * n + c];
-    db[c] = t;
+    for (int s = lane; s < S; s += 32) t += part[(size_t)s * n + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+    if (lane == 0) db[c] = t;
 }
 
 // Adam (Kingma & Ba) on fp32 masters; refresh bf16 W [out, ldi] and W^T [ldi, ldo]
@@ -396,7 +400,7 @@ cudaError_t backward_core(sf_mlp* m, int B, cudaStream_t st, float* dx0 = nullpt
         const int S = (B + kBackRows - 1) / kBackRows;   // partial bias sums, one per kBackRows rows
         act_back_kernel<<<dim3((unsigned)((lo + 31) / 32), (unsigned)S), kTBlock, 0, st>>>(
             m->dA, m->z[l], B, o, lo, act_of(m, l), m->dz, m->dzt, m->bpart);
-        bias_sum_kernel<<<(unsigned)((o + 255) / 256), 256, 0, st>>>(m->bpart, o, S, m->gb[l]);
+        bias_sum_kernel<<<(unsigned)((o + 7) / 8), 256, 0, st>>>(m->bpart, o, S, m->gb[l]);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = weight_grad(m, l, B, m->dzt, st);
         if (e == cudaSuccess && l > 0)
