@@ -46,6 +46,15 @@ __device__ __forceinline__ float act_grad(float z, int act) {
         default: return 1.f;
     }
 }
+// the same from the layer's bf16 output h = act(z) where that determines it: ELU
+// (1 for h > 0, else h + 1 = exp(z)), tanh (1 - h^2), identity
+__device__ __forceinline__ float act_grad_out(float h, int act) {
+    switch (act) {
+        case SF_ACT_ELU: return h > 0.f ? 1.f : h + 1.f;
+        case SF_ACT_TANH: return 1.f - h * h;
+        default: return 1.f;
+    }
+}
 
 
 // x [B, n] f32 -> bf16 [B, ld] with n == ld, ld % 8 == 0 and 16-byte rows: 8 elements per thread
@@ -84,14 +93,15 @@ __global__ void to_bf16_kernel(const float* __restrict__ x, int B, int n, int ld
         if (b < B && c < ld) yt[(size_t)c * B + b] = tile[tx][ty + 8 * j];
     }
 }
-// dZ = dA * act'(Z) as bf16 [B, ld] and its transpose dZ^T [ld, B] (32 x 32 tiles
+// dZ = dA * act'(Z) (Z null: act' from the bf16 output H [B, ld]) as bf16 [B, ld] and its transpose dZ^T [ld, B] (32 x 32 tiles
 // through shared memory), and the partial column sums of the bf16 dZ for the bias
 // gradient: block (x, s) covers columns [32 x, 32 x + 32) of rows [kBackRows s,
 // kBackRows (s + 1)); thread (ty, tx) adds its rows of column tx in order, then the
 // 8 row threads are added in order: part[s][c] (c < n)
 constexpr int kBackRows = 128;
-__global__ void act_back_kernel(const float* __restrict__ dA, const float* __restrict__ Z, int B, int n, int ld,
-                                int act, __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt,
+__global__ void act_back_kernel(const float* __restrict__ dA, const float* __restrict__ Z,
+                                const __nv_bfloat16* __restrict__ H, int B, int n, int ld, int act,
+                                __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt,
                                 float* __restrict__ part) {
     __shared__ __nv_bfloat16 tile[32][34];
     __shared__ float red[8][33];
@@ -105,7 +115,10 @@ __global__ void act_back_kernel(const float* __restrict__ dA, const float* __res
             __nv_bfloat16 v = __float2bfloat16_rn(0.f);
             if (b < B && c < ld) {
                 float g = 0.f;
-                if (c < n) g = dA[(size_t)b * ld + c] * act_grad(Z[(size_t)b * ld + c], act);
+                if (c < n) {
+                    const size_t i = (size_t)b * ld + c;
+                    g = dA[i] * (Z ? act_grad(Z[i], act) : act_grad_out(__bfloat162float(H[i]), act));
+                }
                 v = __float2bfloat16_rn(g);
                 dz[(size_t)b * ld + c] = v;
             }
@@ -286,6 +299,10 @@ cudaError_t malloc_zero(sf_mlp* m, T** p, size_t count) {
 }
 
 int act_of(const sf_mlp* m, int l) { return l == m->L - 1 ? m->out_act : m->hidden_act; }
+// the training forward keeps layer l's fp32 pre-activation for the backward only where the
+// derivative needs it: the output layer and SiLU (ELU, tanh and the identity follow from the
+// bf16 output the next layer reads)
+bool keeps_pre(const sf_mlp* m, int l) { return l == m->L - 1 || act_of(m, l) == SF_ACT_SILU; }
 
 int tile_for(int n) { return n >= 256 ? 256 : (n > 64 ? 128 : 64); }
 
@@ -353,9 +370,10 @@ cudaError_t forward_core(sf_mlp* m, int B, bool train, float* y_out = nullptr, i
             e = gemm_head(m, x_in(m, l), B, y_out ? y_out : m->y, y_out ? ldy : m->ld[m->L], use_st ? st : m->stream);
             break;
         }
-        // the pre-activations keep the layer's own row stride whatever the output's (the backward reads them so)
+        // the pre-activations keep the layer's own row stride whatever the output's (the backward reads them
+        // so); a hidden layer whose activation's derivative follows from its bf16 output keeps none
         e = gemm(m, x_in(m, l), m->wb[l], m->b[l], B, m->dim[l + 1], m->dim[l + 1], m->ld[l], act_of(m, l),
-                 train ? m->z[l] : nullptr, last ? (y_out ? y_out : m->y) : nullptr, last ? nullptr : m->x[l + 1],
+                 train && keeps_pre(m, l) ? m->z[l] : nullptr, last ? (y_out ? y_out : m->y) : nullptr, last ? nullptr : m->x[l + 1],
                  (train && !last) ? m->xt[l + 1] : nullptr, (last && y_out) ? ldy : m->ld[l + 1], B, st, use_st,
                  m->ld[l + 1]);
     }
@@ -399,7 +417,7 @@ cudaError_t backward_core(sf_mlp* m, int B, cudaStream_t st, float* dx0 = nullpt
         const int o = m->dim[l + 1], lo = m->ld[l + 1], li = m->ld[l];
         const int S = (B + kBackRows - 1) / kBackRows;   // partial bias sums, one per kBackRows rows
         act_back_kernel<<<dim3((unsigned)((lo + 31) / 32), (unsigned)S), kTBlock, 0, st>>>(
-            m->dA, m->z[l], B, o, lo, act_of(m, l), m->dz, m->dzt, m->bpart);
+            m->dA, keeps_pre(m, l) ? m->z[l] : nullptr, m->x[l + 1], B, o, lo, act_of(m, l), m->dz, m->dzt, m->bpart);
         bias_sum_kernel<<<(unsigned)((o + 7) / 8), 256, 0, st>>>(m->bpart, o, S, m->gb[l]);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = weight_grad(m, l, B, m->dzt, st);
