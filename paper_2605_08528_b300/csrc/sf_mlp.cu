@@ -93,13 +93,15 @@ __global__ void to_bf16_kernel(const float* __restrict__ x, int B, int n, int ld
         if (b < B && c < ld) yt[(size_t)c * B + b] = tile[tx][ty + 8 * j];
     }
 }
-// dZ = dA * act'(Z) (Z null: act' from the bf16 output H [B, ld]) as bf16 [B, ld] and its transpose dZ^T [ld, B] (32 x 32 tiles
+// dZ = dA * act'(Z) (dA fp32, or bf16 dAb for a hidden layer; Z null: act' from the bf16
+// output H [B, ld]) as bf16 [B, ld] and its transpose dZ^T [ld, B] (32 x 32 tiles
 // through shared memory), and the partial column sums of the bf16 dZ for the bias
 // gradient: block (x, s) covers columns [32 x, 32 x + 32) of rows [kBackRows s,
 // kBackRows (s + 1)); thread (ty, tx) adds its rows of column tx in order, then the
 // 8 row threads are added in order: part[s][c] (c < n)
 constexpr int kBackRows = 128;
-__global__ void act_back_kernel(const float* __restrict__ dA, const float* __restrict__ Z,
+__global__ void act_back_kernel(const float* __restrict__ dA, const __nv_bfloat16* __restrict__ dAb,
+                                const float* __restrict__ Z,
                                 const __nv_bfloat16* __restrict__ H, int B, int n, int ld, int act,
                                 __nv_bfloat16* __restrict__ dz, __nv_bfloat16* __restrict__ dzt,
                                 float* __restrict__ part) {
@@ -117,7 +119,8 @@ __global__ void act_back_kernel(const float* __restrict__ dA, const float* __res
                 float g = 0.f;
                 if (c < n) {
                     const size_t i = (size_t)b * ld + c;
-                    g = dA[i] * (Z ? act_grad(Z[i], act) : act_grad_out(__bfloat162float(H[i]), act));
+                    const float up = dAb ? __bfloat162float(dAb[i]) : dA[i];
+                    g = up * (Z ? act_grad(Z[i], act) : act_grad_out(__bfloat162float(H[i]), act));
                 }
                 v = __float2bfloat16_rn(g);
                 dz[(size_t)b * ld + c] = v;
@@ -268,7 +271,8 @@ struct sf_mlp {
     __nv_bfloat16* xt[kMaxLayers + 1] = {};  // [ld_l, cap]
     float* z[kMaxLayers] = {};               // [cap, ld_{l+1}]
     float* y = nullptr;                      // [cap, ld_L] output f32
-    float* dA = nullptr;                     // [cap, max ld] f32
+    float* dA = nullptr;                     // [cap, max ld] f32: the output layer's upstream gradient
+    __nv_bfloat16* dAb = nullptr;            // [cap, max ld] bf16: a hidden layer's (the dX product of the layer above)
     __nv_bfloat16 *dz = nullptr, *dzt = nullptr;
     float* gwfull = nullptr;                 // [max out, max ld] f32 (padded gradient)
     float* ws = nullptr;                     // [kSplitMax][max out][max ld] f32 split-K partials of dW
@@ -347,6 +351,7 @@ cudaError_t ensure_batch(sf_mlp* m, int B) {
     for (int l = 0; l < m->L && e == cudaSuccess; ++l) e = malloc_zero(m, &m->z[l], (size_t)B * m->ld[l + 1]);
     if (e == cudaSuccess) e = malloc_zero(m, &m->y, (size_t)B * m->ld[m->L]);
     if (e == cudaSuccess) e = malloc_zero(m, &m->dA, (size_t)B * maxld);
+    if (e == cudaSuccess) e = malloc_zero(m, &m->dAb, (size_t)B * maxld);
     if (e == cudaSuccess) e = malloc_zero(m, &m->dz, (size_t)B * maxld);
     if (e == cudaSuccess) e = malloc_zero(m, &m->dzt, (size_t)B * maxld);
     if (e == cudaSuccess) e = malloc_zero(m, &m->bpart, (size_t)((B + kBackRows - 1) / kBackRows) * maxld);
@@ -417,12 +422,13 @@ cudaError_t backward_core(sf_mlp* m, int B, cudaStream_t st, float* dx0 = nullpt
         const int o = m->dim[l + 1], lo = m->ld[l + 1], li = m->ld[l];
         const int S = (B + kBackRows - 1) / kBackRows;   // partial bias sums, one per kBackRows rows
         act_back_kernel<<<dim3((unsigned)((lo + 31) / 32), (unsigned)S), kTBlock, 0, st>>>(
-            m->dA, keeps_pre(m, l) ? m->z[l] : nullptr, m->x[l + 1], B, o, lo, act_of(m, l), m->dz, m->dzt, m->bpart);
+            m->dA, l == m->L - 1 ? nullptr : m->dAb, keeps_pre(m, l) ? m->z[l] : nullptr, m->x[l + 1], B, o, lo,
+            act_of(m, l), m->dz, m->dzt, m->bpart);
         bias_sum_kernel<<<(unsigned)((o + 7) / 8), 256, 0, st>>>(m->bpart, o, S, m->gb[l]);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = weight_grad(m, l, B, m->dzt, st);
         if (e == cudaSuccess && l > 0)
-            e = gemm(m, m->dz, m->wbt[l], nullptr, B, li, li, lo, SF_ACT_NONE, nullptr, m->dA, nullptr, nullptr, li,
+            e = gemm(m, m->dz, m->wbt[l], nullptr, B, li, li, lo, SF_ACT_NONE, nullptr, nullptr, m->dAb, nullptr, li,
                      0, st, true);
         else if (e == cudaSuccess && dx0)
             e = gemm(m, m->dz, m->wbt[0], nullptr, B, li, li, lo, SF_ACT_NONE, nullptr, dx0, nullptr, nullptr, lddx,
