@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const bool vf = args.ldc % 4 == 0 && (reinterpret_cast<uintptr_t>(out_f32) & 15) == 0;
                 const bool vp = ldp % 4 == 0 && (reinterpret_cast<uintptr_t>(args.pre) & 15) == 0;
                 const bool vb = args.ldc % 8 == 0 && (reinterpret_cast<uintptr_t>(args.out_bf16) & 15) == 0;
+                const bool vt = args.ldt % 8 == 0 && (reinterpret_cast<uintptr_t>(args.out_bf16_t) & 15) == 0;
                 // the layer's ELU values leave it only as bf16 (inference hidden layers, a head's input)
                 const bool packed_elu = args.act == SF_ACT_ELU && !args.pre && !out_f32 && !args.out_bf16_t &&
                                         (args.out_bf16 || headed);
@@ -410,7 +411,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 if (nb + k < args.N) args.out_bf16[row + k] = __float2bfloat16_rn(v[k]);
                         }
                     }
-                    if (args.out_bf16_t && live) {   // lanes hold consecutive rows: each column store is contiguous across the warp
+                    if (args.out_bf16_t && full && rows_valid == 32 && vt) {
+                        // staged: 16 columns at a time through the warp's buffer (column k's 32 rows are
+                        // 64 contiguous bytes of the transpose), then 16-byte stores
+                        __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(stg);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                            for (int kk = 0; kk < 16; ++kk) sb[kk * 32 + lane] = __float2bfloat16_rn(v[16 * h + kk]);
+                            __syncwarp();
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) {
+                                const int kk = (lane >> 2) + 8 * i, piece = lane & 3;
+                                const uint4 x = *reinterpret_cast<const uint4*>(stg + kk * 64 + piece * 16);
+                                *reinterpret_cast<uint4*>(args.out_bf16_t + (size_t)(nb + 16 * h + kk) * args.ldt + r0 +
+                                                          piece * 8) = x;
+                            }
+                            __syncwarp();
+                        }
+                    } else if (args.out_bf16_t && live) {   // lanes hold consecutive rows: each column store is contiguous
 #pragma unroll
                         for (int k = 0; k < 32; ++k)
                             if (nb + k < args.N) args.out_bf16_t[(size_t)(nb + k) * args.ldt + r] = __float2bfloat16_rn(v[k]);
