@@ -317,8 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const bool vb = args.ldc % 8 == 0 && (reinterpret_cast<uintptr_t>(args.out_bf16) & 15) == 0;
                 const bool vt = args.ldt % 8 == 0 && (reinterpret_cast<uintptr_t>(args.out_bf16_t) & 15) == 0;
                 // the layer's ELU values leave it only as bf16 (inference hidden layers, a head's input)
-                const bool packed_elu = args.act == SF_ACT_ELU && !args.pre && !out_f32 && !args.out_bf16_t &&
-                                        (args.out_bf16 || headed);
+                const bool packed_elu = args.act == SF_ACT_ELU && !args.pre && !out_f32 && (args.out_bf16 || headed);
 #pragma unroll 1
                 for (int c = part; c < BN / 32; c += kParts) {
                     float v[32];
@@ -364,6 +363,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 for (int k = 0; k < 32; ++k)
                                     if (nb + k < args.N)
                                         args.out_bf16[row + k] = __ushort_as_bfloat16((unsigned short)(pk[k >> 1] >> (16 * (k & 1))));
+                            }
+                        }
+                        if (args.out_bf16_t) {   // the same bf16 values transposed (a training forward)
+                            if (full && rows_valid == 32 && vt) {
+                                __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(stg);
+#pragma unroll
+                                for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                                    for (int kk = 0; kk < 16; ++kk) {
+                                        const int k = 16 * h + kk;
+                                        sb[kk * 32 + lane] = __ushort_as_bfloat16((unsigned short)(pk[k >> 1] >> (16 * (k & 1))));
+                                    }
+                                    __syncwarp();
+#pragma unroll
+                                    for (int i = 0; i < 2; ++i) {
+                                        const int kk = (lane >> 2) + 8 * i, piece = lane & 3;
+                                        const uint4 x = *reinterpret_cast<const uint4*>(stg + kk * 64 + piece * 16);
+                                        *reinterpret_cast<uint4*>(args.out_bf16_t + (size_t)(nb + 16 * h + kk) * args.ldt +
+                                                                  r0 + piece * 8) = x;
+                                    }
+                                    __syncwarp();
+                                }
+                            } else if (live) {
+#pragma unroll
+                                for (int k = 0; k < 32; ++k)
+                                    if (nb + k < args.N)
+                                        args.out_bf16_t[(size_t)(nb + k) * args.ldt + r] =
+                                            __ushort_as_bfloat16((unsigned short)(pk[k >> 1] >> (16 * (k & 1))));
                             }
                         }
                         if (headed) {   // the same bf16 activations times the head weights, columns in order
