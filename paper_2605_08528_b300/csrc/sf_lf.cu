@@ -831,8 +831,13 @@ struct sf_lf {
     // activations (grown on demand)
     int cap = 0;
     __nv_bfloat16 *xego = nullptr, *he1[2] = {nullptr, nullptr}, *x[2] = {nullptr, nullptr};
-    __nv_bfloat16 *t1 = nullptr, *t2 = nullptr;
+    __nv_bfloat16 *t1 = nullptr, *t2 = nullptr, *t1c = nullptr;   // trunk layer 1 outputs (actor, critic)
     unsigned* d_err = nullptr;
+    // the critic's ego and trunk GEMM chains run beside the actor's on a second stream
+    // (forked from and joined back to the caller's stream by events; parallel branches
+    // when captured into a graph)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -914,7 +919,7 @@ sf_status ensure(sf_lf* m, int A) {
     bool okk = lalloc(m, &m->xego, Aa * 16, true) && lalloc(m, &m->he1[0], Aa * 64, true) &&
                lalloc(m, &m->he1[1], Aa * 64, true) && lalloc(m, &m->x[0], Aa * 256, true) &&
                lalloc(m, &m->x[1], Aa * 256, true) && lalloc(m, &m->t1, Aa * 128, true) &&
-               lalloc(m, &m->t2, Aa * 64, true);
+               lalloc(m, &m->t2, Aa * 64, true) && lalloc(m, &m->t1c, Aa * 128, true);
     if (!okk) return lfail(m, SF_ERR_OOM, "sf_lf_forward: cudaMalloc of the activations failed");
     m->cap = A;
     return SF_OK;
@@ -972,6 +977,8 @@ sf_status sf_lf_create(void* cuda_stream, sf_lf_handle* out) {
             okk = okk && lalloc(m, &m->w[n][t], (size_t)o * ip) && lalloc(m, &m->b[n][t], (size_t)o);
         }
     okk = okk && lalloc(m, &m->d_err, 1);
+    okk = okk && cudaStreamCreateWithFlags(&m->aux, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < 4 && okk; ++i) okk = cudaEventCreateWithFlags(&m->ev[i], cudaEventDisableTiming) == cudaSuccess;
     static bool attr = false;
     if (okk && !attr) {
         okk = cudaFuncSetAttribute(lf_set_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) ==
@@ -982,6 +989,9 @@ sf_status sf_lf_create(void* cuda_stream, sf_lf_handle* out) {
     }
     if (!okk || cudaMemset(m->d_err, 0, 4) != cudaSuccess || upload(m) != SF_OK) {
         for (void* p : m->allocs) cudaFree(p);
+        for (cudaEvent_t ev : m->ev)
+            if (ev) cudaEventDestroy(ev);
+        if (m->aux) cudaStreamDestroy(m->aux);
         delete m;
         return SF_ERR_CUDA;
     }
@@ -992,6 +1002,10 @@ sf_status sf_lf_create(void* cuda_stream, sf_lf_handle* out) {
 sf_status sf_lf_destroy(sf_lf_handle m) {
     if (!m) return SF_OK;
     cudaStreamSynchronize(m->stream);
+    if (m->aux) cudaStreamSynchronize(m->aux);
+    for (cudaEvent_t ev : m->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (m->aux) cudaStreamDestroy(m->aux);
     for (void* p : m->allocs) cudaFree(p);
     for (void* p : m->acts) cudaFree(p);
     delete m;
@@ -1039,10 +1053,16 @@ sf_status sf_lf_forward_on(sf_lf_handle m, cudaStream_t st, const float* d_obs, 
     cudaError_t e = cudaSuccess;
     lf_ego_kernel<<<(A * 16 + 255) / 256, 256, 0, st>>>(d_obs, kObs, A, m->xego);
     e = cudaGetLastError();
+    // ego encoders: the actor's on st, the critic's beside it on aux
+    if (e == cudaSuccess) e = cudaEventRecord(m->ev[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(m->aux, m->ev[0], 0);
     for (int n = 0; n < 2 && e == cudaSuccess; ++n) {
-        e = gemm(m, st, m->xego, m->w[n][0], m->b[n][0], A, 64, 16, SF_ACT_ELU, nullptr, m->he1[n], 64);
-        if (e == cudaSuccess) e = gemm(m, st, m->he1[n], m->w[n][1], m->b[n][1], A, 64, 64, SF_ACT_ELU, nullptr, m->x[n], 256);
+        cudaStream_t sn = n == 0 ? st : m->aux;
+        e = gemm(m, sn, m->xego, m->w[n][0], m->b[n][0], A, 64, 16, SF_ACT_ELU, nullptr, m->he1[n], 64);
+        if (e == cudaSuccess) e = gemm(m, sn, m->he1[n], m->w[n][1], m->b[n][1], A, 64, 64, SF_ACT_ELU, nullptr, m->x[n], 256);
     }
+    if (e == cudaSuccess) e = cudaEventRecord(m->ev[1], m->aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, m->ev[1], 0);
     int sms = 148, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (int g = 0; g < 2 && e == cudaSuccess; ++g) {
@@ -1063,13 +1083,24 @@ sf_status sf_lf_forward_on(sf_lf_handle m, cudaStream_t st, const float* d_obs, 
         lf_set_kernel<false><<<2 * (items < sms ? items : sms), kThreads, kSmemBytes, st>>>(sa);
         e = cudaGetLastError();
     }
+    // trunks: the actor's on st, the critic's (when the value is wanted) beside it on aux
+    if (e == cudaSuccess && d_value) {
+        e = cudaEventRecord(m->ev[2], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(m->aux, m->ev[2], 0);
+    }
     for (int n = 0; n < 2 && e == cudaSuccess; ++n) {
         if (n == 1 && !d_value) break;   // no value wanted: the critic's trunk is not run
-        e = gemm(m, st, m->x[n], m->w[n][2], m->b[n][2], A, 128, 256, SF_ACT_ELU, nullptr, m->t1, 128);
+        cudaStream_t sn = n == 0 ? st : m->aux;
+        __nv_bfloat16* t1 = n == 0 ? m->t1 : m->t1c;
+        e = gemm(m, sn, m->x[n], m->w[n][2], m->b[n][2], A, 128, 256, SF_ACT_ELU, nullptr, t1, 128);
         // trunk layer 2 with the linear head (3 action means, or the value) in its epilogue
         if (e == cudaSuccess)
-            e = gemm_head(m, st, m->t1, m->w[n][3], m->b[n][3], A, 64, 128, m->w[n][4], m->b[n][4], n == 0 ? 3 : 1,
+            e = gemm_head(m, sn, t1, m->w[n][3], m->b[n][3], A, 64, 128, m->w[n][4], m->b[n][4], n == 0 ? 3 : 1,
                           n == 0 ? d_mean : d_value);
+    }
+    if (e == cudaSuccess && d_value) {
+        e = cudaEventRecord(m->ev[3], m->aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, m->ev[3], 0);
     }
     if (e == cudaSuccess && d_embed) {
         lf_embed_kernel<<<(A * 512 + 255) / 256, 256, 0, st>>>(m->x[0], m->x[1], A, d_embed);
