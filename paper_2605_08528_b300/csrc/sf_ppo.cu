@@ -320,6 +320,10 @@ struct sf_ppo {
     int32_t *nr_boot = nullptr, *nv_boot = nullptr;
     sf_ppo_config cfg{};
     cudaStream_t st = nullptr;
+    // MLP mode: the critic's rollout forward runs beside the actor's on a second stream
+    // (forked from and joined back to st by events)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     std::string err;
     int A = 0, T = 0, B = 0;               // agents, horizon, minibatch rows
     unsigned long long steps = 0;          // control steps sampled so far (the sampling counter)
@@ -354,8 +358,13 @@ sf_status pfail(sf_ppo* p, sf_status s, const std::string& e) {
 // and Adam of the minibatch
 sf_status nets_infer(sf_ppo* p, const float* obs, const int32_t* nr, const int32_t* nv, float* mu, float* val) {
     if (p->lft) return sf_lf_forward_on(p->lf, p->st, obs, nr, nv, p->A, mu, val, nullptr);
+    const bool both = mu && val && p->aux;
+    if (both && (cudaEventRecord(p->ev[0], p->st) != cudaSuccess || cudaStreamWaitEvent(p->aux, p->ev[0], 0) != cudaSuccess))
+        return SF_ERR_CUDA;
     sf_status s = mu ? sf_mlp_forward_on(p->actor, p->st, obs, kObsW, p->A, mu, 3) : SF_OK;
-    if (s == SF_OK && val) s = sf_mlp_forward_on(p->critic, p->st, obs, kObsW, p->A, val, 1);
+    if (s == SF_OK && val) s = sf_mlp_forward_on(p->critic, both ? p->aux : p->st, obs, kObsW, p->A, val, 1);
+    if (both && (cudaEventRecord(p->ev[1], p->aux) != cudaSuccess || cudaStreamWaitEvent(p->st, p->ev[1], 0) != cudaSuccess))
+        return SF_ERR_CUDA;
     return s;
 }
 sf_status nets_train_forward(sf_ppo* p, int B) {
@@ -458,8 +467,13 @@ sf_status sf_ppo_create(sf_handle h, sf_mlp_handle actor, sf_mlp_handle critic, 
               palloc(p, &p->g_small, (size_t)B * 12) && palloc(p, &p->mu_new, (size_t)B * 3) &&
               palloc(p, &p->v_new, (size_t)B) && palloc(p, &p->d_mu, (size_t)B * 3) && palloc(p, &p->d_v, (size_t)B);
     if (ok) ok = sf_mlp_reserve(actor, std::max(A, B)) == SF_OK && sf_mlp_reserve(critic, std::max(A, B)) == SF_OK;
+    if (ok) ok = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < 2 && ok; ++i) ok = cudaEventCreateWithFlags(&p->ev[i], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         for (void* q : p->allocs) cudaFree(q);
+        for (cudaEvent_t ev : p->ev)
+            if (ev) cudaEventDestroy(ev);
+        if (p->aux) cudaStreamDestroy(p->aux);
         delete p;
         return SF_ERR_OOM;
     }
@@ -557,6 +571,10 @@ sf_status sf_ppo_lf_params(sf_ppo_handle p, float* h_params, size_t n) {
 sf_status sf_ppo_destroy(sf_ppo_handle p) {
     if (!p) return SF_OK;
     cudaStreamSynchronize(p->st);
+    if (p->aux) cudaStreamSynchronize(p->aux);
+    for (cudaEvent_t ev : p->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (p->aux) cudaStreamDestroy(p->aux);
     lft_destroy(p->lft);
     for (void* q : p->allocs) cudaFree(q);
     delete p;
