@@ -381,8 +381,15 @@ sf_status nets_backward(sf_ppo* p, int B) {
         if (s == SF_OK) s = lft_grad_sumsq(p->lft, p->scal + S_SUMSQ);
         return s;
     }
+    // the two backward passes are independent: the critic's runs beside the actor's on aux;
+    // the gradient norm (one accumulator) follows the join
+    const bool fork = p->aux != nullptr;
+    if (fork && (cudaEventRecord(p->ev[0], p->st) != cudaSuccess || cudaStreamWaitEvent(p->aux, p->ev[0], 0) != cudaSuccess))
+        return SF_ERR_CUDA;
     s = sf_mlp_backward_on(p->actor, p->st, p->d_mu, 3, B);
-    if (s == SF_OK) s = sf_mlp_backward_on(p->critic, p->st, p->d_v, 1, B);
+    if (s == SF_OK) s = sf_mlp_backward_on(p->critic, fork ? p->aux : p->st, p->d_v, 1, B);
+    if (fork && (cudaEventRecord(p->ev[1], p->aux) != cudaSuccess || cudaStreamWaitEvent(p->st, p->ev[1], 0) != cudaSuccess))
+        return SF_ERR_CUDA;
     if (s == SF_OK) s = sf_mlp_grad_sumsq_on(p->actor, p->st, p->scal + S_SUMSQ);
     if (s == SF_OK) s = sf_mlp_grad_sumsq_on(p->critic, p->st, p->scal + S_SUMSQ);
     return s;
