@@ -1145,6 +1145,9 @@ sf_status sf_lf_sync(sf_lf_handle m) {
 struct LfTrainer {
     sf_lf* lf = nullptr;
     cudaStream_t st = nullptr;
+    // the critic's dense MLPs (ego encoder, trunk) run beside the actor's on a second stream
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     std::string err;
     std::vector<void*> allocs;
     sf_mlp_handle ego[2] = {nullptr, nullptr}, trunk[2] = {nullptr, nullptr};
@@ -1218,6 +1221,13 @@ sf_status lft_create(sf_lf_handle lf, cudaStream_t st, LfTrainer** out) {
     LfTrainer* t = new LfTrainer();
     t->lf = lf;
     t->st = st;
+    bool streams_ok = cudaStreamCreateWithFlags(&t->aux, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < 2 && streams_ok; ++i)
+        streams_ok = cudaEventCreateWithFlags(&t->ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!streams_ok) {
+        lft_destroy(t);
+        return SF_ERR_CUDA;
+    }
     const FlatLayout FL = flat_layout();
     const float* P = lf->params.data();
     bool ok = true;
@@ -1264,6 +1274,10 @@ sf_status lft_create(sf_lf_handle lf, cudaStream_t st, LfTrainer** out) {
 void lft_destroy(LfTrainer* t) {
     if (!t) return;
     cudaStreamSynchronize(t->st);
+    if (t->aux) cudaStreamSynchronize(t->aux);
+    for (cudaEvent_t ev : t->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (t->aux) cudaStreamDestroy(t->aux);
     for (int n = 0; n < 2; ++n) {
         sf_mlp_destroy(t->ego[n]);
         sf_mlp_destroy(t->trunk[n]);
@@ -1275,6 +1289,13 @@ void lft_destroy(LfTrainer* t) {
 const char* lft_error(LfTrainer* t) { return t ? t->err.c_str() : "NULL trainer"; }
 
 namespace {
+// fork the second stream from st (false: a CUDA error)
+bool lft_fork(LfTrainer* t) {
+    return cudaEventRecord(t->ev[0], t->st) == cudaSuccess && cudaStreamWaitEvent(t->aux, t->ev[0], 0) == cudaSuccess;
+}
+bool lft_join(LfTrainer* t) {
+    return cudaEventRecord(t->ev[1], t->aux) == cudaSuccess && cudaStreamWaitEvent(t->st, t->ev[1], 0) == cudaSuccess;
+}
 sf_status lft_reserve(LfTrainer* t, int rows) {
     if (rows <= t->cap) return SF_OK;
     cudaStreamSynchronize(t->st);
@@ -1307,8 +1328,10 @@ sf_status lft_forward(LfTrainer* t, const float* d_obs, const int32_t* d_n_road,
     t->obs = d_obs;
     t->cnt[0] = d_n_road;
     t->cnt[1] = d_n_veh;
-    for (int n = 0; n < 2 && s == SF_OK; ++n)   // ego encoders into trunk-input columns 0..63
-        s = sf_mlp_forward_train_on(t->ego[n], t->st, d_obs, kObs, rows, t->xf + n * xnet, 256);
+    if (!lft_fork(t)) return tfail(t, SF_ERR_CUDA, "late-fusion training forward: stream fork");
+    for (int n = 0; n < 2 && s == SF_OK; ++n)   // ego encoders into trunk-input columns 0..63 (the critic's on aux)
+        s = sf_mlp_forward_train_on(t->ego[n], n == 0 ? t->st : t->aux, d_obs, kObs, rows, t->xf + n * xnet, 256);
+    if (!lft_join(t) && s == SF_OK) s = SF_ERR_CUDA;
     if (s != SF_OK) return tfail(t, s, "late-fusion training forward: ego encoder");
     int sms = 148, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1333,8 +1356,10 @@ sf_status lft_forward(LfTrainer* t, const float* d_obs, const int32_t* d_n_road,
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return tfail(t, SF_ERR_CUDA, std::string("late-fusion training forward: ") + cudaGetErrorString(e));
+    if (!lft_fork(t)) return tfail(t, SF_ERR_CUDA, "late-fusion training forward: stream fork");
     s = sf_mlp_forward_train_on(t->trunk[0], t->st, t->xf, 256, rows, d_mean, 3);
-    if (s == SF_OK) s = sf_mlp_forward_train_on(t->trunk[1], t->st, t->xf + xnet, 256, rows, d_value, 1);
+    if (s == SF_OK) s = sf_mlp_forward_train_on(t->trunk[1], t->aux, t->xf + xnet, 256, rows, d_value, 1);
+    if (!lft_join(t) && s == SF_OK) s = SF_ERR_CUDA;
     return s == SF_OK ? SF_OK : tfail(t, s, "late-fusion training forward: trunk");
 }
 
@@ -1356,9 +1381,13 @@ cudaError_t back_gemm(LfTrainer* t, const __nv_bfloat16* A, const __nv_bfloat16*
 sf_status lft_backward(LfTrainer* t, const float* d_dmean, const float* d_dvalue, int rows) {
     if (!t || !d_dmean || !d_dvalue || rows != t->rows) return SF_ERR_INVALID_ARG;
     const size_t xnet = (size_t)rows * 256;
+    // each network's trunk then ego encoder, the critic's on aux
+    if (!lft_fork(t)) return tfail(t, SF_ERR_CUDA, "late-fusion backward: stream fork");
     sf_status s = sf_mlp_backward_dx_on(t->trunk[0], t->st, d_dmean, 3, rows, t->dx, 256);
-    if (s == SF_OK) s = sf_mlp_backward_dx_on(t->trunk[1], t->st, d_dvalue, 1, rows, t->dx + xnet, 256);
-    for (int n = 0; n < 2 && s == SF_OK; ++n) s = sf_mlp_backward_on(t->ego[n], t->st, t->dx + n * xnet, 256, rows);
+    if (s == SF_OK) s = sf_mlp_backward_on(t->ego[0], t->st, t->dx, 256, rows);
+    if (s == SF_OK) s = sf_mlp_backward_dx_on(t->trunk[1], t->aux, d_dvalue, 1, rows, t->dx + xnet, 256);
+    if (s == SF_OK) s = sf_mlp_backward_on(t->ego[1], t->aux, t->dx + xnet, 256, rows);
+    if (!lft_join(t) && s == SF_OK) s = SF_ERR_CUDA;
     if (s != SF_OK) return tfail(t, s, "late-fusion backward: dense layers");
     // set encoders: the rows of every (group, network) pass, counted first (one wait for
     // the four row totals, which size the products), then the products pass by pass
