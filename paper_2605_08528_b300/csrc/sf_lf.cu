@@ -1160,8 +1160,8 @@ struct LfTrainer {
     // a sample, the most a sample can have) and the split-K partials
     int* nd[2] = {nullptr, nullptr};      // per group [2][cap]
     int* offs[2] = {nullptr, nullptr};    // per group [2][cap + 1]
-    BackBufs bb{};
-    float *ws1 = nullptr, *ws2 = nullptr;
+    BackBufs bb{}, bbv{};                  // road passes (st), vehicle passes (aux; at most 24 rows a sample)
+    float *ws1 = nullptr, *ws2 = nullptr, *ws1v = nullptr, *ws2v = nullptr;
     float* sq = nullptr;      // [kSqBlocks]
     int adam_t = 0;
     // batch buffers of the last forward
@@ -1253,7 +1253,9 @@ sf_status lft_create(sf_lf_handle lf, cudaStream_t st, LfTrainer** out) {
     ok = ok && talloc(t, &t->theta, t->n_set) && talloc(t, &t->grad, t->n_set) && talloc(t, &t->mom, t->n_set) &&
          talloc(t, &t->var, t->n_set) && talloc(t, &t->sq, kSqBlocks) &&
          talloc(t, &t->ws1, (size_t)kBackSplit * kHid * 16) && talloc(t, &t->ws2, (size_t)kBackSplit * kHid * kLdW2) &&
-         talloc(t, &t->bb.w1b, (size_t)kHid * 16) && talloc(t, &t->bb.w2t, (size_t)kHid * kHid);
+         talloc(t, &t->ws1v, (size_t)kBackSplit * kHid * 16) && talloc(t, &t->ws2v, (size_t)kBackSplit * kHid * kLdW2) &&
+         talloc(t, &t->bb.w1b, (size_t)kHid * 16) && talloc(t, &t->bb.w2t, (size_t)kHid * kHid) &&
+         talloc(t, &t->bbv.w1b, (size_t)kHid * 16) && talloc(t, &t->bbv.w2t, (size_t)kHid * kHid);
     if (ok) {   // the masters from the network's parameters: group blocks are contiguous in the flat layout
         std::vector<float> h(t->n_set);
         for (int g = 0; g < 2; ++g)
@@ -1303,12 +1305,16 @@ sf_status lft_reserve(LfTrainer* t, int rows) {
     for (int g = 0; g < 2 && ok; ++g)
         ok = talloc(t, &t->pmax[g], (size_t)2 * rows * kHid) && talloc(t, &t->amax[g], (size_t)2 * rows * kHid) &&
              talloc(t, &t->nd[g], (size_t)2 * rows) && talloc(t, &t->offs[g], (size_t)2 * (rows + 1));
-    // the backward's rows: at most 96 a sample (one per pooled feature)
-    const size_t ldcap = std::max<size_t>(128, ((size_t)kHid * rows + 63) / 64 * 64);
-    BackBufs& o = t->bb;
-    ok = ok && talloc(t, &o.x, ldcap * 16) && talloc(t, &o.xt, 16 * ldcap) && talloc(t, &o.dz2, ldcap * kHid) &&
-         talloc(t, &o.dz2t, kHid * ldcap) && talloc(t, &o.h1t, (kHid + 1) * ldcap) && talloc(t, &o.dh1t, kHid * ldcap) &&
-         talloc(t, &o.dz1t, kHid * ldcap);
+    // the backward's rows: at most 96 a sample (one per pooled feature) on the road group, 24 (its
+    // slots) on the vehicle group
+    for (int g = 0; g < 2 && ok; ++g) {
+        const size_t per = g == 0 ? kHid : kKV;
+        const size_t ldcap = std::max<size_t>(128, (per * rows + 63) / 64 * 64);
+        BackBufs& o = g == 0 ? t->bb : t->bbv;
+        ok = talloc(t, &o.x, ldcap * 16) && talloc(t, &o.xt, 16 * ldcap) && talloc(t, &o.dz2, ldcap * kHid) &&
+             talloc(t, &o.dz2t, kHid * ldcap) && talloc(t, &o.h1t, (kHid + 1) * ldcap) &&
+             talloc(t, &o.dh1t, kHid * ldcap) && talloc(t, &o.dz1t, kHid * ldcap);
+    }
     for (int n = 0; n < 2 && ok; ++n)
         ok = sf_mlp_reserve(t->ego[n], rows) == SF_OK && sf_mlp_reserve(t->trunk[n], rows) == SF_OK;
     if (!ok) return tfail(t, SF_ERR_OOM, "late-fusion training buffers");
@@ -1366,15 +1372,15 @@ sf_status lft_forward(LfTrainer* t, const float* d_obs, const int32_t* d_n_road,
 namespace {
 // one product of the set-encoder backward on the tensor cores: C = A B^T (A [M][K], B [N][K]
 // bf16), written transposed (out_t [N][ldt]) or as split-K partials (ws [splits][M][ldc])
-cudaError_t back_gemm(LfTrainer* t, const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K, int act,
-                      __nv_bfloat16* out_t, int ldt, float* ws, int splits, int ldc, int bn) {
+cudaError_t back_gemm(LfTrainer* t, cudaStream_t st, const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N,
+                      int K, int act, __nv_bfloat16* out_t, int ldt, float* ws, int splits, int ldc, int bn) {
     GemmArgs g{};
     g.A = A; g.B = B; g.M = M; g.N = N; g.Nb = N; g.K = K; g.act = act;
     g.out_bf16_t = out_t; g.ldt = ldt;
     g.ws = ws; g.splits = splits; g.ldc = ldc;
     g.bn = bn;
     g.err = t->lf->d_err;
-    return sf_gemm_launch(g, t->st);
+    return sf_gemm_launch(g, st);
 }
 }  // namespace
 
@@ -1419,39 +1425,45 @@ sf_status lft_backward(LfTrainer* t, const float* d_dmean, const float* d_dvalue
                                 t->st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(t->st);
+    // the road passes on st, the vehicle passes beside them on aux (buffers of their own)
+    if (e == cudaSuccess && !lft_fork(t)) e = cudaErrorUnknown;
     for (int g = 0; g < 2 && e == cudaSuccess; ++g)
         for (int n = 0; n < 2 && e == cudaSuccess; ++n) {
             const int R = tot[g][n], F = br[g].F, P = t->P[g];
+            cudaStream_t sg = g == 0 ? t->st : t->aux;
+            float* ws1 = g == 0 ? t->ws1 : t->ws1v;
+            float* ws2 = g == 0 ? t->ws2 : t->ws2v;
             float* gout = t->grad + t->goff[g] + (size_t)n * P;
             if (R <= 0) {   // no sample of this group has a filled slot: no gradient
-                e = cudaMemsetAsync(gout, 0, (size_t)P * 4, t->st);
+                e = cudaMemsetAsync(gout, 0, (size_t)P * 4, sg);
                 continue;
             }
-            BackBufs o = t->bb;
+            BackBufs o = g == 0 ? t->bb : t->bbv;
             o.ldR = std::max(128, (R + 63) / 64 * 64);
             const int S = std::min(kBackSplit, o.ldR / 64);   // the GEMM's split of ldR / 64 K tiles
-            lfb_weights_kernel<<<(kHid * 16 + kHid * kHid + 255) / 256, 256, 0, t->st>>>(
+            lfb_weights_kernel<<<(kHid * 16 + kHid * kHid + 255) / 256, 256, 0, sg>>>(
                 br[g].theta + (size_t)n * P, F, o.w1b, o.w2t);
-            lfb_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, t->st>>>(br[g], o, n);
-            lfb_pad_kernel<<<16 + kHid + 1, 128, 0, t->st>>>(o, R);
+            lfb_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, sg>>>(br[g], o, n);
+            lfb_pad_kernel<<<16 + kHid + 1, 128, 0, sg>>>(o, R);
             e = cudaGetLastError();
             // dH1^T = (dZ2 W2)^T on the tensor cores; H1^T and dZ1^T
             if (e == cudaSuccess)
-                e = back_gemm(t, o.dz2, o.w2t, R, kHid, kHid, SF_ACT_NONE, o.dh1t, o.ldR, nullptr, 1, kHid, 128);
+                e = back_gemm(t, sg, o.dz2, o.w2t, R, kHid, kHid, SF_ACT_NONE, o.dh1t, o.ldR, nullptr, 1, kHid, 128);
             if (e == cudaSuccess) {
-                lfb_h1dz1_kernel<<<(unsigned)((o.ldR / 2 + 255) / 256), 256, 0, t->st>>>(o, R);
+                lfb_h1dz1_kernel<<<(unsigned)((o.ldR / 2 + 255) / 256), 256, 0, sg>>>(o, R);
                 e = cudaGetLastError();
             }
             // [dW2 | db2] = dZ2^T [H1 | 1]; [dW1 | . | db1] = dZ1^T X (K: the rows, split)
             if (e == cudaSuccess)
-                e = back_gemm(t, o.dz2t, o.h1t, kHid, kHid + 1, o.ldR, SF_ACT_NONE, nullptr, 0, t->ws2, S, kLdW2, 128);
+                e = back_gemm(t, sg, o.dz2t, o.h1t, kHid, kHid + 1, o.ldR, SF_ACT_NONE, nullptr, 0, ws2, S, kLdW2, 128);
             if (e == cudaSuccess)
-                e = back_gemm(t, o.dz1t, o.xt, kHid, 16, o.ldR, SF_ACT_NONE, nullptr, 0, t->ws1, S, 16, 64);
+                e = back_gemm(t, sg, o.dz1t, o.xt, kHid, 16, o.ldR, SF_ACT_NONE, nullptr, 0, ws1, S, 16, 64);
             if (e == cudaSuccess) {
-                lfb_reduce_kernel<<<(unsigned)((P + 255) / 256), 256, 0, t->st>>>(t->ws1, S, t->ws2, S, F, gout);
+                lfb_reduce_kernel<<<(unsigned)((P + 255) / 256), 256, 0, sg>>>(ws1, S, ws2, S, F, gout);
                 e = cudaGetLastError();
             }
         }
+    if (e == cudaSuccess && !lft_join(t)) e = cudaErrorUnknown;
     return e == cudaSuccess ? SF_OK
                             : tfail(t, SF_ERR_CUDA, std::string("late-fusion backward: ") + cudaGetErrorString(e));
 }
