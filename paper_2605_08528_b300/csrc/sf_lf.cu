@@ -831,7 +831,7 @@ struct sf_lf {
     // activations (grown on demand)
     int cap = 0;
     __nv_bfloat16 *xego = nullptr, *he1[2] = {nullptr, nullptr}, *x[2] = {nullptr, nullptr};
-    __nv_bfloat16 *t1 = nullptr, *t2 = nullptr, *t1c = nullptr;   // trunk layer 1 outputs (actor, critic)
+    __nv_bfloat16 *t1 = nullptr, *t1c = nullptr;   // trunk layer 1 outputs (actor, critic)
     unsigned* d_err = nullptr;
     // the critic's ego and trunk GEMM chains run beside the actor's on a second stream
     // (forked from and joined back to the caller's stream by events; parallel branches
@@ -919,7 +919,7 @@ sf_status ensure(sf_lf* m, int A) {
     bool okk = lalloc(m, &m->xego, Aa * 16, true) && lalloc(m, &m->he1[0], Aa * 64, true) &&
                lalloc(m, &m->he1[1], Aa * 64, true) && lalloc(m, &m->x[0], Aa * 256, true) &&
                lalloc(m, &m->x[1], Aa * 256, true) && lalloc(m, &m->t1, Aa * 128, true) &&
-               lalloc(m, &m->t2, Aa * 64, true) && lalloc(m, &m->t1c, Aa * 128, true);
+               lalloc(m, &m->t1c, Aa * 128, true);
     if (!okk) return lfail(m, SF_ERR_OOM, "sf_lf_forward: cudaMalloc of the activations failed");
     m->cap = A;
     return SF_OK;
