@@ -58,3 +58,29 @@ def test_weather_model_is_validated_before_any_device_call():
     with pytest.raises(sf.SFError) as e:
         sf.sf_create(weather_model=2)
     assert e.value.status == sf.SF_ERR_INVALID_ARG
+
+
+def test_metrics_struct_layout_matches_the_header(tmp_path):
+    """The ctypes sf_metrics has the size and field offsets of the C struct (compiled here)."""
+    import ctypes
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    fields = [n for n, _ in sf.sf_metrics._fields_]
+    prog = tmp_path / "m.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "sf.h"\nint main(void) {\n'
+                    '  printf("%zu", sizeof(sf_metrics));\n' +
+                    "".join('  printf(" %%zu", offsetof(sf_metrics, %s));\n' % n for n in fields) +
+                    "  return 0;\n}\n")
+    exe = tmp_path / "m"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(sf.sf_metrics)
+    assert out[1:] == [getattr(sf.sf_metrics, n).offset for n in fields]
+
+
+def test_metrics_calls_reject_a_null_handle():
+    L = sf.lib()
+    assert L.sf_get_metrics(None, None) == sf.SF_ERR_INVALID_ARG
+    assert L.sf_reset_metrics(None) == sf.SF_ERR_INVALID_ARG
