@@ -60,24 +60,28 @@ def test_weather_model_is_validated_before_any_device_call():
     assert e.value.status == sf.SF_ERR_INVALID_ARG
 
 
-def test_metrics_struct_layout_matches_the_header(tmp_path):
-    """The ctypes sf_metrics has the size and field offsets of the C struct (compiled here)."""
+@pytest.mark.parametrize("name", ["sf_config", "sf_roads", "sf_outputs", "sf_metrics", "sf_lf_outputs",
+                                  "sf_ppo_config", "sf_ppo_rollout"])
+def test_struct_layout_matches_the_header(tmp_path, name):
+    """Each ctypes mirror of a C struct of include/sf.h has the C struct's size and
+    field offsets (a small C program compiled here prints them)."""
     import ctypes
     import shutil
     import subprocess
     if shutil.which("gcc") is None:
         pytest.skip("no C compiler")
-    fields = [n for n, _ in sf.sf_metrics._fields_]
+    S = getattr(sf, name)
+    fields = [n for n, *_ in S._fields_]
     prog = tmp_path / "m.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "sf.h"\nint main(void) {\n'
-                    '  printf("%zu", sizeof(sf_metrics));\n' +
-                    "".join('  printf(" %%zu", offsetof(sf_metrics, %s));\n' % n for n in fields) +
+                    '  printf("%%zu", sizeof(%s));\n' % name +
+                    "".join('  printf(" %%zu", offsetof(%s, %s));\n' % (name, n) for n in fields) +
                     "  return 0;\n}\n")
     exe = tmp_path / "m"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     out = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
-    assert out[0] == ctypes.sizeof(sf.sf_metrics)
-    assert out[1:] == [getattr(sf.sf_metrics, n).offset for n in fields]
+    assert out[0] == ctypes.sizeof(S)
+    assert out[1:] == [getattr(S, n).offset for n in fields]
 
 
 def test_metrics_calls_reject_a_null_handle():
