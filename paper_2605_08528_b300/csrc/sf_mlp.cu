@@ -782,18 +782,29 @@ sf_status sf_mlp_train_step(sf_mlp_handle m, const float* d_x, const float* d_t,
 
 }  // extern "C"
 
-sf_status sf_mlp_forward_train_on(sf_mlp_handle m, cudaStream_t st, const float* d_x, int ldx, int batch, float* d_y,
-                                  int ldy) {
-    if (!m || !d_x || !d_y || batch < 8 || batch % 8 != 0 || ldx < m->dim[0] || ldy < m->dim[m->L])
-        return SF_ERR_INVALID_ARG;
+sf_status sf_mlp_convert_train_on(sf_mlp_handle m, cudaStream_t st, const float* d_x, int ldx, int batch) {
+    if (!m || !d_x || batch < 8 || batch % 8 != 0 || ldx < m->dim[0]) return SF_ERR_INVALID_ARG;
     cudaError_t e = ensure_batch(m, batch);
     if (e != cudaSuccess) return mfail(m, SF_ERR_OOM, "batch buffers");
     m->share = nullptr;
     to_bf16_kernel<<<tgrid(batch, m->ld[0]), kTBlock, 0, st>>>(d_x, batch, m->dim[0], ldx, m->x[0], m->ld[0],
                                                                     m->xt[0]);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = forward_core(m, batch, true, d_y, ldy, st, true);
     return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("forward_train: ") + cudaGetErrorString(e));
+}
+
+sf_status sf_mlp_forward_converted_on(sf_mlp_handle m, cudaStream_t st, int batch, float* d_y, int ldy) {
+    if (!m || !d_y || batch < 8 || batch % 8 != 0 || batch > m->cap || ldy < m->dim[m->L]) return SF_ERR_INVALID_ARG;
+    const cudaError_t e = forward_core(m, batch, true, d_y, ldy, st, true);
+    return e == cudaSuccess ? SF_OK : mfail(m, SF_ERR_CUDA, std::string("forward_train: ") + cudaGetErrorString(e));
+}
+
+sf_status sf_mlp_forward_train_on(sf_mlp_handle m, cudaStream_t st, const float* d_x, int ldx, int batch, float* d_y,
+                                  int ldy) {
+    if (!m || !d_x || !d_y || batch < 8 || batch % 8 != 0 || ldx < m->dim[0] || ldy < m->dim[m->L])
+        return SF_ERR_INVALID_ARG;
+    const sf_status s = sf_mlp_convert_train_on(m, st, d_x, ldx, batch);
+    return s == SF_OK ? sf_mlp_forward_converted_on(m, st, batch, d_y, ldy) : s;
 }
 
 void sf_mlp_end_share(sf_mlp_handle m) {

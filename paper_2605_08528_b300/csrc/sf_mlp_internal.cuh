@@ -19,6 +19,10 @@ sf_status sf_lf_forward_on(sf_lf_handle m, cudaStream_t stream, const float* d_o
 // forward of `batch` rows keeping the activations the backward needs; outputs d_y [batch][ldy]
 sf_status sf_mlp_forward_train_on(sf_mlp_handle m, cudaStream_t stream, const float* d_x, int ldx, int batch,
                                   float* d_y, int ldy);
+// the same in two parts: the input converted into m's bf16 copies (and their transpose), then
+// the forward on them (another network may read the converted input meanwhile, as below)
+sf_status sf_mlp_convert_train_on(sf_mlp_handle m, cudaStream_t stream, const float* d_x, int ldx, int batch);
+sf_status sf_mlp_forward_converted_on(sf_mlp_handle m, cudaStream_t stream, int batch, float* d_y, int ldy);
 // the same on the input src's last training forward converted (same input width): m's layer 0
 // reads src's bf16 copies, which must stay unchanged until m's backward has run
 sf_status sf_mlp_forward_train_shared_on(sf_mlp_handle m, sf_mlp_handle src, cudaStream_t stream, int batch,

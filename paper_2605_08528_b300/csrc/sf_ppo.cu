@@ -369,9 +369,16 @@ sf_status nets_infer(sf_ppo* p, const float* obs, const int32_t* nr, const int32
 }
 sf_status nets_train_forward(sf_ppo* p, int B) {
     if (p->lft) return lft_forward(p->lft, p->g_obs, p->g_nr, p->g_nv, B, p->mu_new, p->v_new);
-    // the critic reads the actor's bf16 copy of the minibatch (converted once)
-    sf_status s = sf_mlp_forward_train_on(p->actor, p->st, p->g_obs, kObsW, B, p->mu_new, 3);
-    if (s == SF_OK) s = sf_mlp_forward_train_shared_on(p->critic, p->actor, p->st, B, p->v_new, 1);
+    // the critic reads the actor's bf16 copy of the minibatch (converted once); the two
+    // forwards then run side by side (the critic's on aux)
+    sf_status s = sf_mlp_convert_train_on(p->actor, p->st, p->g_obs, kObsW, B);
+    const bool fork = s == SF_OK && p->aux != nullptr;
+    if (fork && (cudaEventRecord(p->ev[0], p->st) != cudaSuccess || cudaStreamWaitEvent(p->aux, p->ev[0], 0) != cudaSuccess))
+        return SF_ERR_CUDA;
+    if (s == SF_OK) s = sf_mlp_forward_converted_on(p->actor, p->st, B, p->mu_new, 3);
+    if (s == SF_OK) s = sf_mlp_forward_train_shared_on(p->critic, p->actor, fork ? p->aux : p->st, B, p->v_new, 1);
+    if (fork && (cudaEventRecord(p->ev[1], p->aux) != cudaSuccess || cudaStreamWaitEvent(p->st, p->ev[1], 0) != cudaSuccess))
+        return SF_ERR_CUDA;
     return s;
 }
 sf_status nets_backward(sf_ppo* p, int B) {
